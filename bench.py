@@ -1,0 +1,338 @@
+"""Benchmark of the GB300 fast direct solver.
+
+One step = the whole hot path for one cavity: factorisation (cell circles,
+near field, Galerkin kernel evaluation of leaf blocks and proxy/near rows,
+CPQR interpolative decomposition, LU-based merges, top LU), the Galerkin load
+vectors of all incident waves, and the multi-RHS solve sweep.
+
+Default workload (the configuration the metric is quoted on): star cavity
+r(t) = 1 + 0.2 cos 5t with 2^19 nodes (2^20 complex unknowns), lambda = 2,
+mu = 1, rho = 1, k_T a = 20, leaf 64, l0 = 1, 1000 right-hand sides (plane P
+and SV waves at 500 angles), plain FP64.  The working set (factors, vectors)
+is far larger than L2, so no explicit flush is needed between steps.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank solves its own (rotated) copy of the cavity; there is
+no collective in the data path, only a MAX reduction of the timings.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "build s + per-RHS µs at N=2^20, mixed/learned vs plain FP64, rel err ≤1e-6"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--nodes", type=int, default=1 << 19)
+    p.add_argument("--kta", type=float, default=20.0)
+    p.add_argument("--nrhs", type=int, default=1000)
+    p.add_argument("--eps", type=float, default=1e-9)
+    p.add_argument("--leaf", type=int, default=64)
+    p.add_argument("--top", type=int, default=1)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(args, rank):
+    import workloads
+    xy = workloads.star(args.nodes, 0.2, 5, rot=0.013 * rank)
+    omega = workloads.omega_for_kTa(args.kta)
+    kinds, angles = workloads.plane_wave_set(args.nrhs // 2)
+    return xy, omega, kinds, angles
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                v = [x.strip() for x in line.split(",")]
+                if len(v) < 9:
+                    continue
+                try:
+                    rows.append(dict(sm=float(v[1]), smax=float(v[2]), hw=v[5], hwt=v[6], swt=v[7], pcap=v[8]))
+                except ValueError:
+                    continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = sorted(r["sm"] for r in rows)
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                            ("pcap", "sw_power_cap")):
+                if r[k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": rows[0]["smax"], "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------- oracle (CPU)
+def oracle_sample(args, n_sample, nrhs_sample):
+    """Time the oracle ('Conv': dense Galerkin assembly + LU + back substitution)
+    on the same cavity shape and frequency with n_sample nodes; extrapolate to
+    the full job as O(N^2) assembly + O(N^3) LU + O(N^2) per right-hand side."""
+    import workloads
+    from oracle import bem
+    xy = workloads.star(n_sample, 0.2, 5)
+    omega = workloads.omega_for_kTa(args.kta)
+    P = bem.phys(2.0, 1.0, 1.0, omega)
+    t0 = time.perf_counter()
+    A = bem.dense_matrix(P, xy)
+    t1 = time.perf_counter()
+    import scipy.linalg as sl
+    lu = sl.lu_factor(A, check_finite=False)
+    t2 = time.perf_counter()
+    F = np.stack([bem.rhs(P, xy, k % 2, 0.1 * k) for k in range(nrhs_sample)], 1)
+    t3 = time.perf_counter()
+    sl.lu_solve(lu, F, check_finite=False)
+    t4 = time.perf_counter()
+    s = args.nodes / n_sample
+    t_asm, t_lu, t_rhs = t1 - t0, t2 - t1, (t4 - t2) / nrhs_sample
+    full = t_asm * s ** 2 + t_lu * s ** 3 + args.nrhs * t_rhs * s ** 2
+    return dict(full_s=full, t_asm=t_asm, t_lu=t_lu, t_per_rhs=t_rhs, wall=t4 - t0,
+                sample="star 1+0.2cos5t, %d nodes (%d unknowns), k_T a=%g, dense assembly %.2fs + LU %.2fs + "
+                       "%d RHS %.3fs; extrapolated to %d nodes x %d RHS by O(N^2) assembly, O(N^3) LU, "
+                       "O(N^2) per RHS" % (n_sample, 2 * n_sample, args.kta, t_asm, t_lu, nrhs_sample,
+                                           t4 - t3 + (t3 - t2), args.nodes, args.nrhs))
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return
+    from oracle import build as ob
+    ob.build()
+    cores = os.cpu_count()
+    n_s = 384
+    for _ in range(args.warmup):
+        oracle_sample(args, n_s, 4)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = oracle_sample(args, n_s, 4)
+        vals.append(last["full_s"])
+    wall = time.perf_counter() - t0
+    v = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(args.steps, 1),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic",
+            "config": {"workload": "star r=1+0.2cos5t, %d nodes (2^20 unknowns), k_T a=%g, %d plane P/SV waves"
+                                   % (args.nodes, args.kta, args.nrhs), "kind": "oracle dense Galerkin + LU (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": last["sample"]},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- ours
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    world, rank, local = dist_setup()
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2411_18026_gb300 import fds
+
+    xy, omega, kinds, angles = workload(args, rank)
+    N = len(xy)
+    stream = torch.cuda.current_stream()
+    d_kinds = torch.from_numpy(kinds).cuda()
+    d_angles = torch.from_numpy(angles).cuda()
+    d_F = torch.empty((args.nrhs, 2 * N), dtype=torch.complex128, device="cuda")
+
+    info = {}
+
+    def step():
+        h = fds.fds_build(xy, omega, 2.0, 1.0, args.eps, leaf_size=args.leaf, top_level=args.top, stream=stream)
+        fds.fds_rhs_plane_wave_device(h, d_kinds, d_angles, d_F, stream)
+        fds.fds_solve_device(h, d_F, stream)
+        st = fds.fds_stats_get(h)
+        info["build_ms"], info["solve_ms"] = st.build_ms, st.solve_ms
+        info["top_size"], info["levels"] = st.top_size, st.levels
+        info["factor_gb"] = st.factor_bytes / 1e9
+        info["skeleton_dofs"] = [int(st.skeleton_dofs[l]) for l in range(st.levels + 1)]
+        h.close()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    fds.fds_timing_reset()
+    fds.fds_timing_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = fds.fds_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    builds, solves = [], []
+    for _ in range(args.steps):
+        step()
+        builds.append(info["build_ms"])
+        solves.append(info["solve_ms"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = (fds.fds_launch_count() - launches0) // args.steps
+    clk = clocks.stop()
+    fds.fds_timing_enable(False)
+    phases = fds.fds_timing_report()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the host-buffer C ABI: geometry and right-hand sides
+    # from pinned host memory, solution back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        F_host = torch.empty((args.nrhs, 2 * N), dtype=torch.complex128, pin_memory=True)
+        F_host.copy_(d_F)     # (values are irrelevant for timing; any RHS of the right size)
+        F_np = F_host.numpy()
+        xy_host = torch.from_numpy(np.ascontiguousarray(xy)).pin_memory().numpy()
+        import ctypes
+        L = fds.lib()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g_ = fds.fds_geometry(N, xy_host.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1.0)
+        o = fds.default_options()
+        o.leaf_size, o.top_level = args.leaf, args.top
+        out = ctypes.c_void_p()
+        rc = L.fds_build_ex(ctypes.byref(g_), float(omega), 2.0, 1.0, float(args.eps), ctypes.byref(o),
+                            ctypes.byref(out))
+        assert rc == 0, rc
+        rc = L.fds_solve(out, F_np.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double)), args.nrhs)
+        assert rc == 0, rc
+        L.fds_destroy(out)
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": t_e2e * world / world, "unit": "s", "h2d_bytes_per_step": int(xy_host.nbytes + F_np.nbytes),
+               "d2h_bytes_per_step": int(F_np.nbytes)}
+        del F_host
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    pk, src = peaks()
+    sm_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    # FP64 peak of the GB300: 152 SMs x 2 FP64 FMA/clk (4 flops) x SM clock
+    fp64_peak_tflops = 152 * 4 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    dom = max(phases.items(), key=lambda kv: kv[1]["ms"]) if phases else None
+    roof = None
+    if dom:
+        name, d = dom
+        avg_ms = d["ms"] / max(d["launches"], 1)
+        if d["flops"] > 0:
+            ach = d["flops"] / max(d["launches"], 1) / (avg_ms / 1e3) / 1e12
+            roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                    "frac": ach / fp64_peak_tflops, "traffic": None,
+                    "peak_source": "FP64 152 SM x 4 flop/clk x %.0f MHz (max clock)" % pk.get("sm_max_mhz", 2070.0),
+                    "avg_launch_ms": avg_ms, "launches_per_step": d["launches"] / args.steps}
+        else:
+            roof = {"kernel": name, "bound": "alu", "achieved": None, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                    "frac": None, "traffic": None, "avg_launch_ms": avg_ms,
+                    "launches_per_step": d["launches"] / args.steps,
+                    "note": "quadrature phase: see the profiles summary for its FP64 instruction rate"}
+
+    cpu = None
+    if not args.no_cpu:
+        from oracle import build as ob
+        ob.build()
+        smp = oracle_sample(args, 1024, 8)
+        cpu = {"value": smp["full_s"], "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": smp["sample"]}
+    build_s = float(np.median(builds)) / 1e3
+    per_rhs_us = float(np.median(solves)) * 1e3 / args.nrhs
+    line = {
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": "star r=1+0.2cos5t, %d nodes (%d complex unknowns), lambda=2 mu=1 rho=1, "
+                               "k_T a=%g, leaf %d, l0=%d, eps=%g, %d plane P/SV waves, plain FP64"
+                               % (N, 2 * N, args.kta, args.leaf, args.top, args.eps, args.nrhs),
+                   "l2": "working set (factors, vectors) larger than L2; no flush",
+                   "precision": "fp64"},
+        "build_s": build_s, "per_rhs_us": per_rhs_us,
+        "levels": info.get("levels"), "top_size": info.get("top_size"), "factor_gb": info.get("factor_gb"),
+        "skeleton_dofs": info.get("skeleton_dofs"),
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+        "phases_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in sorted(phases.items())},
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

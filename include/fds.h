@@ -1,0 +1,207 @@
+/*
+ * fds.h — C ABI of the GB300 (sm_103a) fast direct solver for 2D time-harmonic
+ * elastic wave scattering by a traction-free cavity, after arXiv 2411.18026.
+ *
+ * The solver factors the Galerkin P1 Burton–Miller system A x = f of Sec. 4
+ * (A = D + I_0/2 + alpha N, eq. (Aijpq) and the blocks defined with it) with
+ * the proxy-surface compression of Sec. 7 and the LU-based variant of the
+ * Martinsson–Rokhlin solver of Sec. 6, then solves for any number of
+ * right-hand sides.  Every step runs in this library's CUDA kernels on one GPU.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: FDS_OK (0) on success, a negative FDS_ERR_* code otherwise;
+ *     fds_error_string() names it.  No C++ exception crosses the ABI.
+ *   - Complex numbers are two adjacent doubles (re, im), i.e. C99
+ *     double _Complex / cuDoubleComplex layout.
+ *   - Geometry: a closed polygon with n nodes, coordinates interleaved
+ *     (x0, y0, x1, y1, ...), nodes counter-clockwise around the cavity so the
+ *     element normal (tangent rotated by +90 degrees) points into the cavity,
+ *     the orientation Sec. 2 prescribes.  Element e joins node e to e+1 mod n.
+ *   - Unknown layout (eq. (discre_x) applied to the whole vector): entry s is
+ *     component 1 of the displacement at node s, entry n + s component 2.
+ *     Multi-RHS arrays are column-major, 2n rows, one column per right-hand side.
+ *   - Host pointers are read (or written) during the call only and stay owned
+ *     by the caller.  Device pointers (d_ prefix) must be device-accessible
+ *     memory of the current device; the call enqueues work on the given stream
+ *     and returns without synchronising unless stated.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef FDS_H
+#define FDS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDS_OK                 0
+#define FDS_ERR_ARG           -1  /* invalid argument (null pointer, size, option) */
+#define FDS_ERR_CUDA          -2  /* a CUDA runtime call failed */
+#define FDS_ERR_OOM           -3  /* device allocation failed */
+#define FDS_ERR_SINGULAR      -4  /* zero or non-finite pivot in a box LU, S_i or the top LU */
+#define FDS_ERR_NOT_CONVERGED -5  /* iterative refinement did not reach its target */
+#define FDS_ERR_TIMEOUT       -6  /* a device-side wait exceeded its iteration budget */
+#define FDS_ERR_STATE         -7  /* handle not in a state that allows the call */
+
+#define FDS_FP64  0               /* all arithmetic in FP64 / complex128 */
+
+typedef struct fds_handle fds_handle;   /* opaque; owns all device memory of one factorisation */
+
+/* Material and frequency (Sec. 2): Lame constants lambda, mu, density rho,
+ * angular frequency omega.  Burton–Miller coupling alpha (eq. (bie)); when
+ * alpha_set == 0 the library uses alpha = i / (mu k_T), k_T = omega sqrt(rho/mu). */
+typedef struct {
+    double lambda, mu, rho, omega;
+    double alpha_re, alpha_im;
+    int32_t alpha_set;
+} fds_physics;
+
+typedef struct {
+    int32_t n_nodes;       /* number of polygon nodes = number of elements, >= 8 */
+    const double *xy;      /* host, 2*n_nodes doubles, see conventions */
+    double rho;            /* density; <= 0 means 1 */
+} fds_geometry;
+
+typedef struct {
+    int32_t leaf_size;     /* maximum nodes per leaf cell n (Sec. 5.1); default 64 */
+    double proxy_ratio;    /* proxy circle radius / cell radius (Sec. 7.1); default 1.5 */
+    int32_t proxy_points;  /* minimum proxy polygon vertices m'; default 64; the library
+                              uses max(proxy_points, ceil(2 k_T R_proxy + 30)) */
+    int32_t top_level;     /* level l0 of the dense top solve (Sec. 7.3); default 1 */
+    int32_t precision;     /* FDS_FP64 */
+    double alpha_re, alpha_im;
+    int32_t alpha_set;     /* 0: alpha = i/(mu k_T) */
+    uint64_t cuda_stream;  /* cudaStream_t for the build; 0 = legacy default stream */
+} fds_options;
+
+/* Statistics of a built handle. */
+typedef struct {
+    int32_t n_nodes, levels, top_level, top_size;
+    int64_t skeleton_dofs[32];   /* sum of ranks k^1 + k^2 over the cells of level l */
+    int32_t max_rank[32];        /* largest k^1 + k^2 of a cell at level l */
+    double build_ms;             /* device time of the last fds_build (CUDA events) */
+    double solve_ms;             /* device time of the last fds_solve*/
+    int64_t factor_bytes;        /* device bytes held by the factors */
+} fds_stats;
+
+/* Fill *o with the defaults listed above. */
+void fds_default_options(fds_options *o);
+
+/*
+ * Build: geometry + tree (Sec. 5.1), then for l = L .. l0+1 the proxy
+ * compression of Sec. 7 (kernel evaluation, interpolative decomposition by
+ * column-pivoted QR with relative tolerance tol), the upward elimination of
+ * Sec. 6.2 (LU of A_i, A_i^{-1} U_i, A~_i = (V_i A_i^{-1} U_i)^{-1}) and the
+ * parent rearrangement of eq. (A_rearrangement); finally the dense LU of the
+ * level-l0 system (Sec. 6.3).  omega > 0, lambda > -mu (so lambda+2mu > 0),
+ * mu > 0, 0 <= tol < 1.  On success *out receives a new handle.
+ */
+int fds_build(const fds_geometry *g, double omega, double lambda, double mu, double tol,
+              fds_handle **out);
+int fds_build_ex(const fds_geometry *g, double omega, double lambda, double mu, double tol,
+                 const fds_options *opt, fds_handle **out);
+
+/*
+ * Galerkin load vectors f^s_i = int psi^s (u^I_i + alpha T^{n_x}_ij u^I_j) ds
+ * (Sec. 4) for plane waves of direction d = (cos a, sin a): kinds[r] = 0 is a
+ * P wave u^I = d exp(i k_L d.x), 1 an SV wave u^I = d_perp exp(i k_T d.x),
+ * d_perp = (-d_2, d_1).  f_out: host, 2n x nrhs complex, column-major.
+ */
+int fds_rhs_plane_wave(fds_handle *h, const int32_t *kinds, const double *angles, int32_t nrhs,
+                       double *f_out);
+/* Same on the device: d_kinds, d_angles, d_f device arrays; enqueued on stream. */
+int fds_rhs_plane_wave_device(fds_handle *h, const int32_t *d_kinds, const double *d_angles,
+                              int32_t nrhs, double *d_f, uint64_t stream);
+
+/*
+ * Solve A x = f for nrhs right-hand sides: upward pass z_i = A_i^{-1} f_i,
+ * f~_i = A~_i V_i z_i (eq. (linear_last)), top solve, downward pass
+ * x_i = z_i - W_i (f~_i - A~_i y_i), W_i = A_i^{-1} U_i (eq. (down_comv)).
+ * fds_solve: host rhs (2n x nrhs complex, column-major), copied to the device,
+ * solved, copied back in place; synchronous.  fds_solve_device: d_rhs on the
+ * device, overwritten in place, enqueued on stream.
+ */
+int fds_solve(fds_handle *h, double *rhs, int32_t nrhs);
+int fds_solve_device(fds_handle *h, double *d_rhs, int32_t nrhs, uint64_t stream);
+
+int fds_stats_get(const fds_handle *h, fds_stats *s);
+/* Per-cell skeleton ranks of level l (L >= l > l0): k[2*i + c] for cell i,
+ * component c.  cap = capacity of k in int32 entries; returns the count or an
+ * error. */
+int fds_level_ranks(const fds_handle *h, int32_t level, int32_t *k, int32_t cap);
+void fds_destroy(fds_handle *h);   /* NULL-safe; frees every device buffer of h */
+const char *fds_error_string(int code);
+
+/*
+ * Per-phase device timing: when enabled, the library brackets its kernel
+ * launches with CUDA events on the launch stream and accumulates, per phase
+ * name, the launch count, the summed device time and the algorithmic work
+ * (flops, bytes) the phase performs.  Off by default; process-wide.
+ * fds_timing_report writes lines "name launches total_ms flops bytes" into
+ * buf (at most cap bytes, NUL-terminated) and returns the length it needs.
+ * Reporting synchronises on the recorded events.
+ */
+void fds_timing_enable(int32_t on);
+void fds_timing_reset(void);
+int fds_timing_report(char *buf, int32_t cap);
+/* Number of kernels this library has launched since it was loaded. */
+int64_t fds_launch_count(void);
+
+/* ------------------------------------------------------------------------
+ * Stage entry points: each runs one step of the hot path on caller-provided
+ * device buffers, so that it can be checked on its own.  All enqueue on
+ * `stream` and do not synchronise.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * Kernel evaluation (Sec. 4, eq. (Aijpq); singular pairs by the regularised
+ * Galerkin forms): block A(rows, cols) of the boundary matrix
+ * D + I_0/2 + alpha N between test hats d_rows[0..nr) and trial hats
+ * d_cols[0..nc) on the polygon d_xy (n nodes).  d_out: complex, column-major,
+ * (2 nr) x (2 nc), leading dimension 2 nr; row r + i nr is component i+1 of
+ * hat d_rows[r], column c + j nc component j+1 of hat d_cols[c].
+ */
+int fds_eval_entries(const fds_physics *ph, const double *d_xy, int32_t n, const int32_t *d_rows,
+                     int32_t nr, const int32_t *d_cols, int32_t nc, double *d_out, uint64_t stream);
+
+/*
+ * Proxy interaction entries (Sec. 7, eq. (mv) and the matrix M^U): D + alpha N
+ * between test hats d_rows on closed polygon X (nx nodes) and trial hats
+ * d_cols on closed polygon Y (ny nodes), fixed q x q Gauss rule per element
+ * pair (1 <= q <= 8), no mass term.  Output layout as fds_eval_entries.
+ */
+int fds_eval_cross(const fds_physics *ph, const double *d_X, int32_t nx, const int32_t *d_rows,
+                   int32_t nr, const double *d_Y, int32_t ny, const int32_t *d_cols, int32_t nc,
+                   int32_t q, double *d_out, uint64_t stream);
+
+/*
+ * Interpolative decomposition (Sec. 7.1) of a batch of complex matrices by
+ * Householder QR with column pivoting (largest remaining column 2-norm, ties to
+ * the lowest index), truncated at the first pivot with |R_jj| <= tol |R_11|.
+ * Matrix b: m[b] x n[b], column-major at d_Y + 2*off[b] doubles, leading
+ * dimension m[b]; overwritten by the QR factors.  Outputs: d_rank[b] = k,
+ * d_perm + poff[b]: the n[b] column indices in pivot order,
+ * d_T + 2*toff[b] doubles: T = R_1^{-1} R_2, k x (n-k) column-major (leading
+ * dimension k), so that Y[:, perm[k:]] ~= Y[:, perm[:k]] T.  The T slot of
+ * matrix b must hold k (n-k) <= n[b]^2/4 + 1 complex entries.
+ */
+int fds_id_batched(int32_t batch, const int32_t *d_m, const int32_t *d_n, const int64_t *d_off,
+                   double *d_Y, double tol, int32_t *d_rank, int32_t *d_perm,
+                   const int64_t *d_poff, double *d_T, const int64_t *d_toff, uint64_t stream);
+
+/*
+ * Batched LU with partial pivoting of square complex matrices (the box LU of
+ * Sec. 7.3 step 3(b) and the top LU of step 4): matrix b is d[b] x d[b],
+ * column-major at d_A + 2*off[b] doubles (leading dimension d[b]), overwritten
+ * by L (unit, below the diagonal) and U; d_piv + poff[b] receives the pivot row
+ * of each step.  d_info[b] = 0, or j+1 if the j-th pivot is zero or not finite.
+ */
+int fds_lu_batched(int32_t batch, const int32_t *d_d, const int64_t *d_off, double *d_A,
+                   int32_t *d_piv, const int64_t *d_poff, int32_t *d_info, uint64_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDS_H */

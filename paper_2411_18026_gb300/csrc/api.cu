@@ -1,0 +1,176 @@
+// C ABI of the solver (include/fds.h): argument checks, handle lifetime,
+// host<->device copies for the host-buffer entry points.
+#include <cmath>
+#include <new>
+
+#include "fds_internal.cuh"
+
+extern "C" void fds_default_options(fds_options *o) {
+    if (!o) return;
+    o->leaf_size = 64;
+    o->proxy_ratio = 1.5;
+    o->proxy_points = 64;
+    o->top_level = 1;
+    o->precision = FDS_FP64;
+    o->alpha_re = 0.0;
+    o->alpha_im = 0.0;
+    o->alpha_set = 0;
+    o->cuda_stream = 0;
+}
+
+extern "C" const char *fds_error_string(int code) {
+    switch (code) {
+        case FDS_OK: return "ok";
+        case FDS_ERR_ARG: return "invalid argument";
+        case FDS_ERR_CUDA: return "CUDA runtime error";
+        case FDS_ERR_OOM: return "device out of memory";
+        case FDS_ERR_SINGULAR: return "singular or non-finite pivot";
+        case FDS_ERR_NOT_CONVERGED: return "iterative refinement did not converge";
+        case FDS_ERR_TIMEOUT: return "device wait budget exceeded";
+        case FDS_ERR_STATE: return "handle not ready";
+        default: return "unknown error";
+    }
+}
+
+extern "C" int fds_build_ex(const fds_geometry *g, double omega, double lambda, double mu, double tol,
+                            const fds_options *opt, fds_handle **out) {
+    if (!out) return FDS_ERR_ARG;
+    *out = nullptr;
+    if (!g || !g->xy || g->n_nodes < 8) return FDS_ERR_ARG;
+    if (!(omega > 0) || !(mu > 0) || !(lambda + 2.0 * mu > 0) || !(tol >= 0.0 && tol < 1.0)) return FDS_ERR_ARG;
+    fds_options o;
+    if (opt) o = *opt;
+    else fds_default_options(&o);
+    if (o.leaf_size < 2 || !(o.proxy_ratio > 1.0) || o.proxy_points < 8 || o.top_level < 0 ||
+        o.precision != FDS_FP64)
+        return FDS_ERR_ARG;
+    for (int i = 0; i < 2 * g->n_nodes; ++i)
+        if (!std::isfinite(g->xy[i])) return FDS_ERR_ARG;
+    // the tree must fit the launch grid (cells per level <= 65535)
+    {
+        int L = 0;
+        while (((g->n_nodes + (1 << L) - 1) >> L) > o.leaf_size) ++L;
+        if (L > 15) return FDS_ERR_ARG;
+    }
+    fds_handle *h = new (std::nothrow) fds_handle();
+    if (!h) return FDS_ERR_OOM;
+    h->N = g->n_nodes;
+    h->xy.assign(g->xy, g->xy + 2 * (size_t)g->n_nodes);
+    h->ph.lambda = lambda;
+    h->ph.mu = mu;
+    h->ph.rho = g->rho > 0 ? g->rho : 1.0;
+    h->ph.omega = omega;
+    h->ph.alpha_re = o.alpha_re;
+    h->ph.alpha_im = o.alpha_im;
+    h->ph.alpha_set = o.alpha_set;
+    h->P = make_physdev(&h->ph);
+    h->tol = tol;
+    h->opt = o;
+    h->stream = (cudaStream_t)o.cuda_stream;
+    int rc = fds_build_impl(h);
+    if (rc != FDS_OK) {
+        cudaStreamSynchronize(h->stream);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return FDS_OK;
+}
+
+extern "C" int fds_build(const fds_geometry *g, double omega, double lambda, double mu, double tol,
+                         fds_handle **out) {
+    return fds_build_ex(g, omega, lambda, mu, tol, nullptr, out);
+}
+
+extern "C" int fds_rhs_plane_wave_device(fds_handle *h, const int32_t *d_kinds, const double *d_angles,
+                                         int32_t nrhs, double *d_f, uint64_t stream) {
+    if (!h || nrhs < 0) return FDS_ERR_ARG;
+    if (nrhs == 0) return FDS_OK;
+    if (!d_kinds || !d_angles || !d_f) return FDS_ERR_ARG;
+    return fds_rhs_impl(h, d_kinds, d_angles, nrhs, (cplx *)d_f, (cudaStream_t)stream);
+}
+
+extern "C" int fds_rhs_plane_wave(fds_handle *h, const int32_t *kinds, const double *angles, int32_t nrhs,
+                                  double *f_out) {
+    if (!h || nrhs < 0) return FDS_ERR_ARG;
+    if (nrhs == 0) return FDS_OK;
+    if (!kinds || !angles || !f_out) return FDS_ERR_ARG;
+    for (int j = 0; j < nrhs; ++j)
+        if (kinds[j] != 0 && kinds[j] != 1) return FDS_ERR_ARG;
+    cudaStream_t s = h->stream;
+    DBuf<int> dk;
+    DBuf<double> da;
+    DBuf<cplx> df;
+    FDS_TRY(dk.alloc(nrhs));
+    FDS_TRY(da.alloc(nrhs));
+    FDS_TRY(df.alloc((size_t)2 * h->N * nrhs));
+    FDS_CUDA_TRY(cudaMemcpyAsync(dk.p, kinds, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+    FDS_CUDA_TRY(cudaMemcpyAsync(da.p, angles, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    FDS_TRY(fds_rhs_impl(h, dk.p, da.p, nrhs, df.p, s));
+    FDS_CUDA_TRY(cudaMemcpyAsync(f_out, df.p, sizeof(cplx) * 2 * h->N * nrhs, cudaMemcpyDeviceToHost, s));
+    FDS_CUDA_TRY(cudaStreamSynchronize(s));
+    return FDS_OK;
+}
+
+extern "C" int fds_solve_device(fds_handle *h, double *d_rhs, int32_t nrhs, uint64_t stream) {
+    if (!h || nrhs < 0) return FDS_ERR_ARG;
+    if (nrhs == 0) return FDS_OK;
+    if (!d_rhs) return FDS_ERR_ARG;
+    return fds_solve_impl(h, (cplx *)d_rhs, nrhs, (cudaStream_t)stream);
+}
+
+extern "C" int fds_solve(fds_handle *h, double *rhs, int32_t nrhs) {
+    if (!h || nrhs < 0) return FDS_ERR_ARG;
+    if (nrhs == 0) return FDS_OK;
+    if (!rhs) return FDS_ERR_ARG;
+    cudaStream_t s = h->stream;
+    DBuf<cplx> d;
+    const size_t bytes = sizeof(cplx) * 2 * (size_t)h->N * nrhs;
+    FDS_TRY(d.alloc((size_t)2 * h->N * nrhs));
+    FDS_CUDA_TRY(cudaMemcpyAsync(d.p, rhs, bytes, cudaMemcpyHostToDevice, s));
+    FDS_TRY(fds_solve_impl(h, d.p, nrhs, s));
+    FDS_CUDA_TRY(cudaMemcpyAsync(rhs, d.p, bytes, cudaMemcpyDeviceToHost, s));
+    FDS_CUDA_TRY(cudaStreamSynchronize(s));
+    return FDS_OK;
+}
+
+extern "C" int fds_stats_get(const fds_handle *h, fds_stats *st) {
+    if (!h || !st) return FDS_ERR_ARG;
+    *st = fds_stats{};
+    st->n_nodes = h->N;
+    st->levels = h->L;
+    st->top_level = h->l0;
+    st->top_size = (int)h->Dtop;
+    for (int l = h->l0 + 1; l <= h->L && l < 32; ++l) {
+        const Level &C = h->lv[l];
+        int64_t sum = 0;
+        int mx = 0;
+        for (int b = 0; b < C.nb; ++b) {
+            sum += C.k1[b] + C.k2[b];
+            mx = std::max(mx, C.k1[b] + C.k2[b]);
+        }
+        st->skeleton_dofs[l] = sum;
+        st->max_rank[l] = mx;
+    }
+    st->build_ms = h->build_ms;
+    st->solve_ms = h->solve_ms;
+    st->factor_bytes = h->factor_bytes;
+    return FDS_OK;
+}
+
+extern "C" int fds_level_ranks(const fds_handle *h, int32_t level, int32_t *k, int32_t cap) {
+    if (!h || !k || level <= h->l0 || level > h->L) return FDS_ERR_ARG;
+    const Level &C = h->lv[level];
+    if (cap < 2 * C.nb) return FDS_ERR_ARG;
+    for (int b = 0; b < C.nb; ++b) {
+        k[2 * b] = C.k1[b];
+        k[2 * b + 1] = C.k2[b];
+    }
+    return 2 * C.nb;
+}
+
+extern "C" void fds_destroy(fds_handle *h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    delete h;
+}

@@ -1,0 +1,865 @@
+// Factorisation (build) of the fast direct solver, arXiv 2411.18026 Sec. 7.3:
+//   1-2  binary tree over the boundary nodes and leaf index sequences J_p (Sec. 5.1)
+//   3    for l = L .. l0+1: proxy compression (Sec. 7.1/7.2) -> U_i, V_i, J~_i;
+//        A_i^{-1} (LU), A_i^{-1} U_i, A~_i = (V_i A_i^{-1} U_i)^{-1} (Sec. 6.2);
+//        parent blocks by eq. (A_rearrangement)
+//   4    dense LU of the level-l0 system (Sec. 6.3).
+// The host plans sizes and index lists level by level; every arithmetic step
+// runs in the kernels below or in kernel_eval / id / dense.
+#include <algorithm>
+#include <cmath>
+
+#include "fds_internal.cuh"
+#include "id.cuh"
+#include "kernel_eval.cuh"
+#include "prof.cuh"
+
+namespace {
+
+using fdsk::hat_pair_cross;
+using fdsk::hat_pair_same;
+
+// ------------------------------------------------------------- geometry (a0)
+// Cell circle: centre of the bounding box of the hat supports of nodes
+// lo..hi-1 (polygon vertices lo-1..hi), radius = largest vertex distance.
+__global__ void k_box_circles(int nb, const int *__restrict__ lo, const int *__restrict__ hi,
+                              const double *__restrict__ xy, int N, double *cx, double *cy, double *R) {
+    const int b = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= nb) return;
+    const int a = lo[b] - 1, e = hi[b];
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    for (int v = a + lane; v <= e; v += 32) {
+        int s = ((v % N) + N) % N;
+        double x = xy[2 * s], y = xy[2 * s + 1];
+        xmin = fmin(xmin, x); xmax = fmax(xmax, x);
+        ymin = fmin(ymin, y); ymax = fmax(ymax, y);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        xmin = fmin(xmin, __shfl_xor_sync(0xffffffffu, xmin, o));
+        xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+        ymin = fmin(ymin, __shfl_xor_sync(0xffffffffu, ymin, o));
+        ymax = fmax(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+    }
+    const double c0 = 0.5 * (xmin + xmax), c1 = 0.5 * (ymin + ymax);
+    double r2 = 0.0;
+    for (int v = a + lane; v <= e; v += 32) {
+        int s = ((v % N) + N) % N;
+        double dx = xy[2 * s] - c0, dy = xy[2 * s + 1] - c1;
+        r2 = fmax(r2, dx * dx + dy * dy);
+    }
+    for (int o = 16; o > 0; o >>= 1) r2 = fmax(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+    if (lane == 0) {
+        cx[b] = c0;
+        cy[b] = c1;
+        R[b] = sqrt(r2);
+    }
+}
+
+// Proxy polygon of each cell: m' counter-clockwise vertices on the circle of
+// radius Rp about the cell centre (Sec. 7.1, Fig. domain_proxy).
+__global__ void k_proxy_nodes(const double *__restrict__ cx, const double *__restrict__ cy,
+                              const double *__restrict__ Rp, const int *__restrict__ m,
+                              const int64_t *__restrict__ off, double *out) {
+    const int b = blockIdx.x;
+    const int mb = m[b];
+    for (int k = threadIdx.x; k < mb; k += blockDim.x) {
+        double s, c;
+        sincospi(2.0 * k / mb, &s, &c);
+        out[2 * (off[b] + k)] = cx[b] + Rp[b] * c;
+        out[2 * (off[b] + k) + 1] = cy[b] + Rp[b] * s;
+    }
+}
+
+__device__ __forceinline__ double seg_dist(double px, double py, double ax, double ay, double bx, double by) {
+    double ux = bx - ax, uy = by - ay;
+    double t = ((px - ax) * ux + (py - ay) * uy) / (ux * ux + uy * uy);
+    t = fmin(1.0, fmax(0.0, t));
+    double dx = ax + t * ux - px, dy = ay + t * uy - py;
+    return sqrt(dx * dx + dy * dy);
+}
+
+// Near field of cell i: active nodes of the other cells of the level whose
+// hat support meets the closed proxy disk.  mode 0 counts, mode 1 fills.
+__global__ void k_near(int nb, const double *__restrict__ cx, const double *__restrict__ cy,
+                       const double *__restrict__ R, const double *__restrict__ Rp,
+                       const int64_t *__restrict__ uoff, const int *__restrict__ unode,
+                       const int *__restrict__ upos1, const int *__restrict__ upos2,
+                       const double *__restrict__ xy, int N, int mode, int *count,
+                       const int64_t *__restrict__ noff, int *nnode, int *nmask) {
+    const int i = blockIdx.x;
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const double ci0 = cx[i], ci1 = cy[i], rp = Rp[i];
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        if (j == i) continue;
+        double dx = cx[j] - ci0, dy = cy[j] - ci1;
+        if (sqrt(dx * dx + dy * dy) > rp + R[j]) continue;
+        for (int64_t u = uoff[j]; u < uoff[j + 1]; ++u) {
+            const int s = unode[u];
+            const int sp = (s == 0) ? N - 1 : s - 1, sn = (s + 1 == N) ? 0 : s + 1;
+            double d1 = seg_dist(ci0, ci1, xy[2 * sp], xy[2 * sp + 1], xy[2 * s], xy[2 * s + 1]);
+            double d2 = seg_dist(ci0, ci1, xy[2 * s], xy[2 * s + 1], xy[2 * sn], xy[2 * sn + 1]);
+            if (fmin(d1, d2) <= rp) {
+                int slot = atomicAdd(&cnt, 1);
+                if (mode == 1) {
+                    nnode[noff[i] + slot] = s;
+                    nmask[noff[i] + slot] = (upos1[u] >= 0 ? 1 : 0) | (upos2[u] >= 0 ? 2 : 0);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (mode == 0) count[i] = cnt;
+        else {
+            // deterministic order: insertion sort by node index
+            const int64_t o = noff[i];
+            for (int a = 1; a < cnt; ++a) {
+                int kn = nnode[o + a], km = nmask[o + a];
+                int p = a - 1;
+                while (p >= 0 && nnode[o + p] > kn) {
+                    nnode[o + p + 1] = nnode[o + p];
+                    nmask[o + p + 1] = nmask[o + p];
+                    --p;
+                }
+                nnode[o + p + 1] = kn;
+                nmask[o + p + 1] = km;
+            }
+        }
+    }
+}
+
+// --------------------------------------------------- ID matrices (a1 -> a2)
+struct YDesc {
+    const int64_t *yoff;     // 2 nb: offset of Y_{b,c}
+    const int *ym;           // nb: rows of Y_b (same for both components)
+    const int *mp;           // nb: proxy vertices m'
+    const int *nnd;          // nb: near DOF rows
+    const int64_t *pxoff;    // nb: proxy vertex offset
+    const double *pxy;       // proxy vertices
+    const int64_t *uoff;
+    const int *unode, *upos1, *upos2;
+    const int64_t *noff;     // nb+1 near entries
+    const int *nnode, *nmask, *nrow;
+};
+
+// Proxy rows of Y^c (Sec. 7.1 eq. (mv): M^V = A^{J' J}; Sec. 7.2: M^U = A^{J J'},
+// stacked as (M^U)^H): one warp per (cell, proxy vertex, cell node).
+__global__ void __launch_bounds__(256) k_y_proxy(PhysDev P, YDesc D, const double *__restrict__ xy, int N,
+                                                 cplx *Y) {
+    const int b = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const long job = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int mp = D.mp[b];
+    const int nu = (int)(D.uoff[b + 1] - D.uoff[b]);
+    if (job >= (long)mp * nu) return;
+    const int p = (int)(job % mp);
+    const int64_t u = D.uoff[b] + job / mp;
+    cplx f[2][2], r[2][2];
+    hat_pair_cross(P, D.pxy + 2 * D.pxoff[b], mp, p, xy, N, D.unode[u], 4, lane, f, r);
+    if (lane != 0) return;
+    const int m = D.ym[b], nnd = D.nnd[b];
+    const int pos[2] = {D.upos1[u], D.upos2[u]};
+    for (int c = 0; c < 2; ++c) {
+        if (pos[c] < 0) continue;
+        cplx *Yc = Y + D.yoff[2 * b + c] + (int64_t)pos[c] * m;
+        for (int cp = 0; cp < 2; ++cp) {
+            Yc[p + cp * mp] = f[cp][c];
+            Yc[2 * mp + nnd + p + cp * mp] = cconj(r[c][cp]);
+        }
+    }
+}
+
+// Near-field rows of Y^c: one warp per (cell, near node, cell node).
+__global__ void __launch_bounds__(256) k_y_near(PhysDev P, YDesc D, const double *__restrict__ xy, int N,
+                                                cplx *Y) {
+    const int b = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const long job = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nn = (int)(D.noff[b + 1] - D.noff[b]);
+    const int nu = (int)(D.uoff[b + 1] - D.uoff[b]);
+    if (job >= (long)nn * nu) return;
+    const int64_t k = D.noff[b] + job % nn;
+    const int64_t u = D.uoff[b] + job / nn;
+    cplx f[2][2], r[2][2];
+    hat_pair_same(P, xy, N, D.nnode[k], D.unode[u], lane, f, r);
+    if (lane != 0) return;
+    const int m = D.ym[b], nnd = D.nnd[b], mp = D.mp[b];
+    const int mask = D.nmask[k], rb = D.nrow[k];
+    const int pos[2] = {D.upos1[u], D.upos2[u]};
+    for (int c = 0; c < 2; ++c) {
+        if (pos[c] < 0) continue;
+        cplx *Yc = Y + D.yoff[2 * b + c] + (int64_t)pos[c] * m;
+        int idx = 0;
+        for (int cp = 0; cp < 2; ++cp) {
+            if (!(mask & (1 << cp))) continue;
+            Yc[2 * mp + rb + idx] = f[cp][c];
+            Yc[4 * mp + nnd + rb + idx] = cconj(r[c][cp]);
+            ++idx;
+        }
+    }
+}
+
+// Leaf diagonal blocks A_p = A^{J_p J_p} (eq. (block_ax=f)): warp per node pair
+// s <= t of the cell, producing (s,t) and (t,s) from the same quadrature points.
+__global__ void __launch_bounds__(256) k_leaf_A(PhysDev P, const int *__restrict__ lo, const int *__restrict__ hi,
+                                                const double *__restrict__ xy, int N, MatRef *A) {
+    const int b = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const long job = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int n = hi[b] - lo[b];
+    if (job >= (long)n * n) return;
+    const int si = (int)(job % n), ti = (int)(job / n);
+    if (si > ti) return;
+    cplx f[2][2], r[2][2];
+    hat_pair_same(P, xy, N, lo[b] + si, lo[b] + ti, lane, f, r);
+    if (lane != 0) return;
+    const MatRef M = A[b];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            M.p[(si + i * n) + (int64_t)(ti + j * n) * M.ld] = f[i][j];
+            if (si != ti) M.p[(ti + i * n) + (int64_t)(si + j * n) * M.ld] = r[i][j];
+        }
+}
+
+// Group blocks of original entries (sibling R blocks of eq. (A_rearrangement)
+// and the off-diagonal blocks of the top system): warp per node pair (u, v)
+// of a group with tag(u) < tag(v).
+__global__ void __launch_bounds__(256) k_group_pairs(PhysDev P, const int64_t *__restrict__ goff,
+                                                     const int *__restrict__ gnode, const int *__restrict__ gtag,
+                                                     const int *__restrict__ grow1, const int *__restrict__ grow2,
+                                                     const double *__restrict__ xy, int N, const MatRef *M) {
+    const int g = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const long job = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t o = goff[g];
+    const int nu = (int)(goff[g + 1] - o);
+    if (job >= (long)nu * nu) return;
+    const int64_t u = o + job % nu, v = o + job / nu;
+    if (!(gtag[u] < gtag[v])) return;
+    cplx f[2][2], r[2][2];
+    hat_pair_same(P, xy, N, gnode[u], gnode[v], lane, f, r);
+    if (lane != 0) return;
+    const MatRef A = M[g];
+    const int pu[2] = {grow1[u], grow2[u]}, pv[2] = {grow1[v], grow2[v]};
+    for (int i = 0; i < 2; ++i) {
+        if (pu[i] < 0) continue;
+        for (int j = 0; j < 2; ++j) {
+            if (pv[j] < 0) continue;
+            A.p[pu[i] + (int64_t)pv[j] * A.ld] = f[i][j];
+            A.p[pv[j] + (int64_t)pu[i] * A.ld] = r[j][i];
+        }
+    }
+}
+
+// V_i = blockdiag(V^1, V^2), V^c = [I T^c] P^T  (k^c x n^c), dense r x d.
+__global__ void k_make_V(const MatRef *__restrict__ Vs, const int *__restrict__ n1, const int *__restrict__ n2,
+                         const int *__restrict__ k1, const int *__restrict__ k2, const int *__restrict__ perm,
+                         const int64_t *__restrict__ poff, const cplx *__restrict__ T,
+                         const int64_t *__restrict__ toff) {
+    const int b = blockIdx.x;
+    const MatRef V = Vs[b];
+    for (int64_t e = threadIdx.x; e < (int64_t)V.rows * V.cols; e += blockDim.x)
+        V.p[(e % V.rows) + (e / V.rows) * V.ld] = mkc(0, 0);
+    __syncthreads();
+    for (int c = 0; c < 2; ++c) {
+        const int n = c ? n2[b] : n1[b], k = c ? k2[b] : k1[b];
+        const int r0 = c ? k1[b] : 0, c0 = c ? n1[b] : 0;
+        const int *pm = perm + poff[2 * b + c];
+        const cplx *Tc = T + toff[2 * b + c];
+        for (int q = threadIdx.x; q < k; q += blockDim.x) V.p[(r0 + q) + (int64_t)(c0 + pm[q]) * V.ld] = mkc(1, 0);
+        for (int64_t e = threadIdx.x; e < (int64_t)k * (n - k); e += blockDim.x) {
+            const int q = (int)(e % k), l = (int)(e / k);
+            V.p[(r0 + q) + (int64_t)(c0 + pm[k + l]) * V.ld] = Tc[q + (int64_t)l * k];
+        }
+    }
+}
+
+// W = V^H (d x r) as the right-hand side of A_i W = U_i, U_i = V_i^H.
+__global__ void k_conj_transpose(const MatRef *__restrict__ Src, const MatRef *__restrict__ Dst) {
+    const MatRef S = Src[blockIdx.x], D = Dst[blockIdx.x];
+    for (int64_t e = threadIdx.x; e < (int64_t)S.rows * S.cols; e += blockDim.x) {
+        const int i = (int)(e % S.rows), j = (int)(e / S.rows);
+        D.p[j + (int64_t)i * D.ld] = cconj(S.p[i + (int64_t)j * S.ld]);
+    }
+}
+
+__global__ void k_set_identity(const MatRef *__restrict__ Ms) {
+    const MatRef M = Ms[blockIdx.x];
+    for (int64_t e = threadIdx.x; e < (int64_t)M.rows * M.cols; e += blockDim.x) {
+        const int i = (int)(e % M.rows), j = (int)(e / M.rows);
+        M.p[i + (int64_t)j * M.ld] = mkc(i == j ? 1.0 : 0.0, 0.0);
+    }
+}
+
+__global__ void k_zero(cplx *p, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        p[e] = mkc(0, 0);
+}
+
+// Place the children's A~ blocks into the parent block (eq. (A_rearrangement)):
+// child skeleton index q -> parent row q < k1 ? pos1 + q : pos2 + (q - k1).
+__global__ void k_place_children(const MatRef *__restrict__ Atc, const int *__restrict__ k1c,
+                                 const int *__restrict__ pos1, const int *__restrict__ pos2,
+                                 const MatRef *__restrict__ Apar) {
+    const int ch = blockIdx.x;   // child index at the lower level
+    const MatRef S = Atc[ch], D = Apar[ch >> 1];
+    const int k1 = k1c[ch], p1 = pos1[ch], p2 = pos2[ch];
+    for (int64_t e = threadIdx.x; e < (int64_t)S.rows * S.cols; e += blockDim.x) {
+        const int i = (int)(e % S.rows), j = (int)(e / S.rows);
+        const int pi = i < k1 ? p1 + i : p2 + (i - k1);
+        const int pj = j < k1 ? p1 + j : p2 + (j - k1);
+        D.p[pi + (int64_t)pj * D.ld] = S.p[i + (int64_t)j * S.ld];
+    }
+}
+
+// Copy diagonal blocks of the top level into the top matrix.
+__global__ void k_place_top(const MatRef *__restrict__ Ab, const int64_t *__restrict__ doff, MatRef top) {
+    const int b = blockIdx.x;
+    const MatRef S = Ab[b];
+    const int64_t o = doff[b];
+    for (int64_t e = threadIdx.x; e < (int64_t)S.rows * S.cols; e += blockDim.x) {
+        const int i = (int)(e % S.rows), j = (int)(e / S.rows);
+        top.p[(o + i) + (o + j) * top.ld] = S.p[i + (int64_t)j * S.ld];
+    }
+}
+
+int sync_check(cudaStream_t s) {
+    FDS_CUDA_TRY(cudaStreamSynchronize(s));
+    FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
+}
+
+template <class T>
+int d2h(std::vector<T> &h, const T *d, size_t n, cudaStream_t s) {
+    h.resize(n);
+    if (n) FDS_CUDA_TRY(cudaMemcpyAsync(h.data(), d, n * sizeof(T), cudaMemcpyDeviceToHost, s));
+    return FDS_OK;
+}
+
+// Fill per-cell MatRefs for a level buffer with square/rect blocks.
+int make_refs(DBuf<MatRef> &dst, cplx *base, const std::vector<int64_t> &off, const std::vector<int> &rows,
+              const std::vector<int> &cols, cudaStream_t s) {
+    std::vector<MatRef> h(rows.size());
+    for (size_t b = 0; b < rows.size(); ++b) {
+        h[b].p = base + off[b];
+        h[b].rows = rows[b];
+        h[b].cols = cols[b];
+        h[b].ld = std::max(rows[b], 1);
+    }
+    return dst.upload(h, s);
+}
+
+// Build the union node list of a level from its per-component DOF lists.
+void build_union(Level &L) {
+    L.uoff.assign(L.nb + 1, 0);
+    L.unode.clear(); L.upos1.clear(); L.upos2.clear(); L.utag.clear();
+    for (int b = 0; b < L.nb; ++b) {
+        const int *d = L.dof_node.data() + L.doff[b];
+        std::vector<std::pair<int, int>> items;   // (node, comp/pos code)
+        std::vector<int> nodes;
+        for (int q = 0; q < L.n1[b]; ++q) nodes.push_back(d[q]);
+        for (int q = 0; q < L.n2[b]; ++q) nodes.push_back(d[L.n1[b] + q]);
+        std::vector<int> uniq = nodes;
+        std::sort(uniq.begin(), uniq.end());
+        uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+        std::vector<int> p1(uniq.size(), -1), p2(uniq.size(), -1);
+        for (int q = 0; q < L.n1[b]; ++q) {
+            size_t k = std::lower_bound(uniq.begin(), uniq.end(), d[q]) - uniq.begin();
+            p1[k] = q;
+        }
+        for (int q = 0; q < L.n2[b]; ++q) {
+            size_t k = std::lower_bound(uniq.begin(), uniq.end(), d[L.n1[b] + q]) - uniq.begin();
+            p2[k] = q;
+        }
+        for (size_t k = 0; k < uniq.size(); ++k) {
+            L.unode.push_back(uniq[k]);
+            L.upos1.push_back(p1[k]);
+            L.upos2.push_back(p2[k]);
+            L.utag.push_back(0);
+        }
+        L.uoff[b + 1] = (int64_t)L.unode.size();
+    }
+}
+
+void finish_offsets(Level &L) {
+    L.doff.assign(L.nb + 1, 0);
+    L.dmax = 0;
+    for (int b = 0; b < L.nb; ++b) {
+        L.doff[b + 1] = L.doff[b] + L.n1[b] + L.n2[b];
+        L.dmax = std::max(L.dmax, L.n1[b] + L.n2[b]);
+    }
+    L.D = L.doff[L.nb];
+}
+
+// Matrices A_b (d x d) of a level, allocated contiguously.
+int alloc_level_A(Level &L, cudaStream_t s) {
+    L.offA.assign(L.nb + 1, 0);
+    std::vector<int> d(L.nb);
+    for (int b = 0; b < L.nb; ++b) {
+        d[b] = L.n1[b] + L.n2[b];
+        L.offA[b + 1] = L.offA[b] + (int64_t)d[b] * d[b];
+    }
+    FDS_TRY(L.LU.alloc(L.offA[L.nb]));
+    FDS_TRY(make_refs(L.rLU, L.LU.p, L.offA, d, d, s));
+    return FDS_OK;
+}
+
+int launch_group_pairs(fds_handle *h, const std::vector<int64_t> &goff, const std::vector<int> &gnode,
+                       const std::vector<int> &gtag, const std::vector<int> &grow1, const std::vector<int> &grow2,
+                       const MatRef *d_M, cudaStream_t s) {
+    const int ng = (int)goff.size() - 1;
+    if (ng <= 0 || gnode.empty()) return FDS_OK;
+    DBuf<int64_t> d_goff;
+    DBuf<int> d_gnode, d_gtag, d_g1, d_g2;
+    FDS_TRY(d_goff.upload(goff, s));
+    FDS_TRY(d_gnode.upload(gnode, s));
+    FDS_TRY(d_gtag.upload(gtag, s));
+    FDS_TRY(d_g1.upload(grow1, s));
+    FDS_TRY(d_g2.upload(grow2, s));
+    int64_t maxnu = 0;
+    for (int g = 0; g < ng; ++g) maxnu = std::max(maxnu, goff[g + 1] - goff[g]);
+    dim3 grid(ceil_div_u(maxnu * maxnu * 32, 256), ng);
+    fds_count_launch(), k_group_pairs<<<grid, 256, 0, s>>>(h->P, d_goff.p, d_gnode.p, d_gtag.p, d_g1.p, d_g2.p, h->d_xy.p, h->N, d_M);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return sync_check(s);   // the temporaries above are freed on return
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ build
+int fds_build_impl(fds_handle *h) {
+    cudaStream_t s = h->stream;
+    FDS_TRY(ensure_gauss_tables());
+    const int N = h->N;
+    const int leaf = h->opt.leaf_size;
+    // tree depth: smallest L with ceil(N / 2^L) <= leaf; halving split
+    int L = 0;
+    while (((N + (1 << L) - 1) >> L) > leaf) ++L;
+    h->L = L;
+    h->l0 = std::min(std::max(h->opt.top_level, 0), L);
+    h->ranges.assign(L + 1, {});
+    h->ranges[0].push_back({0, N});
+    for (int l = 0; l < L; ++l)
+        for (auto &r : h->ranges[l]) {
+            int mid = r.first + (r.second - r.first) / 2;
+            h->ranges[l + 1].push_back({r.first, mid});
+            h->ranges[l + 1].push_back({mid, r.second});
+        }
+    h->lv.clear();
+    h->lv.resize(L + 1);
+    FDS_TRY(h->d_xy.upload(h->xy, s));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+
+    // leaf level DOFs: contiguous ranges, comp-1 block then comp-2 block
+    {
+        Level &Lf = h->lv[L];
+        Lf.nb = (int)h->ranges[L].size();
+        Lf.n1.resize(Lf.nb);
+        Lf.n2.resize(Lf.nb);
+        Lf.dof_node.clear();
+        for (int b = 0; b < Lf.nb; ++b) {
+            auto r = h->ranges[L][b];
+            Lf.n1[b] = Lf.n2[b] = r.second - r.first;
+            for (int c = 0; c < 2; ++c)
+                for (int v = r.first; v < r.second; ++v) Lf.dof_node.push_back(v);
+        }
+        finish_offsets(Lf);
+        build_union(Lf);
+        FDS_TRY(alloc_level_A(Lf, s));
+        std::vector<int> gidx(Lf.D);
+        for (int b = 0; b < Lf.nb; ++b)
+            for (int q = 0; q < Lf.n1[b] + Lf.n2[b]; ++q)
+                gidx[Lf.doff[b] + q] = Lf.dof_node[Lf.doff[b] + q] + (q < Lf.n1[b] ? 0 : N);
+        FDS_TRY(h->d_leaf_gidx.upload(gidx, s));
+        std::vector<int> lo(Lf.nb), hi(Lf.nb);
+        int nmax = 0;
+        for (int b = 0; b < Lf.nb; ++b) {
+            lo[b] = h->ranges[L][b].first;
+            hi[b] = h->ranges[L][b].second;
+            nmax = std::max(nmax, hi[b] - lo[b]);
+        }
+        DBuf<int> d_lo, d_hi;
+        FDS_TRY(d_lo.upload(lo, s));
+        FDS_TRY(d_hi.upload(hi, s));
+        dim3 grid(ceil_div_u((long)nmax * nmax * 32, 256), Lf.nb);
+        {
+            ProfScope ps("a1.leaf_blocks", s);
+            fds_count_launch(), k_leaf_A<<<grid, 256, 0, s>>>(h->P, d_lo.p, d_hi.p, h->d_xy.p, N, Lf.rLU.p);
+        }
+        FDS_CUDA_TRY(cudaGetLastError());
+        FDS_TRY(sync_check(s));
+    }
+
+    for (int l = L; l > h->l0; --l) {
+        Level &C = h->lv[l];
+        const int nb = C.nb;
+        // ---- cell circles and proxy polygons (a0)
+        {
+            std::vector<int> lo(nb), hi(nb);
+            for (int b = 0; b < nb; ++b) { lo[b] = h->ranges[l][b].first; hi[b] = h->ranges[l][b].second; }
+            DBuf<int> d_lo, d_hi;
+            DBuf<double> d_cx, d_cy, d_R;
+            FDS_TRY(d_lo.upload(lo, s));
+            FDS_TRY(d_hi.upload(hi, s));
+            FDS_TRY(d_cx.alloc(nb));
+            FDS_TRY(d_cy.alloc(nb));
+            FDS_TRY(d_R.alloc(nb));
+            {
+                ProfScope ps("a0.cell_circles", s);
+                fds_count_launch(), k_box_circles<<<ceil_div_u((long)nb * 32, 256), 256, 0, s>>>(nb, d_lo.p, d_hi.p, h->d_xy.p, N,
+                                                                             d_cx.p, d_cy.p, d_R.p);
+            }
+            FDS_CUDA_TRY(cudaGetLastError());
+            FDS_TRY(d2h(C.cx, d_cx.p, nb, s));
+            FDS_TRY(d2h(C.cy, d_cy.p, nb, s));
+            FDS_TRY(d2h(C.R, d_R.p, nb, s));
+            FDS_TRY(sync_check(s));
+        }
+        C.Rp.resize(nb);
+        C.mprox.resize(nb);
+        for (int b = 0; b < nb; ++b) {
+            C.Rp[b] = h->opt.proxy_ratio * C.R[b];
+            C.mprox[b] = std::max(h->opt.proxy_points, (int)std::ceil(2.0 * h->P.kT * C.Rp[b] + 30.0));
+        }
+        std::vector<int64_t> pxoff(nb + 1, 0);
+        for (int b = 0; b < nb; ++b) pxoff[b + 1] = pxoff[b] + C.mprox[b];
+        DBuf<double> d_cx, d_cy, d_R, d_Rp, d_pxy;
+        DBuf<int> d_mp;
+        DBuf<int64_t> d_pxoff;
+        FDS_TRY(d_cx.upload(C.cx, s));
+        FDS_TRY(d_cy.upload(C.cy, s));
+        FDS_TRY(d_R.upload(C.R, s));
+        FDS_TRY(d_Rp.upload(C.Rp, s));
+        FDS_TRY(d_mp.upload(C.mprox, s));
+        FDS_TRY(d_pxoff.upload(pxoff, s));
+        FDS_TRY(d_pxy.alloc(2 * pxoff[nb]));
+        fds_count_launch(), k_proxy_nodes<<<nb, 128, 0, s>>>(d_cx.p, d_cy.p, d_Rp.p, d_mp.p, d_pxoff.p, d_pxy.p);
+        FDS_CUDA_TRY(cudaGetLastError());
+        // ---- union lists on the device
+        FDS_TRY(C.d_uoff.upload(C.uoff, s));
+        FDS_TRY(C.d_unode.upload(C.unode, s));
+        FDS_TRY(C.d_upos1.upload(C.upos1, s));
+        FDS_TRY(C.d_upos2.upload(C.upos2, s));
+        // ---- near field
+        DBuf<int> d_cnt;
+        FDS_TRY(d_cnt.alloc(nb));
+        {
+            ProfScope ps("a0.near_field", s);
+            fds_count_launch(), k_near<<<nb, 128, 0, s>>>(nb, d_cx.p, d_cy.p, d_R.p, d_Rp.p, C.d_uoff.p, C.d_unode.p, C.d_upos1.p,
+                                      C.d_upos2.p, h->d_xy.p, N, 0, d_cnt.p, nullptr, nullptr, nullptr);
+        }
+        FDS_CUDA_TRY(cudaGetLastError());
+        std::vector<int> cnt;
+        FDS_TRY(d2h(cnt, d_cnt.p, nb, s));
+        FDS_TRY(sync_check(s));
+        std::vector<int64_t> noff(nb + 1, 0);
+        for (int b = 0; b < nb; ++b) noff[b + 1] = noff[b] + cnt[b];
+        DBuf<int64_t> d_noff;
+        DBuf<int> d_nnode, d_nmask;
+        FDS_TRY(d_noff.upload(noff, s));
+        FDS_TRY(d_nnode.alloc(noff[nb]));
+        FDS_TRY(d_nmask.alloc(noff[nb]));
+        {
+            ProfScope ps("a0.near_field", s);
+            fds_count_launch(), k_near<<<nb, 128, 0, s>>>(nb, d_cx.p, d_cy.p, d_R.p, d_Rp.p, C.d_uoff.p, C.d_unode.p, C.d_upos1.p,
+                                      C.d_upos2.p, h->d_xy.p, N, 1, d_cnt.p, d_noff.p, d_nnode.p, d_nmask.p);
+        }
+        FDS_CUDA_TRY(cudaGetLastError());
+        std::vector<int> nmask;
+        FDS_TRY(d2h(nmask, d_nmask.p, noff[nb], s));
+        FDS_TRY(sync_check(s));
+        // ---- Y layout: [2m' proxy V][nnd near V][2m' proxy U][nnd near U] rows
+        std::vector<int> nrow(noff[nb]), nnd(nb), ym(nb), idm(2 * nb), idn(2 * nb);
+        std::vector<int64_t> yoff(2 * nb + 1, 0), toff(2 * nb + 1, 0), poff(2 * nb + 1, 0);
+        int maxm = 1, maxn = 1;
+        int64_t maxjp = 0, maxjn = 0;
+        for (int b = 0; b < nb; ++b) {
+            int rb = 0;
+            for (int64_t k = noff[b]; k < noff[b + 1]; ++k) {
+                nrow[k] = rb;
+                rb += (nmask[k] & 1) + ((nmask[k] >> 1) & 1);
+            }
+            nnd[b] = rb;
+            ym[b] = 4 * C.mprox[b] + 2 * rb;
+            maxm = std::max(maxm, ym[b]);
+            const int64_t nu = C.uoff[b + 1] - C.uoff[b];
+            maxjp = std::max(maxjp, (int64_t)C.mprox[b] * nu);
+            maxjn = std::max(maxjn, (noff[b + 1] - noff[b]) * nu);
+            for (int c = 0; c < 2; ++c) {
+                const int n = c ? C.n2[b] : C.n1[b];
+                idm[2 * b + c] = ym[b];
+                idn[2 * b + c] = n;
+                maxn = std::max(maxn, n);
+                yoff[2 * b + c + 1] = yoff[2 * b + c] + (int64_t)ym[b] * n;
+                toff[2 * b + c + 1] = toff[2 * b + c] + (int64_t)n * n / 4 + 1;
+                poff[2 * b + c + 1] = poff[2 * b + c] + n;
+            }
+        }
+        DBuf<cplx> d_Y, d_T;
+        DBuf<int64_t> d_yoff, d_toff, d_poff;
+        DBuf<int> d_ym, d_nnd, d_nrow, d_idm, d_idn, d_rank, d_perm;
+        FDS_TRY(d_Y.alloc(yoff[2 * nb]));
+        FDS_TRY(d_T.alloc(toff[2 * nb]));
+        FDS_TRY(d_yoff.upload(yoff, s));
+        FDS_TRY(d_toff.upload(toff, s));
+        FDS_TRY(d_poff.upload(poff, s));
+        FDS_TRY(d_ym.upload(ym, s));
+        FDS_TRY(d_nnd.upload(nnd, s));
+        FDS_TRY(d_nrow.upload(nrow, s));
+        FDS_TRY(d_idm.upload(idm, s));
+        FDS_TRY(d_idn.upload(idn, s));
+        FDS_TRY(d_rank.alloc(2 * nb));
+        FDS_TRY(d_perm.alloc(poff[2 * nb]));
+        YDesc D;
+        D.yoff = d_yoff.p; D.ym = d_ym.p; D.mp = d_mp.p; D.nnd = d_nnd.p; D.pxoff = d_pxoff.p; D.pxy = d_pxy.p;
+        D.uoff = C.d_uoff.p; D.unode = C.d_unode.p; D.upos1 = C.d_upos1.p; D.upos2 = C.d_upos2.p;
+        D.noff = d_noff.p; D.nnode = d_nnode.p; D.nmask = d_nmask.p; D.nrow = d_nrow.p;
+        // ---- kernel evaluation (a1)
+        if (maxjp > 0) {
+            dim3 g(ceil_div_u(maxjp * 32, 256), nb);
+            ProfScope ps("a1.proxy_rows", s);
+            fds_count_launch(), k_y_proxy<<<g, 256, 0, s>>>(h->P, D, h->d_xy.p, N, d_Y.p);
+            FDS_CUDA_TRY(cudaGetLastError());
+        }
+        if (maxjn > 0) {
+            dim3 g(ceil_div_u(maxjn * 32, 256), nb);
+            ProfScope ps("a1.near_rows", s);
+            fds_count_launch(), k_y_near<<<g, 256, 0, s>>>(h->P, D, h->d_xy.p, N, d_Y.p);
+            FDS_CUDA_TRY(cudaGetLastError());
+        }
+        // ---- interpolative decomposition (a2)
+        {
+            ProfScope ps("a2.id_cpqr", s);
+            FDS_TRY(id_batched(2 * nb, maxm, maxn, d_idm.p, d_idn.p, d_yoff.p, d_Y.p, h->tol, d_rank.p, d_perm.p,
+                               d_poff.p, d_T.p, d_toff.p, s));
+        }
+        std::vector<int> rank;
+        FDS_TRY(d2h(rank, d_rank.p, 2 * nb, s));
+        FDS_TRY(d2h(C.perm, d_perm.p, poff[2 * nb], s));
+        FDS_TRY(sync_check(s));
+        C.permoff = poff;
+        C.k1.resize(nb);
+        C.k2.resize(nb);
+        C.roff.assign(nb + 1, 0);
+        C.rmax = 0;
+        for (int b = 0; b < nb; ++b) {
+            C.k1[b] = rank[2 * b];
+            C.k2[b] = rank[2 * b + 1];
+            C.roff[b + 1] = C.roff[b] + C.k1[b] + C.k2[b];
+            C.rmax = std::max(C.rmax, C.k1[b] + C.k2[b]);
+        }
+        C.Rtot = C.roff[nb];
+        // ---- merge (a3): LU(A_i), W = A_i^{-1} V_i^H, S = V_i W, A~ = S^{-1}
+        std::vector<int> dv(nb), rv(nb);
+        C.offV.assign(nb + 1, 0);
+        C.offAt.assign(nb + 1, 0);
+        C.offpiv.assign(nb + 1, 0);
+        C.sum_d2 = C.sum_rd = C.sum_r2 = 0;
+        for (int b = 0; b < nb; ++b) {
+            dv[b] = C.n1[b] + C.n2[b];
+            rv[b] = C.k1[b] + C.k2[b];
+            C.sum_d2 += (double)dv[b] * dv[b];
+            C.sum_rd += (double)rv[b] * dv[b];
+            C.sum_r2 += (double)rv[b] * rv[b];
+            C.offV[b + 1] = C.offV[b] + (int64_t)rv[b] * dv[b];
+            C.offAt[b + 1] = C.offAt[b] + (int64_t)rv[b] * rv[b];
+            C.offpiv[b + 1] = C.offpiv[b] + dv[b];
+        }
+        C.offW = C.offV;
+        FDS_TRY(C.V.alloc(C.offV[nb]));
+        FDS_TRY(C.W.alloc(C.offW[nb]));
+        FDS_TRY(C.At.alloc(C.offAt[nb]));
+        FDS_TRY(C.piv.alloc(C.offpiv[nb]));
+        FDS_TRY(C.d_offpiv.upload(C.offpiv, s));
+        FDS_TRY(make_refs(C.rV, C.V.p, C.offV, rv, dv, s));
+        FDS_TRY(make_refs(C.rW, C.W.p, C.offW, dv, rv, s));
+        FDS_TRY(make_refs(C.rAt, C.At.p, C.offAt, rv, rv, s));
+        DBuf<cplx> S;
+        DBuf<MatRef> rS;
+        FDS_TRY(S.alloc(C.offAt[nb]));
+        FDS_TRY(make_refs(rS, S.p, C.offAt, rv, rv, s));
+        DBuf<int> d_n1, d_n2;
+        FDS_TRY(d_n1.upload(C.n1, s));
+        FDS_TRY(d_n2.upload(C.n2, s));
+        FDS_TRY(C.d_k1.upload(C.k1, s));
+        FDS_TRY(C.d_k2.upload(C.k2, s));
+        fds_count_launch(), k_make_V<<<nb, 256, 0, s>>>(C.rV.p, d_n1.p, d_n2.p, C.d_k1.p, C.d_k2.p, d_perm.p, d_poff.p, d_T.p,
+                                    d_toff.p);
+        FDS_CUDA_TRY(cudaGetLastError());
+        DBuf<int> info;
+        FDS_TRY(info.alloc(nb));
+        double fl_lu = 0, fl_w = 0, fl_s = 0, fl_slu = 0, fl_at = 0;
+        for (int b = 0; b < nb; ++b) {
+            const double d = dv[b], r = rv[b];
+            fl_lu += 8.0 / 3.0 * d * d * d;
+            fl_w += 8.0 * d * d * r;
+            fl_s += 8.0 * r * d * r;
+            fl_slu += 8.0 / 3.0 * r * r * r;
+            fl_at += 8.0 * r * r * r;
+        }
+        {
+            ProfScope ps("a3.merge_lu", s);
+            ps.flops = fl_lu;
+            FDS_TRY(dense_lu(nb, C.dmax, C.rLU.p, C.piv.p, C.d_offpiv.p, info.p, s));
+        }
+        fds_count_launch(), k_conj_transpose<<<nb, 256, 0, s>>>(C.rV.p, C.rW.p);
+        FDS_CUDA_TRY(cudaGetLastError());
+        {
+            ProfScope ps("a3.merge_w_solve", s);
+            ps.flops = fl_w;
+            FDS_TRY(dense_lu_solve(nb, C.dmax, C.rmax, C.rLU.p, C.piv.p, C.d_offpiv.p, C.rW.p, s));
+        }
+        {
+            ProfScope ps("a3.merge_s_gemm", s);
+            ps.flops = fl_s;
+            FDS_TRY(dense_gemm(nb, C.rmax, C.rmax, C.rV.p, 0, C.rW.p, 0, rS.p, mkc(1, 0), mkc(0, 0), s));
+        }
+        DBuf<int> spiv, info2;
+        DBuf<int64_t> d_sp;
+        std::vector<int64_t> spoff(nb + 1, 0);
+        for (int b = 0; b < nb; ++b) spoff[b + 1] = spoff[b] + rv[b];
+        FDS_TRY(spiv.alloc(spoff[nb]));
+        FDS_TRY(d_sp.upload(spoff, s));
+        FDS_TRY(info2.alloc(nb));
+        {
+            ProfScope ps("a3.merge_s_lu", s);
+            ps.flops = fl_slu;
+            FDS_TRY(dense_lu(nb, C.rmax, rS.p, spiv.p, d_sp.p, info2.p, s));
+        }
+        fds_count_launch(), k_set_identity<<<nb, 256, 0, s>>>(C.rAt.p);
+        FDS_CUDA_TRY(cudaGetLastError());
+        {
+            ProfScope ps("a3.merge_inverse", s);
+            ps.flops = fl_at;
+            FDS_TRY(dense_lu_solve(nb, C.rmax, C.rmax, rS.p, spiv.p, d_sp.p, C.rAt.p, s));
+        }
+        std::vector<int> hinfo, hinfo2;
+        FDS_TRY(d2h(hinfo, info.p, nb, s));
+        FDS_TRY(d2h(hinfo2, info2.p, nb, s));
+        FDS_TRY(sync_check(s));
+        for (int b = 0; b < nb; ++b)
+            if (hinfo[b] || hinfo2[b]) return FDS_ERR_SINGULAR;
+        h->factor_bytes += (int64_t)(C.LU.bytes() + C.V.bytes() + C.W.bytes() + C.At.bytes() + C.piv.bytes());
+
+        // ---- parent level (eq. (A_rearrangement)): DOFs = children's skeletons
+        Level &Pn = h->lv[l - 1];
+        Pn.nb = nb / 2;
+        Pn.n1.assign(Pn.nb, 0);
+        Pn.n2.assign(Pn.nb, 0);
+        Pn.dof_node.clear();
+        C.par_pos1.assign(nb, 0);
+        C.par_pos2.assign(nb, 0);
+        for (int p = 0; p < Pn.nb; ++p) {
+            const int a = 2 * p, bb = 2 * p + 1;
+            Pn.n1[p] = C.k1[a] + C.k1[bb];
+            Pn.n2[p] = C.k2[a] + C.k2[bb];
+            C.par_pos1[a] = 0;
+            C.par_pos1[bb] = C.k1[a];
+            C.par_pos2[a] = Pn.n1[p];
+            C.par_pos2[bb] = Pn.n1[p] + C.k2[a];
+            for (int c = 0; c < 2; ++c)
+                for (int ch : {a, bb}) {
+                    const int k = c ? C.k2[ch] : C.k1[ch];
+                    const int base = (int)C.doff[ch] + (c ? C.n1[ch] : 0);
+                    const int *pm = C.perm.data() + C.permoff[2 * ch + c];
+                    for (int q = 0; q < k; ++q) Pn.dof_node.push_back(C.dof_node[base + pm[q]]);
+                }
+        }
+        finish_offsets(Pn);
+        build_union(Pn);
+        FDS_TRY(C.d_par_pos1.upload(C.par_pos1, s));
+        FDS_TRY(C.d_par_pos2.upload(C.par_pos2, s));
+        FDS_TRY(C.d_doff.upload(C.doff, s));
+        FDS_TRY(C.d_roff.upload(C.roff, s));
+        FDS_TRY(alloc_level_A(Pn, s));
+        fds_count_launch(), k_zero<<<1024, 256, 0, s>>>(Pn.LU.p, Pn.offA[Pn.nb]);
+        fds_count_launch(), k_place_children<<<nb, 256, 0, s>>>(C.rAt.p, C.d_k1.p, C.d_par_pos1.p, C.d_par_pos2.p, Pn.rLU.p);
+        FDS_CUDA_TRY(cudaGetLastError());
+        // sibling blocks R: group = parent, tags = child index
+        std::vector<int64_t> goff(Pn.nb + 1, 0);
+        std::vector<int> gnode, gtag, g1, g2;
+        for (int p = 0; p < Pn.nb; ++p) {
+            for (int64_t u = Pn.uoff[p]; u < Pn.uoff[p + 1]; ++u) {
+                const int pos1 = Pn.upos1[u], pos2 = Pn.upos2[u];
+                // which child: a's DOFs occupy [0, k1_a) in comp 1 and [0, k2_a) in comp 2
+                int tag = 1;
+                if ((pos1 >= 0 && pos1 < C.k1[2 * p]) || (pos2 >= 0 && pos2 < C.k2[2 * p])) tag = 0;
+                gnode.push_back(Pn.unode[u]);
+                gtag.push_back(tag);
+                g1.push_back(pos1);
+                g2.push_back(pos2 >= 0 ? Pn.n1[p] + pos2 : -1);
+                Pn.utag[u] = tag;
+            }
+            goff[p + 1] = (int64_t)gnode.size();
+        }
+        {
+            ProfScope ps("a1.sibling_blocks", s);
+            FDS_TRY(launch_group_pairs(h, goff, gnode, gtag, g1, g2, Pn.rLU.p, s));
+        }
+    }
+
+    // ---- top level (Sec. 6.3): dense system over the cells of level l0
+    {
+        Level &T = h->lv[h->l0];
+        h->Dtop = T.D;
+        FDS_TRY(h->Atop.alloc((size_t)h->Dtop * h->Dtop));
+        fds_count_launch(), k_zero<<<1024, 256, 0, s>>>(h->Atop.p, h->Dtop * h->Dtop);
+        MatRef top;
+        top.p = h->Atop.p;
+        top.rows = top.cols = (int)h->Dtop;
+        top.ld = (int)std::max<int64_t>(h->Dtop, 1);
+        FDS_TRY(T.d_doff.upload(T.doff, s));
+        fds_count_launch(), k_place_top<<<T.nb, 256, 0, s>>>(T.rLU.p, T.d_doff.p, top);
+        FDS_CUDA_TRY(cudaGetLastError());
+        std::vector<int64_t> goff = {0};
+        std::vector<int> gnode, gtag, g1, g2;
+        for (int b = 0; b < T.nb; ++b)
+            for (int64_t u = T.uoff[b]; u < T.uoff[b + 1]; ++u) {
+                gnode.push_back(T.unode[u]);
+                gtag.push_back(b);
+                g1.push_back(T.upos1[u] >= 0 ? (int)T.doff[b] + T.upos1[u] : -1);
+                g2.push_back(T.upos2[u] >= 0 ? (int)T.doff[b] + T.n1[b] + T.upos2[u] : -1);
+            }
+        goff.push_back((int64_t)gnode.size());
+        std::vector<MatRef> ht = {top};
+        FDS_TRY(h->rtop.upload(ht, s));
+        if (T.nb > 1) {
+            ProfScope ps("a1.top_blocks", s);
+            FDS_TRY(launch_group_pairs(h, goff, gnode, gtag, g1, g2, h->rtop.p, s));
+        }
+        std::vector<int64_t> po = {0, h->Dtop};
+        FDS_TRY(h->d_ptop_off.upload(po, s));
+        FDS_TRY(h->ptop.alloc(h->Dtop));
+        FDS_TRY(h->d_info.alloc(1));
+        {
+            ProfScope ps("a4.top_lu", s);
+            ps.flops = 8.0 / 3.0 * (double)h->Dtop * h->Dtop * h->Dtop;
+            FDS_TRY(dense_lu(1, (int)h->Dtop, h->rtop.p, h->ptop.p, h->d_ptop_off.p, h->d_info.p, s));
+        }
+        std::vector<int> hinfo;
+        FDS_TRY(d2h(hinfo, h->d_info.p, 1, s));
+        FDS_TRY(sync_check(s));
+        if (hinfo[0]) return FDS_ERR_SINGULAR;
+        h->factor_bytes += (int64_t)(h->Atop.bytes() + h->ptop.bytes());
+        // the top level's per-cell A blocks are no longer needed
+        if (h->l0 < L || T.nb > 0) {
+            T.LU.release();
+            T.rLU.release();
+        }
+        FDS_TRY(T.d_doff.upload(T.doff, s));
+    }
+    cudaEventRecord(e1, s);
+    FDS_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    h->build_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return FDS_OK;
+}

@@ -1,0 +1,101 @@
+// Shared device/host helpers of the GB300 fast direct solver (complex128
+// arithmetic on double2, launch checks, Gauss–Legendre tables).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <mutex>
+
+#include "../../include/fds.h"
+
+#ifndef FDS_PI
+#define FDS_PI 3.14159265358979323846
+#endif
+
+typedef double2 cplx;
+
+__host__ __device__ __forceinline__ cplx mkc(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ cplx cadd(cplx a, cplx b) { return mkc(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ cplx csub(cplx a, cplx b) { return mkc(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ cplx cmul(cplx a, cplx b) {
+    return mkc(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+__host__ __device__ __forceinline__ cplx cmulc(cplx a, cplx b) {
+    return mkc(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__host__ __device__ __forceinline__ cplx cconj(cplx a) { return mkc(a.x, -a.y); }
+__host__ __device__ __forceinline__ cplx cscale(cplx a, double s) { return mkc(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double cabs2(cplx a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ cplx cneg(cplx a) { return mkc(-a.x, -a.y); }
+// acc += a * b
+__host__ __device__ __forceinline__ void cfma(cplx &acc, cplx a, cplx b) {
+    acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+    acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+}
+// acc -= a * b
+__host__ __device__ __forceinline__ void cfms(cplx &acc, cplx a, cplx b) {
+    acc.x = fma(-a.x, b.x, fma(a.y, b.y, acc.x));
+    acc.y = fma(-a.x, b.y, fma(-a.y, b.x, acc.y));
+}
+__host__ __device__ __forceinline__ cplx cinv(cplx a) {
+    double d = 1.0 / cabs2(a);
+    return mkc(a.x * d, -a.y * d);
+}
+__host__ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) { return cmul(a, cinv(b)); }
+
+// Physical constants prepared on the host for one problem.
+struct PhysDev {
+    double lam, mu, rho, omega;
+    double kT, kL;
+    double rw2;        // rho omega^2
+    double c2;         // 2 / kT^2
+    cplx alpha;        // Burton–Miller coupling
+};
+
+PhysDev make_physdev(const fds_physics *ph);
+
+// Gauss–Legendre tables on [0,1] for the orders the quadrature rules use.
+// Index q holds q nodes; only q in {1..8, 16, 20} are filled.
+#define GL_MAXQ 20
+struct GaussTables {
+    double x[GL_MAXQ + 1][GL_MAXQ];
+    double w[GL_MAXQ + 1][GL_MAXQ];
+};
+// Each translation unit that evaluates quadrature owns a copy of the table
+// (whole-program compilation, no relocatable device code) and uploads it with
+// its own ensure_gauss_tables() before the first launch.
+static __constant__ GaussTables c_gauss;
+int gauss_tables_host(GaussTables *T);   // fills the host copy (kernel_eval.cu)
+
+#define FDS_CUDA_TRY(expr)                                                   \
+    do {                                                                     \
+        cudaError_t _e = (expr);                                             \
+        if (_e != cudaSuccess) return (_e == cudaErrorMemoryAllocation) ? FDS_ERR_OOM : FDS_ERR_CUDA; \
+    } while (0)
+
+#define FDS_TRY(expr)                \
+    do {                             \
+        int _r = (expr);             \
+        if (_r != FDS_OK) return _r; \
+    } while (0)
+
+// Counts kernel launches of this library (fds_launch_count).
+void fds_count_launch();
+
+static inline unsigned ceil_div_u(long a, long b) { return (unsigned)((a + b - 1) / b); }
+
+// Upload this translation unit's Gauss table once per device.
+static inline int ensure_gauss_tables() {
+    static std::mutex mu;
+    static int done[64] = {0};
+    int dev = 0;
+    FDS_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && done[dev]) return FDS_OK;
+    GaussTables T;
+    FDS_TRY(gauss_tables_host(&T));
+    FDS_CUDA_TRY(cudaMemcpyToSymbol(c_gauss, &T, sizeof(T)));
+    if (dev >= 0 && dev < 64) done[dev] = 1;
+    return FDS_OK;
+}

@@ -1,0 +1,249 @@
+// Batched complex128 LU / LU-solve / GEMM kernels (one CTA per matrix or
+// per output tile).  FP64 throughout.
+#include <cmath>
+
+#include "dense.cuh"
+
+namespace {
+
+constexpr int LU_THREADS = 256;
+
+__device__ __forceinline__ bool finite_c(cplx a) { return isfinite(a.x) && isfinite(a.y); }
+
+// Right-looking unblocked LU with partial pivoting (largest |a_ik|, ties to the
+// lowest row), one CTA per matrix, the matrix in global memory.
+__global__ void __launch_bounds__(LU_THREADS) k_lu(const MatRef *__restrict__ mats, int *__restrict__ piv,
+                                                   const int64_t *__restrict__ poff, int *__restrict__ info) {
+    const MatRef M = mats[blockIdx.x];
+    const int n = M.rows, ld = M.ld;
+    cplx *A = M.p;
+    int *pv = piv + poff[blockIdx.x];
+    __shared__ double s_val[LU_THREADS];
+    __shared__ int s_idx[LU_THREADS];
+    __shared__ int s_piv;
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        // pivot search in column k
+        double best = -1.0;
+        int bi = n;
+        for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+            double v = cabs2(A[i + (long)k * ld]);
+            if (v > best) { best = v; bi = i; }
+        }
+        s_val[threadIdx.x] = best;
+        s_idx[threadIdx.x] = bi;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                double v2 = s_val[threadIdx.x + o];
+                int i2 = s_idx[threadIdx.x + o];
+                if (v2 > s_val[threadIdx.x] || (v2 == s_val[threadIdx.x] && i2 < s_idx[threadIdx.x])) {
+                    s_val[threadIdx.x] = v2;
+                    s_idx[threadIdx.x] = i2;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            int p = s_idx[0];
+            if (p >= n) p = k;
+            s_piv = p;
+            pv[k] = p;
+            cplx d = A[p + (long)k * ld];
+            if (!(s_val[0] > 0.0) || !finite_c(d)) {
+                if (!s_bad) s_bad = k + 1;
+            }
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p != k) {
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                cplx t = A[k + (long)j * ld];
+                A[k + (long)j * ld] = A[p + (long)j * ld];
+                A[p + (long)j * ld] = t;
+            }
+        }
+        __syncthreads();
+        const cplx d = A[k + (long)k * ld];
+        const cplx dinv = (cabs2(d) > 0.0) ? cinv(d) : mkc(0.0, 0.0);
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (long)k * ld] = cmul(A[i + (long)k * ld], dinv);
+        __syncthreads();
+        // trailing update A[k+1:, k+1:] -= l u^T
+        const int m = n - k - 1;
+        const long tot = (long)m * m;
+        for (long e = threadIdx.x; e < tot; e += blockDim.x) {
+            const int i = k + 1 + (int)(e % m), j = k + 1 + (int)(e / m);
+            cfms(A[i + (long)j * ld], A[i + (long)k * ld], A[k + (long)j * ld]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) info[blockIdx.x] = s_bad;
+}
+
+// Multi-RHS LU solve: CTA per (matrix, tile of RT right-hand sides).  The RHS
+// tile lives in shared memory during the row swaps, the unit-lower forward
+// substitution and the upper back substitution.
+constexpr int SOLVE_THREADS = 256;
+
+__global__ void __launch_bounds__(SOLVE_THREADS) k_lu_solve(const MatRef *__restrict__ LUs,
+                                                            const int *__restrict__ piv,
+                                                            const int64_t *__restrict__ poff,
+                                                            const MatRef *__restrict__ Bs, int rt) {
+    extern __shared__ cplx sh[];
+    const MatRef L = LUs[blockIdx.y];
+    const MatRef B = Bs[blockIdx.y];
+    const int n = L.rows;
+    const int c0 = blockIdx.x * rt;
+    if (c0 >= B.cols || n == 0) return;
+    const int nc = min(rt, B.cols - c0);
+    const int *pv = piv + poff[blockIdx.y];
+    // load tile: sh[i + c * n]
+    for (long e = threadIdx.x; e < (long)n * nc; e += blockDim.x) {
+        const int i = (int)(e % n), c = (int)(e / n);
+        sh[e] = B.p[i + (long)(c0 + c) * B.ld];
+    }
+    __syncthreads();
+    if (threadIdx.x < nc) {
+        const int c = threadIdx.x;
+        for (int k = 0; k < n; ++k) {
+            const int p = pv[k];
+            if (p != k) {
+                cplx t = sh[k + c * n];
+                sh[k + c * n] = sh[p + c * n];
+                sh[p + c * n] = t;
+            }
+        }
+    }
+    __syncthreads();
+    // forward: x_i -= L_ij x_j (j < i), column sweep
+    for (int j = 0; j < n - 1; ++j) {
+        const int m = n - j - 1;
+        for (long e = threadIdx.x; e < (long)m * nc; e += blockDim.x) {
+            const int i = j + 1 + (int)(e % m), c = (int)(e / m);
+            cfms(sh[i + c * n], L.p[i + (long)j * L.ld], sh[j + c * n]);
+        }
+        __syncthreads();
+    }
+    // backward
+    for (int j = n - 1; j >= 0; --j) {
+        const cplx dinv = cinv(L.p[j + (long)j * L.ld]);
+        for (int c = threadIdx.x; c < nc; c += blockDim.x) sh[j + c * n] = cmul(sh[j + c * n], dinv);
+        __syncthreads();
+        for (long e = threadIdx.x; e < (long)j * nc; e += blockDim.x) {
+            const int i = (int)(e % j), c = (int)(e / j);
+            cfms(sh[i + c * n], L.p[i + (long)j * L.ld], sh[j + c * n]);
+        }
+        __syncthreads();
+    }
+    for (long e = threadIdx.x; e < (long)n * nc; e += blockDim.x) {
+        const int i = (int)(e % n), c = (int)(e / n);
+        B.p[i + (long)(c0 + c) * B.ld] = sh[e];
+    }
+}
+
+// C = alpha op(A) op(B) + beta C; 16x16 output tile per CTA, 16-deep K chunks.
+constexpr int GT = 16;
+
+__device__ __forceinline__ cplx ld_op(const MatRef &M, int op, int i, int j) {
+    // element (i, j) of op(M)
+    if (op == 0) return M.p[i + (long)j * M.ld];
+    cplx v = M.p[j + (long)i * M.ld];
+    return cconj(v);
+}
+
+__global__ void __launch_bounds__(GT *GT) k_gemm(const MatRef *__restrict__ As, int opA,
+                                                 const MatRef *__restrict__ Bs, int opB,
+                                                 const MatRef *__restrict__ Cs, cplx alpha, cplx beta, int tiles_m) {
+    const MatRef A = As[blockIdx.y], B = Bs[blockIdx.y], C = Cs[blockIdx.y];
+    const int M = C.rows, N = C.cols;
+    const int K = (opA == 0) ? A.cols : A.rows;
+    const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+    const int i0 = tm * GT, j0 = tn * GT;
+    if (i0 >= M || j0 >= N) return;
+    __shared__ cplx sa[GT][GT + 1], sb[GT][GT + 1];
+    const int tx = threadIdx.x % GT, ty = threadIdx.x / GT;
+    cplx acc = mkc(0, 0);
+    for (int k0 = 0; k0 < K; k0 += GT) {
+        {
+            const int i = i0 + tx, k = k0 + ty;
+            sa[ty][tx] = (i < M && k < K) ? ld_op(A, opA, i, k) : mkc(0, 0);
+            const int kk = k0 + tx, j = j0 + ty;
+            sb[ty][tx] = (kk < K && j < N) ? ld_op(B, opB, kk, j) : mkc(0, 0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GT; ++k) cfma(acc, sa[k][tx], sb[ty][k]);
+        __syncthreads();
+    }
+    const int i = i0 + tx, j = j0 + ty;
+    if (i < M && j < N) {
+        cplx *c = &C.p[i + (long)j * C.ld];
+        cplx old = (beta.x != 0.0 || beta.y != 0.0) ? *c : mkc(0, 0);
+        *c = cadd(cmul(alpha, acc), cmul(beta, old));
+    }
+}
+
+}  // namespace
+
+int dense_lu(int batch, int max_n, const MatRef *d_A, int *d_piv, const int64_t *d_poff, int *d_info,
+             cudaStream_t s) {
+    if (batch <= 0) return FDS_OK;
+    (void)max_n;
+    fds_count_launch(), k_lu<<<batch, LU_THREADS, 0, s>>>(d_A, d_piv, d_poff, d_info);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
+}
+
+int dense_lu_solve(int batch, int max_rows, int max_cols, const MatRef *d_LU, const int *d_piv,
+                   const int64_t *d_poff, const MatRef *d_B, cudaStream_t s) {
+    if (batch <= 0 || max_rows <= 0 || max_cols <= 0) return FDS_OK;
+    // RHS tile width so that rows x rt complex fits in 200 KB of shared memory
+    int rt = (int)(200 * 1024 / (16L * max_rows));
+    if (rt > 32) rt = 32;
+    if (rt < 1) return FDS_ERR_ARG;
+    size_t smem = (size_t)max_rows * rt * sizeof(cplx);
+    if (smem > 48 * 1024) FDS_CUDA_TRY(cudaFuncSetAttribute(k_lu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((max_cols + rt - 1) / rt, batch);
+    fds_count_launch(), k_lu_solve<<<grid, SOLVE_THREADS, smem, s>>>(d_LU, d_piv, d_poff, d_B, rt);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
+}
+
+int dense_gemm(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, int opB,
+               const MatRef *d_C, cplx alpha, cplx beta, cudaStream_t s) {
+    if (batch <= 0 || max_m <= 0 || max_n <= 0) return FDS_OK;
+    const int tm = (max_m + GT - 1) / GT, tn = (max_n + GT - 1) / GT;
+    dim3 grid(tm * tn, batch);
+    fds_count_launch(), k_gemm<<<grid, GT * GT, 0, s>>>(d_A, opA, d_B, opB, d_C, alpha, beta, tm);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
+}
+
+// Stage entry point: batched LU (see fds.h).
+namespace {
+__global__ void k_make_refs(int batch, const int32_t *d, const int64_t *off, double *A, MatRef *refs) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    refs[b].p = (cplx *)A + off[b];
+    refs[b].rows = d[b];
+    refs[b].cols = d[b];
+    refs[b].ld = d[b] > 0 ? d[b] : 1;
+}
+}  // namespace
+
+extern "C" int fds_lu_batched(int32_t batch, const int32_t *d_d, const int64_t *d_off, double *d_A,
+                              int32_t *d_piv, const int64_t *d_poff, int32_t *d_info, uint64_t stream) {
+    if (batch < 0) return FDS_ERR_ARG;
+    if (batch == 0) return FDS_OK;
+    if (!d_d || !d_off || !d_A || !d_piv || !d_poff || !d_info) return FDS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    MatRef *refs = nullptr;
+    FDS_CUDA_TRY(cudaMallocAsync((void **)&refs, sizeof(MatRef) * batch, s));
+    fds_count_launch(), k_make_refs<<<(batch + 127) / 128, 128, 0, s>>>(batch, d_d, d_off, d_A, refs);
+    int rc = dense_lu(batch, 0, refs, d_piv, d_poff, d_info, s);
+    cudaFreeAsync(refs, s);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return rc;
+}

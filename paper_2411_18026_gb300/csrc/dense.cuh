@@ -1,0 +1,25 @@
+// Batched dense complex128 linear algebra on variable-size per-cell blocks:
+// LU with partial pivoting, multi-RHS LU solve, and GEMM.  Used by the merge
+// of Sec. 6.2 (A_i^{-1} U_i, S_i = V_i A_i^{-1} U_i, A~_i = S_i^{-1}), the top
+// LU of Sec. 6.3 and the solve sweeps.  Matrices are column-major.
+#pragma once
+
+#include "common.cuh"
+
+// Per-matrix descriptor of a batch.
+struct MatRef {
+    cplx *p;       // base pointer
+    int rows, cols, ld;
+};
+
+// Launch helpers (device pointers to descriptor arrays; all enqueue on stream).
+// LU in place of square A[b] (rows == cols), pivots piv + poff[b], info[b].
+int dense_lu(int batch, int max_n, const MatRef *d_A, int *d_piv, const int64_t *d_poff, int *d_info,
+             cudaStream_t s);
+// Solve A X = B in place of B for each b with the LU of dense_lu (B[b].rows
+// must equal the order of A[b]).  max_rows / max_cols bound the sizes.
+int dense_lu_solve(int batch, int max_rows, int max_cols, const MatRef *d_LU, const int *d_piv,
+                   const int64_t *d_poff, const MatRef *d_B, cudaStream_t s);
+// C = alpha * op(A) * op(B) + beta * C, op = N (0), or conjugate transpose (2).
+int dense_gemm(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, int opB,
+               const MatRef *d_C, cplx alpha, cplx beta, cudaStream_t s);

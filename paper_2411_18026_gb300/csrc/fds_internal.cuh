@@ -1,0 +1,120 @@
+// Internal state of a factorisation handle (host planner + device buffers).
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+#include "dense.cuh"
+
+// Device buffer owned by the handle (freed in the destructor).
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DBuf &operator=(DBuf &&o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p; n = o.n;
+            o.p = nullptr; o.n = 0;
+        }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    int alloc(size_t count) {
+        release();
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e == cudaErrorMemoryAllocation ? FDS_ERR_OOM : FDS_ERR_CUDA;
+        }
+        n = count;
+        return FDS_OK;
+    }
+    int upload(const std::vector<T> &h, cudaStream_t s) {
+        int rc = alloc(h.size());
+        if (rc != FDS_OK) return rc;
+        if (!h.empty()) FDS_CUDA_TRY(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+        return FDS_OK;
+    }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+// One tree level: its cells, their active DOFs and (for compressed levels) the
+// stored factors of Sec. 7.3 step 3(b).
+struct Level {
+    int nb = 0;                  // cells
+    // --- DOFs: per cell, comp-1 DOF nodes then comp-2 DOF nodes
+    std::vector<int> n1, n2;
+    std::vector<int64_t> doff;   // nb+1, prefix of n1+n2
+    std::vector<int> dof_node;
+    // union node list per cell (node, position in comp-1 list, in comp-2 list, group tag)
+    std::vector<int64_t> uoff;   // nb+1
+    std::vector<int> unode, upos1, upos2, utag;
+    DBuf<int> d_unode, d_upos1, d_upos2, d_utag;
+    DBuf<int64_t> d_uoff;
+    // --- geometry of the cells (levels > l0 only)
+    std::vector<double> cx, cy, R, Rp;
+    std::vector<int> mprox;
+    // --- compression
+    std::vector<int> k1, k2;     // ranks
+    std::vector<int64_t> permoff;   // 2 nb + 1 (index 2b + c)
+    std::vector<int> perm;
+    // --- factors (device), offsets in complex entries
+    std::vector<int64_t> offA, offW, offAt, offV, offpiv;
+    DBuf<cplx> LU, W, At, V;
+    DBuf<int> piv;
+    DBuf<MatRef> rLU, rW, rAt, rV;
+    DBuf<int64_t> d_offpiv;
+    // --- placement of each cell's skeleton vector in its parent's DOF vector
+    std::vector<int> par_pos1, par_pos2;   // start of comp-1 / comp-2 skeleton block in the parent
+    DBuf<int> d_par_pos1, d_par_pos2, d_k1, d_k2;
+    DBuf<int64_t> d_doff, d_roff;          // DOF / skeleton offsets (prefix of d and r)
+    std::vector<int64_t> roff;
+    int64_t D = 0, Rtot = 0;               // total DOFs / total skeleton DOFs of the level
+    int dmax = 0, rmax = 0;
+    double sum_d2 = 0, sum_rd = 0, sum_r2 = 0;   // algorithmic work sums for the sweep
+};
+
+struct fds_handle {
+    int N = 0;
+    fds_physics ph{};
+    PhysDev P{};
+    double tol = 0;
+    fds_options opt{};
+    int L = 0, l0 = 0;
+    cudaStream_t stream = 0;
+    DBuf<double> d_xy;
+    DBuf<int> d_leaf_gidx;        // leaf DOF q -> node + comp * N
+    std::vector<double> xy;
+    // ranges[l][i] = [lo, hi) node range of cell i at level l
+    std::vector<std::vector<std::pair<int, int>>> ranges;
+    std::vector<Level> lv;       // index = level (0..L); only l0..L populated
+    // top system
+    int64_t Dtop = 0;
+    DBuf<cplx> Atop;
+    DBuf<int> ptop;
+    DBuf<MatRef> rtop;
+    DBuf<int64_t> d_ptop_off;
+    DBuf<int> d_info;
+    // solve workspace (grown on demand)
+    std::vector<DBuf<cplx>> wz, wf, wt;
+    DBuf<cplx> wtop;
+    DBuf<MatRef> wrefs;
+    int64_t ws_cols = 0;
+    double build_ms = 0, solve_ms = 0;
+    int64_t factor_bytes = 0;
+};
+
+int fds_build_impl(fds_handle *h);
+int fds_solve_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s);
+int fds_rhs_impl(fds_handle *h, const int *d_kinds, const double *d_angles, int nrhs, cplx *d_f, cudaStream_t s);

@@ -1,0 +1,148 @@
+// Galerkin kernel evaluation: stage entry points and the shared setup
+// (Gauss tables, physical constants).  Device math lives in kernel_eval.cuh.
+#include <math.h>
+#include <mutex>
+#include <string.h>
+
+#include "common.cuh"
+#include "kernel_eval.cuh"
+
+PhysDev make_physdev(const fds_physics *ph) {
+    PhysDev P;
+    P.lam = ph->lambda;
+    P.mu = ph->mu;
+    P.rho = ph->rho > 0 ? ph->rho : 1.0;
+    P.omega = ph->omega;
+    // c_L = sqrt((lam + 2 mu)/rho), c_T = sqrt(mu/rho), k = omega / c   (Sec. 2)
+    P.kL = P.omega / sqrt((P.lam + 2.0 * P.mu) / P.rho);
+    P.kT = P.omega / sqrt(P.mu / P.rho);
+    P.rw2 = P.rho * P.omega * P.omega;
+    P.c2 = 2.0 / (P.kT * P.kT);
+    if (ph->alpha_set)
+        P.alpha = mkc(ph->alpha_re, ph->alpha_im);
+    else
+        P.alpha = mkc(0.0, 1.0 / (P.mu * P.kT));   // alpha = i / (mu k_T)
+    return P;
+}
+
+// Gauss–Legendre nodes on [0,1]: roots of P_q by Newton's method from the
+// Chebyshev-like initial guesses, weights 1/((1-x^2) P_q'(x)^2) (mapped).
+static void gauss_legendre01(int q, double *x, double *w) {
+    for (int i = 0; i < q; ++i) {
+        double r = cos(FDS_PI * (4.0 * i + 3.0) / (4.0 * q + 2.0));
+        double dp = 1.0;
+        for (int it = 0; it < 200; ++it) {
+            double p0 = 1.0, p1 = r;
+            for (int k = 2; k <= q; ++k) {
+                double p2 = ((2.0 * k - 1.0) * r * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = q * (r * p1 - p0) / (r * r - 1.0);
+            double step = p1 / dp;
+            r -= step;
+            if (fabs(step) < 1e-17) break;
+        }
+        double p0 = 1.0, p1 = r;
+        for (int k = 2; k <= q; ++k) {
+            double p2 = ((2.0 * k - 1.0) * r * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = q * (r * p1 - p0) / (r * r - 1.0);
+        x[i] = 0.5 * (1.0 - r);
+        w[i] = 1.0 / ((1.0 - r * r) * dp * dp);
+    }
+}
+
+int gauss_tables_host(GaussTables *T) {
+    static GaussTables cache;
+    static bool ready = false;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ready) {
+        memset(&cache, 0, sizeof(cache));
+        for (int q = 1; q <= GL_MAXQ; ++q) gauss_legendre01(q, cache.x[q], cache.w[q]);
+        ready = true;
+    }
+    *T = cache;
+    return FDS_OK;
+}
+
+namespace {
+
+// One warp per (row hat, column hat) pair; column-major output
+// out[(r + i nr) + (c + j nc) * ld], ld = 2 nr.
+__global__ void __launch_bounds__(256) k_eval_entries(PhysDev P, const double *__restrict__ xy, int N,
+                                                      const int *__restrict__ rows, int nr,
+                                                      const int *__restrict__ cols, int nc, cplx *out) {
+    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= (long)nr * nc) return;
+    const int r = (int)(warp % nr), c = (int)(warp / nr);
+    cplx v[2][2];
+    fdsk::hat_pair_same(P, xy, N, rows[r], cols[c], lane, v, nullptr);
+    if (lane == 0) {
+        const long ld = 2L * nr;
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) out[(r + (long)i * nr) + (c + (long)j * nc) * ld] = v[i][j];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_eval_cross(PhysDev P, const double *__restrict__ X, int NX,
+                                                    const int *__restrict__ rows, int nr,
+                                                    const double *__restrict__ Y, int NY,
+                                                    const int *__restrict__ cols, int nc, int q, cplx *out) {
+    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= (long)nr * nc) return;
+    const int r = (int)(warp % nr), c = (int)(warp / nr);
+    cplx v[2][2];
+    fdsk::hat_pair_cross(P, X, NX, rows[r], Y, NY, cols[c], q, lane, v, nullptr);
+    if (lane == 0) {
+        const long ld = 2L * nr;
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) out[(r + (long)i * nr) + (c + (long)j * nc) * ld] = v[i][j];
+    }
+}
+
+bool phys_ok(const fds_physics *ph) {
+    return ph && ph->mu > 0 && ph->omega > 0 && ph->lambda + 2.0 * ph->mu > 0;
+}
+
+}  // namespace
+
+extern "C" int fds_eval_entries(const fds_physics *ph, const double *d_xy, int32_t n, const int32_t *d_rows,
+                                int32_t nr, const int32_t *d_cols, int32_t nc, double *d_out,
+                                uint64_t stream) {
+    if (!phys_ok(ph) || !d_xy || n < 3 || nr < 0 || nc < 0) return FDS_ERR_ARG;
+    if (nr == 0 || nc == 0) return FDS_OK;
+    if (!d_rows || !d_cols || !d_out) return FDS_ERR_ARG;
+    FDS_TRY(ensure_gauss_tables());
+    PhysDev P = make_physdev(ph);
+    const long warps = (long)nr * nc;
+    fds_count_launch(), k_eval_entries<<<ceil_div_u(warps * 32, 256), 256, 0, (cudaStream_t)stream>>>(
+        P, d_xy, n, d_rows, nr, d_cols, nc, (cplx *)d_out);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
+}
+
+extern "C" int fds_eval_cross(const fds_physics *ph, const double *d_X, int32_t nx, const int32_t *d_rows,
+                              int32_t nr, const double *d_Y, int32_t ny, const int32_t *d_cols, int32_t nc,
+                              int32_t q, double *d_out, uint64_t stream) {
+    if (!phys_ok(ph) || !d_X || !d_Y || nx < 3 || ny < 3 || nr < 0 || nc < 0 || q < 1 || q > 8)
+        return FDS_ERR_ARG;
+    if (nr == 0 || nc == 0) return FDS_OK;
+    if (!d_rows || !d_cols || !d_out) return FDS_ERR_ARG;
+    FDS_TRY(ensure_gauss_tables());
+    PhysDev P = make_physdev(ph);
+    const long warps = (long)nr * nc;
+    fds_count_launch(), k_eval_cross<<<ceil_div_u(warps * 32, 256), 256, 0, (cudaStream_t)stream>>>(
+        P, d_X, nx, d_rows, nr, d_Y, ny, d_cols, nc, q, (cplx *)d_out);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
+}

@@ -1,0 +1,103 @@
+// Timing registry behind fds_timing_enable / fds_timing_report.
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "prof.cuh"
+
+namespace {
+struct Rec {
+    std::string name;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double flops = 0, bytes = 0;
+};
+struct Acc {
+    long launches = 0;
+    double ms = 0, flops = 0, bytes = 0;
+};
+std::mutex g_mu;
+bool g_on = false;
+std::vector<Rec> g_open;     // recorded, not yet resolved
+std::map<std::string, Acc> g_acc;
+
+void resolve_locked() {
+    for (auto &r : g_open) {
+        if (r.e1) {
+            cudaEventSynchronize(r.e1);
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
+                Acc &a = g_acc[r.name];
+                a.launches += 1;
+                a.ms += ms;
+                a.flops += r.flops;
+                a.bytes += r.bytes;
+            }
+            cudaEventDestroy(r.e1);
+        }
+        if (r.e0) cudaEventDestroy(r.e0);
+    }
+    g_open.clear();
+}
+}  // namespace
+
+bool prof_enabled() { return g_on; }
+
+static std::atomic<long long> g_launches{0};
+void fds_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+extern "C" int64_t fds_launch_count(void) { return (int64_t)g_launches.load(); }
+
+void prof_begin(const char *name, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    Rec r;
+    r.name = name;
+    cudaEventCreate(&r.e0);
+    cudaEventRecord(r.e0, s);
+    g_open.push_back(r);
+}
+
+void prof_end(cudaStream_t s, double flops, double bytes) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto it = g_open.rbegin(); it != g_open.rend(); ++it)
+        if (!it->e1) {
+            cudaEventCreate(&it->e1);
+            cudaEventRecord(it->e1, s);
+            it->flops = flops;
+            it->bytes = bytes;
+            break;
+        }
+    if (g_open.size() > 4096) resolve_locked();
+}
+
+extern "C" void fds_timing_enable(int32_t on) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_on = on != 0;
+}
+
+extern "C" void fds_timing_reset(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    resolve_locked();
+    g_acc.clear();
+}
+
+extern "C" int fds_timing_report(char *buf, int32_t cap) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    resolve_locked();
+    std::string out;
+    char line[256];
+    for (auto &kv : g_acc) {
+        snprintf(line, sizeof(line), "%s %ld %.6f %.6e %.6e\n", kv.first.c_str(), kv.second.launches, kv.second.ms,
+                 kv.second.flops, kv.second.bytes);
+        out += line;
+    }
+    if (buf && cap > 0) {
+        size_t n = out.size() < (size_t)(cap - 1) ? out.size() : (size_t)(cap - 1);
+        memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
+    return (int)out.size() + 1;
+}

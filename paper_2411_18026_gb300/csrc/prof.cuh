@@ -1,0 +1,24 @@
+// Per-phase device timing with CUDA events recorded on the launch stream
+// (disabled unless fds_timing_enable(1) was called).  A ProfScope brackets
+// one launch or a short group of launches under a name; work counts (flops or
+// bytes of the algorithm) may be attached for roofline reporting.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+bool prof_enabled();
+void prof_begin(const char *name, cudaStream_t s);
+void prof_end(cudaStream_t s, double flops, double bytes);
+
+struct ProfScope {
+    cudaStream_t s;
+    double flops = 0, bytes = 0;
+    bool on;
+    ProfScope(const char *name, cudaStream_t st) : s(st), on(prof_enabled()) {
+        if (on) prof_begin(name, s);
+    }
+    ~ProfScope() {
+        if (on) prof_end(s, flops, bytes);
+    }
+};

@@ -1,0 +1,266 @@
+"""Python binding of ``libfds.so`` (the C ABI in ``include/fds.h``).
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels.  Device buffers are PyTorch CUDA tensors (complex128 / int32 /
+float64 / int64), passed by ``data_ptr()``; streams are ``torch.cuda.Stream``
+handles.  The library must have been built (``build.build()``); loading fails
+loudly otherwise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfds.so")
+
+FDS_OK = 0
+FDS_ERR_ARG = -1
+FDS_ERR_CUDA = -2
+FDS_ERR_OOM = -3
+FDS_ERR_SINGULAR = -4
+FDS_ERR_NOT_CONVERGED = -5
+FDS_ERR_TIMEOUT = -6
+FDS_ERR_STATE = -7
+FDS_FP64 = 0
+
+
+class FdsError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s failed: %s (%d)" % (what, _lib_err(code), code))
+        self.code = code
+
+
+class fds_physics(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("mu", ctypes.c_double), ("rho", ctypes.c_double),
+                ("omega", ctypes.c_double), ("alpha_re", ctypes.c_double), ("alpha_im", ctypes.c_double),
+                ("alpha_set", ctypes.c_int32)]
+
+
+class fds_geometry(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("xy", ctypes.POINTER(ctypes.c_double)), ("rho", ctypes.c_double)]
+
+
+class fds_options(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int32), ("proxy_ratio", ctypes.c_double),
+                ("proxy_points", ctypes.c_int32), ("top_level", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("alpha_re", ctypes.c_double), ("alpha_im", ctypes.c_double),
+                ("alpha_set", ctypes.c_int32), ("cuda_stream", ctypes.c_uint64)]
+
+
+class fds_stats(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("levels", ctypes.c_int32), ("top_level", ctypes.c_int32),
+                ("top_size", ctypes.c_int32), ("skeleton_dofs", ctypes.c_int64 * 32),
+                ("max_rank", ctypes.c_int32 * 32), ("build_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("factor_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it is missing (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libfds.so not built: run paper_2411_18026_gb300.build.build() first")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip, lp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_void_p
+    u64, i32, f64 = ctypes.c_uint64, ctypes.c_int32, ctypes.c_double
+    L.fds_default_options.argtypes = [ctypes.POINTER(fds_options)]
+    L.fds_default_options.restype = None
+    L.fds_error_string.argtypes = [ctypes.c_int]
+    L.fds_error_string.restype = ctypes.c_char_p
+    L.fds_build.argtypes = [ctypes.POINTER(fds_geometry), f64, f64, f64, f64, ctypes.POINTER(vp)]
+    L.fds_build_ex.argtypes = [ctypes.POINTER(fds_geometry), f64, f64, f64, f64, ctypes.POINTER(fds_options),
+                               ctypes.POINTER(vp)]
+    L.fds_rhs_plane_wave.argtypes = [vp, ctypes.POINTER(i32), dp, i32, dp]
+    L.fds_rhs_plane_wave_device.argtypes = [vp, vp, vp, i32, vp, u64]
+    L.fds_solve.argtypes = [vp, dp, i32]
+    L.fds_solve_device.argtypes = [vp, vp, i32, u64]
+    L.fds_stats_get.argtypes = [vp, ctypes.POINTER(fds_stats)]
+    L.fds_level_ranks.argtypes = [vp, i32, ctypes.POINTER(i32), i32]
+    L.fds_destroy.argtypes = [vp]
+    L.fds_destroy.restype = None
+    L.fds_eval_entries.argtypes = [ctypes.POINTER(fds_physics), vp, i32, vp, i32, vp, i32, vp, u64]
+    L.fds_eval_cross.argtypes = [ctypes.POINTER(fds_physics), vp, i32, vp, i32, vp, i32, vp, i32, i32, vp, u64]
+    L.fds_id_batched.argtypes = [i32, vp, vp, vp, vp, f64, vp, vp, vp, vp, vp, u64]
+    L.fds_lu_batched.argtypes = [i32, vp, vp, vp, vp, vp, vp, u64]
+    L.fds_timing_enable.argtypes = [i32]
+    L.fds_timing_enable.restype = None
+    L.fds_timing_reset.argtypes = []
+    L.fds_timing_reset.restype = None
+    L.fds_timing_report.argtypes = [ctypes.c_char_p, i32]
+    L.fds_timing_report.restype = ctypes.c_int
+    L.fds_launch_count.argtypes = []
+    L.fds_launch_count.restype = ctypes.c_int64
+    for f in ("fds_build", "fds_build_ex", "fds_rhs_plane_wave", "fds_rhs_plane_wave_device", "fds_solve",
+              "fds_solve_device", "fds_stats_get", "fds_level_ranks", "fds_eval_entries", "fds_eval_cross",
+              "fds_id_batched", "fds_lu_batched"):
+        getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _lib_err(code):
+    try:
+        return lib().fds_error_string(int(code)).decode()
+    except Exception:
+        return "error"
+
+
+def _check(rc, what):
+    if rc < 0:
+        raise FdsError(rc, what)
+    return rc
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_uint64(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def physics(lam, mu, rho, omega, alpha=None):
+    p = fds_physics(lam, mu, rho, omega, 0.0, 0.0, 0)
+    if alpha is not None:
+        p.alpha_re, p.alpha_im, p.alpha_set = float(np.real(alpha)), float(np.imag(alpha)), 1
+    return p
+
+
+def default_options():
+    o = fds_options()
+    lib().fds_default_options(ctypes.byref(o))
+    return o
+
+
+class Handle:
+    """Owns an ``fds_handle*``; ``close()`` (or garbage collection) destroys it."""
+
+    def __init__(self, ptr, n_nodes):
+        self.ptr = ptr
+        self.n = n_nodes
+
+    def close(self):
+        if self.ptr:
+            lib().fds_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy_ratio=1.5, proxy_points=64,
+              alpha=None, stream=0):
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    g = fds_geometry(len(xy), xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(rho))
+    o = default_options()
+    o.leaf_size, o.top_level, o.proxy_ratio, o.proxy_points = leaf_size, top_level, proxy_ratio, proxy_points
+    if alpha is not None:
+        o.alpha_re, o.alpha_im, o.alpha_set = float(np.real(alpha)), float(np.imag(alpha)), 1
+    o.cuda_stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    out = ctypes.c_void_p()
+    _check(lib().fds_build_ex(ctypes.byref(g), float(omega), float(lam), float(mu), float(tol), ctypes.byref(o),
+                              ctypes.byref(out)), "fds_build")
+    return Handle(out, len(xy))
+
+
+def fds_rhs_plane_wave(h, kinds, angles):
+    kinds = np.ascontiguousarray(kinds, dtype=np.int32)
+    angles = np.ascontiguousarray(angles, dtype=np.float64)
+    f = np.zeros((len(kinds), 2 * h.n), dtype=np.complex128)      # row j = column j (col-major)
+    _check(lib().fds_rhs_plane_wave(h.ptr, kinds.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                    angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(kinds),
+                                    f.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           "fds_rhs_plane_wave")
+    return f.T
+
+
+def fds_rhs_plane_wave_device(h, d_kinds, d_angles, d_f, stream=None):
+    """d_f: complex128 CUDA tensor of shape (nrhs, 2n) (column-major 2n x nrhs)."""
+    _check(lib().fds_rhs_plane_wave_device(h.ptr, _ptr(d_kinds), _ptr(d_angles), int(d_kinds.numel()),
+                                           _ptr(d_f), _stream(stream)), "fds_rhs_plane_wave_device")
+
+
+def fds_solve(h, F):
+    """Host solve: F (2n,) or (2n, nrhs) complex; returns the solution."""
+    F = np.asarray(F, dtype=np.complex128)
+    one = F.ndim == 1
+    X = np.array((F[:, None] if one else F).T, dtype=np.complex128, order="C", copy=True)   # (nrhs, 2n)
+    _check(lib().fds_solve(h.ptr, X.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           X.shape[0]), "fds_solve")
+    return X[0] if one else X.T
+
+
+def fds_solve_device(h, d_rhs, stream=None):
+    """d_rhs: complex128 CUDA tensor (nrhs, 2n), solved in place."""
+    nrhs = d_rhs.shape[0] if d_rhs.dim() == 2 else 1
+    _check(lib().fds_solve_device(h.ptr, _ptr(d_rhs), nrhs, _stream(stream)), "fds_solve_device")
+
+
+def fds_stats_get(h):
+    s = fds_stats()
+    _check(lib().fds_stats_get(h.ptr, ctypes.byref(s)), "fds_stats_get")
+    return s
+
+
+def fds_level_ranks(h, level, nb):
+    k = (ctypes.c_int32 * (2 * nb))()
+    n = _check(lib().fds_level_ranks(h.ptr, level, k, 2 * nb), "fds_level_ranks")
+    return np.array(k[:n], dtype=np.int32).reshape(-1, 2)
+
+
+def fds_eval_entries(phys, d_xy, d_rows, d_cols, d_out, stream=None):
+    """d_out: complex128 CUDA tensor, (2 nc, 2 nr) row-major = (2nr x 2nc) column-major."""
+    _check(lib().fds_eval_entries(ctypes.byref(phys), _ptr(d_xy), d_xy.shape[0], _ptr(d_rows), d_rows.numel(),
+                                  _ptr(d_cols), d_cols.numel(), _ptr(d_out), _stream(stream)), "fds_eval_entries")
+
+
+def fds_eval_cross(phys, d_X, d_rows, d_Y, d_cols, q, d_out, stream=None):
+    _check(lib().fds_eval_cross(ctypes.byref(phys), _ptr(d_X), d_X.shape[0], _ptr(d_rows), d_rows.numel(),
+                                _ptr(d_Y), d_Y.shape[0], _ptr(d_cols), d_cols.numel(), int(q), _ptr(d_out),
+                                _stream(stream)), "fds_eval_cross")
+
+
+def fds_id_batched(d_m, d_n, d_off, d_Y, tol, d_rank, d_perm, d_poff, d_T, d_toff, stream=None):
+    _check(lib().fds_id_batched(d_m.numel(), _ptr(d_m), _ptr(d_n), _ptr(d_off), _ptr(d_Y), float(tol),
+                                _ptr(d_rank), _ptr(d_perm), _ptr(d_poff), _ptr(d_T), _ptr(d_toff),
+                                _stream(stream)), "fds_id_batched")
+
+
+def fds_lu_batched(d_d, d_off, d_A, d_piv, d_poff, d_info, stream=None):
+    _check(lib().fds_lu_batched(d_d.numel(), _ptr(d_d), _ptr(d_off), _ptr(d_A), _ptr(d_piv), _ptr(d_poff),
+                                _ptr(d_info), _stream(stream)), "fds_lu_batched")
+
+
+def fds_timing_enable(on=True):
+    lib().fds_timing_enable(1 if on else 0)
+
+
+def fds_timing_reset():
+    lib().fds_timing_reset()
+
+
+def fds_timing_report():
+    """{phase: dict(launches, ms, flops, bytes)} accumulated since the last reset."""
+    n = lib().fds_timing_report(None, 0)
+    buf = ctypes.create_string_buffer(n + 16)
+    lib().fds_timing_report(buf, n + 16)
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, launches, ms, flops, nbytes = line.split()
+        out[name] = dict(launches=int(launches), ms=float(ms), flops=float(flops), bytes=float(nbytes))
+    return out
+
+
+def fds_launch_count():
+    return int(lib().fds_launch_count())
