@@ -328,6 +328,7 @@ def main():
         "skeleton_dofs": info.get("skeleton_dofs"),
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
         "phases_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in sorted(phases.items())},
+        "quad_points_per_step": {k: v["units"] / args.steps for k, v in sorted(phases.items()) if v["units"] > 0},
     }
     print(json.dumps(line))
     if world > 1:

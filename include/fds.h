@@ -137,8 +137,9 @@ const char *fds_error_string(int code);
  * Per-phase device timing: when enabled, the library brackets its kernel
  * launches with CUDA events on the launch stream and accumulates, per phase
  * name, the launch count, the summed device time and the algorithmic work
- * (flops, bytes) the phase performs.  Off by default; process-wide.
- * fds_timing_report writes lines "name launches total_ms flops bytes" into
+ * (flops, bytes) the phase performs, and for quadrature phases the number of
+ * quadrature point evaluations (units).  Off by default; process-wide.
+ * fds_timing_report writes lines "name launches total_ms flops bytes units" into
  * buf (at most cap bytes, NUL-terminated) and returns the length it needs.
  * Reporting synchronises on the recorded events.
  */

@@ -22,6 +22,8 @@ Readings where the paper is silent (stated in the project's design notes):
     nodes, radius = largest distance to them; proxy circle radius
     ratio * radius with m' = max(m'_min, ceil(2 k_T R_p + 30)) counter-
     clockwise vertices;
+  * proxy entries use a 2x2 Gauss rule per element pair (the proxy rows only
+    have to span the far field; higher orders change no result);
   * truncation: stop at the first pivot with |R_jj| <= eps |R_11|; pivot =
     largest remaining column 2-norm, ties to the lowest index; skeleton DOFs
     are kept in pivot order.
@@ -143,7 +145,7 @@ class FDS:
     """Build (upward factorisation, Sec. 7.3 steps 1–4) and solve (steps 3–5)."""
 
     def __init__(self, P, xy, lam, mu, rho, omega, eps, leaf_size=32, top_level=1,
-                 proxy_ratio=1.5, proxy_min=64, record=False):
+                 proxy_ratio=1.5, proxy_min=64, record=False, proxy_q=2):
         self.P, self.xy, self.eps = P, np.asarray(xy, dtype=np.float64), eps
         N = len(self.xy)
         self.N = N
@@ -186,8 +188,8 @@ class FDS:
                     cols = [d for d in b.dofs if d[1] == c]
                     nodes = np.array([d[0] for d in cols], dtype=np.int32)
                     nc = len(nodes)
-                    MVp = bem.cross_entries(P, prox, pidx, self.xy, nodes, q=4)[:, c * nc:(c + 1) * nc]
-                    MUp = bem.cross_entries(P, self.xy, nodes, prox, pidx, q=4)[c * nc:(c + 1) * nc, :]
+                    MVp = bem.cross_entries(P, prox, pidx, self.xy, nodes, q=proxy_q)[:, c * nc:(c + 1) * nc]
+                    MUp = bem.cross_entries(P, self.xy, nodes, prox, pidx, q=proxy_q)[c * nc:(c + 1) * nc, :]
                     blocks = [MVp]
                     if near:
                         blocks.append(dof_entries(P, self.xy, near, cols))

@@ -16,8 +16,7 @@
 
 namespace {
 
-using fdsk::hat_pair_cross;
-using fdsk::hat_pair_same;
+using namespace fdsk;
 
 // ------------------------------------------------------------- geometry (a0)
 // Cell circle: centre of the bounding box of the hat supports of nodes
@@ -145,111 +144,175 @@ struct YDesc {
     const int *nnode, *nmask, *nrow;
 };
 
-// Proxy rows of Y^c (Sec. 7.1 eq. (mv): M^V = A^{J' J}; Sec. 7.2: M^U = A^{J J'},
-// stacked as (M^U)^H): one warp per (cell, proxy vertex, cell node).
-__global__ void __launch_bounds__(256) k_y_proxy(PhysDev P, YDesc D, const double *__restrict__ xy, int N,
-                                                 cplx *Y) {
-    const int b = blockIdx.y;
-    const int lane = threadIdx.x & 31;
-    const long job = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int mp = D.mp[b];
-    const int nu = (int)(D.uoff[b + 1] - D.uoff[b]);
-    if (job >= (long)mp * nu) return;
-    const int p = (int)(job % mp);
-    const int64_t u = D.uoff[b] + job / mp;
-    cplx f[2][2], r[2][2];
-    hat_pair_cross(P, D.pxy + 2 * D.pxoff[b], mp, p, xy, N, D.unode[u], 4, lane, f, r);
-    if (lane != 0) return;
-    const int m = D.ym[b], nnd = D.nnd[b];
-    const int pos[2] = {D.upos1[u], D.upos2[u]};
-    for (int c = 0; c < 2; ++c) {
-        if (pos[c] < 0) continue;
-        cplx *Yc = Y + D.yoff[2 * b + c] + (int64_t)pos[c] * m;
-        for (int cp = 0; cp < 2; ++cp) {
-            Yc[p + cp * mp] = f[cp][c];
-            Yc[2 * mp + nnd + p + cp * mp] = cconj(r[c][cp]);
+// ---- tile jobs: each CTA evaluates a tile of at most TILE x TILE hats
+struct LeafJob {
+    int b, I, J;
+};
+struct YJob {
+    int b, kind, r0, u0;   // kind 0: proxy vertices r0.., kind 1: near entries r0..
+};
+struct GJob {
+    int g, roff, nr, coff, nc;
+};
+
+// Leaf diagonal blocks A_p = A^{J_p J_p} (eq. (block_ax=f)): tile (I, J) of
+// the cell's hats, I <= J; off-diagonal tiles also write the transposed tile.
+__global__ void __launch_bounds__(256) k_tiles_leaf(PhysDev P, const int *__restrict__ lo, const int *__restrict__ hi,
+                                                    const double *__restrict__ xy, int N, const MatRef *A,
+                                                    const LeafJob *__restrict__ jobs) {
+    __shared__ TileSmem S;
+    const LeafJob jb = jobs[blockIdx.x];
+    const int base = lo[jb.b], n = hi[jb.b] - base;
+    load_rules(S.G, 0);
+    tile_zero(S);
+    if (threadIdx.x == 0) {
+        S.R.nh = min(TILE, n - jb.I * TILE);
+        S.C.nh = min(TILE, n - jb.J * TILE);
+        for (int k = 0; k < S.R.nh; ++k) S.R.hats[k] = base + jb.I * TILE + k;
+        for (int k = 0; k < S.C.nh; ++k) S.C.hats[k] = base + jb.J * TILE + k;
+        tile_side_build(S.R, N);
+        tile_side_build(S.C, N);
+    }
+    __syncthreads();
+    const bool diag = jb.I == jb.J;
+    tile_eval(P, S, xy, N, xy, N, true, !diag, diag);
+    __syncthreads();
+    if (diag) {
+        tile_fold(S);
+        __syncthreads();
+    }
+    const MatRef M = A[jb.b];
+    for (int e = threadIdx.x; e < S.R.nh * S.C.nh * 4; e += blockDim.x) {
+        const int r = e % S.R.nh, c = (e / S.R.nh) % S.C.nh, ij = e / (S.R.nh * S.C.nh);
+        const int i = ij >> 1, j = ij & 1;
+        const int rl = jb.I * TILE + r, cl = jb.J * TILE + c;
+        const double m = (i == j) ? 0.5 * mass_entry(xy, N, S.R.hats[r], S.C.hats[c]) : 0.0;
+        cplx v = tile_f(S, r, c, i, j);
+        v.x += m;
+        M.p[(rl + i * n) + (int64_t)(cl + j * n) * M.ld] = v;
+        if (!diag) {
+            cplx w = tile_r(S, c, r, i, j);
+            w.x += m;
+            M.p[(cl + i * n) + (int64_t)(rl + j * n) * M.ld] = w;
         }
     }
 }
 
-// Near-field rows of Y^c: one warp per (cell, near node, cell node).
-__global__ void __launch_bounds__(256) k_y_near(PhysDev P, YDesc D, const double *__restrict__ xy, int N,
-                                                cplx *Y) {
-    const int b = blockIdx.y;
-    const int lane = threadIdx.x & 31;
-    const long job = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nn = (int)(D.noff[b + 1] - D.noff[b]);
-    const int nu = (int)(D.uoff[b + 1] - D.uoff[b]);
-    if (job >= (long)nn * nu) return;
-    const int64_t k = D.noff[b] + job % nn;
-    const int64_t u = D.uoff[b] + job / nn;
-    cplx f[2][2], r[2][2];
-    hat_pair_same(P, xy, N, D.nnode[k], D.unode[u], lane, f, r);
-    if (lane != 0) return;
-    const int m = D.ym[b], nnd = D.nnd[b], mp = D.mp[b];
-    const int mask = D.nmask[k], rb = D.nrow[k];
-    const int pos[2] = {D.upos1[u], D.upos2[u]};
-    for (int c = 0; c < 2; ++c) {
-        if (pos[c] < 0) continue;
-        cplx *Yc = Y + D.yoff[2 * b + c] + (int64_t)pos[c] * m;
-        int idx = 0;
-        for (int cp = 0; cp < 2; ++cp) {
-            if (!(mask & (1 << cp))) continue;
-            Yc[2 * mp + rb + idx] = f[cp][c];
-            Yc[4 * mp + nnd + rb + idx] = cconj(r[c][cp]);
-            ++idx;
+// Rows of the ID matrices Y^c (Sec. 7.1 eq. (mv): M^V = A^{J' J}; Sec. 7.2:
+// M^U = A^{J J'} stacked as (M^U)^H): tile of proxy vertices (cross rule) or
+// near-field hats (boundary rule) against the cell's hats; the transposed
+// entries of the same quadrature points give the M^U rows.
+__global__ void __launch_bounds__(256) k_tiles_y(PhysDev P, YDesc D, const double *__restrict__ xy, int N, cplx *Y,
+                                                 const YJob *__restrict__ jobs) {
+    __shared__ TileSmem S;
+    __shared__ int rowv[TILE][2], colp[TILE][2];
+    const YJob jb = jobs[blockIdx.x];
+    const int b = jb.b, mp = D.mp[b];
+    const int64_t uo0 = D.uoff[b];
+    const int nu = (int)(D.uoff[b + 1] - uo0);
+    const bool prox = jb.kind == 0;
+    load_rules(S.G, prox ? 2 : 0);
+    tile_zero(S);
+    if (threadIdx.x == 0) {
+        if (prox) {
+            S.R.nh = min(TILE, mp - jb.r0);
+            for (int k = 0; k < S.R.nh; ++k) {
+                S.R.hats[k] = jb.r0 + k;
+                rowv[k][0] = jb.r0 + k;
+                rowv[k][1] = jb.r0 + k + mp;
+            }
+        } else {
+            const int64_t n0 = D.noff[b];
+            const int nn = (int)(D.noff[b + 1] - n0);
+            S.R.nh = min(TILE, nn - jb.r0);
+            for (int k = 0; k < S.R.nh; ++k) {
+                const int64_t q = n0 + jb.r0 + k;
+                S.R.hats[k] = D.nnode[q];
+                const int mask = D.nmask[q], rb = 2 * mp + D.nrow[q];
+                rowv[k][0] = (mask & 1) ? rb : -1;
+                rowv[k][1] = (mask & 2) ? rb + (mask & 1) : -1;
+            }
+        }
+        S.C.nh = min(TILE, nu - jb.u0);
+        for (int k = 0; k < S.C.nh; ++k) {
+            S.C.hats[k] = D.unode[uo0 + jb.u0 + k];
+            colp[k][0] = D.upos1[uo0 + jb.u0 + k];
+            colp[k][1] = D.upos2[uo0 + jb.u0 + k];
+        }
+        tile_side_build(S.R, prox ? mp : N);
+        tile_side_build(S.C, N);
+    }
+    __syncthreads();
+    const double *X = prox ? D.pxy + 2 * D.pxoff[b] : xy;
+    const int NX = prox ? mp : N;
+    tile_eval(P, S, X, NX, xy, N, !prox, true, false);
+    __syncthreads();
+    const int m = D.ym[b];
+    const int uoff = 2 * mp + D.nnd[b];
+    for (int e = threadIdx.x; e < S.R.nh * S.C.nh * 4; e += blockDim.x) {
+        const int r = e % S.R.nh, c = (e / S.R.nh) % S.C.nh, ij = e / (S.R.nh * S.C.nh);
+        const int i = ij >> 1, j = ij & 1;
+        const double ms = (!prox && i == j) ? 0.5 * mass_entry(xy, N, S.R.hats[r], S.C.hats[c]) : 0.0;
+        // forward: test = row item (component i), trial = cell hat (component j) -> Y^j
+        if (rowv[r][i] >= 0 && colp[c][j] >= 0) {
+            cplx v = tile_f(S, r, c, i, j);
+            v.x += ms;
+            Y[D.yoff[2 * b + j] + rowv[r][i] + (int64_t)colp[c][j] * m] = v;
+        }
+        // transposed: test = cell hat (component i), trial = row item (component j) -> conj into Y^i
+        if (colp[c][i] >= 0 && rowv[r][j] >= 0) {
+            cplx w = tile_r(S, c, r, i, j);
+            w.x += ms;
+            Y[D.yoff[2 * b + i] + uoff + rowv[r][j] + (int64_t)colp[c][i] * m] = cconj(w);
         }
     }
 }
 
-// Leaf diagonal blocks A_p = A^{J_p J_p} (eq. (block_ax=f)): warp per node pair
-// s <= t of the cell, producing (s,t) and (t,s) from the same quadrature points.
-__global__ void __launch_bounds__(256) k_leaf_A(PhysDev P, const int *__restrict__ lo, const int *__restrict__ hi,
-                                                const double *__restrict__ xy, int N, MatRef *A) {
-    const int b = blockIdx.y;
-    const int lane = threadIdx.x & 31;
-    const long job = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int n = hi[b] - lo[b];
-    if (job >= (long)n * n) return;
-    const int si = (int)(job % n), ti = (int)(job / n);
-    if (si > ti) return;
-    cplx f[2][2], r[2][2];
-    hat_pair_same(P, xy, N, lo[b] + si, lo[b] + ti, lane, f, r);
-    if (lane != 0) return;
-    const MatRef M = A[b];
-    for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 2; ++j) {
-            M.p[(si + i * n) + (int64_t)(ti + j * n) * M.ld] = f[i][j];
-            if (si != ti) M.p[(ti + i * n) + (int64_t)(si + j * n) * M.ld] = r[i][j];
+// Blocks of original entries between two disjoint hat lists of a group:
+// sibling blocks R of eq. (A_rearrangement) and the off-diagonal blocks of the
+// top system.  Items carry the matrix index of each component (or -1).
+__global__ void __launch_bounds__(256) k_tiles_group(PhysDev P, const int *__restrict__ gnode,
+                                                     const int *__restrict__ gi1, const int *__restrict__ gi2,
+                                                     const double *__restrict__ xy, int N, const MatRef *M,
+                                                     const GJob *__restrict__ jobs) {
+    __shared__ TileSmem S;
+    __shared__ int ri[TILE][2], ci[TILE][2];
+    const GJob jb = jobs[blockIdx.x];
+    load_rules(S.G, 0);
+    tile_zero(S);
+    if (threadIdx.x == 0) {
+        S.R.nh = jb.nr;
+        S.C.nh = jb.nc;
+        for (int k = 0; k < jb.nr; ++k) {
+            S.R.hats[k] = gnode[jb.roff + k];
+            ri[k][0] = gi1[jb.roff + k];
+            ri[k][1] = gi2[jb.roff + k];
         }
-}
-
-// Group blocks of original entries (sibling R blocks of eq. (A_rearrangement)
-// and the off-diagonal blocks of the top system): warp per node pair (u, v)
-// of a group with tag(u) < tag(v).
-__global__ void __launch_bounds__(256) k_group_pairs(PhysDev P, const int64_t *__restrict__ goff,
-                                                     const int *__restrict__ gnode, const int *__restrict__ gtag,
-                                                     const int *__restrict__ grow1, const int *__restrict__ grow2,
-                                                     const double *__restrict__ xy, int N, const MatRef *M) {
-    const int g = blockIdx.y;
-    const int lane = threadIdx.x & 31;
-    const long job = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t o = goff[g];
-    const int nu = (int)(goff[g + 1] - o);
-    if (job >= (long)nu * nu) return;
-    const int64_t u = o + job % nu, v = o + job / nu;
-    if (!(gtag[u] < gtag[v])) return;
-    cplx f[2][2], r[2][2];
-    hat_pair_same(P, xy, N, gnode[u], gnode[v], lane, f, r);
-    if (lane != 0) return;
-    const MatRef A = M[g];
-    const int pu[2] = {grow1[u], grow2[u]}, pv[2] = {grow1[v], grow2[v]};
-    for (int i = 0; i < 2; ++i) {
-        if (pu[i] < 0) continue;
-        for (int j = 0; j < 2; ++j) {
-            if (pv[j] < 0) continue;
-            A.p[pu[i] + (int64_t)pv[j] * A.ld] = f[i][j];
-            A.p[pv[j] + (int64_t)pu[i] * A.ld] = r[j][i];
+        for (int k = 0; k < jb.nc; ++k) {
+            S.C.hats[k] = gnode[jb.coff + k];
+            ci[k][0] = gi1[jb.coff + k];
+            ci[k][1] = gi2[jb.coff + k];
+        }
+        tile_side_build(S.R, N);
+        tile_side_build(S.C, N);
+    }
+    __syncthreads();
+    tile_eval(P, S, xy, N, xy, N, true, true, false);
+    __syncthreads();
+    const MatRef A = M[jb.g];
+    for (int e = threadIdx.x; e < S.R.nh * S.C.nh * 4; e += blockDim.x) {
+        const int r = e % S.R.nh, c = (e / S.R.nh) % S.C.nh, ij = e / (S.R.nh * S.C.nh);
+        const int i = ij >> 1, j = ij & 1;
+        const double ms = (i == j) ? 0.5 * mass_entry(xy, N, S.R.hats[r], S.C.hats[c]) : 0.0;
+        if (ri[r][i] >= 0 && ci[c][j] >= 0) {
+            cplx v = tile_f(S, r, c, i, j);
+            v.x += ms;
+            A.p[ri[r][i] + (int64_t)ci[c][j] * A.ld] = v;
+        }
+        if (ci[c][i] >= 0 && ri[r][j] >= 0) {
+            cplx w = tile_r(S, c, r, i, j);
+            w.x += ms;
+            A.p[ci[c][i] + (int64_t)ri[r][j] * A.ld] = w;
         }
     }
 }
@@ -325,6 +388,29 @@ __global__ void k_place_top(const MatRef *__restrict__ Ab, const int64_t *__rest
         top.p[(o + i) + (o + j) * top.ld] = S.p[i + (int64_t)j * S.ld];
     }
 }
+
+// Counts the quadrature points of the a1 launches inside a ProfScope (only
+// while timing is enabled; synchronises the stream to read the count).
+struct PointCount {
+    bool on;
+    cudaStream_t s;
+    explicit PointCount(cudaStream_t st) : on(prof_enabled()), s(st) {
+        if (!on) return;
+        const unsigned long long z = 0;
+        const int one = 1;
+        cudaMemcpyToSymbolAsync(d_quad_points, &z, sizeof(z), 0, cudaMemcpyHostToDevice, s);
+        cudaMemcpyToSymbolAsync(d_count_points, &one, sizeof(one), 0, cudaMemcpyHostToDevice, s);
+    }
+    double read() {
+        if (!on) return 0.0;
+        unsigned long long v = 0;
+        const int zero = 0;
+        cudaMemcpyFromSymbolAsync(&v, d_quad_points, sizeof(v), 0, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyToSymbolAsync(d_count_points, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, s);
+        cudaStreamSynchronize(s);
+        return (double)v;
+    }
+};
 
 int sync_check(cudaStream_t s) {
     FDS_CUDA_TRY(cudaStreamSynchronize(s));
@@ -407,23 +493,50 @@ int alloc_level_A(Level &L, cudaStream_t s) {
     return FDS_OK;
 }
 
-int launch_group_pairs(fds_handle *h, const std::vector<int64_t> &goff, const std::vector<int> &gnode,
-                       const std::vector<int> &gtag, const std::vector<int> &grow1, const std::vector<int> &grow2,
-                       const MatRef *d_M, cudaStream_t s) {
+// Original-entry blocks between the tagged parts of each group (tags
+// ascending: every pair of distinct tags tA < tB is evaluated once, both
+// orientations).  Items of group g occupy [goff[g], goff[g+1]) sorted by tag.
+int launch_group_blocks(fds_handle *h, const char *name, const std::vector<int64_t> &goff,
+                        const std::vector<int> &gnode, const std::vector<int> &gtag, const std::vector<int> &grow1,
+                        const std::vector<int> &grow2, const MatRef *d_M, cudaStream_t s) {
     const int ng = (int)goff.size() - 1;
     if (ng <= 0 || gnode.empty()) return FDS_OK;
-    DBuf<int64_t> d_goff;
-    DBuf<int> d_gnode, d_gtag, d_g1, d_g2;
-    FDS_TRY(d_goff.upload(goff, s));
+    std::vector<GJob> jobs;
+    for (int g = 0; g < ng; ++g) {
+        // split the group's items into runs of equal tag
+        std::vector<std::pair<int64_t, int64_t>> runs;
+        for (int64_t u = goff[g]; u < goff[g + 1];) {
+            int64_t v = u;
+            while (v < goff[g + 1] && gtag[v] == gtag[u]) ++v;
+            runs.push_back({u, v});
+            u = v;
+        }
+        for (size_t a = 0; a < runs.size(); ++a)
+            for (size_t b = a + 1; b < runs.size(); ++b)
+                for (int64_t r0 = runs[a].first; r0 < runs[a].second; r0 += TILE)
+                    for (int64_t c0 = runs[b].first; c0 < runs[b].second; c0 += TILE) {
+                        GJob j;
+                        j.g = g;
+                        j.roff = (int)r0;
+                        j.nr = (int)std::min<int64_t>(TILE, runs[a].second - r0);
+                        j.coff = (int)c0;
+                        j.nc = (int)std::min<int64_t>(TILE, runs[b].second - c0);
+                        jobs.push_back(j);
+                    }
+    }
+    if (jobs.empty()) return FDS_OK;
+    DBuf<int> d_gnode, d_g1, d_g2;
+    DBuf<GJob> d_jobs;
     FDS_TRY(d_gnode.upload(gnode, s));
-    FDS_TRY(d_gtag.upload(gtag, s));
     FDS_TRY(d_g1.upload(grow1, s));
     FDS_TRY(d_g2.upload(grow2, s));
-    int64_t maxnu = 0;
-    for (int g = 0; g < ng; ++g) maxnu = std::max(maxnu, goff[g + 1] - goff[g]);
-    dim3 grid(ceil_div_u(maxnu * maxnu * 32, 256), ng);
-    fds_count_launch(), k_group_pairs<<<grid, 256, 0, s>>>(h->P, d_goff.p, d_gnode.p, d_gtag.p, d_g1.p, d_g2.p, h->d_xy.p, h->N, d_M);
+    FDS_TRY(d_jobs.upload(jobs, s));
+    PointCount pc(s);
+    ProfScope ps(name, s);
+    fds_count_launch(), k_tiles_group<<<(unsigned)jobs.size(), 256, 0, s>>>(h->P, d_gnode.p, d_g1.p, d_g2.p,
+                                                                          h->d_xy.p, h->N, d_M, d_jobs.p);
     FDS_CUDA_TRY(cudaGetLastError());
+    ps.units = pc.read();
     return sync_check(s);   // the temporaries above are freed on return
 }
 
@@ -487,10 +600,20 @@ int fds_build_impl(fds_handle *h) {
         DBuf<int> d_lo, d_hi;
         FDS_TRY(d_lo.upload(lo, s));
         FDS_TRY(d_hi.upload(hi, s));
-        dim3 grid(ceil_div_u((long)nmax * nmax * 32, 256), Lf.nb);
+        std::vector<LeafJob> jobs;
+        for (int b = 0; b < Lf.nb; ++b) {
+            const int T = (hi[b] - lo[b] + TILE - 1) / TILE;
+            for (int I = 0; I < T; ++I)
+                for (int J = I; J < T; ++J) jobs.push_back(LeafJob{b, I, J});
+        }
+        DBuf<LeafJob> d_jobs;
+        FDS_TRY(d_jobs.upload(jobs, s));
         {
+            PointCount pc(s);
             ProfScope ps("a1.leaf_blocks", s);
-            fds_count_launch(), k_leaf_A<<<grid, 256, 0, s>>>(h->P, d_lo.p, d_hi.p, h->d_xy.p, N, Lf.rLU.p);
+            fds_count_launch(), k_tiles_leaf<<<(unsigned)jobs.size(), 256, 0, s>>>(h->P, d_lo.p, d_hi.p, h->d_xy.p, N,
+                                                                                 Lf.rLU.p, d_jobs.p);
+            ps.units = pc.read();
         }
         FDS_CUDA_TRY(cudaGetLastError());
         FDS_TRY(sync_check(s));
@@ -621,17 +744,25 @@ int fds_build_impl(fds_handle *h) {
         D.uoff = C.d_uoff.p; D.unode = C.d_unode.p; D.upos1 = C.d_upos1.p; D.upos2 = C.d_upos2.p;
         D.noff = d_noff.p; D.nnode = d_nnode.p; D.nmask = d_nmask.p; D.nrow = d_nrow.p;
         // ---- kernel evaluation (a1)
-        if (maxjp > 0) {
-            dim3 g(ceil_div_u(maxjp * 32, 256), nb);
-            ProfScope ps("a1.proxy_rows", s);
-            fds_count_launch(), k_y_proxy<<<g, 256, 0, s>>>(h->P, D, h->d_xy.p, N, d_Y.p);
+        for (int kind = 0; kind < 2; ++kind) {
+            std::vector<YJob> jobs;
+            for (int b = 0; b < nb; ++b) {
+                const int nu = (int)(C.uoff[b + 1] - C.uoff[b]);
+                const int nrows = kind == 0 ? C.mprox[b] : (int)(noff[b + 1] - noff[b]);
+                for (int u0 = 0; u0 < nu; u0 += TILE)
+                    for (int r0 = 0; r0 < nrows; r0 += TILE) jobs.push_back(YJob{b, kind, r0, u0});
+            }
+            DBuf<YJob> d_jobs;
+            FDS_TRY(d_jobs.upload(jobs, s));
+            if (!jobs.empty()) {
+                PointCount pc(s);
+                ProfScope ps(kind == 0 ? "a1.proxy_rows" : "a1.near_rows", s);
+                fds_count_launch(), k_tiles_y<<<(unsigned)jobs.size(), 256, 0, s>>>(h->P, D, h->d_xy.p, N, d_Y.p,
+                                                                                   d_jobs.p);
+                ps.units = pc.read();
+            }
             FDS_CUDA_TRY(cudaGetLastError());
-        }
-        if (maxjn > 0) {
-            dim3 g(ceil_div_u(maxjn * 32, 256), nb);
-            ProfScope ps("a1.near_rows", s);
-            fds_count_launch(), k_y_near<<<g, 256, 0, s>>>(h->P, D, h->d_xy.p, N, d_Y.p);
-            FDS_CUDA_TRY(cudaGetLastError());
+            FDS_TRY(sync_check(s));
         }
         // ---- interpolative decomposition (a2)
         {
@@ -798,10 +929,7 @@ int fds_build_impl(fds_handle *h) {
             }
             goff[p + 1] = (int64_t)gnode.size();
         }
-        {
-            ProfScope ps("a1.sibling_blocks", s);
-            FDS_TRY(launch_group_pairs(h, goff, gnode, gtag, g1, g2, Pn.rLU.p, s));
-        }
+        FDS_TRY(launch_group_blocks(h, "a1.sibling_blocks", goff, gnode, gtag, g1, g2, Pn.rLU.p, s));
     }
 
     // ---- top level (Sec. 6.3): dense system over the cells of level l0
@@ -829,10 +957,7 @@ int fds_build_impl(fds_handle *h) {
         goff.push_back((int64_t)gnode.size());
         std::vector<MatRef> ht = {top};
         FDS_TRY(h->rtop.upload(ht, s));
-        if (T.nb > 1) {
-            ProfScope ps("a1.top_blocks", s);
-            FDS_TRY(launch_group_pairs(h, goff, gnode, gtag, g1, g2, h->rtop.p, s));
-        }
+        if (T.nb > 1) FDS_TRY(launch_group_blocks(h, "a1.top_blocks", goff, gnode, gtag, g1, g2, h->rtop.p, s));
         std::vector<int64_t> po = {0, h->Dtop};
         FDS_TRY(h->d_ptop_off.upload(po, s));
         FDS_TRY(h->ptop.alloc(h->Dtop));

@@ -50,6 +50,7 @@ struct PhysDev {
     double kT, kL;
     double rw2;        // rho omega^2
     double c2;         // 2 / kT^2
+    double lhalfT, lhalfL;   // ln(kT/2), ln(kL/2)
     cplx alpha;        // Burton–Miller coupling
 };
 

@@ -18,6 +18,8 @@ PhysDev make_physdev(const fds_physics *ph) {
     P.kT = P.omega / sqrt(P.mu / P.rho);
     P.rw2 = P.rho * P.omega * P.omega;
     P.c2 = 2.0 / (P.kT * P.kT);
+    P.lhalfT = log(0.5 * P.kT);
+    P.lhalfL = log(0.5 * P.kL);
     if (ph->alpha_set)
         P.alpha = mkc(ph->alpha_re, ph->alpha_im);
     else
@@ -71,42 +73,38 @@ int gauss_tables_host(GaussTables *T) {
 
 namespace {
 
-// One warp per (row hat, column hat) pair; column-major output
-// out[(r + i nr) + (c + j nc) * ld], ld = 2 nr.
-__global__ void __launch_bounds__(256) k_eval_entries(PhysDev P, const double *__restrict__ xy, int N,
-                                                      const int *__restrict__ rows, int nr,
-                                                      const int *__restrict__ cols, int nc, cplx *out) {
-    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= (long)nr * nc) return;
-    const int r = (int)(warp % nr), c = (int)(warp / nr);
-    cplx v[2][2];
-    fdsk::hat_pair_same(P, xy, N, rows[r], cols[c], lane, v, nullptr);
-    if (lane == 0) {
-        const long ld = 2L * nr;
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) out[(r + (long)i * nr) + (c + (long)j * nc) * ld] = v[i][j];
-    }
-}
+using namespace fdsk;
 
-__global__ void __launch_bounds__(256) k_eval_cross(PhysDev P, const double *__restrict__ X, int NX,
-                                                    const int *__restrict__ rows, int nr,
-                                                    const double *__restrict__ Y, int NY,
-                                                    const int *__restrict__ cols, int nc, int q, cplx *out) {
-    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= (long)nr * nc) return;
-    const int r = (int)(warp % nr), c = (int)(warp / nr);
-    cplx v[2][2];
-    fdsk::hat_pair_cross(P, X, NX, rows[r], Y, NY, cols[c], q, lane, v, nullptr);
-    if (lane == 0) {
-        const long ld = 2L * nr;
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) out[(r + (long)i * nr) + (c + (long)j * nc) * ld] = v[i][j];
+// Stage kernels: one CTA per (row chunk, column chunk) tile; forward entries
+// only (the row and column lists may overlap).  Output column-major
+// out[(r + i nr) + (c + j nc) * 2 nr].
+__global__ void __launch_bounds__(256) k_stage_tiles(PhysDev P, const double *__restrict__ X, int NX,
+                                                     const int *__restrict__ rows, int nr,
+                                                     const double *__restrict__ Y, int NY,
+                                                     const int *__restrict__ cols, int nc, int q, int same,
+                                                     cplx *out) {
+    __shared__ TileSmem S;
+    const int r0 = blockIdx.x * TILE, c0 = blockIdx.y * TILE;
+    load_rules(S.G, same ? 0 : q);
+    tile_zero(S);
+    if (threadIdx.x == 0) {
+        S.R.nh = min(TILE, nr - r0);
+        S.C.nh = min(TILE, nc - c0);
+        for (int k = 0; k < S.R.nh; ++k) S.R.hats[k] = rows[r0 + k];
+        for (int k = 0; k < S.C.nh; ++k) S.C.hats[k] = cols[c0 + k];
+        tile_side_build(S.R, NX);
+        tile_side_build(S.C, same ? NX : NY);
+    }
+    __syncthreads();
+    tile_eval(P, S, X, NX, Y, NY, same != 0, false, false);
+    __syncthreads();
+    const long ld = 2L * nr;
+    for (int e = threadIdx.x; e < S.R.nh * S.C.nh * 4; e += blockDim.x) {
+        const int r = e % S.R.nh, c = (e / S.R.nh) % S.C.nh, ij = e / (S.R.nh * S.C.nh);
+        const int i = ij >> 1, j = ij & 1;
+        cplx v = tile_f(S, r, c, i, j);
+        if (same && i == j) v.x += 0.5 * mass_entry(X, NX, S.R.hats[r], S.C.hats[c]);
+        out[(r0 + r + (long)i * nr) + (c0 + c + (long)j * nc) * ld] = v;
     }
 }
 
@@ -124,9 +122,9 @@ extern "C" int fds_eval_entries(const fds_physics *ph, const double *d_xy, int32
     if (!d_rows || !d_cols || !d_out) return FDS_ERR_ARG;
     FDS_TRY(ensure_gauss_tables());
     PhysDev P = make_physdev(ph);
-    const long warps = (long)nr * nc;
-    fds_count_launch(), k_eval_entries<<<ceil_div_u(warps * 32, 256), 256, 0, (cudaStream_t)stream>>>(
-        P, d_xy, n, d_rows, nr, d_cols, nc, (cplx *)d_out);
+    dim3 grid(ceil_div_u(nr, TILE), ceil_div_u(nc, TILE));
+    fds_count_launch(), k_stage_tiles<<<grid, 256, 0, (cudaStream_t)stream>>>(
+        P, d_xy, n, d_rows, nr, d_xy, n, d_cols, nc, 0, 1, (cplx *)d_out);
     FDS_CUDA_TRY(cudaGetLastError());
     return FDS_OK;
 }
@@ -140,9 +138,9 @@ extern "C" int fds_eval_cross(const fds_physics *ph, const double *d_X, int32_t 
     if (!d_rows || !d_cols || !d_out) return FDS_ERR_ARG;
     FDS_TRY(ensure_gauss_tables());
     PhysDev P = make_physdev(ph);
-    const long warps = (long)nr * nc;
-    fds_count_launch(), k_eval_cross<<<ceil_div_u(warps * 32, 256), 256, 0, (cudaStream_t)stream>>>(
-        P, d_X, nx, d_rows, nr, d_Y, ny, d_cols, nc, q, (cplx *)d_out);
+    dim3 grid(ceil_div_u(nr, TILE), ceil_div_u(nc, TILE));
+    fds_count_launch(), k_stage_tiles<<<grid, 256, 0, (cudaStream_t)stream>>>(
+        P, d_X, nx, d_rows, nr, d_Y, ny, d_cols, nc, q, 0, (cplx *)d_out);
     FDS_CUDA_TRY(cudaGetLastError());
     return FDS_OK;
 }

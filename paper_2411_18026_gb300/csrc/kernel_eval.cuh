@@ -11,7 +11,7 @@
 //      psi phi' -2 mu [t^x_i d_j g_T - n^x_i eps_jk d_k g_L]
 //      psi' phi -2 mu [n^y_j eps_ik d_k g_L - t^y_j d_i g_T]
 //      psi'phi'  2 mu [2 delta_ij g_T + c eps_ik eps_jp d_k d_p F]
-// with d_k d_p F = -(i/4) P zh zh + (i/4) Q (2 zh zh - I),
+// with d_k d_p F = (i/4) [(2Q - P) zh_k zh_p - Q delta_kp],
 // P = kT^2 H0(kT r) - kL^2 H0(kL r), Q = kT^2 E(kT r) - kL^2 E(kL r),
 // E(z) = (z H1(z) + 2i/pi)/z^2.
 //
@@ -20,126 +20,122 @@
 //             4 in v; both triangles (u and -u) at every node -> principal value
 //   adjacent  Duffy split at the shared vertex, xi = w^4, 16 x 8 nodes
 //   near      midpoint distance < 2.5 max(h): halve both elements, 8x8 per sub-pair
-//   mid       < 6 max(h): 8x8;   far: 6x6
-//   cross     (proxy polygon vs boundary): fixed q x q.
+//   mid       < 6 max(h): 8x8;   far: < 12 max(h): 6x6;   far2: 4x4
+//   cross     (proxy polygon vs boundary): fixed q x q (the build uses q = 2).
+//
+// Work is organised in tiles of at most TILE test hats x TILE trial hats:
+// the hats' supporting elements are deduplicated (consecutive hats share an
+// element), every element-pair integral is evaluated once for all four P1
+// basis combinations and, optionally, for the transposed entry from the same
+// quadrature points, then scattered into the tile's entries in shared memory.
 #pragma once
 
 #include "common.cuh"
 
 namespace fdsk {
 
-// ---------------------------------------------------------------- Bessel
-// H0, H1 of the first kind from CUDA's j0/y0/j1/y1, and E(z) with the small-z
-// branch from the ascending series of J_1 and Y_1 (Abramowitz & Stegun 9.1.10,
-// 9.1.11), which keeps the difference of two E values free of pole cancellation.
-struct Hank {
-    cplx h0T, h1T, h0L, h1L, eT, eL;
+constexpr int TILE = 15;        // 15 consecutive hats span 16 elements: 256 element pairs
+
+// Quadrature points evaluated (point pairs x orientations), counted when
+// d_count_points is set; read back by the timing registry.
+static __device__ unsigned long long d_quad_points;
+static __device__ int d_count_points;
+constexpr int TILE_EL = 2 * TILE;      // worst case: no shared elements
+
+// ---------------------------------------------------------------- rules
+// Gauss–Legendre nodes/weights on [0,1] copied into shared memory at the
+// start of a kernel (divergent indices would serialise __constant__ reads).
+struct Rules {
+    double x4[4], w4[4], x6[6], w6[6], x8[8], w8[8], x16[16], w16[16], x20[20], w20[20];
+    double xq[8], wq[8];
+    int q;
 };
 
-__device__ __forceinline__ cplx ehat_series(double z) {
-    // sum_{m>=0} t_m (1/2),  S = sum_{m>=0} (psi(m+1) + psi(m+2)) t_m,
-    // t_m = (-z^2/4)^m / (m! (m+1)!)
-    const double q = -0.25 * z * z;
-    double t = 1.0, half_sum = 0.0, S = 0.0;
-    double hm = 0.0;   // harmonic number H_m
-    const double g = 0.57721566490153286061;
-#pragma unroll
-    for (int m = 0; m < 11; ++m) {
-        // psi(m+1) + psi(m+2) = 2(H_m - g) + 1/(m+1)
-        double ps = 2.0 * (hm - g) + 1.0 / (m + 1.0);
-        half_sum += 0.5 * t;
-        S += ps * t;
-        hm += 1.0 / (m + 1.0);
-        t *= q / ((m + 1.0) * (m + 2.0));
+__device__ __forceinline__ void load_rules(Rules &R, int qcross) {
+    for (int i = threadIdx.x; i < 20; i += blockDim.x) {
+        if (i < 4) { R.x4[i] = c_gauss.x[4][i]; R.w4[i] = c_gauss.w[4][i]; }
+        if (i < 6) { R.x6[i] = c_gauss.x[6][i]; R.w6[i] = c_gauss.w[6][i]; }
+        if (i < 8) { R.x8[i] = c_gauss.x[8][i]; R.w8[i] = c_gauss.w[8][i]; }
+        if (i < 16) { R.x16[i] = c_gauss.x[16][i]; R.w16[i] = c_gauss.w[16][i]; }
+        R.x20[i] = c_gauss.x[20][i];
+        R.w20[i] = c_gauss.w[20][i];
+        if (qcross > 0 && i < qcross) { R.xq[i] = c_gauss.x[qcross][i]; R.wq[i] = c_gauss.w[qcross][i]; }
     }
-    double re = half_sum;   // J1(z)/z
-    double im = (2.0 / FDS_PI) * log(0.5 * z) * half_sum - S * (0.5 / FDS_PI);
-    return mkc(re, im);
+    if (threadIdx.x == 0) R.q = qcross;
 }
 
-__device__ __forceinline__ void hankels_at(double z, cplx &h0, cplx &h1, cplx &e) {
-    double a0 = j0(z), b0 = y0(z), a1 = j1(z), b1 = y1(z);
-    h0 = mkc(a0, b0);
-    h1 = mkc(a1, b1);
-    if (z < 1.0) {
-        e = ehat_series(z);
+// ---------------------------------------------------------------- Bessel
+// H0^(1)(z), H1^(1)(z) and E(z) = (z H1(z) + 2i/pi)/z^2.  For z < 2 from the
+// ascending series (Abramowitz & Stegun 9.1.10, 9.1.11, 9.1.13), sharing the
+// terms s_m = (-z^2/4)^m/(m!)^2, u_m = s_m/(m+1) and ln(z/2):
+//   J0 = sum s_m,  J1/z = sum u_m / 2,
+//   Y0 = (2/pi) [ (ln(z/2) + g) J0 - sum_{m>=1} H_m s_m ],
+//   Im E = (2/pi) ln(z/2) J1/z - (1/(2 pi)) sum (psi(m+1)+psi(m+2)) u_m,
+//   psi(m+1)+psi(m+2) = 2 (H_m - g) + 1/(m+1),  Y1 = z Im E - 2/(pi z).
+// For z >= 2 from CUDA's j0/y0/j1/y1.
+struct Hk {
+    cplx h0, h1, e;
+};
+
+__device__ __forceinline__ Hk hankel_k(double z, double lhalf) {
+    Hk H;
+    if (z < 2.0) {
+        const double g = 0.57721566490153286061;
+        const double t = 0.25 * z * z;
+        double s = 1.0, hm = 0.0;
+        double J0 = 1.0, Su = 1.0, SH = 0.0, Sp = 1.0 - 2.0 * g;
+        for (int m = 1; m < 20; ++m) {
+            s *= -t / ((double)m * m);
+            hm += 1.0 / m;
+            const double u = s / (m + 1.0);
+            J0 += s;
+            Su += u;
+            SH = fma(hm, s, SH);
+            Sp = fma(2.0 * (hm - g) + 1.0 / (m + 1.0), u, Sp);
+            if (fabs(s) < 1e-18) break;
+        }
+        const double j1z = 0.5 * Su;                      // J1(z)/z
+        const double Y0 = (2.0 / FDS_PI) * ((lhalf + g) * J0 - SH);
+        const double eim = (2.0 / FDS_PI) * lhalf * j1z - Sp * (0.5 / FDS_PI);
+        H.h0 = mkc(J0, Y0);
+        H.e = mkc(j1z, eim);
+        H.h1 = mkc(z * j1z, z * eim - 2.0 / (FDS_PI * z));
     } else {
-        double iz2 = 1.0 / (z * z);
-        e = mkc(z * a1 * iz2, (z * b1 + 2.0 / FDS_PI) * iz2);
+        const double a0 = j0(z), b0 = y0(z), a1 = j1(z), b1 = y1(z);
+        const double iz2 = 1.0 / (z * z);
+        H.h0 = mkc(a0, b0);
+        H.h1 = mkc(a1, b1);
+        H.e = mkc(z * a1 * iz2, (z * b1 + 2.0 / FDS_PI) * iz2);
     }
-}
-
-__device__ __forceinline__ Hank hankels(const PhysDev &P, double r) {
-    Hank H;
-    hankels_at(P.kT * r, H.h0T, H.h1T, H.eT);
-    hankels_at(P.kL * r, H.h0L, H.h1L, H.eL);
     return H;
 }
 
-// ---------------------------------------------------------------- kernel
-// Weighted kernel contribution: acc_ij += w (b0 K0 + b1 K1 + b2 K2 + b3 K3)
-// for the operator D + alpha N at relative position z (test normal nx, trial
-// normal ny), with the Hankel values of r = |z| precomputed.
-__device__ __forceinline__ void kernel_accum(const PhysDev &P, const Hank &H, double2 z, double r,
-                                             double2 nx, double2 ny, double w, double b0, double b1,
-                                             double b2, double b3, cplx acc[2][2]) {
-    const double ir = 1.0 / r;
-    const double zh[2] = {z.x * ir, z.y * ir};
-    const double nxv[2] = {nx.x, nx.y}, nyv[2] = {ny.x, ny.y};
-    const double txv[2] = {nx.y, -nx.x}, tyv[2] = {ny.y, -ny.x};
+// ---------------------------------------------------------------- radial part
+// Quantities of the kernel that depend on r only (shared by both entry
+// orientations of a point pair).
+struct Radial {
+    cplx gT, gL;       // g_T, g_L
+    cplx gTp, gLp;     // g_T', g_L'  (d/dr)
+    cplx a, b;         // d_k d_p F = a zh_k zh_p - b delta_kp
+};
+
+__device__ __forceinline__ Radial radial(const PhysDev &P, double r) {
+    const double lr = log(r);
+    const Hk T = hankel_k(P.kT * r, P.lhalfT + lr);
+    const Hk L = hankel_k(P.kL * r, P.lhalfL + lr);
+    Radial R;
     // g = (i/4) H0 ; g' = -(i/4) k H1
-    const cplx gT = mkc(-0.25 * H.h0T.y, 0.25 * H.h0T.x);
-    const cplx gL = mkc(-0.25 * H.h0L.y, 0.25 * H.h0L.x);
-    const cplx gTp = mkc(0.25 * P.kT * H.h1T.y, -0.25 * P.kT * H.h1T.x);
-    const cplx gLp = mkc(0.25 * P.kL * H.h1L.y, -0.25 * P.kL * H.h1L.x);
+    R.gT = mkc(-0.25 * T.h0.y, 0.25 * T.h0.x);
+    R.gL = mkc(-0.25 * L.h0.y, 0.25 * L.h0.x);
+    R.gTp = mkc(0.25 * P.kT * T.h1.y, -0.25 * P.kT * T.h1.x);
+    R.gLp = mkc(0.25 * P.kL * L.h1.y, -0.25 * P.kL * L.h1.x);
     const double kT2 = P.kT * P.kT, kL2 = P.kL * P.kL;
-    const cplx Pf = mkc(kT2 * H.h0T.x - kL2 * H.h0L.x, kT2 * H.h0T.y - kL2 * H.h0L.y);
-    const cplx Qf = mkc(kT2 * H.eT.x - kL2 * H.eL.x, kT2 * H.eT.y - kL2 * H.eL.y);
-    // HF_ab = (i/4) [ (Q - P) zh_a zh_b - Q delta_ab ] ... written out:
-    // -(i/4) P zz + (i/4) Q (2 zz - delta) = (i/4)[(2Q - P) zz - Q delta]
-    const cplx iq4 = mkc(-0.25 * Qf.y, 0.25 * Qf.x);                 // (i/4) Q
-    const cplx c2qp = mkc(2.0 * Qf.x - Pf.x, 2.0 * Qf.y - Pf.y);
-    const cplx i2qp4 = mkc(-0.25 * c2qp.y, 0.25 * c2qp.x);           // (i/4)(2Q - P)
-    cplx HF[2][2];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            HF[a][b] = cscale(i2qp4, zh[a] * zh[b]);
-            if (a == b) HF[a][b] = csub(HF[a][b], iq4);
-        }
-    cplx dgT[2], dgL[2], edgT[2], edgL[2];
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        dgT[a] = cscale(gTp, zh[a]);
-        dgL[a] = cscale(gLp, zh[a]);
-    }
-    // (eps v)_1 = v_2, (eps v)_2 = -v_1
-    edgT[0] = dgT[1]; edgT[1] = cneg(dgT[0]);
-    edgL[0] = dgL[1]; edgL[1] = cneg(dgL[0]);
-    // eps HF eps^T = [[HF22, -HF12], [-HF21, HF11]]
-    cplx EHE[2][2] = {{HF[1][1], cneg(HF[0][1])}, {cneg(HF[1][0]), HF[0][0]}};
-    // (eps HF)_{ji}: j=1 row [HF21, HF22], j=2 row [-HF11, -HF12]
-    cplx EH[2][2] = {{HF[1][0], HF[1][1]}, {cneg(HF[0][0]), cneg(HF[0][1])}};   // EH[j][i]
-    const double eps_[2][2] = {{0.0, 1.0}, {-1.0, 0.0}};
-    const double c = P.c2, mu2 = 2.0 * P.mu;
-    const cplx al = P.alpha;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            cplx D0 = cadd(cscale(dgL[i], nyv[j]), cscale(edgT[i], tyv[j]));
-            cplx D1 = cneg(cadd(cscale(gT, 2.0 * eps_[j][i]), cscale(EH[j][i], c)));
-            cplx N0 = cscale(cadd(cscale(gL, nxv[i] * nyv[j]), cscale(gT, txv[i] * tyv[j])), P.rw2);
-            cplx N1 = cscale(csub(cscale(dgT[j], txv[i]), cscale(edgL[j], nxv[i])), -mu2);
-            cplx N2 = cscale(csub(cscale(edgL[i], nyv[j]), cscale(dgT[i], tyv[j])), -mu2);
-            cplx N3 = cscale(cadd(cscale(gT, i == j ? 2.0 : 0.0), cscale(EHE[i][j], c)), mu2);
-            cplx Dsum = cadd(cscale(D0, b0), cscale(D1, b1));
-            cplx Nsum = cadd(cadd(cscale(N0, b0), cscale(N1, b1)), cadd(cscale(N2, b2), cscale(N3, b3)));
-            cplx v = cadd(Dsum, cmul(al, Nsum));
-            acc[i][j].x = fma(w, v.x, acc[i][j].x);
-            acc[i][j].y = fma(w, v.y, acc[i][j].y);
-        }
+    const cplx Pf = mkc(kT2 * T.h0.x - kL2 * L.h0.x, kT2 * T.h0.y - kL2 * L.h0.y);
+    const cplx Qf = mkc(kT2 * T.e.x - kL2 * L.e.x, kT2 * T.e.y - kL2 * L.e.y);
+    // a = (i/4)(2Q - P), b = (i/4) Q
+    R.a = mkc(-0.25 * (2.0 * Qf.y - Pf.y), 0.25 * (2.0 * Qf.x - Pf.x));
+    R.b = mkc(-0.25 * Qf.y, 0.25 * Qf.x);
+    return R;
 }
 
 // ---------------------------------------------------------------- elements
@@ -162,7 +158,7 @@ __device__ __forceinline__ Elem load_elem(const double *__restrict__ xy, int N, 
     return E;
 }
 
-enum PairKind { PK_SELF = 0, PK_ADJ_NEXT = 1, PK_ADJ_PREV = 2, PK_NEAR = 3, PK_MID = 4, PK_FAR = 5, PK_CROSS = 6 };
+enum PairKind { PK_SELF = 0, PK_ADJ_NEXT = 1, PK_ADJ_PREV = 2, PK_NEAR = 3, PK_MID = 4, PK_FAR = 5, PK_FAR2 = 6, PK_CROSS = 7 };
 
 __device__ __forceinline__ int pair_kind(const Elem &E, const Elem &F, int ie, int jf, int N) {
     if (ie == jf) return PK_SELF;
@@ -174,10 +170,13 @@ __device__ __forceinline__ int pair_kind(const Elem &E, const Elem &F, int ie, i
     double my = E.a.y + 0.5 * E.h * E.t.y - (F.a.y + 0.5 * F.h * F.t.y);
     double d = sqrt(mx * mx + my * my);
     double L = fmax(E.h, F.h);
+    if (d >= 12.0 * L) return PK_FAR2;
     if (d >= 6.0 * L) return PK_FAR;
     if (d >= 2.5 * L) return PK_MID;
     return PK_NEAR;
 }
+
+__device__ __forceinline__ bool cheap_kind(int kind) { return kind >= PK_MID; }
 
 __device__ __forceinline__ int pair_points(int kind, int qcross) {
     switch (kind) {
@@ -187,26 +186,26 @@ __device__ __forceinline__ int pair_points(int kind, int qcross) {
         case PK_NEAR: return 4 * 64;
         case PK_MID: return 64;
         case PK_FAR: return 36;
+        case PK_FAR2: return 16;
         default: return qcross * qcross;
     }
 }
 
 // One quadrature point of the element-pair rule: local coordinates
 // (sig on E, tau on F), relative vector z = y - x and weight (incl. h_e h_f).
-// For PK_SELF the point p also has a mirror (sig, tau) <-> (tau, sig), z -> -z
-// which the caller evaluates with the same weight.
-__device__ __forceinline__ void pair_point(int kind, int p, int qcross, const Elem &E, const Elem &F,
+// For PK_SELF the point also has the mirror (sig, tau) <-> (tau, sig), z -> -z.
+__device__ __forceinline__ void pair_point(const Rules &G, int kind, int p, const Elem &E, const Elem &F,
                                            double &sig, double &tau, double2 &z, double &w) {
     const double hh = E.h * F.h;
     switch (kind) {
         case PK_SELF: {
-            int a = p >> 2, b = p & 3;
-            double wv = c_gauss.x[20][a];
-            double w2 = wv * wv, w4 = w2 * w2;
-            double u = w4 * wv;
-            double du = c_gauss.w[20][a] * 5.0 * w4;
-            double v = (1.0 - u) * c_gauss.x[4][b];
-            w = du * (1.0 - u) * c_gauss.w[4][b] * hh;
+            const int a = p >> 2, b = p & 3;
+            const double wv = G.x20[a];
+            const double w2 = wv * wv, w4 = w2 * w2;
+            const double u = w4 * wv;
+            const double du = G.w20[a] * 5.0 * w4;
+            const double v = (1.0 - u) * G.x4[b];
+            w = du * (1.0 - u) * G.w4[b] * hh;
             sig = v;
             tau = v + u;
             z = make_double2(u * E.h * E.t.x, u * E.h * E.t.y);
@@ -214,16 +213,16 @@ __device__ __forceinline__ void pair_point(int kind, int p, int qcross, const El
         }
         case PK_ADJ_NEXT:
         case PK_ADJ_PREV: {
-            int tri = p >> 7, rem = p & 127;
-            int a = rem >> 3, b = rem & 7;
-            double wx = c_gauss.x[16][a];
-            double wx2 = wx * wx;
-            double xi = wx2 * wx2;
-            double dxi = c_gauss.w[16][a] * 4.0 * wx2 * wx;
-            double eta = c_gauss.x[8][b];
-            double al = tri == 0 ? xi : xi * eta;
-            double be = tri == 0 ? xi * eta : xi;
-            w = dxi * c_gauss.w[8][b] * xi * hh;
+            const int tri = p >> 7, rem = p & 127;
+            const int a = rem >> 3, b = rem & 7;
+            const double wx = G.x16[a];
+            const double wx2 = wx * wx;
+            const double xi = wx2 * wx2;
+            const double dxi = G.w16[a] * 4.0 * wx2 * wx;
+            const double eta = G.x8[b];
+            const double al = tri == 0 ? xi : xi * eta;
+            const double be = tri == 0 ? xi * eta : xi;
+            w = dxi * G.w8[b] * xi * hh;
             if (kind == PK_ADJ_NEXT) {
                 sig = 1.0 - al;
                 tau = be;
@@ -236,92 +235,416 @@ __device__ __forceinline__ void pair_point(int kind, int p, int qcross, const El
             return;
         }
         case PK_NEAR: {
-            int sub = p >> 6, rem = p & 63;
-            int a = rem >> 3, b = rem & 7;
-            double s0 = 0.5 * (sub >> 1), t0 = 0.5 * (sub & 1);
-            sig = s0 + 0.5 * c_gauss.x[8][a];
-            tau = t0 + 0.5 * c_gauss.x[8][b];
-            w = 0.25 * c_gauss.w[8][a] * c_gauss.w[8][b] * hh;
+            const int sub = p >> 6, rem = p & 63;
+            const int a = rem >> 3, b = rem & 7;
+            sig = 0.5 * (sub >> 1) + 0.5 * G.x8[a];
+            tau = 0.5 * (sub & 1) + 0.5 * G.x8[b];
+            w = 0.25 * G.w8[a] * G.w8[b] * hh;
             break;
         }
         case PK_MID: {
-            int a = p >> 3, b = p & 7;
-            sig = c_gauss.x[8][a];
-            tau = c_gauss.x[8][b];
-            w = c_gauss.w[8][a] * c_gauss.w[8][b] * hh;
+            const int a = p >> 3, b = p & 7;
+            sig = G.x8[a];
+            tau = G.x8[b];
+            w = G.w8[a] * G.w8[b] * hh;
             break;
         }
         case PK_FAR: {
-            int a = p / 6, b = p - 6 * (p / 6);
-            sig = c_gauss.x[6][a];
-            tau = c_gauss.x[6][b];
-            w = c_gauss.w[6][a] * c_gauss.w[6][b] * hh;
+            const int a = p / 6, b = p - 6 * (p / 6);
+            sig = G.x6[a];
+            tau = G.x6[b];
+            w = G.w6[a] * G.w6[b] * hh;
+            break;
+        }
+        case PK_FAR2: {
+            const int a = p >> 2, b = p & 3;
+            sig = G.x4[a];
+            tau = G.x4[b];
+            w = G.w4[a] * G.w4[b] * hh;
             break;
         }
         default: {
-            int a = p / qcross, b = p - qcross * (p / qcross);
-            sig = c_gauss.x[qcross][a];
-            tau = c_gauss.x[qcross][b];
-            w = c_gauss.w[qcross][a] * c_gauss.w[qcross][b] * hh;
+            const int q = G.q;
+            const int a = p / q, b = p - q * (p / q);
+            sig = G.xq[a];
+            tau = G.xq[b];
+            w = G.wq[a] * G.wq[b] * hh;
             break;
         }
     }
-    double xx = E.a.x + sig * E.h * E.t.x, xy_ = E.a.y + sig * E.h * E.t.y;
-    double yx = F.a.x + tau * F.h * F.t.x, yy = F.a.y + tau * F.h * F.t.y;
+    const double xx = E.a.x + sig * E.h * E.t.x, xy_ = E.a.y + sig * E.h * E.t.y;
+    const double yx = F.a.x + tau * F.h * F.t.x, yy = F.a.y + tau * F.h * F.t.y;
     z = make_double2(yx - xx, yy - xy_);
 }
 
-// Basis factors for test local index A on E (coordinate sig) and trial local
-// index B on F (coordinate tau): b0 = N_A N_B, b1 = N_A N_B', b2 = N_A' N_B,
-// b3 = N_A' N_B', with N_0 = 1 - s, N_1 = s, N_0' = -1/h, N_1' = 1/h.
-__device__ __forceinline__ void basis4(int A, int B, double sig, double tau, double he, double hf,
-                                       double &b0, double &b1, double &b2, double &b3) {
-    double na = A ? sig : 1.0 - sig, nb = B ? tau : 1.0 - tau;
-    double da = (A ? 1.0 : -1.0) / he, db = (B ? 1.0 : -1.0) / hf;
-    b0 = na * nb; b1 = na * db; b2 = da * nb; b3 = da * db;
+// ---------------------------------------------------------------- accumulation
+// Element-pair accumulator, flat so that every index is a compile-time
+// constant (keeps it in registers): v[fidx(A,B,i,j)] is the integral for the
+// test hat with local index A on E against the trial hat with local index B on
+// F (component block i, j); v[ridx(B,A,i,j)] the transposed entry (test hat B
+// on F, trial hat A on E) from the same points.
+struct PairAcc {
+    double v[32];
+};
+#define FIDX(A, B, i, j) (((((A)*2 + (B)) * 4) + (i)*2 + (j)) * 2)
+#define RIDX(B, A, i, j) (32 + ((((B)*2 + (A)) * 4) + (i)*2 + (j)) * 2)
+
+__device__ __forceinline__ void acc_zero(PairAcc &S) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) S.v[k] = 0.0;
 }
 
-// Accumulate, in this lane, the part of element pair (E,F) assigned to it
-// (points lane, lane+32, ...).  fwd: A(test hat on E with local index A,
-// trial hat on F with local index B).  If rev != nullptr also the reversed
-// entry A(test hat on F / B, trial hat on E / A) from the same point pairs.
-__device__ __forceinline__ void pair_accum_lane(const PhysDev &P, int kind, int qcross, const Elem &E,
-                                                const Elem &F, int A, int B, int lane, cplx fwd[2][2],
-                                                cplx (*rev)[2]) {
-    const int np = pair_points(kind, qcross);
-    for (int p = lane; p < np; p += 32) {
+// Kernel entry (i, j) of the blocks K0 (psi phi), K1 (psi phi'), K2 (psi' phi)
+// of D + alpha N for unit direction zh = (zx, zy) (z = y - x), test normal
+// nx, trial normal ny; see the header comment for the formulas.
+__device__ __forceinline__ void k012_entry(const PhysDev &P, const Radial &R, const cplx &AgL, const cplx &AgT,
+                                           const cplx &MgTp, const cplx &MgLp, double zx, double zy, double2 nx,
+                                           double2 ny, int i, int j, cplx &k0, cplx &k1, cplx &k2) {
+    const double zhi = i ? zy : zx, zhj = j ? zy : zx;
+    const double zpi = i ? -zx : zy, zpj = j ? -zx : zy;        // eps zh
+    const double nxi = i ? nx.y : nx.x, nyj = j ? ny.y : ny.x;
+    const double txi = i ? -nx.x : nx.y, tyj = j ? -ny.x : ny.y;
+    // K0 = n^y_j g_L' zh_i + t^y_j g_T' zp_i + alpha rw2 (nx_i ny_j gL + tx_i ty_j gT)
+    k0 = cadd(cadd(cscale(R.gLp, nyj * zhi), cscale(R.gTp, tyj * zpi)),
+              cadd(cscale(AgL, nxi * nyj), cscale(AgT, txi * tyj)));
+    // K1 = -(2 eps_ji g_T + c (a zp_j zh_i - b eps_ji)) - 2 mu alpha (t^x_i g_T' zh_j - n^x_i g_L' zp_j)
+    const double eji = (j == 0 && i == 1) ? 1.0 : ((j == 1 && i == 0) ? -1.0 : 0.0);
+    cplx v = cscale(R.a, P.c2 * zpj * zhi);
+    v = csub(v, cscale(R.b, P.c2 * eji));
+    v = cadd(v, cscale(R.gT, 2.0 * eji));
+    k1 = csub(csub(cscale(MgTp, txi * zhj), cscale(MgLp, nxi * zpj)), v);
+    // K2 = -2 mu alpha (n^y_j g_L' zp_i - t^y_j g_T' zh_i)
+    k2 = csub(cscale(MgLp, nyj * zpi), cscale(MgTp, tyj * zhi));
+}
+
+// Add one point (local coords sig, tau; relative z; weight w) to the forward
+// (dir 0) or the transposed (dir 1) entries.  maskA/maskB: local basis
+// indices used on E / F.
+__device__ __forceinline__ void acc_point(const PhysDev &P, const Elem &E, const Elem &F, double sig, double tau,
+                                          double2 z, double w, int dir, int maskA, int maskB, PairAcc &S) {
+    const double r = sqrt(z.x * z.x + z.y * z.y);
+    const double ir = dir ? -1.0 / r : 1.0 / r;     // transposed entry: z -> -z
+    const double zx = z.x * ir, zy = z.y * ir;
+    const Radial R = radial(P, r);
+    const cplx AgL = cmul(P.alpha, cscale(R.gL, P.rw2));
+    const cplx AgT = cmul(P.alpha, cscale(R.gT, P.rw2));
+    const cplx MgTp = cmul(P.alpha, cscale(R.gTp, -2.0 * P.mu));
+    const cplx MgLp = cmul(P.alpha, cscale(R.gLp, -2.0 * P.mu));
+    const cplx A2 = cscale(P.alpha, 2.0 * P.mu);
+    const cplx k3d = csub(cscale(R.gT, 2.0), cscale(R.b, P.c2));
+    // test side (normal, basis on it) and trial side
+    const double2 nx = dir ? F.n : E.n, ny = dir ? E.n : F.n;
+    const double ht = dir ? F.h : E.h, hs = dir ? E.h : F.h;
+    const double ct = dir ? tau : sig, cs = dir ? sig : tau;
+    const double nt[2] = {w * (1.0 - ct), w * ct}, dt[2] = {-w / ht, w / ht};
+    const double ns[2] = {1.0 - cs, cs}, ds[2] = {-1.0 / hs, 1.0 / hs};
+    const int mt = dir ? maskB : maskA, ms = dir ? maskA : maskB;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            cplx k0, k1, k2;
+            k012_entry(P, R, AgL, AgT, MgTp, MgLp, zx, zy, nx, ny, i, j, k0, k1, k2);
+            // K3 = 2 mu alpha (2 delta_ij g_T + c (a zp_i zp_j - b delta_ij))
+            const double zpi = i ? -zx : zy, zpj = j ? -zx : zy;
+            cplx k3 = cscale(R.a, P.c2 * zpi * zpj);
+            if (i == j) k3 = cadd(k3, k3d);
+            k3 = cmul(A2, k3);
+#pragma unroll
+            for (int T = 0; T < 2; ++T) {
+                if (!(mt & (1 << T))) continue;
+#pragma unroll
+                for (int U = 0; U < 2; ++U) {
+                    if (!(ms & (1 << U))) continue;
+                    const double b0 = nt[T] * ns[U], b1 = nt[T] * ds[U];
+                    const double b2 = dt[T] * ns[U], b3 = dt[T] * ds[U];
+                    // forward: v[FIDX(A = T, B = U)]; transposed: v[RIDX(B = T, A = U)]
+                    const int q = dir ? RIDX(T, U, i, j) - 32 : FIDX(T, U, i, j);
+                    S.v[q] += b0 * k0.x + b1 * k1.x + b2 * k2.x + b3 * k3.x;
+                    S.v[q + 1] += b0 * k0.y + b1 * k1.y + b2 * k2.y + b3 * k3.y;
+                }
+            }
+        }
+}
+
+// Both orientations from one evaluation of the radial functions: v[0..31] =
+// forward entries (index FIDX), v[32..63] = transposed entries (RIDX).
+struct PairAcc2 {
+    double v[64];
+};
+
+__device__ __forceinline__ void acc_point2(const PhysDev &P, const Elem &E, const Elem &F, double sig, double tau,
+                                           double2 z, double w, int maskA, int maskB, PairAcc2 &S) {
+    const double r = sqrt(z.x * z.x + z.y * z.y);
+    const double ir = 1.0 / r;
+    const double zx = z.x * ir, zy = z.y * ir;
+    const Radial R = radial(P, r);
+    const cplx AgL = cmul(P.alpha, cscale(R.gL, P.rw2));
+    const cplx AgT = cmul(P.alpha, cscale(R.gT, P.rw2));
+    const cplx MgTp = cmul(P.alpha, cscale(R.gTp, -2.0 * P.mu));
+    const cplx MgLp = cmul(P.alpha, cscale(R.gLp, -2.0 * P.mu));
+    const cplx A2 = cscale(P.alpha, 2.0 * P.mu);
+    const cplx k3d = csub(cscale(R.gT, 2.0), cscale(R.b, P.c2));
+    const double na[2] = {w * (1.0 - sig), w * sig}, da[2] = {-w / E.h, w / E.h};
+    const double nb[2] = {1.0 - tau, tau}, db[2] = {-1.0 / F.h, 1.0 / F.h};
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const double zpi = i ? -zx : zy, zpj = j ? -zx : zy;
+            cplx k3 = cscale(R.a, P.c2 * zpi * zpj);
+            if (i == j) k3 = cadd(k3, k3d);
+            k3 = cmul(A2, k3);
+            {
+                cplx k0, k1, k2;
+                k012_entry(P, R, AgL, AgT, MgTp, MgLp, zx, zy, E.n, F.n, i, j, k0, k1, k2);
+#pragma unroll
+                for (int A = 0; A < 2; ++A) {
+                    if (!(maskA & (1 << A))) continue;
+#pragma unroll
+                    for (int B = 0; B < 2; ++B) {
+                        if (!(maskB & (1 << B))) continue;
+                        const double b0 = na[A] * nb[B], b1 = na[A] * db[B];
+                        const double b2 = da[A] * nb[B], b3 = da[A] * db[B];
+                        const int q = FIDX(A, B, i, j);
+                        S.v[q] += b0 * k0.x + b1 * k1.x + b2 * k2.x + b3 * k3.x;
+                        S.v[q + 1] += b0 * k0.y + b1 * k1.y + b2 * k2.y + b3 * k3.y;
+                    }
+                }
+            }
+            {
+                // transposed: test point on F (normal F.n), trial on E, z -> -z
+                cplx k0, k1, k2;
+                k012_entry(P, R, AgL, AgT, MgTp, MgLp, -zx, -zy, F.n, E.n, i, j, k0, k1, k2);
+#pragma unroll
+                for (int A = 0; A < 2; ++A) {
+                    if (!(maskA & (1 << A))) continue;
+#pragma unroll
+                    for (int B = 0; B < 2; ++B) {
+                        if (!(maskB & (1 << B))) continue;
+                        // test hat B on F, trial hat A on E
+                        const double b0 = na[A] * nb[B], b1 = nb[B] * da[A];
+                        const double b2 = db[B] * na[A], b3 = db[B] * da[A];
+                        const int q = RIDX(B, A, i, j);
+                        S.v[q] += b0 * k0.x + b1 * k1.x + b2 * k2.x + b3 * k3.x;
+                        S.v[q + 1] += b0 * k0.y + b1 * k1.y + b2 * k2.y + b3 * k3.y;
+                    }
+                }
+            }
+        }
+}
+
+__device__ __forceinline__ void acc_pair2(const PhysDev &P, const Rules &G, int kind, const Elem &E, const Elem &F,
+                                          int p0, int stride, int maskA, int maskB, PairAcc2 &S) {
+    const int np = pair_points(kind, G.q);
+    for (int p = p0; p < np; p += stride) {
         double sig, tau, w;
         double2 z;
-        pair_point(kind, p, qcross, E, F, sig, tau, z, w);
-        double r = sqrt(z.x * z.x + z.y * z.y);
-        Hank H = hankels(P, r);
-        double b0, b1, b2, b3;
-        basis4(A, B, sig, tau, E.h, F.h, b0, b1, b2, b3);
-        kernel_accum(P, H, z, r, E.n, F.n, w, b0, b1, b2, b3, fwd);
-        if (rev) kernel_accum(P, H, make_double2(-z.x, -z.y), r, F.n, E.n, w, b0, b2, b1, b3, rev);
-        if (kind == PK_SELF) {
-            // mirror point: (sig, tau) <-> (tau, sig), z -> -z
-            basis4(A, B, tau, sig, E.h, F.h, b0, b1, b2, b3);
-            kernel_accum(P, H, make_double2(-z.x, -z.y), r, E.n, F.n, w, b0, b1, b2, b3, fwd);
-            if (rev) kernel_accum(P, H, z, r, F.n, E.n, w, b0, b2, b1, b3, rev);
+        pair_point(G, kind, p, E, F, sig, tau, z, w);
+        acc_point2(P, E, F, sig, tau, z, w, maskA, maskB, S);
+        if (kind == PK_SELF) acc_point2(P, E, F, tau, sig, make_double2(-z.x, -z.y), w, maskA, maskB, S);
+    }
+}
+
+// All points p = p0, p0 + stride, ... of element pair (E, F) under rule
+// `kind`, for the forward (dir 0) or transposed (dir 1) entries.
+__device__ __forceinline__ void acc_pair(const PhysDev &P, const Rules &G, int kind, const Elem &E, const Elem &F,
+                                         int p0, int stride, int dir, int maskA, int maskB, PairAcc &S) {
+    const int np = pair_points(kind, G.q);
+    for (int p = p0; p < np; p += stride) {
+        double sig, tau, w;
+        double2 z;
+        pair_point(G, kind, p, E, F, sig, tau, z, w);
+        acc_point(P, E, F, sig, tau, z, w, dir, maskA, maskB, S);
+        if (kind == PK_SELF) acc_point(P, E, F, tau, sig, make_double2(-z.x, -z.y), w, dir, maskA, maskB, S);
+    }
+}
+
+// ---------------------------------------------------------------- tiles
+// A tile side: up to TILE hats on one closed polygon; its deduplicated
+// elements with, for each, the tile positions of the hat that uses it as local
+// node 0 (hat = element index) and as local node 1 (hat = element index + 1).
+struct TileSide {
+    int nh;
+    int hats[TILE];
+    int alias[TILE];    // first position holding the same hat (lists may repeat a hat)
+    int ne;
+    int el[TILE_EL];
+    int pos[TILE_EL][2];
+};
+
+// Build the element list of a tile side (single thread).
+__device__ __forceinline__ void tile_side_build(TileSide &T, int N) {
+    T.ne = 0;
+    for (int k = 0; k < T.nh; ++k) {
+        const int s = T.hats[k];
+        T.alias[k] = k;
+        for (int q = 0; q < k; ++q)
+            if (T.hats[q] == s) { T.alias[k] = q; break; }
+        if (T.alias[k] != k) continue;
+        const int e1 = (s == 0) ? N - 1 : s - 1;   // local node 1 of element s-1
+        const int e0 = s;                          // local node 0 of element s
+        for (int which = 0; which < 2; ++which) {
+            const int e = which ? e1 : e0, A = which ? 1 : 0;
+            int slot = -1;
+            for (int q = 0; q < T.ne; ++q)
+                if (T.el[q] == e) { slot = q; break; }
+            if (slot < 0) {
+                slot = T.ne++;
+                T.el[slot] = e;
+                T.pos[slot][0] = -1;
+                T.pos[slot][1] = -1;
+            }
+            T.pos[slot][A] = k;
         }
     }
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+// Shared-memory state of one tile evaluation.
+struct TileSmem {
+    Rules G;
+    TileSide R, C;
+    double ef[TILE][TILE][2][2][2];   // forward entries  [row][col][i][j][re/im]
+    double er[TILE][TILE][2][2][2];   // transposed entries [col][row][i][j][re/im]
+};
+
+__device__ __forceinline__ void tile_zero(TileSmem &S) {
+    double *a = &S.ef[0][0][0][0][0], *b = &S.er[0][0][0][0][0];
+    for (int k = threadIdx.x; k < TILE * TILE * 8; k += blockDim.x) { a[k] = 0.0; b[k] = 0.0; }
+}
+
+// Scatter one element pair's accumulator (forward, dir 0, or transposed,
+// dir 1) into the tile entries: value k is added by lane k % nlanes
+// (nlanes = 1 or 32).
+__device__ __forceinline__ void tile_scatter(TileSmem &S, int re, int ce, const PairAcc &A, int dir, int lane,
+                                             int nlanes) {
+    const int pr0 = S.R.pos[re][0], pr1 = S.R.pos[re][1];
+    const int pc0 = S.C.pos[ce][0], pc1 = S.C.pos[ce][1];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        if (nlanes != 1 && k != lane) continue;
+        const int x = k >> 4, y = (k >> 3) & 1, i = (k >> 2) & 1, j = (k >> 1) & 1, ri = k & 1;
+        if (dir == 0) {
+            // test hat local x on the row element, trial local y on the column element
+            const int pr = x ? pr1 : pr0, pc = y ? pc1 : pc0;
+            if (pr < 0 || pc < 0) continue;
+            atomicAdd(&S.ef[pr][pc][i][j][ri], A.v[k]);
+        } else {
+            // test hat local x on the column element, trial local y on the row element
+            const int pc = x ? pc1 : pc0, pr = y ? pr1 : pr0;
+            if (pr < 0 || pc < 0) continue;
+            atomicAdd(&S.er[pc][pr][i][j][ri], A.v[k]);
+        }
+    }
+}
+
+__device__ __forceinline__ void tile_scatter2(TileSmem &S, int re, int ce, const PairAcc2 &A, int lane,
+                                              int nlanes) {
+    const int pr0 = S.R.pos[re][0], pr1 = S.R.pos[re][1];
+    const int pc0 = S.C.pos[ce][0], pc1 = S.C.pos[ce][1];
+#pragma unroll
+    for (int k = 0; k < 64; ++k) {
+        if (nlanes != 1 && (k & 31) != lane) continue;
+        const int rem = k & 31;
+        const int x = rem >> 4, y = (rem >> 3) & 1, i = (rem >> 2) & 1, j = (rem >> 1) & 1, ri = rem & 1;
+        if (k < 32) {
+            const int pr = x ? pr1 : pr0, pc = y ? pc1 : pc0;
+            if (pr < 0 || pc < 0) continue;
+            atomicAdd(&S.ef[pr][pc][i][j][ri], A.v[k]);
+        } else {
+            const int pc = x ? pc1 : pc0, pr = y ? pr1 : pr0;
+            if (pr < 0 || pc < 0) continue;
+            atomicAdd(&S.er[pc][pr][i][j][ri], A.v[k]);
+        }
+    }
+}
+
+__device__ __forceinline__ double wsum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-__device__ __forceinline__ void warp_reduce_block(cplx a[2][2]) {
+// Evaluate all element pairs of a tile into S.ef / S.er.
+//   same  : both sides on the same polygon X (singular-aware rule set);
+//           otherwise rows on X, columns on Y with the cross rule S.G.q.
+//   dual  : also accumulate the transposed entries.
+//   diag  : rows and columns are the same hat list; only element pairs with
+//           row element index <= column element index are evaluated, the
+//           transposed contributions of pairs re < ce are folded in, and self
+//           pairs are taken once.
+// Cheap rules run one element pair per thread, costly ones one per warp.
+static __device__ void tile_eval(const PhysDev &P, TileSmem &S, const double *__restrict__ X, int NX,
+                          const double *__restrict__ Y, int NY, bool same, bool dual, bool diag) {
+    const int npairs = S.R.ne * S.C.ne;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // pass 1: cheap pairs, one per thread
+    for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
+        const int re = q / S.C.ne, ce = q - re * S.C.ne;
+        const int ie = S.R.el[re], jf = S.C.el[ce];
+        if (diag && ie > jf) continue;
+        const Elem E = load_elem(X, NX, ie);
+        const Elem F = load_elem(same ? X : Y, same ? NX : NY, jf);
+        const int kind = same ? pair_kind(E, F, ie, jf, NX) : PK_CROSS;
+        if (!cheap_kind(kind)) continue;
+        const int mA = (S.R.pos[re][0] >= 0 ? 1 : 0) | (S.R.pos[re][1] >= 0 ? 2 : 0);
+        const int mB = (S.C.pos[ce][0] >= 0 ? 1 : 0) | (S.C.pos[ce][1] >= 0 ? 2 : 0);
+        if (dual || diag) {
+            PairAcc2 A;
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            a[i][j].x = warp_sum(a[i][j].x);
-            a[i][j].y = warp_sum(a[i][j].y);
+            for (int k = 0; k < 64; ++k) A.v[k] = 0.0;
+            acc_pair2(P, S.G, kind, E, F, 0, 1, mA, mB, A);
+            tile_scatter2(S, re, ce, A, 0, 1);
+            if (d_count_points) atomicAdd(&d_quad_points, 2ull * pair_points(kind, S.G.q) * (kind == PK_SELF ? 2 : 1));
+        } else {
+            PairAcc A;
+            acc_zero(A);
+            acc_pair(P, S.G, kind, E, F, 0, 1, 0, mA, mB, A);
+            tile_scatter(S, re, ce, A, 0, 0, 1);
+            if (d_count_points) atomicAdd(&d_quad_points, 1ull * pair_points(kind, S.G.q) * (kind == PK_SELF ? 2 : 1));
         }
+    }
+    // pass 2: singular / near-singular pairs, one per warp
+    for (int q = warp; q < npairs; q += nw) {
+        const int re = q / S.C.ne, ce = q - re * S.C.ne;
+        const int ie = S.R.el[re], jf = S.C.el[ce];
+        if (diag && ie > jf) continue;
+        const Elem E = load_elem(X, NX, ie);
+        const Elem F = load_elem(same ? X : Y, same ? NX : NY, jf);
+        const int kind = same ? pair_kind(E, F, ie, jf, NX) : PK_CROSS;
+        if (cheap_kind(kind)) continue;
+        const int mA = (S.R.pos[re][0] >= 0 ? 1 : 0) | (S.R.pos[re][1] >= 0 ? 2 : 0);
+        const int mB = (S.C.pos[ce][0] >= 0 ? 1 : 0) | (S.C.pos[ce][1] >= 0 ? 2 : 0);
+        // a self pair in a diagonal tile: its transposed entries are forward entries too
+        const bool d = diag ? (ie != jf) : dual;
+        if (d) {
+            PairAcc2 A;
+#pragma unroll
+            for (int k = 0; k < 64; ++k) A.v[k] = 0.0;
+            acc_pair2(P, S.G, kind, E, F, lane, 32, mA, mB, A);
+#pragma unroll
+            for (int k = 0; k < 64; ++k) A.v[k] = wsum(A.v[k]);
+            tile_scatter2(S, re, ce, A, lane, 32);
+            if (d_count_points && lane == 0)
+                atomicAdd(&d_quad_points, 2ull * pair_points(kind, S.G.q) * (kind == PK_SELF ? 2 : 1));
+        } else {
+            PairAcc A;
+            acc_zero(A);
+            acc_pair(P, S.G, kind, E, F, lane, 32, 0, mA, mB, A);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) A.v[k] = wsum(A.v[k]);
+            tile_scatter(S, re, ce, A, 0, lane, 32);
+            if (d_count_points && lane == 0)
+                atomicAdd(&d_quad_points, 1ull * pair_points(kind, S.G.q) * (kind == PK_SELF ? 2 : 1));
+        }
+    }
+}
+
+// Fold the transposed entries of a diagonal tile into the forward ones.
+__device__ __forceinline__ void tile_fold(TileSmem &S) {
+    double *a = &S.ef[0][0][0][0][0];
+    const double *b = &S.er[0][0][0][0][0];
+    for (int k = threadIdx.x; k < TILE * TILE * 8; k += blockDim.x) a[k] += b[k];
 }
 
 // Exact P1 mass entry int phi^s phi^t over the polygon.
@@ -329,7 +652,6 @@ __device__ __forceinline__ double mass_entry(const double *__restrict__ xy, int 
     int sp = (s == 0) ? N - 1 : s - 1;
     int tp = (t == 0) ? N - 1 : t - 1;
     double m = 0.0;
-    // hat s: elements sp (local 1), s (local 0); hat t likewise
     int es[2] = {sp, s}, ls[2] = {1, 0};
     int et[2] = {tp, t}, lt[2] = {1, 0};
 #pragma unroll
@@ -345,72 +667,17 @@ __device__ __forceinline__ double mass_entry(const double *__restrict__ xy, int 
     return m;
 }
 
-// Warp-cooperative Galerkin entry of the boundary matrix between test hat s
-// and trial hat t (same polygon), including I_0/2.  If rev != nullptr the
-// entry (t, s) is produced too from the same quadrature points.  Result is
-// valid in every lane.
-__device__ __forceinline__ void hat_pair_same(const PhysDev &P, const double *__restrict__ xy, int N, int s,
-                                              int t, int lane, cplx out[2][2], cplx (*rev)[2]) {
-    cplx f[2][2], r[2][2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) { f[i][j] = mkc(0, 0); r[i][j] = mkc(0, 0); }
-    const int sp = (s == 0) ? N - 1 : s - 1;
-    const int tp = (t == 0) ? N - 1 : t - 1;
-    for (int a = 0; a < 2; ++a) {
-        const int ie = a == 0 ? sp : s, A = a == 0 ? 1 : 0;
-        const Elem E = load_elem(xy, N, ie);
-        for (int b = 0; b < 2; ++b) {
-            const int jf = b == 0 ? tp : t, B = b == 0 ? 1 : 0;
-            const Elem F = load_elem(xy, N, jf);
-            const int kind = pair_kind(E, F, ie, jf, N);
-            pair_accum_lane(P, kind, 0, E, F, A, B, lane, f, rev ? r : nullptr);
-        }
-    }
-    warp_reduce_block(f);
-    if (rev) warp_reduce_block(r);
-    const double m = 0.5 * mass_entry(xy, N, s, t);
-    f[0][0].x += m; f[1][1].x += m;
-    r[0][0].x += m; r[1][1].x += m;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            out[i][j] = f[i][j];
-            if (rev) rev[i][j] = r[i][j];
-        }
+// Entry (row item r, column item c) of the forward / transposed tile;
+// repeated hats read the first occurrence.
+__device__ __forceinline__ cplx tile_f(const TileSmem &S, int r, int c, int i, int j) {
+    r = S.R.alias[r];
+    c = S.C.alias[c];
+    return mkc(S.ef[r][c][i][j][0], S.ef[r][c][i][j][1]);
 }
-
-// Warp-cooperative entry between test hat s on polygon X and trial hat t on
-// polygon Y (fixed q x q rule, no mass).  With rev: also the entry of test
-// hat t on Y against trial hat s on X.
-__device__ __forceinline__ void hat_pair_cross(const PhysDev &P, const double *__restrict__ X, int NX, int s,
-                                               const double *__restrict__ Y, int NY, int t, int q, int lane,
-                                               cplx out[2][2], cplx (*rev)[2]) {
-    cplx f[2][2], r[2][2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) { f[i][j] = mkc(0, 0); r[i][j] = mkc(0, 0); }
-    const int sp = (s == 0) ? NX - 1 : s - 1;
-    const int tp = (t == 0) ? NY - 1 : t - 1;
-    for (int a = 0; a < 2; ++a) {
-        const Elem E = load_elem(X, NX, a == 0 ? sp : s);
-        for (int b = 0; b < 2; ++b) {
-            const Elem F = load_elem(Y, NY, b == 0 ? tp : t);
-            pair_accum_lane(P, PK_CROSS, q, E, F, a == 0 ? 1 : 0, b == 0 ? 1 : 0, lane, f, rev ? r : nullptr);
-        }
-    }
-    warp_reduce_block(f);
-    if (rev) warp_reduce_block(r);
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            out[i][j] = f[i][j];
-            if (rev) rev[i][j] = r[i][j];
-        }
+__device__ __forceinline__ cplx tile_r(const TileSmem &S, int c, int r, int i, int j) {
+    r = S.R.alias[r];
+    c = S.C.alias[c];
+    return mkc(S.er[c][r][i][j][0], S.er[c][r][i][j][1]);
 }
 
 }  // namespace fdsk

@@ -14,11 +14,11 @@ namespace {
 struct Rec {
     std::string name;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    double flops = 0, bytes = 0;
+    double flops = 0, bytes = 0, units = 0;
 };
 struct Acc {
     long launches = 0;
-    double ms = 0, flops = 0, bytes = 0;
+    double ms = 0, flops = 0, bytes = 0, units = 0;
 };
 std::mutex g_mu;
 bool g_on = false;
@@ -36,6 +36,7 @@ void resolve_locked() {
                 a.ms += ms;
                 a.flops += r.flops;
                 a.bytes += r.bytes;
+                a.units += r.units;
             }
             cudaEventDestroy(r.e1);
         }
@@ -60,7 +61,7 @@ void prof_begin(const char *name, cudaStream_t s) {
     g_open.push_back(r);
 }
 
-void prof_end(cudaStream_t s, double flops, double bytes) {
+void prof_end(cudaStream_t s, double flops, double bytes, double units) {
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto it = g_open.rbegin(); it != g_open.rend(); ++it)
         if (!it->e1) {
@@ -68,6 +69,7 @@ void prof_end(cudaStream_t s, double flops, double bytes) {
             cudaEventRecord(it->e1, s);
             it->flops = flops;
             it->bytes = bytes;
+            it->units = units;
             break;
         }
     if (g_open.size() > 4096) resolve_locked();
@@ -90,8 +92,8 @@ extern "C" int fds_timing_report(char *buf, int32_t cap) {
     std::string out;
     char line[256];
     for (auto &kv : g_acc) {
-        snprintf(line, sizeof(line), "%s %ld %.6f %.6e %.6e\n", kv.first.c_str(), kv.second.launches, kv.second.ms,
-                 kv.second.flops, kv.second.bytes);
+        snprintf(line, sizeof(line), "%s %ld %.6f %.6e %.6e %.6e\n", kv.first.c_str(), kv.second.launches,
+                 kv.second.ms, kv.second.flops, kv.second.bytes, kv.second.units);
         out += line;
     }
     if (buf && cap > 0) {

@@ -9,16 +9,16 @@
 
 bool prof_enabled();
 void prof_begin(const char *name, cudaStream_t s);
-void prof_end(cudaStream_t s, double flops, double bytes);
+void prof_end(cudaStream_t s, double flops, double bytes, double units);
 
 struct ProfScope {
     cudaStream_t s;
-    double flops = 0, bytes = 0;
+    double flops = 0, bytes = 0, units = 0;
     bool on;
     ProfScope(const char *name, cudaStream_t st) : s(st), on(prof_enabled()) {
         if (on) prof_begin(name, s);
     }
     ~ProfScope() {
-        if (on) prof_end(s, flops, bytes);
+        if (on) prof_end(s, flops, bytes, units);
     }
 };

@@ -257,8 +257,9 @@ def fds_timing_report():
     lib().fds_timing_report(buf, n + 16)
     out = {}
     for line in buf.value.decode().splitlines():
-        name, launches, ms, flops, nbytes = line.split()
-        out[name] = dict(launches=int(launches), ms=float(ms), flops=float(flops), bytes=float(nbytes))
+        name, launches, ms, flops, nbytes, units = line.split()
+        out[name] = dict(launches=int(launches), ms=float(ms), flops=float(flops), bytes=float(nbytes),
+                         units=float(units))
     return out
 
 

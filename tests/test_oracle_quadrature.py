@@ -105,7 +105,7 @@ def test_adjacent_pair(nxt):
     assert np.abs(got - ref).max() < 1e-11 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("gap", [2, 3, 5, 9])
+@pytest.mark.parametrize("gap", [2, 3, 5, 9, 16, 24])
 def test_near_mid_far_pairs(gap):
     P = bem.phys(LAM, MU, RHO, 3.0)
     xy = _poly(64)
