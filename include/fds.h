@@ -201,6 +201,28 @@ int fds_id_batched(int32_t batch, const int32_t *d_m, const int32_t *d_n, const 
 int fds_lu_batched(int32_t batch, const int32_t *d_d, const int64_t *d_off, double *d_A,
                    int32_t *d_piv, const int64_t *d_poff, int32_t *d_info, uint64_t stream);
 
+/*
+ * fds_lu_batched_noalloc: the batched LU above without any allocation, for
+ * callers that cannot allocate device memory at the point of the call — for
+ * example code running inside another allocator's callback, a process whose
+ * device memory is reserved up front by a caching allocator so that a fresh
+ * cudaMalloc may fail, or a latency-critical loop that must not pay for the
+ * implicit synchronisation of cudaMalloc/cudaFree.  The paper has no
+ * counterpart; this is a service of the library.
+ * Same arguments, layout and results as fds_lu_batched.  The per-matrix
+ * descriptors live in a static device array of FDS_LU_NOALLOC_MAX_BATCH
+ * (16384) entries (384 KiB, held by every GPU that loads the library until
+ * the process exits); batch > 16384 returns FDS_ERR_ARG.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the array, which keeps the last call's descriptors:
+ * calls that overlap on the GPU (different streams, or different host
+ * threads on the same device) race and must be serialised by the caller.
+ * No cudaMalloc, cudaFree or other allocating call is made.
+ */
+int fds_lu_batched_noalloc(int32_t batch, const int32_t *d_d, const int64_t *d_off, double *d_A,
+                           int32_t *d_piv, const int64_t *d_poff, int32_t *d_info, uint64_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,6 +1,7 @@
 // Batched complex128 LU / LU-solve / GEMM kernels (one CTA per matrix or
 // per output tile).  FP64 throughout.
 #include <cmath>
+#include <mutex>
 
 #include "dense.cuh"
 
@@ -246,4 +247,51 @@ extern "C" int fds_lu_batched(int32_t batch, const int32_t *d_d, const int64_t *
     cudaFreeAsync(refs, s);
     FDS_CUDA_TRY(cudaGetLastError());
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free batched LU.  The per-matrix descriptors that fds_lu_batched
+// builds in a cudaMallocAsync'd buffer live here in a file-scope device array
+// instead; every GPU that loads the library holds it (384 KiB) until exit.
+#define FDS_LU_NOALLOC_MAX_BATCH 16384
+static __device__ __align__(256) MatRef g_lu_noalloc_refs[FDS_LU_NOALLOC_MAX_BATCH];
+
+namespace {
+// Device address of g_lu_noalloc_refs for each device, looked up once per
+// device (with that device current) by cudaGetSymbolAddress: in host code the
+// array's name is only a host-side stand-in.
+MatRef *lu_noalloc_scratch(int *err) {
+    static std::mutex mu;
+    static MatRef *addr[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        *err = FDS_ERR_CUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_lu_noalloc_refs) != cudaSuccess || !p) {
+            *err = FDS_ERR_CUDA;
+            return nullptr;
+        }
+        addr[dev] = (MatRef *)p;
+    }
+    *err = FDS_OK;
+    return addr[dev];
+}
+}  // namespace
+
+extern "C" int fds_lu_batched_noalloc(int32_t batch, const int32_t *d_d, const int64_t *d_off, double *d_A,
+                                      int32_t *d_piv, const int64_t *d_poff, int32_t *d_info, uint64_t stream) {
+    if (batch < 0 || batch > FDS_LU_NOALLOC_MAX_BATCH) return FDS_ERR_ARG;
+    if (batch == 0) return FDS_OK;
+    if (!d_d || !d_off || !d_A || !d_piv || !d_poff || !d_info) return FDS_ERR_ARG;
+    int err = FDS_OK;
+    MatRef *refs = lu_noalloc_scratch(&err);
+    if (err != FDS_OK) return err;
+    cudaStream_t s = (cudaStream_t)stream;
+    fds_count_launch(), k_make_refs<<<(batch + 127) / 128, 128, 0, s>>>(batch, d_d, d_off, d_A, refs);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return dense_lu(batch, 0, refs, d_piv, d_poff, d_info, s);
 }

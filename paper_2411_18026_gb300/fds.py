@@ -87,6 +87,7 @@ def lib():
     L.fds_eval_cross.argtypes = [ctypes.POINTER(fds_physics), vp, i32, vp, i32, vp, i32, vp, i32, i32, vp, u64]
     L.fds_id_batched.argtypes = [i32, vp, vp, vp, vp, f64, vp, vp, vp, vp, vp, u64]
     L.fds_lu_batched.argtypes = [i32, vp, vp, vp, vp, vp, vp, u64]
+    L.fds_lu_batched_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, u64]
     L.fds_timing_enable.argtypes = [i32]
     L.fds_timing_enable.restype = None
     L.fds_timing_reset.argtypes = []
@@ -97,7 +98,7 @@ def lib():
     L.fds_launch_count.restype = ctypes.c_int64
     for f in ("fds_build", "fds_build_ex", "fds_rhs_plane_wave", "fds_rhs_plane_wave_device", "fds_solve",
               "fds_solve_device", "fds_stats_get", "fds_level_ranks", "fds_eval_entries", "fds_eval_cross",
-              "fds_id_batched", "fds_lu_batched"):
+              "fds_id_batched", "fds_lu_batched", "fds_lu_batched_noalloc"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -235,6 +236,12 @@ def fds_id_batched(d_m, d_n, d_off, d_Y, tol, d_rank, d_perm, d_poff, d_T, d_tof
     _check(lib().fds_id_batched(d_m.numel(), _ptr(d_m), _ptr(d_n), _ptr(d_off), _ptr(d_Y), float(tol),
                                 _ptr(d_rank), _ptr(d_perm), _ptr(d_poff), _ptr(d_T), _ptr(d_toff),
                                 _stream(stream)), "fds_id_batched")
+
+
+def fds_lu_batched_noalloc(d_d, d_off, d_A, d_piv, d_poff, d_info, stream=None):
+    """Allocation-free variant of fds_lu_batched (see include/fds.h)."""
+    _check(lib().fds_lu_batched_noalloc(d_d.numel(), _ptr(d_d), _ptr(d_off), _ptr(d_A), _ptr(d_piv), _ptr(d_poff),
+                                        _ptr(d_info), _stream(stream)), "fds_lu_batched_noalloc")
 
 
 def fds_lu_batched(d_d, d_off, d_A, d_piv, d_poff, d_info, stream=None):
