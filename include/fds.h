@@ -45,6 +45,8 @@ extern "C" {
 #define FDS_ERR_STATE         -7  /* handle not in a state that allows the call */
 
 #define FDS_FP64  0               /* all arithmetic in FP64 / complex128 */
+#define FDS_MIXED 1               /* FP64 build; complex64 sweep refined against the FP64
+                                     compressed forward operator */
 
 typedef struct fds_handle fds_handle;   /* opaque; owns all device memory of one factorisation */
 
@@ -69,10 +71,14 @@ typedef struct {
     int32_t proxy_points;  /* minimum proxy polygon vertices m'; default 64; the library
                               uses max(proxy_points, ceil(2 k_T R_proxy + 30)) */
     int32_t top_level;     /* level l0 of the dense top solve (Sec. 7.3); default 1 */
-    int32_t precision;     /* FDS_FP64 */
+    int32_t precision;     /* FDS_FP64 (default) or FDS_MIXED */
     double alpha_re, alpha_im;
     int32_t alpha_set;     /* 0: alpha = i/(mu k_T) */
     uint64_t cuda_stream;  /* cudaStream_t for the build; 0 = legacy default stream */
+    double ir_tol;         /* FDS_MIXED: stop refining when max over right-hand sides of
+                              ||f - A x|| / ||f|| <= ir_tol (A = compressed operator); default 1e-9 */
+    int32_t ir_max_iter;   /* FDS_MIXED: maximum refinement sweeps after the first; default 4;
+                              0 gives the plain complex64 sweep */
 } fds_options;
 
 /* Statistics of a built handle. */
@@ -83,6 +89,8 @@ typedef struct {
     double build_ms;             /* device time of the last fds_build (CUDA events) */
     double solve_ms;             /* device time of the last fds_solve*/
     int64_t factor_bytes;        /* device bytes held by the factors */
+    int32_t ir_iters;            /* FDS_MIXED: refinement sweeps of the last solve */
+    double ir_residual;          /* FDS_MIXED: final max relative residual of the last solve */
 } fds_stats;
 
 /* Fill *o with the defaults listed above. */
@@ -115,12 +123,22 @@ int fds_rhs_plane_wave_device(fds_handle *h, const int32_t *d_kinds, const doubl
                               int32_t nrhs, double *d_f, uint64_t stream);
 
 /*
- * Solve A x = f for nrhs right-hand sides: upward pass z_i = A_i^{-1} f_i,
- * f~_i = A~_i V_i z_i (eq. (linear_last)), top solve, downward pass
- * x_i = z_i - W_i (f~_i - A~_i y_i), W_i = A_i^{-1} U_i (eq. (down_comv)).
+ * Solve A x = f for nrhs right-hand sides (Sec. 6.2-6.3): upward pass
+ * z_i = A_i^{-1} f_i, f~_i = A~_i V_i z_i (eq. (linear_last)), top solve,
+ * downward pass x_i = z_i - W_i (f~_i - A~_i y_i), W_i = A_i^{-1} U_i
+ * (eq. (down_comv)).
+ * FDS_MIXED: the sweep runs on complex64 copies of the factors and is
+ * repeated on the residual r = f - A x, where A is the compressed operator
+ * the factorisation inverts (leaf diagonal blocks, interpolation matrices,
+ * original entries between sibling skeletons and between top cells), applied
+ * in FP64; it stops when max_c ||r_c|| / ||f_c|| <= ir_tol, after ir_max_iter
+ * extra sweeps, or when the residual stops halving.  If the target was not
+ * met the solution reached is still written and FDS_ERR_NOT_CONVERGED is
+ * returned; fds_stats_get reports the sweeps and the final residual.
  * fds_solve: host rhs (2n x nrhs complex, column-major), copied to the device,
  * solved, copied back in place; synchronous.  fds_solve_device: d_rhs on the
- * device, overwritten in place, enqueued on stream.
+ * device, overwritten in place, enqueued on stream (FDS_MIXED synchronises
+ * the stream once per refinement sweep to read the residual norms).
  */
 int fds_solve(fds_handle *h, double *rhs, int32_t nrhs);
 int fds_solve_device(fds_handle *h, double *d_rhs, int32_t nrhs, uint64_t stream);

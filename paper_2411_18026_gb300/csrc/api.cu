@@ -16,6 +16,8 @@ extern "C" void fds_default_options(fds_options *o) {
     o->alpha_im = 0.0;
     o->alpha_set = 0;
     o->cuda_stream = 0;
+    o->ir_tol = 1e-9;
+    o->ir_max_iter = 4;
 }
 
 extern "C" const char *fds_error_string(int code) {
@@ -42,7 +44,8 @@ extern "C" int fds_build_ex(const fds_geometry *g, double omega, double lambda, 
     if (opt) o = *opt;
     else fds_default_options(&o);
     if (o.leaf_size < 2 || !(o.proxy_ratio > 1.0) || o.proxy_points < 8 || o.top_level < 0 ||
-        o.precision != FDS_FP64)
+        (o.precision != FDS_FP64 && o.precision != FDS_MIXED) || !(o.ir_tol >= 0.0) || o.ir_max_iter < 0 ||
+        o.ir_max_iter > 100)
         return FDS_ERR_ARG;
     for (int i = 0; i < 2 * g->n_nodes; ++i)
         if (!std::isfinite(g->xy[i])) return FDS_ERR_ARG;
@@ -128,10 +131,11 @@ extern "C" int fds_solve(fds_handle *h, double *rhs, int32_t nrhs) {
     const size_t bytes = sizeof(cplx) * 2 * (size_t)h->N * nrhs;
     FDS_TRY(d.alloc((size_t)2 * h->N * nrhs));
     FDS_CUDA_TRY(cudaMemcpyAsync(d.p, rhs, bytes, cudaMemcpyHostToDevice, s));
-    FDS_TRY(fds_solve_impl(h, d.p, nrhs, s));
+    const int rc = fds_solve_impl(h, d.p, nrhs, s);
+    if (rc != FDS_OK && rc != FDS_ERR_NOT_CONVERGED) return rc;
     FDS_CUDA_TRY(cudaMemcpyAsync(rhs, d.p, bytes, cudaMemcpyDeviceToHost, s));
     FDS_CUDA_TRY(cudaStreamSynchronize(s));
-    return FDS_OK;
+    return rc;
 }
 
 extern "C" int fds_stats_get(const fds_handle *h, fds_stats *st) {
@@ -155,6 +159,8 @@ extern "C" int fds_stats_get(const fds_handle *h, fds_stats *st) {
     st->build_ms = h->build_ms;
     st->solve_ms = h->solve_ms;
     st->factor_bytes = h->factor_bytes;
+    st->ir_iters = h->ir_iters;
+    st->ir_residual = h->ir_residual;
     return FDS_OK;
 }
 

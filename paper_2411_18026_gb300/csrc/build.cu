@@ -157,7 +157,7 @@ struct GJob {
 
 // Leaf diagonal blocks A_p = A^{J_p J_p} (eq. (block_ax=f)): tile (I, J) of
 // the cell's hats, I <= J; off-diagonal tiles also write the transposed tile.
-__global__ void __launch_bounds__(256) k_tiles_leaf(PhysDev P, const int *__restrict__ lo, const int *__restrict__ hi,
+__global__ void __launch_bounds__(FDS_TILE_THREADS) k_tiles_leaf(PhysDev P, const int *__restrict__ lo, const int *__restrict__ hi,
                                                     const double *__restrict__ xy, int N, const MatRef *A,
                                                     const LeafJob *__restrict__ jobs) {
     __shared__ TileSmem S;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(256) k_tiles_leaf(PhysDev P, const int *__rest
 // M^U = A^{J J'} stacked as (M^U)^H): tile of proxy vertices (cross rule) or
 // near-field hats (boundary rule) against the cell's hats; the transposed
 // entries of the same quadrature points give the M^U rows.
-__global__ void __launch_bounds__(256) k_tiles_y(PhysDev P, YDesc D, const double *__restrict__ xy, int N, cplx *Y,
+__global__ void __launch_bounds__(FDS_TILE_THREADS) k_tiles_y(PhysDev P, YDesc D, const double *__restrict__ xy, int N, cplx *Y,
                                                  const YJob *__restrict__ jobs) {
     __shared__ TileSmem S;
     __shared__ int rowv[TILE][2], colp[TILE][2];
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(256) k_tiles_y(PhysDev P, YDesc D, const doubl
 // Blocks of original entries between two disjoint hat lists of a group:
 // sibling blocks R of eq. (A_rearrangement) and the off-diagonal blocks of the
 // top system.  Items carry the matrix index of each component (or -1).
-__global__ void __launch_bounds__(256) k_tiles_group(PhysDev P, const int *__restrict__ gnode,
+__global__ void __launch_bounds__(FDS_TILE_THREADS) k_tiles_group(PhysDev P, const int *__restrict__ gnode,
                                                      const int *__restrict__ gi1, const int *__restrict__ gi2,
                                                      const double *__restrict__ xy, int N, const MatRef *M,
                                                      const GJob *__restrict__ jobs) {
@@ -533,7 +533,7 @@ int launch_group_blocks(fds_handle *h, const char *name, const std::vector<int64
     FDS_TRY(d_jobs.upload(jobs, s));
     PointCount pc(s);
     ProfScope ps(name, s);
-    fds_count_launch(), k_tiles_group<<<(unsigned)jobs.size(), 256, 0, s>>>(h->P, d_gnode.p, d_g1.p, d_g2.p,
+    fds_count_launch(), k_tiles_group<<<(unsigned)jobs.size(), FDS_TILE_THREADS, 0, s>>>(h->P, d_gnode.p, d_g1.p, d_g2.p,
                                                                           h->d_xy.p, h->N, d_M, d_jobs.p);
     FDS_CUDA_TRY(cudaGetLastError());
     ps.units = pc.read();
@@ -611,11 +611,12 @@ int fds_build_impl(fds_handle *h) {
         {
             PointCount pc(s);
             ProfScope ps("a1.leaf_blocks", s);
-            fds_count_launch(), k_tiles_leaf<<<(unsigned)jobs.size(), 256, 0, s>>>(h->P, d_lo.p, d_hi.p, h->d_xy.p, N,
+            fds_count_launch(), k_tiles_leaf<<<(unsigned)jobs.size(), FDS_TILE_THREADS, 0, s>>>(h->P, d_lo.p, d_hi.p, h->d_xy.p, N,
                                                                                  Lf.rLU.p, d_jobs.p);
             ps.units = pc.read();
         }
         FDS_CUDA_TRY(cudaGetLastError());
+        if (h->opt.precision == FDS_MIXED) FDS_TRY(fds_keep_blocks(Lf, Lf.Dfw, Lf.rDfw, s));
         FDS_TRY(sync_check(s));
     }
 
@@ -757,7 +758,7 @@ int fds_build_impl(fds_handle *h) {
             if (!jobs.empty()) {
                 PointCount pc(s);
                 ProfScope ps(kind == 0 ? "a1.proxy_rows" : "a1.near_rows", s);
-                fds_count_launch(), k_tiles_y<<<(unsigned)jobs.size(), 256, 0, s>>>(h->P, D, h->d_xy.p, N, d_Y.p,
+                fds_count_launch(), k_tiles_y<<<(unsigned)jobs.size(), FDS_TILE_THREADS, 0, s>>>(h->P, D, h->d_xy.p, N, d_Y.p,
                                                                                    d_jobs.p);
                 ps.units = pc.read();
             }
@@ -910,9 +911,11 @@ int fds_build_impl(fds_handle *h) {
         FDS_TRY(C.d_roff.upload(C.roff, s));
         FDS_TRY(alloc_level_A(Pn, s));
         fds_count_launch(), k_zero<<<1024, 256, 0, s>>>(Pn.LU.p, Pn.offA[Pn.nb]);
-        fds_count_launch(), k_place_children<<<nb, 256, 0, s>>>(C.rAt.p, C.d_k1.p, C.d_par_pos1.p, C.d_par_pos2.p, Pn.rLU.p);
         FDS_CUDA_TRY(cudaGetLastError());
-        // sibling blocks R: group = parent, tags = child index
+        // sibling blocks R (group = parent, tags = child index) first, then the
+        // children's A~ blocks on the diagonal (disjoint positions); between
+        // the two the parent blocks hold exactly the sibling coupling S of the
+        // compressed forward operator
         std::vector<int64_t> goff(Pn.nb + 1, 0);
         std::vector<int> gnode, gtag, g1, g2;
         for (int p = 0; p < Pn.nb; ++p) {
@@ -930,6 +933,9 @@ int fds_build_impl(fds_handle *h) {
             goff[p + 1] = (int64_t)gnode.size();
         }
         FDS_TRY(launch_group_blocks(h, "a1.sibling_blocks", goff, gnode, gtag, g1, g2, Pn.rLU.p, s));
+        if (h->opt.precision == FDS_MIXED) FDS_TRY(fds_keep_blocks(Pn, Pn.Sfw, Pn.rSfw, s));
+        fds_count_launch(), k_place_children<<<nb, 256, 0, s>>>(C.rAt.p, C.d_k1.p, C.d_par_pos1.p, C.d_par_pos2.p, Pn.rLU.p);
+        FDS_CUDA_TRY(cudaGetLastError());
     }
 
     // ---- top level (Sec. 6.3): dense system over the cells of level l0
@@ -943,8 +949,6 @@ int fds_build_impl(fds_handle *h) {
         top.rows = top.cols = (int)h->Dtop;
         top.ld = (int)std::max<int64_t>(h->Dtop, 1);
         FDS_TRY(T.d_doff.upload(T.doff, s));
-        fds_count_launch(), k_place_top<<<T.nb, 256, 0, s>>>(T.rLU.p, T.d_doff.p, top);
-        FDS_CUDA_TRY(cudaGetLastError());
         std::vector<int64_t> goff = {0};
         std::vector<int> gnode, gtag, g1, g2;
         for (int b = 0; b < T.nb; ++b)
@@ -957,7 +961,18 @@ int fds_build_impl(fds_handle *h) {
         goff.push_back((int64_t)gnode.size());
         std::vector<MatRef> ht = {top};
         FDS_TRY(h->rtop.upload(ht, s));
+        // off-diagonal blocks between top cells, then the cells' own blocks
         if (T.nb > 1) FDS_TRY(launch_group_blocks(h, "a1.top_blocks", goff, gnode, gtag, g1, g2, h->rtop.p, s));
+        if (h->opt.precision == FDS_MIXED) {
+            FDS_TRY(h->Atop_off.alloc((size_t)h->Dtop * h->Dtop));
+            FDS_CUDA_TRY(cudaMemcpyAsync(h->Atop_off.p, h->Atop.p, h->Atop.bytes(), cudaMemcpyDeviceToDevice, s));
+            MatRef off = top;
+            off.p = h->Atop_off.p;
+            std::vector<MatRef> ho = {off};
+            FDS_TRY(h->rtop_off.upload(ho, s));
+        }
+        fds_count_launch(), k_place_top<<<T.nb, 256, 0, s>>>(T.rLU.p, T.d_doff.p, top);
+        FDS_CUDA_TRY(cudaGetLastError());
         std::vector<int64_t> po = {0, h->Dtop};
         FDS_TRY(h->d_ptop_off.upload(po, s));
         FDS_TRY(h->ptop.alloc(h->Dtop));
@@ -979,6 +994,7 @@ int fds_build_impl(fds_handle *h) {
         }
         FDS_TRY(T.d_doff.upload(T.doff, s));
     }
+    if (h->opt.precision == FDS_MIXED) FDS_TRY(fds_mixed_prepare(h));
     cudaEventRecord(e1, s);
     FDS_CUDA_TRY(cudaEventSynchronize(e1));
     float ms = 0;

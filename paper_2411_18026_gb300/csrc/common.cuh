@@ -44,6 +44,34 @@ __host__ __device__ __forceinline__ cplx cinv(cplx a) {
 }
 __host__ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) { return cmul(a, cinv(b)); }
 
+// complex64 (float2) counterparts for the mixed-precision sweep
+typedef float2 cplxf;
+__host__ __device__ __forceinline__ cplxf mkcf(float r, float i) { return make_float2(r, i); }
+__host__ __device__ __forceinline__ cplxf cadd(cplxf a, cplxf b) { return mkcf(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ cplxf csub(cplxf a, cplxf b) { return mkcf(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ cplxf cmul(cplxf a, cplxf b) {
+    return mkcf(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ cplxf cconj(cplxf a) { return mkcf(a.x, -a.y); }
+__host__ __device__ __forceinline__ float cabs2(cplxf a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ void cfma(cplxf &acc, cplxf a, cplxf b) {
+    acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+    acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+__host__ __device__ __forceinline__ void cfms(cplxf &acc, cplxf a, cplxf b) {
+    acc.x = fmaf(-a.x, b.x, fmaf(a.y, b.y, acc.x));
+    acc.y = fmaf(-a.x, b.y, fmaf(-a.y, b.x, acc.y));
+}
+__host__ __device__ __forceinline__ cplxf cinv(cplxf a) {
+    float d = 1.0f / cabs2(a);
+    return mkcf(a.x * d, -a.y * d);
+}
+template <class C> __host__ __device__ __forceinline__ C czero();
+template <> __host__ __device__ __forceinline__ cplx czero<cplx>() { return mkc(0.0, 0.0); }
+template <> __host__ __device__ __forceinline__ cplxf czero<cplxf>() { return mkcf(0.f, 0.f); }
+__host__ __device__ __forceinline__ cplxf to_c64(cplx a) { return mkcf((float)a.x, (float)a.y); }
+__host__ __device__ __forceinline__ cplx to_c128(cplxf a) { return mkc((double)a.x, (double)a.y); }
+
 // Physical constants prepared on the host for one problem.
 struct PhysDev {
     double lam, mu, rho, omega;
@@ -52,6 +80,8 @@ struct PhysDev {
     double c2;         // 2 / kT^2
     double lhalfT, lhalfL;   // ln(kT/2), ln(kL/2)
     cplx alpha;        // Burton–Miller coupling
+    cplx alpha_rw2;    // alpha rho omega^2
+    cplx alpha_m2mu;   // -2 mu alpha
 };
 
 PhysDev make_physdev(const fds_physics *ph);
@@ -59,9 +89,12 @@ PhysDev make_physdev(const fds_physics *ph);
 // Gauss–Legendre tables on [0,1] for the orders the quadrature rules use.
 // Index q holds q nodes; only q in {1..8, 16, 20} are filled.
 #define GL_MAXQ 20
+#define SER_TERMS 14
 struct GaussTables {
     double x[GL_MAXQ + 1][GL_MAXQ];
     double w[GL_MAXQ + 1][GL_MAXQ];
+    // ascending-series coefficients of the Bessel functions (see kernel_eval.cuh)
+    double sa[SER_TERMS], sb[SER_TERMS], sh[SER_TERMS], sp[SER_TERMS];
 };
 // Each translation unit that evaluates quadrature owns a copy of the table
 // (whole-program compilation, no relocatable device code) and uploads it with

@@ -88,13 +88,15 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu(const MatRef *__restrict__ ma
 // substitution and the upper back substitution.
 constexpr int SOLVE_THREADS = 256;
 
-__global__ void __launch_bounds__(SOLVE_THREADS) k_lu_solve(const MatRef *__restrict__ LUs,
+template <class C>
+__global__ void __launch_bounds__(SOLVE_THREADS) k_lu_solve(const MatRefT<C> *__restrict__ LUs,
                                                             const int *__restrict__ piv,
                                                             const int64_t *__restrict__ poff,
-                                                            const MatRef *__restrict__ Bs, int rt) {
-    extern __shared__ cplx sh[];
-    const MatRef L = LUs[blockIdx.y];
-    const MatRef B = Bs[blockIdx.y];
+                                                            const MatRefT<C> *__restrict__ Bs, int rt) {
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    C *sh = reinterpret_cast<C *>(sh_raw);
+    const MatRefT<C> L = LUs[blockIdx.y];
+    const MatRefT<C> B = Bs[blockIdx.y];
     const int n = L.rows;
     const int c0 = blockIdx.x * rt;
     if (c0 >= B.cols || n == 0) return;
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_lu_solve(const MatRef *__rest
         for (int k = 0; k < n; ++k) {
             const int p = pv[k];
             if (p != k) {
-                cplx t = sh[k + c * n];
+                C t = sh[k + c * n];
                 sh[k + c * n] = sh[p + c * n];
                 sh[p + c * n] = t;
             }
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_lu_solve(const MatRef *__rest
     }
     // backward
     for (int j = n - 1; j >= 0; --j) {
-        const cplx dinv = cinv(L.p[j + (long)j * L.ld]);
+        const C dinv = cinv(L.p[j + (long)j * L.ld]);
         for (int c = threadIdx.x; c < nc; c += blockDim.x) sh[j + c * n] = cmul(sh[j + c * n], dinv);
         __syncthreads();
         for (long e = threadIdx.x; e < (long)j * nc; e += blockDim.x) {
@@ -147,31 +149,33 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_lu_solve(const MatRef *__rest
 // C = alpha op(A) op(B) + beta C; 16x16 output tile per CTA, 16-deep K chunks.
 constexpr int GT = 16;
 
-__device__ __forceinline__ cplx ld_op(const MatRef &M, int op, int i, int j) {
+template <class C>
+__device__ __forceinline__ C ld_op(const MatRefT<C> &M, int op, int i, int j) {
     // element (i, j) of op(M)
     if (op == 0) return M.p[i + (long)j * M.ld];
-    cplx v = M.p[j + (long)i * M.ld];
+    C v = M.p[j + (long)i * M.ld];
     return cconj(v);
 }
 
-__global__ void __launch_bounds__(GT *GT) k_gemm(const MatRef *__restrict__ As, int opA,
-                                                 const MatRef *__restrict__ Bs, int opB,
-                                                 const MatRef *__restrict__ Cs, cplx alpha, cplx beta, int tiles_m) {
-    const MatRef A = As[blockIdx.y], B = Bs[blockIdx.y], C = Cs[blockIdx.y];
-    const int M = C.rows, N = C.cols;
+template <class C>
+__global__ void __launch_bounds__(GT *GT) k_gemm(const MatRefT<C> *__restrict__ As, int opA,
+                                                 const MatRefT<C> *__restrict__ Bs, int opB,
+                                                 const MatRefT<C> *__restrict__ Cs, C alpha, C beta, int tiles_m) {
+    const MatRefT<C> A = As[blockIdx.y], B = Bs[blockIdx.y], Cm = Cs[blockIdx.y];
+    const int M = Cm.rows, N = Cm.cols;
     const int K = (opA == 0) ? A.cols : A.rows;
     const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
     const int i0 = tm * GT, j0 = tn * GT;
     if (i0 >= M || j0 >= N) return;
-    __shared__ cplx sa[GT][GT + 1], sb[GT][GT + 1];
+    __shared__ C sa[GT][GT + 1], sb[GT][GT + 1];
     const int tx = threadIdx.x % GT, ty = threadIdx.x / GT;
-    cplx acc = mkc(0, 0);
+    C acc = czero<C>();
     for (int k0 = 0; k0 < K; k0 += GT) {
         {
             const int i = i0 + tx, k = k0 + ty;
-            sa[ty][tx] = (i < M && k < K) ? ld_op(A, opA, i, k) : mkc(0, 0);
+            sa[ty][tx] = (i < M && k < K) ? ld_op(A, opA, i, k) : czero<C>();
             const int kk = k0 + tx, j = j0 + ty;
-            sb[ty][tx] = (kk < K && j < N) ? ld_op(B, opB, kk, j) : mkc(0, 0);
+            sb[ty][tx] = (kk < K && j < N) ? ld_op(B, opB, kk, j) : czero<C>();
         }
         __syncthreads();
 #pragma unroll
@@ -180,8 +184,8 @@ __global__ void __launch_bounds__(GT *GT) k_gemm(const MatRef *__restrict__ As, 
     }
     const int i = i0 + tx, j = j0 + ty;
     if (i < M && j < N) {
-        cplx *c = &C.p[i + (long)j * C.ld];
-        cplx old = (beta.x != 0.0 || beta.y != 0.0) ? *c : mkc(0, 0);
+        C *c = &Cm.p[i + (long)j * Cm.ld];
+        C old = (beta.x != 0 || beta.y != 0) ? *c : czero<C>();
         *c = cadd(cmul(alpha, acc), cmul(beta, old));
     }
 }
@@ -197,29 +201,49 @@ int dense_lu(int batch, int max_n, const MatRef *d_A, int *d_piv, const int64_t 
     return FDS_OK;
 }
 
-int dense_lu_solve(int batch, int max_rows, int max_cols, const MatRef *d_LU, const int *d_piv,
-                   const int64_t *d_poff, const MatRef *d_B, cudaStream_t s) {
+template <class C>
+static int lu_solve_t(int batch, int max_rows, int max_cols, const MatRefT<C> *d_LU, const int *d_piv,
+                      const int64_t *d_poff, const MatRefT<C> *d_B, cudaStream_t s) {
     if (batch <= 0 || max_rows <= 0 || max_cols <= 0) return FDS_OK;
     // RHS tile width so that rows x rt complex fits in 200 KB of shared memory
-    int rt = (int)(200 * 1024 / (16L * max_rows));
+    int rt = (int)(200 * 1024 / ((long)sizeof(C) * max_rows));
     if (rt > 32) rt = 32;
     if (rt < 1) return FDS_ERR_ARG;
-    size_t smem = (size_t)max_rows * rt * sizeof(cplx);
-    if (smem > 48 * 1024) FDS_CUDA_TRY(cudaFuncSetAttribute(k_lu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    size_t smem = (size_t)max_rows * rt * sizeof(C);
+    if (smem > 48 * 1024)
+        FDS_CUDA_TRY(cudaFuncSetAttribute(k_lu_solve<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((max_cols + rt - 1) / rt, batch);
-    fds_count_launch(), k_lu_solve<<<grid, SOLVE_THREADS, smem, s>>>(d_LU, d_piv, d_poff, d_B, rt);
+    fds_count_launch(), k_lu_solve<C><<<grid, SOLVE_THREADS, smem, s>>>(d_LU, d_piv, d_poff, d_B, rt);
     FDS_CUDA_TRY(cudaGetLastError());
     return FDS_OK;
 }
 
-int dense_gemm(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, int opB,
-               const MatRef *d_C, cplx alpha, cplx beta, cudaStream_t s) {
+template <class C>
+static int gemm_t(int batch, int max_m, int max_n, const MatRefT<C> *d_A, int opA, const MatRefT<C> *d_B, int opB,
+                  const MatRefT<C> *d_C, C alpha, C beta, cudaStream_t s) {
     if (batch <= 0 || max_m <= 0 || max_n <= 0) return FDS_OK;
     const int tm = (max_m + GT - 1) / GT, tn = (max_n + GT - 1) / GT;
     dim3 grid(tm * tn, batch);
-    fds_count_launch(), k_gemm<<<grid, GT * GT, 0, s>>>(d_A, opA, d_B, opB, d_C, alpha, beta, tm);
+    fds_count_launch(), k_gemm<C><<<grid, GT * GT, 0, s>>>(d_A, opA, d_B, opB, d_C, alpha, beta, tm);
     FDS_CUDA_TRY(cudaGetLastError());
     return FDS_OK;
+}
+
+int dense_lu_solve(int batch, int max_rows, int max_cols, const MatRef *d_LU, const int *d_piv,
+                   const int64_t *d_poff, const MatRef *d_B, cudaStream_t s) {
+    return lu_solve_t<cplx>(batch, max_rows, max_cols, d_LU, d_piv, d_poff, d_B, s);
+}
+int dense_lu_solve(int batch, int max_rows, int max_cols, const MatRefF *d_LU, const int *d_piv,
+                   const int64_t *d_poff, const MatRefF *d_B, cudaStream_t s) {
+    return lu_solve_t<cplxf>(batch, max_rows, max_cols, d_LU, d_piv, d_poff, d_B, s);
+}
+int dense_gemm(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, int opB,
+               const MatRef *d_C, cplx alpha, cplx beta, cudaStream_t s) {
+    return gemm_t<cplx>(batch, max_m, max_n, d_A, opA, d_B, opB, d_C, alpha, beta, s);
+}
+int dense_gemm(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, const MatRefF *d_B, int opB,
+               const MatRefF *d_C, cplxf alpha, cplxf beta, cudaStream_t s) {
+    return gemm_t<cplxf>(batch, max_m, max_n, d_A, opA, d_B, opB, d_C, alpha, beta, s);
 }
 
 // Stage entry point: batched LU (see fds.h).

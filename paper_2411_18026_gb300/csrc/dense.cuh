@@ -6,11 +6,14 @@
 
 #include "common.cuh"
 
-// Per-matrix descriptor of a batch.
-struct MatRef {
-    cplx *p;       // base pointer
+// Per-matrix descriptor of a batch (complex128 or complex64 elements).
+template <class C>
+struct MatRefT {
+    C *p;          // base pointer
     int rows, cols, ld;
 };
+typedef MatRefT<cplx> MatRef;
+typedef MatRefT<cplxf> MatRefF;
 
 // Launch helpers (device pointers to descriptor arrays; all enqueue on stream).
 // LU in place of square A[b] (rows == cols), pivots piv + poff[b], info[b].
@@ -23,3 +26,8 @@ int dense_lu_solve(int batch, int max_rows, int max_cols, const MatRef *d_LU, co
 // C = alpha * op(A) * op(B) + beta * C, op = N (0), or conjugate transpose (2).
 int dense_gemm(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, int opB,
                const MatRef *d_C, cplx alpha, cplx beta, cudaStream_t s);
+// complex64 versions (mixed-precision sweep)
+int dense_lu_solve(int batch, int max_rows, int max_cols, const MatRefF *d_LU, const int *d_piv,
+                   const int64_t *d_poff, const MatRefF *d_B, cudaStream_t s);
+int dense_gemm(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, const MatRefF *d_B, int opB,
+               const MatRefF *d_C, cplxf alpha, cplxf beta, cudaStream_t s);

@@ -83,6 +83,13 @@ struct Level {
     int64_t D = 0, Rtot = 0;               // total DOFs / total skeleton DOFs of the level
     int dmax = 0, rmax = 0;
     double sum_d2 = 0, sum_rd = 0, sum_r2 = 0;   // algorithmic work sums for the sweep
+    // --- mixed precision: complex64 copies of the sweep factors
+    DBuf<cplxf> LUf, Wf, Atf, Vf;
+    DBuf<MatRefF> rLUf, rWf, rAtf, rVf;
+    // --- FP64 compressed forward operator: leaf diagonal blocks (leaf level)
+    //     and sibling-coupling blocks S (levels that are parents), both d x d
+    DBuf<cplx> Dfw, Sfw;
+    DBuf<MatRef> rDfw, rSfw;
 };
 
 struct fds_handle {
@@ -106,15 +113,47 @@ struct fds_handle {
     DBuf<MatRef> rtop;
     DBuf<int64_t> d_ptop_off;
     DBuf<int> d_info;
+    // mixed precision: off-diagonal top blocks (FP64) and complex64 top LU
+    DBuf<cplx> Atop_off;
+    DBuf<MatRef> rtop_off;
+    DBuf<cplxf> Atopf;
+    DBuf<MatRefF> rtopf;
     // solve workspace (grown on demand)
-    std::vector<DBuf<cplx>> wz, wf, wt;
-    DBuf<cplx> wtop;
+    std::vector<DBuf<cplx>> wz, wf, wt, wy;
+    std::vector<DBuf<cplxf>> wzf, wff, wtf;
+    DBuf<cplx> wtop, wytop, wX;
+    DBuf<cplxf> wtopf;
     DBuf<MatRef> wrefs;
+    DBuf<MatRefF> wrefsf;
+    DBuf<double> wnorm;
     int64_t ws_cols = 0;
     double build_ms = 0, solve_ms = 0;
     int64_t factor_bytes = 0;
+    int ir_iters = 0;          // refinement sweeps of the last mixed solve
+    double ir_residual = 0;    // max_c ||f_c - A x_c|| / ||f_c|| after the last mixed solve
 };
 
+// Per-cell descriptors of blocks stored back to back at base + off[b].
+template <class C>
+int make_refs_t(DBuf<MatRefT<C>> &dst, C *base, const std::vector<int64_t> &off, const std::vector<int> &rows,
+                const std::vector<int> &cols, cudaStream_t s) {
+    std::vector<MatRefT<C>> h(rows.size());
+    for (size_t b = 0; b < rows.size(); ++b) {
+        h[b].p = base + off[b];
+        h[b].rows = rows[b];
+        h[b].cols = cols[b];
+        h[b].ld = rows[b] > 1 ? rows[b] : 1;
+    }
+    return dst.upload(h, s);
+}
+
 int fds_build_impl(fds_handle *h);
+// FDS_MIXED: copy of a level's square blocks (LU buffer, before it is factored)
+// into a forward-operator store.
+int fds_keep_blocks(const Level &Lv, DBuf<cplx> &dst, DBuf<MatRef> &rdst, cudaStream_t s);
+// FDS_MIXED: complex64 copies of the sweep factors; releases the FP64 ones
+// that the sweep no longer needs.
+int fds_mixed_prepare(fds_handle *h);
+int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s);
 int fds_solve_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s);
 int fds_rhs_impl(fds_handle *h, const int *d_kinds, const double *d_angles, int nrhs, cplx *d_f, cudaStream_t s);

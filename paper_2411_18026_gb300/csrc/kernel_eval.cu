@@ -24,6 +24,8 @@ PhysDev make_physdev(const fds_physics *ph) {
         P.alpha = mkc(ph->alpha_re, ph->alpha_im);
     else
         P.alpha = mkc(0.0, 1.0 / (P.mu * P.kT));   // alpha = i / (mu k_T)
+    P.alpha_rw2 = cscale(P.alpha, P.rw2);
+    P.alpha_m2mu = cscale(P.alpha, -2.0 * P.mu);
     return P;
 }
 
@@ -65,6 +67,22 @@ int gauss_tables_host(GaussTables *T) {
     if (!ready) {
         memset(&cache, 0, sizeof(cache));
         for (int q = 1; q <= GL_MAXQ; ++q) gauss_legendre01(q, cache.x[q], cache.w[q]);
+        // series coefficients in powers of q = -z^2/4:
+        //   sa_m = 1/(m!)^2, sb_m = 1/(m!(m+1)!), sh_m = H_m sa_m,
+        //   sp_m = (2 (H_m - gamma) + 1/(m+1)) sb_m,  H_m = 1 + 1/2 + ... + 1/m
+        const double g = 0.57721566490153286061;
+        double fm = 1.0, hm = 0.0;   // m!, H_m
+        for (int m = 0; m < SER_TERMS; ++m) {
+            if (m > 0) {
+                fm *= m;
+                hm += 1.0 / m;
+            }
+            const double a = 1.0 / (fm * fm), b = 1.0 / (fm * fm * (m + 1.0));
+            cache.sa[m] = a;
+            cache.sb[m] = b;
+            cache.sh[m] = hm * a;
+            cache.sp[m] = (2.0 * (hm - g) + 1.0 / (m + 1.0)) * b;
+        }
         ready = true;
     }
     *T = cache;
@@ -78,7 +96,7 @@ using namespace fdsk;
 // Stage kernels: one CTA per (row chunk, column chunk) tile; forward entries
 // only (the row and column lists may overlap).  Output column-major
 // out[(r + i nr) + (c + j nc) * 2 nr].
-__global__ void __launch_bounds__(256) k_stage_tiles(PhysDev P, const double *__restrict__ X, int NX,
+__global__ void __launch_bounds__(FDS_TILE_THREADS) k_stage_tiles(PhysDev P, const double *__restrict__ X, int NX,
                                                      const int *__restrict__ rows, int nr,
                                                      const double *__restrict__ Y, int NY,
                                                      const int *__restrict__ cols, int nc, int q, int same,
@@ -123,7 +141,7 @@ extern "C" int fds_eval_entries(const fds_physics *ph, const double *d_xy, int32
     FDS_TRY(ensure_gauss_tables());
     PhysDev P = make_physdev(ph);
     dim3 grid(ceil_div_u(nr, TILE), ceil_div_u(nc, TILE));
-    fds_count_launch(), k_stage_tiles<<<grid, 256, 0, (cudaStream_t)stream>>>(
+    fds_count_launch(), k_stage_tiles<<<grid, FDS_TILE_THREADS, 0, (cudaStream_t)stream>>>(
         P, d_xy, n, d_rows, nr, d_xy, n, d_cols, nc, 0, 1, (cplx *)d_out);
     FDS_CUDA_TRY(cudaGetLastError());
     return FDS_OK;
@@ -139,7 +157,7 @@ extern "C" int fds_eval_cross(const fds_physics *ph, const double *d_X, int32_t 
     FDS_TRY(ensure_gauss_tables());
     PhysDev P = make_physdev(ph);
     dim3 grid(ceil_div_u(nr, TILE), ceil_div_u(nc, TILE));
-    fds_count_launch(), k_stage_tiles<<<grid, 256, 0, (cudaStream_t)stream>>>(
+    fds_count_launch(), k_stage_tiles<<<grid, FDS_TILE_THREADS, 0, (cudaStream_t)stream>>>(
         P, d_X, nx, d_rows, nr, d_Y, ny, d_cols, nc, q, 0, (cplx *)d_out);
     FDS_CUDA_TRY(cudaGetLastError());
     return FDS_OK;

@@ -34,6 +34,16 @@
 
 namespace fdsk {
 
+// 1: both orientations of an element pair from one evaluation of the radial
+// functions (more registers); 0: two passes.
+#ifndef FDS_DUAL_ONEPASS
+#define FDS_DUAL_ONEPASS 1
+#endif
+
+#ifndef FDS_TILE_THREADS
+#define FDS_TILE_THREADS 128
+#endif
+
 constexpr int TILE = 15;        // 15 consecutive hats span 16 elements: 256 element pairs
 
 // Quadrature points evaluated (point pairs x orientations), counted when
@@ -66,40 +76,49 @@ __device__ __forceinline__ void load_rules(Rules &R, int qcross) {
 
 // ---------------------------------------------------------------- Bessel
 // H0^(1)(z), H1^(1)(z) and E(z) = (z H1(z) + 2i/pi)/z^2.  For z < 2 from the
-// ascending series (Abramowitz & Stegun 9.1.10, 9.1.11, 9.1.13), sharing the
-// terms s_m = (-z^2/4)^m/(m!)^2, u_m = s_m/(m+1) and ln(z/2):
-//   J0 = sum s_m,  J1/z = sum u_m / 2,
-//   Y0 = (2/pi) [ (ln(z/2) + g) J0 - sum_{m>=1} H_m s_m ],
-//   Im E = (2/pi) ln(z/2) J1/z - (1/(2 pi)) sum (psi(m+1)+psi(m+2)) u_m,
-//   psi(m+1)+psi(m+2) = 2 (H_m - g) + 1/(m+1),  Y1 = z Im E - 2/(pi z).
-// For z >= 2 from CUDA's j0/y0/j1/y1.
+// ascending series (Abramowitz & Stegun 9.1.10, 9.1.11, 9.1.13) as
+// polynomials in q = -z^2/4 with tabulated coefficients (Horner):
+//   J0 = sum q^m/(m!)^2,  J1/z = (1/2) sum q^m/(m!(m+1)!),
+//   Y0 = (2/pi) [ (ln(z/2) + g) J0 - sum_{m>=1} H_m q^m/(m!)^2 ],
+//   Im E = (2/pi) ln(z/2) J1/z - (1/(2 pi)) sum (2 (H_m - g) + 1/(m+1)) q^m/(m!(m+1)!),
+//   Y1 = z Im E - 2/(pi z).
+// 14 terms reach 1e-16 for z < 2.  For z >= 2 from
+// CUDA's j0/y0/j1/y1.
 struct Hk {
     cplx h0, h1, e;
 };
 
-__device__ __forceinline__ Hk hankel_k(double z, double lhalf) {
+// Coefficients are read from __constant__ memory: every lane reads the same
+// address, so the reads are broadcasts and need no registers.
+template <int M>
+__device__ __forceinline__ void series4(const Rules &G, double q, double &J0, double &Su, double &SH, double &Sp) {
+    (void)G;
+    J0 = c_gauss.sa[M - 1];
+    Su = c_gauss.sb[M - 1];
+    SH = c_gauss.sh[M - 1];
+    Sp = c_gauss.sp[M - 1];
+#pragma unroll
+    for (int m = M - 2; m >= 0; --m) {
+        J0 = fma(J0, q, c_gauss.sa[m]);
+        Su = fma(Su, q, c_gauss.sb[m]);
+        SH = fma(SH, q, c_gauss.sh[m]);
+        Sp = fma(Sp, q, c_gauss.sp[m]);
+    }
+}
+
+__device__ __forceinline__ Hk hankel_k(const Rules &G, double z, double lhalf) {
     Hk H;
     if (z < 2.0) {
         const double g = 0.57721566490153286061;
-        const double t = 0.25 * z * z;
-        double s = 1.0, hm = 0.0;
-        double J0 = 1.0, Su = 1.0, SH = 0.0, Sp = 1.0 - 2.0 * g;
-        for (int m = 1; m < 20; ++m) {
-            s *= -t / ((double)m * m);
-            hm += 1.0 / m;
-            const double u = s / (m + 1.0);
-            J0 += s;
-            Su += u;
-            SH = fma(hm, s, SH);
-            Sp = fma(2.0 * (hm - g) + 1.0 / (m + 1.0), u, Sp);
-            if (fabs(s) < 1e-18) break;
-        }
+        const double q = -0.25 * z * z;
+        double J0, Su, SH, Sp;
+        series4<SER_TERMS>(G, q, J0, Su, SH, Sp);
         const double j1z = 0.5 * Su;                      // J1(z)/z
         const double Y0 = (2.0 / FDS_PI) * ((lhalf + g) * J0 - SH);
         const double eim = (2.0 / FDS_PI) * lhalf * j1z - Sp * (0.5 / FDS_PI);
         H.h0 = mkc(J0, Y0);
         H.e = mkc(j1z, eim);
-        H.h1 = mkc(z * j1z, z * eim - 2.0 / (FDS_PI * z));
+        H.h1 = mkc(z * j1z, z * eim - (2.0 / FDS_PI) / z);
     } else {
         const double a0 = j0(z), b0 = y0(z), a1 = j1(z), b1 = y1(z);
         const double iz2 = 1.0 / (z * z);
@@ -119,10 +138,10 @@ struct Radial {
     cplx a, b;         // d_k d_p F = a zh_k zh_p - b delta_kp
 };
 
-__device__ __forceinline__ Radial radial(const PhysDev &P, double r) {
+__device__ __forceinline__ Radial radial(const PhysDev &P, const Rules &G, double r) {
     const double lr = log(r);
-    const Hk T = hankel_k(P.kT * r, P.lhalfT + lr);
-    const Hk L = hankel_k(P.kL * r, P.lhalfL + lr);
+    const Hk T = hankel_k(G, P.kT * r, P.lhalfT + lr);
+    const Hk L = hankel_k(G, P.kL * r, P.lhalfL + lr);
     Radial R;
     // g = (i/4) H0 ; g' = -(i/4) k H1
     R.gT = mkc(-0.25 * T.h0.y, 0.25 * T.h0.x);
@@ -294,77 +313,128 @@ __device__ __forceinline__ void acc_zero(PairAcc &S) {
     for (int k = 0; k < 32; ++k) S.v[k] = 0.0;
 }
 
-// Kernel entry (i, j) of the blocks K0 (psi phi), K1 (psi phi'), K2 (psi' phi)
-// of D + alpha N for unit direction zh = (zx, zy) (z = y - x), test normal
-// nx, trial normal ny; see the header comment for the formulas.
-__device__ __forceinline__ void k012_entry(const PhysDev &P, const Radial &R, const cplx &AgL, const cplx &AgT,
-                                           const cplx &MgTp, const cplx &MgLp, double zx, double zy, double2 nx,
-                                           double2 ny, int i, int j, cplx &k0, cplx &k1, cplx &k2) {
-    const double zhi = i ? zy : zx, zhj = j ? zy : zx;
-    const double zpi = i ? -zx : zy, zpj = j ? -zx : zy;        // eps zh
-    const double nxi = i ? nx.y : nx.x, nyj = j ? ny.y : ny.x;
-    const double txi = i ? -nx.x : nx.y, tyj = j ? -ny.x : ny.y;
-    // K0 = n^y_j g_L' zh_i + t^y_j g_T' zp_i + alpha rw2 (nx_i ny_j gL + tx_i ty_j gT)
-    k0 = cadd(cadd(cscale(R.gLp, nyj * zhi), cscale(R.gTp, tyj * zpi)),
-              cadd(cscale(AgL, nxi * nyj), cscale(AgT, txi * tyj)));
-    // K1 = -(2 eps_ji g_T + c (a zp_j zh_i - b eps_ji)) - 2 mu alpha (t^x_i g_T' zh_j - n^x_i g_L' zp_j)
-    const double eji = (j == 0 && i == 1) ? 1.0 : ((j == 1 && i == 0) ? -1.0 : 0.0);
-    cplx v = cscale(R.a, P.c2 * zpj * zhi);
-    v = csub(v, cscale(R.b, P.c2 * eji));
-    v = cadd(v, cscale(R.gT, 2.0 * eji));
-    k1 = csub(csub(cscale(MgTp, txi * zhj), cscale(MgLp, nxi * zpj)), v);
-    // K2 = -2 mu alpha (n^y_j g_L' zp_i - t^y_j g_T' zh_i)
-    k2 = csub(cscale(MgLp, nyj * zpi), cscale(MgTp, tyj * zhi));
-}
+// Per-point quantities shared by both orientations of a point pair.
+struct PointShared {
+    Radial R;
+    double zx, zy;          // unit vector zh = z / r (forward orientation)
+    cplx AgL, AgT;          // alpha rho w^2 g_L, alpha rho w^2 g_T
+    cplx MgTp, MgLp;        // -2 mu alpha g_T', -2 mu alpha g_L'
+    cplx k3_00, k3_11, k3_01;   // K3 = 2 mu alpha (2 delta g_T + c (a zp zp^T - b I))
+    cplx e1[2][2];          // even part of K1: -(2 eps_ji g_T + c (a zp_j zh_i - b eps_ji))
+};
 
-// Add one point (local coords sig, tau; relative z; weight w) to the forward
-// (dir 0) or the transposed (dir 1) entries.  maskA/maskB: local basis
-// indices used on E / F.
-__device__ __forceinline__ void acc_point(const PhysDev &P, const Elem &E, const Elem &F, double sig, double tau,
-                                          double2 z, double w, int dir, int maskA, int maskB, PairAcc &S) {
+__device__ __forceinline__ void point_shared(const PhysDev &P, const Rules &G, double2 z, PointShared &Q) {
     const double r = sqrt(z.x * z.x + z.y * z.y);
-    const double ir = dir ? -1.0 / r : 1.0 / r;     // transposed entry: z -> -z
-    const double zx = z.x * ir, zy = z.y * ir;
-    const Radial R = radial(P, r);
-    const cplx AgL = cmul(P.alpha, cscale(R.gL, P.rw2));
-    const cplx AgT = cmul(P.alpha, cscale(R.gT, P.rw2));
-    const cplx MgTp = cmul(P.alpha, cscale(R.gTp, -2.0 * P.mu));
-    const cplx MgLp = cmul(P.alpha, cscale(R.gLp, -2.0 * P.mu));
-    const cplx A2 = cscale(P.alpha, 2.0 * P.mu);
-    const cplx k3d = csub(cscale(R.gT, 2.0), cscale(R.b, P.c2));
-    // test side (normal, basis on it) and trial side
-    const double2 nx = dir ? F.n : E.n, ny = dir ? E.n : F.n;
-    const double ht = dir ? F.h : E.h, hs = dir ? E.h : F.h;
-    const double ct = dir ? tau : sig, cs = dir ? sig : tau;
-    const double nt[2] = {w * (1.0 - ct), w * ct}, dt[2] = {-w / ht, w / ht};
-    const double ns[2] = {1.0 - cs, cs}, ds[2] = {-1.0 / hs, 1.0 / hs};
-    const int mt = dir ? maskB : maskA, ms = dir ? maskA : maskB;
+    const double ir = 1.0 / r;
+    Q.zx = z.x * ir;
+    Q.zy = z.y * ir;
+    Q.R = radial(P, G, r);
+    Q.AgL = cmul(P.alpha_rw2, Q.R.gL);
+    Q.AgT = cmul(P.alpha_rw2, Q.R.gT);
+    Q.MgTp = cmul(P.alpha_m2mu, Q.R.gTp);
+    Q.MgLp = cmul(P.alpha_m2mu, Q.R.gLp);
+    const double zp0 = Q.zy, zp1 = -Q.zx;
+    const cplx ca = cscale(Q.R.a, P.c2);
+    const cplx A2 = cscale(P.alpha_m2mu, -1.0);                      // 2 mu alpha
+    const cplx k3d = csub(cscale(Q.R.gT, 2.0), cscale(Q.R.b, P.c2));
+    Q.k3_00 = cmul(A2, cadd(cscale(ca, zp0 * zp0), k3d));
+    Q.k3_11 = cmul(A2, cadd(cscale(ca, zp1 * zp1), k3d));
+    Q.k3_01 = cmul(A2, cscale(ca, zp0 * zp1));
+    // e1_ij = -c a zp_j zh_i + eps_ji (c b - 2 g_T); eps_01 = 1, eps_10 = -1
+    const cplx cb2 = csub(cscale(Q.R.b, P.c2), cscale(Q.R.gT, 2.0));
+    const double zh[2] = {Q.zx, Q.zy}, zp[2] = {zp0, zp1};
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            cplx k0, k1, k2;
-            k012_entry(P, R, AgL, AgT, MgTp, MgLp, zx, zy, nx, ny, i, j, k0, k1, k2);
-            // K3 = 2 mu alpha (2 delta_ij g_T + c (a zp_i zp_j - b delta_ij))
-            const double zpi = i ? -zx : zy, zpj = j ? -zx : zy;
-            cplx k3 = cscale(R.a, P.c2 * zpi * zpj);
-            if (i == j) k3 = cadd(k3, k3d);
-            k3 = cmul(A2, k3);
+            cplx v = cscale(ca, -zp[j] * zh[i]);
+            if (j == 0 && i == 1) v = cadd(v, cb2);
+            if (j == 1 && i == 0) v = csub(v, cb2);
+            Q.e1[i][j] = v;
+        }
+}
+
+// K0, K1, K2 of D + alpha N for one orientation: test normal nx, trial normal
+// ny, direction zh scaled by sgn (+1 forward, -1 transposed):
+//   K0_ij = P_i n^y_j + Q_i t^y_j,  P_i = g_L' zh_i + alpha rho w^2 g_L n^x_i,
+//                                  Q_i = g_T' zp_i + alpha rho w^2 g_T t^x_i
+//   K1_ij = e1_ij + t^x_i X_j + n^x_i Y_j,  X_j = -2 mu alpha g_T' zh_j,
+//                                          Y_j = 2 mu alpha g_L' zp_j
+//   K2_ij = -(n^y_j Y_i + t^y_j X_i)
+__device__ __forceinline__ void blocks_orient(const PointShared &Q, double sgn, double2 nx, double2 ny,
+                                              cplx k0[2][2], cplx k1[2][2], cplx k2[2][2]) {
+    const double zh[2] = {sgn * Q.zx, sgn * Q.zy}, zp[2] = {sgn * Q.zy, -sgn * Q.zx};
+    const double nxv[2] = {nx.x, nx.y}, txv[2] = {nx.y, -nx.x};
+    const double nyv[2] = {ny.x, ny.y}, tyv[2] = {ny.y, -ny.x};
+    cplx Pv[2], Qv[2], X[2], Y[2];
 #pragma unroll
-            for (int T = 0; T < 2; ++T) {
-                if (!(mt & (1 << T))) continue;
+    for (int i = 0; i < 2; ++i) {
+        Pv[i] = cadd(cscale(Q.R.gLp, zh[i]), cscale(Q.AgL, nxv[i]));
+        Qv[i] = cadd(cscale(Q.R.gTp, zp[i]), cscale(Q.AgT, txv[i]));
+        X[i] = cscale(Q.MgTp, zh[i]);
+        Y[i] = cscale(Q.MgLp, -zp[i]);
+    }
 #pragma unroll
-                for (int U = 0; U < 2; ++U) {
-                    if (!(ms & (1 << U))) continue;
-                    const double b0 = nt[T] * ns[U], b1 = nt[T] * ds[U];
-                    const double b2 = dt[T] * ns[U], b3 = dt[T] * ds[U];
-                    // forward: v[FIDX(A = T, B = U)]; transposed: v[RIDX(B = T, A = U)]
-                    const int q = dir ? RIDX(T, U, i, j) - 32 : FIDX(T, U, i, j);
-                    S.v[q] += b0 * k0.x + b1 * k1.x + b2 * k2.x + b3 * k3.x;
-                    S.v[q + 1] += b0 * k0.y + b1 * k1.y + b2 * k2.y + b3 * k3.y;
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            k0[i][j] = cadd(cscale(Pv[i], nyv[j]), cscale(Qv[i], tyv[j]));
+            k1[i][j] = cadd(Q.e1[i][j], cadd(cscale(X[j], txv[i]), cscale(Y[j], nxv[i])));
+            k2[i][j] = cneg(cadd(cscale(Y[i], nyv[j]), cscale(X[i], tyv[j])));
+        }
+}
+
+// acc[T][U] += sum over the four kernel blocks with weights
+//   b0 = nt[T] ns[U], b1 = nt[T] ds[U], b2 = dt[T] ns[U], b3 = dt[T] ds[U]
+// factored as u_U = ns[U] k0 + ds[U] k1, v_U = ns[U] k2 + ds[U] k3,
+// acc[T][U] += nt[T] u_U + dt[T] v_U.
+template <bool TRANSPOSED, int BASE, int NV>
+__device__ __forceinline__ void accum_orient(double (&acc)[NV], const cplx k0[2][2], const cplx k1[2][2],
+                                             const cplx k2[2][2], const PointShared &Q, const double nt[2],
+                                             const double dt[2], const double ns[2], const double ds[2], int mt,
+                                             int ms) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const cplx k3 = (i == j) ? (i == 0 ? Q.k3_00 : Q.k3_11) : Q.k3_01;
+#pragma unroll
+            for (int U = 0; U < 2; ++U) {
+                if (!(ms & (1 << U))) continue;
+                const cplx u = cadd(cscale(k0[i][j], ns[U]), cscale(k1[i][j], ds[U]));
+                const cplx v = cadd(cscale(k2[i][j], ns[U]), cscale(k3, ds[U]));
+#pragma unroll
+                for (int T = 0; T < 2; ++T) {
+                    if (!(mt & (1 << T))) continue;
+                    // forward: FIDX(A = T, B = U); transposed: RIDX(B = T, A = U)
+                    const int q = (TRANSPOSED ? RIDX(T, U, i, j) : FIDX(T, U, i, j)) - BASE;
+                    acc[q] = fma(nt[T], u.x, fma(dt[T], v.x, acc[q]));
+                    acc[q + 1] = fma(nt[T], u.y, fma(dt[T], v.y, acc[q + 1]));
                 }
             }
         }
+}
+
+// Add one point (local coords sig, tau; relative z; weight w) to the forward
+// (dir 0) or the transposed (dir 1) entries.  maskA/maskB: local basis
+// indices used on E / F; ihE, ihF = 1/h of E, F.
+__device__ __forceinline__ void acc_point(const PhysDev &P, const Rules &G, const Elem &E, const Elem &F, double ihE,
+                                          double ihF, double sig, double tau, double2 z, double w, int dir, int maskA,
+                                          int maskB, PairAcc &S) {
+    PointShared Q;
+    point_shared(P, G, z, Q);
+    cplx k0[2][2], k1[2][2], k2[2][2];
+    if (dir == 0) {
+        blocks_orient(Q, 1.0, E.n, F.n, k0, k1, k2);
+        const double nt[2] = {w * (1.0 - sig), w * sig}, dt[2] = {-w * ihE, w * ihE};
+        const double ns[2] = {1.0 - tau, tau}, ds[2] = {-ihF, ihF};
+        accum_orient<false, 0>(S.v, k0, k1, k2, Q, nt, dt, ns, ds, maskA, maskB);
+    } else {
+        blocks_orient(Q, -1.0, F.n, E.n, k0, k1, k2);
+        const double nt[2] = {w * (1.0 - tau), w * tau}, dt[2] = {-w * ihF, w * ihF};
+        const double ns[2] = {1.0 - sig, sig}, ds[2] = {-ihE, ihE};
+        accum_orient<true, 32>(S.v, k0, k1, k2, Q, nt, dt, ns, ds, maskB, maskA);
+    }
 }
 
 // Both orientations from one evaluation of the radial functions: v[0..31] =
@@ -373,76 +443,38 @@ struct PairAcc2 {
     double v[64];
 };
 
-__device__ __forceinline__ void acc_point2(const PhysDev &P, const Elem &E, const Elem &F, double sig, double tau,
-                                           double2 z, double w, int maskA, int maskB, PairAcc2 &S) {
-    const double r = sqrt(z.x * z.x + z.y * z.y);
-    const double ir = 1.0 / r;
-    const double zx = z.x * ir, zy = z.y * ir;
-    const Radial R = radial(P, r);
-    const cplx AgL = cmul(P.alpha, cscale(R.gL, P.rw2));
-    const cplx AgT = cmul(P.alpha, cscale(R.gT, P.rw2));
-    const cplx MgTp = cmul(P.alpha, cscale(R.gTp, -2.0 * P.mu));
-    const cplx MgLp = cmul(P.alpha, cscale(R.gLp, -2.0 * P.mu));
-    const cplx A2 = cscale(P.alpha, 2.0 * P.mu);
-    const cplx k3d = csub(cscale(R.gT, 2.0), cscale(R.b, P.c2));
-    const double na[2] = {w * (1.0 - sig), w * sig}, da[2] = {-w / E.h, w / E.h};
-    const double nb[2] = {1.0 - tau, tau}, db[2] = {-1.0 / F.h, 1.0 / F.h};
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const double zpi = i ? -zx : zy, zpj = j ? -zx : zy;
-            cplx k3 = cscale(R.a, P.c2 * zpi * zpj);
-            if (i == j) k3 = cadd(k3, k3d);
-            k3 = cmul(A2, k3);
-            {
-                cplx k0, k1, k2;
-                k012_entry(P, R, AgL, AgT, MgTp, MgLp, zx, zy, E.n, F.n, i, j, k0, k1, k2);
-#pragma unroll
-                for (int A = 0; A < 2; ++A) {
-                    if (!(maskA & (1 << A))) continue;
-#pragma unroll
-                    for (int B = 0; B < 2; ++B) {
-                        if (!(maskB & (1 << B))) continue;
-                        const double b0 = na[A] * nb[B], b1 = na[A] * db[B];
-                        const double b2 = da[A] * nb[B], b3 = da[A] * db[B];
-                        const int q = FIDX(A, B, i, j);
-                        S.v[q] += b0 * k0.x + b1 * k1.x + b2 * k2.x + b3 * k3.x;
-                        S.v[q + 1] += b0 * k0.y + b1 * k1.y + b2 * k2.y + b3 * k3.y;
-                    }
-                }
-            }
-            {
-                // transposed: test point on F (normal F.n), trial on E, z -> -z
-                cplx k0, k1, k2;
-                k012_entry(P, R, AgL, AgT, MgTp, MgLp, -zx, -zy, F.n, E.n, i, j, k0, k1, k2);
-#pragma unroll
-                for (int A = 0; A < 2; ++A) {
-                    if (!(maskA & (1 << A))) continue;
-#pragma unroll
-                    for (int B = 0; B < 2; ++B) {
-                        if (!(maskB & (1 << B))) continue;
-                        // test hat B on F, trial hat A on E
-                        const double b0 = na[A] * nb[B], b1 = nb[B] * da[A];
-                        const double b2 = db[B] * na[A], b3 = db[B] * da[A];
-                        const int q = RIDX(B, A, i, j);
-                        S.v[q] += b0 * k0.x + b1 * k1.x + b2 * k2.x + b3 * k3.x;
-                        S.v[q + 1] += b0 * k0.y + b1 * k1.y + b2 * k2.y + b3 * k3.y;
-                    }
-                }
-            }
-        }
+__device__ __forceinline__ void acc_point2(const PhysDev &P, const Rules &G, const Elem &E, const Elem &F, double ihE,
+                                           double ihF, double sig, double tau, double2 z, double w, int maskA,
+                                           int maskB, PairAcc2 &S) {
+    PointShared Q;
+    point_shared(P, G, z, Q);
+    {
+        cplx k0[2][2], k1[2][2], k2[2][2];
+        blocks_orient(Q, 1.0, E.n, F.n, k0, k1, k2);
+        const double nt[2] = {w * (1.0 - sig), w * sig}, dt[2] = {-w * ihE, w * ihE};
+        const double ns[2] = {1.0 - tau, tau}, ds[2] = {-ihF, ihF};
+        accum_orient<false, 0>(S.v, k0, k1, k2, Q, nt, dt, ns, ds, maskA, maskB);
+    }
+    {
+        // transposed: test point on F (normal F.n), trial on E, z -> -z
+        cplx k0[2][2], k1[2][2], k2[2][2];
+        blocks_orient(Q, -1.0, F.n, E.n, k0, k1, k2);
+        const double nt[2] = {w * (1.0 - tau), w * tau}, dt[2] = {-w * ihF, w * ihF};
+        const double ns[2] = {1.0 - sig, sig}, ds[2] = {-ihE, ihE};
+        accum_orient<true, 0>(S.v, k0, k1, k2, Q, nt, dt, ns, ds, maskB, maskA);
+    }
 }
 
 __device__ __forceinline__ void acc_pair2(const PhysDev &P, const Rules &G, int kind, const Elem &E, const Elem &F,
                                           int p0, int stride, int maskA, int maskB, PairAcc2 &S) {
     const int np = pair_points(kind, G.q);
+    const double ihE = 1.0 / E.h, ihF = 1.0 / F.h;
     for (int p = p0; p < np; p += stride) {
         double sig, tau, w;
         double2 z;
         pair_point(G, kind, p, E, F, sig, tau, z, w);
-        acc_point2(P, E, F, sig, tau, z, w, maskA, maskB, S);
-        if (kind == PK_SELF) acc_point2(P, E, F, tau, sig, make_double2(-z.x, -z.y), w, maskA, maskB, S);
+        acc_point2(P, G, E, F, ihE, ihF, sig, tau, z, w, maskA, maskB, S);
+        if (kind == PK_SELF) acc_point2(P, G, E, F, ihE, ihF, tau, sig, make_double2(-z.x, -z.y), w, maskA, maskB, S);
     }
 }
 
@@ -451,12 +483,13 @@ __device__ __forceinline__ void acc_pair2(const PhysDev &P, const Rules &G, int 
 __device__ __forceinline__ void acc_pair(const PhysDev &P, const Rules &G, int kind, const Elem &E, const Elem &F,
                                          int p0, int stride, int dir, int maskA, int maskB, PairAcc &S) {
     const int np = pair_points(kind, G.q);
+    const double ihE = 1.0 / E.h, ihF = 1.0 / F.h;
     for (int p = p0; p < np; p += stride) {
         double sig, tau, w;
         double2 z;
         pair_point(G, kind, p, E, F, sig, tau, z, w);
-        acc_point(P, E, F, sig, tau, z, w, dir, maskA, maskB, S);
-        if (kind == PK_SELF) acc_point(P, E, F, tau, sig, make_double2(-z.x, -z.y), w, dir, maskA, maskB, S);
+        acc_point(P, G, E, F, ihE, ihF, sig, tau, z, w, dir, maskA, maskB, S);
+        if (kind == PK_SELF) acc_point(P, G, E, F, ihE, ihF, tau, sig, make_double2(-z.x, -z.y), w, dir, maskA, maskB, S);
     }
 }
 
@@ -590,11 +623,20 @@ static __device__ void tile_eval(const PhysDev &P, TileSmem &S, const double *__
         const int mA = (S.R.pos[re][0] >= 0 ? 1 : 0) | (S.R.pos[re][1] >= 0 ? 2 : 0);
         const int mB = (S.C.pos[ce][0] >= 0 ? 1 : 0) | (S.C.pos[ce][1] >= 0 ? 2 : 0);
         if (dual || diag) {
+#if FDS_DUAL_ONEPASS
             PairAcc2 A;
 #pragma unroll
             for (int k = 0; k < 64; ++k) A.v[k] = 0.0;
             acc_pair2(P, S.G, kind, E, F, 0, 1, mA, mB, A);
             tile_scatter2(S, re, ce, A, 0, 1);
+#else
+            for (int dir = 0; dir < 2; ++dir) {
+                PairAcc A;
+                acc_zero(A);
+                acc_pair(P, S.G, kind, E, F, 0, 1, dir, mA, mB, A);
+                tile_scatter(S, re, ce, A, dir, 0, 1);
+            }
+#endif
             if (d_count_points) atomicAdd(&d_quad_points, 2ull * pair_points(kind, S.G.q) * (kind == PK_SELF ? 2 : 1));
         } else {
             PairAcc A;
@@ -618,6 +660,7 @@ static __device__ void tile_eval(const PhysDev &P, TileSmem &S, const double *__
         // a self pair in a diagonal tile: its transposed entries are forward entries too
         const bool d = diag ? (ie != jf) : dual;
         if (d) {
+#if FDS_DUAL_ONEPASS
             PairAcc2 A;
 #pragma unroll
             for (int k = 0; k < 64; ++k) A.v[k] = 0.0;
@@ -625,6 +668,16 @@ static __device__ void tile_eval(const PhysDev &P, TileSmem &S, const double *__
 #pragma unroll
             for (int k = 0; k < 64; ++k) A.v[k] = wsum(A.v[k]);
             tile_scatter2(S, re, ce, A, lane, 32);
+#else
+            for (int dir = 0; dir < 2; ++dir) {
+                PairAcc A;
+                acc_zero(A);
+                acc_pair(P, S.G, kind, E, F, lane, 32, dir, mA, mB, A);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) A.v[k] = wsum(A.v[k]);
+                tile_scatter(S, re, ce, A, dir, lane, 32);
+            }
+#endif
             if (d_count_points && lane == 0)
                 atomicAdd(&d_quad_points, 2ull * pair_points(kind, S.G.q) * (kind == PK_SELF ? 2 : 1));
         } else {

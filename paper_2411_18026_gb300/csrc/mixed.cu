@@ -1,0 +1,365 @@
+// Mixed-precision solve (FDS_MIXED): the solve sweep of Sec. 6.2-6.3 runs on
+// complex64 copies of the factors and is refined against the compressed
+// operator the factorisation inverts, applied in FP64:
+//
+//   A = D_L + U_L B_L V_L,   B_l = S_{l-1} + U_{l-1} B_{l-1} V_{l-1}  (l > l0+1),
+//   B_{l0+1} = S_{l0} + A_top,off
+//
+// where D_L holds the leaf diagonal blocks A^{J_p J_p} (eq. (block_ax=f)),
+// U_l = V_l^H and V_l are the interpolation matrices of level l (Sec. 7.1),
+// S_l the sibling blocks of the level-l cells (the off-diagonal blocks of
+// eq. (A_rearrangement), original entries between the children's skeletons)
+// and A_top,off the original entries between different top cells (Sec. 6.3).
+// With x_L = x, the apply is
+//   up    x_{l-1} = V_l x_l                        (children -> parent order)
+//   top   y_{l0} = (A_top,off + S_{l0}) x_{l0}     (+ D_L x_L instead of S when l0 = L)
+//   down  y_l = V_l^H y_{l-1}|_l + S_l x_l,  y_L = V_L^H y_{L-1}|_L + D_L x_L.
+// Refinement (per column chunk): x = sweep(f); repeat r = f - A x,
+// x += sweep(r) until max_c ||r_c|| / ||f_c|| <= tol.
+#include <algorithm>
+#include <cmath>
+
+#include "fds_internal.cuh"
+#include "prof.cuh"
+#include "solve.cuh"
+
+namespace {
+
+__global__ void k_to_c64(const cplx *__restrict__ src, cplxf *dst, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = to_c64(src[e]);
+}
+
+__global__ void k_refs(int nb, cplx *base, const int64_t *__restrict__ off, int cols, int64_t ld, MatRef *out) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    out[b].p = base + off[b];
+    out[b].rows = (int)(off[b + 1] - off[b]);
+    out[b].cols = cols;
+    out[b].ld = (int)ld;
+}
+
+// child skeleton vector (R x cols) <-> parent DOF vector (Dp x cols), FP64
+// dir 0: parent[pos] = child;  dir 1: child = parent[pos]
+__global__ void k_child_parent64(int nb, const int64_t *__restrict__ roff, const int *__restrict__ k1,
+                                 const int *__restrict__ pos1, const int *__restrict__ pos2,
+                                 const int64_t *__restrict__ pdoff, cplx *child, int64_t ldc, cplx *parent,
+                                 int64_t ldp, int cols, int dir) {
+    const int b = blockIdx.x;
+    const int64_t o = roff[b];
+    const int r = (int)(roff[b + 1] - o);
+    const int64_t pb = pdoff[b >> 1];
+    const int kk = k1[b], p1 = pos1[b], p2 = pos2[b];
+    for (int64_t e = threadIdx.x; e < (int64_t)r * cols; e += blockDim.x) {
+        const int q = (int)(e % r);
+        const int64_t c = e / r;
+        const int64_t pr = pb + (q < kk ? p1 + q : p2 + (q - kk));
+        if (dir == 0) parent[pr + c * ldp] = child[o + q + c * ldc];
+        else child[o + q + c * ldc] = parent[pr + c * ldp];
+    }
+}
+
+// r = f - y in leaf order (y may be null: r = f), stored as complex64 for the
+// sweep; norms[2c] += |r|^2, norms[2c+1] += |f|^2 over column c.
+__global__ void k_residual(const int *__restrict__ gidx, int64_t D, const cplx *__restrict__ F, int64_t ldf,
+                           const cplx *__restrict__ Y, cplxf *R, double *norms) {
+    const int c = blockIdx.y;
+    double rr = 0.0, ff = 0.0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < D; q += (int64_t)gridDim.x * blockDim.x) {
+        const cplx f = F[gidx[q] + c * ldf];
+        cplx r = f;
+        if (Y) r = csub(f, Y[q + c * D]);
+        R[q + c * D] = to_c64(r);
+        rr += cabs2(r);
+        ff += cabs2(f);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        rr += __shfl_xor_sync(0xffffffffu, rr, o);
+        ff += __shfl_xor_sync(0xffffffffu, ff, o);
+    }
+    __shared__ double sr[32], sf[32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sr[w] = rr; sf[w] = ff; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { a += sr[i]; b += sf[i]; }
+        atomicAdd(&norms[2 * c], a);
+        atomicAdd(&norms[2 * c + 1], b);
+    }
+}
+
+// X (+)= dX (complex64 correction), leaf order
+__global__ void k_update(cplx *X, const cplxf *__restrict__ dX, int64_t n, int set) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const cplx d = to_c128(dX[e]);
+        X[e] = set ? d : cadd(X[e], d);
+    }
+}
+
+// natural-order vector <- leaf-order vector
+__global__ void k_leaf_scatter(const int *__restrict__ gidx, int64_t D, const cplx *__restrict__ X, cplx *out,
+                               int64_t ldo, int cols) {
+    const int64_t tot = D * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = e % D, c = e / D;
+        out[gidx[q] + c * ldo] = X[q + c * D];
+    }
+}
+
+template <class T>
+int grow(DBuf<T> &b, size_t n) {
+    if (b.n >= n && b.p) return FDS_OK;
+    return b.alloc(n);
+}
+
+int convert(const DBuf<cplx> &src, DBuf<cplxf> &dst, cudaStream_t s) {
+    FDS_TRY(dst.alloc(src.n));
+    if (src.n) {
+        fds_count_launch(), k_to_c64<<<1024, 256, 0, s>>>(src.p, dst.p, (int64_t)src.n);
+        FDS_CUDA_TRY(cudaGetLastError());
+    }
+    return FDS_OK;
+}
+
+// Forward-apply workspace: x_l (l0 < l < L), skeleton temporaries, y_l, top.
+int forward_workspace(fds_handle *h, int ncmax) {
+    const int L = h->L, l0 = h->l0;
+    if ((int)h->wz.size() != L + 1) {
+        h->wz = std::vector<DBuf<cplx>>(L + 1);
+        h->wf = std::vector<DBuf<cplx>>(L + 1);
+        h->wt = std::vector<DBuf<cplx>>(L + 1);
+    }
+    if ((int)h->wy.size() != L + 1) h->wy = std::vector<DBuf<cplx>>(L + 1);
+    for (int l = L; l > l0; --l) {
+        const Level &C = h->lv[l];
+        if (l < L) FDS_TRY(grow(h->wz[l], (size_t)C.D * ncmax));
+        FDS_TRY(grow(h->wt[l], (size_t)std::max<int64_t>(C.Rtot, 1) * ncmax));
+        FDS_TRY(grow(h->wy[l], (size_t)C.D * ncmax));
+    }
+    FDS_TRY(grow(h->wtop, (size_t)std::max<int64_t>(h->Dtop, 1) * ncmax));
+    FDS_TRY(grow(h->wytop, (size_t)std::max<int64_t>(h->Dtop, 1) * ncmax));
+    const int maxnb = fds_max_cells(h);
+    if (h->wrefs.n < (size_t)4 * maxnb + 2) FDS_TRY(h->wrefs.alloc((size_t)4 * maxnb + 2));
+    return FDS_OK;
+}
+
+double level_d2(const Level &C) {
+    double s = 0;
+    for (int b = 0; b < C.nb; ++b) {
+        const double d = (double)(C.doff[b + 1] - C.doff[b]);
+        s += d * d;
+    }
+    return s;
+}
+
+// Y = A X for nc leaf-order columns (both D_L x nc, column-major), FP64.
+int forward_apply(fds_handle *h, const cplx *X, cplx *Y, int nc, cudaStream_t s) {
+    const int L = h->L, l0 = h->l0;
+    const int maxnb = fds_max_cells(h);
+    MatRef *rZ = h->wrefs.p, *rT = rZ + maxnb, *rY = rT + maxnb, *rX = rY + maxnb;   // rX: 2 slots
+    const cplx one = mkc(1, 0), zero = mkc(0, 0);
+    ProfScope ps("a7.forward_apply", s);
+    double fl = 0;
+    // up
+    for (int l = L; l > l0; --l) {
+        Level &C = h->lv[l];
+        Level &Pn = h->lv[l - 1];
+        const int nb = C.nb;
+        const int64_t ldr = std::max<int64_t>(C.Rtot, 1);
+        cplx *xl = (l == L) ? (cplx *)X : h->wz[l].p;
+        fds_count_launch(), k_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, xl, C.d_doff.p, nc, C.D, rZ);
+        fds_count_launch(), k_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, h->wt[l].p, C.d_roff.p, nc, ldr, rT);
+        FDS_TRY(dense_gemm(nb, C.rmax, nc, C.rV.p, 0, rZ, 0, rT, one, zero, s));
+        cplx *par = (l - 1 > l0) ? h->wz[l - 1].p : h->wtop.p;
+        const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
+        fds_count_launch(), k_child_parent64<<<nb, 256, 0, s>>>(nb, C.d_roff.p, C.d_k1.p, C.d_par_pos1.p,
+                                                                C.d_par_pos2.p, Pn.d_doff.p, h->wt[l].p, ldr, par,
+                                                                ldp, nc, 0);
+        FDS_CUDA_TRY(cudaGetLastError());
+        fl += 8.0 * C.sum_rd * nc;
+    }
+    // top: off-diagonal blocks between top cells, then the block diagonal
+    {
+        Level &T = h->lv[l0];
+        cplx *xt = (L > l0) ? h->wtop.p : (cplx *)X;
+        cplx *yt = (L > l0) ? h->wytop.p : Y;
+        const int ld = (int)std::max<int64_t>(h->Dtop, 1);
+        MatRef hv[2];
+        hv[0].p = xt; hv[0].rows = (int)h->Dtop; hv[0].cols = nc; hv[0].ld = ld;
+        hv[1].p = yt; hv[1].rows = (int)h->Dtop; hv[1].cols = nc; hv[1].ld = ld;
+        FDS_CUDA_TRY(cudaMemcpyAsync(rX, hv, sizeof(hv), cudaMemcpyHostToDevice, s));
+        FDS_TRY(dense_gemm(1, (int)h->Dtop, nc, h->rtop_off.p, 0, rX, 0, rX + 1, one, zero, s));
+        fl += 8.0 * (double)h->Dtop * h->Dtop * nc;
+        const MatRef *Bd = (L > l0) ? T.rSfw.p : T.rDfw.p;
+        fds_count_launch(), k_refs<<<(T.nb + 127) / 128, 128, 0, s>>>(T.nb, xt, T.d_doff.p, nc, h->Dtop, rZ);
+        fds_count_launch(), k_refs<<<(T.nb + 127) / 128, 128, 0, s>>>(T.nb, yt, T.d_doff.p, nc, h->Dtop, rY);
+        FDS_TRY(dense_gemm(T.nb, T.dmax, nc, Bd, 0, rZ, 0, rY, one, one, s));
+        fl += 8.0 * level_d2(T) * nc;
+    }
+    // down
+    for (int l = l0 + 1; l <= L; ++l) {
+        Level &C = h->lv[l];
+        Level &Pn = h->lv[l - 1];
+        const int nb = C.nb;
+        const int64_t ldr = std::max<int64_t>(C.Rtot, 1);
+        cplx *ypar = (l - 1 > l0) ? h->wy[l - 1].p : h->wytop.p;
+        const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
+        cplx *yl = (l == L) ? Y : h->wy[l].p;
+        cplx *xl = (l == L) ? (cplx *)X : h->wz[l].p;
+        fds_count_launch(), k_child_parent64<<<nb, 256, 0, s>>>(nb, C.d_roff.p, C.d_k1.p, C.d_par_pos1.p,
+                                                                C.d_par_pos2.p, Pn.d_doff.p, h->wt[l].p, ldr, ypar,
+                                                                ldp, nc, 1);
+        fds_count_launch(), k_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, h->wt[l].p, C.d_roff.p, nc, ldr, rT);
+        fds_count_launch(), k_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, yl, C.d_doff.p, nc, C.D, rY);
+        fds_count_launch(), k_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, xl, C.d_doff.p, nc, C.D, rZ);
+        FDS_CUDA_TRY(cudaGetLastError());
+        FDS_TRY(dense_gemm(nb, C.dmax, nc, C.rV.p, 2, rT, 0, rY, one, zero, s));
+        const MatRef *Bd = (l == L) ? C.rDfw.p : C.rSfw.p;
+        FDS_TRY(dense_gemm(nb, C.dmax, nc, Bd, 0, rZ, 0, rY, one, one, s));
+        fl += 8.0 * (C.sum_rd + level_d2(C)) * nc;
+    }
+    ps.flops = fl;
+    return FDS_OK;
+}
+
+}  // namespace
+
+int fds_keep_blocks(const Level &Lv, DBuf<cplx> &dst, DBuf<MatRef> &rdst, cudaStream_t s) {
+    const int64_t n = Lv.offA.empty() ? 0 : Lv.offA[Lv.nb];
+    FDS_TRY(dst.alloc((size_t)n));
+    if (n) FDS_CUDA_TRY(cudaMemcpyAsync(dst.p, Lv.LU.p, sizeof(cplx) * n, cudaMemcpyDeviceToDevice, s));
+    std::vector<int> d(Lv.nb);
+    for (int b = 0; b < Lv.nb; ++b) d[b] = Lv.n1[b] + Lv.n2[b];
+    return make_refs_t(rdst, dst.p, Lv.offA, d, d, s);
+}
+
+int fds_mixed_prepare(fds_handle *h) {
+    cudaStream_t s = h->stream;
+    const int L = h->L, l0 = h->l0;
+    int64_t bytes = 0;
+    for (int l = L; l > l0; --l) {
+        Level &C = h->lv[l];
+        std::vector<int> dv(C.nb), rv(C.nb);
+        for (int b = 0; b < C.nb; ++b) {
+            dv[b] = C.n1[b] + C.n2[b];
+            rv[b] = C.k1[b] + C.k2[b];
+        }
+        FDS_TRY(convert(C.LU, C.LUf, s));
+        FDS_TRY(convert(C.W, C.Wf, s));
+        FDS_TRY(convert(C.At, C.Atf, s));
+        FDS_TRY(convert(C.V, C.Vf, s));
+        FDS_TRY(make_refs_t(C.rLUf, C.LUf.p, C.offA, dv, dv, s));
+        FDS_TRY(make_refs_t(C.rWf, C.Wf.p, C.offW, dv, rv, s));
+        FDS_TRY(make_refs_t(C.rAtf, C.Atf.p, C.offAt, rv, rv, s));
+        FDS_TRY(make_refs_t(C.rVf, C.Vf.p, C.offV, rv, dv, s));
+        bytes += (int64_t)(C.LUf.bytes() + C.Wf.bytes() + C.Atf.bytes() + C.Vf.bytes() + C.piv.bytes() +
+                           C.V.bytes() + C.Dfw.bytes() + C.Sfw.bytes());
+    }
+    bytes += (int64_t)h->lv[l0].Sfw.bytes() + (int64_t)h->lv[l0].Dfw.bytes();
+    FDS_TRY(convert(h->Atop, h->Atopf, s));
+    {
+        MatRefF t;
+        t.p = h->Atopf.p;
+        t.rows = t.cols = (int)h->Dtop;
+        t.ld = (int)std::max<int64_t>(h->Dtop, 1);
+        std::vector<MatRefF> ht = {t};
+        FDS_TRY(h->rtopf.upload(ht, s));
+    }
+    bytes += (int64_t)(h->Atopf.bytes() + h->ptop.bytes() + h->Atop_off.bytes());
+    FDS_CUDA_TRY(cudaStreamSynchronize(s));
+    // the FP64 sweep factors are not used by the mixed solve
+    for (int l = L; l > l0; --l) {
+        Level &C = h->lv[l];
+        C.LU.release();
+        C.rLU.release();
+        C.W.release();
+        C.rW.release();
+        C.At.release();
+        C.rAt.release();
+    }
+    h->Atop.release();
+    h->rtop.release();
+    h->factor_bytes = bytes;
+    return FDS_OK;
+}
+
+int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
+    const int N = h->N, L = h->L;
+    const int64_t ld_rhs = 2LL * N;
+    const int ncmax = std::min(nrhs, SOLVE_CHUNK);
+    const Level &Lf = h->lv[L];
+    const int64_t D = Lf.D;
+    FDS_TRY(sweep_workspace<cplxf>(h, ncmax));
+    const bool refine = h->opt.ir_max_iter > 0;
+    if (refine) FDS_TRY(forward_workspace(h, ncmax));
+    FDS_TRY(grow(h->wX, (size_t)D * ncmax));
+    if (h->wnorm.n < (size_t)2 * ncmax) FDS_TRY(h->wnorm.alloc((size_t)2 * ncmax));
+    cplxf *leaf = sweep_leaf_vector<cplxf>(h);
+    cplx *Yleaf = refine ? ((L > h->l0) ? h->wy[L].p : h->wytop.p) : nullptr;
+    std::vector<double> nrm(2 * ncmax);
+    int iters = 0;
+    double worst = refine ? 0.0 : -1.0;
+    bool converged = true;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    for (int c0 = 0; c0 < nrhs; c0 += SOLVE_CHUNK) {
+        const int nc = std::min(SOLVE_CHUNK, nrhs - c0);
+        cplx *F = d_rhs + (int64_t)c0 * ld_rhs;
+        const unsigned gx = (unsigned)std::min<int64_t>((D + 255) / 256, 64);
+        // x = sweep(f)
+        FDS_CUDA_TRY(cudaMemsetAsync(h->wnorm.p, 0, sizeof(double) * 2 * nc, s));
+        {
+            ProfScope ps("a7.residual", s);
+            fds_count_launch(), k_residual<<<dim3(gx, nc), 256, 0, s>>>(h->d_leaf_gidx.p, D, F, ld_rhs, nullptr,
+                                                                        leaf, h->wnorm.p);
+        }
+        FDS_CUDA_TRY(cudaGetLastError());
+        FDS_TRY(sweep_chunk<cplxf>(h, nc, s));
+        fds_count_launch(), k_update<<<1024, 256, 0, s>>>(h->wX.p, leaf, D * nc, 1);
+        FDS_CUDA_TRY(cudaGetLastError());
+        // refinement against the FP64 compressed operator
+        double prev = INFINITY;
+        for (int it = 0; refine; ++it) {
+            FDS_TRY(forward_apply(h, h->wX.p, Yleaf, nc, s));
+            FDS_CUDA_TRY(cudaMemsetAsync(h->wnorm.p, 0, sizeof(double) * 2 * nc, s));
+            {
+                ProfScope ps("a7.residual", s);
+                fds_count_launch(), k_residual<<<dim3(gx, nc), 256, 0, s>>>(h->d_leaf_gidx.p, D, F, ld_rhs, Yleaf,
+                                                                            leaf, h->wnorm.p);
+            }
+            FDS_CUDA_TRY(cudaGetLastError());
+            FDS_CUDA_TRY(cudaMemcpyAsync(nrm.data(), h->wnorm.p, sizeof(double) * 2 * nc, cudaMemcpyDeviceToHost, s));
+            FDS_CUDA_TRY(cudaStreamSynchronize(s));
+            double res = 0;
+            for (int c = 0; c < nc; ++c)
+                if (nrm[2 * c + 1] > 0) res = std::max(res, std::sqrt(nrm[2 * c] / nrm[2 * c + 1]));
+            if (!(res == res)) return FDS_ERR_SINGULAR;
+            // stop when converged, out of sweeps, or no longer contracting
+            if (res <= h->opt.ir_tol || it >= h->opt.ir_max_iter || res > 0.5 * prev) {
+                worst = std::max(worst, res);
+                if (res > h->opt.ir_tol) converged = false;
+                iters = std::max(iters, it);
+                break;
+            }
+            prev = res;
+            FDS_TRY(sweep_chunk<cplxf>(h, nc, s));
+            fds_count_launch(), k_update<<<1024, 256, 0, s>>>(h->wX.p, leaf, D * nc, 0);
+            FDS_CUDA_TRY(cudaGetLastError());
+        }
+        fds_count_launch(), k_leaf_scatter<<<1024, 256, 0, s>>>(h->d_leaf_gidx.p, D, h->wX.p, F, ld_rhs, nc);
+        FDS_CUDA_TRY(cudaGetLastError());
+    }
+    cudaEventRecord(e1, s);
+    FDS_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    h->solve_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->ir_iters = iters;
+    h->ir_residual = worst;
+    return converged ? FDS_OK : FDS_ERR_NOT_CONVERGED;
+}

@@ -5,17 +5,19 @@
 //   down  y_i from the parent x (eqs. (xtoy1)-(xtoy2)),
 //         x_i = z_i - W_i (f~_i - A~_i y_i) with W_i = A_i^{-1} U_i   (eq. (down_comv))
 // Right-hand sides are processed in column chunks; all arithmetic in the
-// batched kernels of dense.cu and the gathers below.
+// batched kernels of dense.cu and the gathers below.  The sweep is written
+// once for complex128 factors (FDS_FP64) and complex64 copies (FDS_MIXED).
 #include <algorithm>
 
 #include "fds_internal.cuh"
 #include "prof.cuh"
+#include "solve.cuh"
 
 namespace {
 
-constexpr int CHUNK = 256;
-
-__global__ void k_vec_refs(int nb, cplx *base, const int64_t *__restrict__ off, int cols, int64_t ld, MatRef *out) {
+template <class C>
+__global__ void k_vec_refs(int nb, C *base, const int64_t *__restrict__ off, int cols, int64_t ld,
+                           MatRefT<C> *out) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     out[b].p = base + off[b];
@@ -25,8 +27,8 @@ __global__ void k_vec_refs(int nb, cplx *base, const int64_t *__restrict__ off, 
 }
 
 // leaf vector <- global natural-order vector (gather) or back (scatter)
-__global__ void k_leaf_gather(const int *__restrict__ gidx, int64_t D, int N, const cplx *__restrict__ src,
-                              int64_t lds, cplx *dst, int cols, int dir) {
+__global__ void k_leaf_gather(const int *__restrict__ gidx, int64_t D, const cplx *__restrict__ src, int64_t lds,
+                              cplx *dst, int cols, int dir) {
     const int64_t tot = D * cols;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = e % D, c = e / D;
@@ -39,10 +41,11 @@ __global__ void k_leaf_gather(const int *__restrict__ gidx, int64_t D, int N, co
 // child skeleton vector (R x cols) <-> parent DOF vector (Dp x cols)
 // dir 0: parent[pos] = child  (upward scatter of f~)
 // dir 1: child = parent[pos]  (downward gather of y)
+template <class C>
 __global__ void k_child_parent(int nb, const int64_t *__restrict__ roff, const int *__restrict__ k1,
                                const int *__restrict__ pos1, const int *__restrict__ pos2,
-                               const int64_t *__restrict__ pdoff, cplx *child, int64_t ldc, cplx *parent,
-                               int64_t ldp, int cols, int dir) {
+                               const int64_t *__restrict__ pdoff, C *child, int64_t ldc, C *parent, int64_t ldp,
+                               int cols, int dir) {
     const int b = blockIdx.x;
     const int64_t o = roff[b];
     const int r = (int)(roff[b + 1] - o);
@@ -57,113 +60,189 @@ __global__ void k_child_parent(int nb, const int64_t *__restrict__ roff, const i
     }
 }
 
-int grow(DBuf<cplx> &b, size_t n) {
+template <class T>
+int grow(DBuf<T> &b, size_t n) {
     if (b.n >= n && b.p) return FDS_OK;
     return b.alloc(n);
 }
 
+// Factor and workspace views of one precision.
+template <class C>
+struct View;
+
+template <>
+struct View<cplx> {
+    static const MatRef *LU(const Level &v) { return v.rLU.p; }
+    static const MatRef *W(const Level &v) { return v.rW.p; }
+    static const MatRef *At(const Level &v) { return v.rAt.p; }
+    static const MatRef *V(const Level &v) { return v.rV.p; }
+    static const MatRef *top(const fds_handle *h) { return h->rtop.p; }
+    static std::vector<DBuf<cplx>> &z(fds_handle *h) { return h->wz; }
+    static std::vector<DBuf<cplx>> &f(fds_handle *h) { return h->wf; }
+    static std::vector<DBuf<cplx>> &t(fds_handle *h) { return h->wt; }
+    static DBuf<cplx> &wtop(fds_handle *h) { return h->wtop; }
+    static DBuf<MatRef> &refs(fds_handle *h) { return h->wrefs; }
+    static cplx one() { return mkc(1, 0); }
+};
+
+template <>
+struct View<cplxf> {
+    static const MatRefF *LU(const Level &v) { return v.rLUf.p; }
+    static const MatRefF *W(const Level &v) { return v.rWf.p; }
+    static const MatRefF *At(const Level &v) { return v.rAtf.p; }
+    static const MatRefF *V(const Level &v) { return v.rVf.p; }
+    static const MatRefF *top(const fds_handle *h) { return h->rtopf.p; }
+    static std::vector<DBuf<cplxf>> &z(fds_handle *h) { return h->wzf; }
+    static std::vector<DBuf<cplxf>> &f(fds_handle *h) { return h->wff; }
+    static std::vector<DBuf<cplxf>> &t(fds_handle *h) { return h->wtf; }
+    static DBuf<cplxf> &wtop(fds_handle *h) { return h->wtopf; }
+    static DBuf<MatRefF> &refs(fds_handle *h) { return h->wrefsf; }
+    static cplxf one() { return mkcf(1, 0); }
+};
+
 }  // namespace
+
+int fds_max_cells(const fds_handle *h) {
+    int m = 1;
+    for (int l = h->L; l >= h->l0; --l) m = std::max(m, h->lv[l].nb);
+    return m;
+}
+
+template <class C>
+int sweep_workspace(fds_handle *h, int ncmax) {
+    typedef View<C> Vw;
+    const int L = h->L, l0 = h->l0;
+    auto &wz = Vw::z(h), &wf = Vw::f(h), &wt = Vw::t(h);
+    if ((int)wz.size() != L + 1) {
+        wz = std::vector<DBuf<C>>(L + 1);
+        wf = std::vector<DBuf<C>>(L + 1);
+        wt = std::vector<DBuf<C>>(L + 1);
+    }
+    for (int l = L; l > l0; --l) {
+        Level &Cv = h->lv[l];
+        FDS_TRY(grow(wz[l], (size_t)Cv.D * ncmax));
+        FDS_TRY(grow(wf[l], (size_t)std::max<int64_t>(Cv.Rtot, 1) * ncmax));
+        FDS_TRY(grow(wt[l], (size_t)std::max<int64_t>(Cv.Rtot, 1) * ncmax));
+    }
+    FDS_TRY(grow(Vw::wtop(h), (size_t)std::max<int64_t>(h->Dtop, 1) * ncmax));
+    const int maxnb = fds_max_cells(h);
+    if (Vw::refs(h).n < (size_t)4 * maxnb) FDS_TRY(Vw::refs(h).alloc((size_t)4 * maxnb));
+    return FDS_OK;
+}
+
+template <class C>
+C *sweep_leaf_vector(fds_handle *h) {
+    return (h->L > h->l0) ? View<C>::z(h)[h->L].p : View<C>::wtop(h).p;
+}
+
+template <class C>
+int sweep_chunk(fds_handle *h, int nc, cudaStream_t s) {
+    typedef View<C> Vw;
+    const int L = h->L, l0 = h->l0;
+    const C one = Vw::one(), zero = czero<C>();
+    C mone = one;
+    mone.x = -mone.x;
+    const int maxnb = fds_max_cells(h);
+    MatRefT<C> *rZ = Vw::refs(h).p, *rF = rZ + maxnb, *rT = rF + maxnb, *rX = rT + maxnb;
+    auto &wz = Vw::z(h), &wf = Vw::f(h), &wt = Vw::t(h);
+    C *top = Vw::wtop(h).p;
+    const double esz = sizeof(C);
+    // upward
+    for (int l = L; l > l0; --l) {
+        Level &Cv = h->lv[l];
+        Level &Pn = h->lv[l - 1];
+        const int nb = Cv.nb;
+        const int64_t ldr = std::max<int64_t>(Cv.Rtot, 1);
+        C *Z = wz[l].p, *F = wf[l].p, *U = wt[l].p;
+        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, Z, Cv.d_doff.p, nc, Cv.D, rZ);
+        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, U, Cv.d_roff.p, nc, ldr, rT);
+        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, F, Cv.d_roff.p, nc, ldr, rF);
+        {
+            ProfScope ps("a6.up_lu_solve", s);
+            ps.flops = 8.0 * Cv.sum_d2 * nc;
+            ps.bytes = esz * Cv.sum_d2 + 2 * esz * Cv.D * nc;
+            FDS_TRY(dense_lu_solve(nb, Cv.dmax, nc, Vw::LU(Cv), Cv.piv.p, Cv.d_offpiv.p, rZ, s));
+        }
+        {
+            ProfScope ps("a6.up_apply", s);
+            ps.flops = 8.0 * (Cv.sum_rd + Cv.sum_r2) * nc;
+            ps.bytes = esz * (Cv.sum_rd + Cv.sum_r2) + esz * (Cv.D + 2.0 * Cv.Rtot) * nc;
+            FDS_TRY(dense_gemm(nb, Cv.rmax, nc, Vw::V(Cv), 0, rZ, 0, rT, one, zero, s));
+            FDS_TRY(dense_gemm(nb, Cv.rmax, nc, Vw::At(Cv), 0, rT, 0, rF, one, zero, s));
+        }
+        C *par = (l - 1 > l0) ? wz[l - 1].p : top;
+        const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
+        fds_count_launch(), k_child_parent<C><<<nb, 256, 0, s>>>(nb, Cv.d_roff.p, Cv.d_k1.p, Cv.d_par_pos1.p,
+                                                                 Cv.d_par_pos2.p, Pn.d_doff.p, F, ldr, par, ldp,
+                                                                 nc, 0);
+        FDS_CUDA_TRY(cudaGetLastError());
+    }
+    // top
+    {
+        MatRefT<C> tv;
+        tv.p = top;
+        tv.rows = (int)h->Dtop;
+        tv.cols = nc;
+        tv.ld = (int)std::max<int64_t>(h->Dtop, 1);
+        FDS_CUDA_TRY(cudaMemcpyAsync(rX, &tv, sizeof(tv), cudaMemcpyHostToDevice, s));
+        ProfScope ps("a6.top_solve", s);
+        ps.flops = 8.0 * (double)h->Dtop * h->Dtop * nc;
+        ps.bytes = esz * (double)h->Dtop * h->Dtop;
+        FDS_TRY(dense_lu_solve(1, (int)h->Dtop, nc, Vw::top(h), h->ptop.p, h->d_ptop_off.p, rX, s));
+    }
+    // downward
+    for (int l = l0 + 1; l <= L; ++l) {
+        Level &Cv = h->lv[l];
+        Level &Pn = h->lv[l - 1];
+        const int nb = Cv.nb;
+        C *Z = wz[l].p, *F = wf[l].p, *Y = wt[l].p;
+        C *par = (l - 1 > l0) ? wz[l - 1].p : top;
+        const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
+        const int64_t ldr = std::max<int64_t>(Cv.Rtot, 1);
+        fds_count_launch(), k_child_parent<C><<<nb, 256, 0, s>>>(nb, Cv.d_roff.p, Cv.d_k1.p, Cv.d_par_pos1.p,
+                                                                 Cv.d_par_pos2.p, Pn.d_doff.p, Y, ldr, par, ldp,
+                                                                 nc, 1);
+        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, Z, Cv.d_doff.p, nc, Cv.D, rZ);
+        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, Y, Cv.d_roff.p, nc, ldr, rT);
+        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, F, Cv.d_roff.p, nc, ldr, rF);
+        FDS_CUDA_TRY(cudaGetLastError());
+        // F <- f~ - A~ y ;  Z <- z - W F
+        ProfScope ps("a6.down_apply", s);
+        ps.flops = 8.0 * (Cv.sum_r2 + Cv.sum_rd) * nc;
+        ps.bytes = esz * (Cv.sum_r2 + Cv.sum_rd) + esz * (2.0 * Cv.D + 2.0 * Cv.Rtot) * nc;
+        FDS_TRY(dense_gemm(nb, Cv.rmax, nc, Vw::At(Cv), 0, rT, 0, rF, mone, one, s));
+        FDS_TRY(dense_gemm(nb, Cv.dmax, nc, Vw::W(Cv), 0, rF, 0, rZ, mone, one, s));
+    }
+    return FDS_OK;
+}
+
+template int sweep_workspace<cplx>(fds_handle *, int);
+template int sweep_workspace<cplxf>(fds_handle *, int);
+template cplx *sweep_leaf_vector<cplx>(fds_handle *);
+template cplxf *sweep_leaf_vector<cplxf>(fds_handle *);
+template int sweep_chunk<cplx>(fds_handle *, int, cudaStream_t);
+template int sweep_chunk<cplxf>(fds_handle *, int, cudaStream_t);
 
 int fds_solve_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
     if (nrhs <= 0) return FDS_OK;
-    const int L = h->L, l0 = h->l0, N = h->N;
+    if (h->opt.precision == FDS_MIXED) return fds_solve_mixed_impl(h, d_rhs, nrhs, s);
+    const int N = h->N;
     const int64_t ld_rhs = 2LL * N;
-    const int ncmax = std::min(nrhs, CHUNK);
-    // workspace
-    if ((int)h->wz.size() != L + 1) {
-        h->wz = std::vector<DBuf<cplx>>(L + 1);
-        h->wf = std::vector<DBuf<cplx>>(L + 1);
-        h->wt = std::vector<DBuf<cplx>>(L + 1);
-    }
-    for (int l = L; l > l0; --l) {
-        Level &C = h->lv[l];
-        FDS_TRY(grow(h->wz[l], (size_t)C.D * ncmax));
-        FDS_TRY(grow(h->wf[l], (size_t)std::max<int64_t>(C.Rtot, 1) * ncmax));
-        FDS_TRY(grow(h->wt[l], (size_t)std::max<int64_t>(C.Rtot, 1) * ncmax));
-    }
-    FDS_TRY(grow(h->wtop, (size_t)h->Dtop * ncmax));
-    int maxnb = 1;
-    for (int l = L; l >= l0; --l) maxnb = std::max(maxnb, h->lv[l].nb);
-    if (h->wrefs.n < (size_t)4 * maxnb) FDS_TRY(h->wrefs.alloc((size_t)4 * maxnb));
-    MatRef *rZ = h->wrefs.p, *rF = rZ + maxnb, *rT = rF + maxnb, *rX = rT + maxnb;
-
+    const int ncmax = std::min(nrhs, SOLVE_CHUNK);
+    FDS_TRY(sweep_workspace<cplx>(h, ncmax));
+    const Level &Lf = h->lv[h->L];
+    cplx *leafv = sweep_leaf_vector<cplx>(h);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
-    for (int c0 = 0; c0 < nrhs; c0 += CHUNK) {
-        const int nc = std::min(CHUNK, nrhs - c0);
+    for (int c0 = 0; c0 < nrhs; c0 += SOLVE_CHUNK) {
+        const int nc = std::min(SOLVE_CHUNK, nrhs - c0);
         cplx *rhs = d_rhs + (int64_t)c0 * ld_rhs;
-        // leaf gather
-        Level &Lf = h->lv[L];
-        cplx *leafv = (L > l0) ? h->wz[L].p : h->wtop.p;
-        fds_count_launch(), k_leaf_gather<<<1024, 256, 0, s>>>(h->d_leaf_gidx.p, Lf.D, N, rhs, ld_rhs, leafv, nc, 0);
+        fds_count_launch(), k_leaf_gather<<<1024, 256, 0, s>>>(h->d_leaf_gidx.p, Lf.D, rhs, ld_rhs, leafv, nc, 0);
         FDS_CUDA_TRY(cudaGetLastError());
-        // upward
-        for (int l = L; l > l0; --l) {
-            Level &C = h->lv[l];
-            Level &Pn = h->lv[l - 1];
-            const int nb = C.nb;
-            cplx *Z = h->wz[l].p, *F = h->wf[l].p, *U = h->wt[l].p;
-            fds_count_launch(), k_vec_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, Z, C.d_doff.p, nc, C.D, rZ);
-            fds_count_launch(), k_vec_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, U, C.d_roff.p, nc, std::max<int64_t>(C.Rtot, 1), rT);
-            fds_count_launch(), k_vec_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, F, C.d_roff.p, nc, std::max<int64_t>(C.Rtot, 1), rF);
-            {
-                ProfScope ps("a6.up_lu_solve", s);
-                ps.flops = 8.0 * C.sum_d2 * nc;
-                ps.bytes = 16.0 * C.sum_d2 + 32.0 * C.D * nc;
-                FDS_TRY(dense_lu_solve(nb, C.dmax, nc, C.rLU.p, C.piv.p, C.d_offpiv.p, rZ, s));
-            }
-            {
-                ProfScope ps("a6.up_apply", s);
-                ps.flops = 8.0 * (C.sum_rd + C.sum_r2) * nc;
-                ps.bytes = 16.0 * (C.sum_rd + C.sum_r2) + 16.0 * (C.D + 2.0 * C.Rtot) * nc;
-                FDS_TRY(dense_gemm(nb, C.rmax, nc, C.rV.p, 0, rZ, 0, rT, mkc(1, 0), mkc(0, 0), s));
-                FDS_TRY(dense_gemm(nb, C.rmax, nc, C.rAt.p, 0, rT, 0, rF, mkc(1, 0), mkc(0, 0), s));
-            }
-            cplx *par = (l - 1 > l0) ? h->wz[l - 1].p : h->wtop.p;
-            const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
-            fds_count_launch(), k_child_parent<<<nb, 256, 0, s>>>(nb, C.d_roff.p, C.d_k1.p, C.d_par_pos1.p, C.d_par_pos2.p, Pn.d_doff.p, F,
-                                              std::max<int64_t>(C.Rtot, 1), par, ldp, nc, 0);
-            FDS_CUDA_TRY(cudaGetLastError());
-        }
-        // top
-        {
-            MatRef tv;
-            tv.p = h->wtop.p;
-            tv.rows = (int)h->Dtop;
-            tv.cols = nc;
-            tv.ld = (int)std::max<int64_t>(h->Dtop, 1);
-            FDS_CUDA_TRY(cudaMemcpyAsync(rX, &tv, sizeof(MatRef), cudaMemcpyHostToDevice, s));
-            ProfScope ps("a6.top_solve", s);
-            ps.flops = 8.0 * (double)h->Dtop * h->Dtop * nc;
-            ps.bytes = 16.0 * (double)h->Dtop * h->Dtop;
-            FDS_TRY(dense_lu_solve(1, (int)h->Dtop, nc, h->rtop.p, h->ptop.p, h->d_ptop_off.p, rX, s));
-        }
-        // downward
-        for (int l = l0 + 1; l <= L; ++l) {
-            Level &C = h->lv[l];
-            Level &Pn = h->lv[l - 1];
-            const int nb = C.nb;
-            cplx *Z = h->wz[l].p, *F = h->wf[l].p, *Y = h->wt[l].p;
-            cplx *par = (l - 1 > l0) ? h->wz[l - 1].p : h->wtop.p;
-            const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
-            const int64_t ldr = std::max<int64_t>(C.Rtot, 1);
-            fds_count_launch(), k_child_parent<<<nb, 256, 0, s>>>(nb, C.d_roff.p, C.d_k1.p, C.d_par_pos1.p, C.d_par_pos2.p, Pn.d_doff.p, Y,
-                                              ldr, par, ldp, nc, 1);
-            fds_count_launch(), k_vec_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, Z, C.d_doff.p, nc, C.D, rZ);
-            fds_count_launch(), k_vec_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, Y, C.d_roff.p, nc, ldr, rT);
-            fds_count_launch(), k_vec_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, F, C.d_roff.p, nc, ldr, rF);
-            FDS_CUDA_TRY(cudaGetLastError());
-            // F <- f~ - A~ y ;  Z <- z - W F
-            ProfScope ps("a6.down_apply", s);
-            ps.flops = 8.0 * (C.sum_r2 + C.sum_rd) * nc;
-            ps.bytes = 16.0 * (C.sum_r2 + C.sum_rd) + 16.0 * (2.0 * C.D + 2.0 * C.Rtot) * nc;
-            FDS_TRY(dense_gemm(nb, C.rmax, nc, C.rAt.p, 0, rT, 0, rF, mkc(-1, 0), mkc(1, 0), s));
-            FDS_TRY(dense_gemm(nb, C.dmax, nc, C.rW.p, 0, rF, 0, rZ, mkc(-1, 0), mkc(1, 0), s));
-        }
-        cplx *leafx = (L > l0) ? h->wz[L].p : h->wtop.p;
-        fds_count_launch(), k_leaf_gather<<<1024, 256, 0, s>>>(h->d_leaf_gidx.p, Lf.D, N, rhs, ld_rhs, leafx, nc, 1);
+        FDS_TRY(sweep_chunk<cplx>(h, nc, s));
+        fds_count_launch(), k_leaf_gather<<<1024, 256, 0, s>>>(h->d_leaf_gidx.p, Lf.D, rhs, ld_rhs, leafv, nc, 1);
         FDS_CUDA_TRY(cudaGetLastError());
     }
     cudaEventRecord(e1, s);

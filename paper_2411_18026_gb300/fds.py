@@ -23,6 +23,7 @@ FDS_ERR_NOT_CONVERGED = -5
 FDS_ERR_TIMEOUT = -6
 FDS_ERR_STATE = -7
 FDS_FP64 = 0
+FDS_MIXED = 1
 
 
 class FdsError(RuntimeError):
@@ -45,14 +46,15 @@ class fds_options(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int32), ("proxy_ratio", ctypes.c_double),
                 ("proxy_points", ctypes.c_int32), ("top_level", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("alpha_re", ctypes.c_double), ("alpha_im", ctypes.c_double),
-                ("alpha_set", ctypes.c_int32), ("cuda_stream", ctypes.c_uint64)]
+                ("alpha_set", ctypes.c_int32), ("cuda_stream", ctypes.c_uint64), ("ir_tol", ctypes.c_double),
+                ("ir_max_iter", ctypes.c_int32)]
 
 
 class fds_stats(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("levels", ctypes.c_int32), ("top_level", ctypes.c_int32),
                 ("top_size", ctypes.c_int32), ("skeleton_dofs", ctypes.c_int64 * 32),
                 ("max_rank", ctypes.c_int32 * 32), ("build_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
-                ("factor_bytes", ctypes.c_int64)]
+                ("factor_bytes", ctypes.c_int64), ("ir_iters", ctypes.c_int32), ("ir_residual", ctypes.c_double)]
 
 
 _lib = None
@@ -161,7 +163,7 @@ class Handle:
 
 
 def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy_ratio=1.5, proxy_points=64,
-              alpha=None, stream=0):
+              alpha=None, stream=0, precision=FDS_FP64, ir_tol=None, ir_max_iter=None):
     xy = np.ascontiguousarray(xy, dtype=np.float64)
     g = fds_geometry(len(xy), xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(rho))
     o = default_options()
@@ -169,6 +171,11 @@ def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy
     if alpha is not None:
         o.alpha_re, o.alpha_im, o.alpha_set = float(np.real(alpha)), float(np.imag(alpha)), 1
     o.cuda_stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    o.precision = precision
+    if ir_tol is not None:
+        o.ir_tol = ir_tol
+    if ir_max_iter is not None:
+        o.ir_max_iter = ir_max_iter
     out = ctypes.c_void_p()
     _check(lib().fds_build_ex(ctypes.byref(g), float(omega), float(lam), float(mu), float(tol), ctypes.byref(o),
                               ctypes.byref(out)), "fds_build")

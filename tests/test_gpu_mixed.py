@@ -1,0 +1,132 @@
+"""Mixed-precision solve (complex64 sweep + refinement against the FP64
+compressed operator) against the FP64 GPU solve and the oracle's dense
+Galerkin solve."""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_util import fdslib, torch_cuda
+from oracle import bem
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _colmax(a, b):
+    return max(np.linalg.norm(a[:, c] - b[:, c]) / np.linalg.norm(b[:, c]) for c in range(b.shape[1]))
+
+
+def _pair(fds, xy, omega, eps, **kw):
+    h64 = fds.fds_build(xy, omega, 2.0, 1.0, eps, **kw)
+    hmx = fds.fds_build(xy, omega, 2.0, 1.0, eps, precision=fds.FDS_MIXED, **kw)
+    return h64, hmx
+
+
+def test_mixed_matches_fp64_and_dense():
+    # star r = 1 + 0.2 cos 5t, 1024 nodes, k_T a = 10, leaf 32, eps 1e-9;
+    # plane P and SV waves at several angles
+    torch_cuda()
+    fds = fdslib()
+    N, eps = 1024, 1e-9
+    xy = workloads.star(N)
+    omega = workloads.omega_for_kTa(10.0)
+    h64, hmx = _pair(fds, xy, omega, eps, leaf_size=32, top_level=1)
+    kinds = np.array([0, 1, 0, 1, 0], np.int32)
+    ang = np.array([0.0, 0.7, 1.9, 3.0, 5.1])
+    F = fds.fds_rhs_plane_wave(h64, kinds, ang)
+    x64 = fds.fds_solve(h64, F)
+    xmx = fds.fds_solve(hmx, F)
+    st = fds.fds_stats_get(hmx)
+    assert 1 <= st.ir_iters <= 4
+    assert 0 <= st.ir_residual <= 1e-9
+    # refinement reaches the FP64 solution of the same compressed operator
+    assert _colmax(xmx, x64) < 1e-7
+    P = bem.phys(2.0, 1.0, 1.0, omega)
+    xd = np.linalg.solve(bem.dense_matrix(P, xy), F)
+    assert _rel(xmx, xd) <= 1e-7
+    h64.close()
+    hmx.close()
+
+
+def test_refinement_gains_over_plain_complex64_sweep():
+    torch_cuda()
+    fds = fdslib()
+    xy = workloads.star(768)
+    omega = workloads.omega_for_kTa(8.0)
+    h64 = fds.fds_build(xy, omega, 2.0, 1.0, 1e-10, leaf_size=32)
+    h0 = fds.fds_build(xy, omega, 2.0, 1.0, 1e-10, leaf_size=32, precision=fds.FDS_MIXED, ir_max_iter=0)
+    h2 = fds.fds_build(xy, omega, 2.0, 1.0, 1e-10, leaf_size=32, precision=fds.FDS_MIXED, ir_tol=1e-13,
+                       ir_max_iter=6)
+    F = fds.fds_rhs_plane_wave(h64, np.array([0, 1], np.int32), np.array([0.4, 2.2]))
+    x64 = fds.fds_solve(h64, F)
+    e0 = _colmax(fds.fds_solve(h0, F), x64)
+    e2 = _colmax(fds.fds_solve(h2, F), x64)
+    assert fds.fds_stats_get(h0).ir_iters == 0
+    assert fds.fds_stats_get(h0).ir_residual < 0          # not measured without refinement
+    assert 1e-9 < e0 < 1e-3                               # complex64 sweep alone
+    assert e2 < 1e-11 and e2 < 1e-4 * e0
+    for h in (h64, h0, h2):
+        h.close()
+
+
+@pytest.mark.parametrize("l0", [0, 1, 2])
+def test_mixed_exact_without_truncation(l0):
+    # eps = 0: the compressed operator is A itself, so refinement converges
+    # to the dense solve
+    torch_cuda()
+    fds = fdslib()
+    xy = workloads.star(256)
+    h = fds.fds_build(xy, 3.0, 2.0, 1.0, 0.0, leaf_size=32, top_level=l0, precision=fds.FDS_MIXED,
+                      ir_tol=1e-13, ir_max_iter=8)
+    P = bem.phys(2.0, 1.0, 1.0, 3.0)
+    F = np.stack([bem.rhs(P, xy, 0, 0.3), bem.rhs(P, xy, 1, 1.9)], 1)
+    xd = np.linalg.solve(bem.dense_matrix(P, xy), F)
+    assert _rel(fds.fds_solve(h, F), xd) < 1e-11
+    h.close()
+
+
+def test_mixed_single_cell():
+    # one cell: the compressed operator is the top matrix itself
+    torch_cuda()
+    fds = fdslib()
+    xy = workloads.ellipse(40, 2.0, 0.3)
+    h = fds.fds_build(xy, 2.0, 2.0, 1.0, 1e-8, leaf_size=64, precision=fds.FDS_MIXED, ir_tol=1e-13)
+    assert fds.fds_stats_get(h).levels == 0
+    P = bem.phys(2.0, 1.0, 1.0, 2.0)
+    f = bem.rhs(P, xy, 1, 0.25)
+    xd = np.linalg.solve(bem.dense_matrix(P, xy), f)
+    assert _rel(fds.fds_solve(h, f), xd) < 1e-11
+    h.close()
+
+
+def test_mixed_many_rhs_ragged_chunks():
+    # 300 right-hand sides: one full 256-column chunk and a ragged one
+    torch_cuda()
+    fds = fdslib()
+    xy = workloads.ellipse(512, 1.5, 0.0)
+    omega = workloads.omega_for_kTa(6.0)
+    h64, hmx = _pair(fds, xy, omega, 1e-9, leaf_size=32)
+    kinds, ang = workloads.plane_wave_set(150)
+    F = fds.fds_rhs_plane_wave(h64, kinds, ang)
+    assert F.shape[1] == 300
+    assert _colmax(fds.fds_solve(hmx, F), fds.fds_solve(h64, F)) < 1e-7
+    h64.close()
+    hmx.close()
+
+
+def test_mixed_not_converged_is_reported():
+    torch_cuda()
+    fds = fdslib()
+    xy = workloads.star(256)
+    h = fds.fds_build(xy, 3.0, 2.0, 1.0, 1e-8, leaf_size=32, precision=fds.FDS_MIXED, ir_tol=0.0,
+                      ir_max_iter=1)
+    P = bem.phys(2.0, 1.0, 1.0, 3.0)
+    with pytest.raises(fds.FdsError) as e:
+        fds.fds_solve(h, bem.rhs(P, xy, 0, 0.1))
+    assert e.value.code == fds.FDS_ERR_NOT_CONVERGED
+    st = fds.fds_stats_get(h)
+    assert st.ir_residual > 0 and st.ir_iters <= 1
+    h.close()
