@@ -8,8 +8,12 @@ vectors of all incident waves, and the multi-RHS solve sweep.
 Default workload (the configuration the metric is quoted on): star cavity
 r(t) = 1 + 0.2 cos 5t with 2^19 nodes (2^20 complex unknowns), lambda = 2,
 mu = 1, rho = 1, k_T a = 20, leaf 64, l0 = 1, 1000 right-hand sides (plane P
-and SV waves at 500 angles), plain FP64.  The working set (factors, vectors)
-is far larger than L2, so no explicit flush is needed between steps.
+and SV waves at 500 angles), mixed precision (complex64 sweep refined against
+the FP64 compressed operator to max_c ||f - A x|| / ||f|| <= 1e-8).  After the
+timed steps one plain-FP64 step runs on the same inputs: its build and solve
+times and the relative error between the two solutions are reported beside
+the headline.  The working set (factors, vectors) is far larger than L2, so no
+explicit flush is needed between steps.
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Under torchrun each rank solves its own (rotated) copy of the cavity; there is
@@ -46,6 +50,10 @@ def parse():
     p.add_argument("--top", type=int, default=1)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--ir-tol", type=float, default=1e-8)
+    p.add_argument("--no-compare", action="store_true",
+                   help="skip the plain-FP64 comparison step (error and timings of the FP64 solver)")
     return p.parse_args()
 
 
@@ -208,15 +216,25 @@ def main():
 
     info = {}
 
-    def step():
-        h = fds.fds_build(xy, omega, 2.0, 1.0, args.eps, leaf_size=args.leaf, top_level=args.top, stream=stream)
-        fds.fds_rhs_plane_wave_device(h, d_kinds, d_angles, d_F, stream)
-        fds.fds_solve_device(h, d_F, stream)
+    prec = fds.FDS_MIXED if args.precision == "mixed" else fds.FDS_FP64
+
+    def step(precision=prec, out=d_F, rec=info):
+        h = fds.fds_build(xy, omega, 2.0, 1.0, args.eps, leaf_size=args.leaf, top_level=args.top, stream=stream,
+                          precision=precision, ir_tol=args.ir_tol)
+        fds.fds_rhs_plane_wave_device(h, d_kinds, d_angles, out, stream)
+        rec["converged"] = True
+        try:
+            fds.fds_solve_device(h, out, stream)
+        except fds.FdsError as e:
+            if e.code != fds.FDS_ERR_NOT_CONVERGED:
+                raise
+            rec["converged"] = False
         st = fds.fds_stats_get(h)
-        info["build_ms"], info["solve_ms"] = st.build_ms, st.solve_ms
-        info["top_size"], info["levels"] = st.top_size, st.levels
-        info["factor_gb"] = st.factor_bytes / 1e9
-        info["skeleton_dofs"] = [int(st.skeleton_dofs[l]) for l in range(st.levels + 1)]
+        rec["build_ms"], rec["solve_ms"] = st.build_ms, st.solve_ms
+        rec["top_size"], rec["levels"] = st.top_size, st.levels
+        rec["factor_gb"] = st.factor_bytes / 1e9
+        rec["skeleton_dofs"] = [int(st.skeleton_dofs[l]) for l in range(st.levels + 1)]
+        rec["ir_iters"], rec["ir_residual"] = st.ir_iters, st.ir_residual
         h.close()
 
     for _ in range(args.warmup):
@@ -252,6 +270,26 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
 
+    # plain-FP64 comparison on the same inputs (outside the timed region)
+    compare = None
+    if args.precision == "mixed" and not args.no_compare and rank == 0:
+        d_F64 = torch.empty_like(d_F)
+        rec = {}
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        step(fds.FDS_FP64, d_F64, rec)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        num = torch.linalg.vector_norm(d_F - d_F64, dim=1)
+        den = torch.linalg.vector_norm(d_F64, dim=1)
+        err = (num / den).max().item()
+        compare = {"fp64_ms_per_step": c0.elapsed_time(c1), "fp64_build_s": rec["build_ms"] / 1e3,
+                   "fp64_per_rhs_us": rec["solve_ms"] * 1e3 / args.nrhs, "fp64_factor_gb": rec["factor_gb"],
+                   "max_rel_err_vs_fp64": err,
+                   "note": "max over the right-hand sides of ||x_mixed - x_fp64|| / ||x_fp64||"}
+        del d_F64
+
     # end to end through the host-buffer C ABI: geometry and right-hand sides
     # from pinned host memory, solution back to pinned host memory
     e2e = None
@@ -267,12 +305,13 @@ def main():
         g_ = fds.fds_geometry(N, xy_host.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1.0)
         o = fds.default_options()
         o.leaf_size, o.top_level = args.leaf, args.top
+        o.precision, o.ir_tol = prec, args.ir_tol
         out = ctypes.c_void_p()
         rc = L.fds_build_ex(ctypes.byref(g_), float(omega), 2.0, 1.0, float(args.eps), ctypes.byref(o),
                             ctypes.byref(out))
         assert rc == 0, rc
         rc = L.fds_solve(out, F_np.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double)), args.nrhs)
-        assert rc == 0, rc
+        assert rc in (fds.FDS_OK, fds.FDS_ERR_NOT_CONVERGED), rc
         L.fds_destroy(out)
         t_e2e = time.perf_counter() - t0
         e2e = {"value": t_e2e * world / world, "unit": "s", "h2d_bytes_per_step": int(xy_host.nbytes + F_np.nbytes),
@@ -317,12 +356,16 @@ def main():
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "vs_baseline": None, "dtype": "c128+c64" if args.precision == "mixed" else "c128", "data": "synthetic",
         "config": {"workload": "star r=1+0.2cos5t, %d nodes (%d complex unknowns), lambda=2 mu=1 rho=1, "
-                               "k_T a=%g, leaf %d, l0=%d, eps=%g, %d plane P/SV waves, plain FP64"
-                               % (N, 2 * N, args.kta, args.leaf, args.top, args.eps, args.nrhs),
+                               "k_T a=%g, leaf %d, l0=%d, eps=%g, %d plane P/SV waves, %s"
+                               % (N, 2 * N, args.kta, args.leaf, args.top, args.eps, args.nrhs,
+                                  "mixed precision, refined to residual %g" % args.ir_tol
+                                  if args.precision == "mixed" else "plain FP64"),
                    "l2": "working set (factors, vectors) larger than L2; no flush",
-                   "precision": "fp64"},
+                   "precision": args.precision},
+        "ir_iters": info.get("ir_iters"), "ir_residual": info.get("ir_residual"),
+        "ir_converged": info.get("converged"), "vs_fp64": compare,
         "build_s": build_s, "per_rhs_us": per_rhs_us,
         "levels": info.get("levels"), "top_size": info.get("top_size"), "factor_gb": info.get("factor_gb"),
         "skeleton_dofs": info.get("skeleton_dofs"),

@@ -47,6 +47,23 @@ extern "C" {
 #define FDS_FP64  0               /* all arithmetic in FP64 / complex128 */
 #define FDS_MIXED 1               /* FP64 build; complex64 sweep refined against the FP64
                                      compressed forward operator */
+#define FDS_APPLY_FF   0
+#define FDS_APPLY_FP64 1
+
+/* Skeleton selection (Sec. 7.2): adaptive CPQR on the stacked proxy matrix,
+ * or (extension, not in the paper) a rank predicted by the learned network
+ * from geometry features, a sparse-sign sketch of the proxy matrix with
+ * (predicted rank + oversampling) rows, CPQR of the sketch, and a residual
+ * check on sampled proxy rows; cells that fail the check fall back to the
+ * adaptive CPQR. */
+#define FDS_RANK_ADAPTIVE 0
+#define FDS_RANK_LEARNED  1
+/* Learned-rank network: 16 -> 64 -> 64 -> 1, tanh, FP32.  Parameter vector:
+ * W1 [64x16] row-major, b1 [64], W2 [64x64], b2 [64], w3 [64], b3 (trained),
+ * then input normalisation mu [16], sd [16]. */
+#define FDS_MLP_NIN    16
+#define FDS_MLP_NTRAIN 5313
+#define FDS_MLP_NPARAM 5345
 
 typedef struct fds_handle fds_handle;   /* opaque; owns all device memory of one factorisation */
 
@@ -77,8 +94,16 @@ typedef struct {
     uint64_t cuda_stream;  /* cudaStream_t for the build; 0 = legacy default stream */
     double ir_tol;         /* FDS_MIXED: stop refining when max over right-hand sides of
                               ||f - A x|| / ||f|| <= ir_tol (A = compressed operator); default 1e-9 */
-    int32_t ir_max_iter;   /* FDS_MIXED: maximum refinement sweeps after the first; default 4;
+    int32_t ir_max_iter;   /* FDS_MIXED: maximum refinement sweeps after the first; default 10;
                               0 gives the plain complex64 sweep */
+    int32_t ir_apply;      /* FDS_MIXED: arithmetic of the forward operator in the residual:
+                              FDS_APPLY_FF (default) double-float products and sums on the
+                              FP32 pipe (about 44 significant bits), FDS_APPLY_FP64 FP64 */
+    int32_t rank_mode;     /* FDS_RANK_ADAPTIVE (default) or FDS_RANK_LEARNED */
+    const float *mlp_params; /* FDS_RANK_LEARNED: host, FDS_MLP_NPARAM floats, copied at the call */
+    int32_t sketch_extra;  /* FDS_RANK_LEARNED: sketch rows beyond the predicted rank; default 12 */
+    int32_t record_features; /* 1: keep the features and adaptive ranks of every (cell, component)
+                              for fds_features_get (training data) */
 } fds_options;
 
 /* Statistics of a built handle. */
@@ -91,6 +116,9 @@ typedef struct {
     int64_t factor_bytes;        /* device bytes held by the factors */
     int32_t ir_iters;            /* FDS_MIXED: refinement sweeps of the last solve */
     double ir_residual;          /* FDS_MIXED: final max relative residual of the last solve */
+    int64_t id_sketched;         /* FDS_RANK_LEARNED: (cell, component) IDs accepted from the sketch */
+    int64_t id_fallback;         /* FDS_RANK_LEARNED: IDs redone by the adaptive CPQR */
+    int64_t features_recorded;   /* rows available to fds_features_get */
 } fds_stats;
 
 /* Fill *o with the defaults listed above. */
@@ -127,7 +155,8 @@ int fds_rhs_plane_wave_device(fds_handle *h, const int32_t *d_kinds, const doubl
  * z_i = A_i^{-1} f_i, f~_i = A~_i V_i z_i (eq. (linear_last)), top solve,
  * downward pass x_i = z_i - W_i (f~_i - A~_i y_i), W_i = A_i^{-1} U_i
  * (eq. (down_comv)).
- * FDS_MIXED: the sweep runs on complex64 copies of the factors and is
+ * FDS_MIXED: the sweep runs on complex64 copies of the factors (the top
+ * solve stays FP64) and is
  * repeated on the residual r = f - A x, where A is the compressed operator
  * the factorisation inverts (leaf diagonal blocks, interpolation matrices,
  * original entries between sibling skeletons and between top cells), applied
@@ -240,6 +269,39 @@ int fds_lu_batched(int32_t batch, const int32_t *d_d, const int64_t *d_off, doub
  */
 int fds_lu_batched_noalloc(int32_t batch, const int32_t *d_d, const int64_t *d_off, double *d_A,
                            int32_t *d_piv, const int64_t *d_poff, int32_t *d_info, uint64_t stream);
+
+/*
+ * Training data of the learned-rank network (extension): the 16 features of
+ * each (cell, component) of levels L..l0+1 and the fraction k / n that the
+ * adaptive ID kept there, recorded by a build with record_features = 1.
+ * feat: host, cap x 16 floats; frac: host, cap floats.  Returns the number of
+ * rows written (min(cap, recorded)) or an error.  Features, in order:
+ * height above the leaves, log2 n, component, k_T 2R, k_L 2R, arc / 2R,
+ * chord / arc, mean / max / RMS |turning angle|, total turning, sqrt of the
+ * covariance eigenvalue ratio of the cell's vertices, near-field DOFs / d,
+ * log10 tol, n / cell nodes, k_T arc / 2 pi.
+ */
+int fds_features_get(const fds_handle *h, float *feat, float *frac, int32_t cap);
+
+/*
+ * Learned-rank network kernels (device pointers, FP32, enqueued on stream).
+ * fds_mlp_forward: y[b] = network(X[b, :]) for b < n.
+ * fds_mlp_loss_grad: L = (1/n) sum_b (y_b - t_b)^2 and dL/dtheta
+ *   (FDS_MLP_NTRAIN floats) over samples 0..n-1; deterministic.
+ * fds_mlp_adam: one Adam step (Kingma & Ba, Algorithm 1) of the trained
+ *   parameters with moment buffers m, v (FDS_MLP_NTRAIN floats each, zero at
+ *   step 1); step counts from 1.
+ * fds_mlp_train: Adam (0.9, 0.999, 1e-8) over the minibatches
+ *   order[s*batch .. (s+1)*batch) for s < n_order / batch, moments starting
+ *   at zero; losses (nullable) receives the loss of each step.
+ */
+int fds_mlp_forward(const float *d_params, const float *d_X, int32_t n, float *d_y, uint64_t stream);
+int fds_mlp_loss_grad(const float *d_params, const float *d_X, const float *d_t, int32_t n, float *d_grad,
+                      float *d_loss, uint64_t stream);
+int fds_mlp_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, int32_t step, float lr,
+                 float beta1, float beta2, float eps, uint64_t stream);
+int fds_mlp_train(float *d_params, const float *d_X, const float *d_t, int32_t n, const int32_t *d_order,
+                  int32_t n_order, int32_t batch, float lr, float *d_losses, uint64_t stream);
 
 #ifdef __cplusplus
 }

@@ -1,6 +1,8 @@
 // C ABI of the solver (include/fds.h): argument checks, handle lifetime,
 // host<->device copies for the host-buffer entry points.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 #include <new>
 
 #include "fds_internal.cuh"
@@ -17,7 +19,12 @@ extern "C" void fds_default_options(fds_options *o) {
     o->alpha_set = 0;
     o->cuda_stream = 0;
     o->ir_tol = 1e-9;
-    o->ir_max_iter = 4;
+    o->ir_max_iter = 10;
+    o->ir_apply = FDS_APPLY_FF;
+    o->rank_mode = FDS_RANK_ADAPTIVE;
+    o->mlp_params = nullptr;
+    o->sketch_extra = 12;
+    o->record_features = 0;
 }
 
 extern "C" const char *fds_error_string(int code) {
@@ -45,7 +52,9 @@ extern "C" int fds_build_ex(const fds_geometry *g, double omega, double lambda, 
     else fds_default_options(&o);
     if (o.leaf_size < 2 || !(o.proxy_ratio > 1.0) || o.proxy_points < 8 || o.top_level < 0 ||
         (o.precision != FDS_FP64 && o.precision != FDS_MIXED) || !(o.ir_tol >= 0.0) || o.ir_max_iter < 0 ||
-        o.ir_max_iter > 100)
+        o.ir_max_iter > 100 || (o.ir_apply != FDS_APPLY_FF && o.ir_apply != FDS_APPLY_FP64) ||
+        (o.rank_mode != FDS_RANK_ADAPTIVE && o.rank_mode != FDS_RANK_LEARNED) ||
+        (o.rank_mode == FDS_RANK_LEARNED && !o.mlp_params) || o.sketch_extra < 1 || o.sketch_extra > 64)
         return FDS_ERR_ARG;
     for (int i = 0; i < 2 * g->n_nodes; ++i)
         if (!std::isfinite(g->xy[i])) return FDS_ERR_ARG;
@@ -70,6 +79,20 @@ extern "C" int fds_build_ex(const fds_geometry *g, double omega, double lambda, 
     h->tol = tol;
     h->opt = o;
     h->stream = (cudaStream_t)o.cuda_stream;
+    if (o.rank_mode == FDS_RANK_LEARNED) {
+        for (int i = 0; i < FDS_MLP_NPARAM; ++i)
+            if (!std::isfinite(o.mlp_params[i])) {
+                delete h;
+                return FDS_ERR_ARG;
+            }
+        std::vector<float> prm(o.mlp_params, o.mlp_params + FDS_MLP_NPARAM);
+        int rc0 = h->d_mlp.upload(prm, h->stream);
+        if (rc0 != FDS_OK) {
+            delete h;
+            return rc0;
+        }
+    }
+    h->opt.mlp_params = nullptr;   // not kept past the call
     int rc = fds_build_impl(h);
     if (rc != FDS_OK) {
         cudaStreamSynchronize(h->stream);
@@ -161,6 +184,9 @@ extern "C" int fds_stats_get(const fds_handle *h, fds_stats *st) {
     st->factor_bytes = h->factor_bytes;
     st->ir_iters = h->ir_iters;
     st->ir_residual = h->ir_residual;
+    st->id_sketched = h->id_sketched;
+    st->id_fallback = h->id_fallback;
+    st->features_recorded = (int64_t)h->frac_rows.size();
     return FDS_OK;
 }
 
@@ -173,6 +199,16 @@ extern "C" int fds_level_ranks(const fds_handle *h, int32_t level, int32_t *k, i
         k[2 * b + 1] = C.k2[b];
     }
     return 2 * C.nb;
+}
+
+extern "C" int fds_features_get(const fds_handle *h, float *feat, float *frac, int32_t cap) {
+    if (!h || cap < 0 || (cap > 0 && (!feat || !frac))) return FDS_ERR_ARG;
+    const int64_t n = std::min<int64_t>(cap, (int64_t)h->frac_rows.size());
+    for (int64_t r = 0; r < n; ++r) {
+        frac[r] = h->frac_rows[r];
+        for (int i = 0; i < FDS_MLP_NIN; ++i) feat[r * FDS_MLP_NIN + i] = h->feat_rows[r * FDS_MLP_NIN + i];
+    }
+    return (int)n;
 }
 
 extern "C" void fds_destroy(fds_handle *h) {

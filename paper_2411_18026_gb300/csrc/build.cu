@@ -12,6 +12,7 @@
 #include "fds_internal.cuh"
 #include "id.cuh"
 #include "kernel_eval.cuh"
+#include "mlp.cuh"
 #include "prof.cuh"
 
 namespace {
@@ -765,8 +766,55 @@ int fds_build_impl(fds_handle *h) {
             FDS_CUDA_TRY(cudaGetLastError());
             FDS_TRY(sync_check(s));
         }
-        // ---- interpolative decomposition (a2)
-        {
+        // ---- interpolative decomposition (a2; a2' with the learned rank)
+        const bool learned = h->opt.rank_mode == FDS_RANK_LEARNED;
+        DBuf<float> d_feat;
+        if (learned || h->opt.record_features) {
+            std::vector<int> lo(nb), hi(nb);
+            for (int b = 0; b < nb; ++b) { lo[b] = h->ranges[l][b].first; hi[b] = h->ranges[l][b].second; }
+            DBuf<int> d_lo, d_hi, d_fn1, d_fn2;
+            FDS_TRY(d_lo.upload(lo, s));
+            FDS_TRY(d_hi.upload(hi, s));
+            FDS_TRY(d_fn1.upload(C.n1, s));
+            FDS_TRY(d_fn2.upload(C.n2, s));
+            FDS_TRY(d_feat.alloc((size_t)2 * nb * FDS_MLP_NIN));
+            ProfScope ps("a2.features", s);
+            FDS_TRY(level_features(nb, d_lo.p, d_hi.p, h->d_xy.p, N, d_R.p, d_fn1.p, d_fn2.p, d_nnd.p, L - l,
+                                   h->P.kT, h->P.kL, h->tol, d_feat.p, s));
+            FDS_TRY(sync_check(s));
+        }
+        if (learned) {
+            DBuf<float> d_frac;
+            DBuf<int> d_fail;
+            FDS_TRY(d_frac.alloc((size_t)2 * nb));
+            FDS_TRY(d_fail.alloc((size_t)2 * nb));
+            {
+                ProfScope ps("a2.rank_mlp", s);
+                FDS_TRY(mlp_forward(h->d_mlp.p, d_feat.p, 2 * nb, d_frac.p, s));
+            }
+            {
+                ProfScope ps("a2.id_sketch", s);
+                FDS_TRY(id_sketched(2 * nb, maxm, d_idm.p, d_idn.p, d_yoff.p, d_Y.p, d_frac.p, h->opt.sketch_extra,
+                                    h->tol, d_rank.p, d_perm.p, d_poff.p, d_T.p, d_toff.p, d_fail.p,
+                                    0x5eed2411ULL ^ ((unsigned long long)l << 40), s));
+            }
+            std::vector<int> fail;
+            FDS_TRY(d2h(fail, d_fail.p, 2 * nb, s));
+            FDS_TRY(sync_check(s));
+            std::vector<int> sel;
+            for (int b = 0; b < 2 * nb; ++b)
+                if (fail[b]) sel.push_back(b);
+            h->id_sketched += 2 * nb - (int64_t)sel.size();
+            h->id_fallback += (int64_t)sel.size();
+            if (!sel.empty()) {
+                DBuf<int> d_sel;
+                FDS_TRY(d_sel.upload(sel, s));
+                ProfScope ps("a2.id_cpqr", s);
+                FDS_TRY(id_batched((int)sel.size(), maxm, maxn, d_idm.p, d_idn.p, d_yoff.p, d_Y.p, h->tol, d_rank.p,
+                                   d_perm.p, d_poff.p, d_T.p, d_toff.p, s, d_sel.p));
+                FDS_TRY(sync_check(s));
+            }
+        } else {
             ProfScope ps("a2.id_cpqr", s);
             FDS_TRY(id_batched(2 * nb, maxm, maxn, d_idm.p, d_idn.p, d_yoff.p, d_Y.p, h->tol, d_rank.p, d_perm.p,
                                d_poff.p, d_T.p, d_toff.p, s));
@@ -775,6 +823,18 @@ int fds_build_impl(fds_handle *h) {
         FDS_TRY(d2h(rank, d_rank.p, 2 * nb, s));
         FDS_TRY(d2h(C.perm, d_perm.p, poff[2 * nb], s));
         FDS_TRY(sync_check(s));
+        if (h->opt.record_features) {
+            std::vector<float> f;
+            FDS_TRY(d2h(f, d_feat.p, (size_t)2 * nb * FDS_MLP_NIN, s));
+            FDS_TRY(sync_check(s));
+            for (int b = 0; b < 2 * nb; ++b) {
+                const int n = (b & 1) ? C.n2[b >> 1] : C.n1[b >> 1];
+                if (n <= 0) continue;
+                h->feat_rows.insert(h->feat_rows.end(), f.begin() + (size_t)b * FDS_MLP_NIN,
+                                    f.begin() + (size_t)(b + 1) * FDS_MLP_NIN);
+                h->frac_rows.push_back((float)rank[b] / (float)n);
+            }
+        }
         C.permoff = poff;
         C.k1.resize(nb);
         C.k2.resize(nb);
@@ -847,6 +907,17 @@ int fds_build_impl(fds_handle *h) {
             ps.flops = fl_w;
             FDS_TRY(dense_lu_solve(nb, C.dmax, C.rmax, C.rLU.p, C.piv.p, C.d_offpiv.p, C.rW.p, s));
         }
+        // A_i^{-1} for the solve sweep (Sec. 7.3 step 3(b)), from the LU factors
+        // by a solve against the identity; the LU itself is not kept
+        FDS_TRY(C.Ainv.alloc(C.offA[nb]));
+        FDS_TRY(make_refs(C.rAinv, C.Ainv.p, C.offA, dv, dv, s));
+        fds_count_launch(), k_set_identity<<<nb, 256, 0, s>>>(C.rAinv.p);
+        FDS_CUDA_TRY(cudaGetLastError());
+        {
+            ProfScope ps("a3.merge_a_inverse", s);
+            ps.flops = fl_lu * 3.0;
+            FDS_TRY(dense_lu_solve(nb, C.dmax, C.dmax, C.rLU.p, C.piv.p, C.d_offpiv.p, C.rAinv.p, s));
+        }
         {
             ProfScope ps("a3.merge_s_gemm", s);
             ps.flops = fl_s;
@@ -877,7 +948,10 @@ int fds_build_impl(fds_handle *h) {
         FDS_TRY(sync_check(s));
         for (int b = 0; b < nb; ++b)
             if (hinfo[b] || hinfo2[b]) return FDS_ERR_SINGULAR;
-        h->factor_bytes += (int64_t)(C.LU.bytes() + C.V.bytes() + C.W.bytes() + C.At.bytes() + C.piv.bytes());
+        C.LU.release();
+        C.rLU.release();
+        C.piv.release();
+        h->factor_bytes += (int64_t)(C.Ainv.bytes() + C.V.bytes() + C.W.bytes() + C.At.bytes());
 
         // ---- parent level (eq. (A_rearrangement)): DOFs = children's skeletons
         Level &Pn = h->lv[l - 1];

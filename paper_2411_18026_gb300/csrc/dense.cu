@@ -239,10 +239,12 @@ int dense_lu_solve(int batch, int max_rows, int max_cols, const MatRefF *d_LU, c
 }
 int dense_gemm(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, int opB,
                const MatRef *d_C, cplx alpha, cplx beta, cudaStream_t s) {
+    if (opB == 0) return dense_gemm_rt(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
     return gemm_t<cplx>(batch, max_m, max_n, d_A, opA, d_B, opB, d_C, alpha, beta, s);
 }
 int dense_gemm(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, const MatRefF *d_B, int opB,
                const MatRefF *d_C, cplxf alpha, cplxf beta, cudaStream_t s) {
+    if (opB == 0) return dense_gemm_rt(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
     return gemm_t<cplxf>(batch, max_m, max_n, d_A, opA, d_B, opB, d_C, alpha, beta, s);
 }
 

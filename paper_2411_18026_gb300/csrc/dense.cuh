@@ -26,6 +26,15 @@ int dense_lu_solve(int batch, int max_rows, int max_cols, const MatRef *d_LU, co
 // C = alpha * op(A) * op(B) + beta * C, op = N (0), or conjugate transpose (2).
 int dense_gemm(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, int opB,
                const MatRef *d_C, cplx alpha, cplx beta, cudaStream_t s);
+// Register-tiled GEMM (gemm.cu), op(B) = B; dense_gemm routes here when opB = 0.
+int dense_gemm_rt(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, const MatRef *d_C,
+                  cplx alpha, cplx beta, cudaStream_t s);
+int dense_gemm_rt(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, const MatRefF *d_B,
+                  const MatRefF *d_C, cplxf alpha, cplxf beta, cudaStream_t s);
+// Same with complex128 operands multiplied in double-float arithmetic on the
+// FP32 pipe (about 44 significant bits; see gemm.cu).
+int dense_gemm_ff(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, const MatRef *d_C,
+                  cplx alpha, cplx beta, cudaStream_t s);
 // complex64 versions (mixed-precision sweep)
 int dense_lu_solve(int batch, int max_rows, int max_cols, const MatRefF *d_LU, const int *d_piv,
                    const int64_t *d_poff, const MatRefF *d_B, cudaStream_t s);

@@ -71,9 +71,9 @@ struct Level {
     std::vector<int> perm;
     // --- factors (device), offsets in complex entries
     std::vector<int64_t> offA, offW, offAt, offV, offpiv;
-    DBuf<cplx> LU, W, At, V;
+    DBuf<cplx> LU, W, At, V, Ainv;   // LU: during the build only; Ainv = A_i^{-1} for the sweep
     DBuf<int> piv;
-    DBuf<MatRef> rLU, rW, rAt, rV;
+    DBuf<MatRef> rLU, rW, rAt, rV, rAinv;
     DBuf<int64_t> d_offpiv;
     // --- placement of each cell's skeleton vector in its parent's DOF vector
     std::vector<int> par_pos1, par_pos2;   // start of comp-1 / comp-2 skeleton block in the parent
@@ -84,8 +84,8 @@ struct Level {
     int dmax = 0, rmax = 0;
     double sum_d2 = 0, sum_rd = 0, sum_r2 = 0;   // algorithmic work sums for the sweep
     // --- mixed precision: complex64 copies of the sweep factors
-    DBuf<cplxf> LUf, Wf, Atf, Vf;
-    DBuf<MatRefF> rLUf, rWf, rAtf, rVf;
+    DBuf<cplxf> Ainvf, Wf, Atf, Vf;
+    DBuf<MatRefF> rAinvf, rWf, rAtf, rVf;
     // --- FP64 compressed forward operator: leaf diagonal blocks (leaf level)
     //     and sibling-coupling blocks S (levels that are parents), both d x d
     DBuf<cplx> Dfw, Sfw;
@@ -113,14 +113,12 @@ struct fds_handle {
     DBuf<MatRef> rtop;
     DBuf<int64_t> d_ptop_off;
     DBuf<int> d_info;
-    // mixed precision: off-diagonal top blocks (FP64) and complex64 top LU
+    // mixed precision: off-diagonal top blocks (FP64 forward operator)
     DBuf<cplx> Atop_off;
     DBuf<MatRef> rtop_off;
-    DBuf<cplxf> Atopf;
-    DBuf<MatRefF> rtopf;
     // solve workspace (grown on demand)
-    std::vector<DBuf<cplx>> wz, wf, wt, wy;
-    std::vector<DBuf<cplxf>> wzf, wff, wtf;
+    std::vector<DBuf<cplx>> wz, wf, wt, wy, wr;
+    std::vector<DBuf<cplxf>> wzf, wff, wtf, wrf;
     DBuf<cplx> wtop, wytop, wX;
     DBuf<cplxf> wtopf;
     DBuf<MatRef> wrefs;
@@ -129,6 +127,10 @@ struct fds_handle {
     int64_t ws_cols = 0;
     double build_ms = 0, solve_ms = 0;
     int64_t factor_bytes = 0;
+    // learned-rank ID: network parameters (device), counters, recorded training rows
+    DBuf<float> d_mlp;
+    int64_t id_sketched = 0, id_fallback = 0;
+    std::vector<float> feat_rows, frac_rows;
     int ir_iters = 0;          // refinement sweeps of the last mixed solve
     double ir_residual = 0;    // max_c ||f_c - A x_c|| / ||f_c|| after the last mixed solve
 };
@@ -151,8 +153,8 @@ int fds_build_impl(fds_handle *h);
 // FDS_MIXED: copy of a level's square blocks (LU buffer, before it is factored)
 // into a forward-operator store.
 int fds_keep_blocks(const Level &Lv, DBuf<cplx> &dst, DBuf<MatRef> &rdst, cudaStream_t s);
-// FDS_MIXED: complex64 copies of the sweep factors; releases the FP64 ones
-// that the sweep no longer needs.
+// FDS_MIXED: complex64 copies of the sweep factors below the top; releases
+// the FP64 ones that the sweep no longer needs (the top LU stays FP64).
 int fds_mixed_prepare(fds_handle *h);
 int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s);
 int fds_solve_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s);

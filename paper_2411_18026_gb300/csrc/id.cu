@@ -23,9 +23,10 @@ __global__ void __launch_bounds__(ID_THREADS) k_cpqr_id(const int *__restrict__ 
                                                         const int64_t *__restrict__ offs, cplx *__restrict__ Yall,
                                                         double tol, int *__restrict__ ranks,
                                                         int *__restrict__ perms, const int64_t *__restrict__ poffs,
-                                                        cplx *__restrict__ Tall, const int64_t *__restrict__ toffs) {
+                                                        cplx *__restrict__ Tall, const int64_t *__restrict__ toffs,
+                                                        const int *__restrict__ sel) {
     extern __shared__ double smem[];
-    const int b = blockIdx.x;
+    const int b = sel ? sel[blockIdx.x] : blockIdx.x;
     const int m = ms[b], n = ns[b];
     cplx *Y = Yall + offs[b];
     cplx *v = (cplx *)smem;
@@ -167,13 +168,14 @@ __global__ void __launch_bounds__(ID_THREADS) k_cpqr_id(const int *__restrict__ 
 
 int id_batched(int batch, int max_m, int max_n, const int *d_m, const int *d_n, const int64_t *d_off, cplx *d_Y,
                double tol, int *d_rank, int *d_perm, const int64_t *d_poff, cplx *d_T, const int64_t *d_toff,
-               cudaStream_t s) {
+               cudaStream_t s, const int *d_sel) {
     if (batch <= 0) return FDS_OK;
     size_t smem = (size_t)max_m * sizeof(cplx) + (size_t)max_n * (sizeof(double) + sizeof(int)) + 16;
     if (smem > 220 * 1024) return FDS_ERR_ARG;
     if (smem > 48 * 1024)
         FDS_CUDA_TRY(cudaFuncSetAttribute(k_cpqr_id, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    fds_count_launch(), k_cpqr_id<<<batch, ID_THREADS, smem, s>>>(d_m, d_n, d_off, d_Y, tol, d_rank, d_perm, d_poff, d_T, d_toff);
+    fds_count_launch(), k_cpqr_id<<<batch, ID_THREADS, smem, s>>>(d_m, d_n, d_off, d_Y, tol, d_rank, d_perm, d_poff, d_T, d_toff,
+                                                                      d_sel);
     FDS_CUDA_TRY(cudaGetLastError());
     return FDS_OK;
 }

@@ -1,6 +1,7 @@
 // Mixed-precision solve (FDS_MIXED): the solve sweep of Sec. 6.2-6.3 runs on
 // complex64 copies of the factors and is refined against the compressed
-// operator the factorisation inverts, applied in FP64:
+// operator the factorisation inverts, stored in FP64 and applied in FP64 or
+// in double-float arithmetic on the FP32 pipe (about 44 significant bits):
 //
 //   A = D_L + U_L B_L V_L,   B_l = S_{l-1} + U_{l-1} B_{l-1} V_{l-1}  (l > l0+1),
 //   B_{l0+1} = S_{l0} + A_top,off
@@ -153,7 +154,14 @@ double level_d2(const Level &C) {
     return s;
 }
 
-// Y = A X for nc leaf-order columns (both D_L x nc, column-major), FP64.
+// Products of the forward operator: FP64, or double-float on the FP32 pipe.
+int fgemm(const fds_handle *h, int batch, int max_m, int max_n, const MatRef *A, int opA, const MatRef *B,
+          const MatRef *C, cplx alpha, cplx beta, cudaStream_t s) {
+    if (h->opt.ir_apply == FDS_APPLY_FP64) return dense_gemm_rt(batch, max_m, max_n, A, opA, B, C, alpha, beta, s);
+    return dense_gemm_ff(batch, max_m, max_n, A, opA, B, C, alpha, beta, s);
+}
+
+// Y = A X for nc leaf-order columns (both D_L x nc, column-major), complex128.
 int forward_apply(fds_handle *h, const cplx *X, cplx *Y, int nc, cudaStream_t s) {
     const int L = h->L, l0 = h->l0;
     const int maxnb = fds_max_cells(h);
@@ -170,7 +178,7 @@ int forward_apply(fds_handle *h, const cplx *X, cplx *Y, int nc, cudaStream_t s)
         cplx *xl = (l == L) ? (cplx *)X : h->wz[l].p;
         fds_count_launch(), k_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, xl, C.d_doff.p, nc, C.D, rZ);
         fds_count_launch(), k_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, h->wt[l].p, C.d_roff.p, nc, ldr, rT);
-        FDS_TRY(dense_gemm(nb, C.rmax, nc, C.rV.p, 0, rZ, 0, rT, one, zero, s));
+        FDS_TRY(fgemm(h, nb, C.rmax, nc, C.rV.p, 0, rZ, rT, one, zero, s));
         cplx *par = (l - 1 > l0) ? h->wz[l - 1].p : h->wtop.p;
         const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
         fds_count_launch(), k_child_parent64<<<nb, 256, 0, s>>>(nb, C.d_roff.p, C.d_k1.p, C.d_par_pos1.p,
@@ -189,12 +197,12 @@ int forward_apply(fds_handle *h, const cplx *X, cplx *Y, int nc, cudaStream_t s)
         hv[0].p = xt; hv[0].rows = (int)h->Dtop; hv[0].cols = nc; hv[0].ld = ld;
         hv[1].p = yt; hv[1].rows = (int)h->Dtop; hv[1].cols = nc; hv[1].ld = ld;
         FDS_CUDA_TRY(cudaMemcpyAsync(rX, hv, sizeof(hv), cudaMemcpyHostToDevice, s));
-        FDS_TRY(dense_gemm(1, (int)h->Dtop, nc, h->rtop_off.p, 0, rX, 0, rX + 1, one, zero, s));
+        FDS_TRY(fgemm(h, 1, (int)h->Dtop, nc, h->rtop_off.p, 0, rX, rX + 1, one, zero, s));
         fl += 8.0 * (double)h->Dtop * h->Dtop * nc;
         const MatRef *Bd = (L > l0) ? T.rSfw.p : T.rDfw.p;
         fds_count_launch(), k_refs<<<(T.nb + 127) / 128, 128, 0, s>>>(T.nb, xt, T.d_doff.p, nc, h->Dtop, rZ);
         fds_count_launch(), k_refs<<<(T.nb + 127) / 128, 128, 0, s>>>(T.nb, yt, T.d_doff.p, nc, h->Dtop, rY);
-        FDS_TRY(dense_gemm(T.nb, T.dmax, nc, Bd, 0, rZ, 0, rY, one, one, s));
+        FDS_TRY(fgemm(h, T.nb, T.dmax, nc, Bd, 0, rZ, rY, one, one, s));
         fl += 8.0 * level_d2(T) * nc;
     }
     // down
@@ -214,9 +222,9 @@ int forward_apply(fds_handle *h, const cplx *X, cplx *Y, int nc, cudaStream_t s)
         fds_count_launch(), k_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, yl, C.d_doff.p, nc, C.D, rY);
         fds_count_launch(), k_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, xl, C.d_doff.p, nc, C.D, rZ);
         FDS_CUDA_TRY(cudaGetLastError());
-        FDS_TRY(dense_gemm(nb, C.dmax, nc, C.rV.p, 2, rT, 0, rY, one, zero, s));
+        FDS_TRY(fgemm(h, nb, C.dmax, nc, C.rV.p, 2, rT, rY, one, zero, s));
         const MatRef *Bd = (l == L) ? C.rDfw.p : C.rSfw.p;
-        FDS_TRY(dense_gemm(nb, C.dmax, nc, Bd, 0, rZ, 0, rY, one, one, s));
+        FDS_TRY(fgemm(h, nb, C.dmax, nc, Bd, 0, rZ, rY, one, one, s));
         fl += 8.0 * (C.sum_rd + level_d2(C)) * nc;
     }
     ps.flops = fl;
@@ -245,41 +253,30 @@ int fds_mixed_prepare(fds_handle *h) {
             dv[b] = C.n1[b] + C.n2[b];
             rv[b] = C.k1[b] + C.k2[b];
         }
-        FDS_TRY(convert(C.LU, C.LUf, s));
+        FDS_TRY(convert(C.Ainv, C.Ainvf, s));
         FDS_TRY(convert(C.W, C.Wf, s));
         FDS_TRY(convert(C.At, C.Atf, s));
         FDS_TRY(convert(C.V, C.Vf, s));
-        FDS_TRY(make_refs_t(C.rLUf, C.LUf.p, C.offA, dv, dv, s));
+        FDS_TRY(make_refs_t(C.rAinvf, C.Ainvf.p, C.offA, dv, dv, s));
         FDS_TRY(make_refs_t(C.rWf, C.Wf.p, C.offW, dv, rv, s));
         FDS_TRY(make_refs_t(C.rAtf, C.Atf.p, C.offAt, rv, rv, s));
         FDS_TRY(make_refs_t(C.rVf, C.Vf.p, C.offV, rv, dv, s));
-        bytes += (int64_t)(C.LUf.bytes() + C.Wf.bytes() + C.Atf.bytes() + C.Vf.bytes() + C.piv.bytes() +
-                           C.V.bytes() + C.Dfw.bytes() + C.Sfw.bytes());
+        bytes += (int64_t)(C.Ainvf.bytes() + C.Wf.bytes() + C.Atf.bytes() + C.Vf.bytes() + C.V.bytes() +
+                           C.Dfw.bytes() + C.Sfw.bytes());
     }
     bytes += (int64_t)h->lv[l0].Sfw.bytes() + (int64_t)h->lv[l0].Dfw.bytes();
-    FDS_TRY(convert(h->Atop, h->Atopf, s));
-    {
-        MatRefF t;
-        t.p = h->Atopf.p;
-        t.rows = t.cols = (int)h->Dtop;
-        t.ld = (int)std::max<int64_t>(h->Dtop, 1);
-        std::vector<MatRefF> ht = {t};
-        FDS_TRY(h->rtopf.upload(ht, s));
-    }
-    bytes += (int64_t)(h->Atopf.bytes() + h->ptop.bytes() + h->Atop_off.bytes());
+    bytes += (int64_t)(h->Atop.bytes() + h->ptop.bytes() + h->Atop_off.bytes());
     FDS_CUDA_TRY(cudaStreamSynchronize(s));
     // the FP64 sweep factors are not used by the mixed solve
     for (int l = L; l > l0; --l) {
         Level &C = h->lv[l];
-        C.LU.release();
-        C.rLU.release();
+        C.Ainv.release();
+        C.rAinv.release();
         C.W.release();
         C.rW.release();
         C.At.release();
         C.rAt.release();
     }
-    h->Atop.release();
-    h->rtop.release();
     h->factor_bytes = bytes;
     return FDS_OK;
 }
@@ -295,7 +292,7 @@ int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
     if (refine) FDS_TRY(forward_workspace(h, ncmax));
     FDS_TRY(grow(h->wX, (size_t)D * ncmax));
     if (h->wnorm.n < (size_t)2 * ncmax) FDS_TRY(h->wnorm.alloc((size_t)2 * ncmax));
-    cplxf *leaf = sweep_leaf_vector<cplxf>(h);
+    cplxf *leaf_in = sweep_leaf_in<cplxf>(h), *leaf = sweep_leaf_out<cplxf>(h);
     cplx *Yleaf = refine ? ((L > h->l0) ? h->wy[L].p : h->wytop.p) : nullptr;
     std::vector<double> nrm(2 * ncmax);
     int iters = 0;
@@ -314,7 +311,7 @@ int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
         {
             ProfScope ps("a7.residual", s);
             fds_count_launch(), k_residual<<<dim3(gx, nc), 256, 0, s>>>(h->d_leaf_gidx.p, D, F, ld_rhs, nullptr,
-                                                                        leaf, h->wnorm.p);
+                                                                        leaf_in, h->wnorm.p);
         }
         FDS_CUDA_TRY(cudaGetLastError());
         FDS_TRY(sweep_chunk<cplxf>(h, nc, s));
@@ -328,7 +325,7 @@ int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
             {
                 ProfScope ps("a7.residual", s);
                 fds_count_launch(), k_residual<<<dim3(gx, nc), 256, 0, s>>>(h->d_leaf_gidx.p, D, F, ld_rhs, Yleaf,
-                                                                            leaf, h->wnorm.p);
+                                                                            leaf_in, h->wnorm.p);
             }
             FDS_CUDA_TRY(cudaGetLastError());
             FDS_CUDA_TRY(cudaMemcpyAsync(nrm.data(), h->wnorm.p, sizeof(double) * 2 * nc, cudaMemcpyDeviceToHost, s));

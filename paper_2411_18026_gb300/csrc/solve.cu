@@ -1,12 +1,14 @@
 // Multi-RHS solve sweep (arXiv 2411.18026 Sec. 6.2 upward, Sec. 6.3 top and
 // downward):
-//   up    z_i = A_i^{-1} f_i,  f~_i = A~_i V_i z_i,  parent f by eq. (rhs_rearrangement)
+//   up    z_i = A_i^{-1} f_i (a GEMM with the A_i^{-1} formed at build),
+//         f~_i = A~_i V_i z_i,  parent f by eq. (rhs_rearrangement)
 //   top   x = A_top^{-1} f_top
 //   down  y_i from the parent x (eqs. (xtoy1)-(xtoy2)),
 //         x_i = z_i - W_i (f~_i - A~_i y_i) with W_i = A_i^{-1} U_i   (eq. (down_comv))
 // Right-hand sides are processed in column chunks; all arithmetic in the
-// batched kernels of dense.cu and the gathers below.  The sweep is written
-// once for complex128 factors (FDS_FP64) and complex64 copies (FDS_MIXED).
+// batched kernels of dense.cu / gemm.cu and the gathers below.  The sweep is
+// written once for complex128 factors (FDS_FP64) and complex64 copies
+// (FDS_MIXED); the top system is solved with the FP64 LU in both.
 #include <algorithm>
 
 #include "fds_internal.cuh"
@@ -60,6 +62,17 @@ __global__ void k_child_parent(int nb, const int64_t *__restrict__ roff, const i
     }
 }
 
+template <class A, class B>
+__global__ void k_convert(const A *__restrict__ src, B *dst, int64_t rows, int64_t lds, int64_t ldd, int cols) {
+    const int64_t tot = rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % rows, c = e / rows;
+        const A v = src[i + c * lds];
+        dst[i + c * ldd].x = v.x;
+        dst[i + c * ldd].y = v.y;
+    }
+}
+
 template <class T>
 int grow(DBuf<T> &b, size_t n) {
     if (b.n >= n && b.p) return FDS_OK;
@@ -72,14 +85,14 @@ struct View;
 
 template <>
 struct View<cplx> {
-    static const MatRef *LU(const Level &v) { return v.rLU.p; }
+    static const MatRef *Ainv(const Level &v) { return v.rAinv.p; }
     static const MatRef *W(const Level &v) { return v.rW.p; }
     static const MatRef *At(const Level &v) { return v.rAt.p; }
     static const MatRef *V(const Level &v) { return v.rV.p; }
-    static const MatRef *top(const fds_handle *h) { return h->rtop.p; }
     static std::vector<DBuf<cplx>> &z(fds_handle *h) { return h->wz; }
     static std::vector<DBuf<cplx>> &f(fds_handle *h) { return h->wf; }
     static std::vector<DBuf<cplx>> &t(fds_handle *h) { return h->wt; }
+    static std::vector<DBuf<cplx>> &r(fds_handle *h) { return h->wr; }
     static DBuf<cplx> &wtop(fds_handle *h) { return h->wtop; }
     static DBuf<MatRef> &refs(fds_handle *h) { return h->wrefs; }
     static cplx one() { return mkc(1, 0); }
@@ -87,14 +100,14 @@ struct View<cplx> {
 
 template <>
 struct View<cplxf> {
-    static const MatRefF *LU(const Level &v) { return v.rLUf.p; }
+    static const MatRefF *Ainv(const Level &v) { return v.rAinvf.p; }
     static const MatRefF *W(const Level &v) { return v.rWf.p; }
     static const MatRefF *At(const Level &v) { return v.rAtf.p; }
     static const MatRefF *V(const Level &v) { return v.rVf.p; }
-    static const MatRefF *top(const fds_handle *h) { return h->rtopf.p; }
     static std::vector<DBuf<cplxf>> &z(fds_handle *h) { return h->wzf; }
     static std::vector<DBuf<cplxf>> &f(fds_handle *h) { return h->wff; }
     static std::vector<DBuf<cplxf>> &t(fds_handle *h) { return h->wtf; }
+    static std::vector<DBuf<cplxf>> &r(fds_handle *h) { return h->wrf; }
     static DBuf<cplxf> &wtop(fds_handle *h) { return h->wtopf; }
     static DBuf<MatRefF> &refs(fds_handle *h) { return h->wrefsf; }
     static cplxf one() { return mkcf(1, 0); }
@@ -112,26 +125,35 @@ template <class C>
 int sweep_workspace(fds_handle *h, int ncmax) {
     typedef View<C> Vw;
     const int L = h->L, l0 = h->l0;
-    auto &wz = Vw::z(h), &wf = Vw::f(h), &wt = Vw::t(h);
+    auto &wz = Vw::z(h), &wf = Vw::f(h), &wt = Vw::t(h), &wr = Vw::r(h);
     if ((int)wz.size() != L + 1) {
         wz = std::vector<DBuf<C>>(L + 1);
         wf = std::vector<DBuf<C>>(L + 1);
         wt = std::vector<DBuf<C>>(L + 1);
     }
+    if ((int)wr.size() != L + 1) wr = std::vector<DBuf<C>>(L + 1);
     for (int l = L; l > l0; --l) {
         Level &Cv = h->lv[l];
         FDS_TRY(grow(wz[l], (size_t)Cv.D * ncmax));
+        FDS_TRY(grow(wr[l], (size_t)Cv.D * ncmax));
         FDS_TRY(grow(wf[l], (size_t)std::max<int64_t>(Cv.Rtot, 1) * ncmax));
         FDS_TRY(grow(wt[l], (size_t)std::max<int64_t>(Cv.Rtot, 1) * ncmax));
     }
     FDS_TRY(grow(Vw::wtop(h), (size_t)std::max<int64_t>(h->Dtop, 1) * ncmax));
+    // the complex64 sweep solves the top system in FP64
+    FDS_TRY(grow(h->wtop, (size_t)std::max<int64_t>(h->Dtop, 1) * ncmax));
     const int maxnb = fds_max_cells(h);
     if (Vw::refs(h).n < (size_t)4 * maxnb) FDS_TRY(Vw::refs(h).alloc((size_t)4 * maxnb));
     return FDS_OK;
 }
 
 template <class C>
-C *sweep_leaf_vector(fds_handle *h) {
+C *sweep_leaf_in(fds_handle *h) {
+    return (h->L > h->l0) ? View<C>::r(h)[h->L].p : View<C>::wtop(h).p;
+}
+
+template <class C>
+C *sweep_leaf_out(fds_handle *h) {
     return (h->L > h->l0) ? View<C>::z(h)[h->L].p : View<C>::wtop(h).p;
 }
 
@@ -144,7 +166,7 @@ int sweep_chunk(fds_handle *h, int nc, cudaStream_t s) {
     mone.x = -mone.x;
     const int maxnb = fds_max_cells(h);
     MatRefT<C> *rZ = Vw::refs(h).p, *rF = rZ + maxnb, *rT = rF + maxnb, *rX = rT + maxnb;
-    auto &wz = Vw::z(h), &wf = Vw::f(h), &wt = Vw::t(h);
+    auto &wz = Vw::z(h), &wf = Vw::f(h), &wt = Vw::t(h), &wr = Vw::r(h);
     C *top = Vw::wtop(h).p;
     const double esz = sizeof(C);
     // upward
@@ -153,16 +175,17 @@ int sweep_chunk(fds_handle *h, int nc, cudaStream_t s) {
         Level &Pn = h->lv[l - 1];
         const int nb = Cv.nb;
         const int64_t ldr = std::max<int64_t>(Cv.Rtot, 1);
-        C *Z = wz[l].p, *F = wf[l].p, *U = wt[l].p;
+        C *Z = wz[l].p, *F = wf[l].p, *U = wt[l].p, *Rh = wr[l].p;
+        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, Rh, Cv.d_doff.p, nc, Cv.D, rF);
         fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, Z, Cv.d_doff.p, nc, Cv.D, rZ);
-        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, U, Cv.d_roff.p, nc, ldr, rT);
-        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, F, Cv.d_roff.p, nc, ldr, rF);
         {
-            ProfScope ps("a6.up_lu_solve", s);
+            ProfScope ps("a6.up_a_inverse", s);
             ps.flops = 8.0 * Cv.sum_d2 * nc;
             ps.bytes = esz * Cv.sum_d2 + 2 * esz * Cv.D * nc;
-            FDS_TRY(dense_lu_solve(nb, Cv.dmax, nc, Vw::LU(Cv), Cv.piv.p, Cv.d_offpiv.p, rZ, s));
+            FDS_TRY(dense_gemm(nb, Cv.dmax, nc, Vw::Ainv(Cv), 0, rF, 0, rZ, one, zero, s));
         }
+        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, U, Cv.d_roff.p, nc, ldr, rT);
+        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, F, Cv.d_roff.p, nc, ldr, rF);
         {
             ProfScope ps("a6.up_apply", s);
             ps.flops = 8.0 * (Cv.sum_rd + Cv.sum_r2) * nc;
@@ -170,25 +193,37 @@ int sweep_chunk(fds_handle *h, int nc, cudaStream_t s) {
             FDS_TRY(dense_gemm(nb, Cv.rmax, nc, Vw::V(Cv), 0, rZ, 0, rT, one, zero, s));
             FDS_TRY(dense_gemm(nb, Cv.rmax, nc, Vw::At(Cv), 0, rT, 0, rF, one, zero, s));
         }
-        C *par = (l - 1 > l0) ? wz[l - 1].p : top;
+        C *par = (l - 1 > l0) ? wr[l - 1].p : top;
         const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
         fds_count_launch(), k_child_parent<C><<<nb, 256, 0, s>>>(nb, Cv.d_roff.p, Cv.d_k1.p, Cv.d_par_pos1.p,
                                                                  Cv.d_par_pos2.p, Pn.d_doff.p, F, ldr, par, ldp,
                                                                  nc, 0);
         FDS_CUDA_TRY(cudaGetLastError());
     }
-    // top
+    // top: dense LU solve in FP64 (the complex64 sweep converts its top vector
+    // to complex128 and back)
     {
-        MatRefT<C> tv;
-        tv.p = top;
+        const int64_t ldt = std::max<int64_t>(h->Dtop, 1);
+        MatRef tv;
+        tv.p = h->wtop.p;
         tv.rows = (int)h->Dtop;
         tv.cols = nc;
-        tv.ld = (int)std::max<int64_t>(h->Dtop, 1);
-        FDS_CUDA_TRY(cudaMemcpyAsync(rX, &tv, sizeof(tv), cudaMemcpyHostToDevice, s));
-        ProfScope ps("a6.top_solve", s);
-        ps.flops = 8.0 * (double)h->Dtop * h->Dtop * nc;
-        ps.bytes = esz * (double)h->Dtop * h->Dtop;
-        FDS_TRY(dense_lu_solve(1, (int)h->Dtop, nc, Vw::top(h), h->ptop.p, h->d_ptop_off.p, rX, s));
+        tv.ld = (int)ldt;
+        // MatRefT<cplxf> and MatRefT<cplx> have the same layout (pointer + 3 ints)
+        static_assert(sizeof(MatRefF) == sizeof(MatRef), "descriptor layouts differ");
+        MatRef *rX64 = reinterpret_cast<MatRef *>(rX);
+        if (sizeof(C) != sizeof(cplx))
+            fds_count_launch(), k_convert<C, cplx><<<256, 256, 0, s>>>(top, h->wtop.p, h->Dtop, ldt, ldt, nc);
+        FDS_CUDA_TRY(cudaMemcpyAsync(rX64, &tv, sizeof(tv), cudaMemcpyHostToDevice, s));
+        {
+            ProfScope ps("a6.top_solve", s);
+            ps.flops = 8.0 * (double)h->Dtop * h->Dtop * nc;
+            ps.bytes = 16.0 * (double)h->Dtop * h->Dtop;
+            FDS_TRY(dense_lu_solve(1, (int)h->Dtop, nc, h->rtop.p, h->ptop.p, h->d_ptop_off.p, rX64, s));
+        }
+        if (sizeof(C) != sizeof(cplx))
+            fds_count_launch(), k_convert<cplx, C><<<256, 256, 0, s>>>(h->wtop.p, top, h->Dtop, ldt, ldt, nc);
+        FDS_CUDA_TRY(cudaGetLastError());
     }
     // downward
     for (int l = l0 + 1; l <= L; ++l) {
@@ -218,8 +253,10 @@ int sweep_chunk(fds_handle *h, int nc, cudaStream_t s) {
 
 template int sweep_workspace<cplx>(fds_handle *, int);
 template int sweep_workspace<cplxf>(fds_handle *, int);
-template cplx *sweep_leaf_vector<cplx>(fds_handle *);
-template cplxf *sweep_leaf_vector<cplxf>(fds_handle *);
+template cplx *sweep_leaf_in<cplx>(fds_handle *);
+template cplxf *sweep_leaf_in<cplxf>(fds_handle *);
+template cplx *sweep_leaf_out<cplx>(fds_handle *);
+template cplxf *sweep_leaf_out<cplxf>(fds_handle *);
 template int sweep_chunk<cplx>(fds_handle *, int, cudaStream_t);
 template int sweep_chunk<cplxf>(fds_handle *, int, cudaStream_t);
 
@@ -231,7 +268,7 @@ int fds_solve_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
     const int ncmax = std::min(nrhs, SOLVE_CHUNK);
     FDS_TRY(sweep_workspace<cplx>(h, ncmax));
     const Level &Lf = h->lv[h->L];
-    cplx *leafv = sweep_leaf_vector<cplx>(h);
+    cplx *leaf_in = sweep_leaf_in<cplx>(h), *leaf_out = sweep_leaf_out<cplx>(h);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -239,10 +276,10 @@ int fds_solve_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
     for (int c0 = 0; c0 < nrhs; c0 += SOLVE_CHUNK) {
         const int nc = std::min(SOLVE_CHUNK, nrhs - c0);
         cplx *rhs = d_rhs + (int64_t)c0 * ld_rhs;
-        fds_count_launch(), k_leaf_gather<<<1024, 256, 0, s>>>(h->d_leaf_gidx.p, Lf.D, rhs, ld_rhs, leafv, nc, 0);
+        fds_count_launch(), k_leaf_gather<<<1024, 256, 0, s>>>(h->d_leaf_gidx.p, Lf.D, rhs, ld_rhs, leaf_in, nc, 0);
         FDS_CUDA_TRY(cudaGetLastError());
         FDS_TRY(sweep_chunk<cplx>(h, nc, s));
-        fds_count_launch(), k_leaf_gather<<<1024, 256, 0, s>>>(h->d_leaf_gidx.p, Lf.D, rhs, ld_rhs, leafv, nc, 1);
+        fds_count_launch(), k_leaf_gather<<<1024, 256, 0, s>>>(h->d_leaf_gidx.p, Lf.D, rhs, ld_rhs, leaf_out, nc, 1);
         FDS_CUDA_TRY(cudaGetLastError());
     }
     cudaEventRecord(e1, s);

@@ -24,6 +24,13 @@ FDS_ERR_TIMEOUT = -6
 FDS_ERR_STATE = -7
 FDS_FP64 = 0
 FDS_MIXED = 1
+FDS_APPLY_FF = 0
+FDS_APPLY_FP64 = 1
+FDS_RANK_ADAPTIVE = 0
+FDS_RANK_LEARNED = 1
+FDS_MLP_NIN = 16
+FDS_MLP_NTRAIN = 5313
+FDS_MLP_NPARAM = 5345
 
 
 class FdsError(RuntimeError):
@@ -47,14 +54,18 @@ class fds_options(ctypes.Structure):
                 ("proxy_points", ctypes.c_int32), ("top_level", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("alpha_re", ctypes.c_double), ("alpha_im", ctypes.c_double),
                 ("alpha_set", ctypes.c_int32), ("cuda_stream", ctypes.c_uint64), ("ir_tol", ctypes.c_double),
-                ("ir_max_iter", ctypes.c_int32)]
+                ("ir_max_iter", ctypes.c_int32), ("ir_apply", ctypes.c_int32), ("rank_mode", ctypes.c_int32),
+                ("mlp_params", ctypes.POINTER(ctypes.c_float)), ("sketch_extra", ctypes.c_int32),
+                ("record_features", ctypes.c_int32)]
 
 
 class fds_stats(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("levels", ctypes.c_int32), ("top_level", ctypes.c_int32),
                 ("top_size", ctypes.c_int32), ("skeleton_dofs", ctypes.c_int64 * 32),
                 ("max_rank", ctypes.c_int32 * 32), ("build_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
-                ("factor_bytes", ctypes.c_int64), ("ir_iters", ctypes.c_int32), ("ir_residual", ctypes.c_double)]
+                ("factor_bytes", ctypes.c_int64), ("ir_iters", ctypes.c_int32), ("ir_residual", ctypes.c_double),
+                ("id_sketched", ctypes.c_int64), ("id_fallback", ctypes.c_int64),
+                ("features_recorded", ctypes.c_int64)]
 
 
 _lib = None
@@ -98,9 +109,17 @@ def lib():
     L.fds_timing_report.restype = ctypes.c_int
     L.fds_launch_count.argtypes = []
     L.fds_launch_count.restype = ctypes.c_int64
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.fds_features_get.argtypes = [vp, fp, fp, i32]
+    L.fds_mlp_forward.argtypes = [vp, vp, i32, vp, u64]
+    L.fds_mlp_loss_grad.argtypes = [vp, vp, vp, i32, vp, vp, u64]
+    L.fds_mlp_adam.argtypes = [vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                               u64]
+    L.fds_mlp_train.argtypes = [vp, vp, vp, i32, vp, i32, i32, ctypes.c_float, vp, u64]
     for f in ("fds_build", "fds_build_ex", "fds_rhs_plane_wave", "fds_rhs_plane_wave_device", "fds_solve",
               "fds_solve_device", "fds_stats_get", "fds_level_ranks", "fds_eval_entries", "fds_eval_cross",
-              "fds_id_batched", "fds_lu_batched", "fds_lu_batched_noalloc"):
+              "fds_id_batched", "fds_lu_batched", "fds_lu_batched_noalloc", "fds_features_get", "fds_mlp_forward",
+              "fds_mlp_loss_grad", "fds_mlp_adam", "fds_mlp_train"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -163,7 +182,9 @@ class Handle:
 
 
 def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy_ratio=1.5, proxy_points=64,
-              alpha=None, stream=0, precision=FDS_FP64, ir_tol=None, ir_max_iter=None):
+              alpha=None, stream=0, precision=FDS_FP64, ir_tol=None, ir_max_iter=None, ir_apply=None,
+              mlp_params=None, sketch_extra=None, record_features=False):
+    """Factorise; mlp_params (FDS_MLP_NPARAM floats) selects the learned-rank ID."""
     xy = np.ascontiguousarray(xy, dtype=np.float64)
     g = fds_geometry(len(xy), xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(rho))
     o = default_options()
@@ -176,6 +197,18 @@ def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy
         o.ir_tol = ir_tol
     if ir_max_iter is not None:
         o.ir_max_iter = ir_max_iter
+    if ir_apply is not None:
+        o.ir_apply = ir_apply
+    prm = None
+    if mlp_params is not None:
+        prm = np.ascontiguousarray(mlp_params, dtype=np.float32)
+        if prm.size != FDS_MLP_NPARAM:
+            raise ValueError("mlp_params must hold %d floats" % FDS_MLP_NPARAM)
+        o.rank_mode = FDS_RANK_LEARNED
+        o.mlp_params = prm.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    if sketch_extra is not None:
+        o.sketch_extra = sketch_extra
+    o.record_features = 1 if record_features else 0
     out = ctypes.c_void_p()
     _check(lib().fds_build_ex(ctypes.byref(g), float(omega), float(lam), float(mu), float(tol), ctypes.byref(o),
                               ctypes.byref(out)), "fds_build")
@@ -219,6 +252,38 @@ def fds_stats_get(h):
     s = fds_stats()
     _check(lib().fds_stats_get(h.ptr, ctypes.byref(s)), "fds_stats_get")
     return s
+
+
+def fds_features_get(h):
+    """(features [rows, 16] float32, adaptive rank fractions [rows]) recorded by a
+    build with record_features=True."""
+    n = int(fds_stats_get(h).features_recorded)
+    feat = np.zeros((max(n, 1), FDS_MLP_NIN), dtype=np.float32)
+    frac = np.zeros(max(n, 1), dtype=np.float32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    got = _check(lib().fds_features_get(h.ptr, feat.ctypes.data_as(fp), frac.ctypes.data_as(fp), n),
+                 "fds_features_get")
+    return feat[:got], frac[:got]
+
+
+def fds_mlp_forward(d_params, d_X, d_y, stream=None):
+    _check(lib().fds_mlp_forward(_ptr(d_params), _ptr(d_X), d_X.shape[0], _ptr(d_y), _stream(stream)),
+           "fds_mlp_forward")
+
+
+def fds_mlp_loss_grad(d_params, d_X, d_t, d_grad, d_loss, stream=None):
+    _check(lib().fds_mlp_loss_grad(_ptr(d_params), _ptr(d_X), _ptr(d_t), d_X.shape[0], _ptr(d_grad), _ptr(d_loss),
+                                   _stream(stream)), "fds_mlp_loss_grad")
+
+
+def fds_mlp_adam(d_params, d_grad, d_m, d_v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().fds_mlp_adam(_ptr(d_params), _ptr(d_grad), _ptr(d_m), _ptr(d_v), int(step), float(lr), float(beta1),
+                              float(beta2), float(eps), _stream(stream)), "fds_mlp_adam")
+
+
+def fds_mlp_train(d_params, d_X, d_t, d_order, batch, lr, d_losses=None, stream=None):
+    _check(lib().fds_mlp_train(_ptr(d_params), _ptr(d_X), _ptr(d_t), d_X.shape[0], _ptr(d_order), d_order.numel(),
+                               int(batch), float(lr), _ptr(d_losses), _stream(stream)), "fds_mlp_train")
 
 
 def fds_level_ranks(h, level, nb):

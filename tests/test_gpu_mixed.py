@@ -58,7 +58,7 @@ def test_refinement_gains_over_plain_complex64_sweep():
     omega = workloads.omega_for_kTa(8.0)
     h64 = fds.fds_build(xy, omega, 2.0, 1.0, 1e-10, leaf_size=32)
     h0 = fds.fds_build(xy, omega, 2.0, 1.0, 1e-10, leaf_size=32, precision=fds.FDS_MIXED, ir_max_iter=0)
-    h2 = fds.fds_build(xy, omega, 2.0, 1.0, 1e-10, leaf_size=32, precision=fds.FDS_MIXED, ir_tol=1e-13,
+    h2 = fds.fds_build(xy, omega, 2.0, 1.0, 1e-10, leaf_size=32, precision=fds.FDS_MIXED, ir_tol=1e-11,
                        ir_max_iter=6)
     F = fds.fds_rhs_plane_wave(h64, np.array([0, 1], np.int32), np.array([0.4, 2.2]))
     x64 = fds.fds_solve(h64, F)
@@ -67,24 +67,26 @@ def test_refinement_gains_over_plain_complex64_sweep():
     assert fds.fds_stats_get(h0).ir_iters == 0
     assert fds.fds_stats_get(h0).ir_residual < 0          # not measured without refinement
     assert 1e-9 < e0 < 1e-3                               # complex64 sweep alone
-    assert e2 < 1e-11 and e2 < 1e-4 * e0
+    assert e2 < 1e-9 and e2 < 1e-3 * e0
     for h in (h64, h0, h2):
         h.close()
 
 
-@pytest.mark.parametrize("l0", [0, 1, 2])
-def test_mixed_exact_without_truncation(l0):
+@pytest.mark.parametrize("l0,apply,tol,bound", [(0, 0, 1e-11, 1e-9), (1, 0, 1e-11, 1e-9), (2, 0, 1e-11, 1e-9),
+                                                (0, 1, 1e-13, 1e-11), (1, 1, 1e-13, 1e-11), (2, 1, 1e-13, 1e-11)])
+def test_mixed_exact_without_truncation(l0, apply, tol, bound):
     # eps = 0: the compressed operator is A itself, so refinement converges
-    # to the dense solve
+    # to the dense solve (to the precision of the residual's arithmetic:
+    # double-float (apply 0) or FP64 (apply 1))
     torch_cuda()
     fds = fdslib()
     xy = workloads.star(256)
     h = fds.fds_build(xy, 3.0, 2.0, 1.0, 0.0, leaf_size=32, top_level=l0, precision=fds.FDS_MIXED,
-                      ir_tol=1e-13, ir_max_iter=8)
+                      ir_tol=tol, ir_max_iter=8, ir_apply=apply)
     P = bem.phys(2.0, 1.0, 1.0, 3.0)
     F = np.stack([bem.rhs(P, xy, 0, 0.3), bem.rhs(P, xy, 1, 1.9)], 1)
     xd = np.linalg.solve(bem.dense_matrix(P, xy), F)
-    assert _rel(fds.fds_solve(h, F), xd) < 1e-11
+    assert _rel(fds.fds_solve(h, F), xd) < bound
     h.close()
 
 
@@ -93,12 +95,12 @@ def test_mixed_single_cell():
     torch_cuda()
     fds = fdslib()
     xy = workloads.ellipse(40, 2.0, 0.3)
-    h = fds.fds_build(xy, 2.0, 2.0, 1.0, 1e-8, leaf_size=64, precision=fds.FDS_MIXED, ir_tol=1e-13)
+    h = fds.fds_build(xy, 2.0, 2.0, 1.0, 1e-8, leaf_size=64, precision=fds.FDS_MIXED, ir_tol=1e-11)
     assert fds.fds_stats_get(h).levels == 0
     P = bem.phys(2.0, 1.0, 1.0, 2.0)
     f = bem.rhs(P, xy, 1, 0.25)
     xd = np.linalg.solve(bem.dense_matrix(P, xy), f)
-    assert _rel(fds.fds_solve(h, f), xd) < 1e-11
+    assert _rel(fds.fds_solve(h, f), xd) < 1e-9
     h.close()
 
 

@@ -62,6 +62,29 @@ def random_cavities(count, seed=SEED + 2, nmin_log2=12, nmax_log2=15, kta=(1.0, 
     return out
 
 
+def mlp_init(seed=SEED + 5, nin=16, nh=64):
+    """Initial parameters of the learned-rank network (Glorot-uniform weights,
+    zero biases) followed by an identity input normalisation (mu 0, sd 1):
+    the flat layout W1, b1, W2, b2, w3, b3, mu, sd, float64."""
+    rng = np.random.default_rng(seed)
+
+    def glorot(fan_out, fan_in):
+        a = np.sqrt(6.0 / (fan_in + fan_out))
+        return rng.uniform(-a, a, (fan_out, fan_in))
+
+    parts = [glorot(nh, nin).ravel(), np.zeros(nh), glorot(nh, nh).ravel(), np.zeros(nh), glorot(1, nh).ravel(),
+             np.zeros(1), np.zeros(nin), np.ones(nin)]
+    return np.concatenate(parts)
+
+
+def minibatch_order(n, batch, epochs, seed=SEED + 6):
+    """Sample order of minibatch training: per epoch a seeded permutation of
+    range(n), truncated to whole batches."""
+    rng = np.random.default_rng(seed)
+    per = (n // batch) * batch
+    return np.concatenate([rng.permutation(n)[:per] for _ in range(epochs)]).astype(np.int32)
+
+
 def plane_wave_set(n_per_kind):
     """Alternating P (kind 0) and SV (kind 1) plane waves at uniform angles:
     returns (kinds[int32], angles[float64]) of length 2*n_per_kind."""
