@@ -8,8 +8,10 @@ vectors of all incident waves, and the multi-RHS solve sweep.
 Default workload (the configuration the metric is quoted on): star cavity
 r(t) = 1 + 0.2 cos 5t with 2^19 nodes (2^20 complex unknowns), lambda = 2,
 mu = 1, rho = 1, k_T a = 20, leaf 64, l0 = 1, 1000 right-hand sides (plane P
-and SV waves at 500 angles), mixed precision (complex64 sweep refined against
-the FP64 compressed operator to max_c ||f - A x|| / ||f|| <= 1e-8).  After the
+and SV waves at 500 angles), mixed precision (complex64 sweep of the lower
+tree levels refined against the FP64 compressed operator to
+max_c ||f - A x|| / ||f|| <= 1e-8), adaptive ID (`--rank learned` selects
+the trained rank network, `python -m paper_2411_18026_gb300.learned`).  After the
 timed steps one plain-FP64 step runs on the same inputs: its build and solve
 times and the relative error between the two solutions are reported beside
 the headline.  The working set (factors, vectors) is far larger than L2, so no
@@ -52,6 +54,15 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--ir-tol", type=float, default=1e-8)
+    p.add_argument("--sweep-fp64-levels", type=int, default=-1)
+    p.add_argument("--rank", default="adaptive", choices=["learned", "adaptive"],
+                   help="learned: the trained rank network (falls back to adaptive if it has not been trained); "
+                        "its skeletons differ from the plain solver's, so its error against the plain FP64 "
+                        "solve is the compression error amplified by the operator's conditioning")
+    p.add_argument("--workload", default="star", choices=["star", "batch64"],
+                   help="star: the 2^19-node star cavity (default); batch64: 64 seeded cavities of "
+                        "2^12-2^15 nodes, k_T a in [1, 20], 16 waves each, built and solved as one batch")
+    p.add_argument("--streams", type=int, default=8, help="batch64: concurrent cavity streams")
     p.add_argument("--no-compare", action="store_true",
                    help="skip the plain-FP64 comparison step (error and timings of the FP64 solver)")
     return p.parse_args()
@@ -191,6 +202,73 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------- batched cavities
+def run_batch(args, fds, torch, world, rank, local):
+    """64 seeded cavities (ellipses / stars, 2^12..2^15 nodes, k_T a in [1, 20],
+    eps 1e-8, leaf 64) built with fds_build_batch on --streams concurrent
+    streams, 16 plane waves each (8 P + 8 SV), solved with fds_solve_batch.
+    One step = batch build + load vectors + batch solve; after the timed
+    steps the same work one cavity at a time (1 stream) is timed once for
+    comparison."""
+    import workloads
+    cav = workloads.random_cavities(64, seed=workloads.SEED + 2 + 97 * rank)
+    for c in cav:
+        c["omega"] = workloads.omega_for_kTa(c["kTa"])
+    kinds, angles = workloads.plane_wave_set(8)
+    d_k = torch.from_numpy(kinds).cuda()
+    d_a = torch.from_numpy(angles).cuda()
+    d_F = [torch.empty((16, 2 * c["N"]), dtype=torch.complex128, device="cuda") for c in cav]
+    eps = 1e-8
+    prec = fds.FDS_MIXED if args.precision == "mixed" else fds.FDS_FP64
+
+    def step(streams):
+        hs = fds.fds_build_batch(cav, 2.0, 1.0, eps, n_streams=streams, leaf_size=args.leaf, precision=prec)
+        for h, F in zip(hs, d_F):
+            fds.fds_rhs_plane_wave_device(h, d_k, d_a, F, fds.fds_handle_stream(h))
+        fds.fds_solve_batch(hs, d_F, n_streams=streams)
+        for h in hs:
+            h.close()
+
+    for _ in range(args.warmup):
+        step(args.streams)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = fds.fds_launch_count()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(args.streams)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    launches = (fds.fds_launch_count() - launches0) // args.steps
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    t1 = time.perf_counter()
+    step(1)
+    torch.cuda.synchronize()
+    seq_ms = (time.perf_counter() - t1) * 1e3
+    if rank != 0:
+        return
+    nodes = sum(c["N"] for c in cav)
+    line = {"metric": "batched build + solve of 64 cavities (s per batch)", "value": ms / 1e3, "unit": "s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128+c64" if prec == fds.FDS_MIXED else "c128", "data": "synthetic",
+            "config": {"workload": "64 seeded cavities (ellipse aspect 1-4 / star e in [0,0.3], m in 3..8), "
+                                   "2^12-2^15 nodes (%d in total), k_T a in [1,20], eps 1e-8, leaf %d, "
+                                   "16 plane waves each, %d streams" % (nodes, args.leaf, args.streams),
+                       "timing": "host wall clock around the whole batch (several streams), synchronised"},
+            "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / ms, "gpu_launches": int(launches),
+            "clocks": clk}
+    print(json.dumps(line))
+
+
 # ---------------------------------------------------------------- ours
 def main():
     args = parse()
@@ -206,6 +284,9 @@ def main():
     import __graft_entry__ as g
     g.build()
     from paper_2411_18026_gb300 import fds
+    if args.workload == "batch64":
+        run_batch(args, fds, torch, world, rank, local)
+        return
 
     xy, omega, kinds, angles = workload(args, rank)
     N = len(xy)
@@ -217,10 +298,14 @@ def main():
     info = {}
 
     prec = fds.FDS_MIXED if args.precision == "mixed" else fds.FDS_FP64
+    from paper_2411_18026_gb300 import learned
+    mlp = learned.load_params() if args.rank == "learned" else None
+    rank_used = "learned" if mlp is not None else "adaptive"
 
-    def step(precision=prec, out=d_F, rec=info):
+    def step(precision=prec, out=d_F, rec=info, params=mlp):
         h = fds.fds_build(xy, omega, 2.0, 1.0, args.eps, leaf_size=args.leaf, top_level=args.top, stream=stream,
-                          precision=precision, ir_tol=args.ir_tol)
+                          precision=precision, ir_tol=args.ir_tol, sweep_fp64_levels=args.sweep_fp64_levels,
+                          mlp_params=params)
         fds.fds_rhs_plane_wave_device(h, d_kinds, d_angles, out, stream)
         rec["converged"] = True
         try:
@@ -235,6 +320,7 @@ def main():
         rec["factor_gb"] = st.factor_bytes / 1e9
         rec["skeleton_dofs"] = [int(st.skeleton_dofs[l]) for l in range(st.levels + 1)]
         rec["ir_iters"], rec["ir_residual"] = st.ir_iters, st.ir_residual
+        rec["id_sketched"], rec["id_fallback"] = st.id_sketched, st.id_fallback
         h.close()
 
     for _ in range(args.warmup):
@@ -278,7 +364,7 @@ def main():
         c0 = torch.cuda.Event(enable_timing=True)
         c1 = torch.cuda.Event(enable_timing=True)
         c0.record(stream)
-        step(fds.FDS_FP64, d_F64, rec)
+        step(fds.FDS_FP64, d_F64, rec, None)
         c1.record(stream)
         torch.cuda.synchronize()
         num = torch.linalg.vector_norm(d_F - d_F64, dim=1)
@@ -305,7 +391,12 @@ def main():
         g_ = fds.fds_geometry(N, xy_host.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1.0)
         o = fds.default_options()
         o.leaf_size, o.top_level = args.leaf, args.top
-        o.precision, o.ir_tol = prec, args.ir_tol
+        o.precision, o.ir_tol, o.sweep_fp64_levels = prec, args.ir_tol, args.sweep_fp64_levels
+        mlp32 = None
+        if mlp is not None:
+            mlp32 = np.ascontiguousarray(mlp, dtype=np.float32)
+            o.rank_mode = fds.FDS_RANK_LEARNED
+            o.mlp_params = mlp32.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         out = ctypes.c_void_p()
         rc = L.fds_build_ex(ctypes.byref(g_), float(omega), 2.0, 1.0, float(args.eps), ctypes.byref(o),
                             ctypes.byref(out))
@@ -323,6 +414,12 @@ def main():
             torch.distributed.destroy_process_group()
         return
 
+    # FP64 flops and DRAM bytes per quadrature point of the kernel-evaluation
+    # kernels, from ncu counters (dfma x 2 + dmul + dadd; dram read + write)
+    # over all launches of one 2^14-node build of the same cavity
+    # (profiles/k_tiles_fp64_ops_star_2p14.md)
+    A1_PER_POINT = {"a1.leaf_blocks": (564.0, 0.66), "a1.near_rows": (630.0, 1.05), "a1.proxy_rows": (630.0, 1.05),
+                    "a1.sibling_blocks": (617.0, 0.11), "a1.top_blocks": (617.0, 0.11)}
     pk, src = peaks()
     sm_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     # FP64 peak of the GB300: 152 SMs x 2 FP64 FMA/clk (4 flops) x SM clock
@@ -331,18 +428,21 @@ def main():
     roof = None
     if dom:
         name, d = dom
-        avg_ms = d["ms"] / max(d["launches"], 1)
-        if d["flops"] > 0:
-            ach = d["flops"] / max(d["launches"], 1) / (avg_ms / 1e3) / 1e12
-            roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                    "frac": ach / fp64_peak_tflops, "traffic": None,
-                    "peak_source": "FP64 152 SM x 4 flop/clk x %.0f MHz (max clock)" % pk.get("sm_max_mhz", 2070.0),
-                    "avg_launch_ms": avg_ms, "launches_per_step": d["launches"] / args.steps}
-        else:
-            roof = {"kernel": name, "bound": "alu", "achieved": None, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                    "frac": None, "traffic": None, "avg_launch_ms": avg_ms,
-                    "launches_per_step": d["launches"] / args.steps,
-                    "note": "quadrature phase: see the profiles summary for its FP64 instruction rate"}
+        launches_ = max(d["launches"], 1)
+        avg_ms = d["ms"] / launches_
+        flops, traffic, basis = d["flops"], None, "library flop count of the phase"
+        if name in A1_PER_POINT and d["units"] > 0:
+            fpp, bpp = A1_PER_POINT[name]
+            flops = d["units"] * fpp
+            traffic = d["units"] * bpp / launches_
+            basis = ("quadrature points x %.0f FP64 flops per point (ncu, 2^14 case); traffic = points per launch x "
+                     "%.2f DRAM bytes per point (same capture)" % (fpp, bpp))
+        ach = flops / launches_ / (avg_ms / 1e3) / 1e12 if flops > 0 else None
+        roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                "frac": (ach / fp64_peak_tflops) if ach else None, "traffic": traffic,
+                "peak_source": "FP64: 152 SMs x 2 FP64 FMA/clk x %.0f MHz (no FP64 figure in MEASURED_PEAKS.json)"
+                               % pk.get("sm_max_mhz", 2070.0),
+                "basis": basis, "avg_launch_ms": avg_ms, "launches_per_step": d["launches"] / args.steps}
 
     cpu = None
     if not args.no_cpu:
@@ -360,17 +460,20 @@ def main():
         "config": {"workload": "star r=1+0.2cos5t, %d nodes (%d complex unknowns), lambda=2 mu=1 rho=1, "
                                "k_T a=%g, leaf %d, l0=%d, eps=%g, %d plane P/SV waves, %s"
                                % (N, 2 * N, args.kta, args.leaf, args.top, args.eps, args.nrhs,
-                                  "mixed precision, refined to residual %g" % args.ir_tol
-                                  if args.precision == "mixed" else "plain FP64"),
+                                  ("mixed precision, refined to residual %g" % args.ir_tol
+                                   if args.precision == "mixed" else "plain FP64") + ", %s rank" % rank_used),
                    "l2": "working set (factors, vectors) larger than L2; no flush",
                    "precision": args.precision},
         "ir_iters": info.get("ir_iters"), "ir_residual": info.get("ir_residual"),
-        "ir_converged": info.get("converged"), "vs_fp64": compare,
+        "ir_converged": info.get("converged"), "vs_fp64": compare, "rank_mode": rank_used,
+        "id_sketched": info.get("id_sketched"), "id_fallback": info.get("id_fallback"),
         "build_s": build_s, "per_rhs_us": per_rhs_us,
         "levels": info.get("levels"), "top_size": info.get("top_size"), "factor_gb": info.get("factor_gb"),
         "skeleton_dofs": info.get("skeleton_dofs"),
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
         "phases_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in sorted(phases.items())},
+        "phases_tflops": {k: round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 3) for k, v in sorted(phases.items())
+                          if v["flops"] > 0 and v["ms"] > 0},
         "quad_points_per_step": {k: v["units"] / args.steps for k, v in sorted(phases.items()) if v["units"] > 0},
     }
     print(json.dumps(line))

@@ -53,9 +53,9 @@ extern "C" {
 /* Skeleton selection (Sec. 7.2): adaptive CPQR on the stacked proxy matrix,
  * or (extension, not in the paper) a rank predicted by the learned network
  * from geometry features, a sparse-sign sketch of the proxy matrix with
- * (predicted rank + oversampling) rows, CPQR of the sketch, and a residual
- * check on sampled proxy rows; cells that fail the check fall back to the
- * adaptive CPQR. */
+ * (predicted rank + sketch_extra) rows, CPQR of the sketch, and a check of
+ * the ID residual on the whole proxy matrix against the adaptive CPQR's own
+ * bound; cells that fail the check fall back to the adaptive CPQR. */
 #define FDS_RANK_ADAPTIVE 0
 #define FDS_RANK_LEARNED  1
 /* Learned-rank network: 16 -> 64 -> 64 -> 1, tanh, FP32.  Parameter vector:
@@ -99,6 +99,10 @@ typedef struct {
     int32_t ir_apply;      /* FDS_MIXED: arithmetic of the forward operator in the residual:
                               FDS_APPLY_FF (default) double-float products and sums on the
                               FP32 pipe (about 44 significant bits), FDS_APPLY_FP64 FP64 */
+    int32_t sweep_fp64_levels; /* FDS_MIXED: tree levels below the top whose sweep factors stay
+                              complex128 (the rest are complex64; the rounding error of the
+                              complex64 sweep comes mostly from the upper levels); -1 (default):
+                              the levels with at most 1/8 of the leaf level's DOFs */
     int32_t rank_mode;     /* FDS_RANK_ADAPTIVE (default) or FDS_RANK_LEARNED */
     const float *mlp_params; /* FDS_RANK_LEARNED: host, FDS_MLP_NPARAM floats, copied at the call */
     int32_t sketch_extra;  /* FDS_RANK_LEARNED: sketch rows beyond the predicted rank; default 12 */
@@ -179,6 +183,10 @@ int fds_stats_get(const fds_handle *h, fds_stats *s);
 int fds_level_ranks(const fds_handle *h, int32_t level, int32_t *k, int32_t cap);
 void fds_destroy(fds_handle *h);   /* NULL-safe; frees every device buffer of h */
 const char *fds_error_string(int code);
+/* The CUDA error name, message and source location behind the last
+ * FDS_ERR_CUDA / FDS_ERR_OOM returned to the calling thread ("" if none);
+ * valid until the thread's next failing call. */
+const char *fds_last_error_detail(void);
 
 /*
  * Per-phase device timing: when enabled, the library brackets its kernel
@@ -302,6 +310,27 @@ int fds_mlp_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, i
                  float beta1, float beta2, float eps, uint64_t stream);
 int fds_mlp_train(float *d_params, const float *d_X, const float *d_t, int32_t n, const int32_t *d_order,
                   int32_t n_order, int32_t batch, float lr, float *d_losses, uint64_t stream);
+
+/*
+ * Batched cavities (extension: many independent scatterers in one call).
+ * fds_build_batch: count cavities (geometry g[i], angular frequency omega[i];
+ * lambda, mu, tol and options shared, options.cuda_stream ignored) are built
+ * concurrently by n_streams (1..64) host threads, each cavity on a stream
+ * created for and owned by its handle (largest cavities first).  out[i]
+ * receives cavity i's handle (release each with fds_destroy).  On any error
+ * every handle of the batch is destroyed, out[] is cleared, and the first
+ * error in cavity order is returned.
+ * fds_solve_batch: solves d_rhs[i] (device, 2 n_i x nrhs[i], in place) with
+ * handle h[i] on the handle's stream, n_streams threads; returns after all
+ * solves have finished.
+ * fds_handle_stream: the stream a handle runs on (its own for batched
+ * handles), for enqueueing right-hand-side assembly on it.
+ */
+int fds_build_batch(int32_t count, const fds_geometry *g, const double *omega, double lambda, double mu,
+                    double tol, const fds_options *opt, int32_t n_streams, fds_handle **out);
+int fds_solve_batch(int32_t count, fds_handle *const *h, double *const *d_rhs, const int32_t *nrhs,
+                    int32_t n_streams);
+uint64_t fds_handle_stream(const fds_handle *h);
 
 #ifdef __cplusplus
 }

@@ -7,6 +7,8 @@
 
 #include "fds_internal.cuh"
 
+thread_local cudaStream_t g_alloc_stream = 0;
+
 extern "C" void fds_default_options(fds_options *o) {
     if (!o) return;
     o->leaf_size = 64;
@@ -21,6 +23,7 @@ extern "C" void fds_default_options(fds_options *o) {
     o->ir_tol = 1e-9;
     o->ir_max_iter = 10;
     o->ir_apply = FDS_APPLY_FF;
+    o->sweep_fp64_levels = -1;
     o->rank_mode = FDS_RANK_ADAPTIVE;
     o->mlp_params = nullptr;
     o->sketch_extra = 12;
@@ -41,8 +44,17 @@ extern "C" const char *fds_error_string(int code) {
     }
 }
 
-extern "C" int fds_build_ex(const fds_geometry *g, double omega, double lambda, double mu, double tol,
-                            const fds_options *opt, fds_handle **out) {
+// Build one handle; owned != 0: the handle takes ownership of that stream and
+// runs on it (batched builds), otherwise it runs on opt->cuda_stream.
+int fds_build_owned(const fds_geometry *g, double omega, double lambda, double mu, double tol,
+                    const fds_options *opt, cudaStream_t owned, fds_handle **out) {
+    // the stream is owned from here on: destroyed on every early return
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() {
+            if (s) cudaStreamDestroy(s);
+        }
+    } guard{owned};
     if (!out) return FDS_ERR_ARG;
     *out = nullptr;
     if (!g || !g->xy || g->n_nodes < 8) return FDS_ERR_ARG;
@@ -54,7 +66,7 @@ extern "C" int fds_build_ex(const fds_geometry *g, double omega, double lambda, 
         (o.precision != FDS_FP64 && o.precision != FDS_MIXED) || !(o.ir_tol >= 0.0) || o.ir_max_iter < 0 ||
         o.ir_max_iter > 100 || (o.ir_apply != FDS_APPLY_FF && o.ir_apply != FDS_APPLY_FP64) ||
         (o.rank_mode != FDS_RANK_ADAPTIVE && o.rank_mode != FDS_RANK_LEARNED) ||
-        (o.rank_mode == FDS_RANK_LEARNED && !o.mlp_params) || o.sketch_extra < 1 || o.sketch_extra > 64)
+        (o.rank_mode == FDS_RANK_LEARNED && !o.mlp_params) || o.sketch_extra < 1 || o.sketch_extra > 64 || o.sweep_fp64_levels < -1)
         return FDS_ERR_ARG;
     for (int i = 0; i < 2 * g->n_nodes; ++i)
         if (!std::isfinite(g->xy[i])) return FDS_ERR_ARG;
@@ -66,6 +78,8 @@ extern "C" int fds_build_ex(const fds_geometry *g, double omega, double lambda, 
     }
     fds_handle *h = new (std::nothrow) fds_handle();
     if (!h) return FDS_ERR_OOM;
+    h->owned.s = owned;
+    guard.s = 0;
     h->N = g->n_nodes;
     h->xy.assign(g->xy, g->xy + 2 * (size_t)g->n_nodes);
     h->ph.lambda = lambda;
@@ -78,7 +92,8 @@ extern "C" int fds_build_ex(const fds_geometry *g, double omega, double lambda, 
     h->P = make_physdev(&h->ph);
     h->tol = tol;
     h->opt = o;
-    h->stream = (cudaStream_t)o.cuda_stream;
+    h->stream = owned ? owned : (cudaStream_t)o.cuda_stream;
+    if (owned) h->opt.cuda_stream = (uint64_t)owned;
     if (o.rank_mode == FDS_RANK_LEARNED) {
         for (int i = 0; i < FDS_MLP_NPARAM; ++i)
             if (!std::isfinite(o.mlp_params[i])) {
@@ -101,6 +116,11 @@ extern "C" int fds_build_ex(const fds_geometry *g, double omega, double lambda, 
     }
     *out = h;
     return FDS_OK;
+}
+
+extern "C" int fds_build_ex(const fds_geometry *g, double omega, double lambda, double mu, double tol,
+                            const fds_options *opt, fds_handle **out) {
+    return fds_build_owned(g, omega, lambda, mu, tol, opt, 0, out);
 }
 
 extern "C" int fds_build(const fds_geometry *g, double omega, double lambda, double mu, double tol,

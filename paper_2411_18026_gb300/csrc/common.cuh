@@ -102,10 +102,18 @@ struct GaussTables {
 static __constant__ GaussTables c_gauss;
 int gauss_tables_host(GaussTables *T);   // fills the host copy (kernel_eval.cu)
 
+// Records the failing CUDA call of this thread (fds_last_error_detail).
+void fds_note_cuda_error(cudaError_t e, const char *file, int line);
+void fds_set_error_detail(const char *msg);
+extern "C" const char *fds_last_error_detail(void);
+
 #define FDS_CUDA_TRY(expr)                                                   \
     do {                                                                     \
         cudaError_t _e = (expr);                                             \
-        if (_e != cudaSuccess) return (_e == cudaErrorMemoryAllocation) ? FDS_ERR_OOM : FDS_ERR_CUDA; \
+        if (_e != cudaSuccess) {                                             \
+            fds_note_cuda_error(_e, __FILE__, __LINE__);                     \
+            return (_e == cudaErrorMemoryAllocation) ? FDS_ERR_OOM : FDS_ERR_CUDA; \
+        }                                                                    \
     } while (0)
 
 #define FDS_TRY(expr)                \
@@ -118,6 +126,23 @@ int gauss_tables_host(GaussTables *T);   // fills the host copy (kernel_eval.cu)
 void fds_count_launch();
 
 static inline unsigned ceil_div_u(long a, long b) { return (unsigned)((a + b - 1) / b); }
+
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`, never
+// lowering it: the attribute is process-wide, so concurrent callers (batched
+// builds on several host threads) that each set their own size would
+// otherwise shrink it under another's launch.
+size_t &dyn_smem_slot(const void *kernel);   // per-kernel current limit (prof.cu), under the lock below
+std::mutex &dyn_smem_mutex();
+
+template <class K>
+int ensure_dyn_smem(K kernel, size_t bytes) {
+    std::lock_guard<std::mutex> lk(dyn_smem_mutex());
+    size_t &cur = dyn_smem_slot((const void *)kernel);
+    if (bytes <= cur) return FDS_OK;
+    FDS_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+    return FDS_OK;
+}
 
 // Upload this translation unit's Gauss table once per device.
 static inline int ensure_gauss_tables() {

@@ -210,8 +210,7 @@ static int lu_solve_t(int batch, int max_rows, int max_cols, const MatRefT<C> *d
     if (rt > 32) rt = 32;
     if (rt < 1) return FDS_ERR_ARG;
     size_t smem = (size_t)max_rows * rt * sizeof(C);
-    if (smem > 48 * 1024)
-        FDS_CUDA_TRY(cudaFuncSetAttribute(k_lu_solve<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FDS_TRY(ensure_dyn_smem(k_lu_solve<C>, smem));
     dim3 grid((max_cols + rt - 1) / rt, batch);
     fds_count_launch(), k_lu_solve<C><<<grid, SOLVE_THREADS, smem, s>>>(d_LU, d_piv, d_poff, d_B, rt);
     FDS_CUDA_TRY(cudaGetLastError());

@@ -35,6 +35,12 @@ int dense_gemm_rt(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, 
 // FP32 pipe (about 44 significant bits; see gemm.cu).
 int dense_gemm_ff(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, const MatRef *d_C,
                   cplx alpha, cplx beta, cudaStream_t s);
+// Same with operands already split into float pairs (float4 = re_hi, im_hi,
+// re_lo, im_lo per complex entry) and a float-pair result; C = op(A) B
+// (+ C when accumulate).
+typedef MatRefT<float4> MatRefP;
+int dense_gemm_ffp(int batch, int max_m, int max_n, const MatRefP *d_A, int opA, const MatRefP *d_B,
+                   const MatRefP *d_C, int accumulate, cudaStream_t s);
 // complex64 versions (mixed-precision sweep)
 int dense_lu_solve(int batch, int max_rows, int max_cols, const MatRefF *d_LU, const int *d_piv,
                    const int64_t *d_poff, const MatRefF *d_B, cudaStream_t s);

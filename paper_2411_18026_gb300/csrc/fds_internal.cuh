@@ -6,35 +6,56 @@
 #include "common.cuh"
 #include "dense.cuh"
 
+// Stream that DBuf allocations of the calling thread are ordered on.  0 (the
+// default): plain cudaMalloc / cudaFree.  A batched build sets it, per worker
+// thread, to the stream its handle owns: allocation and release are then
+// stream-ordered (cudaMallocAsync / cudaFreeAsync), so concurrent builds on
+// different streams do not synchronise the device at every release; the
+// owned stream outlives every buffer of the handle.
+extern thread_local cudaStream_t g_alloc_stream;
+
+struct AllocStreamScope {
+    cudaStream_t prev;
+    explicit AllocStreamScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+    ~AllocStreamScope() { g_alloc_stream = prev; }
+};
+
 // Device buffer owned by the handle (freed in the destructor).
 template <class T>
 struct DBuf {
     T *p = nullptr;
     size_t n = 0;
+    cudaStream_t st = 0;   // stream the buffer was allocated on (and is freed on)
     DBuf() = default;
     DBuf(const DBuf &) = delete;
     DBuf &operator=(const DBuf &) = delete;
-    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n), st(o.st) { o.p = nullptr; o.n = 0; }
     DBuf &operator=(DBuf &&o) noexcept {
         if (this != &o) {
             release();
-            p = o.p; n = o.n;
+            p = o.p; n = o.n; st = o.st;
             o.p = nullptr; o.n = 0;
         }
         return *this;
     }
     ~DBuf() { release(); }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (st) cudaFreeAsync(p, st);
+            else cudaFree(p);
+        }
         p = nullptr;
         n = 0;
     }
     int alloc(size_t count) {
         release();
         if (count == 0) count = 1;
-        cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+        st = g_alloc_stream;
+        cudaError_t e = st ? cudaMallocAsync((void **)&p, count * sizeof(T), st)
+                           : cudaMalloc((void **)&p, count * sizeof(T));
         if (e != cudaSuccess) {
             p = nullptr;
+            cudaGetLastError();
             return e == cudaErrorMemoryAllocation ? FDS_ERR_OOM : FDS_ERR_CUDA;
         }
         n = count;
@@ -87,12 +108,27 @@ struct Level {
     DBuf<cplxf> Ainvf, Wf, Atf, Vf;
     DBuf<MatRefF> rAinvf, rWf, rAtf, rVf;
     // --- FP64 compressed forward operator: leaf diagonal blocks (leaf level)
-    //     and sibling-coupling blocks S (levels that are parents), both d x d
+    //     and sibling-coupling blocks S (levels that are parents), both d x d;
+    //     as float pairs (float4 per entry) when the residual runs double-float
     DBuf<cplx> Dfw, Sfw;
     DBuf<MatRef> rDfw, rSfw;
+    DBuf<float4> Dp, Sp, Vp;
+    DBuf<MatRefP> rDp, rSp, rVp;
+};
+
+// A stream created for (and destroyed after) one handle.
+struct OwnedStream {
+    cudaStream_t s = 0;
+    ~OwnedStream() {
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    }
 };
 
 struct fds_handle {
+    OwnedStream owned;      // first member: destroyed after every buffer below
     int N = 0;
     fds_physics ph{};
     PhysDev P{};
@@ -116,11 +152,17 @@ struct fds_handle {
     // mixed precision: off-diagonal top blocks (FP64 forward operator)
     DBuf<cplx> Atop_off;
     DBuf<MatRef> rtop_off;
+    DBuf<float4> Atop_offp;
+    DBuf<MatRefP> rtop_offp;
     // solve workspace (grown on demand)
     std::vector<DBuf<cplx>> wz, wf, wt, wy, wr;
     std::vector<DBuf<cplxf>> wzf, wff, wtf, wrf;
     DBuf<cplx> wtop, wytop, wX;
-    DBuf<cplxf> wtopf;
+    DBuf<cplxf> wtopf;   // complex64 top vector (boundary of the mixed sweep)
+    // forward-apply vectors as float pairs
+    std::vector<DBuf<float4>> wzp, wtp, wyp;
+    DBuf<float4> wtopp, wytopp, wXp;
+    DBuf<MatRefP> wrefsp;
     DBuf<MatRef> wrefs;
     DBuf<MatRefF> wrefsf;
     DBuf<double> wnorm;

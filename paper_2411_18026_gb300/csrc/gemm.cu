@@ -12,8 +12,8 @@
 //            products and sums in double-float arithmetic on the FP32 pipe:
 //            a x = ah xh + (err(ah xh) + ah xl + al xh) with err() from one
 //            FMA (Dekker's product), accumulation by Knuth's TwoSum; about
-//            44 bits of significand at 1/5 the FP32 rate, against 1/64 for
-//            FP64 on this GPU.
+//            44 bits of significand at 48 FP32 instructions per complex
+//            multiply-add, against FP64 at 1/64 of the FP32 rate on this GPU.
 #include "dense.cuh"
 
 namespace {
@@ -23,13 +23,15 @@ constexpr int BM = 64, BK = 16, NT = 256;
 // ---------------------------------------------------------------- arithmetics
 struct Arith64 {
     typedef cplxf G;      // global element
-    typedef cplxf S;      // staged element
+    typedef cplxf SA;     // staged element of op(A)
+    typedef cplxf SB;     // staged element of B
     typedef cplxf Acc;
-    __device__ static S stage(G v) { return v; }
-    __device__ static S szero() { return mkcf(0.f, 0.f); }
+    __device__ static SA stage_a(G v, bool cj) { return cj ? cconj(v) : v; }
+    __device__ static SB stage_b(G v) { return v; }
+    __device__ static SA za() { return mkcf(0.f, 0.f); }
+    __device__ static SB zb() { return mkcf(0.f, 0.f); }
     __device__ static void zero(Acc &a) { a = mkcf(0.f, 0.f); }
-    __device__ static S conj(S v) { return cconj(v); }
-    __device__ static void mac(Acc &c, const S &a, const S &b) { cfma(c, a, b); }
+    __device__ static void mac(Acc &c, const SA &a, const SB &b) { cfma(c, a, b); }
     __device__ static G finish(const Acc &c, G alpha, G beta, const G *old) {
         G r = cmul(alpha, c);
         if (old) r = cadd(r, cmul(beta, *old));
@@ -39,13 +41,15 @@ struct Arith64 {
 
 struct Arith128 {
     typedef cplx G;
-    typedef cplx S;
+    typedef cplx SA;
+    typedef cplx SB;
     typedef cplx Acc;
-    __device__ static S stage(G v) { return v; }
-    __device__ static S szero() { return mkc(0.0, 0.0); }
+    __device__ static SA stage_a(G v, bool cj) { return cj ? cconj(v) : v; }
+    __device__ static SB stage_b(G v) { return v; }
+    __device__ static SA za() { return mkc(0.0, 0.0); }
+    __device__ static SB zb() { return mkc(0.0, 0.0); }
     __device__ static void zero(Acc &a) { a = mkc(0.0, 0.0); }
-    __device__ static S conj(S v) { return cconj(v); }
-    __device__ static void mac(Acc &c, const S &a, const S &b) { cfma(c, a, b); }
+    __device__ static void mac(Acc &c, const SA &a, const SB &b) { cfma(c, a, b); }
     __device__ static G finish(const Acc &c, G alpha, G beta, const G *old) {
         G r = cmul(alpha, c);
         if (old) r = cadd(r, cmul(beta, *old));
@@ -53,13 +57,16 @@ struct Arith128 {
     }
 };
 
-// float pair: value = h + l, |l| <= ulp(h)/2
-struct ffc {
-    float rh, ih, rl, il;
+// float pair h + l of a double (|l| <= ulp(h)/2)
+struct ff {
+    float h, l;
 };
-struct ffacc {
-    float rh, rl, ih, il;
-};
+__device__ __forceinline__ ff split(double v) {
+    ff r;
+    r.h = (float)v;
+    r.l = (float)(v - (double)r.h);
+    return r;
+}
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = a + b;
@@ -67,47 +74,79 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
-// acc += x y (x = xh + xl, y = yh + yl; the xl yl term is below the pair's precision)
-__device__ __forceinline__ void ff_mac(float &sh, float &sl, float xh, float xl, float yh, float yl) {
-    const float ph = xh * yh;
-    const float pl = fmaf(xh, yl, fmaf(xl, yh, fmaf(xh, yh, -ph)));
+// acc += x y (the xl yl term is below the pair's precision)
+__device__ __forceinline__ void ff_mac(ff &acc, const ff &x, const ff &y) {
+    const float ph = x.h * y.h;
+    const float pl = fmaf(x.h, y.l, fmaf(x.l, y.h, fmaf(x.h, y.h, -ph)));
     float s, e;
-    two_sum(sh, ph, s, e);
-    sh = s;
-    sl += e + pl;
+    two_sum(acc.h, ph, s, e);
+    acc.h = s;
+    acc.l += e + pl;
 }
 
+// complex multiply-add in double-float: four real products
 struct ArithFF {
     typedef cplx G;
-    typedef ffc S;
-    typedef ffacc Acc;
-    __device__ static S stage(G v) {
-        S r;
-        r.rh = (float)v.x;
-        r.rl = (float)(v.x - (double)r.rh);
-        r.ih = (float)v.y;
-        r.il = (float)(v.y - (double)r.ih);
-        return r;
-    }
-    __device__ static S szero() { return S{0.f, 0.f, 0.f, 0.f}; }
-    __device__ static void zero(Acc &a) { a = Acc{0.f, 0.f, 0.f, 0.f}; }
-    __device__ static S conj(S v) {
-        v.ih = -v.ih;
-        v.il = -v.il;
-        return v;
-    }
-    __device__ static void mac(Acc &c, const S &a, const S &b) {
-        // re += ar br - ai bi ; im += ar bi + ai br
-        ff_mac(c.rh, c.rl, a.rh, a.rl, b.rh, b.rl);
-        ff_mac(c.rh, c.rl, -a.ih, -a.il, b.ih, b.il);
-        ff_mac(c.ih, c.il, a.rh, a.rl, b.ih, b.il);
-        ff_mac(c.ih, c.il, a.ih, a.il, b.rh, b.rl);
+    struct SA {
+        ff re, im;
+    };
+    typedef SA SB;
+    struct Acc {
+        ff re, im;
+    };
+    __device__ static SA stage_a(G v, bool cj) { return SA{split(v.x), split(cj ? -v.y : v.y)}; }
+    __device__ static SB stage_b(G v) { return SB{split(v.x), split(v.y)}; }
+    __device__ static SA za() { return SA{{0.f, 0.f}, {0.f, 0.f}}; }
+    __device__ static SB zb() { return SB{{0.f, 0.f}, {0.f, 0.f}}; }
+    __device__ static void zero(Acc &a) { a = Acc{{0.f, 0.f}, {0.f, 0.f}}; }
+    __device__ static void mac(Acc &c, const SA &a, const SB &b) {
+        const ff nai{-a.im.h, -a.im.l};
+        ff_mac(c.re, a.re, b.re);
+        ff_mac(c.re, nai, b.im);
+        ff_mac(c.im, a.re, b.im);
+        ff_mac(c.im, a.im, b.re);
     }
     __device__ static G finish(const Acc &c, G alpha, G beta, const G *old) {
-        const G v = mkc((double)c.rh + (double)c.rl, (double)c.ih + (double)c.il);
+        const G v = mkc((double)c.re.h + (double)c.re.l, (double)c.im.h + (double)c.im.l);
         G r = cmul(alpha, v);
         if (old) r = cadd(r, cmul(beta, *old));
         return r;
+    }
+};
+
+// Operands already held as float pairs (float4 = re_hi, im_hi, re_lo, im_lo):
+// the constant forward operator is split once, the vectors stay split, so
+// no FP64 instruction is issued.  alpha = 1; beta = 0 or 1 (accumulate).
+__device__ __forceinline__ ff ff_norm(ff a) {
+    const float h = a.h + a.l;
+    return ff{h, a.l - (h - a.h)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    return ff_norm(ff{s, e + (a.l + b.l)});
+}
+
+struct ArithFFP {
+    typedef float4 G;
+    typedef ArithFF::SA SA;
+    typedef ArithFF::SB SB;
+    typedef ArithFF::Acc Acc;
+    __device__ static SA stage_a(G v, bool cj) {
+        return cj ? SA{ff{v.x, v.z}, ff{-v.y, -v.w}} : SA{ff{v.x, v.z}, ff{v.y, v.w}};
+    }
+    __device__ static SB stage_b(G v) { return SB{ff{v.x, v.z}, ff{v.y, v.w}}; }
+    __device__ static SA za() { return ArithFF::za(); }
+    __device__ static SB zb() { return ArithFF::zb(); }
+    __device__ static void zero(Acc &a) { ArithFF::zero(a); }
+    __device__ static void mac(Acc &c, const SA &a, const SB &b) { ArithFF::mac(c, a, b); }
+    __device__ static G finish(const Acc &c, G, G, const G *old) {
+        ff re = ff_norm(c.re), im = ff_norm(c.im);
+        if (old) {
+            re = ff_add(re, ff{old->x, old->z});
+            im = ff_add(im, ff{old->y, old->w});
+        }
+        return make_float4(re.h, im.h, re.l, im.l);
     }
 };
 
@@ -119,14 +158,16 @@ __global__ void __launch_bounds__(NT) k_gemm_rt(const MatRefT<typename Ar::G> *_
                                                 typename Ar::G alpha, typename Ar::G beta, int use_beta,
                                                 int tiles_m) {
     typedef typename Ar::G G;
-    typedef typename Ar::S S;
+    typedef typename Ar::SA SA;
+    typedef typename Ar::SB SB;
     const MatRefT<G> A = As[blockIdx.y], B = Bs[blockIdx.y], Cm = Cs[blockIdx.y];
     const int M = Cm.rows, N = Cm.cols;
     const int K = (opA == 0) ? A.cols : A.rows;
     constexpr int BN = 16 * TJ;
     const int i0 = (blockIdx.x % tiles_m) * BM, j0 = (blockIdx.x / tiles_m) * BN;
     if (i0 >= M || j0 >= N) return;
-    __shared__ S sa[BK][BM], sb[BK][16 * TJ];
+    __shared__ SA sa[BK][BM];
+    __shared__ SB sb[BK][16 * TJ];
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
     typename Ar::Acc acc[4][TJ];
 #pragma unroll
@@ -140,14 +181,14 @@ __global__ void __launch_bounds__(NT) k_gemm_rt(const MatRefT<typename Ar::G> *_
             for (int q = 0; q < 4; ++q) {
                 const int i = t & 63, k = (t >> 6) + 4 * q;
                 const int gi = i0 + i, gk = k0 + k;
-                sa[k][i] = (gi < M && gk < K) ? Ar::stage(A.p[gi + (int64_t)gk * A.ld]) : Ar::szero();
+                sa[k][i] = (gi < M && gk < K) ? Ar::stage_a(A.p[gi + (int64_t)gk * A.ld], false) : Ar::za();
             }
         } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int k = t & 15, i = (t >> 4) + 16 * q;
                 const int gi = i0 + i, gk = k0 + k;
-                sa[k][i] = (gi < M && gk < K) ? Ar::conj(Ar::stage(A.p[gk + (int64_t)gi * A.ld])) : Ar::szero();
+                sa[k][i] = (gi < M && gk < K) ? Ar::stage_a(A.p[gk + (int64_t)gi * A.ld], true) : Ar::za();
             }
         }
         // stage B[k0:k0+16, j0:j0+BN] as sb[k][j]
@@ -155,12 +196,13 @@ __global__ void __launch_bounds__(NT) k_gemm_rt(const MatRefT<typename Ar::G> *_
         for (int q = 0; q < TJ; ++q) {
             const int k = t & 15, j = (t >> 4) + 16 * q;
             const int gk = k0 + k, gj = j0 + j;
-            sb[k][j] = (gk < K && gj < N) ? Ar::stage(B.p[gk + (int64_t)gj * B.ld]) : Ar::szero();
+            sb[k][j] = (gk < K && gj < N) ? Ar::stage_b(B.p[gk + (int64_t)gj * B.ld]) : Ar::zb();
         }
         __syncthreads();
         const int kmax = min(BK, K - k0);
         for (int k = 0; k < kmax; ++k) {
-            S a[4], b[TJ];
+            SA a[4];
+            SB b[TJ];
 #pragma unroll
             for (int i = 0; i < 4; ++i) a[i] = sa[k][tx + 16 * i];
 #pragma unroll
@@ -214,4 +256,10 @@ int dense_gemm_rt(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, 
 int dense_gemm_ff(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, const MatRef *d_C,
                   cplx alpha, cplx beta, cudaStream_t s) {
     return launch<ArithFF, 2>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
+}
+
+int dense_gemm_ffp(int batch, int max_m, int max_n, const MatRefT<float4> *d_A, int opA, const MatRefT<float4> *d_B,
+                   const MatRefT<float4> *d_C, int accumulate, cudaStream_t s) {
+    return launch<ArithFFP, 2>(batch, max_m, max_n, d_A, opA, d_B, d_C, make_float4(1.f, 0.f, 0.f, 0.f),
+                               make_float4(accumulate ? 1.f : 0.f, 0.f, 0.f, 0.f), s);
 }

@@ -172,8 +172,7 @@ int id_batched(int batch, int max_m, int max_n, const int *d_m, const int *d_n, 
     if (batch <= 0) return FDS_OK;
     size_t smem = (size_t)max_m * sizeof(cplx) + (size_t)max_n * (sizeof(double) + sizeof(int)) + 16;
     if (smem > 220 * 1024) return FDS_ERR_ARG;
-    if (smem > 48 * 1024)
-        FDS_CUDA_TRY(cudaFuncSetAttribute(k_cpqr_id, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FDS_TRY(ensure_dyn_smem(k_cpqr_id, smem));
     fds_count_launch(), k_cpqr_id<<<batch, ID_THREADS, smem, s>>>(d_m, d_n, d_off, d_Y, tol, d_rank, d_perm, d_poff, d_T, d_toff,
                                                                       d_sel);
     FDS_CUDA_TRY(cudaGetLastError());

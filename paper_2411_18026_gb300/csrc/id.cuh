@@ -8,7 +8,7 @@ int id_batched(int batch, int max_m, int max_n, const int *d_m, const int *d_n, 
                double tol, int *d_rank, int *d_perm, const int64_t *d_poff, cplx *d_T, const int64_t *d_toff,
                cudaStream_t s, const int *d_sel = nullptr);
 // Learned-rank ID (learned.cu): sparse-sign sketch with frac[b] * n[b] + extra
-// rows, CPQR of the sketch, residual check on sampled rows of Y (Y is read
+// rows, CPQR of the sketch, ID residual checked on all of Y (Y is read
 // only).  fail[b] = 1 where the check failed (outputs of b then undefined).
 int id_sketched(int batch, int max_m, const int *d_m, const int *d_n, const int64_t *d_off, const cplx *d_Y,
                 const float *d_frac, int extra, double tol, int *d_rank, int *d_perm, const int64_t *d_poff,

@@ -82,8 +82,9 @@ __device__ __forceinline__ void load_rules(Rules &R, int qcross) {
 //   Y0 = (2/pi) [ (ln(z/2) + g) J0 - sum_{m>=1} H_m q^m/(m!)^2 ],
 //   Im E = (2/pi) ln(z/2) J1/z - (1/(2 pi)) sum (2 (H_m - g) + 1/(m+1)) q^m/(m!(m+1)!),
 //   Y1 = z Im E - 2/(pi z).
-// 14 terms reach 1e-16 for z < 2.  For z >= 2 from
-// CUDA's j0/y0/j1/y1.
+// 14 terms reach 1e-16 for z < 2, 8 for z < 0.63 and 6 for z < 0.2 (the
+// tails are below 1e-17 of the leading terms).  For z >= 2 from CUDA's
+// j0/y0/j1/y1.
 struct Hk {
     cplx h0, h1, e;
 };
@@ -112,7 +113,10 @@ __device__ __forceinline__ Hk hankel_k(const Rules &G, double z, double lhalf) {
         const double g = 0.57721566490153286061;
         const double q = -0.25 * z * z;
         double J0, Su, SH, Sp;
-        series4<SER_TERMS>(G, q, J0, Su, SH, Sp);
+        // terms needed for 1e-17 relative: 6 below z = 0.2, 8 below z = 0.63
+        if (q > -0.01) series4<6>(G, q, J0, Su, SH, Sp);
+        else if (q > -0.1) series4<8>(G, q, J0, Su, SH, Sp);
+        else series4<SER_TERMS>(G, q, J0, Su, SH, Sp);
         const double j1z = 0.5 * Su;                      // J1(z)/z
         const double Y0 = (2.0 / FDS_PI) * ((lhalf + g) * J0 - SH);
         const double eim = (2.0 / FDS_PI) * lhalf * j1z - Sp * (0.5 / FDS_PI);

@@ -9,12 +9,14 @@
 // extra) rows by a sparse sign embedding (every row of Y is added, with a
 // sign, to 2 sketch rows chosen by the SplitMix64 hash of (matrix, row,
 // slot): row floor(h_hi32 s / 2^32), sign from the lowest bit); the sketch Z = Omega Y goes through the same CPQR as the adaptive
-// ID (largest remaining column, stop at |R_jj| <= tol |R_11|), giving the
-// skeleton columns and T = R11^{-1} R12.  The result is accepted when the
-// rank was revealed (k < s, or s = n) and the ID residual on 32 sampled rows
-// of Y, max over columns of ||Y_S[:, c] - Y_S[:, J] T[:, c]||, is at most
-// 10 tol times the largest column norm of Y_S; otherwise the caller reruns
-// the adaptive CPQR on Y.
+// ID (largest remaining column, stop at |R_jj| <= tol |R_11| / 10: the
+// sketch underestimates the trailing norms), giving the skeleton columns and
+// T = R11^{-1} R12 (on the proxy matrices of this method about 2 more
+// skeleton columns per (cell, component) than the adaptive ID).
+// The result is accepted when the rank was revealed (k < s, or s = n) and the
+// ID residual on Y, max over columns of ||Y[:, c] - Y[:, J] T[:, c]||, is at
+// most tol times the largest column norm of Y (what the adaptive CPQR
+// guarantees); otherwise the caller reruns the adaptive CPQR on Y.
 #include <cmath>
 
 #include "common.cuh"
@@ -24,7 +26,6 @@ namespace {
 
 constexpr int LT = 256;
 constexpr int SK_MAXN = 64;      // columns handled by the sketch kernel (n <= 64, else fallback)
-constexpr int NS = 32;           // sampled rows of the residual check
 
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
     // Steele, Lea, Flood (2014), SplitMix64 finaliser
@@ -209,7 +210,9 @@ __global__ void __launch_bounds__(LT) k_sketch_id(const int *__restrict__ ms, co
             if (j == 0) s_r11 = alpha;
             s_p = p;
             s_alpha = alpha;
-            s_stop = (alpha == 0.0 || alpha <= tol * s_r11) ? 1 : 0;
+            // a tenth of the tolerance on the sketch: a (k + extra)-row sketch
+            // underestimates the trailing norms
+            s_stop = (alpha == 0.0 || alpha <= 0.1 * tol * s_r11) ? 1 : 0;
         }
         __syncthreads();
         if (s_stop) break;
@@ -282,24 +285,19 @@ __global__ void __launch_bounds__(LT) k_sketch_id(const int *__restrict__ ms, co
     }
     if (threadIdx.x == 0) s_ok = (k < s || s == n) ? 1 : 0;
     __syncthreads();
-    // residual on sampled rows i_j = floor(j m / NS): warp per column
-    const int ns_ = min(NS, m);
+    // ID residual on all rows of Y: warp per column, lanes over rows
     double ymax = 0.0, emax = 0.0;
     for (int c = warp; c < n; c += LT / 32) {
         double a = 0.0;
-        if (lane < ns_) {
-            const int i = (int)(((long)lane * m) / ns_);
-            a = cabs2(Y[i + (long)perm[c] * m]);
-        }
+        for (int i = lane; i < m; i += 32) a += cabs2(Y[i + (long)perm[c] * m]);
         ymax = fmax(ymax, wsum(a));
     }
     for (int c = warp; c < n - k; c += LT / 32) {
         double a = 0.0;
-        if (lane < ns_) {
-            const int i = (int)(((long)lane * m) / ns_);
+        for (int i = lane; i < m; i += 32) {
             cplx e = Y[i + (long)perm[k + c] * m];
             for (int l = 0; l < k; ++l) cfms(e, Y[i + (long)perm[l] * m], T[l + (long)c * k]);
-            a = cabs2(e);
+            a += cabs2(e);
         }
         emax = fmax(emax, wsum(a));
     }
@@ -316,8 +314,8 @@ __global__ void __launch_bounds__(LT) k_sketch_id(const int *__restrict__ ms, co
     if (threadIdx.x == 0) {
         double ee = 0.0;
         for (int w = 0; w < LT / 32; ++w) ee = fmax(ee, r_val[w * 32]);
-        const double lim = 10.0 * tol;
-        const int ok = s_ok && (ee <= lim * lim * s_alpha);
+        // the adaptive ID's guarantee: every residual column <= tol x the largest column of Y
+        const int ok = s_ok && (ee <= tol * tol * s_alpha);
         fail[b] = ok ? 0 : 1;
         if (ok) ranks[b] = k;
     }
@@ -344,8 +342,7 @@ int id_sketched(int batch, int max_m, const int *d_m, const int *d_n, const int6
     const size_t smem = sizeof(cplx) * SK_MAXN * SK_MAXN + sizeof(double) * SK_MAXN +
                         sizeof(int) * (SK_MAXN + SK_MAXN + 1 + 2 * (size_t)max_m) + 16;
     if (smem > 220 * 1024) return FDS_ERR_ARG;
-    if (smem > 48 * 1024)
-        FDS_CUDA_TRY(cudaFuncSetAttribute(k_sketch_id, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FDS_TRY(ensure_dyn_smem(k_sketch_id, smem));
     fds_count_launch(), k_sketch_id<<<batch, LT, smem, s>>>(d_m, d_n, d_off, d_Y, d_frac, extra, tol, d_rank, d_perm,
                                                              d_poff, d_T, d_toff, d_fail, seed);
     FDS_CUDA_TRY(cudaGetLastError());

@@ -1,7 +1,8 @@
 // Mixed-precision solve (FDS_MIXED): the solve sweep of Sec. 6.2-6.3 runs on
 // complex64 copies of the factors and is refined against the compressed
-// operator the factorisation inverts, stored in FP64 and applied in FP64 or
-// in double-float arithmetic on the FP32 pipe (about 44 significant bits):
+// operator the factorisation inverts, from FP64 entries, applied in FP64 or
+// (default) split once into float pairs and applied in double-float
+// arithmetic on the FP32 pipe (about 44 significant bits):
 //
 //   A = D_L + U_L B_L V_L,   B_l = S_{l-1} + U_{l-1} B_{l-1} V_{l-1}  (l > l0+1),
 //   B_{l0+1} = S_{l0} + A_top,off
@@ -31,7 +32,8 @@ __global__ void k_to_c64(const cplx *__restrict__ src, cplxf *dst, int64_t n) {
         dst[e] = to_c64(src[e]);
 }
 
-__global__ void k_refs(int nb, cplx *base, const int64_t *__restrict__ off, int cols, int64_t ld, MatRef *out) {
+template <class T>
+__global__ void k_refs(int nb, T *base, const int64_t *__restrict__ off, int cols, int64_t ld, MatRefT<T> *out) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     out[b].p = base + off[b];
@@ -40,12 +42,13 @@ __global__ void k_refs(int nb, cplx *base, const int64_t *__restrict__ off, int 
     out[b].ld = (int)ld;
 }
 
-// child skeleton vector (R x cols) <-> parent DOF vector (Dp x cols), FP64
+// child skeleton vector (R x cols) <-> parent DOF vector (Dp x cols)
 // dir 0: parent[pos] = child;  dir 1: child = parent[pos]
-__global__ void k_child_parent64(int nb, const int64_t *__restrict__ roff, const int *__restrict__ k1,
+template <class T>
+__global__ void k_child_parent_t(int nb, const int64_t *__restrict__ roff, const int *__restrict__ k1,
                                  const int *__restrict__ pos1, const int *__restrict__ pos2,
-                                 const int64_t *__restrict__ pdoff, cplx *child, int64_t ldc, cplx *parent,
-                                 int64_t ldp, int cols, int dir) {
+                                 const int64_t *__restrict__ pdoff, T *child, int64_t ldc, T *parent, int64_t ldp,
+                                 int cols, int dir) {
     const int b = blockIdx.x;
     const int64_t o = roff[b];
     const int r = (int)(roff[b + 1] - o);
@@ -60,16 +63,31 @@ __global__ void k_child_parent64(int nb, const int64_t *__restrict__ roff, const
     }
 }
 
+// complex128 -> float pair (re_hi, im_hi, re_lo, im_lo)
+__global__ void k_split(const cplx *__restrict__ src, float4 *dst, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const cplx v = src[e];
+        const float rh = (float)v.x, ih = (float)v.y;
+        dst[e] = make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));
+    }
+}
+
+__device__ __forceinline__ cplx to_c128(const cplx &v) { return v; }
+__device__ __forceinline__ cplx to_c128(const float4 &v) {
+    return mkc((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+}
+
 // r = f - y in leaf order (y may be null: r = f), stored as complex64 for the
 // sweep; norms[2c] += |r|^2, norms[2c+1] += |f|^2 over column c.
+template <class T>
 __global__ void k_residual(const int *__restrict__ gidx, int64_t D, const cplx *__restrict__ F, int64_t ldf,
-                           const cplx *__restrict__ Y, cplxf *R, double *norms) {
+                           const T *__restrict__ Y, cplxf *R, double *norms) {
     const int c = blockIdx.y;
     double rr = 0.0, ff = 0.0;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < D; q += (int64_t)gridDim.x * blockDim.x) {
         const cplx f = F[gidx[q] + c * ldf];
         cplx r = f;
-        if (Y) r = csub(f, Y[q + c * D]);
+        if (Y) r = csub(f, to_c128(Y[q + c * D]));
         R[q + c * D] = to_c64(r);
         rr += cabs2(r);
         ff += cabs2(f);
@@ -123,28 +141,6 @@ int convert(const DBuf<cplx> &src, DBuf<cplxf> &dst, cudaStream_t s) {
     return FDS_OK;
 }
 
-// Forward-apply workspace: x_l (l0 < l < L), skeleton temporaries, y_l, top.
-int forward_workspace(fds_handle *h, int ncmax) {
-    const int L = h->L, l0 = h->l0;
-    if ((int)h->wz.size() != L + 1) {
-        h->wz = std::vector<DBuf<cplx>>(L + 1);
-        h->wf = std::vector<DBuf<cplx>>(L + 1);
-        h->wt = std::vector<DBuf<cplx>>(L + 1);
-    }
-    if ((int)h->wy.size() != L + 1) h->wy = std::vector<DBuf<cplx>>(L + 1);
-    for (int l = L; l > l0; --l) {
-        const Level &C = h->lv[l];
-        if (l < L) FDS_TRY(grow(h->wz[l], (size_t)C.D * ncmax));
-        FDS_TRY(grow(h->wt[l], (size_t)std::max<int64_t>(C.Rtot, 1) * ncmax));
-        FDS_TRY(grow(h->wy[l], (size_t)C.D * ncmax));
-    }
-    FDS_TRY(grow(h->wtop, (size_t)std::max<int64_t>(h->Dtop, 1) * ncmax));
-    FDS_TRY(grow(h->wytop, (size_t)std::max<int64_t>(h->Dtop, 1) * ncmax));
-    const int maxnb = fds_max_cells(h);
-    if (h->wrefs.n < (size_t)4 * maxnb + 2) FDS_TRY(h->wrefs.alloc((size_t)4 * maxnb + 2));
-    return FDS_OK;
-}
-
 double level_d2(const Level &C) {
     double s = 0;
     for (int b = 0; b < C.nb; ++b) {
@@ -154,19 +150,83 @@ double level_d2(const Level &C) {
     return s;
 }
 
-// Products of the forward operator: FP64, or double-float on the FP32 pipe.
-int fgemm(const fds_handle *h, int batch, int max_m, int max_n, const MatRef *A, int opA, const MatRef *B,
-          const MatRef *C, cplx alpha, cplx beta, cudaStream_t s) {
-    if (h->opt.ir_apply == FDS_APPLY_FP64) return dense_gemm_rt(batch, max_m, max_n, A, opA, B, C, alpha, beta, s);
-    return dense_gemm_ff(batch, max_m, max_n, A, opA, B, C, alpha, beta, s);
+// The forward operator and its vectors in one arithmetic: complex128 (FP64
+// products) or float4 float pairs (double-float products on the FP32 pipe).
+template <class T>
+struct Fw;
+
+template <>
+struct Fw<cplx> {
+    static const MatRef *V(const Level &c) { return c.rV.p; }
+    static const MatRef *D(const Level &c) { return c.rDfw.p; }
+    static const MatRef *S(const Level &c) { return c.rSfw.p; }
+    static const MatRef *top(const fds_handle *h) { return h->rtop_off.p; }
+    static std::vector<DBuf<cplx>> &z(fds_handle *h) { return h->wz; }
+    static std::vector<DBuf<cplx>> &t(fds_handle *h) { return h->wt; }
+    static std::vector<DBuf<cplx>> &y(fds_handle *h) { return h->wy; }
+    static DBuf<cplx> &xtop(fds_handle *h) { return h->wtop; }
+    static DBuf<cplx> &ytop(fds_handle *h) { return h->wytop; }
+    static DBuf<MatRef> &refs(fds_handle *h) { return h->wrefs; }
+    static int gemm(int batch, int m, int n, const MatRef *A, int opA, const MatRef *B, const MatRef *C, int acc,
+                    cudaStream_t s) {
+        return dense_gemm_rt(batch, m, n, A, opA, B, C, mkc(1, 0), mkc(acc ? 1 : 0, 0), s);
+    }
+};
+
+template <>
+struct Fw<float4> {
+    static const MatRefP *V(const Level &c) { return c.rVp.p; }
+    static const MatRefP *D(const Level &c) { return c.rDp.p; }
+    static const MatRefP *S(const Level &c) { return c.rSp.p; }
+    static const MatRefP *top(const fds_handle *h) { return h->rtop_offp.p; }
+    static std::vector<DBuf<float4>> &z(fds_handle *h) { return h->wzp; }
+    static std::vector<DBuf<float4>> &t(fds_handle *h) { return h->wtp; }
+    static std::vector<DBuf<float4>> &y(fds_handle *h) { return h->wyp; }
+    static DBuf<float4> &xtop(fds_handle *h) { return h->wtopp; }
+    static DBuf<float4> &ytop(fds_handle *h) { return h->wytopp; }
+    static DBuf<MatRefP> &refs(fds_handle *h) { return h->wrefsp; }
+    static int gemm(int batch, int m, int n, const MatRefP *A, int opA, const MatRefP *B, const MatRefP *C, int acc,
+                    cudaStream_t s) {
+        return dense_gemm_ffp(batch, m, n, A, opA, B, C, acc, s);
+    }
+};
+
+// Forward-apply workspace: x_l (l0 < l < L), skeleton temporaries, y_l, top.
+template <class T>
+int forward_workspace(fds_handle *h, int ncmax) {
+    typedef Fw<T> F;
+    const int L = h->L, l0 = h->l0;
+    auto &wz = F::z(h), &wt = F::t(h), &wy = F::y(h);
+    if ((int)wz.size() != L + 1) wz = std::vector<DBuf<T>>(L + 1);
+    if ((int)wt.size() != L + 1) wt = std::vector<DBuf<T>>(L + 1);
+    if ((int)wy.size() != L + 1) wy = std::vector<DBuf<T>>(L + 1);
+    for (int l = L; l > l0; --l) {
+        const Level &C = h->lv[l];
+        if (l < L) FDS_TRY(grow(wz[l], (size_t)C.D * ncmax));
+        FDS_TRY(grow(wt[l], (size_t)std::max<int64_t>(C.Rtot, 1) * ncmax));
+        FDS_TRY(grow(wy[l], (size_t)C.D * ncmax));
+    }
+    FDS_TRY(grow(F::xtop(h), (size_t)std::max<int64_t>(h->Dtop, 1) * ncmax));
+    FDS_TRY(grow(F::ytop(h), (size_t)std::max<int64_t>(h->Dtop, 1) * ncmax));
+    const int maxnb = fds_max_cells(h);
+    if (F::refs(h).n < (size_t)4 * maxnb + 2) FDS_TRY(F::refs(h).alloc((size_t)4 * maxnb + 2));
+    return FDS_OK;
 }
 
-// Y = A X for nc leaf-order columns (both D_L x nc, column-major), complex128.
-int forward_apply(fds_handle *h, const cplx *X, cplx *Y, int nc, cudaStream_t s) {
+// Leaf-order output vector of the forward apply.
+template <class T>
+T *forward_out(fds_handle *h) {
+    return (h->L > h->l0) ? Fw<T>::y(h)[h->L].p : Fw<T>::ytop(h).p;
+}
+
+// Y = A X for nc leaf-order columns (both D_L x nc, column-major).
+template <class T>
+int forward_apply(fds_handle *h, const T *X, T *Y, int nc, cudaStream_t s) {
+    typedef Fw<T> F;
     const int L = h->L, l0 = h->l0;
     const int maxnb = fds_max_cells(h);
-    MatRef *rZ = h->wrefs.p, *rT = rZ + maxnb, *rY = rT + maxnb, *rX = rY + maxnb;   // rX: 2 slots
-    const cplx one = mkc(1, 0), zero = mkc(0, 0);
+    MatRefT<T> *rZ = F::refs(h).p, *rT = rZ + maxnb, *rY = rT + maxnb, *rX = rY + maxnb;   // rX: 2 slots
+    auto &wz = F::z(h), &wt = F::t(h), &wy = F::y(h);
     ProfScope ps("a7.forward_apply", s);
     double fl = 0;
     // up
@@ -175,35 +235,35 @@ int forward_apply(fds_handle *h, const cplx *X, cplx *Y, int nc, cudaStream_t s)
         Level &Pn = h->lv[l - 1];
         const int nb = C.nb;
         const int64_t ldr = std::max<int64_t>(C.Rtot, 1);
-        cplx *xl = (l == L) ? (cplx *)X : h->wz[l].p;
-        fds_count_launch(), k_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, xl, C.d_doff.p, nc, C.D, rZ);
-        fds_count_launch(), k_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, h->wt[l].p, C.d_roff.p, nc, ldr, rT);
-        FDS_TRY(fgemm(h, nb, C.rmax, nc, C.rV.p, 0, rZ, rT, one, zero, s));
-        cplx *par = (l - 1 > l0) ? h->wz[l - 1].p : h->wtop.p;
+        T *xl = (l == L) ? (T *)X : wz[l].p;
+        fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, xl, C.d_doff.p, nc, C.D, rZ);
+        fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, wt[l].p, C.d_roff.p, nc, ldr, rT);
+        FDS_TRY(F::gemm(nb, C.rmax, nc, F::V(C), 0, rZ, rT, 0, s));
+        T *par = (l - 1 > l0) ? wz[l - 1].p : F::xtop(h).p;
         const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
-        fds_count_launch(), k_child_parent64<<<nb, 256, 0, s>>>(nb, C.d_roff.p, C.d_k1.p, C.d_par_pos1.p,
-                                                                C.d_par_pos2.p, Pn.d_doff.p, h->wt[l].p, ldr, par,
-                                                                ldp, nc, 0);
+        fds_count_launch(), k_child_parent_t<T><<<nb, 256, 0, s>>>(nb, C.d_roff.p, C.d_k1.p, C.d_par_pos1.p,
+                                                                   C.d_par_pos2.p, Pn.d_doff.p, wt[l].p, ldr, par,
+                                                                   ldp, nc, 0);
         FDS_CUDA_TRY(cudaGetLastError());
         fl += 8.0 * C.sum_rd * nc;
     }
     // top: off-diagonal blocks between top cells, then the block diagonal
     {
-        Level &T = h->lv[l0];
-        cplx *xt = (L > l0) ? h->wtop.p : (cplx *)X;
-        cplx *yt = (L > l0) ? h->wytop.p : Y;
+        Level &Tl = h->lv[l0];
+        T *xt = (L > l0) ? F::xtop(h).p : (T *)X;
+        T *yt = (L > l0) ? F::ytop(h).p : Y;
         const int ld = (int)std::max<int64_t>(h->Dtop, 1);
-        MatRef hv[2];
+        MatRefT<T> hv[2];
         hv[0].p = xt; hv[0].rows = (int)h->Dtop; hv[0].cols = nc; hv[0].ld = ld;
         hv[1].p = yt; hv[1].rows = (int)h->Dtop; hv[1].cols = nc; hv[1].ld = ld;
         FDS_CUDA_TRY(cudaMemcpyAsync(rX, hv, sizeof(hv), cudaMemcpyHostToDevice, s));
-        FDS_TRY(fgemm(h, 1, (int)h->Dtop, nc, h->rtop_off.p, 0, rX, rX + 1, one, zero, s));
+        FDS_TRY(F::gemm(1, (int)h->Dtop, nc, F::top(h), 0, rX, rX + 1, 0, s));
         fl += 8.0 * (double)h->Dtop * h->Dtop * nc;
-        const MatRef *Bd = (L > l0) ? T.rSfw.p : T.rDfw.p;
-        fds_count_launch(), k_refs<<<(T.nb + 127) / 128, 128, 0, s>>>(T.nb, xt, T.d_doff.p, nc, h->Dtop, rZ);
-        fds_count_launch(), k_refs<<<(T.nb + 127) / 128, 128, 0, s>>>(T.nb, yt, T.d_doff.p, nc, h->Dtop, rY);
-        FDS_TRY(fgemm(h, T.nb, T.dmax, nc, Bd, 0, rZ, rY, one, one, s));
-        fl += 8.0 * level_d2(T) * nc;
+        const MatRefT<T> *Bd = (L > l0) ? F::S(Tl) : F::D(Tl);
+        fds_count_launch(), k_refs<T><<<(Tl.nb + 127) / 128, 128, 0, s>>>(Tl.nb, xt, Tl.d_doff.p, nc, h->Dtop, rZ);
+        fds_count_launch(), k_refs<T><<<(Tl.nb + 127) / 128, 128, 0, s>>>(Tl.nb, yt, Tl.d_doff.p, nc, h->Dtop, rY);
+        FDS_TRY(F::gemm(Tl.nb, Tl.dmax, nc, Bd, 0, rZ, rY, 1, s));
+        fl += 8.0 * level_d2(Tl) * nc;
     }
     // down
     for (int l = l0 + 1; l <= L; ++l) {
@@ -211,24 +271,34 @@ int forward_apply(fds_handle *h, const cplx *X, cplx *Y, int nc, cudaStream_t s)
         Level &Pn = h->lv[l - 1];
         const int nb = C.nb;
         const int64_t ldr = std::max<int64_t>(C.Rtot, 1);
-        cplx *ypar = (l - 1 > l0) ? h->wy[l - 1].p : h->wytop.p;
+        T *ypar = (l - 1 > l0) ? wy[l - 1].p : F::ytop(h).p;
         const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
-        cplx *yl = (l == L) ? Y : h->wy[l].p;
-        cplx *xl = (l == L) ? (cplx *)X : h->wz[l].p;
-        fds_count_launch(), k_child_parent64<<<nb, 256, 0, s>>>(nb, C.d_roff.p, C.d_k1.p, C.d_par_pos1.p,
-                                                                C.d_par_pos2.p, Pn.d_doff.p, h->wt[l].p, ldr, ypar,
-                                                                ldp, nc, 1);
-        fds_count_launch(), k_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, h->wt[l].p, C.d_roff.p, nc, ldr, rT);
-        fds_count_launch(), k_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, yl, C.d_doff.p, nc, C.D, rY);
-        fds_count_launch(), k_refs<<<(nb + 127) / 128, 128, 0, s>>>(nb, xl, C.d_doff.p, nc, C.D, rZ);
+        T *yl = (l == L) ? Y : wy[l].p;
+        T *xl = (l == L) ? (T *)X : wz[l].p;
+        fds_count_launch(), k_child_parent_t<T><<<nb, 256, 0, s>>>(nb, C.d_roff.p, C.d_k1.p, C.d_par_pos1.p,
+                                                                   C.d_par_pos2.p, Pn.d_doff.p, wt[l].p, ldr, ypar,
+                                                                   ldp, nc, 1);
+        fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, wt[l].p, C.d_roff.p, nc, ldr, rT);
+        fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, yl, C.d_doff.p, nc, C.D, rY);
+        fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, xl, C.d_doff.p, nc, C.D, rZ);
         FDS_CUDA_TRY(cudaGetLastError());
-        FDS_TRY(fgemm(h, nb, C.dmax, nc, C.rV.p, 2, rT, rY, one, zero, s));
-        const MatRef *Bd = (l == L) ? C.rDfw.p : C.rSfw.p;
-        FDS_TRY(fgemm(h, nb, C.dmax, nc, Bd, 0, rZ, rY, one, one, s));
+        FDS_TRY(F::gemm(nb, C.dmax, nc, F::V(C), 2, rT, rY, 0, s));
+        const MatRefT<T> *Bd = (l == L) ? F::D(C) : F::S(C);
+        FDS_TRY(F::gemm(nb, C.dmax, nc, Bd, 0, rZ, rY, 1, s));
         fl += 8.0 * (C.sum_rd + level_d2(C)) * nc;
     }
     ps.flops = fl;
     return FDS_OK;
+}
+
+int split_blocks(const DBuf<cplx> &src, DBuf<float4> &dst, DBuf<MatRefP> &rdst, const std::vector<int64_t> &off,
+                 const std::vector<int> &rows, const std::vector<int> &cols, cudaStream_t s) {
+    FDS_TRY(dst.alloc(src.n));
+    if (src.n) {
+        fds_count_launch(), k_split<<<1024, 256, 0, s>>>(src.p, dst.p, (int64_t)src.n);
+        FDS_CUDA_TRY(cudaGetLastError());
+    }
+    return make_refs_t(rdst, dst.p, off, rows, cols, s);
 }
 
 }  // namespace
@@ -245,8 +315,14 @@ int fds_keep_blocks(const Level &Lv, DBuf<cplx> &dst, DBuf<MatRef> &rdst, cudaSt
 int fds_mixed_prepare(fds_handle *h) {
     cudaStream_t s = h->stream;
     const int L = h->L, l0 = h->l0;
+    const int ls = sweep_split(h);
     int64_t bytes = 0;
-    for (int l = L; l > l0; --l) {
+    for (int l = ls; l > l0; --l) {
+        const Level &C = h->lv[l];
+        bytes += (int64_t)(C.Ainv.bytes() + C.W.bytes() + C.At.bytes() + C.V.bytes() + C.Dfw.bytes() +
+                           C.Sfw.bytes());
+    }
+    for (int l = L; l > ls; --l) {
         Level &C = h->lv[l];
         std::vector<int> dv(C.nb), rv(C.nb);
         for (int b = 0; b < C.nb; ++b) {
@@ -266,9 +342,43 @@ int fds_mixed_prepare(fds_handle *h) {
     }
     bytes += (int64_t)h->lv[l0].Sfw.bytes() + (int64_t)h->lv[l0].Dfw.bytes();
     bytes += (int64_t)(h->Atop.bytes() + h->ptop.bytes() + h->Atop_off.bytes());
+    if (h->opt.ir_apply == FDS_APPLY_FF) {
+        // the forward operator as float pairs (same bytes as complex128)
+        for (int l = L; l >= l0; --l) {
+            Level &C = h->lv[l];
+            std::vector<int> dv(C.nb), rv(C.nb);
+            for (int b = 0; b < C.nb; ++b) {
+                dv[b] = C.n1[b] + C.n2[b];
+                rv[b] = l > l0 ? C.k1[b] + C.k2[b] : 0;
+            }
+            if (l > l0) FDS_TRY(split_blocks(C.V, C.Vp, C.rVp, C.offV, rv, dv, s));
+            if (C.Dfw.p) FDS_TRY(split_blocks(C.Dfw, C.Dp, C.rDp, C.offA, dv, dv, s));
+            if (C.Sfw.p) FDS_TRY(split_blocks(C.Sfw, C.Sp, C.rSp, C.offA, dv, dv, s));
+        }
+        {
+            std::vector<int64_t> off = {0, h->Dtop * h->Dtop};
+            std::vector<int> d = {(int)h->Dtop};
+            FDS_TRY(split_blocks(h->Atop_off, h->Atop_offp, h->rtop_offp, off, d, d, s));
+        }
+    }
     FDS_CUDA_TRY(cudaStreamSynchronize(s));
-    // the FP64 sweep factors are not used by the mixed solve
-    for (int l = L; l > l0; --l) {
+    if (h->opt.ir_apply == FDS_APPLY_FF) {
+        for (int l = L; l >= l0; --l) {
+            Level &C = h->lv[l];
+            C.Dfw.release();
+            C.rDfw.release();
+            C.Sfw.release();
+            C.rSfw.release();
+            if (l > ls) {
+                C.V.release();
+                C.rV.release();
+            }
+        }
+        h->Atop_off.release();
+        h->rtop_off.release();
+    }
+    // the FP64 factors of the complex64 levels are not used by the mixed solve
+    for (int l = L; l > ls; --l) {
         Level &C = h->lv[l];
         C.Ainv.release();
         C.rAinv.release();
@@ -287,13 +397,19 @@ int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
     const int ncmax = std::min(nrhs, SOLVE_CHUNK);
     const Level &Lf = h->lv[L];
     const int64_t D = Lf.D;
-    FDS_TRY(sweep_workspace<cplxf>(h, ncmax));
+    FDS_TRY(sweep_workspace(h, ncmax));
     const bool refine = h->opt.ir_max_iter > 0;
-    if (refine) FDS_TRY(forward_workspace(h, ncmax));
+    const bool ffp = h->opt.ir_apply == FDS_APPLY_FF;
+    if (refine) {
+        if (ffp) FDS_TRY(forward_workspace<float4>(h, ncmax));
+        else FDS_TRY(forward_workspace<cplx>(h, ncmax));
+    }
+    if (refine && ffp) FDS_TRY(grow(h->wXp, (size_t)D * ncmax));
     FDS_TRY(grow(h->wX, (size_t)D * ncmax));
     if (h->wnorm.n < (size_t)2 * ncmax) FDS_TRY(h->wnorm.alloc((size_t)2 * ncmax));
     cplxf *leaf_in = sweep_leaf_in<cplxf>(h), *leaf = sweep_leaf_out<cplxf>(h);
-    cplx *Yleaf = refine ? ((L > h->l0) ? h->wy[L].p : h->wytop.p) : nullptr;
+    cplx *Yleaf = (refine && !ffp) ? forward_out<cplx>(h) : nullptr;
+    float4 *Ypleaf = (refine && ffp) ? forward_out<float4>(h) : nullptr;
     std::vector<double> nrm(2 * ncmax);
     int iters = 0;
     double worst = refine ? 0.0 : -1.0;
@@ -310,22 +426,31 @@ int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
         FDS_CUDA_TRY(cudaMemsetAsync(h->wnorm.p, 0, sizeof(double) * 2 * nc, s));
         {
             ProfScope ps("a7.residual", s);
-            fds_count_launch(), k_residual<<<dim3(gx, nc), 256, 0, s>>>(h->d_leaf_gidx.p, D, F, ld_rhs, nullptr,
-                                                                        leaf_in, h->wnorm.p);
+            fds_count_launch(), k_residual<cplx><<<dim3(gx, nc), 256, 0, s>>>(h->d_leaf_gidx.p, D, F, ld_rhs,
+                                                                              nullptr, leaf_in, h->wnorm.p);
         }
         FDS_CUDA_TRY(cudaGetLastError());
-        FDS_TRY(sweep_chunk<cplxf>(h, nc, s));
+        FDS_TRY(sweep_chunk(h, nc, s));
         fds_count_launch(), k_update<<<1024, 256, 0, s>>>(h->wX.p, leaf, D * nc, 1);
         FDS_CUDA_TRY(cudaGetLastError());
         // refinement against the FP64 compressed operator
         double prev = INFINITY;
         for (int it = 0; refine; ++it) {
-            FDS_TRY(forward_apply(h, h->wX.p, Yleaf, nc, s));
+            if (ffp) {
+                fds_count_launch(), k_split<<<1024, 256, 0, s>>>(h->wX.p, h->wXp.p, D * nc);
+                FDS_TRY(forward_apply<float4>(h, h->wXp.p, Ypleaf, nc, s));
+            } else {
+                FDS_TRY(forward_apply<cplx>(h, h->wX.p, Yleaf, nc, s));
+            }
             FDS_CUDA_TRY(cudaMemsetAsync(h->wnorm.p, 0, sizeof(double) * 2 * nc, s));
             {
                 ProfScope ps("a7.residual", s);
-                fds_count_launch(), k_residual<<<dim3(gx, nc), 256, 0, s>>>(h->d_leaf_gidx.p, D, F, ld_rhs, Yleaf,
-                                                                            leaf_in, h->wnorm.p);
+                if (ffp)
+                    fds_count_launch(), k_residual<float4><<<dim3(gx, nc), 256, 0, s>>>(
+                        h->d_leaf_gidx.p, D, F, ld_rhs, Ypleaf, leaf_in, h->wnorm.p);
+                else
+                    fds_count_launch(), k_residual<cplx><<<dim3(gx, nc), 256, 0, s>>>(
+                        h->d_leaf_gidx.p, D, F, ld_rhs, Yleaf, leaf_in, h->wnorm.p);
             }
             FDS_CUDA_TRY(cudaGetLastError());
             FDS_CUDA_TRY(cudaMemcpyAsync(nrm.data(), h->wnorm.p, sizeof(double) * 2 * nc, cudaMemcpyDeviceToHost, s));
@@ -342,7 +467,7 @@ int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
                 break;
             }
             prev = res;
-            FDS_TRY(sweep_chunk<cplxf>(h, nc, s));
+            FDS_TRY(sweep_chunk(h, nc, s));
             fds_count_launch(), k_update<<<1024, 256, 0, s>>>(h->wX.p, leaf, D * nc, 0);
             FDS_CUDA_TRY(cudaGetLastError());
         }

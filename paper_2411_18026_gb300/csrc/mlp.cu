@@ -240,7 +240,7 @@ int grad_launch(const float *params, const float *X, const float *t, const int *
                 float *loss, float *part, float *ploss, cudaStream_t s) {
     const int nblk = (n + GRAD_PER - 1) / GRAD_PER;
     const size_t smem = sizeof(GradSmem);
-    FDS_CUDA_TRY(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FDS_TRY(ensure_dyn_smem(k_mlp_grad, smem));
     const float inv = 1.f / (float)n;
     fds_count_launch(), k_mlp_grad<<<nblk, MT, smem, s>>>(params, X, t, idx, n, GRAD_PER, inv, part, ploss);
     FDS_CUDA_TRY(cudaGetLastError());

@@ -3,6 +3,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 #include <cstdio>
 #include <cstring>
@@ -13,6 +14,7 @@
 namespace {
 struct Rec {
     std::string name;
+    std::thread::id tid;     // scopes nest per thread (concurrent batched builds)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double flops = 0, bytes = 0, units = 0;
 };
@@ -56,6 +58,7 @@ void prof_begin(const char *name, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_mu);
     Rec r;
     r.name = name;
+    r.tid = std::this_thread::get_id();
     cudaEventCreate(&r.e0);
     cudaEventRecord(r.e0, s);
     g_open.push_back(r);
@@ -63,8 +66,9 @@ void prof_begin(const char *name, cudaStream_t s) {
 
 void prof_end(cudaStream_t s, double flops, double bytes, double units) {
     std::lock_guard<std::mutex> lk(g_mu);
+    const std::thread::id me = std::this_thread::get_id();
     for (auto it = g_open.rbegin(); it != g_open.rend(); ++it)
-        if (!it->e1) {
+        if (!it->e1 && it->tid == me) {
             cudaEventCreate(&it->e1);
             cudaEventRecord(it->e1, s);
             it->flops = flops;
@@ -102,4 +106,30 @@ extern "C" int fds_timing_report(char *buf, int32_t cap) {
         buf[n] = 0;
     }
     return (int)out.size() + 1;
+}
+
+namespace {
+thread_local char g_err[256] = "";
+}
+
+void fds_note_cuda_error(cudaError_t e, const char *file, int line) {
+    const char *f = strrchr(file, '/');
+    snprintf(g_err, sizeof(g_err), "%s (%s) at %s:%d", cudaGetErrorName(e), cudaGetErrorString(e), f ? f + 1 : file,
+             line);
+}
+
+extern "C" const char *fds_last_error_detail(void) { return g_err; }
+
+void fds_set_error_detail(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg ? msg : ""); }
+
+std::mutex &dyn_smem_mutex() {
+    static std::mutex m;
+    return m;
+}
+
+size_t &dyn_smem_slot(const void *kernel) {
+    static std::map<const void *, size_t> cur;   // default limit 48 KB until raised
+    auto it = cur.find(kernel);
+    if (it == cur.end()) it = cur.emplace(kernel, (size_t)48 * 1024).first;
+    return it->second;
 }

@@ -121,10 +121,22 @@ int fds_max_cells(const fds_handle *h) {
     return m;
 }
 
+// Levels l0 < l <= lsplit run in complex128, levels above lsplit in the
+// precision of the mixed sweep (complex64); the top solve is FP64.
+int sweep_split(const fds_handle *h) {
+    if (h->opt.precision != FDS_MIXED || h->L == h->l0) return h->L;
+    if (h->opt.sweep_fp64_levels >= 0) return std::min(h->L - 1, h->l0 + h->opt.sweep_fp64_levels);
+    // automatic: complex128 for the levels holding at most 1/8 of the leaf DOFs
+    int ls = h->l0;
+    for (int l = h->l0 + 1; l < h->L; ++l)
+        if (8 * h->lv[l].D <= h->lv[h->L].D) ls = l;
+    return ls;
+}
+
 template <class C>
-int sweep_workspace(fds_handle *h, int ncmax) {
+int workspace_levels(fds_handle *h, int ncmax, int lo, int hi, bool top) {
     typedef View<C> Vw;
-    const int L = h->L, l0 = h->l0;
+    const int L = h->L;
     auto &wz = Vw::z(h), &wf = Vw::f(h), &wt = Vw::t(h), &wr = Vw::r(h);
     if ((int)wz.size() != L + 1) {
         wz = std::vector<DBuf<C>>(L + 1);
@@ -132,18 +144,26 @@ int sweep_workspace(fds_handle *h, int ncmax) {
         wt = std::vector<DBuf<C>>(L + 1);
     }
     if ((int)wr.size() != L + 1) wr = std::vector<DBuf<C>>(L + 1);
-    for (int l = L; l > l0; --l) {
+    for (int l = hi; l >= lo && l > h->l0; --l) {
         Level &Cv = h->lv[l];
         FDS_TRY(grow(wz[l], (size_t)Cv.D * ncmax));
         FDS_TRY(grow(wr[l], (size_t)Cv.D * ncmax));
         FDS_TRY(grow(wf[l], (size_t)std::max<int64_t>(Cv.Rtot, 1) * ncmax));
         FDS_TRY(grow(wt[l], (size_t)std::max<int64_t>(Cv.Rtot, 1) * ncmax));
     }
-    FDS_TRY(grow(Vw::wtop(h), (size_t)std::max<int64_t>(h->Dtop, 1) * ncmax));
-    // the complex64 sweep solves the top system in FP64
-    FDS_TRY(grow(h->wtop, (size_t)std::max<int64_t>(h->Dtop, 1) * ncmax));
+    if (top) FDS_TRY(grow(Vw::wtop(h), (size_t)std::max<int64_t>(h->Dtop, 1) * ncmax));
     const int maxnb = fds_max_cells(h);
     if (Vw::refs(h).n < (size_t)4 * maxnb) FDS_TRY(Vw::refs(h).alloc((size_t)4 * maxnb));
+    return FDS_OK;
+}
+
+int sweep_workspace(fds_handle *h, int ncmax) {
+    const int ls = sweep_split(h);
+    FDS_TRY(workspace_levels<cplx>(h, ncmax, h->l0 + 1, ls, true));
+    if (ls < h->L || (h->opt.precision == FDS_MIXED)) {
+        // complex64 levels, the boundary level's vectors and the top in complex64
+        FDS_TRY(workspace_levels<cplxf>(h, ncmax, ls, h->L, true));
+    }
     return FDS_OK;
 }
 
@@ -157,108 +177,142 @@ C *sweep_leaf_out(fds_handle *h) {
     return (h->L > h->l0) ? View<C>::z(h)[h->L].p : View<C>::wtop(h).p;
 }
 
+namespace {
+
+// Upward step of level l: z_i = A_i^{-1} f_i, f~_i = A~_i V_i z_i, scattered
+// into the parent's right-hand side (level l-1 vector of type C, or the top).
 template <class C>
-int sweep_chunk(fds_handle *h, int nc, cudaStream_t s) {
+int up_level(fds_handle *h, int l, int nc, cudaStream_t s) {
     typedef View<C> Vw;
-    const int L = h->L, l0 = h->l0;
+    const int l0 = h->l0;
     const C one = Vw::one(), zero = czero<C>();
+    const int maxnb = fds_max_cells(h);
+    MatRefT<C> *rZ = Vw::refs(h).p, *rF = rZ + maxnb, *rT = rF + maxnb;
+    auto &wz = Vw::z(h), &wf = Vw::f(h), &wt = Vw::t(h), &wr = Vw::r(h);
+    const double esz = sizeof(C);
+    Level &Cv = h->lv[l];
+    Level &Pn = h->lv[l - 1];
+    const int nb = Cv.nb;
+    const int64_t ldr = std::max<int64_t>(Cv.Rtot, 1);
+    C *Z = wz[l].p, *F = wf[l].p, *U = wt[l].p, *Rh = wr[l].p;
+    fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, Rh, Cv.d_doff.p, nc, Cv.D, rF);
+    fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, Z, Cv.d_doff.p, nc, Cv.D, rZ);
+    {
+        ProfScope ps("a6.up_a_inverse", s);
+        ps.flops = 8.0 * Cv.sum_d2 * nc;
+        ps.bytes = esz * Cv.sum_d2 + 2 * esz * Cv.D * nc;
+        FDS_TRY(dense_gemm(nb, Cv.dmax, nc, Vw::Ainv(Cv), 0, rF, 0, rZ, one, zero, s));
+    }
+    fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, U, Cv.d_roff.p, nc, ldr, rT);
+    fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, F, Cv.d_roff.p, nc, ldr, rF);
+    {
+        ProfScope ps("a6.up_apply", s);
+        ps.flops = 8.0 * (Cv.sum_rd + Cv.sum_r2) * nc;
+        ps.bytes = esz * (Cv.sum_rd + Cv.sum_r2) + esz * (Cv.D + 2.0 * Cv.Rtot) * nc;
+        FDS_TRY(dense_gemm(nb, Cv.rmax, nc, Vw::V(Cv), 0, rZ, 0, rT, one, zero, s));
+        FDS_TRY(dense_gemm(nb, Cv.rmax, nc, Vw::At(Cv), 0, rT, 0, rF, one, zero, s));
+    }
+    C *par = (l - 1 > l0) ? wr[l - 1].p : Vw::wtop(h).p;
+    const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
+    fds_count_launch(), k_child_parent<C><<<nb, 256, 0, s>>>(nb, Cv.d_roff.p, Cv.d_k1.p, Cv.d_par_pos1.p,
+                                                             Cv.d_par_pos2.p, Pn.d_doff.p, F, ldr, par, ldp, nc, 0);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
+}
+
+// Downward step of level l: y_i from the parent's solution, then
+// x_i = z_i - W_i (f~_i - A~_i y_i).
+template <class C>
+int down_level(fds_handle *h, int l, int nc, cudaStream_t s) {
+    typedef View<C> Vw;
+    const int l0 = h->l0;
+    const C one = Vw::one();
     C mone = one;
     mone.x = -mone.x;
     const int maxnb = fds_max_cells(h);
-    MatRefT<C> *rZ = Vw::refs(h).p, *rF = rZ + maxnb, *rT = rF + maxnb, *rX = rT + maxnb;
-    auto &wz = Vw::z(h), &wf = Vw::f(h), &wt = Vw::t(h), &wr = Vw::r(h);
-    C *top = Vw::wtop(h).p;
+    MatRefT<C> *rZ = Vw::refs(h).p, *rF = rZ + maxnb, *rT = rF + maxnb;
+    auto &wz = Vw::z(h), &wf = Vw::f(h), &wt = Vw::t(h);
     const double esz = sizeof(C);
-    // upward
+    Level &Cv = h->lv[l];
+    Level &Pn = h->lv[l - 1];
+    const int nb = Cv.nb;
+    C *Z = wz[l].p, *F = wf[l].p, *Y = wt[l].p;
+    C *par = (l - 1 > l0) ? wz[l - 1].p : Vw::wtop(h).p;
+    const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
+    const int64_t ldr = std::max<int64_t>(Cv.Rtot, 1);
+    fds_count_launch(), k_child_parent<C><<<nb, 256, 0, s>>>(nb, Cv.d_roff.p, Cv.d_k1.p, Cv.d_par_pos1.p,
+                                                             Cv.d_par_pos2.p, Pn.d_doff.p, Y, ldr, par, ldp, nc, 1);
+    fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, Z, Cv.d_doff.p, nc, Cv.D, rZ);
+    fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, Y, Cv.d_roff.p, nc, ldr, rT);
+    fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, F, Cv.d_roff.p, nc, ldr, rF);
+    FDS_CUDA_TRY(cudaGetLastError());
+    ProfScope ps("a6.down_apply", s);
+    ps.flops = 8.0 * (Cv.sum_r2 + Cv.sum_rd) * nc;
+    ps.bytes = esz * (Cv.sum_r2 + Cv.sum_rd) + esz * (2.0 * Cv.D + 2.0 * Cv.Rtot) * nc;
+    FDS_TRY(dense_gemm(nb, Cv.rmax, nc, Vw::At(Cv), 0, rT, 0, rF, mone, one, s));
+    FDS_TRY(dense_gemm(nb, Cv.dmax, nc, Vw::W(Cv), 0, rF, 0, rZ, mone, one, s));
+    return FDS_OK;
+}
+
+template <class A, class B>
+int convert_vec(const A *src, B *dst, int64_t rows, int nc, cudaStream_t s) {
+    const int64_t ld = std::max<int64_t>(rows, 1);
+    fds_count_launch(), k_convert<A, B><<<256, 256, 0, s>>>(src, dst, rows, ld, ld, nc);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
+}
+
+int top_solve(fds_handle *h, int nc, cudaStream_t s) {
+    const int64_t ldt = std::max<int64_t>(h->Dtop, 1);
+    MatRef tv;
+    tv.p = h->wtop.p;
+    tv.rows = (int)h->Dtop;
+    tv.cols = nc;
+    tv.ld = (int)ldt;
+    MatRef *rX = h->wrefs.p + 3 * fds_max_cells(h);
+    FDS_CUDA_TRY(cudaMemcpyAsync(rX, &tv, sizeof(tv), cudaMemcpyHostToDevice, s));
+    ProfScope ps("a6.top_solve", s);
+    ps.flops = 8.0 * (double)h->Dtop * h->Dtop * nc;
+    ps.bytes = 16.0 * (double)h->Dtop * h->Dtop;
+    return dense_lu_solve(1, (int)h->Dtop, nc, h->rtop.p, h->ptop.p, h->d_ptop_off.p, rX, s);
+}
+
+}  // namespace
+
+// One sweep over nc columns: the right-hand sides are in sweep_leaf_in of the
+// leaf level's precision, the solution is left in sweep_leaf_out.
+int sweep_chunk(fds_handle *h, int nc, cudaStream_t s) {
+    const int L = h->L, l0 = h->l0;
+    const int ls = sweep_split(h);
+    const bool mixed = h->opt.precision == FDS_MIXED;
     for (int l = L; l > l0; --l) {
-        Level &Cv = h->lv[l];
-        Level &Pn = h->lv[l - 1];
-        const int nb = Cv.nb;
-        const int64_t ldr = std::max<int64_t>(Cv.Rtot, 1);
-        C *Z = wz[l].p, *F = wf[l].p, *U = wt[l].p, *Rh = wr[l].p;
-        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, Rh, Cv.d_doff.p, nc, Cv.D, rF);
-        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, Z, Cv.d_doff.p, nc, Cv.D, rZ);
-        {
-            ProfScope ps("a6.up_a_inverse", s);
-            ps.flops = 8.0 * Cv.sum_d2 * nc;
-            ps.bytes = esz * Cv.sum_d2 + 2 * esz * Cv.D * nc;
-            FDS_TRY(dense_gemm(nb, Cv.dmax, nc, Vw::Ainv(Cv), 0, rF, 0, rZ, one, zero, s));
+        if (l > ls) FDS_TRY(up_level<cplxf>(h, l, nc, s));
+        else FDS_TRY(up_level<cplx>(h, l, nc, s));
+        if (l == ls + 1) {
+            // complex64 right-hand side of level ls (or the top) -> complex128
+            if (ls > l0) FDS_TRY(convert_vec(h->wrf[ls].p, h->wr[ls].p, h->lv[ls].D, nc, s));
+            else FDS_TRY(convert_vec(h->wtopf.p, h->wtop.p, h->Dtop, nc, s));
         }
-        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, U, Cv.d_roff.p, nc, ldr, rT);
-        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, F, Cv.d_roff.p, nc, ldr, rF);
-        {
-            ProfScope ps("a6.up_apply", s);
-            ps.flops = 8.0 * (Cv.sum_rd + Cv.sum_r2) * nc;
-            ps.bytes = esz * (Cv.sum_rd + Cv.sum_r2) + esz * (Cv.D + 2.0 * Cv.Rtot) * nc;
-            FDS_TRY(dense_gemm(nb, Cv.rmax, nc, Vw::V(Cv), 0, rZ, 0, rT, one, zero, s));
-            FDS_TRY(dense_gemm(nb, Cv.rmax, nc, Vw::At(Cv), 0, rT, 0, rF, one, zero, s));
-        }
-        C *par = (l - 1 > l0) ? wr[l - 1].p : top;
-        const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
-        fds_count_launch(), k_child_parent<C><<<nb, 256, 0, s>>>(nb, Cv.d_roff.p, Cv.d_k1.p, Cv.d_par_pos1.p,
-                                                                 Cv.d_par_pos2.p, Pn.d_doff.p, F, ldr, par, ldp,
-                                                                 nc, 0);
-        FDS_CUDA_TRY(cudaGetLastError());
     }
-    // top: dense LU solve in FP64 (the complex64 sweep converts its top vector
-    // to complex128 and back)
-    {
-        const int64_t ldt = std::max<int64_t>(h->Dtop, 1);
-        MatRef tv;
-        tv.p = h->wtop.p;
-        tv.rows = (int)h->Dtop;
-        tv.cols = nc;
-        tv.ld = (int)ldt;
-        // MatRefT<cplxf> and MatRefT<cplx> have the same layout (pointer + 3 ints)
-        static_assert(sizeof(MatRefF) == sizeof(MatRef), "descriptor layouts differ");
-        MatRef *rX64 = reinterpret_cast<MatRef *>(rX);
-        if (sizeof(C) != sizeof(cplx))
-            fds_count_launch(), k_convert<C, cplx><<<256, 256, 0, s>>>(top, h->wtop.p, h->Dtop, ldt, ldt, nc);
-        FDS_CUDA_TRY(cudaMemcpyAsync(rX64, &tv, sizeof(tv), cudaMemcpyHostToDevice, s));
-        {
-            ProfScope ps("a6.top_solve", s);
-            ps.flops = 8.0 * (double)h->Dtop * h->Dtop * nc;
-            ps.bytes = 16.0 * (double)h->Dtop * h->Dtop;
-            FDS_TRY(dense_lu_solve(1, (int)h->Dtop, nc, h->rtop.p, h->ptop.p, h->d_ptop_off.p, rX64, s));
-        }
-        if (sizeof(C) != sizeof(cplx))
-            fds_count_launch(), k_convert<cplx, C><<<256, 256, 0, s>>>(h->wtop.p, top, h->Dtop, ldt, ldt, nc);
-        FDS_CUDA_TRY(cudaGetLastError());
-    }
-    // downward
+    if (mixed && L == l0) FDS_TRY(convert_vec(h->wtopf.p, h->wtop.p, h->Dtop, nc, s));
+    FDS_TRY(top_solve(h, nc, s));
+    if (mixed && L == l0) FDS_TRY(convert_vec(h->wtop.p, h->wtopf.p, h->Dtop, nc, s));
     for (int l = l0 + 1; l <= L; ++l) {
-        Level &Cv = h->lv[l];
-        Level &Pn = h->lv[l - 1];
-        const int nb = Cv.nb;
-        C *Z = wz[l].p, *F = wf[l].p, *Y = wt[l].p;
-        C *par = (l - 1 > l0) ? wz[l - 1].p : top;
-        const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
-        const int64_t ldr = std::max<int64_t>(Cv.Rtot, 1);
-        fds_count_launch(), k_child_parent<C><<<nb, 256, 0, s>>>(nb, Cv.d_roff.p, Cv.d_k1.p, Cv.d_par_pos1.p,
-                                                                 Cv.d_par_pos2.p, Pn.d_doff.p, Y, ldr, par, ldp,
-                                                                 nc, 1);
-        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, Z, Cv.d_doff.p, nc, Cv.D, rZ);
-        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, Y, Cv.d_roff.p, nc, ldr, rT);
-        fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, F, Cv.d_roff.p, nc, ldr, rF);
-        FDS_CUDA_TRY(cudaGetLastError());
-        // F <- f~ - A~ y ;  Z <- z - W F
-        ProfScope ps("a6.down_apply", s);
-        ps.flops = 8.0 * (Cv.sum_r2 + Cv.sum_rd) * nc;
-        ps.bytes = esz * (Cv.sum_r2 + Cv.sum_rd) + esz * (2.0 * Cv.D + 2.0 * Cv.Rtot) * nc;
-        FDS_TRY(dense_gemm(nb, Cv.rmax, nc, Vw::At(Cv), 0, rT, 0, rF, mone, one, s));
-        FDS_TRY(dense_gemm(nb, Cv.dmax, nc, Vw::W(Cv), 0, rF, 0, rZ, mone, one, s));
+        if (l == ls + 1) {
+            // complex128 solution of level ls (or the top) -> complex64
+            if (ls > l0) FDS_TRY(convert_vec(h->wz[ls].p, h->wzf[ls].p, h->lv[ls].D, nc, s));
+            else FDS_TRY(convert_vec(h->wtop.p, h->wtopf.p, h->Dtop, nc, s));
+        }
+        if (l > ls) FDS_TRY(down_level<cplxf>(h, l, nc, s));
+        else FDS_TRY(down_level<cplx>(h, l, nc, s));
     }
     return FDS_OK;
 }
 
-template int sweep_workspace<cplx>(fds_handle *, int);
-template int sweep_workspace<cplxf>(fds_handle *, int);
 template cplx *sweep_leaf_in<cplx>(fds_handle *);
 template cplxf *sweep_leaf_in<cplxf>(fds_handle *);
 template cplx *sweep_leaf_out<cplx>(fds_handle *);
 template cplxf *sweep_leaf_out<cplxf>(fds_handle *);
-template int sweep_chunk<cplx>(fds_handle *, int, cudaStream_t);
-template int sweep_chunk<cplxf>(fds_handle *, int, cudaStream_t);
 
 int fds_solve_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
     if (nrhs <= 0) return FDS_OK;
@@ -266,7 +320,7 @@ int fds_solve_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
     const int N = h->N;
     const int64_t ld_rhs = 2LL * N;
     const int ncmax = std::min(nrhs, SOLVE_CHUNK);
-    FDS_TRY(sweep_workspace<cplx>(h, ncmax));
+    FDS_TRY(sweep_workspace(h, ncmax));
     const Level &Lf = h->lv[h->L];
     cplx *leaf_in = sweep_leaf_in<cplx>(h), *leaf_out = sweep_leaf_out<cplx>(h);
     cudaEvent_t e0, e1;
@@ -278,7 +332,7 @@ int fds_solve_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
         cplx *rhs = d_rhs + (int64_t)c0 * ld_rhs;
         fds_count_launch(), k_leaf_gather<<<1024, 256, 0, s>>>(h->d_leaf_gidx.p, Lf.D, rhs, ld_rhs, leaf_in, nc, 0);
         FDS_CUDA_TRY(cudaGetLastError());
-        FDS_TRY(sweep_chunk<cplx>(h, nc, s));
+        FDS_TRY(sweep_chunk(h, nc, s));
         fds_count_launch(), k_leaf_gather<<<1024, 256, 0, s>>>(h->d_leaf_gidx.p, Lf.D, rhs, ld_rhs, leaf_out, nc, 1);
         FDS_CUDA_TRY(cudaGetLastError());
     }

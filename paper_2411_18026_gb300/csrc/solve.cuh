@@ -6,8 +6,10 @@
 constexpr int SOLVE_CHUNK = 256;   // right-hand sides per sweep
 
 int fds_max_cells(const fds_handle *h);
-// Grow the sweep workspace of precision C for ncmax columns.
-template <class C>
+// Last level (from the top) of the sweep that runs in complex128: L for
+// FDS_FP64; for FDS_MIXED min(L - 1, l0 + sweep_fp64_levels) (L when L = l0).
+int sweep_split(const fds_handle *h);
+// Grow the sweep workspace for ncmax columns.
 int sweep_workspace(fds_handle *h, int ncmax);
 // Leaf-order vectors (D_L x nc, column-major): the sweep reads the right-hand
 // sides from sweep_leaf_in and leaves the solution in sweep_leaf_out (the
@@ -16,6 +18,5 @@ template <class C>
 C *sweep_leaf_in(fds_handle *h);
 template <class C>
 C *sweep_leaf_out(fds_handle *h);
-// One sweep over nc columns.
-template <class C>
+// One sweep over nc columns (levels above sweep_split in complex64).
 int sweep_chunk(fds_handle *h, int nc, cudaStream_t s);

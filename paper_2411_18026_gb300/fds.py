@@ -35,7 +35,13 @@ FDS_MLP_NPARAM = 5345
 
 class FdsError(RuntimeError):
     def __init__(self, code, what):
-        super().__init__("%s failed: %s (%d)" % (what, _lib_err(code), code))
+        detail = ""
+        if code in (FDS_ERR_CUDA, FDS_ERR_OOM):
+            try:
+                detail = " [" + lib().fds_last_error_detail().decode() + "]"
+            except Exception:
+                detail = ""
+        super().__init__("%s failed: %s (%d)%s" % (what, _lib_err(code), code, detail))
         self.code = code
 
 
@@ -54,7 +60,8 @@ class fds_options(ctypes.Structure):
                 ("proxy_points", ctypes.c_int32), ("top_level", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("alpha_re", ctypes.c_double), ("alpha_im", ctypes.c_double),
                 ("alpha_set", ctypes.c_int32), ("cuda_stream", ctypes.c_uint64), ("ir_tol", ctypes.c_double),
-                ("ir_max_iter", ctypes.c_int32), ("ir_apply", ctypes.c_int32), ("rank_mode", ctypes.c_int32),
+                ("ir_max_iter", ctypes.c_int32), ("ir_apply", ctypes.c_int32), ("sweep_fp64_levels", ctypes.c_int32),
+                ("rank_mode", ctypes.c_int32),
                 ("mlp_params", ctypes.POINTER(ctypes.c_float)), ("sketch_extra", ctypes.c_int32),
                 ("record_features", ctypes.c_int32)]
 
@@ -85,6 +92,8 @@ def lib():
     L.fds_default_options.restype = None
     L.fds_error_string.argtypes = [ctypes.c_int]
     L.fds_error_string.restype = ctypes.c_char_p
+    L.fds_last_error_detail.argtypes = []
+    L.fds_last_error_detail.restype = ctypes.c_char_p
     L.fds_build.argtypes = [ctypes.POINTER(fds_geometry), f64, f64, f64, f64, ctypes.POINTER(vp)]
     L.fds_build_ex.argtypes = [ctypes.POINTER(fds_geometry), f64, f64, f64, f64, ctypes.POINTER(fds_options),
                                ctypes.POINTER(vp)]
@@ -116,10 +125,15 @@ def lib():
     L.fds_mlp_adam.argtypes = [vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                u64]
     L.fds_mlp_train.argtypes = [vp, vp, vp, i32, vp, i32, i32, ctypes.c_float, vp, u64]
+    L.fds_build_batch.argtypes = [i32, ctypes.POINTER(fds_geometry), dp, f64, f64, f64, ctypes.POINTER(fds_options),
+                                  i32, ctypes.POINTER(vp)]
+    L.fds_solve_batch.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i32), i32]
+    L.fds_handle_stream.argtypes = [vp]
+    L.fds_handle_stream.restype = ctypes.c_uint64
     for f in ("fds_build", "fds_build_ex", "fds_rhs_plane_wave", "fds_rhs_plane_wave_device", "fds_solve",
               "fds_solve_device", "fds_stats_get", "fds_level_ranks", "fds_eval_entries", "fds_eval_cross",
               "fds_id_batched", "fds_lu_batched", "fds_lu_batched_noalloc", "fds_features_get", "fds_mlp_forward",
-              "fds_mlp_loss_grad", "fds_mlp_adam", "fds_mlp_train"):
+              "fds_mlp_loss_grad", "fds_mlp_adam", "fds_mlp_train", "fds_build_batch", "fds_solve_batch"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -183,7 +197,7 @@ class Handle:
 
 def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy_ratio=1.5, proxy_points=64,
               alpha=None, stream=0, precision=FDS_FP64, ir_tol=None, ir_max_iter=None, ir_apply=None,
-              mlp_params=None, sketch_extra=None, record_features=False):
+              mlp_params=None, sketch_extra=None, record_features=False, sweep_fp64_levels=None):
     """Factorise; mlp_params (FDS_MLP_NPARAM floats) selects the learned-rank ID."""
     xy = np.ascontiguousarray(xy, dtype=np.float64)
     g = fds_geometry(len(xy), xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(rho))
@@ -208,11 +222,44 @@ def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy
         o.mlp_params = prm.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
     if sketch_extra is not None:
         o.sketch_extra = sketch_extra
+    if sweep_fp64_levels is not None:
+        o.sweep_fp64_levels = sweep_fp64_levels
     o.record_features = 1 if record_features else 0
     out = ctypes.c_void_p()
     _check(lib().fds_build_ex(ctypes.byref(g), float(omega), float(lam), float(mu), float(tol), ctypes.byref(o),
                               ctypes.byref(out)), "fds_build")
     return Handle(out, len(xy))
+
+
+def fds_build_batch(cavities, lam, mu, tol, n_streams=8, rho=1.0, leaf_size=64, top_level=1, precision=FDS_FP64,
+                    ir_tol=None):
+    """Build many cavities concurrently (dicts with 'xy' and 'omega'); returns handles."""
+    n = len(cavities)
+    xys = [np.ascontiguousarray(c["xy"], dtype=np.float64) for c in cavities]
+    geoms = (fds_geometry * n)(*[fds_geometry(len(x), x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(rho))
+                                 for x in xys])
+    om = np.ascontiguousarray([c["omega"] for c in cavities], dtype=np.float64)
+    o = default_options()
+    o.leaf_size, o.top_level, o.precision = leaf_size, top_level, precision
+    if ir_tol is not None:
+        o.ir_tol = ir_tol
+    out = (ctypes.c_void_p * n)()
+    _check(lib().fds_build_batch(n, geoms, om.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(lam), float(mu),
+                                 float(tol), ctypes.byref(o), int(n_streams), out), "fds_build_batch")
+    return [Handle(ctypes.c_void_p(out[i]), len(xys[i])) for i in range(n)]
+
+
+def fds_solve_batch(handles, d_rhs_list, n_streams=8):
+    """Solve in place: d_rhs_list[i] complex128 CUDA tensor (nrhs_i, 2 n_i) for handle i."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.ptr.value for h in handles])
+    ps = (ctypes.c_void_p * n)(*[t.data_ptr() for t in d_rhs_list])
+    nr = (ctypes.c_int32 * n)(*[t.shape[0] for t in d_rhs_list])
+    _check(lib().fds_solve_batch(n, hs, ps, nr, int(n_streams)), "fds_solve_batch")
+
+
+def fds_handle_stream(h):
+    return int(lib().fds_handle_stream(h.ptr))
 
 
 def fds_rhs_plane_wave(h, kinds, angles):

@@ -45,3 +45,50 @@ def train(features, fracs, init, order, batch=256, lr=2e-3, stream=None):
     fds.fds_mlp_train(d_p, d_X, d_t, d_o, batch, lr, d_l, stream)
     torch.cuda.synchronize()
     return d_p.cpu().numpy(), d_l.cpu().numpy()
+
+
+PARAMS_FILE = __import__("os").path.join(__import__("os").path.dirname(__file__), "rank_mlp_params.npy")
+
+
+def load_params(path=PARAMS_FILE):
+    """The parameter vector trained by `python -m paper_2411_18026_gb300.learned`
+    (float32, FDS_MLP_NPARAM), or None if it has not been trained."""
+    import os
+    if not os.path.exists(path):
+        return None
+    p = np.load(path)
+    return p if p.size == fds.FDS_MLP_NPARAM else None
+
+
+def main(argv=None):
+    """Train the rank network on seeded random cavities (ellipses and stars,
+    2^12..2^15 nodes, k_T a in [1, 20], tol 1e-9 and 1e-8, leaf 64) and save
+    the parameters next to this module."""
+    import argparse
+    import sys
+    import time
+    ap = argparse.ArgumentParser(prog="python -m paper_2411_18026_gb300.learned")
+    ap.add_argument("--count", type=int, default=160, help="training cavities")
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--out", default=PARAMS_FILE)
+    a = ap.parse_args(argv)
+    sys.path.insert(0, __import__("os").path.dirname(__import__("os").path.dirname(__file__)))
+    import workloads
+    from . import build
+    build.build()
+    t0 = time.time()
+    cav = workloads.random_cavities(a.count, seed=workloads.SEED + 4, nmin_log2=12, nmax_log2=15)
+    half = len(cav) // 2
+    F1, r1 = collect(cav[:half], 1e-9)
+    F2, r2 = collect(cav[half:], 1e-8)
+    F, r = np.concatenate([F1, F2]), np.concatenate([r1, r2])
+    t1 = time.time()
+    order = workloads.minibatch_order(len(F), 256, a.epochs)
+    p, losses = train(F, r, workloads.mlp_init(), order, batch=256, lr=2e-3)
+    np.save(a.out, p.astype(np.float32))
+    print("samples %d, collect %.1fs, train %.1fs, loss %.3e -> %.3e, saved %s" %
+          (len(F), t1 - t0, time.time() - t1, losses[:10].mean(), losses[-50:].mean(), a.out))
+
+
+if __name__ == "__main__":
+    main()

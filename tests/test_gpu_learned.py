@@ -185,3 +185,59 @@ def test_untrained_prediction_falls_back():
         assert np.array_equal(fds.fds_level_ranks(ha, l, nb), fds.fds_level_ranks(hl, l, nb))
     ha.close()
     hl.close()
+
+
+def _id_ms(fds, xy, omega, tol, params):
+    fds.fds_timing_reset()
+    fds.fds_timing_enable(True)
+    h = fds.fds_build(xy, omega, 2.0, 1.0, tol, leaf_size=64, mlp_params=params)
+    fds.fds_timing_enable(False)
+    rep = fds.fds_timing_report()
+    st = fds.fds_stats_get(h)
+    ms = sum(v["ms"] for k, v in rep.items() if k.startswith("a2."))
+    return h, ms, st
+
+
+def test_trained_network_gains_over_adaptive_id():
+    # The trained network sizes the sketch; the gain is the ID time against the
+    # adaptive CPQR (same tolerance), at an accuracy that stays within 10 eps
+    # of the adaptive build's solution.  A network predicting k = n (sketch of
+    # n + extra rows) isolates what the prediction adds to the sketch.
+    torch_cuda()
+    fds = fdslib()
+    from paper_2411_18026_gb300 import learned
+    p = learned.load_params()
+    if p is None:
+        p, _, _, _ = _trained(fds)
+    full = np.zeros(fds.FDS_MLP_NPARAM)
+    full[fds.FDS_MLP_NTRAIN - 1] = 1.0            # b3 = 1: predicts k / n = 1
+    full[fds.FDS_MLP_NTRAIN + 16:] = 1.0
+    xy = workloads.star(1 << 16, 0.25, 6, rot=0.7)
+    omega = workloads.omega_for_kTa(12.0)
+    tol = 1e-8
+    for _ in range(2):      # warm-up (first launches load the kernels)
+        ha, ms_a, _ = _id_ms(fds, xy, omega, tol, None)
+        ha.close()
+    ha, ms_a, st_a = _id_ms(fds, xy, omega, tol, None)
+    hl, ms_l, st_l = _id_ms(fds, xy, omega, tol, p)
+    hf, ms_f, st_f = _id_ms(fds, xy, omega, tol, full)
+    print("ID ms: adaptive %.2f, sketch k=n %.2f (fallback %d), learned %.2f (sketched %d, fallback %d)"
+          % (ms_a, ms_f, st_f.id_fallback, ms_l, st_l.id_sketched, st_l.id_fallback))
+    assert st_l.id_fallback <= 0.2 * (st_l.id_sketched + st_l.id_fallback)
+    assert ms_l < ms_a
+    # the sketch keeps a few more skeleton columns than the adaptive ID
+    ka = sum(st_a.skeleton_dofs[l] for l in range(st_a.top_level + 1, st_a.levels + 1))
+    kl = sum(st_l.skeleton_dofs[l] for l in range(st_l.top_level + 1, st_l.levels + 1))
+    print("skeleton DOFs: adaptive %d, learned %d (+%.1f%%)" % (ka, kl, 100.0 * (kl - ka) / ka))
+    assert ka <= kl <= 1.25 * ka
+    kinds, ang = workloads.plane_wave_set(2)
+    F = fds.fds_rhs_plane_wave(ha, kinds, ang)
+    xa = fds.fds_solve(ha, F)
+    xl = fds.fds_solve(hl, F)
+    # two compressions at the same tolerance: they differ by the compression
+    # error amplified by the operator's conditioning, which grows with N
+    err = np.linalg.norm(xl - xa) / np.linalg.norm(xa)
+    print("learned vs adaptive solution: %.2e" % err)
+    assert err <= 1e-5
+    for h in (ha, hl, hf):
+        h.close()

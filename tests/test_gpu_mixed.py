@@ -132,3 +132,22 @@ def test_mixed_not_converged_is_reported():
     st = fds.fds_stats_get(h)
     assert st.ir_residual > 0 and st.ir_iters <= 1
     h.close()
+
+
+@pytest.mark.parametrize("levels", [1, 3, 20])
+def test_mixed_sweep_with_fp64_upper_levels(levels):
+    # the upper tree levels keep complex128 factors; 20 exceeds the depth
+    # (clamped to all but the leaf level)
+    torch_cuda()
+    fds = fdslib()
+    xy = workloads.star(1024)
+    omega = workloads.omega_for_kTa(10.0)
+    h64, hmx = _pair(fds, xy, omega, 1e-9, leaf_size=32, top_level=1)
+    hmx.close()
+    hmx = fds.fds_build(xy, omega, 2.0, 1.0, 1e-9, leaf_size=32, top_level=1, precision=fds.FDS_MIXED,
+                        sweep_fp64_levels=levels)
+    F = fds.fds_rhs_plane_wave(h64, np.array([0, 1, 1], np.int32), np.array([0.1, 1.1, 4.0]))
+    assert _colmax(fds.fds_solve(hmx, F), fds.fds_solve(h64, F)) < 1e-7
+    assert fds.fds_stats_get(hmx).ir_iters >= 1
+    h64.close()
+    hmx.close()
