@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--ir-tol", type=float, default=1e-8)
     p.add_argument("--sweep-fp64-levels", type=int, default=-1)
+    p.add_argument("--merge-c64", action="store_true", help="merge the complex64 levels in complex64")
     p.add_argument("--rank", default="adaptive", choices=["learned", "adaptive"],
                    help="learned: the trained rank network (falls back to adaptive if it has not been trained); "
                         "its skeletons differ from the plain solver's, so its error against the plain FP64 "
@@ -305,7 +306,7 @@ def main():
     def step(precision=prec, out=d_F, rec=info, params=mlp):
         h = fds.fds_build(xy, omega, 2.0, 1.0, args.eps, leaf_size=args.leaf, top_level=args.top, stream=stream,
                           precision=precision, ir_tol=args.ir_tol, sweep_fp64_levels=args.sweep_fp64_levels,
-                          mlp_params=params)
+                          mlp_params=params, merge_c64=args.merge_c64 and precision == fds.FDS_MIXED)
         fds.fds_rhs_plane_wave_device(h, d_kinds, d_angles, out, stream)
         rec["converged"] = True
         try:
@@ -392,6 +393,7 @@ def main():
         o = fds.default_options()
         o.leaf_size, o.top_level = args.leaf, args.top
         o.precision, o.ir_tol, o.sweep_fp64_levels = prec, args.ir_tol, args.sweep_fp64_levels
+        o.merge_c64 = 1 if args.merge_c64 else 0
         mlp32 = None
         if mlp is not None:
             mlp32 = np.ascontiguousarray(mlp, dtype=np.float32)

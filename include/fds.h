@@ -103,6 +103,9 @@ typedef struct {
                               complex128 (the rest are complex64; the rounding error of the
                               complex64 sweep comes mostly from the upper levels); -1 (default):
                               the levels with at most 1/8 of the leaf level's DOFs */
+    int32_t merge_c64;     /* FDS_MIXED: 1 merges the complex64 levels in complex64 too (faster
+                              build; their rounding then also enters the upper levels'
+                              factors, so refinement may need more sweeps); default 0 */
     int32_t rank_mode;     /* FDS_RANK_ADAPTIVE (default) or FDS_RANK_LEARNED */
     const float *mlp_params; /* FDS_RANK_LEARNED: host, FDS_MLP_NPARAM floats, copied at the call */
     int32_t sketch_extra;  /* FDS_RANK_LEARNED: sketch rows beyond the predicted rank; default 12 */

@@ -24,6 +24,7 @@ extern "C" void fds_default_options(fds_options *o) {
     o->ir_max_iter = 10;
     o->ir_apply = FDS_APPLY_FF;
     o->sweep_fp64_levels = -1;
+    o->merge_c64 = 0;
     o->rank_mode = FDS_RANK_ADAPTIVE;
     o->mlp_params = nullptr;
     o->sketch_extra = 12;

@@ -342,19 +342,32 @@ __global__ void k_make_V(const MatRef *__restrict__ Vs, const int *__restrict__ 
 }
 
 // W = V^H (d x r) as the right-hand side of A_i W = U_i, U_i = V_i^H.
-__global__ void k_conj_transpose(const MatRef *__restrict__ Src, const MatRef *__restrict__ Dst) {
-    const MatRef S = Src[blockIdx.x], D = Dst[blockIdx.x];
+template <class C>
+__global__ void k_conj_transpose(const MatRefT<C> *__restrict__ Src, const MatRefT<C> *__restrict__ Dst) {
+    const MatRefT<C> S = Src[blockIdx.x], D = Dst[blockIdx.x];
     for (int64_t e = threadIdx.x; e < (int64_t)S.rows * S.cols; e += blockDim.x) {
         const int i = (int)(e % S.rows), j = (int)(e / S.rows);
         D.p[j + (int64_t)i * D.ld] = cconj(S.p[i + (int64_t)j * S.ld]);
     }
 }
 
-__global__ void k_set_identity(const MatRef *__restrict__ Ms) {
-    const MatRef M = Ms[blockIdx.x];
+template <class C>
+__global__ void k_set_identity(const MatRefT<C> *__restrict__ Ms) {
+    const MatRefT<C> M = Ms[blockIdx.x];
     for (int64_t e = threadIdx.x; e < (int64_t)M.rows * M.cols; e += blockDim.x) {
         const int i = (int)(e % M.rows), j = (int)(e / M.rows);
-        M.p[i + (int64_t)j * M.ld] = mkc(i == j ? 1.0 : 0.0, 0.0);
+        C v = czero<C>();
+        if (i == j) v.x = 1;
+        M.p[i + (int64_t)j * M.ld] = v;
+    }
+}
+
+// element-wise precision change of a contiguous buffer
+template <class A, class B>
+__global__ void k_cast(const A *__restrict__ src, B *dst, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        dst[e].x = src[e].x;
+        dst[e].y = src[e].y;
     }
 }
 
@@ -864,18 +877,32 @@ int fds_build_impl(fds_handle *h) {
             C.offpiv[b + 1] = C.offpiv[b] + dv[b];
         }
         C.offW = C.offV;
+        // FDS_MIXED: the lower levels, whose sweep runs in complex64, are merged
+        // in complex64 too (decided from the top down so that the complex128
+        // levels stay a prefix below the top)
+        C.c64 = false;
+        if (h->opt.precision == FDS_MIXED && !h->fp64_reached) {
+            if (h->opt.sweep_fp64_levels >= 0) C.c64 = l > std::min(L - 1, h->l0 + h->opt.sweep_fp64_levels);
+            else C.c64 = (l == L) || 8 * C.D > h->lv[L].D;
+            if (!C.c64) h->fp64_reached = true;
+        }
+        const bool merge64 = C.c64 && h->opt.merge_c64;   // merged in complex64 (else FP64, converted later)
         FDS_TRY(C.V.alloc(C.offV[nb]));
-        FDS_TRY(C.W.alloc(C.offW[nb]));
         FDS_TRY(C.At.alloc(C.offAt[nb]));
         FDS_TRY(C.piv.alloc(C.offpiv[nb]));
         FDS_TRY(C.d_offpiv.upload(C.offpiv, s));
         FDS_TRY(make_refs(C.rV, C.V.p, C.offV, rv, dv, s));
-        FDS_TRY(make_refs(C.rW, C.W.p, C.offW, dv, rv, s));
         FDS_TRY(make_refs(C.rAt, C.At.p, C.offAt, rv, rv, s));
+        if (!merge64) {
+            FDS_TRY(C.W.alloc(C.offW[nb]));
+            FDS_TRY(make_refs(C.rW, C.W.p, C.offW, dv, rv, s));
+        }
         DBuf<cplx> S;
         DBuf<MatRef> rS;
-        FDS_TRY(S.alloc(C.offAt[nb]));
-        FDS_TRY(make_refs(rS, S.p, C.offAt, rv, rv, s));
+        if (!merge64) {
+            FDS_TRY(S.alloc(C.offAt[nb]));
+            FDS_TRY(make_refs(rS, S.p, C.offAt, rv, rv, s));
+        }
         DBuf<int> d_n1, d_n2;
         FDS_TRY(d_n1.upload(C.n1, s));
         FDS_TRY(d_n2.upload(C.n2, s));
@@ -884,6 +911,25 @@ int fds_build_impl(fds_handle *h) {
         fds_count_launch(), k_make_V<<<nb, 256, 0, s>>>(C.rV.p, d_n1.p, d_n2.p, C.d_k1.p, C.d_k2.p, d_perm.p, d_poff.p, d_T.p,
                                     d_toff.p);
         FDS_CUDA_TRY(cudaGetLastError());
+        // keep T and the permuted DOF order for the structured V of the solve
+        {
+            std::vector<int> vmap(C.D);
+            C.kmax = 0;
+            C.sum_tm = 0;
+            for (int b = 0; b < nb; ++b)
+                for (int c = 0; c < 2; ++c) {
+                    const int n = c ? C.n2[b] : C.n1[b], k = c ? C.k2[b] : C.k1[b];
+                    const int coff = c ? C.n1[b] : 0;
+                    for (int q = 0; q < n; ++q) vmap[C.doff[b] + coff + q] = coff + C.perm[C.permoff[2 * b + c] + q];
+                    C.kmax = std::max(C.kmax, k);
+                    C.sum_tm += (double)k * (n - k);
+                }
+            FDS_TRY(C.d_vmap.upload(vmap, s));
+            FDS_TRY(C.d_toff.upload(toff, s));
+            FDS_TRY(C.d_n1.upload(C.n1, s));
+            FDS_TRY(C.d_n2.upload(C.n2, s));
+            C.T = std::move(d_T);
+        }
         DBuf<int> info;
         FDS_TRY(info.alloc(nb));
         double fl_lu = 0, fl_w = 0, fl_s = 0, fl_slu = 0, fl_at = 0;
@@ -895,34 +941,6 @@ int fds_build_impl(fds_handle *h) {
             fl_slu += 8.0 / 3.0 * r * r * r;
             fl_at += 8.0 * r * r * r;
         }
-        {
-            ProfScope ps("a3.merge_lu", s);
-            ps.flops = fl_lu;
-            FDS_TRY(dense_lu(nb, C.dmax, C.rLU.p, C.piv.p, C.d_offpiv.p, info.p, s));
-        }
-        fds_count_launch(), k_conj_transpose<<<nb, 256, 0, s>>>(C.rV.p, C.rW.p);
-        FDS_CUDA_TRY(cudaGetLastError());
-        {
-            ProfScope ps("a3.merge_w_solve", s);
-            ps.flops = fl_w;
-            FDS_TRY(dense_lu_solve(nb, C.dmax, C.rmax, C.rLU.p, C.piv.p, C.d_offpiv.p, C.rW.p, s));
-        }
-        // A_i^{-1} for the solve sweep (Sec. 7.3 step 3(b)), from the LU factors
-        // by a solve against the identity; the LU itself is not kept
-        FDS_TRY(C.Ainv.alloc(C.offA[nb]));
-        FDS_TRY(make_refs(C.rAinv, C.Ainv.p, C.offA, dv, dv, s));
-        fds_count_launch(), k_set_identity<<<nb, 256, 0, s>>>(C.rAinv.p);
-        FDS_CUDA_TRY(cudaGetLastError());
-        {
-            ProfScope ps("a3.merge_a_inverse", s);
-            ps.flops = fl_lu * 3.0;
-            FDS_TRY(dense_lu_solve(nb, C.dmax, C.dmax, C.rLU.p, C.piv.p, C.d_offpiv.p, C.rAinv.p, s));
-        }
-        {
-            ProfScope ps("a3.merge_s_gemm", s);
-            ps.flops = fl_s;
-            FDS_TRY(dense_gemm(nb, C.rmax, C.rmax, C.rV.p, 0, C.rW.p, 0, rS.p, mkc(1, 0), mkc(0, 0), s));
-        }
         DBuf<int> spiv, info2;
         DBuf<int64_t> d_sp;
         std::vector<int64_t> spoff(nb + 1, 0);
@@ -930,17 +948,106 @@ int fds_build_impl(fds_handle *h) {
         FDS_TRY(spiv.alloc(spoff[nb]));
         FDS_TRY(d_sp.upload(spoff, s));
         FDS_TRY(info2.alloc(nb));
-        {
-            ProfScope ps("a3.merge_s_lu", s);
-            ps.flops = fl_slu;
-            FDS_TRY(dense_lu(nb, C.rmax, rS.p, spiv.p, d_sp.p, info2.p, s));
-        }
-        fds_count_launch(), k_set_identity<<<nb, 256, 0, s>>>(C.rAt.p);
-        FDS_CUDA_TRY(cudaGetLastError());
-        {
-            ProfScope ps("a3.merge_inverse", s);
-            ps.flops = fl_at;
-            FDS_TRY(dense_lu_solve(nb, C.rmax, C.rmax, rS.p, spiv.p, d_sp.p, C.rAt.p, s));
+        if (merge64) {
+            // complex64 copies of the level's blocks and of V; W, A_i^{-1},
+            // S and A~ in complex64; A~ back in complex128 for the parent
+            const int64_t nA = C.offA[nb], nV = C.offV[nb], nS = C.offAt[nb];
+            DBuf<cplxf> LUf, Sf;
+            DBuf<MatRefF> rLUf, rSf;
+            FDS_TRY(LUf.alloc(nA));
+            FDS_TRY(C.Vf.alloc(nV));
+            FDS_TRY(C.Wf.alloc(nV));
+            FDS_TRY(C.Ainvf.alloc(nA));
+            FDS_TRY(C.Atf.alloc(nS));
+            FDS_TRY(Sf.alloc(nS));
+            FDS_TRY(make_refs_t(rLUf, LUf.p, C.offA, dv, dv, s));
+            FDS_TRY(make_refs_t(C.rVf, C.Vf.p, C.offV, rv, dv, s));
+            FDS_TRY(make_refs_t(C.rWf, C.Wf.p, C.offW, dv, rv, s));
+            FDS_TRY(make_refs_t(C.rAinvf, C.Ainvf.p, C.offA, dv, dv, s));
+            FDS_TRY(make_refs_t(C.rAtf, C.Atf.p, C.offAt, rv, rv, s));
+            FDS_TRY(make_refs_t(rSf, Sf.p, C.offAt, rv, rv, s));
+            fds_count_launch(), k_cast<cplx, cplxf><<<1024, 256, 0, s>>>(C.LU.p, LUf.p, nA);
+            fds_count_launch(), k_cast<cplx, cplxf><<<1024, 256, 0, s>>>(C.V.p, C.Vf.p, nV);
+            FDS_CUDA_TRY(cudaGetLastError());
+            {
+                ProfScope ps("a3.merge_lu", s);
+                ps.flops = fl_lu;
+                FDS_TRY(dense_lu(nb, C.dmax, rLUf.p, C.piv.p, C.d_offpiv.p, info.p, s));
+            }
+            fds_count_launch(), k_conj_transpose<cplxf><<<nb, 256, 0, s>>>(C.rVf.p, C.rWf.p);
+            FDS_CUDA_TRY(cudaGetLastError());
+            {
+                ProfScope ps("a3.merge_w_solve", s);
+                ps.flops = fl_w;
+                FDS_TRY(dense_lu_solve(nb, C.dmax, C.rmax, rLUf.p, C.piv.p, C.d_offpiv.p, C.rWf.p, s));
+            }
+            fds_count_launch(), k_set_identity<cplxf><<<nb, 256, 0, s>>>(C.rAinvf.p);
+            FDS_CUDA_TRY(cudaGetLastError());
+            {
+                ProfScope ps("a3.merge_a_inverse", s);
+                ps.flops = fl_lu * 3.0;
+                FDS_TRY(dense_lu_solve(nb, C.dmax, C.dmax, rLUf.p, C.piv.p, C.d_offpiv.p, C.rAinvf.p, s));
+            }
+            {
+                ProfScope ps("a3.merge_s_gemm", s);
+                ps.flops = fl_s;
+                FDS_TRY(dense_gemm(nb, C.rmax, C.rmax, C.rVf.p, 0, C.rWf.p, 0, rSf.p, mkcf(1, 0), mkcf(0, 0), s));
+            }
+            {
+                ProfScope ps("a3.merge_s_lu", s);
+                ps.flops = fl_slu;
+                FDS_TRY(dense_lu(nb, C.rmax, rSf.p, spiv.p, d_sp.p, info2.p, s));
+            }
+            fds_count_launch(), k_set_identity<cplxf><<<nb, 256, 0, s>>>(C.rAtf.p);
+            FDS_CUDA_TRY(cudaGetLastError());
+            {
+                ProfScope ps("a3.merge_inverse", s);
+                ps.flops = fl_at;
+                FDS_TRY(dense_lu_solve(nb, C.rmax, C.rmax, rSf.p, spiv.p, d_sp.p, C.rAtf.p, s));
+            }
+            fds_count_launch(), k_cast<cplxf, cplx><<<1024, 256, 0, s>>>(C.Atf.p, C.At.p, nS);
+            FDS_CUDA_TRY(cudaGetLastError());
+        } else {
+            {
+                ProfScope ps("a3.merge_lu", s);
+                ps.flops = fl_lu;
+                FDS_TRY(dense_lu(nb, C.dmax, C.rLU.p, C.piv.p, C.d_offpiv.p, info.p, s));
+            }
+            fds_count_launch(), k_conj_transpose<cplx><<<nb, 256, 0, s>>>(C.rV.p, C.rW.p);
+            FDS_CUDA_TRY(cudaGetLastError());
+            {
+                ProfScope ps("a3.merge_w_solve", s);
+                ps.flops = fl_w;
+                FDS_TRY(dense_lu_solve(nb, C.dmax, C.rmax, C.rLU.p, C.piv.p, C.d_offpiv.p, C.rW.p, s));
+            }
+            // A_i^{-1} for the solve sweep (Sec. 7.3 step 3(b)), from the LU factors
+            // by a solve against the identity; the LU itself is not kept
+            FDS_TRY(C.Ainv.alloc(C.offA[nb]));
+            FDS_TRY(make_refs(C.rAinv, C.Ainv.p, C.offA, dv, dv, s));
+            fds_count_launch(), k_set_identity<cplx><<<nb, 256, 0, s>>>(C.rAinv.p);
+            FDS_CUDA_TRY(cudaGetLastError());
+            {
+                ProfScope ps("a3.merge_a_inverse", s);
+                ps.flops = fl_lu * 3.0;
+                FDS_TRY(dense_lu_solve(nb, C.dmax, C.dmax, C.rLU.p, C.piv.p, C.d_offpiv.p, C.rAinv.p, s));
+            }
+            {
+                ProfScope ps("a3.merge_s_gemm", s);
+                ps.flops = fl_s;
+                FDS_TRY(dense_gemm(nb, C.rmax, C.rmax, C.rV.p, 0, C.rW.p, 0, rS.p, mkc(1, 0), mkc(0, 0), s));
+            }
+            {
+                ProfScope ps("a3.merge_s_lu", s);
+                ps.flops = fl_slu;
+                FDS_TRY(dense_lu(nb, C.rmax, rS.p, spiv.p, d_sp.p, info2.p, s));
+            }
+            fds_count_launch(), k_set_identity<cplx><<<nb, 256, 0, s>>>(C.rAt.p);
+            FDS_CUDA_TRY(cudaGetLastError());
+            {
+                ProfScope ps("a3.merge_inverse", s);
+                ps.flops = fl_at;
+                FDS_TRY(dense_lu_solve(nb, C.rmax, C.rmax, rS.p, spiv.p, d_sp.p, C.rAt.p, s));
+            }
         }
         std::vector<int> hinfo, hinfo2;
         FDS_TRY(d2h(hinfo, info.p, nb, s));
@@ -951,7 +1058,8 @@ int fds_build_impl(fds_handle *h) {
         C.LU.release();
         C.rLU.release();
         C.piv.release();
-        h->factor_bytes += (int64_t)(C.Ainv.bytes() + C.V.bytes() + C.W.bytes() + C.At.bytes());
+        h->factor_bytes += (int64_t)(C.Ainv.bytes() + C.V.bytes() + C.W.bytes() + C.At.bytes() + C.Ainvf.bytes() +
+                                     C.Wf.bytes() + C.Atf.bytes() + C.Vf.bytes());
 
         // ---- parent level (eq. (A_rearrangement)): DOFs = children's skeletons
         Level &Pn = h->lv[l - 1];
@@ -1069,6 +1177,19 @@ int fds_build_impl(fds_handle *h) {
         FDS_TRY(T.d_doff.upload(T.doff, s));
     }
     if (h->opt.precision == FDS_MIXED) FDS_TRY(fds_mixed_prepare(h));
+    // the solve applies V through T (vapply.cu): the dense V_i are not kept
+    FDS_TRY(sync_check(s));
+    for (int l = L; l > h->l0; --l) {
+        Level &C = h->lv[l];
+        h->factor_bytes -= (int64_t)(C.V.bytes() + C.Vf.bytes());
+        h->factor_bytes += (int64_t)(C.T.bytes() + C.Tf.bytes() + C.Tp.bytes());
+        C.V.release();
+        C.rV.release();
+        C.Vf.release();
+        C.rVf.release();
+        C.Vp.release();
+        C.rVp.release();
+    }
     cudaEventRecord(e1, s);
     FDS_CUDA_TRY(cudaEventSynchronize(e1));
     float ms = 0;

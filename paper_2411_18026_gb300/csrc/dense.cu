@@ -9,15 +9,17 @@ namespace {
 
 constexpr int LU_THREADS = 256;
 
-__device__ __forceinline__ bool finite_c(cplx a) { return isfinite(a.x) && isfinite(a.y); }
+template <class C>
+__device__ __forceinline__ bool finite_c(C a) { return isfinite(a.x) && isfinite(a.y); }
 
 // Right-looking unblocked LU with partial pivoting (largest |a_ik|, ties to the
 // lowest row), one CTA per matrix, the matrix in global memory.
-__global__ void __launch_bounds__(LU_THREADS) k_lu(const MatRef *__restrict__ mats, int *__restrict__ piv,
+template <class C>
+__global__ void __launch_bounds__(LU_THREADS) k_lu(const MatRefT<C> *__restrict__ mats, int *__restrict__ piv,
                                                    const int64_t *__restrict__ poff, int *__restrict__ info) {
-    const MatRef M = mats[blockIdx.x];
+    const MatRefT<C> M = mats[blockIdx.x];
     const int n = M.rows, ld = M.ld;
-    cplx *A = M.p;
+    C *A = M.p;
     int *pv = piv + poff[blockIdx.x];
     __shared__ double s_val[LU_THREADS];
     __shared__ int s_idx[LU_THREADS];
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu(const MatRef *__restrict__ ma
             if (p >= n) p = k;
             s_piv = p;
             pv[k] = p;
-            cplx d = A[p + (long)k * ld];
+            const C d = A[p + (long)k * ld];
             if (!(s_val[0] > 0.0) || !finite_c(d)) {
                 if (!s_bad) s_bad = k + 1;
             }
@@ -61,14 +63,14 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu(const MatRef *__restrict__ ma
         const int p = s_piv;
         if (p != k) {
             for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                cplx t = A[k + (long)j * ld];
+                const C t = A[k + (long)j * ld];
                 A[k + (long)j * ld] = A[p + (long)j * ld];
                 A[p + (long)j * ld] = t;
             }
         }
         __syncthreads();
-        const cplx d = A[k + (long)k * ld];
-        const cplx dinv = (cabs2(d) > 0.0) ? cinv(d) : mkc(0.0, 0.0);
+        const C d = A[k + (long)k * ld];
+        const C dinv = (cabs2(d) > 0) ? cinv(d) : czero<C>();
         for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (long)k * ld] = cmul(A[i + (long)k * ld], dinv);
         __syncthreads();
         // trailing update A[k+1:, k+1:] -= l u^T
@@ -196,7 +198,15 @@ int dense_lu(int batch, int max_n, const MatRef *d_A, int *d_piv, const int64_t 
              cudaStream_t s) {
     if (batch <= 0) return FDS_OK;
     (void)max_n;
-    fds_count_launch(), k_lu<<<batch, LU_THREADS, 0, s>>>(d_A, d_piv, d_poff, d_info);
+    fds_count_launch(), k_lu<cplx><<<batch, LU_THREADS, 0, s>>>(d_A, d_piv, d_poff, d_info);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
+}
+int dense_lu(int batch, int max_n, const MatRefF *d_A, int *d_piv, const int64_t *d_poff, int *d_info,
+             cudaStream_t s) {
+    if (batch <= 0) return FDS_OK;
+    (void)max_n;
+    fds_count_launch(), k_lu<cplxf><<<batch, LU_THREADS, 0, s>>>(d_A, d_piv, d_poff, d_info);
     FDS_CUDA_TRY(cudaGetLastError());
     return FDS_OK;
 }

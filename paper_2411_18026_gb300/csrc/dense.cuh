@@ -14,6 +14,13 @@ struct MatRefT {
 };
 typedef MatRefT<cplx> MatRef;
 typedef MatRefT<cplxf> MatRefF;
+typedef MatRefT<float4> MatRefP;
+
+// Row maps of one batch entry of a mapped GEMM (device pointers, nullable).
+struct RowMaps {
+    const int *b;   // B row k is read from row b[k]
+    const int *c;   // C row i is written to row c[i]
+};
 
 // Launch helpers (device pointers to descriptor arrays; all enqueue on stream).
 // LU in place of square A[b] (rows == cols), pivots piv + poff[b], info[b].
@@ -38,10 +45,19 @@ int dense_gemm_ff(int batch, int max_m, int max_n, const MatRef *d_A, int opA, c
 // Same with operands already split into float pairs (float4 = re_hi, im_hi,
 // re_lo, im_lo per complex entry) and a float-pair result; C = op(A) B
 // (+ C when accumulate).
-typedef MatRefT<float4> MatRefP;
 int dense_gemm_ffp(int batch, int max_m, int max_n, const MatRefP *d_A, int opA, const MatRefP *d_B,
                    const MatRefP *d_C, int accumulate, cudaStream_t s);
-// complex64 versions (mixed-precision sweep)
+// C = op(A) B[bmap] (+ C when accumulate), rows of C written through cmap
+// (the interpolation matrices applied without their identity part).
+int dense_gemm_map(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, const MatRef *d_C,
+                   const RowMaps *d_maps, int accumulate, cudaStream_t s);
+int dense_gemm_map(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, const MatRefF *d_B,
+                   const MatRefF *d_C, const RowMaps *d_maps, int accumulate, cudaStream_t s);
+int dense_gemm_map(int batch, int max_m, int max_n, const MatRefP *d_A, int opA, const MatRefP *d_B,
+                   const MatRefP *d_C, const RowMaps *d_maps, int accumulate, cudaStream_t s);
+// complex64 versions (mixed-precision merge and sweep)
+int dense_lu(int batch, int max_n, const MatRefF *d_A, int *d_piv, const int64_t *d_poff, int *d_info,
+             cudaStream_t s);
 int dense_lu_solve(int batch, int max_rows, int max_cols, const MatRefF *d_LU, const int *d_piv,
                    const int64_t *d_poff, const MatRefF *d_B, cudaStream_t s);
 int dense_gemm(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, const MatRefF *d_B, int opB,

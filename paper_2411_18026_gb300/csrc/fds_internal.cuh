@@ -104,6 +104,17 @@ struct Level {
     int64_t D = 0, Rtot = 0;               // total DOFs / total skeleton DOFs of the level
     int dmax = 0, rmax = 0;
     double sum_d2 = 0, sum_rd = 0, sum_r2 = 0;   // algorithmic work sums for the sweep
+    bool c64 = false;            // FDS_MIXED: merged and swept in complex64
+    // --- interpolation blocks T^c (k_c x (n_c - k_c) per cell and component,
+    //     offsets toff[2b + c]) and the cell-local permuted DOF order vmap
+    //     (skeleton DOFs of each component first), for the structured V
+    DBuf<cplx> T;
+    DBuf<cplxf> Tf;
+    DBuf<float4> Tp;
+    DBuf<int64_t> d_toff;
+    DBuf<int> d_vmap, d_n1, d_n2;
+    int kmax = 0;                // largest k_c of the level
+    double sum_tm = 0;           // sum over cells and components of k_c (n_c - k_c)
     // --- mixed precision: complex64 copies of the sweep factors
     DBuf<cplxf> Ainvf, Wf, Atf, Vf;
     DBuf<MatRefF> rAinvf, rWf, rAtf, rVf;
@@ -163,6 +174,7 @@ struct fds_handle {
     std::vector<DBuf<float4>> wzp, wtp, wyp;
     DBuf<float4> wtopp, wytopp, wXp;
     DBuf<MatRefP> wrefsp;
+    DBuf<unsigned char> wvref;   // descriptors of the structured V applications
     DBuf<MatRef> wrefs;
     DBuf<MatRefF> wrefsf;
     DBuf<double> wnorm;
@@ -173,6 +185,7 @@ struct fds_handle {
     DBuf<float> d_mlp;
     int64_t id_sketched = 0, id_fallback = 0;
     std::vector<float> feat_rows, frac_rows;
+    bool fp64_reached = false; // build: a complex128 level has been merged (all above are too)
     int ir_iters = 0;          // refinement sweeps of the last mixed solve
     double ir_residual = 0;    // max_c ||f_c - A x_c|| / ||f_c|| after the last mixed solve
 };

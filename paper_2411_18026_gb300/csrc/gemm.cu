@@ -151,16 +151,20 @@ struct ArithFFP {
 };
 
 // TJ columns per thread (CTA tile 64 x 16 TJ)
+// Optional row maps (maps nullable, and each pointer nullable): B's row k is
+// read from row bmap[k], C's row i is written to row cmap[i].
 template <class Ar, int TJ>
 __global__ void __launch_bounds__(NT) k_gemm_rt(const MatRefT<typename Ar::G> *__restrict__ As, int opA,
                                                 const MatRefT<typename Ar::G> *__restrict__ Bs,
                                                 const MatRefT<typename Ar::G> *__restrict__ Cs,
                                                 typename Ar::G alpha, typename Ar::G beta, int use_beta,
-                                                int tiles_m) {
+                                                int tiles_m, const RowMaps *__restrict__ maps) {
     typedef typename Ar::G G;
     typedef typename Ar::SA SA;
     typedef typename Ar::SB SB;
     const MatRefT<G> A = As[blockIdx.y], B = Bs[blockIdx.y], Cm = Cs[blockIdx.y];
+    const int *bmap = maps ? maps[blockIdx.y].b : nullptr;
+    const int *cmap = maps ? maps[blockIdx.y].c : nullptr;
     const int M = Cm.rows, N = Cm.cols;
     const int K = (opA == 0) ? A.cols : A.rows;
     constexpr int BN = 16 * TJ;
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(NT) k_gemm_rt(const MatRefT<typename Ar::G> *_
         for (int q = 0; q < TJ; ++q) {
             const int k = t & 15, j = (t >> 4) + 16 * q;
             const int gk = k0 + k, gj = j0 + j;
-            sb[k][j] = (gk < K && gj < N) ? Ar::stage_b(B.p[gk + (int64_t)gj * B.ld]) : Ar::zb();
+            sb[k][j] = (gk < K && gj < N) ? Ar::stage_b(B.p[(bmap ? bmap[gk] : gk) + (int64_t)gj * B.ld]) : Ar::zb();
         }
         __syncthreads();
         const int kmax = min(BK, K - k0);
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(NT) k_gemm_rt(const MatRefT<typename Ar::G> *_
         for (int j = 0; j < TJ; ++j) {
             const int gi = i0 + tx + 16 * i, gj = j0 + ty + 16 * j;
             if (gi < M && gj < N) {
-                G *c = &Cm.p[gi + (int64_t)gj * Cm.ld];
+                G *c = &Cm.p[(cmap ? cmap[gi] : gi) + (int64_t)gj * Cm.ld];
                 *c = Ar::finish(acc[i][j], alpha, beta, use_beta ? c : nullptr);
             }
         }
@@ -229,14 +233,14 @@ __global__ void __launch_bounds__(NT) k_gemm_rt(const MatRefT<typename Ar::G> *_
 template <class Ar, int TJ>
 int launch(int batch, int max_m, int max_n, const MatRefT<typename Ar::G> *d_A, int opA,
            const MatRefT<typename Ar::G> *d_B, const MatRefT<typename Ar::G> *d_C, typename Ar::G alpha,
-           typename Ar::G beta, cudaStream_t s) {
+           typename Ar::G beta, cudaStream_t s, const RowMaps *maps = nullptr) {
     if (batch <= 0 || max_m <= 0 || max_n <= 0) return FDS_OK;
     if (opA != 0 && opA != 2) return FDS_ERR_ARG;
     constexpr int BN = 16 * TJ;
     const int tm = (max_m + BM - 1) / BM, tn = (max_n + BN - 1) / BN;
     const int use_beta = (beta.x != 0 || beta.y != 0) ? 1 : 0;
     dim3 grid(tm * tn, batch);
-    fds_count_launch(), k_gemm_rt<Ar, TJ><<<grid, NT, 0, s>>>(d_A, opA, d_B, d_C, alpha, beta, use_beta, tm);
+    fds_count_launch(), k_gemm_rt<Ar, TJ><<<grid, NT, 0, s>>>(d_A, opA, d_B, d_C, alpha, beta, use_beta, tm, maps);
     FDS_CUDA_TRY(cudaGetLastError());
     return FDS_OK;
 }
@@ -262,4 +266,20 @@ int dense_gemm_ffp(int batch, int max_m, int max_n, const MatRefT<float4> *d_A, 
                    const MatRefT<float4> *d_C, int accumulate, cudaStream_t s) {
     return launch<ArithFFP, 2>(batch, max_m, max_n, d_A, opA, d_B, d_C, make_float4(1.f, 0.f, 0.f, 0.f),
                                make_float4(accumulate ? 1.f : 0.f, 0.f, 0.f, 0.f), s);
+}
+
+int dense_gemm_map(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, const MatRef *d_C,
+                   const RowMaps *d_maps, int accumulate, cudaStream_t s) {
+    return launch<Arith128, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, mkc(1, 0), mkc(accumulate ? 1 : 0, 0), s,
+                               d_maps);
+}
+int dense_gemm_map(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, const MatRefF *d_B,
+                   const MatRefF *d_C, const RowMaps *d_maps, int accumulate, cudaStream_t s) {
+    return launch<Arith64, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, mkcf(1, 0), mkcf(accumulate ? 1 : 0, 0), s,
+                              d_maps);
+}
+int dense_gemm_map(int batch, int max_m, int max_n, const MatRefP *d_A, int opA, const MatRefP *d_B,
+                   const MatRefP *d_C, const RowMaps *d_maps, int accumulate, cudaStream_t s) {
+    return launch<ArithFFP, 2>(batch, max_m, max_n, d_A, opA, d_B, d_C, make_float4(1.f, 0.f, 0.f, 0.f),
+                               make_float4(accumulate ? 1.f : 0.f, 0.f, 0.f, 0.f), s, d_maps);
 }

@@ -24,6 +24,7 @@
 #include "fds_internal.cuh"
 #include "prof.cuh"
 #include "solve.cuh"
+#include "vapply.cuh"
 
 namespace {
 
@@ -158,6 +159,7 @@ struct Fw;
 template <>
 struct Fw<cplx> {
     static const MatRef *V(const Level &c) { return c.rV.p; }
+    static const cplx *Tm(const Level &c) { return c.T.p; }
     static const MatRef *D(const Level &c) { return c.rDfw.p; }
     static const MatRef *S(const Level &c) { return c.rSfw.p; }
     static const MatRef *top(const fds_handle *h) { return h->rtop_off.p; }
@@ -176,6 +178,7 @@ struct Fw<cplx> {
 template <>
 struct Fw<float4> {
     static const MatRefP *V(const Level &c) { return c.rVp.p; }
+    static const float4 *Tm(const Level &c) { return c.Tp.p; }
     static const MatRefP *D(const Level &c) { return c.rDp.p; }
     static const MatRefP *S(const Level &c) { return c.rSp.p; }
     static const MatRefP *top(const fds_handle *h) { return h->rtop_offp.p; }
@@ -236,16 +239,14 @@ int forward_apply(fds_handle *h, const T *X, T *Y, int nc, cudaStream_t s) {
         const int nb = C.nb;
         const int64_t ldr = std::max<int64_t>(C.Rtot, 1);
         T *xl = (l == L) ? (T *)X : wz[l].p;
-        fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, xl, C.d_doff.p, nc, C.D, rZ);
-        fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, wt[l].p, C.d_roff.p, nc, ldr, rT);
-        FDS_TRY(F::gemm(nb, C.rmax, nc, F::V(C), 0, rZ, rT, 0, s));
+        FDS_TRY(apply_V<T>(h, C, F::Tm(C), xl, C.D, wt[l].p, ldr, nc, s));
         T *par = (l - 1 > l0) ? wz[l - 1].p : F::xtop(h).p;
         const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
         fds_count_launch(), k_child_parent_t<T><<<nb, 256, 0, s>>>(nb, C.d_roff.p, C.d_k1.p, C.d_par_pos1.p,
                                                                    C.d_par_pos2.p, Pn.d_doff.p, wt[l].p, ldr, par,
                                                                    ldp, nc, 0);
         FDS_CUDA_TRY(cudaGetLastError());
-        fl += 8.0 * C.sum_rd * nc;
+        fl += 8.0 * C.sum_tm * nc;
     }
     // top: off-diagonal blocks between top cells, then the block diagonal
     {
@@ -278,14 +279,13 @@ int forward_apply(fds_handle *h, const T *X, T *Y, int nc, cudaStream_t s) {
         fds_count_launch(), k_child_parent_t<T><<<nb, 256, 0, s>>>(nb, C.d_roff.p, C.d_k1.p, C.d_par_pos1.p,
                                                                    C.d_par_pos2.p, Pn.d_doff.p, wt[l].p, ldr, ypar,
                                                                    ldp, nc, 1);
-        fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, wt[l].p, C.d_roff.p, nc, ldr, rT);
+        FDS_TRY(apply_VH<T>(h, C, F::Tm(C), wt[l].p, ldr, yl, C.D, nc, s));
         fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, yl, C.d_doff.p, nc, C.D, rY);
         fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, xl, C.d_doff.p, nc, C.D, rZ);
         FDS_CUDA_TRY(cudaGetLastError());
-        FDS_TRY(F::gemm(nb, C.dmax, nc, F::V(C), 2, rT, rY, 0, s));
         const MatRefT<T> *Bd = (l == L) ? F::D(C) : F::S(C);
         FDS_TRY(F::gemm(nb, C.dmax, nc, Bd, 0, rZ, rY, 1, s));
-        fl += 8.0 * (C.sum_rd + level_d2(C)) * nc;
+        fl += 8.0 * (C.sum_tm + level_d2(C)) * nc;
     }
     ps.flops = fl;
     return FDS_OK;
@@ -329,6 +329,12 @@ int fds_mixed_prepare(fds_handle *h) {
             dv[b] = C.n1[b] + C.n2[b];
             rv[b] = C.k1[b] + C.k2[b];
         }
+        FDS_TRY(convert(C.T, C.Tf, s));
+        if (C.Ainvf.p) {   // merged in complex64 by the build
+            bytes += (int64_t)(C.Ainvf.bytes() + C.Wf.bytes() + C.Atf.bytes() + C.Vf.bytes() + C.V.bytes() +
+                               C.Dfw.bytes() + C.Sfw.bytes());
+            continue;
+        }
         FDS_TRY(convert(C.Ainv, C.Ainvf, s));
         FDS_TRY(convert(C.W, C.Wf, s));
         FDS_TRY(convert(C.At, C.Atf, s));
@@ -351,7 +357,11 @@ int fds_mixed_prepare(fds_handle *h) {
                 dv[b] = C.n1[b] + C.n2[b];
                 rv[b] = l > l0 ? C.k1[b] + C.k2[b] : 0;
             }
-            if (l > l0) FDS_TRY(split_blocks(C.V, C.Vp, C.rVp, C.offV, rv, dv, s));
+            if (l > l0) {
+                FDS_TRY(C.Tp.alloc(C.T.n));
+                fds_count_launch(), k_split<<<1024, 256, 0, s>>>(C.T.p, C.Tp.p, (int64_t)C.T.n);
+                FDS_CUDA_TRY(cudaGetLastError());
+            }
             if (C.Dfw.p) FDS_TRY(split_blocks(C.Dfw, C.Dp, C.rDp, C.offA, dv, dv, s));
             if (C.Sfw.p) FDS_TRY(split_blocks(C.Sfw, C.Sp, C.rSp, C.offA, dv, dv, s));
         }
@@ -369,10 +379,6 @@ int fds_mixed_prepare(fds_handle *h) {
             C.rDfw.release();
             C.Sfw.release();
             C.rSfw.release();
-            if (l > ls) {
-                C.V.release();
-                C.rV.release();
-            }
         }
         h->Atop_off.release();
         h->rtop_off.release();

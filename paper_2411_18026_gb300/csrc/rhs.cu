@@ -6,6 +6,7 @@
 // the hat's support.
 #include "fds_internal.cuh"
 #include "kernel_eval.cuh"
+#include "prof.cuh"
 
 namespace {
 
@@ -23,13 +24,24 @@ __global__ void k_rhs(PhysDev P, const double *__restrict__ xy, int N, const int
     for (int a = 0; a < 2; ++a) {
         const int el = a == 0 ? (s == 0 ? N - 1 : s - 1) : s;
         const fdsk::Elem E = fdsk::load_elem(xy, N, el);
+        // phase k d.x at x = a + sig h t: theta_a + sig phi; exp(i sig phi) by
+        // its Taylor polynomial while |phi| < 0.05 (error < 3e-20), else sincos
+        double sa, ca;
+        sincos(k * (d0 * E.a.x + d1 * E.a.y), &sa, &ca);
+        const double phi = k * E.h * (d0 * E.t.x + d1 * E.t.y);
         for (int g = 0; g < 8; ++g) {
             const double sig = c_gauss.x[8][g];
             const double w = c_gauss.w[8][g] * E.h * (a == 0 ? sig : 1.0 - sig);
-            const double x0 = E.a.x + sig * E.h * E.t.x, x1 = E.a.y + sig * E.h * E.t.y;
-            double sp, cp;
-            sincos(k * (d0 * x0 + d1 * x1), &sp, &cp);
-            const cplx ph = mkc(cp, sp);
+            const double xg = sig * phi;
+            double sx, cx;
+            if (fabs(phi) < 0.05) {
+                const double x2 = xg * xg;
+                cx = 1.0 + x2 * (-1.0 / 2 + x2 * (1.0 / 24 + x2 * (-1.0 / 720 + x2 * (1.0 / 40320))));
+                sx = xg * (1.0 + x2 * (-1.0 / 6 + x2 * (1.0 / 120 + x2 * (-1.0 / 5040 + x2 * (1.0 / 362880)))));
+            } else {
+                sincos(xg, &sx, &cx);
+            }
+            const cplx ph = mkc(ca * cx - sa * sx, sa * cx + ca * sx);
             const double n0 = E.n.x, n1 = E.n.y;
             cplx u0, u1, t0, t1;
             if (kind == 0) {
@@ -61,6 +73,8 @@ int fds_rhs_impl(fds_handle *h, const int *d_kinds, const double *d_angles, int 
     if (nrhs <= 0) return FDS_OK;
     FDS_TRY(ensure_gauss_tables());
     const int64_t tot = (int64_t)h->N * nrhs;
+    ProfScope ps("a5.load_vectors", s);
+    ps.units = (double)tot;
     fds_count_launch(), k_rhs<<<ceil_div_u(tot, 256), 256, 0, s>>>(h->P, h->d_xy.p, h->N, d_kinds, d_angles, nrhs, d_f);
     FDS_CUDA_TRY(cudaGetLastError());
     return FDS_OK;

@@ -14,6 +14,7 @@
 #include "fds_internal.cuh"
 #include "prof.cuh"
 #include "solve.cuh"
+#include "vapply.cuh"
 
 namespace {
 
@@ -89,6 +90,7 @@ struct View<cplx> {
     static const MatRef *W(const Level &v) { return v.rW.p; }
     static const MatRef *At(const Level &v) { return v.rAt.p; }
     static const MatRef *V(const Level &v) { return v.rV.p; }
+    static const cplx *Tm(const Level &v) { return v.T.p; }
     static std::vector<DBuf<cplx>> &z(fds_handle *h) { return h->wz; }
     static std::vector<DBuf<cplx>> &f(fds_handle *h) { return h->wf; }
     static std::vector<DBuf<cplx>> &t(fds_handle *h) { return h->wt; }
@@ -104,6 +106,7 @@ struct View<cplxf> {
     static const MatRefF *W(const Level &v) { return v.rWf.p; }
     static const MatRefF *At(const Level &v) { return v.rAtf.p; }
     static const MatRefF *V(const Level &v) { return v.rVf.p; }
+    static const cplxf *Tm(const Level &v) { return v.Tf.p; }
     static std::vector<DBuf<cplxf>> &z(fds_handle *h) { return h->wzf; }
     static std::vector<DBuf<cplxf>> &f(fds_handle *h) { return h->wff; }
     static std::vector<DBuf<cplxf>> &t(fds_handle *h) { return h->wtf; }
@@ -125,11 +128,12 @@ int fds_max_cells(const fds_handle *h) {
 // precision of the mixed sweep (complex64); the top solve is FP64.
 int sweep_split(const fds_handle *h) {
     if (h->opt.precision != FDS_MIXED || h->L == h->l0) return h->L;
-    if (h->opt.sweep_fp64_levels >= 0) return std::min(h->L - 1, h->l0 + h->opt.sweep_fp64_levels);
-    // automatic: complex128 for the levels holding at most 1/8 of the leaf DOFs
+    // the build decided per level (Level::c64; complex128 levels form a prefix
+    // below the top): by sweep_fp64_levels, or automatically complex128 for
+    // the levels holding at most 1/8 of the leaf DOFs
     int ls = h->l0;
-    for (int l = h->l0 + 1; l < h->L; ++l)
-        if (8 * h->lv[l].D <= h->lv[h->L].D) ls = l;
+    for (int l = h->l0 + 1; l <= h->L; ++l)
+        if (!h->lv[l].c64) ls = l;
     return ls;
 }
 
@@ -206,10 +210,11 @@ int up_level(fds_handle *h, int l, int nc, cudaStream_t s) {
     fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, U, Cv.d_roff.p, nc, ldr, rT);
     fds_count_launch(), k_vec_refs<C><<<(nb + 127) / 128, 128, 0, s>>>(nb, F, Cv.d_roff.p, nc, ldr, rF);
     {
+        // U = V z through V = [I T] P^T, then f~ = A~ U
         ProfScope ps("a6.up_apply", s);
-        ps.flops = 8.0 * (Cv.sum_rd + Cv.sum_r2) * nc;
-        ps.bytes = esz * (Cv.sum_rd + Cv.sum_r2) + esz * (Cv.D + 2.0 * Cv.Rtot) * nc;
-        FDS_TRY(dense_gemm(nb, Cv.rmax, nc, Vw::V(Cv), 0, rZ, 0, rT, one, zero, s));
+        ps.flops = 8.0 * (Cv.sum_tm + Cv.sum_r2) * nc;
+        ps.bytes = esz * (Cv.sum_tm + Cv.sum_r2) + esz * (Cv.D + 2.0 * Cv.Rtot) * nc;
+        FDS_TRY(apply_V<C>(h, Cv, Vw::Tm(Cv), Z, Cv.D, U, ldr, nc, s));
         FDS_TRY(dense_gemm(nb, Cv.rmax, nc, Vw::At(Cv), 0, rT, 0, rF, one, zero, s));
     }
     C *par = (l - 1 > l0) ? wr[l - 1].p : Vw::wtop(h).p;

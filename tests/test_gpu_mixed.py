@@ -151,3 +151,22 @@ def test_mixed_sweep_with_fp64_upper_levels(levels):
     assert fds.fds_stats_get(hmx).ir_iters >= 1
     h64.close()
     hmx.close()
+
+
+@pytest.mark.parametrize("levels", [-1, 2])
+def test_mixed_with_complex64_merge(levels):
+    # the complex64 levels merged in complex64: still refined to the FP64
+    # operator's solution
+    torch_cuda()
+    fds = fdslib()
+    xy = workloads.star(2048, 0.2, 5, rot=0.2)
+    omega = workloads.omega_for_kTa(12.0)
+    h64 = fds.fds_build(xy, omega, 2.0, 1.0, 1e-9, leaf_size=32)
+    hmx = fds.fds_build(xy, omega, 2.0, 1.0, 1e-9, leaf_size=32, precision=fds.FDS_MIXED, merge_c64=True,
+                        sweep_fp64_levels=levels, ir_tol=1e-10)
+    F = fds.fds_rhs_plane_wave(h64, np.array([0, 1], np.int32), np.array([0.5, 2.0]))
+    assert _colmax(fds.fds_solve(hmx, F), fds.fds_solve(h64, F)) < 1e-8
+    st = fds.fds_stats_get(hmx)
+    assert st.ir_residual <= 1e-10
+    h64.close()
+    hmx.close()

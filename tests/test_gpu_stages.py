@@ -151,3 +151,18 @@ def test_rhs_matches_oracle():
         ref = bem.rhs(P, xy, int(kinds[j]), float(angles[j]))
         assert np.abs(got[:, j] - ref).max() <= 1e-13 * np.abs(ref).max()
     h.close()
+
+
+def test_rhs_coarse_elements_matches_oracle():
+    # k h ~ 1: the per-element phase steps take the sincos branch
+    fds = fdslib()
+    torch_cuda()
+    xy = workloads.circle(64)
+    h = fds.fds_build(xy, 10.0, 2.0, 1.0, 1e-6, leaf_size=16)
+    kinds, angles = np.array([0, 1], np.int32), np.array([0.3, 1.7])
+    got = fds.fds_rhs_plane_wave(h, kinds, angles)
+    P = bem.phys(2.0, 1.0, 1.0, 10.0)
+    for j in range(2):
+        ref = bem.rhs(P, xy, int(kinds[j]), float(angles[j]))
+        assert np.abs(got[:, j] - ref).max() <= 1e-13 * np.abs(ref).max()
+    h.close()
