@@ -32,9 +32,10 @@
  *
  * Quadrature definition (the same definition is restated independently on
  * the GPU):  element pairs are SELF, ADJACENT (shared vertex), NEAR
- * (midpoint distance < 2.5 max(h)), MID (< 6 max(h)), FAR (< 12 max(h)) or
- * FAR2.  FAR2: 4x4 Gauss; FAR: 6x6; MID: 8x8; NEAR: both elements halved, 8x8
- * on each of the 4 sub-pairs;
+ * (midpoint distance < 2.5 max(h)), MID (< 6 max(h)), FAR (< 12 max(h)),
+ * FAR2, or FAR3 (>= 24 max(h) on a fine mesh: k_T max(h) <= 0.02).  FAR3: 3x3
+ * Gauss; FAR2: 4x4; FAR: 6x6; MID: 8x8; NEAR: both elements halved, 8x8 on
+ * each of the 4 sub-pairs;
  * ADJACENT: Duffy split at the shared vertex, radial variable xi = w^4 with 16
  * Gauss points in w, 8 in the angular variable; SELF: (u = tau - sigma,
  * v) coordinates with u = w^5, 20 Gauss points in w and 4 in v, the two
@@ -333,6 +334,7 @@ static void pair_integral(const phys_t *P, const double *xy, int N, int ie, int 
     double mf[2] = { 0.5 * (f.a[0] + f.b[0]), 0.5 * (f.a[1] + f.b[1]) };
     double d = hypot(me[0] - mf[0], me[1] - mf[1]);
     double L = e.h > f.h ? e.h : f.h;
+    if (d >= 24.0 * L && P->kT * L <= 0.02) { pair_gauss(P, &e, &f, 0, 1, 0, 1, 3, out); return; }
     if (d >= 12.0 * L) { pair_gauss(P, &e, &f, 0, 1, 0, 1, 4, out); return; }
     if (d >= 6.0 * L) { pair_gauss(P, &e, &f, 0, 1, 0, 1, 6, out); return; }
     if (d >= 2.5 * L) { pair_gauss(P, &e, &f, 0, 1, 0, 1, 8, out); return; }

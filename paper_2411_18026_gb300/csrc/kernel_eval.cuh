@@ -20,7 +20,8 @@
 //             4 in v; both triangles (u and -u) at every node -> principal value
 //   adjacent  Duffy split at the shared vertex, xi = w^4, 16 x 8 nodes
 //   near      midpoint distance < 2.5 max(h): halve both elements, 8x8 per sub-pair
-//   mid       < 6 max(h): 8x8;   far: < 12 max(h): 6x6;   far2: 4x4
+//   mid       < 6 max(h): 8x8;   far: < 12 max(h): 6x6;   far2: 4x4;
+//   far3      >= 24 max(h) with k_T max(h) <= 0.02: 3x3
 //   cross     (proxy polygon vs boundary): fixed q x q (the build uses q = 2).
 //
 // Work is organised in tiles of at most TILE test hats x TILE trial hats:
@@ -56,13 +57,14 @@ constexpr int TILE_EL = 2 * TILE;      // worst case: no shared elements
 // Gauss–Legendre nodes/weights on [0,1] copied into shared memory at the
 // start of a kernel (divergent indices would serialise __constant__ reads).
 struct Rules {
-    double x4[4], w4[4], x6[6], w6[6], x8[8], w8[8], x16[16], w16[16], x20[20], w20[20];
+    double x3[3], w3[3], x4[4], w4[4], x6[6], w6[6], x8[8], w8[8], x16[16], w16[16], x20[20], w20[20];
     double xq[8], wq[8];
     int q;
 };
 
 __device__ __forceinline__ void load_rules(Rules &R, int qcross) {
     for (int i = threadIdx.x; i < 20; i += blockDim.x) {
+        if (i < 3) { R.x3[i] = c_gauss.x[3][i]; R.w3[i] = c_gauss.w[3][i]; }
         if (i < 4) { R.x4[i] = c_gauss.x[4][i]; R.w4[i] = c_gauss.w[4][i]; }
         if (i < 6) { R.x6[i] = c_gauss.x[6][i]; R.w6[i] = c_gauss.w[6][i]; }
         if (i < 8) { R.x8[i] = c_gauss.x[8][i]; R.w8[i] = c_gauss.w[8][i]; }
@@ -181,9 +183,12 @@ __device__ __forceinline__ Elem load_elem(const double *__restrict__ xy, int N, 
     return E;
 }
 
-enum PairKind { PK_SELF = 0, PK_ADJ_NEXT = 1, PK_ADJ_PREV = 2, PK_NEAR = 3, PK_MID = 4, PK_FAR = 5, PK_FAR2 = 6, PK_CROSS = 7 };
+enum PairKind {
+    PK_SELF = 0, PK_ADJ_NEXT = 1, PK_ADJ_PREV = 2, PK_NEAR = 3, PK_MID = 4, PK_FAR = 5, PK_FAR2 = 6, PK_CROSS = 7,
+    PK_FAR3 = 8
+};
 
-__device__ __forceinline__ int pair_kind(const Elem &E, const Elem &F, int ie, int jf, int N) {
+__device__ __forceinline__ int pair_kind(const Elem &E, const Elem &F, int ie, int jf, int N, double kT) {
     if (ie == jf) return PK_SELF;
     int in = (ie + 1 == N) ? 0 : ie + 1;
     int jn = (jf + 1 == N) ? 0 : jf + 1;
@@ -193,6 +198,7 @@ __device__ __forceinline__ int pair_kind(const Elem &E, const Elem &F, int ie, i
     double my = E.a.y + 0.5 * E.h * E.t.y - (F.a.y + 0.5 * F.h * F.t.y);
     double d = sqrt(mx * mx + my * my);
     double L = fmax(E.h, F.h);
+    if (d >= 24.0 * L && kT * L <= 0.02) return PK_FAR3;
     if (d >= 12.0 * L) return PK_FAR2;
     if (d >= 6.0 * L) return PK_FAR;
     if (d >= 2.5 * L) return PK_MID;
@@ -210,6 +216,7 @@ __device__ __forceinline__ int pair_points(int kind, int qcross) {
         case PK_MID: return 64;
         case PK_FAR: return 36;
         case PK_FAR2: return 16;
+        case PK_FAR3: return 9;
         default: return qcross * qcross;
     }
 }
@@ -284,6 +291,13 @@ __device__ __forceinline__ void pair_point(const Rules &G, int kind, int p, cons
             sig = G.x4[a];
             tau = G.x4[b];
             w = G.w4[a] * G.w4[b] * hh;
+            break;
+        }
+        case PK_FAR3: {
+            const int a = p / 3, b = p - 3 * (p / 3);
+            sig = G.x3[a];
+            tau = G.x3[b];
+            w = G.w3[a] * G.w3[b] * hh;
             break;
         }
         default: {
@@ -622,7 +636,7 @@ static __device__ void tile_eval(const PhysDev &P, TileSmem &S, const double *__
         if (diag && ie > jf) continue;
         const Elem E = load_elem(X, NX, ie);
         const Elem F = load_elem(same ? X : Y, same ? NX : NY, jf);
-        const int kind = same ? pair_kind(E, F, ie, jf, NX) : PK_CROSS;
+        const int kind = same ? pair_kind(E, F, ie, jf, NX, P.kT) : PK_CROSS;
         if (!cheap_kind(kind)) continue;
         const int mA = (S.R.pos[re][0] >= 0 ? 1 : 0) | (S.R.pos[re][1] >= 0 ? 2 : 0);
         const int mB = (S.C.pos[ce][0] >= 0 ? 1 : 0) | (S.C.pos[ce][1] >= 0 ? 2 : 0);
@@ -657,7 +671,7 @@ static __device__ void tile_eval(const PhysDev &P, TileSmem &S, const double *__
         if (diag && ie > jf) continue;
         const Elem E = load_elem(X, NX, ie);
         const Elem F = load_elem(same ? X : Y, same ? NX : NY, jf);
-        const int kind = same ? pair_kind(E, F, ie, jf, NX) : PK_CROSS;
+        const int kind = same ? pair_kind(E, F, ie, jf, NX, P.kT) : PK_CROSS;
         if (cheap_kind(kind)) continue;
         const int mA = (S.R.pos[re][0] >= 0 ? 1 : 0) | (S.R.pos[re][1] >= 0 ? 2 : 0);
         const int mB = (S.C.pos[ce][0] >= 0 ? 1 : 0) | (S.C.pos[ce][1] >= 0 ? 2 : 0);

@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 LAM, MU, RHO = 2.0, 1.0, 1.0
 
 
-@pytest.mark.parametrize("N,omega", [(200, 5.0), (64, 0.1), (4096, 20.0)])
+@pytest.mark.parametrize("N,omega", [(200, 5.0), (64, 0.1), (4096, 20.0), (8192, 5.0)])
 def test_eval_entries_matches_oracle(N, omega):
     torch = torch_cuda()
     fds = fdslib()

@@ -112,3 +112,13 @@ def test_near_mid_far_pairs(gap):
     got = bem.pair(P, xy, 20, 20 + gap)
     ref = _ref_regular(P, _elem(xy, 20), _elem(xy, 20 + gap))
     assert np.abs(got - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("gap", [24, 40])
+def test_far3_pairs_on_a_fine_mesh(gap):
+    # 3x3 rule at >= 24 max(h) when k_T max(h) <= 0.02 (here 0.012)
+    P = bem.phys(LAM, MU, RHO, 1.0)
+    xy = _poly(512)
+    got = bem.pair(P, xy, 20, 20 + gap)
+    ref = _ref_regular(P, _elem(xy, 20), _elem(xy, 20 + gap))
+    assert np.abs(got - ref).max() < 1e-11 * np.abs(ref).max()
