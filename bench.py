@@ -9,7 +9,8 @@ Default workload (the configuration the metric is quoted on): star cavity
 r(t) = 1 + 0.2 cos 5t with 2^19 nodes (2^20 complex unknowns), lambda = 2,
 mu = 1, rho = 1, k_T a = 20, leaf 64, l0 = 1, 1000 right-hand sides (plane P
 and SV waves at 500 angles), mixed precision (complex64 sweep of the lower
-tree levels refined against the FP64 compressed operator to
+tree levels, double-float sweep of the upper ones, refined against the FP64
+compressed operator to
 max_c ||f - A x|| / ||f|| <= 1e-8), adaptive ID (`--rank learned` selects
 the trained rank network, `python -m paper_2411_18026_gb300.learned`).  After the
 timed steps one plain-FP64 step runs on the same inputs: its build and solve
@@ -56,6 +57,8 @@ def parse():
     p.add_argument("--ir-tol", type=float, default=1e-8)
     p.add_argument("--sweep-fp64-levels", type=int, default=-1)
     p.add_argument("--merge-c64", action="store_true", help="merge the complex64 levels in complex64")
+    p.add_argument("--sweep-ff", type=int, default=1, choices=[0, 1, 2],
+                   help="mixed sweep: 1 double-float upper levels, 2 double-float everywhere")
     p.add_argument("--rank", default="adaptive", choices=["learned", "adaptive"],
                    help="learned: the trained rank network (falls back to adaptive if it has not been trained); "
                         "its skeletons differ from the plain solver's, so its error against the plain FP64 "
@@ -306,7 +309,8 @@ def main():
     def step(precision=prec, out=d_F, rec=info, params=mlp):
         h = fds.fds_build(xy, omega, 2.0, 1.0, args.eps, leaf_size=args.leaf, top_level=args.top, stream=stream,
                           precision=precision, ir_tol=args.ir_tol, sweep_fp64_levels=args.sweep_fp64_levels,
-                          mlp_params=params, merge_c64=args.merge_c64 and precision == fds.FDS_MIXED)
+                          mlp_params=params, merge_c64=args.merge_c64 and precision == fds.FDS_MIXED,
+                          sweep_ff=args.sweep_ff if precision == fds.FDS_MIXED else 0)
         fds.fds_rhs_plane_wave_device(h, d_kinds, d_angles, out, stream)
         rec["converged"] = True
         try:
@@ -394,6 +398,7 @@ def main():
         o.leaf_size, o.top_level = args.leaf, args.top
         o.precision, o.ir_tol, o.sweep_fp64_levels = prec, args.ir_tol, args.sweep_fp64_levels
         o.merge_c64 = 1 if args.merge_c64 else 0
+        o.sweep_ff = args.sweep_ff
         mlp32 = None
         if mlp is not None:
             mlp32 = np.ascontiguousarray(mlp, dtype=np.float32)
@@ -420,8 +425,8 @@ def main():
     # kernels, from ncu counters (dfma x 2 + dmul + dadd; dram read + write)
     # over all launches of one 2^14-node build of the same cavity
     # (profiles/k_tiles_fp64_ops_star_2p14.md)
-    A1_PER_POINT = {"a1.leaf_blocks": (564.0, 0.66), "a1.near_rows": (630.0, 1.05), "a1.proxy_rows": (630.0, 1.05),
-                    "a1.sibling_blocks": (617.0, 0.11), "a1.top_blocks": (617.0, 0.11)}
+    A1_PER_POINT = {"a1.leaf_blocks": (568.0, 0.72), "a1.near_rows": (687.0, 1.53), "a1.proxy_rows": (687.0, 1.53),
+                    "a1.sibling_blocks": (681.0, 0.19), "a1.top_blocks": (681.0, 0.19)}
     pk, src = peaks()
     sm_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     # FP64 peak of the GB300: 152 SMs x 2 FP64 FMA/clk (4 flops) x SM clock

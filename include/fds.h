@@ -103,6 +103,9 @@ typedef struct {
                               complex128 (the rest are complex64; the rounding error of the
                               complex64 sweep comes mostly from the upper levels); -1 (default):
                               the levels with at most 1/8 of the leaf level's DOFs */
+    int32_t sweep_ff;      /* FDS_MIXED: the levels above the complex64 ones sweep in 0 complex128,
+                              1 (default) double-float arithmetic on the FP32 pipe (float pairs,
+                              ~44 bits); 2: every level in double-float (no complex64 level) */
     int32_t merge_c64;     /* FDS_MIXED: 1 merges the complex64 levels in complex64 too (faster
                               build; their rounding then also enters the upper levels'
                               factors, so refinement may need more sweeps); default 0 */

@@ -24,6 +24,7 @@ extern "C" void fds_default_options(fds_options *o) {
     o->ir_max_iter = 10;
     o->ir_apply = FDS_APPLY_FF;
     o->sweep_fp64_levels = -1;
+    o->sweep_ff = 1;
     o->merge_c64 = 0;
     o->rank_mode = FDS_RANK_ADAPTIVE;
     o->mlp_params = nullptr;
@@ -67,7 +68,8 @@ int fds_build_owned(const fds_geometry *g, double omega, double lambda, double m
         (o.precision != FDS_FP64 && o.precision != FDS_MIXED) || !(o.ir_tol >= 0.0) || o.ir_max_iter < 0 ||
         o.ir_max_iter > 100 || (o.ir_apply != FDS_APPLY_FF && o.ir_apply != FDS_APPLY_FP64) ||
         (o.rank_mode != FDS_RANK_ADAPTIVE && o.rank_mode != FDS_RANK_LEARNED) ||
-        (o.rank_mode == FDS_RANK_LEARNED && !o.mlp_params) || o.sketch_extra < 1 || o.sketch_extra > 64 || o.sweep_fp64_levels < -1)
+        (o.rank_mode == FDS_RANK_LEARNED && !o.mlp_params) || o.sketch_extra < 1 || o.sketch_extra > 64 || o.sweep_fp64_levels < -1 || o.sweep_ff < 0 ||
+        o.sweep_ff > 2)
         return FDS_ERR_ARG;
     for (int i = 0; i < 2 * g->n_nodes; ++i)
         if (!std::isfinite(g->xy[i])) return FDS_ERR_ARG;

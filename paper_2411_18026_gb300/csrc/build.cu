@@ -881,7 +881,7 @@ int fds_build_impl(fds_handle *h) {
         // in complex64 too (decided from the top down so that the complex128
         // levels stay a prefix below the top)
         C.c64 = false;
-        if (h->opt.precision == FDS_MIXED && !h->fp64_reached) {
+        if (h->opt.precision == FDS_MIXED && h->opt.sweep_ff < 2 && !h->fp64_reached) {
             if (h->opt.sweep_fp64_levels >= 0) C.c64 = l > std::min(L - 1, h->l0 + h->opt.sweep_fp64_levels);
             else C.c64 = (l == L) || 8 * C.D > h->lv[L].D;
             if (!C.c64) h->fp64_reached = true;

@@ -69,6 +69,7 @@ __host__ __device__ __forceinline__ cplxf cinv(cplxf a) {
 template <class C> __host__ __device__ __forceinline__ C czero();
 template <> __host__ __device__ __forceinline__ cplx czero<cplx>() { return mkc(0.0, 0.0); }
 template <> __host__ __device__ __forceinline__ cplxf czero<cplxf>() { return mkcf(0.f, 0.f); }
+template <> __host__ __device__ __forceinline__ float4 czero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 __host__ __device__ __forceinline__ cplxf to_c64(cplx a) { return mkcf((float)a.x, (float)a.y); }
 __host__ __device__ __forceinline__ cplx to_c128(cplxf a) { return mkc((double)a.x, (double)a.y); }
 

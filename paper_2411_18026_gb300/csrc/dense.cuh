@@ -47,6 +47,9 @@ int dense_gemm_ff(int batch, int max_m, int max_n, const MatRef *d_A, int opA, c
 // (+ C when accumulate).
 int dense_gemm_ffp(int batch, int max_m, int max_n, const MatRefP *d_A, int opA, const MatRefP *d_B,
                    const MatRefP *d_C, int accumulate, cudaStream_t s);
+// float-pair GEMM with alpha = +-1 (sign of alpha.x), beta = 0 or 1 (beta.x), opB = 0
+int dense_gemm(int batch, int max_m, int max_n, const MatRefP *d_A, int opA, const MatRefP *d_B, int opB,
+               const MatRefP *d_C, float4 alpha, float4 beta, cudaStream_t s);
 // C = op(A) B[bmap] (+ C when accumulate), rows of C written through cmap
 // (the interpolation matrices applied without their identity part).
 int dense_gemm_map(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, const MatRef *d_C,

@@ -118,6 +118,9 @@ struct Level {
     // --- mixed precision: complex64 copies of the sweep factors
     DBuf<cplxf> Ainvf, Wf, Atf, Vf;
     DBuf<MatRefF> rAinvf, rWf, rAtf, rVf;
+    // --- mixed precision with double-float levels: float-pair copies
+    DBuf<float4> Ainvp, Wp, Atp;
+    DBuf<MatRefP> rAinvp, rWp, rAtp;
     // --- FP64 compressed forward operator: leaf diagonal blocks (leaf level)
     //     and sibling-coupling blocks S (levels that are parents), both d x d;
     //     as float pairs (float4 per entry) when the residual runs double-float
@@ -170,6 +173,9 @@ struct fds_handle {
     std::vector<DBuf<cplxf>> wzf, wff, wtf, wrf;
     DBuf<cplx> wtop, wytop, wX;
     DBuf<cplxf> wtopf;   // complex64 top vector (boundary of the mixed sweep)
+    std::vector<DBuf<float4>> wzq, wfq, wtq, wrq;   // float-pair sweep vectors
+    DBuf<float4> wtopq;
+    DBuf<MatRefP> wrefsq;
     // forward-apply vectors as float pairs
     std::vector<DBuf<float4>> wzp, wtp, wyp;
     DBuf<float4> wtopp, wytopp, wXp;

@@ -115,8 +115,8 @@ struct ArithFF {
 };
 
 // Operands already held as float pairs (float4 = re_hi, im_hi, re_lo, im_lo):
-// the constant forward operator is split once, the vectors stay split, so
-// no FP64 instruction is issued.  alpha = 1; beta = 0 or 1 (accumulate).
+// the constant operators are split once, the vectors stay split, so no FP64
+// instruction is issued.  alpha = 1 or -1 (sign of alpha.x); beta = 0 or 1.
 __device__ __forceinline__ ff ff_norm(ff a) {
     const float h = a.h + a.l;
     return ff{h, a.l - (h - a.h)};
@@ -140,8 +140,12 @@ struct ArithFFP {
     __device__ static SB zb() { return ArithFF::zb(); }
     __device__ static void zero(Acc &a) { ArithFF::zero(a); }
     __device__ static void mac(Acc &c, const SA &a, const SB &b) { ArithFF::mac(c, a, b); }
-    __device__ static G finish(const Acc &c, G, G, const G *old) {
+    __device__ static G finish(const Acc &c, G alpha, G, const G *old) {
         ff re = ff_norm(c.re), im = ff_norm(c.im);
+        if (alpha.x < 0.f) {   // alpha = -1
+            re = ff{-re.h, -re.l};
+            im = ff{-im.h, -im.l};
+        }
         if (old) {
             re = ff_add(re, ff{old->x, old->z});
             im = ff_add(im, ff{old->y, old->w});
@@ -282,4 +286,10 @@ int dense_gemm_map(int batch, int max_m, int max_n, const MatRefP *d_A, int opA,
                    const MatRefP *d_C, const RowMaps *d_maps, int accumulate, cudaStream_t s) {
     return launch<ArithFFP, 2>(batch, max_m, max_n, d_A, opA, d_B, d_C, make_float4(1.f, 0.f, 0.f, 0.f),
                                make_float4(accumulate ? 1.f : 0.f, 0.f, 0.f, 0.f), s, d_maps);
+}
+
+int dense_gemm(int batch, int max_m, int max_n, const MatRefP *d_A, int opA, const MatRefP *d_B, int opB,
+               const MatRefP *d_C, float4 alpha, float4 beta, cudaStream_t s) {
+    if (opB != 0) return FDS_ERR_ARG;
+    return launch<ArithFFP, 2>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
 }

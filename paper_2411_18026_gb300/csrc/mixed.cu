@@ -80,16 +80,22 @@ __device__ __forceinline__ cplx to_c128(const float4 &v) {
 
 // r = f - y in leaf order (y may be null: r = f), stored as complex64 for the
 // sweep; norms[2c] += |r|^2, norms[2c+1] += |f|^2 over column c.
-template <class T>
+__device__ __forceinline__ void put(const cplx &a, cplxf &b) { b = to_c64(a); }
+__device__ __forceinline__ void put(const cplx &a, float4 &b) {
+    const float rh = (float)a.x, ih = (float)a.y;
+    b = make_float4(rh, ih, (float)(a.x - (double)rh), (float)(a.y - (double)ih));
+}
+
+template <class T, class LT>
 __global__ void k_residual(const int *__restrict__ gidx, int64_t D, const cplx *__restrict__ F, int64_t ldf,
-                           const T *__restrict__ Y, cplxf *R, double *norms) {
+                           const T *__restrict__ Y, LT *R, double *norms) {
     const int c = blockIdx.y;
     double rr = 0.0, ff = 0.0;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < D; q += (int64_t)gridDim.x * blockDim.x) {
         const cplx f = F[gidx[q] + c * ldf];
         cplx r = f;
         if (Y) r = csub(f, to_c128(Y[q + c * D]));
-        R[q + c * D] = to_c64(r);
+        put(r, R[q + c * D]);
         rr += cabs2(r);
         ff += cabs2(f);
     }
@@ -110,7 +116,8 @@ __global__ void k_residual(const int *__restrict__ gidx, int64_t D, const cplx *
 }
 
 // X (+)= dX (complex64 correction), leaf order
-__global__ void k_update(cplx *X, const cplxf *__restrict__ dX, int64_t n, int set) {
+template <class LT>
+__global__ void k_update(cplx *X, const LT *__restrict__ dX, int64_t n, int set) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const cplx d = to_c128(dX[e]);
         X[e] = set ? d : cadd(X[e], d);
@@ -348,6 +355,26 @@ int fds_mixed_prepare(fds_handle *h) {
     }
     bytes += (int64_t)h->lv[l0].Sfw.bytes() + (int64_t)h->lv[l0].Dfw.bytes();
     bytes += (int64_t)(h->Atop.bytes() + h->ptop.bytes() + h->Atop_off.bytes());
+    for (int l = ls; l > l0; --l) {
+        Level &C = h->lv[l];
+        if (level_prec(h, l) != PREC_FF) continue;
+        std::vector<int> dv(C.nb), rv(C.nb);
+        for (int b = 0; b < C.nb; ++b) {
+            dv[b] = C.n1[b] + C.n2[b];
+            rv[b] = C.k1[b] + C.k2[b];
+        }
+        FDS_TRY(split_blocks(C.Ainv, C.Ainvp, C.rAinvp, C.offA, dv, dv, s));
+        FDS_TRY(split_blocks(C.W, C.Wp, C.rWp, C.offW, dv, rv, s));
+        FDS_TRY(split_blocks(C.At, C.Atp, C.rAtp, C.offAt, rv, rv, s));
+    }
+    if (h->opt.ir_apply == FDS_APPLY_FF || h->opt.sweep_ff) {
+        for (int l = L; l > l0; --l) {
+            Level &C = h->lv[l];
+            FDS_TRY(C.Tp.alloc(C.T.n));
+            fds_count_launch(), k_split<<<1024, 256, 0, s>>>(C.T.p, C.Tp.p, (int64_t)C.T.n);
+            FDS_CUDA_TRY(cudaGetLastError());
+        }
+    }
     if (h->opt.ir_apply == FDS_APPLY_FF) {
         // the forward operator as float pairs (same bytes as complex128)
         for (int l = L; l >= l0; --l) {
@@ -356,11 +383,6 @@ int fds_mixed_prepare(fds_handle *h) {
             for (int b = 0; b < C.nb; ++b) {
                 dv[b] = C.n1[b] + C.n2[b];
                 rv[b] = l > l0 ? C.k1[b] + C.k2[b] : 0;
-            }
-            if (l > l0) {
-                FDS_TRY(C.Tp.alloc(C.T.n));
-                fds_count_launch(), k_split<<<1024, 256, 0, s>>>(C.T.p, C.Tp.p, (int64_t)C.T.n);
-                FDS_CUDA_TRY(cudaGetLastError());
             }
             if (C.Dfw.p) FDS_TRY(split_blocks(C.Dfw, C.Dp, C.rDp, C.offA, dv, dv, s));
             if (C.Sfw.p) FDS_TRY(split_blocks(C.Sfw, C.Sp, C.rSp, C.offA, dv, dv, s));
@@ -383,8 +405,9 @@ int fds_mixed_prepare(fds_handle *h) {
         h->Atop_off.release();
         h->rtop_off.release();
     }
-    // the FP64 factors of the complex64 levels are not used by the mixed solve
-    for (int l = L; l > ls; --l) {
+    // the FP64 factors of the complex64 and double-float levels are not used by the mixed solve
+    for (int l = L; l > l0; --l) {
+        if (level_prec(h, l) == PREC_C128) continue;
         Level &C = h->lv[l];
         C.Ainv.release();
         C.rAinv.release();
@@ -397,7 +420,8 @@ int fds_mixed_prepare(fds_handle *h) {
     return FDS_OK;
 }
 
-int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
+template <class LT>
+int solve_mixed(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
     const int N = h->N, L = h->L;
     const int64_t ld_rhs = 2LL * N;
     const int ncmax = std::min(nrhs, SOLVE_CHUNK);
@@ -413,7 +437,7 @@ int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
     if (refine && ffp) FDS_TRY(grow(h->wXp, (size_t)D * ncmax));
     FDS_TRY(grow(h->wX, (size_t)D * ncmax));
     if (h->wnorm.n < (size_t)2 * ncmax) FDS_TRY(h->wnorm.alloc((size_t)2 * ncmax));
-    cplxf *leaf_in = sweep_leaf_in<cplxf>(h), *leaf = sweep_leaf_out<cplxf>(h);
+    LT *leaf_in = sweep_leaf_in<LT>(h), *leaf = sweep_leaf_out<LT>(h);
     cplx *Yleaf = (refine && !ffp) ? forward_out<cplx>(h) : nullptr;
     float4 *Ypleaf = (refine && ffp) ? forward_out<float4>(h) : nullptr;
     std::vector<double> nrm(2 * ncmax);
@@ -432,12 +456,12 @@ int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
         FDS_CUDA_TRY(cudaMemsetAsync(h->wnorm.p, 0, sizeof(double) * 2 * nc, s));
         {
             ProfScope ps("a7.residual", s);
-            fds_count_launch(), k_residual<cplx><<<dim3(gx, nc), 256, 0, s>>>(h->d_leaf_gidx.p, D, F, ld_rhs,
+            fds_count_launch(), k_residual<cplx, LT><<<dim3(gx, nc), 256, 0, s>>>(h->d_leaf_gidx.p, D, F, ld_rhs,
                                                                               nullptr, leaf_in, h->wnorm.p);
         }
         FDS_CUDA_TRY(cudaGetLastError());
         FDS_TRY(sweep_chunk(h, nc, s));
-        fds_count_launch(), k_update<<<1024, 256, 0, s>>>(h->wX.p, leaf, D * nc, 1);
+        fds_count_launch(), k_update<LT><<<1024, 256, 0, s>>>(h->wX.p, leaf, D * nc, 1);
         FDS_CUDA_TRY(cudaGetLastError());
         // refinement against the FP64 compressed operator
         double prev = INFINITY;
@@ -452,10 +476,10 @@ int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
             {
                 ProfScope ps("a7.residual", s);
                 if (ffp)
-                    fds_count_launch(), k_residual<float4><<<dim3(gx, nc), 256, 0, s>>>(
+                    fds_count_launch(), k_residual<float4, LT><<<dim3(gx, nc), 256, 0, s>>>(
                         h->d_leaf_gidx.p, D, F, ld_rhs, Ypleaf, leaf_in, h->wnorm.p);
                 else
-                    fds_count_launch(), k_residual<cplx><<<dim3(gx, nc), 256, 0, s>>>(
+                    fds_count_launch(), k_residual<cplx, LT><<<dim3(gx, nc), 256, 0, s>>>(
                         h->d_leaf_gidx.p, D, F, ld_rhs, Yleaf, leaf_in, h->wnorm.p);
             }
             FDS_CUDA_TRY(cudaGetLastError());
@@ -474,7 +498,7 @@ int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
             }
             prev = res;
             FDS_TRY(sweep_chunk(h, nc, s));
-            fds_count_launch(), k_update<<<1024, 256, 0, s>>>(h->wX.p, leaf, D * nc, 0);
+            fds_count_launch(), k_update<LT><<<1024, 256, 0, s>>>(h->wX.p, leaf, D * nc, 0);
             FDS_CUDA_TRY(cudaGetLastError());
         }
         fds_count_launch(), k_leaf_scatter<<<1024, 256, 0, s>>>(h->d_leaf_gidx.p, D, h->wX.p, F, ld_rhs, nc);
@@ -490,4 +514,10 @@ int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
     h->ir_iters = iters;
     h->ir_residual = worst;
     return converged ? FDS_OK : FDS_ERR_NOT_CONVERGED;
+}
+
+int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
+    // the refinement's sweep vectors are in the leaf level's precision
+    if (h->L > h->l0 && level_prec(h, h->L) == PREC_FF) return solve_mixed<float4>(h, d_rhs, nrhs, s);
+    return solve_mixed<cplxf>(h, d_rhs, nrhs, s);
 }

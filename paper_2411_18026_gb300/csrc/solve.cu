@@ -63,14 +63,24 @@ __global__ void k_child_parent(int nb, const int64_t *__restrict__ roff, const i
     }
 }
 
+// precision changes of vector entries: complex128, complex64, float pair
+__device__ __forceinline__ void cvt(const cplx &a, cplx &b) { b = a; }
+__device__ __forceinline__ void cvt(const cplx &a, cplxf &b) { b = to_c64(a); }
+__device__ __forceinline__ void cvt(const cplxf &a, cplx &b) { b = to_c128(a); }
+__device__ __forceinline__ void cvt(const cplx &a, float4 &b) {
+    const float rh = (float)a.x, ih = (float)a.y;
+    b = make_float4(rh, ih, (float)(a.x - (double)rh), (float)(a.y - (double)ih));
+}
+__device__ __forceinline__ void cvt(const float4 &a, cplx &b) { b = mkc((double)a.x + a.z, (double)a.y + a.w); }
+__device__ __forceinline__ void cvt(const cplxf &a, float4 &b) { b = make_float4(a.x, a.y, 0.f, 0.f); }
+__device__ __forceinline__ void cvt(const float4 &a, cplxf &b) { b = mkcf(a.x + a.z, a.y + a.w); }
+
 template <class A, class B>
 __global__ void k_convert(const A *__restrict__ src, B *dst, int64_t rows, int64_t lds, int64_t ldd, int cols) {
     const int64_t tot = rows * cols;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e % rows, c = e / rows;
-        const A v = src[i + c * lds];
-        dst[i + c * ldd].x = v.x;
-        dst[i + c * ldd].y = v.y;
+        cvt(src[i + c * lds], dst[i + c * ldd]);
     }
 }
 
@@ -89,7 +99,6 @@ struct View<cplx> {
     static const MatRef *Ainv(const Level &v) { return v.rAinv.p; }
     static const MatRef *W(const Level &v) { return v.rW.p; }
     static const MatRef *At(const Level &v) { return v.rAt.p; }
-    static const MatRef *V(const Level &v) { return v.rV.p; }
     static const cplx *Tm(const Level &v) { return v.T.p; }
     static std::vector<DBuf<cplx>> &z(fds_handle *h) { return h->wz; }
     static std::vector<DBuf<cplx>> &f(fds_handle *h) { return h->wf; }
@@ -105,7 +114,6 @@ struct View<cplxf> {
     static const MatRefF *Ainv(const Level &v) { return v.rAinvf.p; }
     static const MatRefF *W(const Level &v) { return v.rWf.p; }
     static const MatRefF *At(const Level &v) { return v.rAtf.p; }
-    static const MatRefF *V(const Level &v) { return v.rVf.p; }
     static const cplxf *Tm(const Level &v) { return v.Tf.p; }
     static std::vector<DBuf<cplxf>> &z(fds_handle *h) { return h->wzf; }
     static std::vector<DBuf<cplxf>> &f(fds_handle *h) { return h->wff; }
@@ -116,6 +124,21 @@ struct View<cplxf> {
     static cplxf one() { return mkcf(1, 0); }
 };
 
+template <>
+struct View<float4> {
+    static const MatRefP *Ainv(const Level &v) { return v.rAinvp.p; }
+    static const MatRefP *W(const Level &v) { return v.rWp.p; }
+    static const MatRefP *At(const Level &v) { return v.rAtp.p; }
+    static const float4 *Tm(const Level &v) { return v.Tp.p; }
+    static std::vector<DBuf<float4>> &z(fds_handle *h) { return h->wzq; }
+    static std::vector<DBuf<float4>> &f(fds_handle *h) { return h->wfq; }
+    static std::vector<DBuf<float4>> &t(fds_handle *h) { return h->wtq; }
+    static std::vector<DBuf<float4>> &r(fds_handle *h) { return h->wrq; }
+    static DBuf<float4> &wtop(fds_handle *h) { return h->wtopq; }
+    static DBuf<MatRefP> &refs(fds_handle *h) { return h->wrefsq; }
+    static float4 one() { return make_float4(1.f, 0.f, 0.f, 0.f); }
+};
+
 }  // namespace
 
 int fds_max_cells(const fds_handle *h) {
@@ -124,13 +147,17 @@ int fds_max_cells(const fds_handle *h) {
     return m;
 }
 
-// Levels l0 < l <= lsplit run in complex128, levels above lsplit in the
-// precision of the mixed sweep (complex64); the top solve is FP64.
+// Arithmetic of each level's sweep: FDS_FP64 complex128 throughout; FDS_MIXED
+// complex64 for the levels the build marked (Level::c64, a suffix ending at
+// the leaves) and, for the others, complex128 or (sweep_ff) float pairs.
+int level_prec(const fds_handle *h, int l) {
+    if (h->opt.precision != FDS_MIXED) return PREC_C128;
+    if (h->lv[l].c64) return PREC_C64;
+    return h->opt.sweep_ff ? PREC_FF : PREC_C128;
+}
+
 int sweep_split(const fds_handle *h) {
     if (h->opt.precision != FDS_MIXED || h->L == h->l0) return h->L;
-    // the build decided per level (Level::c64; complex128 levels form a prefix
-    // below the top): by sweep_fp64_levels, or automatically complex128 for
-    // the levels holding at most 1/8 of the leaf DOFs
     int ls = h->l0;
     for (int l = h->l0 + 1; l <= h->L; ++l)
         if (!h->lv[l].c64) ls = l;
@@ -161,12 +188,25 @@ int workspace_levels(fds_handle *h, int ncmax, int lo, int hi, bool top) {
     return FDS_OK;
 }
 
+template <class C>
+int workspace_prec(fds_handle *h, int ncmax, int prec) {
+    // the levels of this precision, the level (or top) above each of them and
+    // the top vector, which may carry a converted copy at a precision change
+    const int L = h->L, l0 = h->l0;
+    FDS_TRY(workspace_levels<C>(h, ncmax, L + 1, L, true));    // top vector and descriptors
+    for (int l = L; l > l0; --l) {
+        const bool mine = level_prec(h, l) == prec;
+        const bool above = l < L && level_prec(h, l + 1) == prec;   // parent of a level of this precision
+        if (mine || above) FDS_TRY(workspace_levels<C>(h, ncmax, l, l, false));
+    }
+    return FDS_OK;
+}
+
 int sweep_workspace(fds_handle *h, int ncmax) {
-    const int ls = sweep_split(h);
-    FDS_TRY(workspace_levels<cplx>(h, ncmax, h->l0 + 1, ls, true));
-    if (ls < h->L || (h->opt.precision == FDS_MIXED)) {
-        // complex64 levels, the boundary level's vectors and the top in complex64
-        FDS_TRY(workspace_levels<cplxf>(h, ncmax, ls, h->L, true));
+    FDS_TRY(workspace_prec<cplx>(h, ncmax, PREC_C128));
+    if (h->opt.precision == FDS_MIXED) {
+        FDS_TRY(workspace_prec<cplxf>(h, ncmax, PREC_C64));
+        if (h->opt.sweep_ff) FDS_TRY(workspace_prec<float4>(h, ncmax, PREC_FF));
     }
     return FDS_OK;
 }
@@ -180,6 +220,40 @@ template <class C>
 C *sweep_leaf_out(fds_handle *h) {
     return (h->L > h->l0) ? View<C>::z(h)[h->L].p : View<C>::wtop(h).p;
 }
+
+namespace {
+
+// vector of level l (l > l0) or of the top (l = l0) in precision C:
+// which 0 = right-hand side, 1 = solution
+template <class C>
+C *level_vec(fds_handle *h, int l, int which) {
+    if (l == h->l0) return View<C>::wtop(h).p;
+    return which ? View<C>::z(h)[l].p : View<C>::r(h)[l].p;
+}
+
+template <class A, class B>
+int convert_level(fds_handle *h, int l, int which, int nc, cudaStream_t s) {
+    const int64_t rows = l == h->l0 ? h->Dtop : h->lv[l].D;
+    const int64_t ld = std::max<int64_t>(rows, 1);
+    fds_count_launch(), k_convert<A, B><<<256, 256, 0, s>>>(level_vec<A>(h, l, which), level_vec<B>(h, l, which),
+                                                           rows, ld, ld, nc);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
+}
+
+// vector of level l (or the top) from precision pa to pb
+int convert_prec(fds_handle *h, int l, int which, int pa, int pb, int nc, cudaStream_t s) {
+    if (pa == pb) return FDS_OK;
+    if (pa == PREC_C64 && pb == PREC_C128) return convert_level<cplxf, cplx>(h, l, which, nc, s);
+    if (pa == PREC_C128 && pb == PREC_C64) return convert_level<cplx, cplxf>(h, l, which, nc, s);
+    if (pa == PREC_C64 && pb == PREC_FF) return convert_level<cplxf, float4>(h, l, which, nc, s);
+    if (pa == PREC_FF && pb == PREC_C64) return convert_level<float4, cplxf>(h, l, which, nc, s);
+    if (pa == PREC_FF && pb == PREC_C128) return convert_level<float4, cplx>(h, l, which, nc, s);
+    if (pa == PREC_C128 && pb == PREC_FF) return convert_level<cplx, float4>(h, l, which, nc, s);
+    return FDS_ERR_ARG;
+}
+
+}  // namespace
 
 namespace {
 
@@ -259,13 +333,6 @@ int down_level(fds_handle *h, int l, int nc, cudaStream_t s) {
     return FDS_OK;
 }
 
-template <class A, class B>
-int convert_vec(const A *src, B *dst, int64_t rows, int nc, cudaStream_t s) {
-    const int64_t ld = std::max<int64_t>(rows, 1);
-    fds_count_launch(), k_convert<A, B><<<256, 256, 0, s>>>(src, dst, rows, ld, ld, nc);
-    FDS_CUDA_TRY(cudaGetLastError());
-    return FDS_OK;
-}
 
 int top_solve(fds_handle *h, int nc, cudaStream_t s) {
     const int64_t ldt = std::max<int64_t>(h->Dtop, 1);
@@ -288,36 +355,47 @@ int top_solve(fds_handle *h, int nc, cudaStream_t s) {
 // leaf level's precision, the solution is left in sweep_leaf_out.
 int sweep_chunk(fds_handle *h, int nc, cudaStream_t s) {
     const int L = h->L, l0 = h->l0;
-    const int ls = sweep_split(h);
-    const bool mixed = h->opt.precision == FDS_MIXED;
-    for (int l = L; l > l0; --l) {
-        if (l > ls) FDS_TRY(up_level<cplxf>(h, l, nc, s));
-        else FDS_TRY(up_level<cplx>(h, l, nc, s));
-        if (l == ls + 1) {
-            // complex64 right-hand side of level ls (or the top) -> complex128
-            if (ls > l0) FDS_TRY(convert_vec(h->wrf[ls].p, h->wr[ls].p, h->lv[ls].D, nc, s));
-            else FDS_TRY(convert_vec(h->wtopf.p, h->wtop.p, h->Dtop, nc, s));
+    auto prec = [&](int l) { return l == l0 ? PREC_C128 : level_prec(h, l); };
+    auto up = [&](int l) -> int {
+        switch (prec(l)) {
+            case PREC_C64: return up_level<cplxf>(h, l, nc, s);
+            case PREC_FF: return up_level<float4>(h, l, nc, s);
+            default: return up_level<cplx>(h, l, nc, s);
         }
+    };
+    auto down = [&](int l) -> int {
+        switch (prec(l)) {
+            case PREC_C64: return down_level<cplxf>(h, l, nc, s);
+            case PREC_FF: return down_level<float4>(h, l, nc, s);
+            default: return down_level<cplx>(h, l, nc, s);
+        }
+    };
+    if (L == l0) {
+        // one cell: the leaf vector is the top vector, held in the leaf precision
+        const int pl = h->opt.precision == FDS_MIXED ? PREC_C64 : PREC_C128;
+        FDS_TRY(convert_prec(h, l0, 0, pl, PREC_C128, nc, s));
+        FDS_TRY(top_solve(h, nc, s));
+        return convert_prec(h, l0, 0, PREC_C128, pl, nc, s);
     }
-    if (mixed && L == l0) FDS_TRY(convert_vec(h->wtopf.p, h->wtop.p, h->Dtop, nc, s));
+    for (int l = L; l > l0; --l) {
+        FDS_TRY(up(l));
+        // the parent's right-hand side arrives in this level's precision
+        FDS_TRY(convert_prec(h, l - 1, 0, prec(l), prec(l - 1), nc, s));
+    }
     FDS_TRY(top_solve(h, nc, s));
-    if (mixed && L == l0) FDS_TRY(convert_vec(h->wtop.p, h->wtopf.p, h->Dtop, nc, s));
     for (int l = l0 + 1; l <= L; ++l) {
-        if (l == ls + 1) {
-            // complex128 solution of level ls (or the top) -> complex64
-            if (ls > l0) FDS_TRY(convert_vec(h->wz[ls].p, h->wzf[ls].p, h->lv[ls].D, nc, s));
-            else FDS_TRY(convert_vec(h->wtop.p, h->wtopf.p, h->Dtop, nc, s));
-        }
-        if (l > ls) FDS_TRY(down_level<cplxf>(h, l, nc, s));
-        else FDS_TRY(down_level<cplx>(h, l, nc, s));
+        FDS_TRY(convert_prec(h, l - 1, 1, prec(l - 1), prec(l), nc, s));
+        FDS_TRY(down(l));
     }
     return FDS_OK;
 }
 
 template cplx *sweep_leaf_in<cplx>(fds_handle *);
 template cplxf *sweep_leaf_in<cplxf>(fds_handle *);
+template float4 *sweep_leaf_in<float4>(fds_handle *);
 template cplx *sweep_leaf_out<cplx>(fds_handle *);
 template cplxf *sweep_leaf_out<cplxf>(fds_handle *);
+template float4 *sweep_leaf_out<float4>(fds_handle *);
 
 int fds_solve_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
     if (nrhs <= 0) return FDS_OK;

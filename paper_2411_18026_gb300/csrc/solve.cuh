@@ -5,6 +5,10 @@
 
 constexpr int SOLVE_CHUNK = 256;   // right-hand sides per sweep
 
+// arithmetic of a level's sweep
+enum { PREC_C128 = 0, PREC_C64 = 1, PREC_FF = 2 };
+int level_prec(const fds_handle *h, int l);
+
 int fds_max_cells(const fds_handle *h);
 // Last level (from the top) of the sweep that runs in complex128: L for
 // FDS_FP64; for FDS_MIXED min(L - 1, l0 + sweep_fp64_levels) (L when L = l0).

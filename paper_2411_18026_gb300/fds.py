@@ -61,7 +61,7 @@ class fds_options(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("alpha_re", ctypes.c_double), ("alpha_im", ctypes.c_double),
                 ("alpha_set", ctypes.c_int32), ("cuda_stream", ctypes.c_uint64), ("ir_tol", ctypes.c_double),
                 ("ir_max_iter", ctypes.c_int32), ("ir_apply", ctypes.c_int32), ("sweep_fp64_levels", ctypes.c_int32),
-                ("merge_c64", ctypes.c_int32), ("rank_mode", ctypes.c_int32),
+                ("sweep_ff", ctypes.c_int32), ("merge_c64", ctypes.c_int32), ("rank_mode", ctypes.c_int32),
                 ("mlp_params", ctypes.POINTER(ctypes.c_float)), ("sketch_extra", ctypes.c_int32),
                 ("record_features", ctypes.c_int32)]
 
@@ -197,7 +197,8 @@ class Handle:
 
 def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy_ratio=1.5, proxy_points=64,
               alpha=None, stream=0, precision=FDS_FP64, ir_tol=None, ir_max_iter=None, ir_apply=None,
-              mlp_params=None, sketch_extra=None, record_features=False, sweep_fp64_levels=None, merge_c64=False):
+              mlp_params=None, sketch_extra=None, record_features=False, sweep_fp64_levels=None, merge_c64=False,
+              sweep_ff=1):
     """Factorise; mlp_params (FDS_MLP_NPARAM floats) selects the learned-rank ID."""
     xy = np.ascontiguousarray(xy, dtype=np.float64)
     g = fds_geometry(len(xy), xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(rho))
@@ -225,6 +226,7 @@ def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy
     if sweep_fp64_levels is not None:
         o.sweep_fp64_levels = sweep_fp64_levels
     o.merge_c64 = 1 if merge_c64 else 0
+    o.sweep_ff = int(sweep_ff)
     o.record_features = 1 if record_features else 0
     out = ctypes.c_void_p()
     _check(lib().fds_build_ex(ctypes.byref(g), float(omega), float(lam), float(mu), float(tol), ctypes.byref(o),

@@ -136,6 +136,7 @@ def test_mixed_not_converged_is_reported():
 
 @pytest.mark.parametrize("levels", [1, 3, 20])
 def test_mixed_sweep_with_fp64_upper_levels(levels):
+    # (complex128 upper levels: sweep_ff = 0)
     # the upper tree levels keep complex128 factors; 20 exceeds the depth
     # (clamped to all but the leaf level)
     torch_cuda()
@@ -145,7 +146,7 @@ def test_mixed_sweep_with_fp64_upper_levels(levels):
     h64, hmx = _pair(fds, xy, omega, 1e-9, leaf_size=32, top_level=1)
     hmx.close()
     hmx = fds.fds_build(xy, omega, 2.0, 1.0, 1e-9, leaf_size=32, top_level=1, precision=fds.FDS_MIXED,
-                        sweep_fp64_levels=levels)
+                        sweep_fp64_levels=levels, sweep_ff=0)
     F = fds.fds_rhs_plane_wave(h64, np.array([0, 1, 1], np.int32), np.array([0.1, 1.1, 4.0]))
     assert _colmax(fds.fds_solve(hmx, F), fds.fds_solve(h64, F)) < 1e-7
     assert fds.fds_stats_get(hmx).ir_iters >= 1
@@ -168,5 +169,30 @@ def test_mixed_with_complex64_merge(levels):
     assert _colmax(fds.fds_solve(hmx, F), fds.fds_solve(h64, F)) < 1e-8
     st = fds.fds_stats_get(hmx)
     assert st.ir_residual <= 1e-10
+    h64.close()
+    hmx.close()
+
+
+@pytest.mark.parametrize("ff", [1, 2])
+def test_mixed_double_float_sweep_levels(ff):
+    # ff = 1: the levels above the complex64 ones in double-float; ff = 2: all
+    torch_cuda()
+    fds = fdslib()
+    xy = workloads.star(2048, 0.2, 5, rot=0.4)
+    omega = workloads.omega_for_kTa(12.0)
+    h64 = fds.fds_build(xy, omega, 2.0, 1.0, 1e-9, leaf_size=32)
+    hmx = fds.fds_build(xy, omega, 2.0, 1.0, 1e-9, leaf_size=32, precision=fds.FDS_MIXED, sweep_ff=ff,
+                        sweep_fp64_levels=2, ir_tol=1e-11)
+    kinds, ang = workloads.plane_wave_set(2)
+    F = fds.fds_rhs_plane_wave(h64, kinds, ang)
+    assert _colmax(fds.fds_solve(hmx, F), fds.fds_solve(h64, F)) < 1e-9
+    st = fds.fds_stats_get(hmx)
+    assert st.ir_residual <= 1e-11
+    # the all-double-float sweep alone is accurate to ~1e-10: no complex64 rounding
+    if ff == 2:
+        h0 = fds.fds_build(xy, omega, 2.0, 1.0, 1e-9, leaf_size=32, precision=fds.FDS_MIXED, sweep_ff=2,
+                           ir_max_iter=0)
+        assert _colmax(fds.fds_solve(h0, F), fds.fds_solve(h64, F)) < 1e-8
+        h0.close()
     h64.close()
     hmx.close()
