@@ -72,6 +72,17 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(value, device):
+    """The largest of the ranks' values (the job's time is its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -249,10 +260,7 @@ def run_batch(args, fds, torch, world, rank, local):
     ms = (time.perf_counter() - t0) * 1e3 / args.steps
     launches = (fds.fds_launch_count() - launches0) // args.steps
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, "cuda")
     t1 = time.perf_counter()
     step(1)
     torch.cuda.synchronize()
@@ -356,10 +364,7 @@ def main():
     clk = clocks.stop()
     fds.fds_timing_enable(False)
     phases = fds.fds_timing_report()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, "cuda")
 
     # plain-FP64 comparison on the same inputs (outside the timed region)
     compare = None
