@@ -128,6 +128,15 @@ struct Level {
     DBuf<MatRef> rDfw, rSfw;
     DBuf<float4> Dp, Sp, Vp;
     DBuf<MatRefP> rDp, rSp, rVp;
+    // --- the sibling coupling as its two nonzero blocks per parent cell:
+    //     entry 2p = rows of child a x columns of child b, 2p + 1 the other;
+    //     sperm: the parent's DOFs grouped by child (a's first)
+    DBuf<cplx> Sc;
+    DBuf<float4> Scp;
+    DBuf<int64_t> d_scoff;
+    DBuf<int> d_sperm, d_ra, d_rb;
+    int srmax = 0;
+    double sum_s2 = 0;            // sum over cells of 2 r_a r_b
 };
 
 // A stream created for (and destroyed after) one handle.

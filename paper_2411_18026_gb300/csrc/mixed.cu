@@ -149,6 +149,52 @@ int convert(const DBuf<cplx> &src, DBuf<cplxf> &dst, cudaStream_t s) {
     return FDS_OK;
 }
 
+// compact sibling blocks from the parent's d x d coupling block
+__global__ void k_extract_s(const MatRef *__restrict__ S, const int *__restrict__ sperm,
+                            const int64_t *__restrict__ doff, const int *__restrict__ ra,
+                            const int *__restrict__ rb, const int64_t *__restrict__ scoff, cplx *out) {
+    const int p = blockIdx.x;
+    const MatRef M = S[p];
+    const int a = ra[p], b = rb[p];
+    const int *pm = sperm + doff[p];
+    cplx *o0 = out + scoff[2 * p], *o1 = out + scoff[2 * p + 1];
+    for (int64_t e = threadIdx.x; e < (int64_t)a * b; e += blockDim.x) {
+        const int i = (int)(e % a), j = (int)(e / a);
+        o0[i + (int64_t)j * a] = M.p[pm[i] + (int64_t)pm[a + j] * M.ld];
+    }
+    for (int64_t e = threadIdx.x; e < (int64_t)a * b; e += blockDim.x) {
+        const int i = (int)(e % b), j = (int)(e / b);
+        o1[i + (int64_t)j * b] = M.p[pm[a + i] + (int64_t)pm[j] * M.ld];
+    }
+}
+
+template <class T>
+__global__ void k_srefs(int nb, const T *Sc, const int64_t *__restrict__ scoff, const int *__restrict__ ra,
+                        const int *__restrict__ rb, const int64_t *__restrict__ doff, const int *sperm, const T *x,
+                        int64_t ldx, T *y, int64_t ldy, int nc, MatRefT<T> *A, MatRefT<T> *B, MatRefT<T> *Cm,
+                        RowMaps *M) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 2 * nb) return;
+    const int p = e >> 1, side = e & 1;
+    const int a = ra[p], b = rb[p];
+    const int rows = side ? b : a, cols = side ? a : b;
+    const int *pm = sperm + doff[p];
+    A[e].p = (T *)Sc + scoff[e];
+    A[e].rows = rows;
+    A[e].cols = cols;
+    A[e].ld = rows > 1 ? rows : 1;
+    B[e].p = (T *)x + doff[p];
+    B[e].rows = (int)(doff[p + 1] - doff[p]);
+    B[e].cols = nc;
+    B[e].ld = (int)ldx;
+    Cm[e].p = y + doff[p];
+    Cm[e].rows = rows;
+    Cm[e].cols = nc;
+    Cm[e].ld = (int)ldy;
+    M[e].b = side ? pm : pm + a;
+    M[e].c = side ? pm + a : pm;
+}
+
 double level_d2(const Level &C) {
     double s = 0;
     for (int b = 0; b < C.nb; ++b) {
@@ -169,6 +215,7 @@ struct Fw<cplx> {
     static const cplx *Tm(const Level &c) { return c.T.p; }
     static const MatRef *D(const Level &c) { return c.rDfw.p; }
     static const MatRef *S(const Level &c) { return c.rSfw.p; }
+    static const cplx *Sc(const Level &c) { return c.Sc.p; }
     static const MatRef *top(const fds_handle *h) { return h->rtop_off.p; }
     static std::vector<DBuf<cplx>> &z(fds_handle *h) { return h->wz; }
     static std::vector<DBuf<cplx>> &t(fds_handle *h) { return h->wt; }
@@ -188,6 +235,7 @@ struct Fw<float4> {
     static const float4 *Tm(const Level &c) { return c.Tp.p; }
     static const MatRefP *D(const Level &c) { return c.rDp.p; }
     static const MatRefP *S(const Level &c) { return c.rSp.p; }
+    static const float4 *Sc(const Level &c) { return c.Scp.p; }
     static const MatRefP *top(const fds_handle *h) { return h->rtop_offp.p; }
     static std::vector<DBuf<float4>> &z(fds_handle *h) { return h->wzp; }
     static std::vector<DBuf<float4>> &t(fds_handle *h) { return h->wtp; }
@@ -229,6 +277,24 @@ T *forward_out(fds_handle *h) {
     return (h->L > h->l0) ? Fw<T>::y(h)[h->L].p : Fw<T>::ytop(h).p;
 }
 
+// y_l += S_l x_l through the compact sibling blocks of level l (a parent level)
+template <class T>
+int apply_S(fds_handle *h, const Level &C, const T *x, int64_t ldx, T *y, int64_t ldy, int nc, cudaStream_t s) {
+    const int nb = C.nb;
+    if (nb == 0) return FDS_OK;
+    const int maxnb = fds_max_cells(h);
+    const size_t need = (size_t)2 * maxnb * (3 * sizeof(MatRefT<T>) + sizeof(RowMaps)) + 64;
+    if (h->wvref.n < need) FDS_TRY(h->wvref.alloc(need));
+    MatRefT<T> *A = reinterpret_cast<MatRefT<T> *>(h->wvref.p);
+    MatRefT<T> *B = A + 2 * maxnb, *Cr = B + 2 * maxnb;
+    RowMaps *M = reinterpret_cast<RowMaps *>(Cr + 2 * maxnb);
+    fds_count_launch(), k_srefs<T><<<(2 * nb + 127) / 128, 128, 0, s>>>(
+        nb, Fw<T>::Sc(C), C.d_scoff.p, C.d_ra.p, C.d_rb.p, C.d_doff.p, C.d_sperm.p, x, ldx, y, ldy, nc, A, B, Cr,
+        M);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return dense_gemm_map(2 * nb, std::max(C.srmax, 1), nc, A, 0, B, Cr, M, 1, s);
+}
+
 // Y = A X for nc leaf-order columns (both D_L x nc, column-major).
 template <class T>
 int forward_apply(fds_handle *h, const T *X, T *Y, int nc, cudaStream_t s) {
@@ -267,11 +333,17 @@ int forward_apply(fds_handle *h, const T *X, T *Y, int nc, cudaStream_t s) {
         FDS_CUDA_TRY(cudaMemcpyAsync(rX, hv, sizeof(hv), cudaMemcpyHostToDevice, s));
         FDS_TRY(F::gemm(1, (int)h->Dtop, nc, F::top(h), 0, rX, rX + 1, 0, s));
         fl += 8.0 * (double)h->Dtop * h->Dtop * nc;
-        const MatRefT<T> *Bd = (L > l0) ? F::S(Tl) : F::D(Tl);
-        fds_count_launch(), k_refs<T><<<(Tl.nb + 127) / 128, 128, 0, s>>>(Tl.nb, xt, Tl.d_doff.p, nc, h->Dtop, rZ);
-        fds_count_launch(), k_refs<T><<<(Tl.nb + 127) / 128, 128, 0, s>>>(Tl.nb, yt, Tl.d_doff.p, nc, h->Dtop, rY);
-        FDS_TRY(F::gemm(Tl.nb, Tl.dmax, nc, Bd, 0, rZ, rY, 1, s));
-        fl += 8.0 * level_d2(Tl) * nc;
+        if (L > l0) {
+            FDS_TRY(apply_S<T>(h, Tl, xt, h->Dtop, yt, h->Dtop, nc, s));
+            fl += 8.0 * Tl.sum_s2 * nc;
+        } else {
+            fds_count_launch(), k_refs<T><<<(Tl.nb + 127) / 128, 128, 0, s>>>(Tl.nb, xt, Tl.d_doff.p, nc, h->Dtop,
+                                                                              rZ);
+            fds_count_launch(), k_refs<T><<<(Tl.nb + 127) / 128, 128, 0, s>>>(Tl.nb, yt, Tl.d_doff.p, nc, h->Dtop,
+                                                                              rY);
+            FDS_TRY(F::gemm(Tl.nb, Tl.dmax, nc, F::D(Tl), 0, rZ, rY, 1, s));
+            fl += 8.0 * level_d2(Tl) * nc;
+        }
     }
     // down
     for (int l = l0 + 1; l <= L; ++l) {
@@ -287,12 +359,16 @@ int forward_apply(fds_handle *h, const T *X, T *Y, int nc, cudaStream_t s) {
                                                                    C.d_par_pos2.p, Pn.d_doff.p, wt[l].p, ldr, ypar,
                                                                    ldp, nc, 1);
         FDS_TRY(apply_VH<T>(h, C, F::Tm(C), wt[l].p, ldr, yl, C.D, nc, s));
-        fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, yl, C.d_doff.p, nc, C.D, rY);
-        fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, xl, C.d_doff.p, nc, C.D, rZ);
-        FDS_CUDA_TRY(cudaGetLastError());
-        const MatRefT<T> *Bd = (l == L) ? F::D(C) : F::S(C);
-        FDS_TRY(F::gemm(nb, C.dmax, nc, Bd, 0, rZ, rY, 1, s));
-        fl += 8.0 * (C.sum_tm + level_d2(C)) * nc;
+        if (l < L) {
+            FDS_TRY(apply_S<T>(h, C, xl, C.D, yl, C.D, nc, s));
+            fl += 8.0 * (C.sum_tm + C.sum_s2) * nc;
+        } else {
+            fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, yl, C.d_doff.p, nc, C.D, rY);
+            fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, xl, C.d_doff.p, nc, C.D, rZ);
+            FDS_CUDA_TRY(cudaGetLastError());
+            FDS_TRY(F::gemm(nb, C.dmax, nc, F::D(C), 0, rZ, rY, 1, s));
+            fl += 8.0 * (C.sum_tm + level_d2(C)) * nc;
+        }
     }
     ps.flops = fl;
     return FDS_OK;
@@ -367,6 +443,48 @@ int fds_mixed_prepare(fds_handle *h) {
         FDS_TRY(split_blocks(C.W, C.Wp, C.rWp, C.offW, dv, rv, s));
         FDS_TRY(split_blocks(C.At, C.Atp, C.rAtp, C.offAt, rv, rv, s));
     }
+    // compact sibling blocks of every parent level (l0 .. L-1): child a's and
+    // b's skeleton DOFs of the parent, grouped by child
+    for (int l = L - 1; l >= l0; --l) {
+        Level &Pn = h->lv[l];
+        const Level &Ch = h->lv[l + 1];
+        if (!Pn.Sfw.p) continue;
+        std::vector<int> sperm(Pn.D), ra(Pn.nb), rb(Pn.nb);
+        std::vector<int64_t> scoff(2 * (size_t)Pn.nb + 1, 0);
+        Pn.srmax = 0;
+        Pn.sum_s2 = 0;
+        for (int p = 0; p < Pn.nb; ++p) {
+            const int a = 2 * p, b = 2 * p + 1;
+            const int n1p = Pn.n1[p];
+            int q = 0;
+            const int64_t o = Pn.doff[p];
+            for (int i = 0; i < Ch.k1[a]; ++i) sperm[o + q++] = i;
+            for (int i = 0; i < Ch.k2[a]; ++i) sperm[o + q++] = n1p + i;
+            for (int i = 0; i < Ch.k1[b]; ++i) sperm[o + q++] = Ch.k1[a] + i;
+            for (int i = 0; i < Ch.k2[b]; ++i) sperm[o + q++] = n1p + Ch.k2[a] + i;
+            ra[p] = Ch.k1[a] + Ch.k2[a];
+            rb[p] = Ch.k1[b] + Ch.k2[b];
+            scoff[2 * p + 1] = scoff[2 * p] + (int64_t)ra[p] * rb[p];
+            scoff[2 * p + 2] = scoff[2 * p + 1] + (int64_t)ra[p] * rb[p];
+            Pn.srmax = std::max(Pn.srmax, std::max(ra[p], rb[p]));
+            Pn.sum_s2 += 2.0 * ra[p] * rb[p];
+        }
+        FDS_TRY(Pn.d_sperm.upload(sperm, s));
+        FDS_TRY(Pn.d_ra.upload(ra, s));
+        FDS_TRY(Pn.d_rb.upload(rb, s));
+        FDS_TRY(Pn.d_scoff.upload(scoff, s));
+        FDS_TRY(Pn.Sc.alloc((size_t)std::max<int64_t>(scoff[2 * Pn.nb], 1)));
+        if (Pn.d_doff.n < (size_t)Pn.nb + 1) FDS_TRY(Pn.d_doff.upload(Pn.doff, s));
+        fds_count_launch(), k_extract_s<<<Pn.nb, 256, 0, s>>>(Pn.rSfw.p, Pn.d_sperm.p, Pn.d_doff.p, Pn.d_ra.p,
+                                                              Pn.d_rb.p, Pn.d_scoff.p, Pn.Sc.p);
+        FDS_CUDA_TRY(cudaGetLastError());
+        if (h->opt.ir_apply == FDS_APPLY_FF) {
+            FDS_TRY(Pn.Scp.alloc(Pn.Sc.n));
+            fds_count_launch(), k_split<<<1024, 256, 0, s>>>(Pn.Sc.p, Pn.Scp.p, (int64_t)Pn.Sc.n);
+            FDS_CUDA_TRY(cudaGetLastError());
+        }
+        bytes += (int64_t)(Pn.Sc.bytes() + Pn.Scp.bytes()) - (int64_t)Pn.Sfw.bytes();
+    }
     if (h->opt.ir_apply == FDS_APPLY_FF || h->opt.sweep_ff) {
         for (int l = L; l > l0; --l) {
             Level &C = h->lv[l];
@@ -385,7 +503,7 @@ int fds_mixed_prepare(fds_handle *h) {
                 rv[b] = l > l0 ? C.k1[b] + C.k2[b] : 0;
             }
             if (C.Dfw.p) FDS_TRY(split_blocks(C.Dfw, C.Dp, C.rDp, C.offA, dv, dv, s));
-            if (C.Sfw.p) FDS_TRY(split_blocks(C.Sfw, C.Sp, C.rSp, C.offA, dv, dv, s));
+
         }
         {
             std::vector<int64_t> off = {0, h->Dtop * h->Dtop};
@@ -394,13 +512,16 @@ int fds_mixed_prepare(fds_handle *h) {
         }
     }
     FDS_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int l = L; l >= l0; --l) {   // the compact blocks replace the d x d sibling coupling
+        Level &C = h->lv[l];
+        C.Sfw.release();
+        C.rSfw.release();
+    }
     if (h->opt.ir_apply == FDS_APPLY_FF) {
         for (int l = L; l >= l0; --l) {
             Level &C = h->lv[l];
             C.Dfw.release();
             C.rDfw.release();
-            C.Sfw.release();
-            C.rSfw.release();
         }
         h->Atop_off.release();
         h->rtop_off.release();
