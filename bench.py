@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--ir-tol", type=float, default=1e-8)
     p.add_argument("--sweep-fp64-levels", type=int, default=-1)
     p.add_argument("--merge-c64", action="store_true", help="merge the complex64 levels in complex64")
+    p.add_argument("--c64-engine", default="simt", choices=["tensor", "simt"],
+                   help="complex64 products on the tensor cores (3xTF32) or the FP32 pipe")
     p.add_argument("--sweep-ff", type=int, default=1, choices=[0, 1, 2],
                    help="mixed sweep: 1 double-float upper levels, 2 double-float everywhere")
     p.add_argument("--rank", default="adaptive", choices=["learned", "adaptive"],
@@ -313,12 +315,14 @@ def main():
     from paper_2411_18026_gb300 import learned
     mlp = learned.load_params() if args.rank == "learned" else None
     rank_used = "learned" if mlp is not None else "adaptive"
+    c64_engine = fds.FDS_C64_TENSOR if args.c64_engine == "tensor" else fds.FDS_C64_SIMT
 
     def step(precision=prec, out=d_F, rec=info, params=mlp):
         h = fds.fds_build(xy, omega, 2.0, 1.0, args.eps, leaf_size=args.leaf, top_level=args.top, stream=stream,
                           precision=precision, ir_tol=args.ir_tol, sweep_fp64_levels=args.sweep_fp64_levels,
                           mlp_params=params, merge_c64=args.merge_c64 and precision == fds.FDS_MIXED,
-                          sweep_ff=args.sweep_ff if precision == fds.FDS_MIXED else 0)
+                          sweep_ff=args.sweep_ff if precision == fds.FDS_MIXED else 0,
+                          c64_engine=c64_engine)
         fds.fds_rhs_plane_wave_device(h, d_kinds, d_angles, out, stream)
         rec["converged"] = True
         try:
@@ -404,6 +408,7 @@ def main():
         o.precision, o.ir_tol, o.sweep_fp64_levels = prec, args.ir_tol, args.sweep_fp64_levels
         o.merge_c64 = 1 if args.merge_c64 else 0
         o.sweep_ff = args.sweep_ff
+        o.c64_engine = c64_engine
         mlp32 = None
         if mlp is not None:
             mlp32 = np.ascontiguousarray(mlp, dtype=np.float32)
@@ -475,7 +480,7 @@ def main():
                                   ("mixed precision, refined to residual %g" % args.ir_tol
                                    if args.precision == "mixed" else "plain FP64") + ", %s rank" % rank_used),
                    "l2": "working set (factors, vectors) larger than L2; no flush",
-                   "precision": args.precision},
+                   "precision": args.precision, "c64_engine": args.c64_engine},
         "ir_iters": info.get("ir_iters"), "ir_residual": info.get("ir_residual"),
         "ir_converged": info.get("converged"), "vs_fp64": compare, "rank_mode": rank_used,
         "id_sketched": info.get("id_sketched"), "id_fallback": info.get("id_fallback"),

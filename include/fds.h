@@ -56,6 +56,13 @@ extern "C" {
  * (predicted rank + sketch_extra) rows, CPQR of the sketch, and a check of
  * the ID residual on the whole proxy matrix against the adaptive CPQR's own
  * bound; cells that fail the check fall back to the adaptive CPQR. */
+/* Engine of the complex64 products (sweep levels below the double-float ones,
+ * and the merges with merge_c64 = 1): plain FP32 FMA, or the tensor cores
+ * (tcgen05, each fp32 operand split into three bf16 pieces, six products,
+ * fp32 accumulation in tensor memory). */
+#define FDS_C64_SIMT   0
+#define FDS_C64_TENSOR 1
+
 #define FDS_RANK_ADAPTIVE 0
 #define FDS_RANK_LEARNED  1
 /* Learned-rank network: 16 -> 64 -> 64 -> 1, tanh, FP32.  Parameter vector:
@@ -114,6 +121,9 @@ typedef struct {
     int32_t sketch_extra;  /* FDS_RANK_LEARNED: sketch rows beyond the predicted rank; default 12 */
     int32_t record_features; /* 1: keep the features and adaptive ranks of every (cell, component)
                               for fds_features_get (training data) */
+    int32_t c64_engine;    /* FDS_MIXED: FDS_C64_SIMT (default) or FDS_C64_TENSOR; the tensor
+                              cores' fp32 accumulation is less accurate than fp32 FMA, which
+                              can cost the refinement an extra sweep */
 } fds_options;
 
 /* Statistics of a built handle. */
@@ -283,6 +293,24 @@ int fds_lu_batched(int32_t batch, const int32_t *d_d, const int64_t *d_off, doub
  */
 int fds_lu_batched_noalloc(int32_t batch, const int32_t *d_d, const int64_t *d_off, double *d_A,
                            int32_t *d_piv, const int64_t *d_poff, int32_t *d_info, uint64_t stream);
+
+/*
+ * Batched complex64 GEMM of the mixed-precision levels (Sec. 7.3 products in
+ * complex64; stage entry for tests and benchmarks):
+ *   C_b = alpha op(A_b) B_b + beta C_b,   b = 0 .. batch-1,
+ * op = identity (opA 0) or conjugate transpose (opA 2); op(A_b) is m[b] x k[b],
+ * B_b k[b] x n[b], C_b m[b] x n[b].  All column-major complex64 (re, im float
+ * pairs) with leading dimension = rows, at d_A + 2*aoff[b], d_B + 2*boff[b],
+ * d_C + 2*coff[b] floats (A_b stored k[b] x m[b] for opA 2).  alpha, beta real.
+ * engine: FDS_C64_TENSOR (tcgen05, bf16 x 3 pieces) or FDS_C64_SIMT.  d_m, d_n, d_k,
+ * d_*off are host arrays of batch entries; the call allocates (and frees,
+ * after synchronising the stream) the device descriptors.  batch <= 65535.
+ * FDS_ERR_TIMEOUT if a tensor-core wait gave up (the stream is synchronised).
+ */
+int fds_cgemm_c64_batched(int32_t batch, const int32_t *m, const int32_t *n, const int32_t *k,
+                          const int64_t *aoff, const int64_t *boff, const int64_t *coff, const float *d_A,
+                          const float *d_B, float *d_C, int32_t opA, float alpha, float beta, int32_t engine,
+                          uint64_t stream);
 
 /*
  * Training data of the learned-rank network (extension): the 16 features of

@@ -8,6 +8,7 @@
 #include "fds_internal.cuh"
 
 thread_local cudaStream_t g_alloc_stream = 0;
+thread_local int g_c64_tensor = 1;
 
 extern "C" void fds_default_options(fds_options *o) {
     if (!o) return;
@@ -30,6 +31,7 @@ extern "C" void fds_default_options(fds_options *o) {
     o->mlp_params = nullptr;
     o->sketch_extra = 12;
     o->record_features = 0;
+    o->c64_engine = FDS_C64_SIMT;
 }
 
 extern "C" const char *fds_error_string(int code) {
@@ -69,7 +71,7 @@ int fds_build_owned(const fds_geometry *g, double omega, double lambda, double m
         o.ir_max_iter > 100 || (o.ir_apply != FDS_APPLY_FF && o.ir_apply != FDS_APPLY_FP64) ||
         (o.rank_mode != FDS_RANK_ADAPTIVE && o.rank_mode != FDS_RANK_LEARNED) ||
         (o.rank_mode == FDS_RANK_LEARNED && !o.mlp_params) || o.sketch_extra < 1 || o.sketch_extra > 64 || o.sweep_fp64_levels < -1 || o.sweep_ff < 0 ||
-        o.sweep_ff > 2)
+        o.sweep_ff > 2 || (o.c64_engine != FDS_C64_SIMT && o.c64_engine != FDS_C64_TENSOR))
         return FDS_ERR_ARG;
     for (int i = 0; i < 2 * g->n_nodes; ++i)
         if (!std::isfinite(g->xy[i])) return FDS_ERR_ARG;

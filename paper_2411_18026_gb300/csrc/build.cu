@@ -559,6 +559,7 @@ int launch_group_blocks(fds_handle *h, const char *name, const std::vector<int64
 // ------------------------------------------------------------------ build
 int fds_build_impl(fds_handle *h) {
     cudaStream_t s = h->stream;
+    C64EngineScope eng(h->opt.c64_engine == FDS_C64_TENSOR);
     FDS_TRY(ensure_gauss_tables());
     const int N = h->N;
     const int leaf = h->opt.leaf_size;
@@ -1197,5 +1198,13 @@ int fds_build_impl(fds_handle *h) {
     h->build_ms = ms;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (h->opt.precision == FDS_MIXED && h->opt.merge_c64 && h->opt.c64_engine == FDS_C64_TENSOR) {
+        int st = 0;
+        FDS_TRY(tc_status_take(s, &st));
+        if (st) {
+            fds_set_error_detail("tensor-core GEMM: wait on the MMA barrier timed out");
+            return FDS_ERR_TIMEOUT;
+        }
+    }
     return FDS_OK;
 }

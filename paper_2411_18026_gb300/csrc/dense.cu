@@ -4,6 +4,7 @@
 #include <mutex>
 
 #include "dense.cuh"
+#include "fds_internal.cuh"
 
 namespace {
 
@@ -253,6 +254,8 @@ int dense_gemm(int batch, int max_m, int max_n, const MatRef *d_A, int opA, cons
 }
 int dense_gemm(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, const MatRefF *d_B, int opB,
                const MatRefF *d_C, cplxf alpha, cplxf beta, cudaStream_t s) {
+    if (opB == 0 && g_c64_tensor && alpha.y == 0.f && beta.y == 0.f)
+        return dense_gemm_tc(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha.x, beta.x, nullptr, s);
     if (opB == 0) return dense_gemm_rt(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
     return gemm_t<cplxf>(batch, max_m, max_n, d_A, opA, d_B, opB, d_C, alpha, beta, s);
 }

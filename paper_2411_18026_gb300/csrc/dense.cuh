@@ -58,6 +58,12 @@ int dense_gemm_map(int batch, int max_m, int max_n, const MatRefF *d_A, int opA,
                    const MatRefF *d_C, const RowMaps *d_maps, int accumulate, cudaStream_t s);
 int dense_gemm_map(int batch, int max_m, int max_n, const MatRefP *d_A, int opA, const MatRefP *d_B,
                    const MatRefP *d_C, const RowMaps *d_maps, int accumulate, cudaStream_t s);
+// complex64 GEMM on the tensor cores (tcgen05, bf16 pieces; gemm_tc.cu): real
+// alpha, beta; opA 0 or 2; optional row maps.
+int dense_gemm_tc(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, const MatRefF *d_B,
+                  const MatRefF *d_C, float alpha, float beta, const RowMaps *d_maps, cudaStream_t s);
+// Reads and clears the tensor-core timeout status (synchronises s).
+int tc_status_take(cudaStream_t s, int *status);
 // complex64 versions (mixed-precision merge and sweep)
 int dense_lu(int batch, int max_n, const MatRefF *d_A, int *d_piv, const int64_t *d_poff, int *d_info,
              cudaStream_t s);

@@ -13,6 +13,13 @@
 // different streams do not synchronise the device at every release; the
 // owned stream outlives every buffer of the handle.
 extern thread_local cudaStream_t g_alloc_stream;
+// complex64 GEMMs of this thread on the tensor cores (1) or FP32 FMA (0)
+extern thread_local int g_c64_tensor;
+struct C64EngineScope {
+    int prev;
+    explicit C64EngineScope(int v) : prev(g_c64_tensor) { g_c64_tensor = v; }
+    ~C64EngineScope() { g_c64_tensor = prev; }
+};
 
 struct AllocStreamScope {
     cudaStream_t prev;

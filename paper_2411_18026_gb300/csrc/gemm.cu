@@ -15,6 +15,7 @@
 //            44 bits of significand at 48 FP32 instructions per complex
 //            multiply-add, against FP64 at 1/64 of the FP32 rate on this GPU.
 #include "dense.cuh"
+#include "fds_internal.cuh"
 
 namespace {
 
@@ -279,6 +280,8 @@ int dense_gemm_map(int batch, int max_m, int max_n, const MatRef *d_A, int opA, 
 }
 int dense_gemm_map(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, const MatRefF *d_B,
                    const MatRefF *d_C, const RowMaps *d_maps, int accumulate, cudaStream_t s) {
+    if (g_c64_tensor)
+        return dense_gemm_tc(batch, max_m, max_n, d_A, opA, d_B, d_C, 1.f, accumulate ? 1.f : 0.f, d_maps, s);
     return launch<Arith64, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, mkcf(1, 0), mkcf(accumulate ? 1 : 0, 0), s,
                               d_maps);
 }

@@ -35,12 +35,6 @@
 
 namespace fdsk {
 
-// 1: both orientations of an element pair from one evaluation of the radial
-// functions (more registers); 0: two passes.
-#ifndef FDS_DUAL_ONEPASS
-#define FDS_DUAL_ONEPASS 1
-#endif
-
 #ifndef FDS_TILE_THREADS
 #define FDS_TILE_THREADS 128
 #endif
@@ -555,6 +549,7 @@ __device__ __forceinline__ void tile_side_build(TileSide &T, int N) {
 struct TileSmem {
     Rules G;
     TileSide R, C;
+    Elem eR[TILE_EL], eC[TILE_EL];        // geometry of the tile's elements
     double ef[TILE][TILE][2][2][2];   // forward entries  [row][col][i][j][re/im]
     double er[TILE][TILE][2][2][2];   // transposed entries [col][row][i][j][re/im]
 };
@@ -610,11 +605,45 @@ __device__ __forceinline__ void tile_scatter2(TileSmem &S, int re, int ce, const
     }
 }
 
-__device__ __forceinline__ double wsum(double v) {
+// Warp reduce-scatter of NV values (NV = 32 or 64): afterwards lane L holds
+// in v[0] the warp sum of index L and (NV = 64) in v[32] that of index L + 32.
+// Five halving steps (16, 8, 4, 2, 1 values per set of 32): 31 additions and
+// shuffles per set instead of 160 for a full reduction of every value.
+template <int NV>
+__device__ __forceinline__ void warp_reduce_scatter(double (&v)[NV], int lane) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int s = 0; s < 5; ++s) {
+        const int o = 16 >> s;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int set = 0; set < NV / 32; ++set)
+#pragma unroll
+            for (int i = 0; i < (16 >> s); ++i) {
+                const double a = v[set * 32 + i], b = v[set * 32 + i + (16 >> s)];
+                const double keep = up ? b : a, send = up ? a : b;
+                v[set * 32 + i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+    }
 }
+
+
+// Add one value of a pair's accumulator to the tile entries: k in 0..31
+// forward (dir 0) or transposed (dir 1); for the dual accumulator k in 0..63
+// (k >= 32 transposed).
+__device__ __forceinline__ void tile_add_one(TileSmem &S, int re, int ce, int k, int dir, double val) {
+    const int pr0 = S.R.pos[re][0], pr1 = S.R.pos[re][1];
+    const int pc0 = S.C.pos[ce][0], pc1 = S.C.pos[ce][1];
+    const int rem = k & 31;
+    const int x = rem >> 4, y = (rem >> 3) & 1, i = (rem >> 2) & 1, j = (rem >> 1) & 1, ri = rem & 1;
+    if (dir == 0 && k < 32) {
+        const int pr = x ? pr1 : pr0, pc = y ? pc1 : pc0;
+        if (pr >= 0 && pc >= 0) atomicAdd(&S.ef[pr][pc][i][j][ri], val);
+    } else {
+        const int pc = x ? pc1 : pc0, pr = y ? pr1 : pr0;
+        if (pr >= 0 && pc >= 0) atomicAdd(&S.er[pc][pr][i][j][ri], val);
+    }
+}
+
 
 // Evaluate all element pairs of a tile into S.ef / S.er.
 //   same  : both sides on the same polygon X (singular-aware rule set);
@@ -629,32 +658,33 @@ static __device__ void tile_eval(const PhysDev &P, TileSmem &S, const double *__
                           const double *__restrict__ Y, int NY, bool same, bool dual, bool diag) {
     const int npairs = S.R.ne * S.C.ne;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // element geometry once per tile
+    for (int k = threadIdx.x; k < S.R.ne + S.C.ne; k += blockDim.x) {
+        if (k < S.R.ne) {
+            S.eR[k] = load_elem(X, NX, S.R.el[k]);
+        } else {
+            const int c = k - S.R.ne;
+            S.eC[c] = load_elem(same ? X : Y, same ? NX : NY, S.C.el[c]);
+        }
+    }
+    __syncthreads();
     // pass 1: cheap pairs, one per thread
     for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
         const int re = q / S.C.ne, ce = q - re * S.C.ne;
         const int ie = S.R.el[re], jf = S.C.el[ce];
         if (diag && ie > jf) continue;
-        const Elem E = load_elem(X, NX, ie);
-        const Elem F = load_elem(same ? X : Y, same ? NX : NY, jf);
+        const Elem E = S.eR[re];
+        const Elem F = S.eC[ce];
         const int kind = same ? pair_kind(E, F, ie, jf, NX, P.kT) : PK_CROSS;
         if (!cheap_kind(kind)) continue;
         const int mA = (S.R.pos[re][0] >= 0 ? 1 : 0) | (S.R.pos[re][1] >= 0 ? 2 : 0);
         const int mB = (S.C.pos[ce][0] >= 0 ? 1 : 0) | (S.C.pos[ce][1] >= 0 ? 2 : 0);
         if (dual || diag) {
-#if FDS_DUAL_ONEPASS
             PairAcc2 A;
 #pragma unroll
             for (int k = 0; k < 64; ++k) A.v[k] = 0.0;
             acc_pair2(P, S.G, kind, E, F, 0, 1, mA, mB, A);
             tile_scatter2(S, re, ce, A, 0, 1);
-#else
-            for (int dir = 0; dir < 2; ++dir) {
-                PairAcc A;
-                acc_zero(A);
-                acc_pair(P, S.G, kind, E, F, 0, 1, dir, mA, mB, A);
-                tile_scatter(S, re, ce, A, dir, 0, 1);
-            }
-#endif
             if (d_count_points) atomicAdd(&d_quad_points, 2ull * pair_points(kind, S.G.q) * (kind == PK_SELF ? 2 : 1));
         } else {
             PairAcc A;
@@ -669,8 +699,8 @@ static __device__ void tile_eval(const PhysDev &P, TileSmem &S, const double *__
         const int re = q / S.C.ne, ce = q - re * S.C.ne;
         const int ie = S.R.el[re], jf = S.C.el[ce];
         if (diag && ie > jf) continue;
-        const Elem E = load_elem(X, NX, ie);
-        const Elem F = load_elem(same ? X : Y, same ? NX : NY, jf);
+        const Elem E = S.eR[re];
+        const Elem F = S.eC[ce];
         const int kind = same ? pair_kind(E, F, ie, jf, NX, P.kT) : PK_CROSS;
         if (cheap_kind(kind)) continue;
         const int mA = (S.R.pos[re][0] >= 0 ? 1 : 0) | (S.R.pos[re][1] >= 0 ? 2 : 0);
@@ -678,33 +708,21 @@ static __device__ void tile_eval(const PhysDev &P, TileSmem &S, const double *__
         // a self pair in a diagonal tile: its transposed entries are forward entries too
         const bool d = diag ? (ie != jf) : dual;
         if (d) {
-#if FDS_DUAL_ONEPASS
             PairAcc2 A;
 #pragma unroll
             for (int k = 0; k < 64; ++k) A.v[k] = 0.0;
             acc_pair2(P, S.G, kind, E, F, lane, 32, mA, mB, A);
-#pragma unroll
-            for (int k = 0; k < 64; ++k) A.v[k] = wsum(A.v[k]);
-            tile_scatter2(S, re, ce, A, lane, 32);
-#else
-            for (int dir = 0; dir < 2; ++dir) {
-                PairAcc A;
-                acc_zero(A);
-                acc_pair(P, S.G, kind, E, F, lane, 32, dir, mA, mB, A);
-#pragma unroll
-                for (int k = 0; k < 32; ++k) A.v[k] = wsum(A.v[k]);
-                tile_scatter(S, re, ce, A, dir, lane, 32);
-            }
-#endif
+            warp_reduce_scatter<64>(A.v, lane);
+            tile_add_one(S, re, ce, lane, 0, A.v[0]);
+            tile_add_one(S, re, ce, lane + 32, 0, A.v[32]);
             if (d_count_points && lane == 0)
                 atomicAdd(&d_quad_points, 2ull * pair_points(kind, S.G.q) * (kind == PK_SELF ? 2 : 1));
         } else {
             PairAcc A;
             acc_zero(A);
             acc_pair(P, S.G, kind, E, F, lane, 32, 0, mA, mB, A);
-#pragma unroll
-            for (int k = 0; k < 32; ++k) A.v[k] = wsum(A.v[k]);
-            tile_scatter(S, re, ce, A, 0, lane, 32);
+            warp_reduce_scatter<32>(A.v, lane);
+            tile_add_one(S, re, ce, lane, 0, A.v[0]);
             if (d_count_points && lane == 0)
                 atomicAdd(&d_quad_points, 1ull * pair_points(kind, S.G.q) * (kind == PK_SELF ? 2 : 1));
         }

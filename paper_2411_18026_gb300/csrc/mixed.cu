@@ -638,7 +638,16 @@ int solve_mixed(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
 }
 
 int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
+    C64EngineScope eng(h->opt.c64_engine == FDS_C64_TENSOR);
     // the refinement's sweep vectors are in the leaf level's precision
-    if (h->L > h->l0 && level_prec(h, h->L) == PREC_FF) return solve_mixed<float4>(h, d_rhs, nrhs, s);
-    return solve_mixed<cplxf>(h, d_rhs, nrhs, s);
+    const int rc = (h->L > h->l0 && level_prec(h, h->L) == PREC_FF) ? solve_mixed<float4>(h, d_rhs, nrhs, s)
+                                                                   : solve_mixed<cplxf>(h, d_rhs, nrhs, s);
+    if (h->opt.c64_engine != FDS_C64_TENSOR) return rc;
+    int st = 0;
+    const int rs = tc_status_take(s, &st);
+    if (st) {
+        fds_set_error_detail("tensor-core GEMM: wait on the MMA barrier timed out");
+        return FDS_ERR_TIMEOUT;
+    }
+    return rc != FDS_OK ? rc : rs;
 }

@@ -26,6 +26,8 @@ FDS_FP64 = 0
 FDS_MIXED = 1
 FDS_APPLY_FF = 0
 FDS_APPLY_FP64 = 1
+FDS_C64_SIMT = 0
+FDS_C64_TENSOR = 1
 FDS_RANK_ADAPTIVE = 0
 FDS_RANK_LEARNED = 1
 FDS_MLP_NIN = 16
@@ -63,7 +65,7 @@ class fds_options(ctypes.Structure):
                 ("ir_max_iter", ctypes.c_int32), ("ir_apply", ctypes.c_int32), ("sweep_fp64_levels", ctypes.c_int32),
                 ("sweep_ff", ctypes.c_int32), ("merge_c64", ctypes.c_int32), ("rank_mode", ctypes.c_int32),
                 ("mlp_params", ctypes.POINTER(ctypes.c_float)), ("sketch_extra", ctypes.c_int32),
-                ("record_features", ctypes.c_int32)]
+                ("record_features", ctypes.c_int32), ("c64_engine", ctypes.c_int32)]
 
 
 class fds_stats(ctypes.Structure):
@@ -110,6 +112,9 @@ def lib():
     L.fds_id_batched.argtypes = [i32, vp, vp, vp, vp, f64, vp, vp, vp, vp, vp, u64]
     L.fds_lu_batched.argtypes = [i32, vp, vp, vp, vp, vp, vp, u64]
     L.fds_lu_batched_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, u64]
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    L.fds_cgemm_c64_batched.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), i64p,
+                                        i64p, i64p, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, i32, u64]
     L.fds_timing_enable.argtypes = [i32]
     L.fds_timing_enable.restype = None
     L.fds_timing_reset.argtypes = []
@@ -198,7 +203,7 @@ class Handle:
 def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy_ratio=1.5, proxy_points=64,
               alpha=None, stream=0, precision=FDS_FP64, ir_tol=None, ir_max_iter=None, ir_apply=None,
               mlp_params=None, sketch_extra=None, record_features=False, sweep_fp64_levels=None, merge_c64=False,
-              sweep_ff=1):
+              sweep_ff=1, c64_engine=FDS_C64_SIMT):
     """Factorise; mlp_params (FDS_MLP_NPARAM floats) selects the learned-rank ID."""
     xy = np.ascontiguousarray(xy, dtype=np.float64)
     g = fds_geometry(len(xy), xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(rho))
@@ -228,6 +233,7 @@ def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy
     o.merge_c64 = 1 if merge_c64 else 0
     o.sweep_ff = int(sweep_ff)
     o.record_features = 1 if record_features else 0
+    o.c64_engine = int(c64_engine)
     out = ctypes.c_void_p()
     _check(lib().fds_build_ex(ctypes.byref(g), float(omega), float(lam), float(mu), float(tol), ctypes.byref(o),
                               ctypes.byref(out)), "fds_build")
@@ -369,6 +375,21 @@ def fds_lu_batched_noalloc(d_d, d_off, d_A, d_piv, d_poff, d_info, stream=None):
 def fds_lu_batched(d_d, d_off, d_A, d_piv, d_poff, d_info, stream=None):
     _check(lib().fds_lu_batched(d_d.numel(), _ptr(d_d), _ptr(d_off), _ptr(d_A), _ptr(d_piv), _ptr(d_poff),
                                 _ptr(d_info), _stream(stream)), "fds_lu_batched")
+
+
+def fds_cgemm_c64_batched(m, n, k, aoff, boff, coff, d_A, d_B, d_C, opA=0, alpha=1.0, beta=0.0,
+                          engine=FDS_C64_TENSOR, stream=None):
+    """Batched complex64 C_b = alpha op(A_b) B_b + beta C_b (device complex64 buffers, host sizes)."""
+    batch = len(m)
+    arr = lambda v, t: np.ascontiguousarray(v, dtype=t)
+    m, n, k = arr(m, np.int32), arr(n, np.int32), arr(k, np.int32)
+    aoff, boff, coff = arr(aoff, np.int64), arr(boff, np.int64), arr(coff, np.int64)
+    i32p, i64p = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
+    _check(lib().fds_cgemm_c64_batched(batch, m.ctypes.data_as(i32p), n.ctypes.data_as(i32p),
+                                       k.ctypes.data_as(i32p), aoff.ctypes.data_as(i64p),
+                                       boff.ctypes.data_as(i64p), coff.ctypes.data_as(i64p), _ptr(d_A), _ptr(d_B),
+                                       _ptr(d_C), int(opA), float(alpha), float(beta), int(engine),
+                                       _stream(stream)), "fds_cgemm_c64_batched")
 
 
 def fds_timing_enable(on=True):
