@@ -1,9 +1,9 @@
 // Register-tiled batched complex GEMM, C = alpha op(A) B + beta C, for the
-// solve sweep and the forward operator.  One CTA computes a 64 x 16 TJ tile
-// of one matrix of the batch; 256 threads, each a 4 x TJ micro-tile with rows
-// tx + 16 i and columns ty + 16 j (conflict-free shared-memory reads), K in
-// steps of 16 staged in shared memory.  TJ = 4 for complex64/128, 2 for the
-// double-float variant (register budget).
+// solve sweep and the forward operator.  One CTA computes a 16 MI x 16 TJ
+// tile of one matrix of the batch (MI = 2, 3 or 4 row groups, picked per
+// launch from the largest row count); 256 threads, each an MI x TJ
+// micro-tile with rows tx + 16 i and columns ty + 16 j (conflict-free
+// shared-memory reads), K in steps of 16 staged in shared memory.
 //
 // Three arithmetics share the tiling:
 //   Arith64  complex64 loads, FP32 FMA
@@ -19,7 +19,7 @@
 
 namespace {
 
-constexpr int BM = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 
 // ---------------------------------------------------------------- arithmetics
 struct Arith64 {
@@ -155,10 +155,58 @@ struct ArithFFP {
     }
 };
 
+// Float-pair operands with Gauss's three-product complex multiply:
+//   (a + i b)(c + i d) = (k1 - k3) + i (k1 + k2),
+//   k1 = c (a + b),  k2 = a (d - c),  k3 = b (c + d),
+// the sums a + b (per staged element of op(A)) and d - c, c + d (per staged
+// element of B) formed once when the tile is staged and reused by every
+// product of the tile: 36 FP32 instructions per complex multiply-add.
+struct ArithFFP3 {
+    typedef float4 G;
+    struct SA {
+        ff a, b, s;     // re, im, re + im
+    };
+    struct SB {
+        ff c, dm, dp;   // re, im - re, re + im
+    };
+    struct Acc {
+        ff k1, k2, k3;
+    };
+    __device__ static SA stage_a(G v, bool cj) {
+        const ff a{v.x, v.z}, b = cj ? ff{-v.y, -v.w} : ff{v.y, v.w};
+        return SA{a, b, ff_add(a, b)};
+    }
+    __device__ static SB stage_b(G v) {
+        const ff c{v.x, v.z}, d{v.y, v.w};
+        return SB{c, ff_add(d, ff{-c.h, -c.l}), ff_add(c, d)};
+    }
+    __device__ static SA za() { return SA{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}; }
+    __device__ static SB zb() { return SB{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}; }
+    __device__ static void zero(Acc &x) { x = Acc{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}; }
+    __device__ static void mac(Acc &x, const SA &a, const SB &b) {
+        ff_mac(x.k1, b.c, a.s);
+        ff_mac(x.k2, a.a, b.dm);
+        ff_mac(x.k3, a.b, b.dp);
+    }
+    __device__ static G finish(const Acc &x, G alpha, G, const G *old) {
+        const ff k1 = ff_norm(x.k1), k2 = ff_norm(x.k2), k3 = ff_norm(x.k3);
+        ff re = ff_add(k1, ff{-k3.h, -k3.l}), im = ff_add(k1, k2);
+        if (alpha.x < 0.f) {   // alpha = -1
+            re = ff{-re.h, -re.l};
+            im = ff{-im.h, -im.l};
+        }
+        if (old) {
+            re = ff_add(re, ff{old->x, old->z});
+            im = ff_add(im, ff{old->y, old->w});
+        }
+        return make_float4(re.h, im.h, re.l, im.l);
+    }
+};
+
 // TJ columns per thread (CTA tile 64 x 16 TJ)
 // Optional row maps (maps nullable, and each pointer nullable): B's row k is
 // read from row bmap[k], C's row i is written to row cmap[i].
-template <class Ar, int TJ>
+template <class Ar, int TJ, int MI>
 __global__ void __launch_bounds__(NT) k_gemm_rt(const MatRefT<typename Ar::G> *__restrict__ As, int opA,
                                                 const MatRefT<typename Ar::G> *__restrict__ Bs,
                                                 const MatRefT<typename Ar::G> *__restrict__ Cs,
@@ -172,29 +220,29 @@ __global__ void __launch_bounds__(NT) k_gemm_rt(const MatRefT<typename Ar::G> *_
     const int *cmap = maps ? maps[blockIdx.y].c : nullptr;
     const int M = Cm.rows, N = Cm.cols;
     const int K = (opA == 0) ? A.cols : A.rows;
-    constexpr int BN = 16 * TJ;
-    const int i0 = (blockIdx.x % tiles_m) * BM, j0 = (blockIdx.x / tiles_m) * BN;
+    constexpr int BN = 16 * TJ, BMt = 16 * MI;
+    const int i0 = (blockIdx.x % tiles_m) * BMt, j0 = (blockIdx.x / tiles_m) * BN;
     if (i0 >= M || j0 >= N) return;
-    __shared__ SA sa[BK][BM];
+    __shared__ SA sa[BK][BMt];
     __shared__ SB sb[BK][16 * TJ];
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-    typename Ar::Acc acc[4][TJ];
+    typename Ar::Acc acc[MI][TJ];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < MI; ++i)
 #pragma unroll
         for (int j = 0; j < TJ; ++j) Ar::zero(acc[i][j]);
     for (int k0 = 0; k0 < K; k0 += BK) {
-        // stage op(A)[i0:i0+64, k0:k0+16] as sa[k][i]
+        // stage op(A)[i0:i0+BMt, k0:k0+16] as sa[k][i]
         if (opA == 0) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int i = t & 63, k = (t >> 6) + 4 * q;
+            for (int q = 0; q < MI; ++q) {
+                const int e = t + NT * q, i = e % BMt, k = e / BMt;
                 const int gi = i0 + i, gk = k0 + k;
                 sa[k][i] = (gi < M && gk < K) ? Ar::stage_a(A.p[gi + (int64_t)gk * A.ld], false) : Ar::za();
             }
         } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < MI; ++q) {
                 const int k = t & 15, i = (t >> 4) + 16 * q;
                 const int gi = i0 + i, gk = k0 + k;
                 sa[k][i] = (gi < M && gk < K) ? Ar::stage_a(A.p[gk + (int64_t)gi * A.ld], true) : Ar::za();
@@ -210,21 +258,21 @@ __global__ void __launch_bounds__(NT) k_gemm_rt(const MatRefT<typename Ar::G> *_
         __syncthreads();
         const int kmax = min(BK, K - k0);
         for (int k = 0; k < kmax; ++k) {
-            SA a[4];
+            SA a[MI];
             SB b[TJ];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = sa[k][tx + 16 * i];
+            for (int i = 0; i < MI; ++i) a[i] = sa[k][tx + 16 * i];
 #pragma unroll
             for (int j = 0; j < TJ; ++j) b[j] = sb[k][ty + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < MI; ++i)
 #pragma unroll
                 for (int j = 0; j < TJ; ++j) Ar::mac(acc[i][j], a[i], b[j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < MI; ++i)
 #pragma unroll
         for (int j = 0; j < TJ; ++j) {
             const int gi = i0 + tx + 16 * i, gj = j0 + ty + 16 * j;
@@ -235,64 +283,85 @@ __global__ void __launch_bounds__(NT) k_gemm_rt(const MatRefT<typename Ar::G> *_
         }
 }
 
-template <class Ar, int TJ>
+template <class Ar, int TJ, int MI>
+int launch_t(int batch, int max_m, int max_n, const MatRefT<typename Ar::G> *d_A, int opA,
+             const MatRefT<typename Ar::G> *d_B, const MatRefT<typename Ar::G> *d_C, typename Ar::G alpha,
+             typename Ar::G beta, cudaStream_t s, const RowMaps *maps) {
+    constexpr int BN = 16 * TJ, BMt = 16 * MI;
+    const int tm = (max_m + BMt - 1) / BMt, tn = (max_n + BN - 1) / BN;
+    const int use_beta = (beta.x != 0 || beta.y != 0) ? 1 : 0;
+    dim3 grid(tm * tn, batch);
+    fds_count_launch(),
+        k_gemm_rt<Ar, TJ, MI><<<grid, NT, 0, s>>>(d_A, opA, d_B, d_C, alpha, beta, use_beta, tm, maps);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
+}
+
+// Tile height 32, 48 or 64 rows, whichever pads the largest row count of the
+// batch least (ties to the taller tile); the column width keeps about the
+// same number of products per thread (TJ2, TJ3, TJ4 for 2, 3, 4 row groups).
+template <class Ar, int TJ4, int TJ3, int TJ2>
 int launch(int batch, int max_m, int max_n, const MatRefT<typename Ar::G> *d_A, int opA,
            const MatRefT<typename Ar::G> *d_B, const MatRefT<typename Ar::G> *d_C, typename Ar::G alpha,
            typename Ar::G beta, cudaStream_t s, const RowMaps *maps = nullptr) {
     if (batch <= 0 || max_m <= 0 || max_n <= 0) return FDS_OK;
     if (opA != 0 && opA != 2) return FDS_ERR_ARG;
-    constexpr int BN = 16 * TJ;
-    const int tm = (max_m + BM - 1) / BM, tn = (max_n + BN - 1) / BN;
-    const int use_beta = (beta.x != 0 || beta.y != 0) ? 1 : 0;
-    dim3 grid(tm * tn, batch);
-    fds_count_launch(), k_gemm_rt<Ar, TJ><<<grid, NT, 0, s>>>(d_A, opA, d_B, d_C, alpha, beta, use_beta, tm, maps);
-    FDS_CUDA_TRY(cudaGetLastError());
-    return FDS_OK;
+    int best = 4, pad = 1 << 30;
+    for (int mi = 4; mi >= 2; --mi) {
+        const int p = (max_m + 16 * mi - 1) / (16 * mi) * 16 * mi;
+        if (p < pad) {
+            pad = p;
+            best = mi;
+        }
+    }
+    if (best == 2) return launch_t<Ar, TJ2, 2>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s, maps);
+    if (best == 3) return launch_t<Ar, TJ3, 3>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s, maps);
+    return launch_t<Ar, TJ4, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s, maps);
 }
 
 }  // namespace
 
 int dense_gemm_rt(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, const MatRef *d_C,
                   cplx alpha, cplx beta, cudaStream_t s) {
-    return launch<Arith128, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
+    return launch<Arith128, 4, 4, 8>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
 }
 
 int dense_gemm_rt(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, const MatRefF *d_B,
                   const MatRefF *d_C, cplxf alpha, cplxf beta, cudaStream_t s) {
-    return launch<Arith64, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
+    return launch<Arith64, 4, 4, 8>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
 }
 
 int dense_gemm_ff(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, const MatRef *d_C,
                   cplx alpha, cplx beta, cudaStream_t s) {
-    return launch<ArithFF, 2>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
+    return launch<ArithFF, 2, 2, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
 }
 
 int dense_gemm_ffp(int batch, int max_m, int max_n, const MatRefT<float4> *d_A, int opA, const MatRefT<float4> *d_B,
                    const MatRefT<float4> *d_C, int accumulate, cudaStream_t s) {
-    return launch<ArithFFP, 2>(batch, max_m, max_n, d_A, opA, d_B, d_C, make_float4(1.f, 0.f, 0.f, 0.f),
-                               make_float4(accumulate ? 1.f : 0.f, 0.f, 0.f, 0.f), s);
+    return launch<ArithFFP3, 2, 3, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, make_float4(1.f, 0.f, 0.f, 0.f),
+                                make_float4(accumulate ? 1.f : 0.f, 0.f, 0.f, 0.f), s);
 }
 
 int dense_gemm_map(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, const MatRef *d_C,
                    const RowMaps *d_maps, int accumulate, cudaStream_t s) {
-    return launch<Arith128, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, mkc(1, 0), mkc(accumulate ? 1 : 0, 0), s,
+    return launch<Arith128, 4, 4, 8>(batch, max_m, max_n, d_A, opA, d_B, d_C, mkc(1, 0), mkc(accumulate ? 1 : 0, 0), s,
                                d_maps);
 }
 int dense_gemm_map(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, const MatRefF *d_B,
                    const MatRefF *d_C, const RowMaps *d_maps, int accumulate, cudaStream_t s) {
     if (g_c64_tensor)
         return dense_gemm_tc(batch, max_m, max_n, d_A, opA, d_B, d_C, 1.f, accumulate ? 1.f : 0.f, d_maps, s);
-    return launch<Arith64, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, mkcf(1, 0), mkcf(accumulate ? 1 : 0, 0), s,
+    return launch<Arith64, 4, 4, 8>(batch, max_m, max_n, d_A, opA, d_B, d_C, mkcf(1, 0), mkcf(accumulate ? 1 : 0, 0), s,
                               d_maps);
 }
 int dense_gemm_map(int batch, int max_m, int max_n, const MatRefP *d_A, int opA, const MatRefP *d_B,
                    const MatRefP *d_C, const RowMaps *d_maps, int accumulate, cudaStream_t s) {
-    return launch<ArithFFP, 2>(batch, max_m, max_n, d_A, opA, d_B, d_C, make_float4(1.f, 0.f, 0.f, 0.f),
-                               make_float4(accumulate ? 1.f : 0.f, 0.f, 0.f, 0.f), s, d_maps);
+    return launch<ArithFFP3, 2, 3, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, make_float4(1.f, 0.f, 0.f, 0.f),
+                                make_float4(accumulate ? 1.f : 0.f, 0.f, 0.f, 0.f), s, d_maps);
 }
 
 int dense_gemm(int batch, int max_m, int max_n, const MatRefP *d_A, int opA, const MatRefP *d_B, int opB,
                const MatRefP *d_C, float4 alpha, float4 beta, cudaStream_t s) {
     if (opB != 0) return FDS_ERR_ARG;
-    return launch<ArithFFP, 2>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
+    return launch<ArithFFP3, 2, 3, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
 }

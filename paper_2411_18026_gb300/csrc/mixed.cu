@@ -312,7 +312,11 @@ int forward_apply(fds_handle *h, const T *X, T *Y, int nc, cudaStream_t s) {
         const int nb = C.nb;
         const int64_t ldr = std::max<int64_t>(C.Rtot, 1);
         T *xl = (l == L) ? (T *)X : wz[l].p;
-        FDS_TRY(apply_V<T>(h, C, F::Tm(C), xl, C.D, wt[l].p, ldr, nc, s));
+        {
+            ProfScope pv("a7.fw_interp_up", s);
+            pv.flops = 8.0 * C.sum_tm * nc;
+            FDS_TRY(apply_V<T>(h, C, F::Tm(C), xl, C.D, wt[l].p, ldr, nc, s));
+        }
         T *par = (l - 1 > l0) ? wz[l - 1].p : F::xtop(h).p;
         const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
         fds_count_launch(), k_child_parent_t<T><<<nb, 256, 0, s>>>(nb, C.d_roff.p, C.d_k1.p, C.d_par_pos1.p,
@@ -330,6 +334,8 @@ int forward_apply(fds_handle *h, const T *X, T *Y, int nc, cudaStream_t s) {
         MatRefT<T> hv[2];
         hv[0].p = xt; hv[0].rows = (int)h->Dtop; hv[0].cols = nc; hv[0].ld = ld;
         hv[1].p = yt; hv[1].rows = (int)h->Dtop; hv[1].cols = nc; hv[1].ld = ld;
+        ProfScope pt("a7.fw_top", s);
+        pt.flops = 8.0 * (double)h->Dtop * h->Dtop * nc;
         FDS_CUDA_TRY(cudaMemcpyAsync(rX, hv, sizeof(hv), cudaMemcpyHostToDevice, s));
         FDS_TRY(F::gemm(1, (int)h->Dtop, nc, F::top(h), 0, rX, rX + 1, 0, s));
         fl += 8.0 * (double)h->Dtop * h->Dtop * nc;
@@ -358,11 +364,19 @@ int forward_apply(fds_handle *h, const T *X, T *Y, int nc, cudaStream_t s) {
         fds_count_launch(), k_child_parent_t<T><<<nb, 256, 0, s>>>(nb, C.d_roff.p, C.d_k1.p, C.d_par_pos1.p,
                                                                    C.d_par_pos2.p, Pn.d_doff.p, wt[l].p, ldr, ypar,
                                                                    ldp, nc, 1);
-        FDS_TRY(apply_VH<T>(h, C, F::Tm(C), wt[l].p, ldr, yl, C.D, nc, s));
+        {
+            ProfScope pv("a7.fw_interp_down", s);
+            pv.flops = 8.0 * C.sum_tm * nc;
+            FDS_TRY(apply_VH<T>(h, C, F::Tm(C), wt[l].p, ldr, yl, C.D, nc, s));
+        }
         if (l < L) {
+            ProfScope pss("a7.fw_sibling", s);
+            pss.flops = 8.0 * C.sum_s2 * nc;
             FDS_TRY(apply_S<T>(h, C, xl, C.D, yl, C.D, nc, s));
             fl += 8.0 * (C.sum_tm + C.sum_s2) * nc;
         } else {
+            ProfScope pd("a7.fw_leaf_diag", s);
+            pd.flops = 8.0 * level_d2(C) * nc;
             fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, yl, C.d_doff.p, nc, C.D, rY);
             fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, xl, C.d_doff.p, nc, C.D, rZ);
             FDS_CUDA_TRY(cudaGetLastError());
