@@ -435,8 +435,8 @@ def main():
     # kernels, from ncu counters (dfma x 2 + dmul + dadd; dram read + write)
     # over all launches of one 2^14-node build of the same cavity
     # (profiles/k_tiles_fp64_ops_star_2p14.md)
-    A1_PER_POINT = {"a1.leaf_blocks": (568.0, 0.72), "a1.near_rows": (687.0, 1.53), "a1.proxy_rows": (687.0, 1.53),
-                    "a1.sibling_blocks": (681.0, 0.19), "a1.top_blocks": (681.0, 0.19)}
+    A1_PER_POINT = {"a1.leaf_blocks": (534.0, 0.72), "a1.near_rows": (552.0, 1.52), "a1.proxy_rows": (552.0, 1.52),
+                    "a1.sibling_blocks": (578.0, 0.18), "a1.top_blocks": (578.0, 0.18)}
     pk, src = peaks()
     sm_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     # FP64 peak of the GB300: 152 SMs x 2 FP64 FMA/clk (4 flops) x SM clock

@@ -117,7 +117,8 @@ struct ArithFF {
 
 // Operands already held as float pairs (float4 = re_hi, im_hi, re_lo, im_lo):
 // the constant operators are split once, the vectors stay split, so no FP64
-// instruction is issued.  alpha = 1 or -1 (sign of alpha.x); beta = 0 or 1.
+// instruction is issued (ArithFFP3 below).  alpha = 1 or -1 (sign of
+// alpha.x); beta = 0 or 1.
 __device__ __forceinline__ ff ff_norm(ff a) {
     const float h = a.h + a.l;
     return ff{h, a.l - (h - a.h)};
@@ -127,33 +128,6 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
     two_sum(a.h, b.h, s, e);
     return ff_norm(ff{s, e + (a.l + b.l)});
 }
-
-struct ArithFFP {
-    typedef float4 G;
-    typedef ArithFF::SA SA;
-    typedef ArithFF::SB SB;
-    typedef ArithFF::Acc Acc;
-    __device__ static SA stage_a(G v, bool cj) {
-        return cj ? SA{ff{v.x, v.z}, ff{-v.y, -v.w}} : SA{ff{v.x, v.z}, ff{v.y, v.w}};
-    }
-    __device__ static SB stage_b(G v) { return SB{ff{v.x, v.z}, ff{v.y, v.w}}; }
-    __device__ static SA za() { return ArithFF::za(); }
-    __device__ static SB zb() { return ArithFF::zb(); }
-    __device__ static void zero(Acc &a) { ArithFF::zero(a); }
-    __device__ static void mac(Acc &c, const SA &a, const SB &b) { ArithFF::mac(c, a, b); }
-    __device__ static G finish(const Acc &c, G alpha, G, const G *old) {
-        ff re = ff_norm(c.re), im = ff_norm(c.im);
-        if (alpha.x < 0.f) {   // alpha = -1
-            re = ff{-re.h, -re.l};
-            im = ff{-im.h, -im.l};
-        }
-        if (old) {
-            re = ff_add(re, ff{old->x, old->z});
-            im = ff_add(im, ff{old->y, old->w});
-        }
-        return make_float4(re.h, im.h, re.l, im.l);
-    }
-};
 
 // Float-pair operands with Gauss's three-product complex multiply:
 //   (a + i b)(c + i d) = (k1 - k3) + i (k1 + k2),
