@@ -58,16 +58,19 @@ def parse():
     p.add_argument("--sweep-fp64-levels", type=int, default=-1)
     p.add_argument("--merge-c64", action="store_true", help="merge the complex64 levels in complex64")
     p.add_argument("--c64-engine", default="simt", choices=["tensor", "simt"],
-                   help="complex64 products on the tensor cores (3xTF32) or the FP32 pipe")
+                   help="complex64 products on the tensor cores (bf16 pieces) or the FP32 pipe")
     p.add_argument("--sweep-ff", type=int, default=1, choices=[0, 1, 2],
                    help="mixed sweep: 1 double-float upper levels, 2 double-float everywhere")
     p.add_argument("--rank", default="adaptive", choices=["learned", "adaptive"],
                    help="learned: the trained rank network (falls back to adaptive if it has not been trained); "
                         "its skeletons differ from the plain solver's, so its error against the plain FP64 "
                         "solve is the compression error amplified by the operator's conditioning")
-    p.add_argument("--workload", default="star", choices=["star", "batch64"],
+    p.add_argument("--workload", default="star", choices=["star", "batch64", "cgemm"],
                    help="star: the 2^19-node star cavity (default); batch64: 64 seeded cavities of "
-                        "2^12-2^15 nodes, k_T a in [1, 20], 16 waves each, built and solved as one batch")
+                        "2^12-2^15 nodes, k_T a in [1, 20], 16 waves each, built and solved as one batch; "
+                        "cgemm: the batched complex64 GEMM stage alone (--gemm-batch products of "
+                        "128 x 128 by 128 x --nrhs, the leaf shape of the sweep) on both engines")
+    p.add_argument("--gemm-batch", type=int, default=8192, help="cgemm: number of products")
     p.add_argument("--streams", type=int, default=8, help="batch64: concurrent cavity streams")
     p.add_argument("--no-compare", action="store_true",
                    help="skip the plain-FP64 comparison step (error and timings of the FP64 solver)")
@@ -220,6 +223,51 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- batched cavities
+def run_cgemm(args, fds, torch, rank):
+    """Stage benchmark of the batched complex64 GEMM: nb products of
+    128 x 128 by 128 x n (seeded normal entries), each engine timed with CUDA
+    events over --steps calls after --warmup, and its normwise error on eight
+    products against the complex128 product of the same inputs."""
+    import numpy as np
+    nb, d, n = args.gemm_batch, 128, args.nrhs
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1 + rank)
+    A = torch.randn(nb * d * d * 2, device="cuda", generator=g)
+    B = torch.randn(nb * d * n * 2, device="cuda", generator=g)
+    aoff = np.arange(nb, dtype=np.int64) * d * d
+    boff = np.arange(nb, dtype=np.int64) * d * n
+    out = {}
+    for name, eng in (("tensor", fds.FDS_C64_TENSOR), ("simt", fds.FDS_C64_SIMT)):
+        C = torch.zeros(nb * d * n * 2, device="cuda")
+        call = lambda: fds.fds_cgemm_c64_batched([d] * nb, [n] * nb, [d] * nb, aoff, boff, boff, A, B, C,
+                                                 engine=eng)
+        for _ in range(args.warmup):
+            call()
+        ts = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            call()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        Ah, Bh, Ch = A.view(-1, 2).cpu().numpy(), B.view(-1, 2).cpu().numpy(), C.view(-1, 2).cpu().numpy()
+        err = 0.0
+        for b in range(0, nb, max(1, nb // 8)):
+            cp = lambda X, o, r, c: (X[o:o + r * c, 0] + 1j * X[o:o + r * c, 1]).reshape(c, r).T
+            a = cp(Ah, b * d * d, d, d).astype(np.complex128)
+            x = cp(Bh, b * d * n, d, n).astype(np.complex128)
+            ref = a @ x
+            got = cp(Ch, b * d * n, d, n)
+            err = max(err, float(np.max(np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0))))
+        ms = float(np.median(ts))
+        out[name] = {"ms": ms, "tflops_complex": 8.0 * nb * d * d * n / ms / 1e9, "max_rel_err": err}
+    if rank == 0:
+        print(json.dumps({"workload": "cgemm %d x (128 x 128) x (128 x %d) complex64" % (nb, n),
+                          "steps": args.steps, "warmup": args.warmup, "engines": out}))
+
+
 def run_batch(args, fds, torch, world, rank, local):
     """64 seeded cavities (ellipses / stars, 2^12..2^15 nodes, k_T a in [1, 20],
     eps 1e-8, leaf 64) built with fds_build_batch on --streams concurrent
@@ -300,6 +348,9 @@ def main():
     from paper_2411_18026_gb300 import fds
     if args.workload == "batch64":
         run_batch(args, fds, torch, world, rank, local)
+        return
+    if args.workload == "cgemm":
+        run_cgemm(args, fds, torch, rank)
         return
 
     xy, omega, kinds, angles = workload(args, rank)
