@@ -179,8 +179,9 @@ __device__ __forceinline__ Elem load_elem(const double *__restrict__ xy, int N, 
 
 enum PairKind {
     PK_SELF = 0, PK_ADJ_NEXT = 1, PK_ADJ_PREV = 2, PK_NEAR = 3, PK_MID = 4, PK_FAR = 5, PK_FAR2 = 6, PK_CROSS = 7,
-    PK_FAR3 = 8
+    PK_FAR3 = 8, PK_SKIP = 9    // PK_SKIP: a pair a diagonal tile leaves out
 };
+constexpr int PK_N = 10;
 
 __device__ __forceinline__ int pair_kind(const Elem &E, const Elem &F, int ie, int jf, int N, double kT) {
     if (ie == jf) return PK_SELF;
@@ -190,12 +191,13 @@ __device__ __forceinline__ int pair_kind(const Elem &E, const Elem &F, int ie, i
     if (ie == jn) return PK_ADJ_PREV;
     double mx = E.a.x + 0.5 * E.h * E.t.x - (F.a.x + 0.5 * F.h * F.t.x);
     double my = E.a.y + 0.5 * E.h * E.t.y - (F.a.y + 0.5 * F.h * F.t.y);
-    double d = sqrt(mx * mx + my * my);
-    double L = fmax(E.h, F.h);
-    if (d >= 24.0 * L && kT * L <= 0.02) return PK_FAR3;
-    if (d >= 12.0 * L) return PK_FAR2;
-    if (d >= 6.0 * L) return PK_FAR;
-    if (d >= 2.5 * L) return PK_MID;
+    // midpoint distance d against multiples of L, compared as squares
+    const double d2 = mx * mx + my * my;
+    const double L = fmax(E.h, F.h), L2 = L * L;
+    if (d2 >= 576.0 * L2 && kT * L <= 0.02) return PK_FAR3;   // d >= 24 L
+    if (d2 >= 144.0 * L2) return PK_FAR2;                      // d >= 12 L
+    if (d2 >= 36.0 * L2) return PK_FAR;                        // d >= 6 L
+    if (d2 >= 6.25 * L2) return PK_MID;                        // d >= 2.5 L
     return PK_NEAR;
 }
 
@@ -550,6 +552,11 @@ struct TileSmem {
     Rules G;
     TileSide R, C;
     Elem eR[TILE_EL], eC[TILE_EL];        // geometry of the tile's elements
+    // the tile's element pairs grouped by rule: cheap rules first (costliest
+    // first), then the singular ones; pk[q] = rule of pair q
+    unsigned short plist[TILE_EL * TILE_EL];
+    unsigned char pk[TILE_EL * TILE_EL];
+    int kcount[PK_N], kstart[PK_N], ncheap, ncostly;
     double ef[TILE][TILE][2][2][2];   // forward entries  [row][col][i][j][re/im]
     double er[TILE][TILE][2][2][2];   // transposed entries [col][row][i][j][re/im]
 };
@@ -668,15 +675,45 @@ static __device__ void tile_eval(const PhysDev &P, TileSmem &S, const double *__
         }
     }
     __syncthreads();
-    // pass 1: cheap pairs, one per thread
+    // classify the pairs and group them by rule (counting sort), so that the
+    // threads of a warp integrate pairs with the same number of points
+    for (int k = threadIdx.x; k < PK_N; k += blockDim.x) S.kcount[k] = 0;
+    __syncthreads();
     for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
         const int re = q / S.C.ne, ce = q - re * S.C.ne;
         const int ie = S.R.el[re], jf = S.C.el[ce];
-        if (diag && ie > jf) continue;
+        int kind = PK_SKIP;
+        if (!(diag && ie > jf)) kind = same ? pair_kind(S.eR[re], S.eC[ce], ie, jf, NX, P.kT) : PK_CROSS;
+        S.pk[q] = (unsigned char)kind;
+        atomicAdd(&S.kcount[kind], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // order: mid, far, far2, far3, cross (cheap, costliest first), then self, adjacent, near
+        const int ord[PK_N] = {PK_MID, PK_FAR, PK_FAR2, PK_FAR3, PK_CROSS, PK_SELF, PK_ADJ_NEXT, PK_ADJ_PREV,
+                               PK_NEAR, PK_SKIP};
+        int pos = 0;
+        for (int o = 0; o < PK_N; ++o) {
+            S.kstart[ord[o]] = pos;
+            pos += S.kcount[ord[o]];
+            if (o == 4) S.ncheap = pos;
+            if (o == 8) S.ncostly = pos - S.ncheap;
+            S.kcount[ord[o]] = 0;
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
+        const int kind = S.pk[q];
+        S.plist[S.kstart[kind] + atomicAdd(&S.kcount[kind], 1)] = (unsigned short)q;
+    }
+    __syncthreads();
+    // pass 1: cheap pairs, one per thread
+    for (int idx = threadIdx.x; idx < S.ncheap; idx += blockDim.x) {
+        const int q = S.plist[idx];
+        const int re = q / S.C.ne, ce = q - re * S.C.ne;
         const Elem E = S.eR[re];
         const Elem F = S.eC[ce];
-        const int kind = same ? pair_kind(E, F, ie, jf, NX, P.kT) : PK_CROSS;
-        if (!cheap_kind(kind)) continue;
+        const int kind = S.pk[q];
         const int mA = (S.R.pos[re][0] >= 0 ? 1 : 0) | (S.R.pos[re][1] >= 0 ? 2 : 0);
         const int mB = (S.C.pos[ce][0] >= 0 ? 1 : 0) | (S.C.pos[ce][1] >= 0 ? 2 : 0);
         if (dual || diag) {
@@ -695,14 +732,13 @@ static __device__ void tile_eval(const PhysDev &P, TileSmem &S, const double *__
         }
     }
     // pass 2: singular / near-singular pairs, one per warp
-    for (int q = warp; q < npairs; q += nw) {
+    for (int idx = warp; idx < S.ncostly; idx += nw) {
+        const int q = S.plist[S.ncheap + idx];
         const int re = q / S.C.ne, ce = q - re * S.C.ne;
         const int ie = S.R.el[re], jf = S.C.el[ce];
-        if (diag && ie > jf) continue;
         const Elem E = S.eR[re];
         const Elem F = S.eC[ce];
-        const int kind = same ? pair_kind(E, F, ie, jf, NX, P.kT) : PK_CROSS;
-        if (cheap_kind(kind)) continue;
+        const int kind = S.pk[q];
         const int mA = (S.R.pos[re][0] >= 0 ? 1 : 0) | (S.R.pos[re][1] >= 0 ? 2 : 0);
         const int mB = (S.C.pos[ce][0] >= 0 ? 1 : 0) | (S.C.pos[ce][1] >= 0 ? 2 : 0);
         // a self pair in a diagonal tile: its transposed entries are forward entries too
