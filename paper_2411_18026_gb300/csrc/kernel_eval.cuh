@@ -78,8 +78,9 @@ __device__ __forceinline__ void load_rules(Rules &R, int qcross) {
 //   Y0 = (2/pi) [ (ln(z/2) + g) J0 - sum_{m>=1} H_m q^m/(m!)^2 ],
 //   Im E = (2/pi) ln(z/2) J1/z - (1/(2 pi)) sum (2 (H_m - g) + 1/(m+1)) q^m/(m!(m+1)!),
 //   Y1 = z Im E - 2/(pi z).
-// 14 terms reach 1e-16 for z < 2, 8 for z < 0.63 and 6 for z < 0.2 (the
-// tails are below 1e-17 of the leading terms).  For z >= 2 from CUDA's
+// 14 terms reach 1e-16 for z < 2, 8 for z < 0.63, 6 for z < 0.2, 4 for
+// z < 0.02 and 3 for z < 0.002 (the tails are below 1e-17 of the leading
+// terms).  For z >= 2 from CUDA's
 // j0/y0/j1/y1.
 struct Hk {
     cplx h0, h1, e;
@@ -109,8 +110,11 @@ __device__ __forceinline__ Hk hankel_k(const Rules &G, double z, double lhalf) {
         const double g = 0.57721566490153286061;
         const double q = -0.25 * z * z;
         double J0, Su, SH, Sp;
-        // terms needed for 1e-17 relative: 6 below z = 0.2, 8 below z = 0.63
-        if (q > -0.01) series4<6>(G, q, J0, Su, SH, Sp);
+        // terms needed for 1e-17 relative: 3 below z = 0.002, 4 below 0.02,
+        // 6 below 0.2, 8 below 0.63
+        if (q > -1e-6) series4<3>(G, q, J0, Su, SH, Sp);
+        else if (q > -1e-4) series4<4>(G, q, J0, Su, SH, Sp);
+        else if (q > -0.01) series4<6>(G, q, J0, Su, SH, Sp);
         else if (q > -0.1) series4<8>(G, q, J0, Su, SH, Sp);
         else series4<SER_TERMS>(G, q, J0, Su, SH, Sp);
         const double j1z = 0.5 * Su;                      // J1(z)/z
@@ -139,7 +143,8 @@ struct Radial {
 };
 
 __device__ __forceinline__ Radial radial(const PhysDev &P, const Rules &G, double r) {
-    const double lr = log(r);
+    // ln r enters the series branch only (z < 2; k_L < k_T)
+    const double lr = (P.kL * r < 2.0) ? log(r) : 0.0;
     const Hk T = hankel_k(G, P.kT * r, P.lhalfT + lr);
     const Hk L = hankel_k(G, P.kL * r, P.lhalfL + lr);
     Radial R;
@@ -412,11 +417,15 @@ __device__ __forceinline__ void accum_orient(double (&acc)[NV], const cplx k0[2]
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const cplx k3 = (i == j) ? (i == 0 ? Q.k3_00 : Q.k3_11) : Q.k3_01;
+            // ns = (1 - ns[1], ns[1]) and ds = (-ds[1], ds[1]): the U = 0 terms
+            // are the U = 1 ones subtracted from k0 and k2
+            const cplx u1 = cadd(cscale(k0[i][j], ns[1]), cscale(k1[i][j], ds[1]));
+            const cplx v1 = cadd(cscale(k2[i][j], ns[1]), cscale(k3, ds[1]));
 #pragma unroll
             for (int U = 0; U < 2; ++U) {
                 if (!(ms & (1 << U))) continue;
-                const cplx u = cadd(cscale(k0[i][j], ns[U]), cscale(k1[i][j], ds[U]));
-                const cplx v = cadd(cscale(k2[i][j], ns[U]), cscale(k3, ds[U]));
+                const cplx u = U ? u1 : csub(k0[i][j], u1);
+                const cplx v = U ? v1 : csub(k2[i][j], v1);
 #pragma unroll
                 for (int T = 0; T < 2; ++T) {
                     if (!(mt & (1 << T))) continue;
