@@ -1163,13 +1163,30 @@ int fds_build_impl(fds_handle *h) {
         {
             ProfScope ps("a4.top_lu", s);
             ps.flops = 8.0 / 3.0 * (double)h->Dtop * h->Dtop * h->Dtop;
-            FDS_TRY(dense_lu(1, (int)h->Dtop, h->rtop.p, h->ptop.p, h->d_ptop_off.p, h->d_info.p, s));
+            if (h->Dtop > 128)
+                FDS_TRY(dense_lu_blocked((int)h->Dtop, h->Atop.p, top.ld, h->ptop.p, h->d_info.p, s));
+            else
+                FDS_TRY(dense_lu(1, (int)h->Dtop, h->rtop.p, h->ptop.p, h->d_ptop_off.p, h->d_info.p, s));
         }
         std::vector<int> hinfo;
         FDS_TRY(d2h(hinfo, h->d_info.p, 1, s));
         FDS_TRY(sync_check(s));
         if (hinfo[0]) return FDS_ERR_SINGULAR;
-        h->factor_bytes += (int64_t)(h->Atop.bytes() + h->ptop.bytes());
+        // A_top^{-1} from the LU, so that each top solve of the sweep is one GEMM
+        {
+            ProfScope ps("a4.top_inverse", s);
+            ps.flops = 8.0 * (double)h->Dtop * h->Dtop * h->Dtop;
+            FDS_TRY(h->Atop_inv.alloc((size_t)h->Dtop * h->Dtop));
+            MatRef inv = top;
+            inv.p = h->Atop_inv.p;
+            std::vector<MatRef> hi = {inv};
+            FDS_TRY(h->rtop_inv.upload(hi, s));
+            fds_count_launch(), k_set_identity<cplx><<<1, 256, 0, s>>>(h->rtop_inv.p);
+            FDS_CUDA_TRY(cudaGetLastError());
+            FDS_TRY(dense_lu_solve(1, (int)h->Dtop, (int)h->Dtop, h->rtop.p, h->ptop.p, h->d_ptop_off.p,
+                                   h->rtop_inv.p, s));
+        }
+        h->factor_bytes += (int64_t)(h->Atop.bytes() + h->ptop.bytes() + h->Atop_inv.bytes());
         // the top level's per-cell A blocks are no longer needed
         if (h->l0 < L || T.nb > 0) {
             T.LU.release();

@@ -1,7 +1,9 @@
 // Batched complex128 LU / LU-solve / GEMM kernels (one CTA per matrix or
 // per output tile).  FP64 throughout.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "dense.cuh"
 #include "fds_internal.cuh"
@@ -84,6 +86,80 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu(const MatRefT<C> *__restrict_
         __syncthreads();
     }
     if (threadIdx.x == 0) info[blockIdx.x] = s_bad;
+}
+
+// Blocked LU of one large matrix (the top system): panel kernel on columns
+// k0 .. k0+nb-1 (pivot search in the panel column over rows k.., row swap
+// across all n columns, scaling, update of the panel's remaining columns),
+// then the block row U12 = L11^{-1} A12 (one thread per column) and the
+// trailing update A22 -= L21 U12 as a register-tiled GEMM over many CTAs.
+template <class C>
+__global__ void __launch_bounds__(LU_THREADS) k_lu_panel(C *A, int n, int ld, int k0, int nb, int *pv,
+                                                         int *info) {
+    __shared__ double s_val[LU_THREADS];
+    __shared__ int s_idx[LU_THREADS];
+    __shared__ int s_piv;
+    for (int k = k0; k < k0 + nb; ++k) {
+        double best = -1.0;
+        int bi = n;
+        for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+            const double v = cabs2(A[i + (long)k * ld]);
+            if (v > best) { best = v; bi = i; }
+        }
+        s_val[threadIdx.x] = best;
+        s_idx[threadIdx.x] = bi;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                const double v2 = s_val[threadIdx.x + o];
+                const int i2 = s_idx[threadIdx.x + o];
+                if (v2 > s_val[threadIdx.x] || (v2 == s_val[threadIdx.x] && i2 < s_idx[threadIdx.x])) {
+                    s_val[threadIdx.x] = v2;
+                    s_idx[threadIdx.x] = i2;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            int p = s_idx[0];
+            if (p >= n) p = k;
+            s_piv = p;
+            pv[k] = p;
+            const C d = A[p + (long)k * ld];
+            if ((!(s_val[0] > 0.0) || !finite_c(d)) && *info == 0) *info = k + 1;
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p != k) {
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                const C t = A[k + (long)j * ld];
+                A[k + (long)j * ld] = A[p + (long)j * ld];
+                A[p + (long)j * ld] = t;
+            }
+        }
+        __syncthreads();
+        const C d = A[k + (long)k * ld];
+        const C dinv = (cabs2(d) > 0) ? cinv(d) : czero<C>();
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (long)k * ld] = cmul(A[i + (long)k * ld], dinv);
+        __syncthreads();
+        const int m = n - k - 1, w = k0 + nb - k - 1;   // rows below, panel columns right of k
+        for (long e = threadIdx.x; e < (long)m * w; e += blockDim.x) {
+            const int i = k + 1 + (int)(e % m), j = k + 1 + (int)(e / m);
+            cfms(A[i + (long)j * ld], A[i + (long)k * ld], A[k + (long)j * ld]);
+        }
+        __syncthreads();
+    }
+}
+
+template <class C>
+__global__ void k_trsm_l11(C *A, int n, int ld, int k0, int nb) {
+    const int j = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    for (int i = k0 + 1; i < k0 + nb; ++i) {
+        C acc = A[i + (long)j * ld];
+        for (int t = k0; t < i; ++t) cfms(acc, A[i + (long)t * ld], A[t + (long)j * ld]);
+        A[i + (long)j * ld] = acc;
+    }
 }
 
 // Multi-RHS LU solve: CTA per (matrix, tile of RT right-hand sides).  The RHS
@@ -209,6 +285,47 @@ int dense_lu(int batch, int max_n, const MatRefF *d_A, int *d_piv, const int64_t
     (void)max_n;
     fds_count_launch(), k_lu<cplxf><<<batch, LU_THREADS, 0, s>>>(d_A, d_piv, d_poff, d_info);
     FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
+}
+
+int dense_lu_blocked(int n, cplx *A, int ld, int *d_piv, int *d_info, cudaStream_t s) {
+    if (n <= 0) return FDS_OK;
+    constexpr int NB = 32;
+    FDS_CUDA_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
+    std::vector<MatRef> refs;
+    for (int k0 = 0; k0 < n; k0 += NB) {
+        const int nb = std::min(NB, n - k0), r = n - k0 - nb;
+        MatRef L21, U12, A22;
+        L21.p = A + (k0 + nb) + (int64_t)k0 * ld;
+        L21.rows = r;
+        L21.cols = nb;
+        L21.ld = ld;
+        U12.p = A + k0 + (int64_t)(k0 + nb) * ld;
+        U12.rows = nb;
+        U12.cols = r;
+        U12.ld = ld;
+        A22.p = A + (k0 + nb) + (int64_t)(k0 + nb) * ld;
+        A22.rows = r;
+        A22.cols = r;
+        A22.ld = ld;
+        refs.push_back(L21);
+        refs.push_back(U12);
+        refs.push_back(A22);
+    }
+    DBuf<MatRef> d_refs;
+    FDS_TRY(d_refs.upload(refs, s));
+    int panel = 0;
+    for (int k0 = 0; k0 < n; k0 += NB, ++panel) {
+        const int nb = std::min(NB, n - k0), r = n - k0 - nb;
+        fds_count_launch(), k_lu_panel<cplx><<<1, LU_THREADS, 0, s>>>(A, n, ld, k0, nb, d_piv, d_info);
+        FDS_CUDA_TRY(cudaGetLastError());
+        if (r == 0) break;
+        fds_count_launch(), k_trsm_l11<cplx><<<(r + 127) / 128, 128, 0, s>>>(A, n, ld, k0, nb);
+        FDS_CUDA_TRY(cudaGetLastError());
+        const MatRef *R = d_refs.p + 3 * panel;
+        FDS_TRY(dense_gemm_rt(1, r, r, R, 0, R + 1, R + 2, mkc(-1.0, 0.0), mkc(1.0, 0.0), s));
+    }
+    FDS_CUDA_TRY(cudaStreamSynchronize(s));   // the descriptors die with this call
     return FDS_OK;
 }
 

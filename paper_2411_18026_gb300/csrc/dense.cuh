@@ -62,6 +62,10 @@ int dense_gemm_map(int batch, int max_m, int max_n, const MatRefP *d_A, int opA,
 // alpha, beta; opA 0 or 2; optional row maps.
 int dense_gemm_tc(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, const MatRefF *d_B,
                   const MatRefF *d_C, float alpha, float beta, const RowMaps *d_maps, cudaStream_t s);
+// LU with partial pivoting of one n x n matrix A (leading dimension ld) in
+// 32-column panels, the trailing updates as GEMMs (the top system); pivots in
+// d_piv[0..n), d_info as for dense_lu.  Synchronises s.
+int dense_lu_blocked(int n, cplx *A, int ld, int *d_piv, int *d_info, cudaStream_t s);
 // Reads and clears the tensor-core timeout status (synchronises s).
 int tc_status_take(cudaStream_t s, int *status);
 // complex64 versions (mixed-precision merge and sweep)

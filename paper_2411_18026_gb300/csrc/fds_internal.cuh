@@ -177,6 +177,8 @@ struct fds_handle {
     DBuf<cplx> Atop;
     DBuf<int> ptop;
     DBuf<MatRef> rtop;
+    DBuf<cplx> Atop_inv;         // A_top^{-1} (the sweep's top solve is one GEMM)
+    DBuf<MatRef> rtop_inv;
     DBuf<int64_t> d_ptop_off;
     DBuf<int> d_info;
     // mixed precision: off-diagonal top blocks (FP64 forward operator)
@@ -188,6 +190,7 @@ struct fds_handle {
     std::vector<DBuf<cplx>> wz, wf, wt, wy, wr;
     std::vector<DBuf<cplxf>> wzf, wff, wtf, wrf;
     DBuf<cplx> wtop, wytop, wX;
+    DBuf<cplx> wtop2;                 // output of the top solve's GEMM
     DBuf<cplxf> wtopf;   // complex64 top vector (boundary of the mixed sweep)
     std::vector<DBuf<float4>> wzq, wfq, wtq, wrq;   // float-pair sweep vectors
     DBuf<float4> wtopq;

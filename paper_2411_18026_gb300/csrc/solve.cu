@@ -184,7 +184,7 @@ int workspace_levels(fds_handle *h, int ncmax, int lo, int hi, bool top) {
     }
     if (top) FDS_TRY(grow(Vw::wtop(h), (size_t)std::max<int64_t>(h->Dtop, 1) * ncmax));
     const int maxnb = fds_max_cells(h);
-    if (Vw::refs(h).n < (size_t)4 * maxnb) FDS_TRY(Vw::refs(h).alloc((size_t)4 * maxnb));
+    if (Vw::refs(h).n < (size_t)4 * maxnb + 2) FDS_TRY(Vw::refs(h).alloc((size_t)4 * maxnb + 2));
     return FDS_OK;
 }
 
@@ -204,6 +204,7 @@ int workspace_prec(fds_handle *h, int ncmax, int prec) {
 
 int sweep_workspace(fds_handle *h, int ncmax) {
     FDS_TRY(workspace_prec<cplx>(h, ncmax, PREC_C128));
+    FDS_TRY(grow(h->wtop2, (size_t)std::max<int64_t>(h->Dtop, 1) * ncmax));
     if (h->opt.precision == FDS_MIXED) {
         FDS_TRY(workspace_prec<cplxf>(h, ncmax, PREC_C64));
         if (h->opt.sweep_ff) FDS_TRY(workspace_prec<float4>(h, ncmax, PREC_FF));
@@ -334,19 +335,25 @@ int down_level(fds_handle *h, int l, int nc, cudaStream_t s) {
 }
 
 
+// x_top = A_top^{-1} f_top (Sec. 6.3) as one GEMM with the inverse formed at build
 int top_solve(fds_handle *h, int nc, cudaStream_t s) {
     const int64_t ldt = std::max<int64_t>(h->Dtop, 1);
-    MatRef tv;
-    tv.p = h->wtop.p;
-    tv.rows = (int)h->Dtop;
-    tv.cols = nc;
-    tv.ld = (int)ldt;
+    MatRef tv[2];
+    tv[0].p = h->wtop.p;
+    tv[1].p = h->wtop2.p;
+    for (int q = 0; q < 2; ++q) {
+        tv[q].rows = (int)h->Dtop;
+        tv[q].cols = nc;
+        tv[q].ld = (int)ldt;
+    }
     MatRef *rX = h->wrefs.p + 3 * fds_max_cells(h);
-    FDS_CUDA_TRY(cudaMemcpyAsync(rX, &tv, sizeof(tv), cudaMemcpyHostToDevice, s));
+    FDS_CUDA_TRY(cudaMemcpyAsync(rX, tv, sizeof(tv), cudaMemcpyHostToDevice, s));
     ProfScope ps("a6.top_solve", s);
     ps.flops = 8.0 * (double)h->Dtop * h->Dtop * nc;
     ps.bytes = 16.0 * (double)h->Dtop * h->Dtop;
-    return dense_lu_solve(1, (int)h->Dtop, nc, h->rtop.p, h->ptop.p, h->d_ptop_off.p, rX, s);
+    FDS_TRY(dense_gemm(1, (int)h->Dtop, nc, h->rtop_inv.p, 0, rX, 0, rX + 1, mkc(1.0, 0.0), mkc(0.0, 0.0), s));
+    FDS_CUDA_TRY(cudaMemcpyAsync(h->wtop.p, h->wtop2.p, sizeof(cplx) * ldt * nc, cudaMemcpyDeviceToDevice, s));
+    return FDS_OK;
 }
 
 }  // namespace
