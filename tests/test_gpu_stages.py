@@ -166,3 +166,19 @@ def test_rhs_coarse_elements_matches_oracle():
         ref = bem.rhs(P, xy, int(kinds[j]), float(angles[j]))
         assert np.abs(got[:, j] - ref).max() <= 1e-13 * np.abs(ref).max()
     h.close()
+
+
+def test_rhs_fine_elements_series_branch_matches_oracle():
+    # k h ~ 1e-2: the closed-form Taylor integrals of the phase; 5 waves cover
+    # a partial group of the kernel's waves per block
+    fds = fdslib()
+    torch_cuda()
+    xy = workloads.star(4096)
+    h = fds.fds_build(xy, 5.0, 2.0, 1.0, 1e-6, leaf_size=64)
+    kinds, angles = np.array([0, 1, 1, 0, 1], np.int32), np.array([0.0, 0.4, 2.5, 4.0, 5.9])
+    got = fds.fds_rhs_plane_wave(h, kinds, angles)
+    P = bem.phys(2.0, 1.0, 1.0, 5.0)
+    for j in range(len(kinds)):
+        ref = bem.rhs(P, xy, int(kinds[j]), float(angles[j]))
+        assert np.abs(got[:, j] - ref).max() <= 1e-13 * np.abs(ref).max()
+    h.close()
