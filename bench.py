@@ -486,8 +486,8 @@ def main():
     # kernels, from ncu counters (dfma x 2 + dmul + dadd; dram read + write)
     # over all launches of one 2^14-node build of the same cavity
     # (profiles/k_tiles_fp64_ops_star_2p14.md)
-    A1_PER_POINT = {"a1.leaf_blocks": (534.0, 0.72), "a1.near_rows": (552.0, 1.52), "a1.proxy_rows": (552.0, 1.52),
-                    "a1.sibling_blocks": (578.0, 0.18), "a1.top_blocks": (578.0, 0.18)}
+    A1_PER_POINT = {"a1.leaf_blocks": (475.0, 0.66), "a1.near_rows": (493.0, 1.54), "a1.proxy_rows": (493.0, 1.54),
+                    "a1.sibling_blocks": (509.0, 0.18), "a1.top_blocks": (509.0, 0.18)}
     pk, src = peaks()
     sm_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     # FP64 peak of the GB300: 152 SMs x 2 FP64 FMA/clk (4 flops) x SM clock

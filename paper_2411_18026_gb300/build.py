@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include")]
-# extra nvcc flags for experiments (e.g. -DFDS_DUAL_ONEPASS=1); delete libfds.so to rebuild
+# extra nvcc flags for experiments (e.g. -DFDS_FFP_TJ4=4); build(force=True) to rebuild
 FLAGS += os.environ.get("FDS_NVCC_FLAGS", "").split()
 
 

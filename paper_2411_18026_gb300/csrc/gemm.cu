@@ -20,6 +20,10 @@
 namespace {
 
 constexpr int BK = 16, NT = 256;
+// columns per thread of the float-pair kernel at 4 row groups (register budget)
+#ifndef FDS_FFP_TJ4
+#define FDS_FFP_TJ4 2
+#endif
 
 // ---------------------------------------------------------------- arithmetics
 struct Arith64 {
@@ -312,7 +316,7 @@ int dense_gemm_ff(int batch, int max_m, int max_n, const MatRef *d_A, int opA, c
 
 int dense_gemm_ffp(int batch, int max_m, int max_n, const MatRefT<float4> *d_A, int opA, const MatRefT<float4> *d_B,
                    const MatRefT<float4> *d_C, int accumulate, cudaStream_t s) {
-    return launch<ArithFFP3, 2, 3, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, make_float4(1.f, 0.f, 0.f, 0.f),
+    return launch<ArithFFP3, FDS_FFP_TJ4, 3, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, make_float4(1.f, 0.f, 0.f, 0.f),
                                 make_float4(accumulate ? 1.f : 0.f, 0.f, 0.f, 0.f), s);
 }
 
@@ -330,12 +334,12 @@ int dense_gemm_map(int batch, int max_m, int max_n, const MatRefF *d_A, int opA,
 }
 int dense_gemm_map(int batch, int max_m, int max_n, const MatRefP *d_A, int opA, const MatRefP *d_B,
                    const MatRefP *d_C, const RowMaps *d_maps, int accumulate, cudaStream_t s) {
-    return launch<ArithFFP3, 2, 3, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, make_float4(1.f, 0.f, 0.f, 0.f),
+    return launch<ArithFFP3, FDS_FFP_TJ4, 3, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, make_float4(1.f, 0.f, 0.f, 0.f),
                                 make_float4(accumulate ? 1.f : 0.f, 0.f, 0.f, 0.f), s, d_maps);
 }
 
 int dense_gemm(int batch, int max_m, int max_n, const MatRefP *d_A, int opA, const MatRefP *d_B, int opB,
                const MatRefP *d_C, float4 alpha, float4 beta, cudaStream_t s) {
     if (opB != 0) return FDS_ERR_ARG;
-    return launch<ArithFFP3, 2, 3, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
+    return launch<ArithFFP3, FDS_FFP_TJ4, 3, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
 }
