@@ -170,20 +170,75 @@ extern "C" int fds_solve_device(fds_handle *h, double *d_rhs, int32_t nrhs, uint
     return fds_solve_impl(h, (cplx *)d_rhs, nrhs, (cudaStream_t)stream);
 }
 
+// Host buffers: column chunks of the right-hand sides stream through two
+// device buffers; the copies of the next chunk in and of the previous chunk
+// out run on a second stream while the handle's stream solves the current
+// chunk (they overlap when the host memory is page-locked).
+namespace {
+constexpr int SOLVE_CHUNK_HOST = 256;   // right-hand sides per host-buffer chunk
+struct CopyPipe {
+    cudaStream_t c = nullptr;
+    cudaEvent_t in[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr};
+    ~CopyPipe() {
+        if (c) cudaStreamSynchronize(c);
+        for (int q = 0; q < 2; ++q) {
+            if (in[q]) cudaEventDestroy(in[q]);
+            if (done[q]) cudaEventDestroy(done[q]);
+        }
+        if (c) cudaStreamDestroy(c);
+    }
+};
+}  // namespace
+
 extern "C" int fds_solve(fds_handle *h, double *rhs, int32_t nrhs) {
     if (!h || nrhs < 0) return FDS_ERR_ARG;
     if (nrhs == 0) return FDS_OK;
     if (!rhs) return FDS_ERR_ARG;
     cudaStream_t s = h->stream;
-    DBuf<cplx> d;
-    const size_t bytes = sizeof(cplx) * 2 * (size_t)h->N * nrhs;
-    FDS_TRY(d.alloc((size_t)2 * h->N * nrhs));
-    FDS_CUDA_TRY(cudaMemcpyAsync(d.p, rhs, bytes, cudaMemcpyHostToDevice, s));
-    const int rc = fds_solve_impl(h, d.p, nrhs, s);
-    if (rc != FDS_OK && rc != FDS_ERR_NOT_CONVERGED) return rc;
-    FDS_CUDA_TRY(cudaMemcpyAsync(rhs, d.p, bytes, cudaMemcpyDeviceToHost, s));
-    FDS_CUDA_TRY(cudaStreamSynchronize(s));
-    return rc;
+    const int64_t ld = 2LL * h->N;
+    const int chunk = std::min<int>(nrhs, SOLVE_CHUNK_HOST);
+    const int nch = (nrhs + chunk - 1) / chunk;
+    cplx *host = reinterpret_cast<cplx *>(rhs);
+    DBuf<cplx> buf[2];
+    for (int q = 0; q < std::min(nch, 2); ++q) FDS_TRY(buf[q].alloc((size_t)ld * chunk));
+    CopyPipe P;
+    FDS_CUDA_TRY(cudaStreamCreateWithFlags(&P.c, cudaStreamNonBlocking));
+    for (int q = 0; q < 2; ++q) {
+        FDS_CUDA_TRY(cudaEventCreateWithFlags(&P.in[q], cudaEventDisableTiming));
+        FDS_CUDA_TRY(cudaEventCreateWithFlags(&P.done[q], cudaEventDisableTiming));
+    }
+    auto cols = [&](int c) { return std::min(chunk, nrhs - c * chunk); };
+    auto copy_in = [&](int c) -> int {
+        cplx *d = buf[c & 1].p;
+        FDS_CUDA_TRY(cudaMemcpyAsync(d, host + (int64_t)c * chunk * ld, sizeof(cplx) * ld * cols(c),
+                                     cudaMemcpyHostToDevice, P.c));
+        FDS_CUDA_TRY(cudaEventRecord(P.in[c & 1], P.c));
+        return FDS_OK;
+    };
+    FDS_TRY(copy_in(0));
+    if (nch > 1) FDS_TRY(copy_in(1));
+    int worst = FDS_OK, iters = 0;
+    double ms = 0, res = -1.0;
+    for (int c = 0; c < nch; ++c) {
+        const int q = c & 1;
+        FDS_CUDA_TRY(cudaStreamWaitEvent(s, P.in[q], 0));
+        const int rc = fds_solve_impl(h, buf[q].p, cols(c), s);
+        if (rc != FDS_OK && rc != FDS_ERR_NOT_CONVERGED) return rc;
+        if (rc != FDS_OK) worst = rc;
+        ms += h->solve_ms;
+        iters = std::max(iters, h->ir_iters);
+        res = std::max(res, h->ir_residual);
+        FDS_CUDA_TRY(cudaEventRecord(P.done[q], s));
+        FDS_CUDA_TRY(cudaStreamWaitEvent(P.c, P.done[q], 0));
+        FDS_CUDA_TRY(cudaMemcpyAsync(host + (int64_t)c * chunk * ld, buf[q].p, sizeof(cplx) * ld * cols(c),
+                                     cudaMemcpyDeviceToHost, P.c));
+        if (c + 2 < nch) FDS_TRY(copy_in(c + 2));
+    }
+    FDS_CUDA_TRY(cudaStreamSynchronize(P.c));
+    h->solve_ms = ms;
+    h->ir_iters = iters;
+    h->ir_residual = res;
+    return worst;
 }
 
 extern "C" int fds_stats_get(const fds_handle *h, fds_stats *st) {
