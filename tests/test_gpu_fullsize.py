@@ -1,0 +1,71 @@
+"""Parity at the benchmark's full size (2^19 nodes, 2^20 unknowns), where no
+dense oracle solve fits: the mixed solver against the plain FP64 one, the
+exact Galerkin residual of the FP64 solution on sampled rows computed by the
+oracle entry by entry, and the circle against the Pao-Mow series."""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import workloads
+from gpu_util import fdslib, torch_cuda
+from oracle import paomow
+
+pytestmark = pytest.mark.gpu
+
+N = 1 << 19
+LAM, MU, RHO = 2.0, 1.0, 1.0
+
+
+def test_fullsize_star_mixed_vs_fp64_and_sampled_residual():
+    torch = torch_cuda()
+    fds = fdslib()
+    xy = workloads.star(N)
+    omega = workloads.omega_for_kTa(20.0)
+    eps = 1e-9
+    kinds, ang = np.array([0, 1], np.int32), np.array([0.3, 2.1])
+    h64 = fds.fds_build(xy, omega, LAM, MU, eps, leaf_size=64, top_level=1)
+    F = fds.fds_rhs_plane_wave(h64, kinds, ang)
+    x64 = fds.fds_solve(h64, F)
+    h64.close()
+    hm = fds.fds_build(xy, omega, LAM, MU, eps, leaf_size=64, top_level=1, precision=fds.FDS_MIXED, ir_tol=1e-8)
+    xm = fds.fds_solve(hm, F)
+    st = fds.fds_stats_get(hm)
+    hm.close()
+    # the metric's tolerance: mixed within 1e-6 of plain FP64, per right-hand side
+    err = np.linalg.norm(xm - x64, axis=0) / np.linalg.norm(x64, axis=0)
+    assert err.max() <= 1e-6, err
+    assert st.ir_residual <= 1e-8
+    # exact residual f - A x of the FP64 solution on 4 seeded nodes (8 rows),
+    # relative to the componentwise bound |A| |x| of each row
+    nodes = np.random.default_rng(20241127).choice(N, 4, replace=False)
+    with mp.get_context("spawn").Pool(4) as pool:
+        import oracle_rows
+        res = pool.map(oracle_rows.node_rows, [(LAM, MU, RHO, omega, xy, int(s)) for s in nodes])
+    for node, A in res:
+        for c in range(2):
+            r = node + c * N
+            a = A[c]
+            for j in range(x64.shape[1]):
+                resid = abs(F[r, j] - a @ x64[:, j])
+                bound = np.abs(a) @ np.abs(x64[:, j])
+                assert resid <= 1e-7 * bound, (node, c, j, resid / bound)
+
+
+def test_fullsize_circle_matches_pao_mow():
+    torch_cuda()
+    fds = fdslib()
+    xy = workloads.circle(N)
+    omega = workloads.omega_for_kTa(20.0)
+    h = fds.fds_build(xy, omega, LAM, MU, 1e-10, leaf_size=64, top_level=1)
+    f = fds.fds_rhs_plane_wave(h, np.array([0, 1], np.int32), np.array([0.0, 0.0]))
+    x = fds.fds_solve(h, f)
+    h.close()
+    # the series on 4096 evenly spaced sampled nodes (both components)
+    idx = np.arange(0, N, N // 4096)
+    th = 2 * np.pi * idx / N
+    for j, kind in enumerate((0, 1)):
+        u1, u2 = paomow.boundary_displacement(th, 1.0, LAM, MU, RHO, omega, kind, 0.0)
+        ref = np.concatenate([u1, u2])
+        got = np.concatenate([x[idx, j], x[N + idx, j]])
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-4
