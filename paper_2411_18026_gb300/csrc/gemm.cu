@@ -24,6 +24,9 @@ constexpr int BK = 16, NT = 256;
 #ifndef FDS_FFP_TJ4
 #define FDS_FFP_TJ4 2
 #endif
+#ifndef FDS_C64_TJ4
+#define FDS_C64_TJ4 4
+#endif
 
 // ---------------------------------------------------------------- arithmetics
 struct Arith64 {
@@ -306,7 +309,7 @@ int dense_gemm_rt(int batch, int max_m, int max_n, const MatRef *d_A, int opA, c
 
 int dense_gemm_rt(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, const MatRefF *d_B,
                   const MatRefF *d_C, cplxf alpha, cplxf beta, cudaStream_t s) {
-    return launch<Arith64, 4, 4, 8>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
+    return launch<Arith64, FDS_C64_TJ4, 4, 8>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
 }
 
 int dense_gemm_ff(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, const MatRef *d_C,
@@ -329,7 +332,7 @@ int dense_gemm_map(int batch, int max_m, int max_n, const MatRefF *d_A, int opA,
                    const MatRefF *d_C, const RowMaps *d_maps, int accumulate, cudaStream_t s) {
     if (g_c64_tensor)
         return dense_gemm_tc(batch, max_m, max_n, d_A, opA, d_B, d_C, 1.f, accumulate ? 1.f : 0.f, d_maps, s);
-    return launch<Arith64, 4, 4, 8>(batch, max_m, max_n, d_A, opA, d_B, d_C, mkcf(1, 0), mkcf(accumulate ? 1 : 0, 0), s,
+    return launch<Arith64, FDS_C64_TJ4, 4, 8>(batch, max_m, max_n, d_A, opA, d_B, d_C, mkcf(1, 0), mkcf(accumulate ? 1 : 0, 0), s,
                               d_maps);
 }
 int dense_gemm_map(int batch, int max_m, int max_n, const MatRefP *d_A, int opA, const MatRefP *d_B,
