@@ -34,8 +34,9 @@ def lib():
         _lib.orc_kernel_blocks.argtypes = [P, dp, dp, dp, dp]
         _lib.orc_ehat.argtypes = [ctypes.c_double, dp]
         _lib.orc_pair.argtypes = [P, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+        _lib.orc_field.argtypes = [P, dp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_double, dp, ctypes.c_int, dp]
         for f in ("orc_entries", "orc_cross_entries", "orc_rhs", "orc_kernel_blocks", "orc_ehat",
-                  "orc_pair"):
+                  "orc_pair", "orc_field"):
             getattr(_lib, f).restype = None
     return _lib
 
@@ -95,6 +96,19 @@ def rhs(P, xy, kind, theta):
     lib().orc_rhs(ctypes.byref(P), _dp(xy), len(xy), int(kind), float(theta),
                   _dp(out.view(np.float64)))
     return out
+
+
+def field(P, xy, u, kind, theta, pts):
+    """Displacement at points off the boundary (Sec. 3, eq. (integ_rep)) from
+    the boundary solution u (2N complex) of a plane P (kind 0) or SV (kind 1)
+    wave.  pts: (npts, 2).  Returns (2, npts) complex."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.complex128)
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    out = np.zeros(2 * len(pts), dtype=np.complex128)
+    lib().orc_field(ctypes.byref(P), _dp(xy), len(xy), _dp(u.view(np.float64)), int(kind), float(theta),
+                    _dp(pts), len(pts), _dp(out.view(np.float64)))
+    return out.reshape(2, len(pts))
 
 
 def kernel_blocks(P, z, nx, ny):

@@ -11,7 +11,9 @@
  *   and the block definitions just before it), the right-hand side
  *   f = int psi (u^I + alpha T u^I)  (Sec. 4, eq. (gal)), and, for the proxy
  *   matrices of Sec. 7 (eq. (mv) and the M^U definition), entries between hats
- *   on an auxiliary polygon and hats on the boundary.
+ *   on an auxiliary polygon and hats on the boundary; and the displacement
+ *   off the boundary from the boundary solution by the integral
+ *   representation of Sec. 3, eq. (integ_rep).
  *
  * Kernel (Sec. 3, eq. (funda)): G = (1/mu) g_T I + (1/(rho w^2)) grad grad
  * (g_T - g_L) with g_k = (i/4) H0^(1)(k r).  The double-layer kernel
@@ -486,6 +488,95 @@ void orc_rhs(const orc_phys *pp, const double *xy, int N, int kind, double th, d
                 for (int i = 0; i < 2; i++)
                     out[nodes[A] + (long)i * N] += g.w[a] * E.h * Nl[A] * (u[i] + P.alpha * tr[i]);
         }
+    }
+}
+
+/*
+ * Displacement at points x off the boundary from the boundary solution u
+ * (Sec. 3, eq. (integ_rep)), for a traction-free cavity:
+ *   u_i(x) = u^I_i(x) - int_Gamma K_ij(x, y) u_j(y) ds(y),
+ *   K_ij = T^{n_y}_{jk} G_ik = lam n_j d_k G_ik + mu (n_q d_q G_ij + n_k d_j G_ik),
+ * the derivatives taken in y, with z = y - x:
+ *   G_ik(z) = i/(4 mu) [H0(k_T r) delta_ik + k_T^-2 d_i d_k (H0(k_T r) - H0(k_L r))].
+ * For a radial f(r) with D_m = (r^-1 d/dr)^m f:  d_a f = z_a D_1,
+ *   d_a d_b d_c f = (delta_ab z_c + delta_ac z_b + delta_bc z_a) D_2 + z_a z_b z_c D_3,
+ * and for f = H0(k r), D_m = (-k/r)^m H_m(k r).  u is linear on each element
+ * (P1 nodal values, component 1 at nodes 0..N-1 then component 2), 8-point
+ * Gauss per element.  u^I: the plane wave of orc_rhs (kind, th).
+ * u: 2N complex; pts: 2 npts doubles; out: 2 npts complex (component 1 at the
+ * points, then component 2).
+ */
+static void hankel0123(double x, cplx H[4])
+{
+    hankel01(x, &H[0], &H[1]);
+    H[2] = (2.0 / x) * H[1] - H[0];
+    H[3] = (4.0 / x) * H[2] - H[1];
+}
+
+void orc_field(const orc_phys *pp, const double *xy, int N, const double *u_ri, int kind, double th,
+               const double *pts, int npts, double *out_ri)
+{
+    phys_t P = make_phys(pp);
+    const cplx *u = (const cplx *)u_ri;
+    cplx *out = (cplx *)out_ri;
+    rule_t g; gauss01(8, &g);
+    const double d[2] = { cos(th), sin(th) };
+    const double dp[2] = { -d[1], d[0] };
+    const double del[2][2] = { { 1.0, 0.0 }, { 0.0, 1.0 } };
+    const cplx a = I / (4.0 * P.mu);
+    for (int p = 0; p < npts; p++) {
+        const double x[2] = { pts[2 * p], pts[2 * p + 1] };
+        cplx acc[2] = { 0.0, 0.0 };
+        for (int e = 0; e < N; e++) {
+            elem_t E; make_elem(xy, N, e, &E);
+            const int e1 = (e + 1) % N;
+            for (int q = 0; q < g.n; q++) {
+                const double sig = g.x[q];
+                const double z[2] = { E.a[0] + sig * E.h * E.t[0] - x[0], E.a[1] + sig * E.h * E.t[1] - x[1] };
+                const double r = hypot(z[0], z[1]);
+                cplx HT[4], HL[4];
+                hankel0123(P.kT * r, HT);
+                hankel0123(P.kL * r, HL);
+                cplx DT[4], DL[4];
+                for (int m = 0; m < 4; m++) {
+                    DT[m] = cpow(-P.kT / r, m) * HT[m];
+                    DL[m] = cpow(-P.kL / r, m) * HL[m];
+                }
+                /* G1[i][k][c] = d_c G_ik */
+                cplx G1[2][2][2];
+                for (int i = 0; i < 2; i++)
+                    for (int k = 0; k < 2; k++)
+                        for (int c = 0; c < 2; c++) {
+                            const double t3 = del[i][k] * z[c] + del[i][c] * z[k] + del[k][c] * z[i];
+                            const cplx d3 = t3 * (DT[2] - DL[2]) + z[i] * z[k] * z[c] * (DT[3] - DL[3]);
+                            G1[i][k][c] = a * (del[i][k] * z[c] * DT[1] + d3 / (P.kT * P.kT));
+                        }
+                const double *n = E.n;
+                cplx uy[2];
+                for (int j = 0; j < 2; j++) uy[j] = (1.0 - sig) * u[e + (long)j * N] + sig * u[e1 + (long)j * N];
+                const double w = g.w[q] * E.h;
+                for (int i = 0; i < 2; i++) {
+                    const cplx div = G1[i][0][0] + G1[i][1][1];
+                    for (int j = 0; j < 2; j++) {
+                        const cplx K = P.lam * n[j] * div + P.mu * (n[0] * G1[i][j][0] + n[1] * G1[i][j][1])
+                                       + P.mu * (n[0] * G1[i][0][j] + n[1] * G1[i][1][j]);
+                        acc[i] += w * K * uy[j];
+                    }
+                }
+            }
+        }
+        cplx uI[2];
+        if (kind == 0) {
+            const cplx ph = cexp(I * P.kL * (d[0] * x[0] + d[1] * x[1]));
+            uI[0] = d[0] * ph;
+            uI[1] = d[1] * ph;
+        } else {
+            const cplx ph = cexp(I * P.kT * (d[0] * x[0] + d[1] * x[1]));
+            uI[0] = dp[0] * ph;
+            uI[1] = dp[1] * ph;
+        }
+        out[p] = uI[0] - acc[0];
+        out[p + (long)npts] = uI[1] - acc[1];
     }
 }
 
