@@ -65,11 +65,14 @@ def parse():
                    help="learned: the trained rank network (falls back to adaptive if it has not been trained); "
                         "its skeletons differ from the plain solver's, so its error against the plain FP64 "
                         "solve is the compression error amplified by the operator's conditioning")
-    p.add_argument("--workload", default="star", choices=["star", "batch64", "cgemm"],
+    p.add_argument("--workload", default="star", choices=["star", "batch64", "cgemm", "field"],
                    help="star: the 2^19-node star cavity (default); batch64: 64 seeded cavities of "
                         "2^12-2^15 nodes, k_T a in [1, 20], 16 waves each, built and solved as one batch; "
                         "cgemm: the batched complex64 GEMM stage alone (--gemm-batch products of "
-                        "128 x 128 by 128 x --nrhs, the leaf shape of the sweep) on both engines")
+                        "128 x 128 by 128 x --nrhs, the leaf shape of the sweep) on both engines; "
+                        "field: the displacement off the boundary (eq. integ_rep) at --field-points points "
+                        "for 16 waves of the star cavity")
+    p.add_argument("--field-points", type=int, default=64, help="field: observation points")
     p.add_argument("--gemm-batch", type=int, default=8192, help="cgemm: number of products")
     p.add_argument("--streams", type=int, default=8, help="batch64: concurrent cavity streams")
     p.add_argument("--no-compare", action="store_true",
@@ -268,6 +271,49 @@ def run_cgemm(args, fds, torch, rank):
                           "steps": args.steps, "warmup": args.warmup, "engines": out}))
 
 
+def run_field(args, fds, torch, rank):
+    """Field evaluation off the boundary (eq. integ_rep): the star cavity of
+    the default workload is built (mixed) and solved for 16 waves (8 P + 8 SV)
+    on the device; then fds_field at --field-points points on circles of radius
+    1.5-3 is timed with CUDA events over --steps calls after --warmup.
+    Unit: quadrature sums per second (point x element x wave)."""
+    import workloads
+    N = args.nodes
+    xy = workloads.star(N)
+    omega = workloads.omega_for_kTa(args.kta)
+    kinds, angles = workloads.plane_wave_set(8)
+    h = fds.fds_build(xy, omega, 2.0, 1.0, args.eps, leaf_size=args.leaf, top_level=args.top,
+                      precision=fds.FDS_MIXED, ir_tol=args.ir_tol)
+    F = fds.fds_rhs_plane_wave(h, kinds, angles)
+    d = torch.tensor(np.ascontiguousarray(F.T), device="cuda")
+    fds.fds_solve_device(h, d)
+    npts = args.field_points
+    rng = np.random.default_rng(7 + rank)
+    r, th = rng.uniform(1.5, 3.0, npts), rng.uniform(0, 2 * np.pi, npts)
+    pts = np.stack([r * np.cos(th), r * np.sin(th)], 1)
+    for _ in range(args.warmup):
+        fds.fds_field(h, d, kinds, angles, pts)
+    ts = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        fds.fds_field(h, d, kinds, angles, pts)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    h.close()
+    ms = float(np.median(ts))
+    sums = float(npts) * N * len(kinds)
+    if rank == 0:
+        print(json.dumps({"metric": "field off the boundary (eq. integ_rep): quadrature sums per second",
+                          "value": sums / ms / 1e6, "unit": "Gsum/s", "ms_per_step": ms, "steps": args.steps,
+                          "warmup": args.warmup, "higher_is_better": True, "data": "synthetic",
+                          "config": {"workload": "star r=1+0.2cos5t, %d nodes, k_T a=%g, %d waves, %d points, "
+                                                 "8 Gauss points per element, direct summation"
+                                                 % (N, args.kta, len(kinds), npts)}}))
+
+
 def run_batch(args, fds, torch, world, rank, local):
     """64 seeded cavities (ellipses / stars, 2^12..2^15 nodes, k_T a in [1, 20],
     eps 1e-8, leaf 64) built with fds_build_batch on --streams concurrent
@@ -351,6 +397,9 @@ def main():
         return
     if args.workload == "cgemm":
         run_cgemm(args, fds, torch, rank)
+        return
+    if args.workload == "field":
+        run_field(args, fds, torch, rank)
         return
 
     xy, omega, kinds, angles = workload(args, rank)

@@ -295,6 +295,23 @@ int fds_lu_batched_noalloc(int32_t batch, const int32_t *d_d, const int64_t *d_o
                            int32_t *d_piv, const int64_t *d_poff, int32_t *d_info, uint64_t stream);
 
 /*
+ * Displacement off the boundary (Sec. 3, eq. (integ_rep)), for the
+ * traction-free cavity of handle h:
+ *   u_i(x) = u^I_i(x) - int_Gamma T^{n_y}_{jk} G_ik(x - y) u_j(y) ds(y),
+ * with u the boundary solution (P1 nodal values) and u^I the plane wave it
+ * was solved for.  d_u: device, 2n x nrhs complex128, column-major in the
+ * unknown layout above (as left by fds_solve_device); kinds/angles: host,
+ * nrhs entries as given to fds_rhs_plane_wave (0 = P, 1 = SV); d_pts:
+ * device, npts points (x, y interleaved) off the boundary (the 8-point rule
+ * per element is accurate at distances of a few element lengths and more);
+ * d_out: device, 2 npts x nrhs complex128, column j = component 1 at the
+ * points, then component 2.  Direct summation over the elements
+ * (O(n npts nrhs)); synchronises the stream.
+ */
+int fds_field(fds_handle *h, const double *d_u, int32_t nrhs, const int32_t *kinds, const double *angles,
+              const double *d_pts, int32_t npts, double *d_out, uint64_t stream);
+
+/*
  * Batched complex64 GEMM of the mixed-precision levels (Sec. 7.3 products in
  * complex64; stage entry for tests and benchmarks):
  *   C_b = alpha op(A_b) B_b + beta C_b,   b = 0 .. batch-1,

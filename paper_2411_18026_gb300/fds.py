@@ -112,6 +112,7 @@ def lib():
     L.fds_id_batched.argtypes = [i32, vp, vp, vp, vp, f64, vp, vp, vp, vp, vp, u64]
     L.fds_lu_batched.argtypes = [i32, vp, vp, vp, vp, vp, vp, u64]
     L.fds_lu_batched_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, u64]
+    L.fds_field.argtypes = [vp, vp, i32, ctypes.POINTER(i32), dp, vp, i32, vp, u64]
     i64p = ctypes.POINTER(ctypes.c_int64)
     L.fds_cgemm_c64_batched.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), i64p,
                                         i64p, i64p, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, i32, u64]
@@ -375,6 +376,23 @@ def fds_lu_batched_noalloc(d_d, d_off, d_A, d_piv, d_poff, d_info, stream=None):
 def fds_lu_batched(d_d, d_off, d_A, d_piv, d_poff, d_info, stream=None):
     _check(lib().fds_lu_batched(d_d.numel(), _ptr(d_d), _ptr(d_off), _ptr(d_A), _ptr(d_piv), _ptr(d_poff),
                                 _ptr(d_info), _stream(stream)), "fds_lu_batched")
+
+
+def fds_field(h, d_u, kinds, angles, pts, stream=None):
+    """Displacement at points off the boundary (eq. integ_rep) from the device
+    solution d_u ((nrhs, 2n) complex128 CUDA tensor) of the given waves.
+    pts: (npts, 2).  Returns (2, npts, nrhs) complex numpy."""
+    import torch
+    kinds = np.ascontiguousarray(kinds, dtype=np.int32)
+    angles = np.ascontiguousarray(angles, dtype=np.float64)
+    nrhs = len(kinds)
+    d_pts = torch.tensor(np.ascontiguousarray(pts, dtype=np.float64).ravel(), device=d_u.device)
+    npts = d_pts.numel() // 2
+    d_out = torch.zeros((nrhs, 2 * npts), dtype=torch.complex128, device=d_u.device)
+    _check(lib().fds_field(h.ptr, _ptr(d_u), nrhs, kinds.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                           angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(d_pts), npts, _ptr(d_out),
+                           _stream(stream)), "fds_field")
+    return d_out.cpu().numpy().T.reshape(2, npts, nrhs)
 
 
 def fds_cgemm_c64_batched(m, n, k, aoff, boff, coff, d_A, d_B, d_C, opA=0, alpha=1.0, beta=0.0,

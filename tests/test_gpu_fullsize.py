@@ -53,14 +53,24 @@ def test_fullsize_star_mixed_vs_fp64_and_sampled_residual():
 
 
 def test_fullsize_circle_matches_pao_mow():
-    torch_cuda()
+    torch = torch_cuda()
     fds = fdslib()
     xy = workloads.circle(N)
     omega = workloads.omega_for_kTa(20.0)
     h = fds.fds_build(xy, omega, LAM, MU, 1e-10, leaf_size=64, top_level=1)
-    f = fds.fds_rhs_plane_wave(h, np.array([0, 1], np.int32), np.array([0.0, 0.0]))
-    x = fds.fds_solve(h, f)
+    kinds, angles = np.array([0, 1], np.int32), np.array([0.0, 0.0])
+    f = fds.fds_rhs_plane_wave(h, kinds, angles)
+    d = torch.tensor(np.ascontiguousarray(f.T), device="cuda")
+    fds.fds_solve_device(h, d)
+    x = d.cpu().numpy().T
+    # the field off the boundary (eq. integ_rep) at 8 points
+    rr, tt = np.linspace(1.1, 2.5, 8), np.linspace(0.2, 6.0, 8)
+    fld = fds.fds_field(h, d, kinds, angles, np.stack([rr * np.cos(tt), rr * np.sin(tt)], 1))
     h.close()
+    for j, kind in enumerate((0, 1)):
+        ref = np.array(paomow.field(rr, tt, 1.0, LAM, MU, RHO, omega, kind, 0.0))
+        err = np.abs(fld[:, :, j] - ref).max() / np.abs(ref).max()
+        assert err < 1e-4, ("field", kind, err, np.abs(fld[:, :, j] - ref).max(axis=0))
     # the series on 4096 evenly spaced sampled nodes (both components)
     idx = np.arange(0, N, N // 4096)
     th = 2 * np.pi * idx / N
@@ -68,4 +78,5 @@ def test_fullsize_circle_matches_pao_mow():
         u1, u2 = paomow.boundary_displacement(th, 1.0, LAM, MU, RHO, omega, kind, 0.0)
         ref = np.concatenate([u1, u2])
         got = np.concatenate([x[idx, j], x[N + idx, j]])
-        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-4
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err < 1e-4, ("boundary", kind, err)
