@@ -54,9 +54,13 @@ def coefficients(a, lam, mu, rho, omega, kind=0, theta0=0.0, nmax=None):
 
 
 def field(r, th, a, lam, mu, rho, omega, kind=0, theta0=0.0, nmax=None, coef=None):
-    """Total displacement (u1, u2) at polar points (r >= a, th)."""
+    """Total displacement (u1, u2) at polar points (r >= a, th).  By default the
+    series runs to |n| = ceil(k_T max(a, r)) + 30: the incident wave's
+    Bessel expansion at radius r needs orders beyond k r."""
     kL, kT = _wavenumbers(lam, mu, rho, omega)
     if coef is None:
+        if nmax is None:
+            nmax = int(np.ceil(kT * max(a, float(np.max(r))))) + 30
         coef = coefficients(a, lam, mu, rho, omega, kind, theta0, nmax)
     r = np.asarray(r, dtype=np.float64) * np.ones_like(np.asarray(th, dtype=np.float64))
     th = np.asarray(th, dtype=np.float64) * np.ones_like(r)
