@@ -38,10 +38,6 @@ int dense_gemm_rt(int batch, int max_m, int max_n, const MatRef *d_A, int opA, c
                   cplx alpha, cplx beta, cudaStream_t s);
 int dense_gemm_rt(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, const MatRefF *d_B,
                   const MatRefF *d_C, cplxf alpha, cplxf beta, cudaStream_t s);
-// Same with complex128 operands multiplied in double-float arithmetic on the
-// FP32 pipe (about 44 significant bits; see gemm.cu).
-int dense_gemm_ff(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, const MatRef *d_C,
-                  cplx alpha, cplx beta, cudaStream_t s);
 // Same with operands already split into float pairs (float4 = re_hi, im_hi,
 // re_lo, im_lo per complex entry) and a float-pair result; C = op(A) B
 // (+ C when accumulate).

@@ -6,14 +6,15 @@
 // shared-memory reads), K in steps of 16 staged in shared memory.
 //
 // Three arithmetics share the tiling:
-//   Arith64  complex64 loads, FP32 FMA
-//   Arith128 complex128 loads, FP64 FMA
-//   ArithFF  complex128 loads split into float pairs (hi + lo) when staged,
-//            products and sums in double-float arithmetic on the FP32 pipe:
-//            a x = ah xh + (err(ah xh) + ah xl + al xh) with err() from one
-//            FMA (Dekker's product), accumulation by Knuth's TwoSum; about
-//            44 bits of significand at 48 FP32 instructions per complex
-//            multiply-add, against FP64 at 1/64 of the FP32 rate on this GPU.
+//   Arith64   complex64 loads, FP32 FMA
+//   Arith128  complex128 loads, FP64 FMA
+//   ArithFFP3 operands stored as float pairs (hi + lo), products and sums in
+//             double-float arithmetic on the FP32 pipe: a x = ah xh +
+//             (err(ah xh) + ah xl + al xh) with err() from one FMA (Dekker's
+//             product), accumulation by Knuth's TwoSum, and Gauss's
+//             three-product complex multiply; about 44 bits of significand
+//             at 36 FP32 instructions per complex multiply-add, against FP64
+//             at 1/64 of the FP32 rate on this GPU.
 #include "dense.cuh"
 #include "fds_internal.cuh"
 
@@ -69,12 +70,6 @@ struct Arith128 {
 struct ff {
     float h, l;
 };
-__device__ __forceinline__ ff split(double v) {
-    ff r;
-    r.h = (float)v;
-    r.l = (float)(v - (double)r.h);
-    return r;
-}
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = a + b;
@@ -92,35 +87,6 @@ __device__ __forceinline__ void ff_mac(ff &acc, const ff &x, const ff &y) {
     acc.l += e + pl;
 }
 
-// complex multiply-add in double-float: four real products
-struct ArithFF {
-    typedef cplx G;
-    struct SA {
-        ff re, im;
-    };
-    typedef SA SB;
-    struct Acc {
-        ff re, im;
-    };
-    __device__ static SA stage_a(G v, bool cj) { return SA{split(v.x), split(cj ? -v.y : v.y)}; }
-    __device__ static SB stage_b(G v) { return SB{split(v.x), split(v.y)}; }
-    __device__ static SA za() { return SA{{0.f, 0.f}, {0.f, 0.f}}; }
-    __device__ static SB zb() { return SB{{0.f, 0.f}, {0.f, 0.f}}; }
-    __device__ static void zero(Acc &a) { a = Acc{{0.f, 0.f}, {0.f, 0.f}}; }
-    __device__ static void mac(Acc &c, const SA &a, const SB &b) {
-        const ff nai{-a.im.h, -a.im.l};
-        ff_mac(c.re, a.re, b.re);
-        ff_mac(c.re, nai, b.im);
-        ff_mac(c.im, a.re, b.im);
-        ff_mac(c.im, a.im, b.re);
-    }
-    __device__ static G finish(const Acc &c, G alpha, G beta, const G *old) {
-        const G v = mkc((double)c.re.h + (double)c.re.l, (double)c.im.h + (double)c.im.l);
-        G r = cmul(alpha, v);
-        if (old) r = cadd(r, cmul(beta, *old));
-        return r;
-    }
-};
 
 // Operands already held as float pairs (float4 = re_hi, im_hi, re_lo, im_lo):
 // the constant operators are split once, the vectors stay split, so no FP64
@@ -310,11 +276,6 @@ int dense_gemm_rt(int batch, int max_m, int max_n, const MatRef *d_A, int opA, c
 int dense_gemm_rt(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, const MatRefF *d_B,
                   const MatRefF *d_C, cplxf alpha, cplxf beta, cudaStream_t s) {
     return launch<Arith64, FDS_C64_TJ4, 4, 8>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
-}
-
-int dense_gemm_ff(int batch, int max_m, int max_n, const MatRef *d_A, int opA, const MatRef *d_B, const MatRef *d_C,
-                  cplx alpha, cplx beta, cudaStream_t s) {
-    return launch<ArithFF, 2, 2, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
 }
 
 int dense_gemm_ffp(int batch, int max_m, int max_n, const MatRefT<float4> *d_A, int opA, const MatRefT<float4> *d_B,
