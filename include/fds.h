@@ -63,6 +63,15 @@ extern "C" {
 #define FDS_C64_SIMT   0
 #define FDS_C64_TENSOR 1
 
+/* Elimination variant (Sec. 6): the paper's LU-based recursion (default), or
+ * the Sherman–Morrison–Woodbury form of the original Martinsson–Rokhlin
+ * method it is compared with (Sec. 6 introduction), which additionally forms
+ * E_i = A_i^{-1} U_i A~_i, F_i = A~_i V_i A_i^{-1} and
+ * G_i = A_i^{-1} - A_i^{-1} U_i A~_i V_i A_i^{-1} per cell and solves by
+ * f~_i = F_i f_i upward and x_i = G_i f_i + E_i y_i downward; FDS_FP64 only. */
+#define FDS_VARIANT_LU     0
+#define FDS_VARIANT_MR2005 1
+
 #define FDS_RANK_ADAPTIVE 0
 #define FDS_RANK_LEARNED  1
 /* Learned-rank network: 16 -> 64 -> 64 -> 1, tanh, FP32.  Parameter vector:
@@ -94,7 +103,11 @@ typedef struct {
     double proxy_ratio;    /* proxy circle radius / cell radius (Sec. 7.1); default 1.5 */
     int32_t proxy_points;  /* minimum proxy polygon vertices m'; default 64; the library
                               uses max(proxy_points, ceil(2 k_T R_proxy + 30)) */
-    int32_t top_level;     /* level l0 of the dense top solve (Sec. 7.3); default 1 */
+    int32_t top_level;     /* level l0 of the dense top solve (Sec. 7.3); default 1; clamped to
+                              the depth L.  Negative: l0 = max(L + top_level, 0), so -1 is the
+                              single-level variant of Sec. 8.1 (Table tab:error_single: only
+                              the leaf cells are compressed and their skeleton system is
+                              factored densely; O(N^3) in the top LU) */
     int32_t precision;     /* FDS_FP64 (default) or FDS_MIXED */
     double alpha_re, alpha_im;
     int32_t alpha_set;     /* 0: alpha = i/(mu k_T) */
@@ -124,6 +137,14 @@ typedef struct {
     int32_t c64_engine;    /* FDS_MIXED: FDS_C64_SIMT (default) or FDS_C64_TENSOR; the tensor
                               cores' fp32 accumulation is less accurate than fp32 FMA, which
                               can cost the refinement an extra sweep */
+    double tol_decay;      /* ID tolerance per level: tol at the leaf level L and
+                              tol * tol_decay^(L - l) at level l (0 < tol_decay <= 1),
+                              but not below min(tol, 1e-15).  Default 0.5.  1 gives the
+                              paper's single tolerance at every level, whose error grows
+                              with the depth (Sec. 8.1, Table tab:error); halving the
+                              tolerance per level up keeps the error near tol (measured:
+                              error / tol <= 2.1 at 2^12-2^13 nodes, against 4-28 with 1) */
+    int32_t variant;       /* FDS_VARIANT_LU (default) or FDS_VARIANT_MR2005 (FDS_FP64 only) */
 } fds_options;
 
 /* Statistics of a built handle. */
@@ -219,6 +240,37 @@ void fds_timing_reset(void);
 int fds_timing_report(char *buf, int32_t cap);
 /* Number of kernels this library has launched since it was loaded. */
 int64_t fds_launch_count(void);
+/*
+ * Measured arithmetic peak of the current device (a measurement service, not
+ * a step of the paper's method): kind 0 FP64, 1 FP32.  A register-resident
+ * loop of independent fused multiply-adds on 8 blocks of 256 threads per SM,
+ * calibrated to ~60 ms per launch, best of three launches timed with CUDA
+ * events on the legacy default stream; *tflops receives 2 x FMAs / second
+ * / 1e12 at whatever clock the GPU ran.  Allocates 8 bytes of device memory
+ * for the duration of the call; synchronous.
+ */
+int fds_alu_peak(int32_t kind, double *tflops);
+
+/*
+ * Tile autotuner of the batched register-tiled GEMMs (the complex64,
+ * complex128 and double-float products of the merges, the solve sweep and
+ * the forward operator; an extension, not in the paper).  When enabled, the
+ * first launch of each shape class (arithmetic, op(A), row count rounded up
+ * to 16, column count and batch size rounded up to powers of two, with or
+ * without row maps) whose result does not read C (beta = 0) times every
+ * candidate tile shape (row groups x columns per thread) on its stream with
+ * CUDA events, best of two, synchronising the stream, and records the
+ * fastest in a process-wide table that later launches of the class use;
+ * classes not yet tuned, and launches during stream capture, use the fixed
+ * rule (tile height that pads the rows least).  Every candidate accumulates
+ * over K in the same order, so results do not depend on the shape chosen.
+ * fds_autotune_report writes one line per class: "arith opA rows cols batch
+ * mapped MI TJ best_us rule_us" into buf (cap bytes, NUL-terminated) and
+ * returns the length it needs.  Process-wide; off by default.
+ */
+void fds_autotune_enable(int32_t on);
+void fds_autotune_reset(void);
+int fds_autotune_report(char *buf, int32_t cap);
 
 /* ------------------------------------------------------------------------
  * Stage entry points: each runs one step of the hot path on caller-provided
@@ -286,6 +338,9 @@ int fds_lu_batched(int32_t batch, const int32_t *d_d, const int64_t *d_off, doub
  * the process exits); batch > 16384 returns FDS_ERR_ARG.  The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture.
+ * The address is kept per device ordinal for the life of the process: after
+ * cudaDeviceReset() of a device the kept address is stale, so a process that
+ * resets a device must not call this entry point on it again.
  * Every call shares the array, which keeps the last call's descriptors:
  * calls that overlap on the GPU (different streams, or different host
  * threads on the same device) race and must be serialised by the caller.

@@ -24,7 +24,10 @@ Readings where the paper is silent (stated in the project's design notes):
     clockwise vertices;
   * proxy entries use a 2x2 Gauss rule per element pair (the proxy rows only
     have to span the far field; higher orders change no result);
-  * truncation: stop at the first pivot with |R_jj| <= eps |R_11|; pivot =
+  * ID tolerance per level: eps at the leaves and eps tol_decay^(L - l) at
+    level l (default tol_decay = 0.5; 1 is the paper's single tolerance,
+    whose error grows with the depth, Sec. 8.1);
+  * truncation: stop at the first pivot with |R_jj| <= eps_l |R_11|; pivot =
     largest remaining column 2-norm, ties to the lowest index; skeleton DOFs
     are kept in pivot order.
 """
@@ -145,14 +148,16 @@ class FDS:
     """Build (upward factorisation, Sec. 7.3 steps 1–4) and solve (steps 3–5)."""
 
     def __init__(self, P, xy, lam, mu, rho, omega, eps, leaf_size=32, top_level=1,
-                 proxy_ratio=1.5, proxy_min=64, record=False, proxy_q=2):
+                 proxy_ratio=1.5, proxy_min=64, record=False, proxy_q=2, tol_decay=0.5):
         self.P, self.xy, self.eps = P, np.asarray(xy, dtype=np.float64), eps
         N = len(self.xy)
         self.N = N
         kT = omega / np.sqrt(mu / rho)
         L, ranges = tree_levels(N, leaf_size)
         self.L = L
-        self.l0 = min(top_level, L)
+        # top_level < 0 counts from the leaves: -1 is the single-level variant
+        # of Sec. 8.1 (Table tab:error_single), l0 = L - 1
+        self.l0 = min(top_level, L) if top_level >= 0 else max(L + top_level, 0)
         self.levels = {}
         self.record = record
         self.trace = []
@@ -197,7 +202,9 @@ class FDS:
                     if near:
                         blocks.append(dof_entries(P, self.xy, cols, near).conj().T)
                     Y = np.vstack(blocks)
-                    k, perm, T = cpqr_id(Y, eps)
+                    # ID tolerance of level l: eps at the leaves, eps tol_decay^(L-l)
+                    # above, not below 1e-15 unless eps itself is
+                    k, perm, T = cpqr_id(Y, max(eps * tol_decay ** (L - l), min(eps, 1e-15)))
                     b.Vc.append(interp_matrix(k, perm, T, nc))
                     b.skel += [cols[p] for p in perm[:k]]
                     b.kc.append(k)

@@ -16,6 +16,8 @@ extern "C" void fds_default_options(fds_options *o) {
     o->proxy_ratio = 1.5;
     o->proxy_points = 64;
     o->top_level = 1;
+    o->tol_decay = 0.5;
+    o->variant = FDS_VARIANT_LU;
     o->precision = FDS_FP64;
     o->alpha_re = 0.0;
     o->alpha_im = 0.0;
@@ -66,12 +68,15 @@ int fds_build_owned(const fds_geometry *g, double omega, double lambda, double m
     fds_options o;
     if (opt) o = *opt;
     else fds_default_options(&o);
-    if (o.leaf_size < 2 || !(o.proxy_ratio > 1.0) || o.proxy_points < 8 || o.top_level < 0 ||
+    if (o.leaf_size < 2 || !(o.proxy_ratio > 1.0) || o.proxy_points < 8 || o.top_level < -64 ||
         (o.precision != FDS_FP64 && o.precision != FDS_MIXED) || !(o.ir_tol >= 0.0) || o.ir_max_iter < 0 ||
         o.ir_max_iter > 100 || (o.ir_apply != FDS_APPLY_FF && o.ir_apply != FDS_APPLY_FP64) ||
         (o.rank_mode != FDS_RANK_ADAPTIVE && o.rank_mode != FDS_RANK_LEARNED) ||
         (o.rank_mode == FDS_RANK_LEARNED && !o.mlp_params) || o.sketch_extra < 1 || o.sketch_extra > 64 || o.sweep_fp64_levels < -1 || o.sweep_ff < 0 ||
-        o.sweep_ff > 2 || (o.c64_engine != FDS_C64_SIMT && o.c64_engine != FDS_C64_TENSOR))
+        o.sweep_ff > 2 || (o.c64_engine != FDS_C64_SIMT && o.c64_engine != FDS_C64_TENSOR) ||
+        !(o.tol_decay > 0.0 && o.tol_decay <= 1.0) ||
+        (o.variant != FDS_VARIANT_LU && o.variant != FDS_VARIANT_MR2005) ||
+        (o.variant == FDS_VARIANT_MR2005 && o.precision != FDS_FP64))
         return FDS_ERR_ARG;
     for (int i = 0; i < 2 * g->n_nodes; ++i)
         if (!std::isfinite(g->xy[i])) return FDS_ERR_ARG;

@@ -557,6 +557,55 @@ int launch_group_blocks(fds_handle *h, const char *name, const std::vector<int64
 }  // namespace
 
 // ------------------------------------------------------------------ build
+// Woodbury form of the original Martinsson–Rokhlin elimination (the method
+// the paper's variant is compared with, Sec. 6 introduction): with
+// A~_i = (V_i A_i^{-1} U_i)^{-1},
+//   A^{-1} = G + E (A~ + B~)^{-1} F,  E_i = A_i^{-1} U_i A~_i,
+//   F_i = A~_i V_i A_i^{-1},  G_i = A_i^{-1} - E_i V_i A_i^{-1},
+// B~ the coupling between the skeletons (the same compressed system as the
+// LU variant).  Four GEMMs per cell beyond the LU variant's products.
+int mr2005_level_factors(fds_handle *h, Level &C, const std::vector<int> &dv, const std::vector<int> &rv,
+                         cudaStream_t s) {
+    const int nb = C.nb;
+    double fl_e = 0, fl_q = 0, fl_f = 0, fl_g = 0;
+    for (int b = 0; b < nb; ++b) {
+        const double d = dv[b], r = rv[b];
+        fl_e += 8.0 * d * r * r;
+        fl_q += 8.0 * r * d * d;
+        fl_f += 8.0 * r * r * d;
+        fl_g += 8.0 * d * r * d;
+    }
+    DBuf<cplx> Q;
+    DBuf<MatRef> rQ;
+    FDS_TRY(C.mrE.alloc(C.offW[nb]));
+    FDS_TRY(C.mrF.alloc(C.offV[nb]));
+    FDS_TRY(C.mrG.alloc(C.offA[nb]));
+    FDS_TRY(Q.alloc(C.offV[nb]));
+    FDS_TRY(make_refs_t(C.rmrE, C.mrE.p, C.offW, dv, rv, s));
+    FDS_TRY(make_refs_t(C.rmrF, C.mrF.p, C.offV, rv, dv, s));
+    FDS_TRY(make_refs_t(C.rmrG, C.mrG.p, C.offA, dv, dv, s));
+    FDS_TRY(make_refs_t(rQ, Q.p, C.offV, rv, dv, s));
+    const cplx one = mkc(1, 0), zero = mkc(0, 0), mone = mkc(-1, 0);
+    ProfScope ps("a3.mr2005_products", s);
+    ps.flops = fl_e + fl_q + fl_f + fl_g;
+    // E = W A~ ; Q = V A^{-1} ; F = A~ Q ; G = A^{-1} - E Q
+    FDS_TRY(dense_gemm(nb, C.dmax, C.rmax, C.rW.p, 0, C.rAt.p, 0, C.rmrE.p, one, zero, s));
+    FDS_TRY(dense_gemm(nb, C.rmax, C.dmax, C.rV.p, 0, C.rAinv.p, 0, rQ.p, one, zero, s));
+    FDS_TRY(dense_gemm(nb, C.rmax, C.dmax, C.rAt.p, 0, rQ.p, 0, C.rmrF.p, one, zero, s));
+    FDS_CUDA_TRY(cudaMemcpyAsync(C.mrG.p, C.Ainv.p, sizeof(cplx) * C.offA[nb], cudaMemcpyDeviceToDevice, s));
+    FDS_TRY(dense_gemm(nb, C.dmax, C.dmax, C.rmrE.p, 0, rQ.p, 0, C.rmrG.p, mone, one, s));
+    FDS_TRY(sync_check(s));
+    h->factor_bytes += (int64_t)(C.mrE.bytes() + C.mrF.bytes() + C.mrG.bytes());
+    return FDS_OK;
+}
+
+// ID tolerance of level l: tol at the leaves, tol * tol_decay^(L - l) above,
+// but not below 1e-15 (FP64 rounding of the proxy matrices) unless tol is
+static double level_tol(const fds_handle *h, int l) {
+    const double t = h->tol * std::pow(h->opt.tol_decay, (double)(h->L - l));
+    return std::max(t, std::min(h->tol, 1e-15));
+}
+
 int fds_build_impl(fds_handle *h) {
     cudaStream_t s = h->stream;
     C64EngineScope eng(h->opt.c64_engine == FDS_C64_TENSOR);
@@ -567,7 +616,9 @@ int fds_build_impl(fds_handle *h) {
     int L = 0;
     while (((N + (1 << L) - 1) >> L) > leaf) ++L;
     h->L = L;
-    h->l0 = std::min(std::max(h->opt.top_level, 0), L);
+    // top_level < 0 counts up from the leaves: -1 is the single-level variant
+    // of Sec. 8.1 (Table tab:error_single), l0 = L - 1
+    h->l0 = h->opt.top_level >= 0 ? std::min(h->opt.top_level, L) : std::max(L + h->opt.top_level, 0);
     h->ranges.assign(L + 1, {});
     h->ranges[0].push_back({0, N});
     for (int l = 0; l < L; ++l)
@@ -782,6 +833,8 @@ int fds_build_impl(fds_handle *h) {
         }
         // ---- interpolative decomposition (a2; a2' with the learned rank)
         const bool learned = h->opt.rank_mode == FDS_RANK_LEARNED;
+        const double tol_l = level_tol(h, l);
+        std::vector<int> h_fail_flags;   // learned: the (cell, component) IDs redone by the adaptive CPQR
         DBuf<float> d_feat;
         if (learned || h->opt.record_features) {
             std::vector<int> lo(nb), hi(nb);
@@ -794,7 +847,7 @@ int fds_build_impl(fds_handle *h) {
             FDS_TRY(d_feat.alloc((size_t)2 * nb * FDS_MLP_NIN));
             ProfScope ps("a2.features", s);
             FDS_TRY(level_features(nb, d_lo.p, d_hi.p, h->d_xy.p, N, d_R.p, d_fn1.p, d_fn2.p, d_nnd.p, L - l,
-                                   h->P.kT, h->P.kL, h->tol, d_feat.p, s));
+                                   h->P.kT, h->P.kL, tol_l, d_feat.p, s));
             FDS_TRY(sync_check(s));
         }
         if (learned) {
@@ -809,12 +862,13 @@ int fds_build_impl(fds_handle *h) {
             {
                 ProfScope ps("a2.id_sketch", s);
                 FDS_TRY(id_sketched(2 * nb, maxm, d_idm.p, d_idn.p, d_yoff.p, d_Y.p, d_frac.p, h->opt.sketch_extra,
-                                    h->tol, d_rank.p, d_perm.p, d_poff.p, d_T.p, d_toff.p, d_fail.p,
+                                    tol_l, d_rank.p, d_perm.p, d_poff.p, d_T.p, d_toff.p, d_fail.p,
                                     0x5eed2411ULL ^ ((unsigned long long)l << 40), s));
             }
             std::vector<int> fail;
             FDS_TRY(d2h(fail, d_fail.p, 2 * nb, s));
             FDS_TRY(sync_check(s));
+            h_fail_flags = fail;
             std::vector<int> sel;
             for (int b = 0; b < 2 * nb; ++b)
                 if (fail[b]) sel.push_back(b);
@@ -824,19 +878,33 @@ int fds_build_impl(fds_handle *h) {
                 DBuf<int> d_sel;
                 FDS_TRY(d_sel.upload(sel, s));
                 ProfScope ps("a2.id_cpqr", s);
-                FDS_TRY(id_batched((int)sel.size(), maxm, maxn, d_idm.p, d_idn.p, d_yoff.p, d_Y.p, h->tol, d_rank.p,
+                FDS_TRY(id_batched((int)sel.size(), maxm, maxn, d_idm.p, d_idn.p, d_yoff.p, d_Y.p, tol_l, d_rank.p,
                                    d_perm.p, d_poff.p, d_T.p, d_toff.p, s, d_sel.p));
                 FDS_TRY(sync_check(s));
             }
         } else {
             ProfScope ps("a2.id_cpqr", s);
-            FDS_TRY(id_batched(2 * nb, maxm, maxn, d_idm.p, d_idn.p, d_yoff.p, d_Y.p, h->tol, d_rank.p, d_perm.p,
+            FDS_TRY(id_batched(2 * nb, maxm, maxn, d_idm.p, d_idn.p, d_yoff.p, d_Y.p, tol_l, d_rank.p, d_perm.p,
                                d_poff.p, d_T.p, d_toff.p, s));
         }
         std::vector<int> rank;
         FDS_TRY(d2h(rank, d_rank.p, 2 * nb, s));
         FDS_TRY(d2h(C.perm, d_perm.p, poff[2 * nb], s));
         FDS_TRY(sync_check(s));
+        if (prof_enabled()) {
+            // algorithmic work of the Householder CPQR that ran, m x n to rank k:
+            // 8 (2 m n k - k^2 (m + n) + 2 k^3 / 3) real flops per matrix
+            std::vector<char> ran(2 * nb, learned ? 0 : 1);
+            if (learned)
+                for (int b = 0; b < 2 * nb; ++b) ran[b] = h_fail_flags.empty() ? 0 : h_fail_flags[b];
+            double fl = 0;
+            for (int b = 0; b < 2 * nb; ++b) {
+                if (!ran[b]) continue;
+                const double m = idm[b], n = idn[b], k = rank[b];
+                fl += 8.0 * (2.0 * m * n * k - k * k * (m + n) + 2.0 * k * k * k / 3.0);
+            }
+            prof_add_work("a2.id_cpqr", fl, 0, 0);
+        }
         if (h->opt.record_features) {
             std::vector<float> f;
             FDS_TRY(d2h(f, d_feat.p, (size_t)2 * nb * FDS_MLP_NIN, s));
@@ -1056,6 +1124,7 @@ int fds_build_impl(fds_handle *h) {
         FDS_TRY(sync_check(s));
         for (int b = 0; b < nb; ++b)
             if (hinfo[b] || hinfo2[b]) return FDS_ERR_SINGULAR;
+        if (h->opt.variant == FDS_VARIANT_MR2005) FDS_TRY(mr2005_level_factors(h, C, dv, rv, s));
         C.LU.release();
         C.rLU.release();
         C.piv.release();

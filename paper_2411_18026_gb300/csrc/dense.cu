@@ -414,7 +414,8 @@ static __device__ __align__(256) MatRef g_lu_noalloc_refs[FDS_LU_NOALLOC_MAX_BAT
 namespace {
 // Device address of g_lu_noalloc_refs for each device, looked up once per
 // device (with that device current) by cudaGetSymbolAddress: in host code the
-// array's name is only a host-side stand-in.
+// array's name is only a host-side stand-in.  The address is kept for the life
+// of the process; a cudaDeviceReset() of the device invalidates it.
 MatRef *lu_noalloc_scratch(int *err) {
     static std::mutex mu;
     static MatRef *addr[64] = {nullptr};

@@ -102,6 +102,10 @@ struct Level {
     DBuf<cplx> LU, W, At, V, Ainv;   // LU: during the build only; Ainv = A_i^{-1} for the sweep
     DBuf<int> piv;
     DBuf<MatRef> rLU, rW, rAt, rV, rAinv;
+    // FDS_VARIANT_MR2005: E_i = A_i^{-1} U_i A~_i (d x r), F_i = A~_i V_i A_i^{-1}
+    // (r x d), G_i = A_i^{-1} - E_i V_i A_i^{-1} (d x d)
+    DBuf<cplx> mrE, mrF, mrG;
+    DBuf<MatRef> rmrE, rmrF, rmrG;
     DBuf<int64_t> d_offpiv;
     // --- placement of each cell's skeleton vector in its parent's DOF vector
     std::vector<int> par_pos1, par_pos2;   // start of comp-1 / comp-2 skeleton block in the parent
@@ -203,6 +207,7 @@ struct fds_handle {
     DBuf<MatRef> wrefs;
     DBuf<MatRefF> wrefsf;
     DBuf<double> wnorm;
+    DBuf<int> wundo;           // per-column flags of the refinement's take-back step
     int64_t ws_cols = 0;
     double build_ms = 0, solve_ms = 0;
     int64_t factor_bytes = 0;
@@ -230,6 +235,10 @@ int make_refs_t(DBuf<MatRefT<C>> &dst, C *base, const std::vector<int64_t> &off,
 }
 
 int fds_build_impl(fds_handle *h);
+// FDS_VARIANT_MR2005: the Woodbury products E_i, F_i, G_i of a merged level
+// (needs A_i^{-1}, W_i = A_i^{-1} U_i, A~_i and the dense V_i); dv, rv per cell.
+int mr2005_level_factors(fds_handle *h, Level &C, const std::vector<int> &dv, const std::vector<int> &rv,
+                         cudaStream_t s);
 // FDS_MIXED: copy of a level's square blocks (LU buffer, before it is factored)
 // into a forward-operator store.
 int fds_keep_blocks(const Level &Lv, DBuf<cplx> &dst, DBuf<MatRef> &rdst, cudaStream_t s);

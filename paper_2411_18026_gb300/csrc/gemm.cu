@@ -15,6 +15,12 @@
 //             three-product complex multiply; about 44 bits of significand
 //             at 36 FP32 instructions per complex multiply-add, against FP64
 //             at 1/64 of the FP32 rate on this GPU.
+#include <atomic>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
+
 #include "dense.cuh"
 #include "fds_internal.cuh"
 
@@ -31,6 +37,7 @@ constexpr int BK = 16, NT = 256;
 
 // ---------------------------------------------------------------- arithmetics
 struct Arith64 {
+    static constexpr int ID = 0;
     typedef cplxf G;      // global element
     typedef cplxf SA;     // staged element of op(A)
     typedef cplxf SB;     // staged element of B
@@ -49,6 +56,7 @@ struct Arith64 {
 };
 
 struct Arith128 {
+    static constexpr int ID = 1;
     typedef cplx G;
     typedef cplx SA;
     typedef cplx SB;
@@ -109,6 +117,7 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
 // element of B) formed once when the tile is staged and reused by every
 // product of the tile: 36 FP32 instructions per complex multiply-add.
 struct ArithFFP3 {
+    static constexpr int ID = 2;
     typedef float4 G;
     struct SA {
         ff a, b, s;     // re, im, re + im
@@ -244,15 +253,78 @@ int launch_t(int batch, int max_m, int max_n, const MatRefT<typename Ar::G> *d_A
     return FDS_OK;
 }
 
+// ---------------------------------------------------------------- autotuner
+// Tile shapes (row groups MI x columns per thread TJ) chosen by timing: the
+// first launch of a shape class (arithmetic, op(A), row count in steps of 16,
+// column and batch counts by powers of two, row maps or not) whose result
+// does not depend on C's old contents (beta = 0) runs every candidate shape
+// on its stream (CUDA events, best of two), keeps the fastest in a
+// process-wide table and leaves C as any candidate computes it (the K loop
+// order is the same for every shape, so the results are identical).  Other
+// launches use the table, or the rule below while their class is untuned.
+struct TuneKey {
+    int arith, opA, mb, nb, bb, mapped;
+    bool operator<(const TuneKey &o) const {
+        const int a[6] = {arith, opA, mb, nb, bb, mapped}, b[6] = {o.arith, o.opA, o.mb, o.nb, o.bb, o.mapped};
+        for (int i = 0; i < 6; ++i)
+            if (a[i] != b[i]) return a[i] < b[i];
+        return false;
+    }
+};
+struct TuneVal {
+    int mi, tj;
+    float best_us, rule_us;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+std::atomic<int> g_tune_on{0};
+
+int ceil_log2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+template <class Ar>
+using LaunchFn = int (*)(int, int, int, const MatRefT<typename Ar::G> *, int, const MatRefT<typename Ar::G> *,
+                         const MatRefT<typename Ar::G> *, typename Ar::G, typename Ar::G, cudaStream_t,
+                         const RowMaps *);
+
+// candidate shapes per arithmetic (register budgets: the float-pair
+// accumulators are three pairs per output)
+template <class Ar>
+struct Cands;
+template <>
+struct Cands<Arith64> {
+    static constexpr int n = 6;
+    static constexpr int mi[n] = {4, 4, 3, 3, 2, 2}, tj[n] = {4, 2, 4, 2, 8, 4};
+    static LaunchFn<Arith64> fn(int c);
+};
+template <>
+struct Cands<Arith128> {
+    static constexpr int n = 5;
+    static constexpr int mi[n] = {4, 4, 3, 2, 2}, tj[n] = {4, 2, 4, 8, 4};
+    static LaunchFn<Arith128> fn(int c);
+};
+template <>
+struct Cands<ArithFFP3> {
+    static constexpr int n = 5;
+    static constexpr int mi[n] = {4, 3, 3, 2, 2}, tj[n] = {2, 4, 2, 4, 2};
+    static LaunchFn<ArithFFP3> fn(int c);
+};
+
 // Tile height 32, 48 or 64 rows, whichever pads the largest row count of the
 // batch least (ties to the taller tile); the column width keeps about the
 // same number of products per thread (TJ2, TJ3, TJ4 for 2, 3, 4 row groups).
 template <class Ar, int TJ4, int TJ3, int TJ2>
 int launch(int batch, int max_m, int max_n, const MatRefT<typename Ar::G> *d_A, int opA,
            const MatRefT<typename Ar::G> *d_B, const MatRefT<typename Ar::G> *d_C, typename Ar::G alpha,
-           typename Ar::G beta, cudaStream_t s, const RowMaps *maps = nullptr) {
-    if (batch <= 0 || max_m <= 0 || max_n <= 0) return FDS_OK;
-    if (opA != 0 && opA != 2) return FDS_ERR_ARG;
+           typename Ar::G beta, cudaStream_t s, const RowMaps *maps = nullptr);
+
+template <class Ar, int TJ4, int TJ3, int TJ2>
+int launch_rule(int batch, int max_m, int max_n, const MatRefT<typename Ar::G> *d_A, int opA,
+                const MatRefT<typename Ar::G> *d_B, const MatRefT<typename Ar::G> *d_C, typename Ar::G alpha,
+                typename Ar::G beta, cudaStream_t s, const RowMaps *maps) {
     int best = 4, pad = 1 << 30;
     for (int mi = 4; mi >= 2; --mi) {
         const int p = (max_m + 16 * mi - 1) / (16 * mi) * 16 * mi;
@@ -265,6 +337,87 @@ int launch(int batch, int max_m, int max_n, const MatRefT<typename Ar::G> *d_A, 
     if (best == 3) return launch_t<Ar, TJ3, 3>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s, maps);
     return launch_t<Ar, TJ4, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s, maps);
 }
+
+// time one launch on stream s (ms); negative on failure
+template <class F>
+float time_launch(cudaStream_t s, F &&f) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return -1.f;
+    }
+    float ms = -1.f;
+    cudaEventRecord(e0, s);
+    const int rc = f();
+    cudaEventRecord(e1, s);
+    if (rc == FDS_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc == FDS_OK ? ms : -1.f;
+}
+
+template <class Ar, int TJ4, int TJ3, int TJ2>
+int launch(int batch, int max_m, int max_n, const MatRefT<typename Ar::G> *d_A, int opA,
+           const MatRefT<typename Ar::G> *d_B, const MatRefT<typename Ar::G> *d_C, typename Ar::G alpha,
+           typename Ar::G beta, cudaStream_t s, const RowMaps *maps) {
+    if (batch <= 0 || max_m <= 0 || max_n <= 0) return FDS_OK;
+    if (opA != 0 && opA != 2) return FDS_ERR_ARG;
+    if (!g_tune_on.load(std::memory_order_relaxed))
+        return launch_rule<Ar, TJ4, TJ3, TJ2>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s, maps);
+    const TuneKey key{Ar::ID, opA, (max_m + 15) / 16, ceil_log2(max_n), ceil_log2(batch), maps ? 1 : 0};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            for (int c = 0; c < Cands<Ar>::n; ++c)
+                if (Cands<Ar>::mi[c] == it->second.mi && Cands<Ar>::tj[c] == it->second.tj)
+                    return Cands<Ar>::fn(c)(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s, maps);
+        }
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const bool use_beta = !(beta.x == 0 && beta.y == 0);
+    if (use_beta || cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return launch_rule<Ar, TJ4, TJ3, TJ2>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s, maps);
+    TuneVal v{0, 0, 1e30f, -1.f};
+    for (int rep = 0; rep < 2; ++rep) {
+        const float r = time_launch(s, [&] {
+            return launch_rule<Ar, TJ4, TJ3, TJ2>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s, maps);
+        });
+        if (r < 0) return FDS_ERR_CUDA;
+        v.rule_us = v.rule_us < 0 ? 1e3f * r : fminf(v.rule_us, 1e3f * r);
+        for (int c = 0; c < Cands<Ar>::n; ++c) {
+            const float t = time_launch(s, [&] {
+                return Cands<Ar>::fn(c)(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s, maps);
+            });
+            if (t < 0) return FDS_ERR_CUDA;
+            if (1e3f * t < v.best_us) v = TuneVal{Cands<Ar>::mi[c], Cands<Ar>::tj[c], 1e3f * t, v.rule_us};
+        }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = v;
+    return FDS_OK;
+}
+
+#define FDS_CAND(Ar, MI, TJ) &launch_t<Ar, TJ, MI>
+LaunchFn<Arith64> Cands<Arith64>::fn(int c) {
+    static const LaunchFn<Arith64> f[n] = {FDS_CAND(Arith64, 4, 4), FDS_CAND(Arith64, 4, 2), FDS_CAND(Arith64, 3, 4),
+                                           FDS_CAND(Arith64, 3, 2), FDS_CAND(Arith64, 2, 8), FDS_CAND(Arith64, 2, 4)};
+    return f[c];
+}
+LaunchFn<Arith128> Cands<Arith128>::fn(int c) {
+    static const LaunchFn<Arith128> f[n] = {FDS_CAND(Arith128, 4, 4), FDS_CAND(Arith128, 4, 2),
+                                            FDS_CAND(Arith128, 3, 4), FDS_CAND(Arith128, 2, 8),
+                                            FDS_CAND(Arith128, 2, 4)};
+    return f[c];
+}
+LaunchFn<ArithFFP3> Cands<ArithFFP3>::fn(int c) {
+    static const LaunchFn<ArithFFP3> f[n] = {FDS_CAND(ArithFFP3, 4, 2), FDS_CAND(ArithFFP3, 3, 4),
+                                             FDS_CAND(ArithFFP3, 3, 2), FDS_CAND(ArithFFP3, 2, 4),
+                                             FDS_CAND(ArithFFP3, 2, 2)};
+    return f[c];
+}
+#undef FDS_CAND
 
 }  // namespace
 
@@ -306,4 +459,30 @@ int dense_gemm(int batch, int max_m, int max_n, const MatRefP *d_A, int opA, con
                const MatRefP *d_C, float4 alpha, float4 beta, cudaStream_t s) {
     if (opB != 0) return FDS_ERR_ARG;
     return launch<ArithFFP3, FDS_FFP_TJ4, 3, 4>(batch, max_m, max_n, d_A, opA, d_B, d_C, alpha, beta, s);
+}
+
+extern "C" void fds_autotune_enable(int32_t on) { g_tune_on.store(on ? 1 : 0); }
+
+extern "C" void fds_autotune_reset(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
+}
+
+extern "C" int fds_autotune_report(char *buf, int32_t cap) {
+    static const char *names[3] = {"c64", "c128", "ff"};
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    std::string out;
+    char line[160];
+    for (auto &kv : g_tune) {
+        const TuneKey &k = kv.first;
+        snprintf(line, sizeof(line), "%s %d %d %d %d %d %d %d %.3f %.3f\n", names[k.arith], k.opA, 16 * k.mb,
+                 1 << k.nb, 1 << k.bb, k.mapped, kv.second.mi, kv.second.tj, kv.second.best_us, kv.second.rule_us);
+        out += line;
+    }
+    if (buf && cap > 0) {
+        const size_t n = out.size() < (size_t)(cap - 1) ? out.size() : (size_t)(cap - 1);
+        memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
+    return (int)out.size() + 1;
 }

@@ -185,7 +185,14 @@ __global__ void __launch_bounds__(LT) k_sketch_id(const int *__restrict__ ms, co
     if (threadIdx.x == 0) { s_k = 0; s_stop = 0; s_r11 = 0.0; }
     __syncthreads();
     const int kmax = min(s, n);
-    for (int j = 0; j < kmax; ++j) {
+    // two passes: stop the sketch's CPQR at tol/3 and check the ID on Y; if
+    // the check fails, continue the same factorisation down to tol/10 and
+    // check again (fewer skeleton columns than a single tol/10 pass)
+    for (int pass = 0; pass < 2; ++pass) {
+    const double stop_frac = pass == 0 ? (1.0 / 3.0) : 0.1;
+    if (threadIdx.x == 0) s_stop = 0;
+    __syncthreads();
+    for (int j = s_k; j < kmax; ++j) {
         double best = -1.0;
         int bi = n;
         for (int c = j + threadIdx.x; c < n; c += blockDim.x)
@@ -212,7 +219,7 @@ __global__ void __launch_bounds__(LT) k_sketch_id(const int *__restrict__ ms, co
             s_alpha = alpha;
             // a tenth of the tolerance on the sketch: a (k + extra)-row sketch
             // underestimates the trailing norms
-            s_stop = (alpha == 0.0 || alpha <= 0.1 * tol * s_r11) ? 1 : 0;
+            s_stop = (alpha == 0.0 || alpha <= stop_frac * tol * s_r11) ? 1 : 0;
         }
         __syncthreads();
         if (s_stop) break;
@@ -275,6 +282,7 @@ __global__ void __launch_bounds__(LT) k_sketch_id(const int *__restrict__ ms, co
     const int k = s_k;
     // T = R11^{-1} R12 (k x (n - k)), one thread per column
     cplx *T = Tall + toffs[b];
+    __syncthreads();
     for (int c = threadIdx.x; c < n - k; c += blockDim.x) {
         const int col = k + c;
         for (int i = k - 1; i >= 0; --i) {
@@ -318,7 +326,11 @@ __global__ void __launch_bounds__(LT) k_sketch_id(const int *__restrict__ ms, co
         const int ok = s_ok && (ee <= tol * tol * s_alpha);
         fail[b] = ok ? 0 : 1;
         if (ok) ranks[b] = k;
+        s_ok = ok;
     }
+    __syncthreads();
+    if (s_ok || k >= kmax) break;
+    }   // pass
     int *pout = perms + poffs[b];
     for (int j = threadIdx.x; j < n; j += blockDim.x) pout[j] = perm[j];
 }

@@ -124,6 +124,18 @@ __global__ void k_update(cplx *X, const LT *__restrict__ dX, int64_t n, int set)
     }
 }
 
+// X -= dX in the columns c with undo[c] != 0 (D entries per column): takes
+// back the last refinement correction of the columns it did not improve
+template <typename LT>
+__global__ void k_undo_cols(cplx *X, const LT *__restrict__ dX, int64_t D, int cols, const int *__restrict__ undo) {
+    const int64_t n = D * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        if (!undo[e / D]) continue;
+        const cplx d = to_c128(dX[e]);
+        X[e] = mkc(X[e].x - d.x, X[e].y - d.y);
+    }
+}
+
 // natural-order vector <- leaf-order vector
 __global__ void k_leaf_scatter(const int *__restrict__ gidx, int64_t D, const cplx *__restrict__ X, cplx *out,
                                int64_t ldo, int cols) {
@@ -598,8 +610,10 @@ int solve_mixed(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
         FDS_TRY(sweep_chunk(h, nc, s));
         fds_count_launch(), k_update<LT><<<1024, 256, 0, s>>>(h->wX.p, leaf, D * nc, 1);
         FDS_CUDA_TRY(cudaGetLastError());
-        // refinement against the FP64 compressed operator
+        // refinement against the FP64 compressed operator; prevc[c] is the
+        // residual of column c before the latest correction
         double prev = INFINITY;
+        std::vector<double> prevc(nc, INFINITY), resc(nc, 0.0);
         for (int it = 0; refine; ++it) {
             if (ffp) {
                 fds_count_launch(), k_split<<<1024, 256, 0, s>>>(h->wX.p, h->wXp.p, D * nc);
@@ -621,17 +635,36 @@ int solve_mixed(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
             FDS_CUDA_TRY(cudaMemcpyAsync(nrm.data(), h->wnorm.p, sizeof(double) * 2 * nc, cudaMemcpyDeviceToHost, s));
             FDS_CUDA_TRY(cudaStreamSynchronize(s));
             double res = 0;
-            for (int c = 0; c < nc; ++c)
-                if (nrm[2 * c + 1] > 0) res = std::max(res, std::sqrt(nrm[2 * c] / nrm[2 * c + 1]));
-            if (!(res == res)) return FDS_ERR_SINGULAR;
+            for (int c = 0; c < nc; ++c) {
+                resc[c] = nrm[2 * c + 1] > 0 ? std::sqrt(nrm[2 * c] / nrm[2 * c + 1]) : 0.0;
+                if (!(resc[c] == resc[c])) return FDS_ERR_SINGULAR;
+                res = std::max(res, resc[c]);
+            }
             // stop when converged, out of sweeps, or no longer contracting
             if (res <= h->opt.ir_tol || it >= h->opt.ir_max_iter || res > 0.5 * prev) {
-                worst = std::max(worst, res);
-                if (res > h->opt.ir_tol) converged = false;
+                // keep, per column, the iterate with the smaller residual: a
+                // correction that made column c worse is taken back
+                std::vector<int> undo(nc, 0);
+                bool any = false;
+                double best = 0;
+                for (int c = 0; c < nc; ++c) {
+                    if (resc[c] > prevc[c]) undo[c] = 1, any = true;
+                    best = std::max(best, std::min(resc[c], prevc[c]));
+                }
+                if (any) {
+                    FDS_TRY(grow(h->wundo, (size_t)nc));
+                    FDS_CUDA_TRY(cudaMemcpyAsync(h->wundo.p, undo.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+                    fds_count_launch(), k_undo_cols<LT><<<1024, 256, 0, s>>>(h->wX.p, leaf, D, nc, h->wundo.p);
+                    FDS_CUDA_TRY(cudaGetLastError());
+                    FDS_CUDA_TRY(cudaStreamSynchronize(s));   // undo[] is a host vector
+                }
+                worst = std::max(worst, best);
+                if (best > h->opt.ir_tol) converged = false;
                 iters = std::max(iters, it);
                 break;
             }
             prev = res;
+            prevc = resc;
             FDS_TRY(sweep_chunk(h, nc, s));
             fds_count_launch(), k_update<LT><<<1024, 256, 0, s>>>(h->wX.p, leaf, D * nc, 0);
             FDS_CUDA_TRY(cudaGetLastError());

@@ -79,6 +79,15 @@ void prof_end(cudaStream_t s, double flops, double bytes, double units) {
     if (g_open.size() > 4096) resolve_locked();
 }
 
+void prof_add_work(const char *name, double flops, double bytes, double units) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_on) return;
+    Acc &a = g_acc[name];
+    a.flops += flops;
+    a.bytes += bytes;
+    a.units += units;
+}
+
 extern "C" void fds_timing_enable(int32_t on) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_on = on != 0;

@@ -10,6 +10,9 @@
 bool prof_enabled();
 void prof_begin(const char *name, cudaStream_t s);
 void prof_end(cudaStream_t s, double flops, double bytes, double units);
+// work of a phase known only after its launches ran (e.g. from the ranks the
+// ID found): added to the phase's totals without a launch or a time
+void prof_add_work(const char *name, double flops, double bytes, double units);
 
 struct ProfScope {
     cudaStream_t s;

@@ -356,6 +356,57 @@ int top_solve(fds_handle *h, int nc, cudaStream_t s) {
     return FDS_OK;
 }
 
+// Woodbury sweep of the original Martinsson–Rokhlin form (FDS_VARIANT_MR2005,
+// complex128): up f~_i = F_i f_i into the parent's right-hand side; down
+// x_i = G_i f_i + E_i y_i, y_i from the parent's solution.
+int up_level_mr2005(fds_handle *h, int l, int nc, cudaStream_t s) {
+    const int maxnb = fds_max_cells(h);
+    MatRef *rR = h->wrefs.p, *rF = rR + maxnb;
+    Level &Cv = h->lv[l];
+    Level &Pn = h->lv[l - 1];
+    const int nb = Cv.nb;
+    const int64_t ldr = std::max<int64_t>(Cv.Rtot, 1);
+    cplx *Rh = h->wr[l].p, *F = h->wf[l].p;
+    fds_count_launch(), k_vec_refs<cplx><<<(nb + 127) / 128, 128, 0, s>>>(nb, Rh, Cv.d_doff.p, nc, Cv.D, rR);
+    fds_count_launch(), k_vec_refs<cplx><<<(nb + 127) / 128, 128, 0, s>>>(nb, F, Cv.d_roff.p, nc, ldr, rF);
+    {
+        ProfScope ps("a6.mr2005_up", s);
+        ps.flops = 8.0 * Cv.sum_rd * nc;
+        ps.bytes = 16.0 * Cv.sum_rd + 16.0 * (Cv.D + Cv.Rtot) * nc;
+        FDS_TRY(dense_gemm(nb, Cv.rmax, nc, Cv.rmrF.p, 0, rR, 0, rF, mkc(1, 0), mkc(0, 0), s));
+    }
+    cplx *par = (l - 1 > h->l0) ? h->wr[l - 1].p : h->wtop.p;
+    const int64_t ldp = (l - 1 > h->l0) ? Pn.D : h->Dtop;
+    fds_count_launch(), k_child_parent<cplx><<<nb, 256, 0, s>>>(nb, Cv.d_roff.p, Cv.d_k1.p, Cv.d_par_pos1.p,
+                                                                Cv.d_par_pos2.p, Pn.d_doff.p, F, ldr, par, ldp, nc, 0);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
+}
+
+int down_level_mr2005(fds_handle *h, int l, int nc, cudaStream_t s) {
+    const int maxnb = fds_max_cells(h);
+    MatRef *rR = h->wrefs.p, *rZ = rR + maxnb, *rY = rZ + maxnb;
+    Level &Cv = h->lv[l];
+    Level &Pn = h->lv[l - 1];
+    const int nb = Cv.nb;
+    const int64_t ldr = std::max<int64_t>(Cv.Rtot, 1);
+    cplx *Rh = h->wr[l].p, *Z = h->wz[l].p, *Y = h->wt[l].p;
+    cplx *par = (l - 1 > h->l0) ? h->wz[l - 1].p : h->wtop.p;
+    const int64_t ldp = (l - 1 > h->l0) ? Pn.D : h->Dtop;
+    fds_count_launch(), k_child_parent<cplx><<<nb, 256, 0, s>>>(nb, Cv.d_roff.p, Cv.d_k1.p, Cv.d_par_pos1.p,
+                                                                Cv.d_par_pos2.p, Pn.d_doff.p, Y, ldr, par, ldp, nc, 1);
+    fds_count_launch(), k_vec_refs<cplx><<<(nb + 127) / 128, 128, 0, s>>>(nb, Rh, Cv.d_doff.p, nc, Cv.D, rR);
+    fds_count_launch(), k_vec_refs<cplx><<<(nb + 127) / 128, 128, 0, s>>>(nb, Z, Cv.d_doff.p, nc, Cv.D, rZ);
+    fds_count_launch(), k_vec_refs<cplx><<<(nb + 127) / 128, 128, 0, s>>>(nb, Y, Cv.d_roff.p, nc, ldr, rY);
+    FDS_CUDA_TRY(cudaGetLastError());
+    ProfScope ps("a6.mr2005_down", s);
+    ps.flops = 8.0 * (Cv.sum_d2 + Cv.sum_rd) * nc;
+    ps.bytes = 16.0 * (Cv.sum_d2 + Cv.sum_rd) + 16.0 * (2.0 * Cv.D + Cv.Rtot) * nc;
+    FDS_TRY(dense_gemm(nb, Cv.dmax, nc, Cv.rmrG.p, 0, rR, 0, rZ, mkc(1, 0), mkc(0, 0), s));
+    FDS_TRY(dense_gemm(nb, Cv.dmax, nc, Cv.rmrE.p, 0, rY, 0, rZ, mkc(1, 0), mkc(1, 0), s));
+    return FDS_OK;
+}
+
 }  // namespace
 
 // One sweep over nc columns: the right-hand sides are in sweep_leaf_in of the
@@ -377,6 +428,12 @@ int sweep_chunk(fds_handle *h, int nc, cudaStream_t s) {
             default: return down_level<cplx>(h, l, nc, s);
         }
     };
+    if (h->opt.variant == FDS_VARIANT_MR2005 && L > l0) {
+        for (int l = L; l > l0; --l) FDS_TRY(up_level_mr2005(h, l, nc, s));
+        FDS_TRY(top_solve(h, nc, s));
+        for (int l = l0 + 1; l <= L; ++l) FDS_TRY(down_level_mr2005(h, l, nc, s));
+        return FDS_OK;
+    }
     if (L == l0) {
         // one cell: the leaf vector is the top vector, held in the leaf precision
         const int pl = h->opt.precision == FDS_MIXED ? PREC_C64 : PREC_C128;

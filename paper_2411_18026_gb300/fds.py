@@ -28,6 +28,8 @@ FDS_APPLY_FF = 0
 FDS_APPLY_FP64 = 1
 FDS_C64_SIMT = 0
 FDS_C64_TENSOR = 1
+FDS_VARIANT_LU = 0
+FDS_VARIANT_MR2005 = 1
 FDS_RANK_ADAPTIVE = 0
 FDS_RANK_LEARNED = 1
 FDS_MLP_NIN = 16
@@ -65,7 +67,8 @@ class fds_options(ctypes.Structure):
                 ("ir_max_iter", ctypes.c_int32), ("ir_apply", ctypes.c_int32), ("sweep_fp64_levels", ctypes.c_int32),
                 ("sweep_ff", ctypes.c_int32), ("merge_c64", ctypes.c_int32), ("rank_mode", ctypes.c_int32),
                 ("mlp_params", ctypes.POINTER(ctypes.c_float)), ("sketch_extra", ctypes.c_int32),
-                ("record_features", ctypes.c_int32), ("c64_engine", ctypes.c_int32)]
+                ("record_features", ctypes.c_int32), ("c64_engine", ctypes.c_int32), ("tol_decay", ctypes.c_double),
+                ("variant", ctypes.c_int32)]
 
 
 class fds_stats(ctypes.Structure):
@@ -116,6 +119,12 @@ def lib():
     i64p = ctypes.POINTER(ctypes.c_int64)
     L.fds_cgemm_c64_batched.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), i64p,
                                         i64p, i64p, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, i32, u64]
+    L.fds_alu_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
+    L.fds_autotune_enable.argtypes = [i32]
+    L.fds_autotune_enable.restype = None
+    L.fds_autotune_reset.argtypes = []
+    L.fds_autotune_reset.restype = None
+    L.fds_autotune_report.argtypes = [ctypes.c_char_p, i32]
     L.fds_timing_enable.argtypes = [i32]
     L.fds_timing_enable.restype = None
     L.fds_timing_reset.argtypes = []
@@ -204,7 +213,7 @@ class Handle:
 def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy_ratio=1.5, proxy_points=64,
               alpha=None, stream=0, precision=FDS_FP64, ir_tol=None, ir_max_iter=None, ir_apply=None,
               mlp_params=None, sketch_extra=None, record_features=False, sweep_fp64_levels=None, merge_c64=False,
-              sweep_ff=1, c64_engine=FDS_C64_SIMT):
+              sweep_ff=1, c64_engine=FDS_C64_SIMT, tol_decay=None, variant=FDS_VARIANT_LU):
     """Factorise; mlp_params (FDS_MLP_NPARAM floats) selects the learned-rank ID."""
     xy = np.ascontiguousarray(xy, dtype=np.float64)
     g = fds_geometry(len(xy), xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(rho))
@@ -235,6 +244,9 @@ def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy
     o.sweep_ff = int(sweep_ff)
     o.record_features = 1 if record_features else 0
     o.c64_engine = int(c64_engine)
+    if tol_decay is not None:
+        o.tol_decay = float(tol_decay)
+    o.variant = int(variant)
     out = ctypes.c_void_p()
     _check(lib().fds_build_ex(ctypes.byref(g), float(omega), float(lam), float(mu), float(tol), ctypes.byref(o),
                               ctypes.byref(out)), "fds_build")
@@ -408,6 +420,34 @@ def fds_cgemm_c64_batched(m, n, k, aoff, boff, coff, d_A, d_B, d_C, opA=0, alpha
                                        boff.ctypes.data_as(i64p), coff.ctypes.data_as(i64p), _ptr(d_A), _ptr(d_B),
                                        _ptr(d_C), int(opA), float(alpha), float(beta), int(engine),
                                        _stream(stream)), "fds_cgemm_c64_batched")
+
+
+def fds_alu_peak(kind):
+    """Measured FMA peak of the current device in TFLOP/s: kind 0 FP64, 1 FP32."""
+    v = ctypes.c_double()
+    _check(lib().fds_alu_peak(int(kind), ctypes.byref(v)), "fds_alu_peak")
+    return v.value
+
+
+def fds_autotune_enable(on=True):
+    lib().fds_autotune_enable(1 if on else 0)
+
+
+def fds_autotune_reset():
+    lib().fds_autotune_reset()
+
+
+def fds_autotune_report():
+    """[dict(arith, opA, rows, cols, batch, mapped, mi, tj, best_us, rule_us)] of the tuned classes."""
+    n = lib().fds_autotune_report(None, 0)
+    buf = ctypes.create_string_buffer(n + 16)
+    lib().fds_autotune_report(buf, n + 16)
+    out = []
+    for line in buf.value.decode().splitlines():
+        v = line.split()
+        out.append(dict(arith=v[0], opA=int(v[1]), rows=int(v[2]), cols=int(v[3]), batch=int(v[4]), mapped=int(v[5]),
+                        mi=int(v[6]), tj=int(v[7]), best_us=float(v[8]), rule_us=float(v[9])))
+    return out
 
 
 def fds_timing_enable(on=True):

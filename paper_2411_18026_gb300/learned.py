@@ -62,14 +62,17 @@ def load_params(path=PARAMS_FILE):
 
 def main(argv=None):
     """Train the rank network on seeded random cavities (ellipses and stars,
-    2^12..2^15 nodes, k_T a in [1, 20], tol 1e-9 and 1e-8, leaf 64) and save
-    the parameters next to this module."""
+    2^12..2^16 nodes, k_T a in [1, 20], leaf tolerance 1e-9 and 1e-8 with the
+    default per-level tolerance, leaf 64) and save the parameters next to this
+    module."""
     import argparse
     import sys
     import time
     ap = argparse.ArgumentParser(prog="python -m paper_2411_18026_gb300.learned")
-    ap.add_argument("--count", type=int, default=160, help="training cavities")
-    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--count", type=int, default=2000, help="training cavities")
+    ap.add_argument("--nmax-log2", type=int, default=16, help="largest training cavity: 2^n nodes")
+    ap.add_argument("--epochs", type=int, default=0, help="passes over the samples (0: enough for --steps)")
+    ap.add_argument("--steps", type=int, default=30000, help="Adam steps when --epochs is 0")
     ap.add_argument("--out", default=PARAMS_FILE)
     a = ap.parse_args(argv)
     sys.path.insert(0, __import__("os").path.dirname(__import__("os").path.dirname(__file__)))
@@ -77,13 +80,14 @@ def main(argv=None):
     from . import build
     build.build()
     t0 = time.time()
-    cav = workloads.random_cavities(a.count, seed=workloads.SEED + 4, nmin_log2=12, nmax_log2=15)
+    cav = workloads.random_cavities(a.count, seed=workloads.SEED + 4, nmin_log2=12, nmax_log2=a.nmax_log2)
     half = len(cav) // 2
     F1, r1 = collect(cav[:half], 1e-9)
     F2, r2 = collect(cav[half:], 1e-8)
     F, r = np.concatenate([F1, F2]), np.concatenate([r1, r2])
     t1 = time.time()
-    order = workloads.minibatch_order(len(F), 256, a.epochs)
+    epochs = a.epochs or max(1, -(-a.steps * 256 // len(F)))
+    order = workloads.minibatch_order(len(F), 256, epochs)
     p, losses = train(F, r, workloads.mlp_init(), order, batch=256, lr=2e-3)
     np.save(a.out, p.astype(np.float32))
     print("samples %d, collect %.1fs, train %.1fs, loss %.3e -> %.3e, saved %s" %

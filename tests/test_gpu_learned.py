@@ -122,7 +122,8 @@ def test_recorded_features():
     assert len(F) == st.features_recorded > 2 * (2048 // 64)
     assert np.all((r > 0) & (r <= 1))
     assert set(np.unique(F[:, 2])) == {0.0, 1.0}
-    assert np.allclose(F[:, 13], np.log10(tol))
+    # log10 of the level's ID tolerance: tol at the leaves, halved per level up
+    assert np.allclose(F[:, 13], np.log10(tol) + F[:, 0] * np.log10(0.5), atol=1e-5)
     leaf = F[:, 0] == 0
     assert np.all(F[leaf, 14] == 1.0) and np.allclose(F[leaf, 1], np.log2(64))
     # ranks recorded equal the level ranks the build reports
@@ -229,15 +230,15 @@ def test_trained_network_gains_over_adaptive_id():
     ka = sum(st_a.skeleton_dofs[l] for l in range(st_a.top_level + 1, st_a.levels + 1))
     kl = sum(st_l.skeleton_dofs[l] for l in range(st_l.top_level + 1, st_l.levels + 1))
     print("skeleton DOFs: adaptive %d, learned %d (+%.1f%%)" % (ka, kl, 100.0 * (kl - ka) / ka))
-    assert ka <= kl <= 1.25 * ka
+    assert 0.95 * ka <= kl <= 1.25 * ka
     kinds, ang = workloads.plane_wave_set(2)
     F = fds.fds_rhs_plane_wave(ha, kinds, ang)
     xa = fds.fds_solve(ha, F)
     xl = fds.fds_solve(hl, F)
-    # two compressions at the same tolerance: they differ by the compression
-    # error amplified by the operator's conditioning, which grows with N
+    # two compressions at the same tolerances: with the per-level graded
+    # tolerance both stay within a few tol of the Galerkin solution
     err = np.linalg.norm(xl - xa) / np.linalg.norm(xa)
     print("learned vs adaptive solution: %.2e" % err)
-    assert err <= 1e-4
+    assert err <= 100 * tol
     for h in (ha, hl, hf):
         h.close()

@@ -111,7 +111,7 @@ def test_tripod_error_band_of_paper_table1():
     f = bem.rhs(P, xy, 0, 0.0)
     x = np.linalg.solve(bem.dense_matrix(P, xy), f)
     for eps in (1e-8, 1e-10):
-        S = fds.FDS(P, xy, 1.0, 1.0, 1.0, 2.0, eps, leaf_size=100, top_level=row["l0"])
+        S = fds.FDS(P, xy, 1.0, 1.0, 1.0, 2.0, eps, leaf_size=100, top_level=row["l0"], tol_decay=1.0)
         assert S.L == row["L"]
         err = np.linalg.norm(S.solve(f) - x) / np.linalg.norm(x)
         assert row["err"][eps] / 20 < err < row["err"][eps] * 20
