@@ -5,8 +5,8 @@ Calls only the oracle ("Conv" of Sec. 8: dense Galerkin assembly of
 A = D + I_0/2 + alpha N and partial-pivot LU, Sec. 4) on seeded star cavities
 r = 1 + 0.2 cos 5t (lambda = 2, mu = 1, rho = 1) with one plane P wave
 (angle 0.3) and one plane SV wave (angle 1.9).  Output per case:
-dense_star_N<nodes>_kta<kTa>.npz with F (load vectors, 2N x 2) and x (the
-dense solution, 2N x 2), complex128.
+dense_star_N<nodes>_kta<kTa>.npz with x, the dense solution (2N x 2,
+complex128) for the load vectors F = load_vectors(N, kTa).
 
 python tests/golden/make_dense.py [N:kTa ...]    (default: the four cases)
 """
@@ -31,14 +31,20 @@ def path(N, kta):
     return os.path.join(HERE, "dense_star_N%d_kta%d.npz" % (N, int(kta)))
 
 
+def load_vectors(N, kta):
+    """The oracle's Galerkin load vectors of the two waves (2N x 2)."""
+    P = bem.phys(2.0, 1.0, 1.0, workloads.omega_for_kTa(kta))
+    xy = workloads.star(N)
+    return np.stack([bem.rhs(P, xy, k, a) for k, a in WAVES], 1)
+
+
 def make(N, kta):
     xy = workloads.star(N)
-    omega = workloads.omega_for_kTa(kta)
-    P = bem.phys(2.0, 1.0, 1.0, omega)
-    F = np.stack([bem.rhs(P, xy, k, a) for k, a in WAVES], 1)
+    P = bem.phys(2.0, 1.0, 1.0, workloads.omega_for_kTa(kta))
+    F = load_vectors(N, kta)
     t = time.time()
     x = bem.dense_solve(P, xy, F)
-    np.savez(path(N, kta), F=F, x=x)
+    np.savez(path(N, kta), x=x)
     print("N=%d kTa=%g: %.1f s" % (N, kta, time.time() - t), flush=True)
 
 
