@@ -7,15 +7,15 @@ vectors of all incident waves, and the multi-RHS solve sweep.
 
 Default workload (the configuration the metric is quoted on): star cavity
 r(t) = 1 + 0.2 cos 5t with 2^19 nodes (2^20 complex unknowns), lambda = 2,
-mu = 1, rho = 1, k_T a = 20, leaf 64, l0 = 1, 1000 right-hand sides (plane P
-and SV waves at 500 angles), mixed precision (complex64 sweep of the lower
+mu = 1, rho = 1, k_T a = 20, leaf 64, l0 = 1, ID tolerance 1e-9 at the leaves
+and halved per level up, 1000 right-hand sides (plane P and SV waves at 500
+angles), learned rank (the trained network sizes a sketched ID, adaptive
+CPQR as fallback), mixed precision (complex64 merges and sweep of the lower
 tree levels, double-float sweep of the upper ones, refined against the FP64
-compressed operator to
-max_c ||f - A x|| / ||f|| <= 1e-8), adaptive ID (`--rank learned` selects
-the trained rank network, `python -m paper_2411_18026_gb300.learned`).  After the
-timed steps one plain-FP64 step runs on the same inputs: its build and solve
-times and the relative error between the two solutions are reported beside
-the headline.  The working set (factors, vectors) is far larger than L2, so no
+compressed operator to max_c ||f - A x|| / ||f|| <= 1e-8).  After the timed
+steps one plain-FP64 step (adaptive CPQR, FP64 merges and sweep) runs on the
+same inputs: its build and solve times and the relative error between the
+two solutions are reported beside the headline.  The working set (factors, vectors) is far larger than L2, so no
 explicit flush is needed between steps.
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
@@ -56,23 +56,34 @@ def parse():
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--ir-tol", type=float, default=1e-8)
     p.add_argument("--sweep-fp64-levels", type=int, default=-1)
-    p.add_argument("--merge-c64", action="store_true", help="merge the complex64 levels in complex64")
+    p.add_argument("--merge", default="c64", choices=["c64", "fp64"],
+                   help="mixed: merge the complex64 levels in complex64 (default) or FP64")
+    p.add_argument("--tol-decay", type=float, default=0.5,
+                   help="ID tolerance eps at the leaves, eps * decay^(L-l) at level l (1: the paper's single eps)")
+    p.add_argument("--autotune", action="store_true", help="GEMM tile shapes from the autotuner (tuned in warm-up)")
     p.add_argument("--c64-engine", default="simt", choices=["tensor", "simt"],
                    help="complex64 products on the tensor cores (bf16 pieces) or the FP32 pipe")
     p.add_argument("--sweep-ff", type=int, default=1, choices=[0, 1, 2],
                    help="mixed sweep: 1 double-float upper levels, 2 double-float everywhere")
-    p.add_argument("--rank", default="adaptive", choices=["learned", "adaptive"],
-                   help="learned: the trained rank network (falls back to adaptive if it has not been trained); "
-                        "its skeletons differ from the plain solver's, so its error against the plain FP64 "
-                        "solve is the compression error amplified by the operator's conditioning")
-    p.add_argument("--workload", default="star", choices=["star", "batch64", "cgemm", "field"],
+    p.add_argument("--rank", default="learned", choices=["learned", "adaptive"],
+                   help="learned (default): the trained rank network sizes a sketched ID, with the adaptive "
+                        "CPQR as fallback; adaptive: the CPQR alone.  The plain FP64 comparison step always "
+                        "uses the adaptive CPQR")
+    p.add_argument("--workload", default="star", choices=["star", "batch64", "cgemm", "field", "omega", "mr2005"],
                    help="star: the 2^19-node star cavity (default); batch64: 64 seeded cavities of "
                         "2^12-2^15 nodes, k_T a in [1, 20], 16 waves each, built and solved as one batch; "
                         "cgemm: the batched complex64 GEMM stage alone (--gemm-batch products of "
                         "128 x 128 by 128 x --nrhs, the leaf shape of the sweep) on both engines; "
                         "field: the displacement off the boundary (eq. integ_rep) at --field-points points "
-                        "for 16 waves of the star cavity")
+                        "for 16 waves of the star cavity, direct and proxy-compressed; "
+                        "omega: the tripod of Sec. 8 swept over omega with and without the Burton-Miller term "
+                        "(wave intensity at (1, 0), Fig. wave_intensity; time per omega, Fig. omega_time); "
+                        "mr2005: build and solve of the LU variant against the Woodbury form of the original "
+                        "Martinsson-Rokhlin method (FP64, the default star cavity)")
     p.add_argument("--field-points", type=int, default=64, help="field: observation points")
+    p.add_argument("--omega-nodes", type=int, default=6400, help="omega: tripod nodes")
+    p.add_argument("--omega-max", type=float, default=40.0, help="omega: largest angular frequency")
+    p.add_argument("--omega-step", type=float, default=0.05, help="omega: frequency step")
     p.add_argument("--gemm-batch", type=int, default=8192, help="cgemm: number of products")
     p.add_argument("--streams", type=int, default=8, help="batch64: concurrent cavity streams")
     p.add_argument("--no-compare", action="store_true",
@@ -164,6 +175,16 @@ def peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def phase_on_fp32(name, precision):
+    """Whether a phase's arithmetic runs on the FP32 pipe: the mixed solve's
+    sweep levels (complex64 and double-float) and the refinement's
+    double-float forward operator; everything else (quadrature, CPQR, merges,
+    top LU and top solve) is FP64."""
+    if precision != "mixed":
+        return False
+    return (name.startswith("a6.") and name != "a6.top_solve") or name.startswith("a7.")
 
 
 # ---------------------------------------------------------------- oracle (CPU)
@@ -291,19 +312,24 @@ def run_field(args, fds, torch, rank):
     rng = np.random.default_rng(7 + rank)
     r, th = rng.uniform(1.5, 3.0, npts), rng.uniform(0, 2 * np.pi, npts)
     pts = np.stack([r * np.cos(th), r * np.sin(th)], 1)
-    for _ in range(args.warmup):
-        fds.fds_field(h, d, kinds, angles, pts)
-    ts = []
-    for _ in range(args.steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record()
-        fds.fds_field(h, d, kinds, angles, pts)
-        e1.record()
-        torch.cuda.synchronize()
-        ts.append(e0.elapsed_time(e1))
+    def timed(compressed):
+        for _ in range(args.warmup):
+            fds.fds_field(h, d, kinds, angles, pts, compressed=compressed)
+        ts = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            out = fds.fds_field(h, d, kinds, angles, pts, compressed=compressed)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts)), out
+
+    ms, ref = timed(False)
+    ms_c, got = timed(True)
+    err_c = float(np.abs(got - ref).max() / np.abs(ref).max())
     h.close()
-    ms = float(np.median(ts))
     sums = float(npts) * N * len(kinds)
     if rank == 0:
         print(json.dumps({"metric": "field off the boundary (eq. integ_rep): quadrature sums per second",
@@ -311,7 +337,109 @@ def run_field(args, fds, torch, rank):
                           "warmup": args.warmup, "higher_is_better": True, "data": "synthetic",
                           "config": {"workload": "star r=1+0.2cos5t, %d nodes, k_T a=%g, %d waves, %d points, "
                                                  "8 Gauss points per element, direct summation"
-                                                 % (N, args.kta, len(kinds), npts)}}))
+                                                 % (N, args.kta, len(kinds), npts)},
+                          "compressed": {"ms": ms_c, "speedup_vs_direct": ms / ms_c,
+                                         "max_rel_diff_vs_direct": err_c,
+                                         "note": "tree skeletons as equivalent sources (fds_field_compressed); "
+                                                 "same points and waves"}}))
+
+
+def run_omega(args, fds, torch, rank):
+    """The tripod of Sec. 8 (lambda = mu = 1, rho = 1, leaf 100, l0 = 1,
+    eps 1e-8) swept over omega = step .. --omega-max: each omega is built and
+    solved with the Burton-Miller formulation (the solver's default alpha) and
+    without it (alpha = 0, eq. bie_non_bie) for one plane P wave at angle 0;
+    the wave intensity |u_1|^2 + |u_2|^2 at x = (1, 0), which is node 0 of the
+    tripod, is recorded for both (Fig. wave_intensity), and the device time of
+    build + solve per omega (Fig. omega_time)."""
+    import workloads
+    N = args.omega_nodes
+    xy = workloads.tripod(N)
+    ws = np.arange(args.omega_step, args.omega_max + 0.5 * args.omega_step, args.omega_step)
+    kinds, angles = np.array([0], np.int32), np.array([0.0])
+    out = {"bm": [], "non_bm": [], "ms_bm": []}
+    for _ in range(args.warmup):
+        h = fds.fds_build(xy, float(ws[0]), 1.0, 1.0, 1e-8, leaf_size=100, top_level=1)
+        h.close()
+    t0 = time.perf_counter()
+    for w in ws:
+        for name, alpha in (("bm", None), ("non_bm", 0.0)):
+            h = fds.fds_build(xy, float(w), 1.0, 1.0, 1e-8, leaf_size=100, top_level=1, alpha=alpha,
+                              tol_decay=args.tol_decay)
+            x = fds.fds_solve(h, fds.fds_rhs_plane_wave(h, kinds, angles))
+            st = fds.fds_stats_get(h)
+            h.close()
+            out[name].append(float(abs(x[0, 0]) ** 2 + abs(x[N, 0]) ** 2))
+            if name == "bm":
+                out["ms_bm"].append(st.build_ms + st.solve_ms)
+    wall = time.perf_counter() - t0
+    bm, nb = np.array(out["bm"]), np.array(out["non_bm"])
+    dev = np.abs(nb - bm) / bm
+    # a spike: the non-BM intensity more than 10% off the BM one
+    spikes = [round(float(w), 3) for w, d in zip(ws, dev) if d > 0.1]
+    # smoothness of the BM curve: largest jump relative to its neighbours' mean
+    mid = 0.5 * (bm[:-2] + bm[2:])
+    bm_jump = float(np.max(np.abs(bm[1:-1] - mid) / mid)) if len(bm) > 2 else 0.0
+    ms = np.array(out["ms_bm"])
+    if rank == 0:
+        print(json.dumps({"metric": "omega sweep: build + solve per omega (tripod, Sec. 8.4)",
+                          "value": float(np.median(ms)), "unit": "ms", "higher_is_better": False,
+                          "data": "synthetic", "warmup": args.warmup, "wall_s": wall,
+                          "config": {"workload": "tripod (Sec. 8, Fig. tripod), %d nodes, lambda=mu=1, rho=1, leaf 100, "
+                                                 "l0=1, eps 1e-8, tol_decay %g, one plane P wave at 0, omega %g..%g "
+                                                 "step %g" % (N, args.tol_decay, ws[0], ws[-1], args.omega_step)},
+                          "ms_per_omega_by_range": {"%g-%g" % (a, b): float(np.median(ms[(ws >= a) & (ws < b)]))
+                                                    for a, b in ((0, 10), (10, 20), (20, 30), (30, 41))
+                                                    if np.any((ws >= a) & (ws < b))},
+                          "non_bm_spikes": spikes, "non_bm_spike_count": len(spikes),
+                          "max_rel_dev_non_bm_vs_bm": float(dev.max()),
+                          "bm_max_rel_jump": bm_jump,
+                          "omega": [round(float(w), 4) for w in ws],
+                          "intensity_bm": [float("%.6g" % v) for v in bm],
+                          "intensity_non_bm": [float("%.6g" % v) for v in nb]}))
+
+
+def run_mr2005(args, fds, torch, rank):
+    """The paper's LU-based variant against the Woodbury form of the original
+    Martinsson-Rokhlin method (FDS_VARIANT_MR2005), both plain FP64 on the
+    default star cavity: build time, the build's matrix-matrix work (flops of
+    the merge phases), per-RHS solve time, and the relative difference of the
+    two solutions (same skeletons: rounding only)."""
+    import workloads
+    xy = workloads.star(args.nodes)
+    omega = workloads.omega_for_kTa(args.kta)
+    kinds, angles = workloads.plane_wave_set(args.nrhs // 2)
+    res, sols = {}, {}
+    for name, var in (("lu", fds.FDS_VARIANT_LU), ("mr2005", fds.FDS_VARIANT_MR2005)):
+        for it in range(args.warmup + 1):
+            fds.fds_timing_reset()
+            fds.fds_timing_enable(it == args.warmup)
+            h = fds.fds_build(xy, omega, 2.0, 1.0, args.eps, leaf_size=args.leaf, top_level=args.top,
+                              tol_decay=args.tol_decay, variant=var)
+            d = torch.empty((len(kinds), 2 * args.nodes), dtype=torch.complex128, device="cuda")
+            fds.fds_rhs_plane_wave_device(h, torch.from_numpy(kinds).cuda(), torch.from_numpy(angles).cuda(), d)
+            fds.fds_solve_device(h, d)
+            torch.cuda.synchronize()
+            fds.fds_timing_enable(False)
+            st = fds.fds_stats_get(h)
+            h.close()
+        rep = fds.fds_timing_report()
+        res[name] = {"build_s": st.build_ms / 1e3, "per_rhs_us": st.solve_ms * 1e3 / len(kinds),
+                     "factor_gb": st.factor_bytes / 1e9,
+                     "merge_gflop": sum(v["flops"] for k, v in rep.items() if k.startswith("a3.")) / 1e9,
+                     "merge_ms": sum(v["ms"] for k, v in rep.items() if k.startswith("a3.")),
+                     "sweep_gflop": sum(v["flops"] for k, v in rep.items() if k.startswith("a6.")) / 1e9}
+        sols[name] = d
+    err = (torch.linalg.vector_norm(sols["mr2005"] - sols["lu"], dim=1) /
+           torch.linalg.vector_norm(sols["lu"], dim=1)).max().item()
+    if rank == 0:
+        print(json.dumps({"metric": "LU variant vs Woodbury (MR2005) form: build s, merge GFLOP, per-RHS us",
+                          "value": res["mr2005"]["build_s"] / res["lu"]["build_s"], "unit": "build time ratio "
+                          "MR2005 / LU", "higher_is_better": False, "data": "synthetic", "warmup": args.warmup,
+                          "config": {"workload": "star r=1+0.2cos5t, %d nodes, k_T a=%g, eps %g, tol_decay %g, "
+                                                 "leaf %d, %d waves, FP64" % (args.nodes, args.kta, args.eps,
+                                                                              args.tol_decay, args.leaf, len(kinds))},
+                          "lu": res["lu"], "mr2005": res["mr2005"], "max_rel_diff": err}))
 
 
 def run_batch(args, fds, torch, world, rank, local):
@@ -401,6 +529,14 @@ def main():
     if args.workload == "field":
         run_field(args, fds, torch, rank)
         return
+    if args.workload == "omega":
+        run_omega(args, fds, torch, rank)
+        return
+    if args.workload == "mr2005":
+        run_mr2005(args, fds, torch, rank)
+        return
+    if args.autotune:
+        fds.fds_autotune_enable(True)
 
     xy, omega, kinds, angles = workload(args, rank)
     N = len(xy)
@@ -420,7 +556,8 @@ def main():
     def step(precision=prec, out=d_F, rec=info, params=mlp):
         h = fds.fds_build(xy, omega, 2.0, 1.0, args.eps, leaf_size=args.leaf, top_level=args.top, stream=stream,
                           precision=precision, ir_tol=args.ir_tol, sweep_fp64_levels=args.sweep_fp64_levels,
-                          mlp_params=params, merge_c64=args.merge_c64 and precision == fds.FDS_MIXED,
+                          mlp_params=params, merge_c64=args.merge == "c64" and precision == fds.FDS_MIXED,
+                          tol_decay=args.tol_decay,
                           sweep_ff=args.sweep_ff if precision == fds.FDS_MIXED else 0,
                           c64_engine=c64_engine)
         fds.fds_rhs_plane_wave_device(h, d_kinds, d_angles, out, stream)
@@ -443,6 +580,9 @@ def main():
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # roofline denominators of the FP64 and FP32 phases, measured on this GPU
+    alu_peaks = {"fp64_tflops": fds.fds_alu_peak(0), "fp32_tflops": fds.fds_alu_peak(1),
+                 "sms": torch.cuda.get_device_properties(local).multi_processor_count}
     fds.fds_timing_reset()
     fds.fds_timing_enable(True)
     clocks = ClockSampler(local)
@@ -506,7 +646,8 @@ def main():
         o = fds.default_options()
         o.leaf_size, o.top_level = args.leaf, args.top
         o.precision, o.ir_tol, o.sweep_fp64_levels = prec, args.ir_tol, args.sweep_fp64_levels
-        o.merge_c64 = 1 if args.merge_c64 else 0
+        o.merge_c64 = 1 if args.merge == "c64" and prec == fds.FDS_MIXED else 0
+        o.tol_decay = args.tol_decay
         o.sweep_ff = args.sweep_ff
         o.c64_engine = c64_engine
         mlp32 = None
@@ -533,33 +674,49 @@ def main():
 
     # FP64 flops and DRAM bytes per quadrature point of the kernel-evaluation
     # kernels, from ncu counters (dfma x 2 + dmul + dadd; dram read + write)
-    # over all launches of one 2^14-node build of the same cavity
-    # (profiles/k_tiles_fp64_ops_star_2p14.md)
+    # over the launches of one 2^14-node build of the same cavity: executed
+    # FP64 operations of the evaluator, so the fraction below is the FP64
+    # pipe's use by the quadrature
     A1_PER_POINT = {"a1.leaf_blocks": (475.0, 0.66), "a1.near_rows": (493.0, 1.54), "a1.proxy_rows": (493.0, 1.54),
                     "a1.sibling_blocks": (509.0, 0.18), "a1.top_blocks": (509.0, 0.18)}
     pk, src = peaks()
-    sm_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    # FP64 peak of the GB300: 152 SMs x 2 FP64 FMA/clk (4 flops) x SM clock
-    fp64_peak_tflops = 152 * 4 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    dom = max(phases.items(), key=lambda kv: kv[1]["ms"]) if phases else None
-    roof = None
-    if dom:
-        name, d = dom
+    alu = alu_peaks
+    roof, per_phase = None, {}
+    for name, d in sorted(phases.items()):
+        if d["ms"] <= 0:
+            continue
         launches_ = max(d["launches"], 1)
-        avg_ms = d["ms"] / launches_
-        flops, traffic, basis = d["flops"], None, "library flop count of the phase"
+        flops, traffic, basis = d["flops"], None, "algorithmic flop count of the phase (library)"
         if name in A1_PER_POINT and d["units"] > 0:
             fpp, bpp = A1_PER_POINT[name]
             flops = d["units"] * fpp
             traffic = d["units"] * bpp / launches_
-            basis = ("quadrature points x %.0f FP64 flops per point (ncu, 2^14 case); traffic = points per launch x "
-                     "%.2f DRAM bytes per point (same capture)" % (fpp, bpp))
-        ach = flops / launches_ / (avg_ms / 1e3) / 1e12 if flops > 0 else None
-        roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                "frac": (ach / fp64_peak_tflops) if ach else None, "traffic": traffic,
-                "peak_source": "FP64: 152 SMs x 2 FP64 FMA/clk x %.0f MHz (no FP64 figure in MEASURED_PEAKS.json)"
-                               % pk.get("sm_max_mhz", 2070.0),
-                "basis": basis, "avg_launch_ms": avg_ms, "launches_per_step": d["launches"] / args.steps}
+            basis = ("quadrature points x %.0f executed FP64 flops per point (ncu, 2^14-node build); traffic = points "
+                     "per launch x %.2f DRAM bytes per point (same capture)" % (fpp, bpp))
+        fp32 = phase_on_fp32(name, args.precision)
+        peak = alu["fp32_tflops"] if fp32 else alu["fp64_tflops"]
+        ent = {"ms_per_step": d["ms"] / args.steps, "launches_per_step": d["launches"] / args.steps,
+               "bound": "alu", "pipe": "fp32" if fp32 else "fp64", "basis": basis}
+        if flops > 0:
+            ach = flops / (d["ms"] / 1e3) / 1e12
+            ent.update(achieved_tflops=ach, peak_tflops=peak, frac=ach / peak)
+        if d["bytes"] > 0:
+            gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9
+            ent.update(achieved_gbs=gbs, hbm_frac=gbs / pk["hbm_gbs"])
+            if flops <= 0 or gbs / pk["hbm_gbs"] > ent.get("frac", 0):
+                ent["bound"] = "hbm"
+        if d["units"] > 0:
+            ent["quad_points_per_s"] = d["units"] / (d["ms"] / 1e3)
+        per_phase[name] = ent
+        if roof is None or d["ms"] > roof["_ms"]:
+            roof = {"_ms": d["ms"], "kernel": name, "bound": ent["bound"], "achieved": ent.get("achieved_tflops"),
+                    "peak": peak, "unit": "TFLOP/s", "frac": ent.get("frac"), "traffic": traffic,
+                    "peak_source": "measured on this GPU before the timed steps (fds_alu_peak: FMA loop, %s pipe, "
+                                   "%d SMs)" % ("FP32" if fp32 else "FP64", alu["sms"]),
+                    "basis": basis, "avg_launch_ms": d["ms"] / launches_,
+                    "launches_per_step": d["launches"] / args.steps}
+    if roof:
+        roof.pop("_ms")
 
     cpu = None
     if not args.no_cpu:
@@ -575,12 +732,16 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "c128+c64" if args.precision == "mixed" else "c128", "data": "synthetic",
         "config": {"workload": "star r=1+0.2cos5t, %d nodes (%d complex unknowns), lambda=2 mu=1 rho=1, "
-                               "k_T a=%g, leaf %d, l0=%d, eps=%g, %d plane P/SV waves, %s"
-                               % (N, 2 * N, args.kta, args.leaf, args.top, args.eps, args.nrhs,
-                                  ("mixed precision, refined to residual %g" % args.ir_tol
-                                   if args.precision == "mixed" else "plain FP64") + ", %s rank" % rank_used),
+                               "k_T a=%g, leaf %d, l0=%d, eps=%g (leaf level; x%g per level up), %d plane P/SV "
+                               "waves, %s"
+                               % (N, 2 * N, args.kta, args.leaf, args.top, args.eps, args.tol_decay, args.nrhs,
+                                  ("mixed precision (%s merges of the complex64 levels), refined to residual %g"
+                                   % (args.merge, args.ir_tol) if args.precision == "mixed" else "plain FP64")
+                                  + ", %s rank" % rank_used),
                    "l2": "working set (factors, vectors) larger than L2; no flush",
-                   "precision": args.precision, "c64_engine": args.c64_engine},
+                   "precision": args.precision, "c64_engine": args.c64_engine, "merge": args.merge,
+                   "tol_decay": args.tol_decay, "autotune": bool(args.autotune),
+                   "fp64_reference": "plain FP64 build (adaptive CPQR, same eps and tol_decay) on the same inputs"},
         "ir_iters": info.get("ir_iters"), "ir_residual": info.get("ir_residual"),
         "ir_converged": info.get("converged"), "vs_fp64": compare, "rank_mode": rank_used,
         "id_sketched": info.get("id_sketched"), "id_fallback": info.get("id_fallback"),
@@ -588,9 +749,7 @@ def main():
         "levels": info.get("levels"), "top_size": info.get("top_size"), "factor_gb": info.get("factor_gb"),
         "skeleton_dofs": info.get("skeleton_dofs"),
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
-        "phases_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in sorted(phases.items())},
-        "phases_tflops": {k: round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 3) for k, v in sorted(phases.items())
-                          if v["flops"] > 0 and v["ms"] > 0},
+        "alu_peaks": alu, "phases_roofline": per_phase,
         "quad_points_per_step": {k: v["units"] / args.steps for k, v in sorted(phases.items()) if v["units"] > 0},
     }
     print(json.dumps(line))

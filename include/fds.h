@@ -365,6 +365,22 @@ int fds_lu_batched_noalloc(int32_t batch, const int32_t *d_d, const int64_t *d_o
  */
 int fds_field(fds_handle *h, const double *d_u, int32_t nrhs, const int32_t *kinds, const double *angles,
               const double *d_pts, int32_t npts, double *d_out, uint64_t stream);
+/*
+ * The same field with the tree's proxy compression (Sec. 3 eq. (integ_rep)
+ * evaluated through the skeletons of Sec. 7): a cell's boundary sources seen
+ * from a point outside its proxy circle are replaced by its skeleton hats
+ * with coefficients u~ = V u (recursively u~_parent = V_parent applied to the
+ * children's u~); each point sums the skeletons of the largest cells (levels
+ * l0+1 .. L) whose proxy circle it lies outside, and the hats of the leaf
+ * cells whose proxy circle holds it directly.  Work per point
+ * O(skeleton DOFs of those cells) instead of O(n).  Accuracy follows the ID
+ * tolerance of the build.  Same arguments and layout as fds_field; the
+ * points are read back to the host to choose each point's cells;
+ * synchronises the stream.  FDS_ERR_STATE if the handle has no interpolation
+ * blocks.
+ */
+int fds_field_compressed(fds_handle *h, const double *d_u, int32_t nrhs, const int32_t *kinds,
+                         const double *angles, const double *d_pts, int32_t npts, double *d_out, uint64_t stream);
 
 /*
  * Batched complex64 GEMM of the mixed-precision levels (Sec. 7.3 products in

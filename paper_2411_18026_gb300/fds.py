@@ -116,6 +116,7 @@ def lib():
     L.fds_lu_batched.argtypes = [i32, vp, vp, vp, vp, vp, vp, u64]
     L.fds_lu_batched_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, u64]
     L.fds_field.argtypes = [vp, vp, i32, ctypes.POINTER(i32), dp, vp, i32, vp, u64]
+    L.fds_field_compressed.argtypes = [vp, vp, i32, ctypes.POINTER(i32), dp, vp, i32, vp, u64]
     i64p = ctypes.POINTER(ctypes.c_int64)
     L.fds_cgemm_c64_batched.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), i64p,
                                         i64p, i64p, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, i32, u64]
@@ -390,10 +391,12 @@ def fds_lu_batched(d_d, d_off, d_A, d_piv, d_poff, d_info, stream=None):
                                 _ptr(d_info), _stream(stream)), "fds_lu_batched")
 
 
-def fds_field(h, d_u, kinds, angles, pts, stream=None):
+def fds_field(h, d_u, kinds, angles, pts, stream=None, compressed=False):
     """Displacement at points off the boundary (eq. integ_rep) from the device
     solution d_u ((nrhs, 2n) complex128 CUDA tensor) of the given waves.
-    pts: (npts, 2).  Returns (2, npts, nrhs) complex numpy."""
+    pts: (npts, 2).  compressed: through the tree's skeletons
+    (fds_field_compressed) instead of direct summation.  Returns
+    (2, npts, nrhs) complex numpy."""
     import torch
     kinds = np.ascontiguousarray(kinds, dtype=np.int32)
     angles = np.ascontiguousarray(angles, dtype=np.float64)
@@ -401,9 +404,10 @@ def fds_field(h, d_u, kinds, angles, pts, stream=None):
     d_pts = torch.tensor(np.ascontiguousarray(pts, dtype=np.float64).ravel(), device=d_u.device)
     npts = d_pts.numel() // 2
     d_out = torch.zeros((nrhs, 2 * npts), dtype=torch.complex128, device=d_u.device)
-    _check(lib().fds_field(h.ptr, _ptr(d_u), nrhs, kinds.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                           angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(d_pts), npts, _ptr(d_out),
-                           _stream(stream)), "fds_field")
+    fn = lib().fds_field_compressed if compressed else lib().fds_field
+    _check(fn(h.ptr, _ptr(d_u), nrhs, kinds.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+              angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(d_pts), npts, _ptr(d_out),
+              _stream(stream)), "fds_field")
     return d_out.cpu().numpy().T.reshape(2, npts, nrhs)
 
 
