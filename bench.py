@@ -177,14 +177,16 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def phase_on_fp32(name, precision):
+def phase_on_fp32(name, precision, merge_c64=False):
     """Whether a phase's arithmetic runs on the FP32 pipe: the mixed solve's
-    sweep levels (complex64 and double-float) and the refinement's
-    double-float forward operator; everything else (quadrature, CPQR, merges,
-    top LU and top solve) is FP64."""
+    sweep levels (complex64 and double-float), the refinement's double-float
+    forward operator and, with complex64 merges, the merges (their complex64
+    levels hold most of the merge flops; the upper levels stay FP64);
+    everything else (quadrature, CPQR, top LU and top solve) is FP64."""
     if precision != "mixed":
         return False
-    return (name.startswith("a6.") and name != "a6.top_solve") or name.startswith("a7.")
+    return ((name.startswith("a6.") and name != "a6.top_solve") or name.startswith("a7.")
+            or (merge_c64 and name.startswith("a3.")))
 
 
 # ---------------------------------------------------------------- oracle (CPU)
@@ -693,7 +695,7 @@ def main():
             traffic = d["units"] * bpp / launches_
             basis = ("quadrature points x %.0f executed FP64 flops per point (ncu, 2^14-node build); traffic = points "
                      "per launch x %.2f DRAM bytes per point (same capture)" % (fpp, bpp))
-        fp32 = phase_on_fp32(name, args.precision)
+        fp32 = phase_on_fp32(name, args.precision, args.merge == "c64")
         peak = alu["fp32_tflops"] if fp32 else alu["fp64_tflops"]
         ent = {"ms_per_step": d["ms"] / args.steps, "launches_per_step": d["launches"] / args.steps,
                "bound": "alu", "pipe": "fp32" if fp32 else "fp64", "basis": basis}

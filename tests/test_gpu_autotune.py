@@ -38,6 +38,10 @@ def test_autotuned_solve_equals_fixed_rule(precision):
     for r in rep:
         assert r["best_us"] <= 1.2 * r["rule_us"] + 2.0, r
     rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
-    # same K order in every tile shape: the solutions agree to rounding
-    assert rel(x1, x0) <= 1e-12
-    assert rel(x2, x0) <= 1e-12
+    # same K order in every tile shape: the FP64 solutions agree to rounding;
+    # the refined mixed ones to the refinement's accuracy (its residual norms
+    # and the forward operator's sums use atomics, so the iterates differ at
+    # rounding level from run to run)
+    tol = 1e-12 if precision == 0 else 1e-10
+    assert rel(x1, x0) <= tol
+    assert rel(x2, x0) <= tol
