@@ -61,6 +61,9 @@ def parse():
     p.add_argument("--tol-decay", type=float, default=0.5,
                    help="ID tolerance eps at the leaves, eps * decay^(L-l) at level l (1: the paper's single eps)")
     p.add_argument("--autotune", action="store_true", help="GEMM tile shapes from the autotuner (tuned in warm-up)")
+    p.add_argument("--fw-engine", default="ff", choices=["ff", "tensor"],
+                   help="mixed: leaf blocks of the refinement's forward operator as double-float products (ff) "
+                        "or on the tensor cores (six bf16 slices per FP64 operand)")
     p.add_argument("--c64-engine", default="simt", choices=["tensor", "simt"],
                    help="complex64 products on the tensor cores (bf16 pieces) or the FP32 pipe")
     p.add_argument("--sweep-ff", type=int, default=1, choices=[0, 1, 2],
@@ -86,6 +89,8 @@ def parse():
     p.add_argument("--omega-step", type=float, default=0.05, help="omega: frequency step")
     p.add_argument("--gemm-batch", type=int, default=8192, help="cgemm: number of products")
     p.add_argument("--streams", type=int, default=8, help="batch64: concurrent cavity streams")
+    p.add_argument("--no-graph", action="store_true", help="batch64: launch the solve sweeps kernel by kernel "
+                   "instead of replaying their CUDA graphs")
     p.add_argument("--no-compare", action="store_true",
                    help="skip the plain-FP64 comparison step (error and timings of the FP64 solver)")
     return p.parse_args()
@@ -417,7 +422,9 @@ def run_mr2005(args, fds, torch, rank):
             fds.fds_timing_reset()
             fds.fds_timing_enable(it == args.warmup)
             h = fds.fds_build(xy, omega, 2.0, 1.0, args.eps, leaf_size=args.leaf, top_level=args.top,
-                              tol_decay=args.tol_decay, variant=var)
+                              tol_decay=args.tol_decay,
+                          fw_engine=fds.FDS_FW_TENSOR if args.fw_engine == "tensor" and precision == fds.FDS_MIXED
+                          else fds.FDS_FW_FF, variant=var)
             d = torch.empty((len(kinds), 2 * args.nodes), dtype=torch.complex128, device="cuda")
             fds.fds_rhs_plane_wave_device(h, torch.from_numpy(kinds).cuda(), torch.from_numpy(angles).cuda(), d)
             fds.fds_solve_device(h, d)
@@ -462,8 +469,9 @@ def run_batch(args, fds, torch, world, rank, local):
     eps = 1e-8
     prec = fds.FDS_MIXED if args.precision == "mixed" else fds.FDS_FP64
 
-    def step(streams):
-        hs = fds.fds_build_batch(cav, 2.0, 1.0, eps, n_streams=streams, leaf_size=args.leaf, precision=prec)
+    def step(streams, graph=not args.no_graph):
+        hs = fds.fds_build_batch(cav, 2.0, 1.0, eps, n_streams=streams, leaf_size=args.leaf, precision=prec,
+                                 use_graph=graph)
         for h, F in zip(hs, d_F):
             fds.fds_rhs_plane_wave_device(h, d_k, d_a, F, fds.fds_handle_stream(h))
         fds.fds_solve_batch(hs, d_F, n_streams=streams)
@@ -491,6 +499,11 @@ def run_batch(args, fds, torch, world, rank, local):
     step(1)
     torch.cuda.synchronize()
     seq_ms = (time.perf_counter() - t1) * 1e3
+    # the other sweep mode (graph replay vs kernel by kernel), once
+    t2 = time.perf_counter()
+    step(args.streams, graph=args.no_graph)
+    torch.cuda.synchronize()
+    other_ms = (time.perf_counter() - t2) * 1e3
     if rank != 0:
         return
     nodes = sum(c["N"] for c in cav)
@@ -503,6 +516,7 @@ def run_batch(args, fds, torch, world, rank, local):
                                    "16 plane waves each, %d streams" % (nodes, args.leaf, args.streams),
                        "timing": "host wall clock around the whole batch (several streams), synchronised"},
             "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / ms, "gpu_launches": int(launches),
+            "graph": not args.no_graph, ("no_graph_ms" if not args.no_graph else "graph_ms"): other_ms,
             "clocks": clk}
     print(json.dumps(line))
 
@@ -650,6 +664,7 @@ def main():
         o.precision, o.ir_tol, o.sweep_fp64_levels = prec, args.ir_tol, args.sweep_fp64_levels
         o.merge_c64 = 1 if args.merge == "c64" and prec == fds.FDS_MIXED else 0
         o.tol_decay = args.tol_decay
+        o.fw_engine = fds.FDS_FW_TENSOR if args.fw_engine == "tensor" and prec == fds.FDS_MIXED else fds.FDS_FW_FF
         o.sweep_ff = args.sweep_ff
         o.c64_engine = c64_engine
         mlp32 = None
@@ -697,8 +712,14 @@ def main():
                      "per launch x %.2f DRAM bytes per point (same capture)" % (fpp, bpp))
         fp32 = phase_on_fp32(name, args.precision, args.merge == "c64")
         peak = alu["fp32_tflops"] if fp32 else alu["fp64_tflops"]
+        pipe, bound = "fp32" if fp32 else "fp64", "alu"
+        if name == "a7.fw_leaf_diag" and args.fw_engine == "tensor" and args.precision == "mixed":
+            # 21 bf16 slice products per FP64-accurate product, on the tensor cores
+            flops, pipe, bound = 21.0 * flops, "tensor (bf16)", "tensor"
+            peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0))
+            basis = "21 bf16 products x the phase's algorithmic flops (8 d^2 per column per leaf)"
         ent = {"ms_per_step": d["ms"] / args.steps, "launches_per_step": d["launches"] / args.steps,
-               "bound": "alu", "pipe": "fp32" if fp32 else "fp64", "basis": basis}
+               "bound": bound, "pipe": pipe, "basis": basis}
         if flops > 0:
             ach = flops / (d["ms"] / 1e3) / 1e12
             ent.update(achieved_tflops=ach, peak_tflops=peak, frac=ach / peak)
@@ -710,10 +731,15 @@ def main():
         if d["units"] > 0:
             ent["quad_points_per_s"] = d["units"] / (d["ms"] / 1e3)
         per_phase[name] = ent
+        # a7.forward_apply brackets its a7.fw_* parts: not a kernel of its own
+        if name == "a7.forward_apply":
+            ent["note"] = "sum of the a7.fw_* phases"
+            continue
         if roof is None or d["ms"] > roof["_ms"]:
             roof = {"_ms": d["ms"], "kernel": name, "bound": ent["bound"], "achieved": ent.get("achieved_tflops"),
                     "peak": peak, "unit": "TFLOP/s", "frac": ent.get("frac"), "traffic": traffic,
-                    "peak_source": "measured on this GPU before the timed steps (fds_alu_peak: FMA loop, %s pipe, "
+                    "peak_source": ("MEASURED_PEAKS.json bf16 (sustained), %s" % src) if bound == "tensor" else
+                                   "measured on this GPU before the timed steps (fds_alu_peak: FMA loop, %s pipe, "
                                    "%d SMs)" % ("FP32" if fp32 else "FP64", alu["sms"]),
                     "basis": basis, "avg_launch_ms": d["ms"] / launches_,
                     "launches_per_step": d["launches"] / args.steps}
@@ -742,7 +768,7 @@ def main():
                                   + ", %s rank" % rank_used),
                    "l2": "working set (factors, vectors) larger than L2; no flush",
                    "precision": args.precision, "c64_engine": args.c64_engine, "merge": args.merge,
-                   "tol_decay": args.tol_decay, "autotune": bool(args.autotune),
+                   "tol_decay": args.tol_decay, "autotune": bool(args.autotune), "fw_engine": args.fw_engine,
                    "fp64_reference": "plain FP64 build (adaptive CPQR, same eps and tol_decay) on the same inputs"},
         "ir_iters": info.get("ir_iters"), "ir_residual": info.get("ir_residual"),
         "ir_converged": info.get("converged"), "vs_fp64": compare, "rank_mode": rank_used,
