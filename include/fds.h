@@ -62,6 +62,15 @@ extern "C" {
  * fp32 accumulation in tensor memory). */
 #define FDS_C64_SIMT   0
 #define FDS_C64_TENSOR 1
+/* Engine of the leaf diagonal blocks of the refinement's forward operator
+ * (FDS_MIXED with FDS_APPLY_FF): double-float products on the FP32 pipe, or
+ * the tensor cores with the FP64 blocks and vectors cut into six bf16 slices
+ * each (per-row / per-column powers of two), the 21 slice products with
+ * i + j <= 5 accumulated in fp32 tensor memory (exact for the leading
+ * groups) and summed in FP64: about 2^-40 of |D| |x|, against 2^-44 for the
+ * double-float products.  Leaves of at most 64 nodes. */
+#define FDS_FW_FF     0
+#define FDS_FW_TENSOR 1
 
 /* Elimination variant (Sec. 6): the paper's LU-based recursion (default), or
  * the Sherman–Morrison–Woodbury form of the original Martinsson–Rokhlin
@@ -145,6 +154,13 @@ typedef struct {
                               tolerance per level up keeps the error near tol (measured:
                               error / tol <= 2.1 at 2^12-2^13 nodes, against 4-28 with 1) */
     int32_t variant;       /* FDS_VARIANT_LU (default) or FDS_VARIANT_MR2005 (FDS_FP64 only) */
+    int32_t use_graph;     /* 1: each solve sweep (all levels up, top, all levels down, for one
+                              column chunk) replays a CUDA graph captured on the first sweep of
+                              that column count, instead of launching its kernels one by one;
+                              needs a non-default stream (handles built by fds_build_batch
+                              have one); default 0 */
+    int32_t fw_engine;     /* FDS_MIXED: FDS_FW_FF (default) or FDS_FW_TENSOR for the leaf
+                              diagonal blocks of the refinement's forward operator */
 } fds_options;
 
 /* Statistics of a built handle. */

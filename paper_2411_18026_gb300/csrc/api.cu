@@ -18,6 +18,8 @@ extern "C" void fds_default_options(fds_options *o) {
     o->top_level = 1;
     o->tol_decay = 0.5;
     o->variant = FDS_VARIANT_LU;
+    o->use_graph = 0;
+    o->fw_engine = FDS_FW_FF;
     o->precision = FDS_FP64;
     o->alpha_re = 0.0;
     o->alpha_im = 0.0;
@@ -76,7 +78,8 @@ int fds_build_owned(const fds_geometry *g, double omega, double lambda, double m
         o.sweep_ff > 2 || (o.c64_engine != FDS_C64_SIMT && o.c64_engine != FDS_C64_TENSOR) ||
         !(o.tol_decay > 0.0 && o.tol_decay <= 1.0) ||
         (o.variant != FDS_VARIANT_LU && o.variant != FDS_VARIANT_MR2005) ||
-        (o.variant == FDS_VARIANT_MR2005 && o.precision != FDS_FP64))
+        (o.variant == FDS_VARIANT_MR2005 && o.precision != FDS_FP64) ||
+        (o.fw_engine != FDS_FW_FF && o.fw_engine != FDS_FW_TENSOR))
         return FDS_ERR_ARG;
     for (int i = 0; i < 2 * g->n_nodes; ++i)
         if (!std::isfinite(g->xy[i])) return FDS_ERR_ARG;

@@ -146,6 +146,10 @@ struct Level {
     DBuf<float4> Scp;
     DBuf<int64_t> d_scoff;
     DBuf<int> d_sperm, d_ra, d_rb;
+    // --- fw_engine = FDS_FW_TENSOR (leaf level): bf16 slices of the diagonal
+    //     blocks in pre-swizzled tensor-core tiles and their row exponents
+    DBuf<unsigned char> oz_a;
+    DBuf<int> oz_rowexp;
     int srmax = 0;
     double sum_s2 = 0;            // sum over cells of 2 r_a r_b
 };
@@ -208,6 +212,19 @@ struct fds_handle {
     DBuf<MatRefF> wrefsf;
     DBuf<double> wnorm;
     DBuf<int> wundo;           // per-column flags of the refinement's take-back step
+    DBuf<unsigned char> oz_x;  // fw_engine = FDS_FW_TENSOR: bf16 slices of the leaf vectors
+    DBuf<int> oz_colexp;
+    // use_graph: one CUDA graph of the sweep per column count, with the
+    // workspace layout (hash of its buffer addresses) it was captured against
+    struct SweepGraph {
+        cudaGraphExec_t exec = nullptr;
+        uint64_t ws_hash = 0;
+    };
+    std::vector<std::pair<int, SweepGraph>> sweep_graphs;
+    ~fds_handle() {
+        for (auto &g : sweep_graphs)
+            if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+    }
     int64_t ws_cols = 0;
     double build_ms = 0, solve_ms = 0;
     int64_t factor_bytes = 0;

@@ -1,0 +1,411 @@
+// Leaf diagonal blocks of the FP64 compressed forward operator (the residual
+// r = f - A x of the mixed-precision refinement) on the 5th-generation tensor
+// cores, with FP64-level accuracy from bf16 products (an Ozaki-type split):
+//
+//   y_b += D_b x_b   for every leaf b (D_b: d_b x d_b complex, d_b <= 128).
+//
+// Real form: D_b is the 2d x 2d real matrix of 2 x 2 blocks [[a_r, -a_i],
+// [a_i, a_r]], x the interleaved (re, im) vector.  Each real row r of D_b is
+// scaled by 2^e_r (e_r from frexp of the row's largest entry) and cut into
+// six slices s_0..s_5: v = D_rk / 2^e_r in (-1, 1), s_i = trunc(256 v_i),
+// v_{i+1} = 256 v_i - s_i, so D_rk = 2^e_r sum_i s_i 2^(-8(i+1)) with every
+// s_i an integer of at most 8 bits (exact in bf16); slice i is stored times
+// 2^(-8i).  Each column c of x is cut the same way with its own exponent.
+// The product needs the 21 slice pairs with i + j <= 5 (the others are below
+// 2^-48 of |D| |x|).  Four fp32 accumulators in tensor memory keep what must
+// be exact apart: (0,0), (0,1) and (1,0) hold sums of K <= 256 products of
+// 8-bit integers (exact in fp32), the fourth the pairs with i + j >= 2,
+// whose fp32 rounding lies below 2^-40 of the result.  The epilogue adds the
+// four in FP64, scales by 2^(e_r + f_c - 16) and adds the result to y (float
+// pairs, the refinement's forward-operator format).
+//
+// Kernel: one CTA per (leaf, 128 real rows, 128 columns); a pipeline of
+// 32 KB stages (one A slice tile and one x slice tile, 128 rows x 64 K of
+// bf16 each, stored pre-swizzled so that each is one bulk copy) fed by one
+// producer thread with cp.async.bulk and mbarrier transaction counts, one
+// thread issuing tcgen05.mma (kind::f16, bf16, M 128, N 128, K 16) into the
+// accumulator of the pair's group and committing each stage back to the
+// producer.  Every wait is bounded: after about two seconds the kernel
+// records a status, waits (bounded again) for its own MMAs, frees its TMEM
+// and returns.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "fds_internal.cuh"
+#include "fw_tc.cuh"
+
+namespace {
+
+constexpr int OZ_SLICES = 6;
+constexpr int OZ_PAIRS = 21;           // (i, j) with i + j <= 5
+constexpr int OZ_TILE = 128 * 128;     // bytes of one 128 x 64 bf16 tile
+constexpr int OZ_STAGES = 6;
+constexpr int OZ_THREADS = 128;
+constexpr int OZ_KC = 4;               // 64-wide K chunks of a 256-real K
+constexpr int OZ_ACC = 4;
+constexpr unsigned long long OZ_WAIT_NS = 2000000000ull;
+
+struct OzLayout {
+    static constexpr int STAGE = 2 * OZ_TILE;
+    static constexpr int TOTAL = OZ_STAGES * STAGE + 1024 + 256;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// K-major operand tile, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// fp32 accumulator, bf16 A and B, both K-major, N 128, M 128
+__device__ __forceinline__ uint32_t idesc_bf16_128() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+// byte offset of element (row r, k) in a 128 x 64 bf16 tile with 128-byte swizzle
+__device__ __forceinline__ uint32_t sw_elem(int r, int k) {
+    const int c = k >> 3;
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4) + (k & 7) * 2);
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try(bar, parity))
+        if (global_ns() - t0 > OZ_WAIT_NS) return false;
+    return true;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// slice pair p -> (i, j), ordered by group
+__constant__ unsigned char c_pair_i[OZ_PAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
+__constant__ unsigned char c_pair_j[OZ_PAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
+
+__device__ __forceinline__ int pair_acc(int i, int j) {
+    return (i + j == 0) ? 0 : (i + j == 1 ? (i == 0 ? 1 : 2) : 3);
+}
+
+// six slices of v in (-1, 1), slice i times 2^(-8i) (all exact in bf16)
+__device__ __forceinline__ void cut6(double v, unsigned short (&out)[OZ_SLICES]) {
+    double sc = 1.0;
+#pragma unroll
+    for (int i = 0; i < OZ_SLICES; ++i) {
+        v *= 256.0;
+        const double t = trunc(v);
+        v -= t;
+        out[i] = __bfloat16_as_ushort(__double2bfloat16(t * sc));
+        sc *= 1.0 / 256.0;
+    }
+}
+
+// ------------------------------------------------------------------ slicing
+// A slices: one warp per real row r of one leaf block; tiles at
+// base + (((b * 2 + mt) * OZ_KC + kc) * OZ_SLICES + i) * OZ_TILE; exponent per row.
+__global__ void k_oz_slice_a(int nb, const MatRef *__restrict__ D, unsigned char *slices, int *rowexp) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= nb * 256) return;
+    const int b = warp >> 8, r = warp & 255;
+    const MatRef A = D[b];
+    const int d = A.rows;
+    const int i = r >> 1;
+    const bool im_row = r & 1;
+    // row r of the real form: k = 2 l -> (re ? a_r : a_i), k = 2 l + 1 -> (re ? -a_i : a_r)
+    double m = 0.0;
+    if (i < d)
+        for (int l = lane; l < d; l += 32) {
+            const cplx a = A.p[i + (int64_t)l * A.ld];
+            m = fmax(m, fmax(fabs(a.x), fabs(a.y)));
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);
+    if (lane == 0) rowexp[b * 256 + r] = e;
+    const double inv = ldexp(1.0, -e);
+    const int mt = r >> 7, rr = r & 127;
+    for (int k = lane; k < 256; k += 32) {
+        double v = 0.0;
+        const int l = k >> 1;
+        if (i < d && l < d) {
+            const cplx a = A.p[i + (int64_t)l * A.ld];
+            v = !im_row ? ((k & 1) ? -a.y : a.x) : ((k & 1) ? a.x : a.y);
+        }
+        unsigned short s[OZ_SLICES];
+        cut6(v * inv, s);
+        const int kc = k >> 6;
+        unsigned char *t = slices + (size_t)(((b * 2 + mt) * OZ_KC + kc) * OZ_SLICES) * OZ_TILE;
+        const uint32_t off = sw_elem(rr, k & 63);
+#pragma unroll
+        for (int q = 0; q < OZ_SLICES; ++q) *reinterpret_cast<unsigned short *>(t + (size_t)q * OZ_TILE + off) = s[q];
+    }
+}
+
+// x slices: one warp per (leaf b, column c); the leaf's rows are
+// xin[doff[b] .. doff[b] + d) of column c (float pairs); tiles at
+// base + (((b * ntile + nt) * OZ_KC + kc) * OZ_SLICES + j) * OZ_TILE.
+__global__ void k_oz_slice_x(int nb, const int64_t *__restrict__ doff, const float4 *__restrict__ x, int64_t ldx,
+                             int nc, int ntile, unsigned char *slices, int *colexp) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int cols = ntile * 128;
+    if (warp >= nb * cols) return;
+    const int b = warp / cols, c = warp % cols;
+    const int64_t o = doff[b];
+    const int d = (int)(doff[b + 1] - o);
+    double m = 0.0;
+    if (c < nc)
+        for (int l = lane; l < d; l += 32) {
+            const float4 v = x[o + l + (int64_t)c * ldx];
+            m = fmax(m, fmax(fabs((double)v.x + v.z), fabs((double)v.y + v.w)));
+        }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, s));
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);
+    if (lane == 0) colexp[b * cols + c] = e;
+    const double inv = ldexp(1.0, -e);
+    const int nt = c >> 7, n = c & 127;
+    for (int k = lane; k < 256; k += 32) {
+        const int l = k >> 1;
+        double v = 0.0;
+        if (c < nc && l < d) {
+            const float4 q = x[o + l + (int64_t)c * ldx];
+            v = (k & 1) ? (double)q.y + q.w : (double)q.x + q.z;
+        }
+        unsigned short s[OZ_SLICES];
+        cut6(v * inv, s);
+        const int kc = k >> 6;
+        unsigned char *t = slices + (size_t)(((b * ntile + nt) * OZ_KC + kc) * OZ_SLICES) * OZ_TILE;
+        const uint32_t off = sw_elem(n, k & 63);
+#pragma unroll
+        for (int q = 0; q < OZ_SLICES; ++q) *reinterpret_cast<unsigned short *>(t + (size_t)q * OZ_TILE + off) = s[q];
+    }
+}
+
+}  // namespace
+
+__device__ int g_oz_status;   // 1 once a leaf-block tensor-core product gave up waiting
+
+namespace {
+
+// ------------------------------------------------------------------ product
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_oz_leaf(int nb, int ntile, const int64_t *__restrict__ doff, const unsigned char *__restrict__ aslices,
+              const int *__restrict__ rowexp, const unsigned char *__restrict__ xslices,
+              const int *__restrict__ colexp, float4 *y, int64_t ldy, int nc) {
+    extern __shared__ unsigned char oz_raw[];
+    const int tile = blockIdx.x;
+    const int b = tile / (2 * ntile), mt = (tile / ntile) & 1, nt = tile % ntile;
+    const int64_t o = doff[b];
+    const int d = (int)(doff[b + 1] - o);
+    if (2 * d <= mt * 128) return;     // no rows of this leaf in the lower half
+    const uint32_t raw = smem_u32(oz_raw);
+    const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
+    const uint32_t sbase = raw + pad;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(oz_raw + pad + OZ_STAGES * OzLayout::STAGE);
+    // full[s] = bars[s], empty[s] = bars[OZ_STAGES + s], done = bars[2 OZ_STAGES]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * OZ_STAGES + 1);
+    int *sflag = reinterpret_cast<int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        for (int s = 0; s < 2 * OZ_STAGES + 1; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + s)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *sflag = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const int nkc = (2 * d + 63) / 64;
+    const int steps = nkc * OZ_PAIRS;
+    const unsigned char *abase = aslices + (size_t)((b * 2 + mt) * OZ_KC) * OZ_SLICES * OZ_TILE;
+    const unsigned char *xbase = xslices + (size_t)((b * ntile + nt) * OZ_KC) * OZ_SLICES * OZ_TILE;
+    if (tid == 0) {
+        // producer: stage q of step t holds A slice i and x slice j of K chunk t / 21
+        for (int t = 0; t < steps; ++t) {
+            const int q = t % OZ_STAGES;
+            if (t >= OZ_STAGES && !mbar_wait(smem_u32(bars + OZ_STAGES + q), (uint32_t)(((t / OZ_STAGES) - 1) & 1))) {
+                atomicExch(sflag, 1);
+                break;
+            }
+            if (*(volatile int *)sflag) break;
+            const int kc = t / OZ_PAIRS, p = t % OZ_PAIRS;
+            const uint32_t full = smem_u32(bars + q);
+            const uint32_t dst = sbase + q * OzLayout::STAGE;
+            const unsigned char *src_a = abase + (size_t)(kc * OZ_SLICES + c_pair_i[p]) * OZ_TILE;
+            const unsigned char *src_x = xbase + (size_t)(kc * OZ_SLICES + c_pair_j[p]) * OZ_TILE;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"(2 * OZ_TILE)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                "l"(src_a), "r"(OZ_TILE), "r"(full)
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    dst + OZ_TILE),
+                "l"(src_x), "r"(OZ_TILE), "r"(full)
+                : "memory");
+        }
+    } else if (tid == 32) {
+        // MMA issuer
+        const uint32_t idesc = idesc_bf16_128();
+        int started = 0;   // bit g: accumulator g written once
+        int t = 0;
+        for (; t < steps; ++t) {
+            const int q = t % OZ_STAGES;
+            if (!mbar_wait(smem_u32(bars + q), (uint32_t)((t / OZ_STAGES) & 1)) || *(volatile int *)sflag) {
+                atomicExch(sflag, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int p = t % OZ_PAIRS;
+            const int g = pair_acc(c_pair_i[p], c_pair_j[p]);
+            const uint32_t sa = sbase + q * OzLayout::STAGE, sb = sa + OZ_TILE;
+            const int kc = t / OZ_PAIRS;
+            const int kin = min(64, 2 * d - kc * 64);   // reals of this chunk holding data
+            for (int ks = 0; ks < (kin + 15) / 16; ++ks) {
+                mma_bf16(tmem + (uint32_t)(g * 128), sw128_desc(sa + 32u * ks), sw128_desc(sb + 32u * ks), idesc,
+                         ((started >> g) & 1) ? 1u : 0u);
+                started |= 1 << g;
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(bars + OZ_STAGES + q))
+                         : "memory");
+        }
+        // all MMAs issued so far complete -> done
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(bars + 2 * OZ_STAGES))
+                     : "memory");
+        if (started != 15 && t == steps) atomicExch(sflag, 1);   // an accumulator never written: not expected
+    }
+    __syncwarp();
+    const bool done_ok = mbar_wait(smem_u32(bars + 2 * OZ_STAGES), 0u);
+    const int bad = __syncthreads_or(!done_ok || *(volatile int *)sflag);
+    if (bad) {
+        if (tid == 0) atomicExch(&g_oz_status, 1);
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int lane = tid & 31;
+        const int r = mt * 128 + warp * 32 + lane;            // real row of the leaf block
+        const uint32_t tq = tmem + ((uint32_t)(warp * 32) << 16);
+        const int er = rowexp[b * 256 + r];
+        const int cols = ntile * 128;
+        for (int cb = 0; cb < 128; cb += 16) {
+            const int c0 = nt * 128 + cb;
+            if (c0 >= nc) break;
+            float v[OZ_ACC][16];
+#pragma unroll
+            for (int g = 0; g < OZ_ACC; ++g) tmem_ld16(tq + (uint32_t)(g * 128 + cb), v[g]);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int c = c0 + j;
+                const double sum = ((double)v[0][j] + (double)v[1][j]) + ((double)v[2][j] + (double)v[3][j]);
+                const double val = c < nc ? ldexp(sum, er + colexp[b * cols + c] - 16) : 0.0;
+                const double other = __shfl_xor_sync(0xffffffffu, val, 1);   // the partner real row
+                if (!(lane & 1) && c < nc && r < 2 * d) {
+                    float4 *yp = y + o + (r >> 1) + (int64_t)c * ldy;
+                    const float4 cur = *yp;
+                    const double re = (double)cur.x + cur.z + val, im = (double)cur.y + cur.w + other;
+                    const float rh = (float)re, ih = (float)im;
+                    *yp = make_float4(rh, ih, (float)(re - (double)rh), (float)(im - (double)ih));
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+}  // namespace
+
+int oz_leaf_prepare(Level &C, const MatRef *d_blocks, cudaStream_t s) {
+    const int nb = C.nb;
+    for (int b = 0; b < nb; ++b)
+        if (C.n1[b] + C.n2[b] > 128) return FDS_ERR_ARG;
+    FDS_TRY(C.oz_a.alloc((size_t)nb * 2 * OZ_KC * OZ_SLICES * OZ_TILE));
+    FDS_TRY(C.oz_rowexp.alloc((size_t)nb * 256));
+    const int64_t warps = (int64_t)nb * 256;
+    fds_count_launch(), k_oz_slice_a<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(nb, d_blocks, C.oz_a.p,
+                                                                                         C.oz_rowexp.p);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
+}
+
+int oz_leaf_apply(fds_handle *h, Level &C, const float4 *x, float4 *y, int64_t ld, int nc, cudaStream_t s) {
+    const int nb = C.nb;
+    if (nb == 0 || nc == 0) return FDS_OK;
+    const int ntile = (nc + 127) / 128;
+    const size_t need = (size_t)nb * ntile * OZ_KC * OZ_SLICES * OZ_TILE;
+    if (h->oz_x.n < need) FDS_TRY(h->oz_x.alloc(need));
+    if (h->oz_colexp.n < (size_t)nb * ntile * 128) FDS_TRY(h->oz_colexp.alloc((size_t)nb * ntile * 128));
+    const int64_t warps = (int64_t)nb * ntile * 128;
+    fds_count_launch(), k_oz_slice_x<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(
+        nb, C.d_doff.p, x, ld, nc, ntile, h->oz_x.p, h->oz_colexp.p);
+    FDS_CUDA_TRY(cudaGetLastError());
+    constexpr int smem = OzLayout::TOTAL;
+    FDS_TRY(ensure_dyn_smem(k_oz_leaf, smem));
+    const int64_t tiles = (int64_t)nb * 2 * ntile;
+    if (tiles > 2147483647) return FDS_ERR_ARG;
+    fds_count_launch(), k_oz_leaf<<<(unsigned)tiles, OZ_THREADS, smem, s>>>(nb, ntile, C.d_doff.p, C.oz_a.p,
+                                                                            C.oz_rowexp.p, h->oz_x.p,
+                                                                            h->oz_colexp.p, y, ld, nc);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
+}
+
+int oz_status_take(cudaStream_t s, int *status) {
+    int v = 0, zero = 0;
+    FDS_CUDA_TRY(cudaMemcpyFromSymbolAsync(&v, g_oz_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+    FDS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (v) FDS_CUDA_TRY(cudaMemcpyToSymbolAsync(g_oz_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    *status = v;
+    return FDS_OK;
+}

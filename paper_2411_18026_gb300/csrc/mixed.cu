@@ -25,6 +25,7 @@
 #include "prof.cuh"
 #include "solve.cuh"
 #include "vapply.cuh"
+#include "fw_tc.cuh"
 
 namespace {
 
@@ -307,6 +308,20 @@ int apply_S(fds_handle *h, const Level &C, const T *x, int64_t ldx, T *y, int64_
     return dense_gemm_map(2 * nb, std::max(C.srmax, 1), nc, A, 0, B, Cr, M, 1, s);
 }
 
+// leaf blocks on the tensor cores: float-pair vectors with slices prepared
+template <class T>
+bool leaf_on_tensor(const Level &C) {
+    return false;
+}
+template <>
+bool leaf_on_tensor<float4>(const Level &C) {
+    return C.oz_a.p != nullptr;
+}
+inline int oz_leaf(fds_handle *h, Level &C, const cplx *, cplx *, int64_t, int, cudaStream_t) { return FDS_ERR_STATE; }
+inline int oz_leaf(fds_handle *h, Level &C, const float4 *x, float4 *y, int64_t ld, int nc, cudaStream_t s) {
+    return oz_leaf_apply(h, C, x, y, ld, nc, s);
+}
+
 // Y = A X for nc leaf-order columns (both D_L x nc, column-major).
 template <class T>
 int forward_apply(fds_handle *h, const T *X, T *Y, int nc, cudaStream_t s) {
@@ -389,10 +404,14 @@ int forward_apply(fds_handle *h, const T *X, T *Y, int nc, cudaStream_t s) {
         } else {
             ProfScope pd("a7.fw_leaf_diag", s);
             pd.flops = 8.0 * level_d2(C) * nc;
-            fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, yl, C.d_doff.p, nc, C.D, rY);
-            fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, xl, C.d_doff.p, nc, C.D, rZ);
-            FDS_CUDA_TRY(cudaGetLastError());
-            FDS_TRY(F::gemm(nb, C.dmax, nc, F::D(C), 0, rZ, rY, 1, s));
+            if (leaf_on_tensor<T>(C)) {
+                FDS_TRY(oz_leaf(h, C, xl, yl, C.D, nc, s));
+            } else {
+                fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, yl, C.d_doff.p, nc, C.D, rY);
+                fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, xl, C.d_doff.p, nc, C.D, rZ);
+                FDS_CUDA_TRY(cudaGetLastError());
+                FDS_TRY(F::gemm(nb, C.dmax, nc, F::D(C), 0, rZ, rY, 1, s));
+            }
             fl += 8.0 * (C.sum_tm + level_d2(C)) * nc;
         }
     }
@@ -529,6 +548,9 @@ int fds_mixed_prepare(fds_handle *h) {
                 rv[b] = l > l0 ? C.k1[b] + C.k2[b] : 0;
             }
             if (C.Dfw.p) FDS_TRY(split_blocks(C.Dfw, C.Dp, C.rDp, C.offA, dv, dv, s));
+            // tensor-core slices of the leaf blocks (leaves of up to 64 nodes)
+            if (l == L && L > l0 && C.Dfw.p && h->opt.fw_engine == FDS_FW_TENSOR && C.dmax <= 128)
+                FDS_TRY(oz_leaf_prepare(C, C.rDfw.p, s));
 
         }
         {
@@ -607,7 +629,7 @@ int solve_mixed(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
                                                                               nullptr, leaf_in, h->wnorm.p);
         }
         FDS_CUDA_TRY(cudaGetLastError());
-        FDS_TRY(sweep_chunk(h, nc, s));
+        FDS_TRY(sweep_chunk_run(h, nc, s));
         fds_count_launch(), k_update<LT><<<1024, 256, 0, s>>>(h->wX.p, leaf, D * nc, 1);
         FDS_CUDA_TRY(cudaGetLastError());
         // refinement against the FP64 compressed operator; prevc[c] is the
@@ -665,7 +687,7 @@ int solve_mixed(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
             }
             prev = res;
             prevc = resc;
-            FDS_TRY(sweep_chunk(h, nc, s));
+            FDS_TRY(sweep_chunk_run(h, nc, s));
             fds_count_launch(), k_update<LT><<<1024, 256, 0, s>>>(h->wX.p, leaf, D * nc, 0);
             FDS_CUDA_TRY(cudaGetLastError());
         }
@@ -689,6 +711,14 @@ int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
     // the refinement's sweep vectors are in the leaf level's precision
     const int rc = (h->L > h->l0 && level_prec(h, h->L) == PREC_FF) ? solve_mixed<float4>(h, d_rhs, nrhs, s)
                                                                    : solve_mixed<cplxf>(h, d_rhs, nrhs, s);
+    if (h->L > h->l0 && h->lv[h->L].oz_a.p) {
+        int st = 0;
+        FDS_TRY(oz_status_take(s, &st));
+        if (st) {
+            fds_set_error_detail("tensor-core forward operator: wait on a pipeline barrier timed out");
+            return FDS_ERR_TIMEOUT;
+        }
+    }
     if (h->opt.c64_engine != FDS_C64_TENSOR) return rc;
     int st = 0;
     const int rs = tc_status_take(s, &st);

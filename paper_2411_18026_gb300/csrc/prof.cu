@@ -48,7 +48,9 @@ void resolve_locked() {
 }
 }  // namespace
 
-bool prof_enabled() { return g_on; }
+thread_local bool g_capturing = false;
+void prof_set_capturing(bool on) { g_capturing = on; }
+bool prof_enabled() { return g_on && !g_capturing; }
 
 static std::atomic<long long> g_launches{0};
 void fds_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }

@@ -8,6 +8,13 @@
 #include <stdint.h>
 
 bool prof_enabled();
+// timing is suspended on the calling thread while it captures a CUDA graph
+// (the events would belong to the graph, not to this launch)
+void prof_set_capturing(bool on);
+struct ProfCaptureScope {
+    ProfCaptureScope() { prof_set_capturing(true); }
+    ~ProfCaptureScope() { prof_set_capturing(false); }
+};
 void prof_begin(const char *name, cudaStream_t s);
 void prof_end(cudaStream_t s, double flops, double bytes, double units);
 // work of a phase known only after its launches ran (e.g. from the ranks the

@@ -203,6 +203,7 @@ int workspace_prec(fds_handle *h, int ncmax, int prec) {
 }
 
 int sweep_workspace(fds_handle *h, int ncmax) {
+    FDS_TRY(vapply_workspace(h));
     FDS_TRY(workspace_prec<cplx>(h, ncmax, PREC_C128));
     FDS_TRY(grow(h->wtop2, (size_t)std::max<int64_t>(h->Dtop, 1) * ncmax));
     if (h->opt.precision == FDS_MIXED) {
@@ -335,19 +336,23 @@ int down_level(fds_handle *h, int l, int nc, cudaStream_t s) {
 }
 
 
+__global__ void k_top_refs(MatRef *rX, cplx *a, cplx *b, int rows, int cols, int ld) {
+    if (threadIdx.x < 2) {
+        MatRef r;
+        r.p = threadIdx.x ? b : a;
+        r.rows = rows;
+        r.cols = cols;
+        r.ld = ld;
+        rX[threadIdx.x] = r;
+    }
+}
+
 // x_top = A_top^{-1} f_top (Sec. 6.3) as one GEMM with the inverse formed at build
 int top_solve(fds_handle *h, int nc, cudaStream_t s) {
     const int64_t ldt = std::max<int64_t>(h->Dtop, 1);
-    MatRef tv[2];
-    tv[0].p = h->wtop.p;
-    tv[1].p = h->wtop2.p;
-    for (int q = 0; q < 2; ++q) {
-        tv[q].rows = (int)h->Dtop;
-        tv[q].cols = nc;
-        tv[q].ld = (int)ldt;
-    }
     MatRef *rX = h->wrefs.p + 3 * fds_max_cells(h);
-    FDS_CUDA_TRY(cudaMemcpyAsync(rX, tv, sizeof(tv), cudaMemcpyHostToDevice, s));
+    fds_count_launch(), k_top_refs<<<1, 32, 0, s>>>(rX, h->wtop.p, h->wtop2.p, (int)h->Dtop, nc, (int)ldt);
+    FDS_CUDA_TRY(cudaGetLastError());
     ProfScope ps("a6.top_solve", s);
     ps.flops = 8.0 * (double)h->Dtop * h->Dtop * nc;
     ps.bytes = 16.0 * (double)h->Dtop * h->Dtop;
@@ -454,6 +459,82 @@ int sweep_chunk(fds_handle *h, int nc, cudaStream_t s) {
     return FDS_OK;
 }
 
+namespace {
+
+// addresses of every buffer a sweep touches: a graph captured against one
+// layout must not be replayed after the workspace was regrown
+uint64_t workspace_hash(const fds_handle *h) {
+    uint64_t x = 1469598103934665603ull;
+    auto mix = [&](const void *p, size_t n) {
+        x = (x ^ (uint64_t)(uintptr_t)p) * 1099511628211ull;
+        x = (x ^ (uint64_t)n) * 1099511628211ull;
+    };
+    auto vec = [&](const auto &v) {
+        for (const auto &b : v) mix(b.p, b.n);
+    };
+    vec(h->wz); vec(h->wf); vec(h->wt); vec(h->wr);
+    vec(h->wzf); vec(h->wff); vec(h->wtf); vec(h->wrf);
+    vec(h->wzq); vec(h->wfq); vec(h->wtq); vec(h->wrq);
+    mix(h->wtop.p, h->wtop.n); mix(h->wtop2.p, h->wtop2.n); mix(h->wtopf.p, h->wtopf.n);
+    mix(h->wtopq.p, h->wtopq.n); mix(h->wrefs.p, h->wrefs.n); mix(h->wrefsf.p, h->wrefsf.n);
+    mix(h->wrefsq.p, h->wrefsq.n); mix(h->wvref.p, h->wvref.n);
+    return x;
+}
+
+bool capturable(cudaStream_t s) {
+    if (s == 0 || s == cudaStreamLegacy || s == cudaStreamPerThread) return false;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusNone;
+}
+
+}  // namespace
+
+int sweep_chunk_run(fds_handle *h, int nc, cudaStream_t s) {
+    if (!h->opt.use_graph || !capturable(s)) return sweep_chunk(h, nc, s);
+    const uint64_t hash = workspace_hash(h);
+    fds_handle::SweepGraph *g = nullptr;
+    for (auto &e : h->sweep_graphs)
+        if (e.first == nc) g = &e.second;
+    if (g && g->exec && g->ws_hash == hash) {
+        fds_count_launch();
+        FDS_CUDA_TRY(cudaGraphLaunch(g->exec, s));
+        return FDS_OK;
+    }
+    // capture the sweep (the workspace is allocated before any sweep, so the
+    // captured launches allocate nothing), then replay it; if anything in it
+    // cannot be captured, this sweep runs as plain launches
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return sweep_chunk(h, nc, s);
+    }
+    int rc;
+    {
+        ProfCaptureScope pc;
+        rc = sweep_chunk(h, nc, s);
+    }
+    const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+    cudaGraphExec_t exec = nullptr;
+    const bool ok = rc == FDS_OK && ec == cudaSuccess && graph && workspace_hash(h) == hash &&
+                    cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        return sweep_chunk(h, nc, s);
+    }
+    if (!g) {
+        h->sweep_graphs.push_back({nc, fds_handle::SweepGraph{}});
+        g = &h->sweep_graphs.back().second;
+    }
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    g->exec = exec;
+    g->ws_hash = hash;
+    fds_count_launch();
+    FDS_CUDA_TRY(cudaGraphLaunch(g->exec, s));
+    return FDS_OK;
+}
+
 template cplx *sweep_leaf_in<cplx>(fds_handle *);
 template cplxf *sweep_leaf_in<cplxf>(fds_handle *);
 template float4 *sweep_leaf_in<float4>(fds_handle *);
@@ -479,7 +560,7 @@ int fds_solve_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
         cplx *rhs = d_rhs + (int64_t)c0 * ld_rhs;
         fds_count_launch(), k_leaf_gather<<<1024, 256, 0, s>>>(h->d_leaf_gidx.p, Lf.D, rhs, ld_rhs, leaf_in, nc, 0);
         FDS_CUDA_TRY(cudaGetLastError());
-        FDS_TRY(sweep_chunk(h, nc, s));
+        FDS_TRY(sweep_chunk_run(h, nc, s));
         fds_count_launch(), k_leaf_gather<<<1024, 256, 0, s>>>(h->d_leaf_gidx.p, Lf.D, rhs, ld_rhs, leaf_out, nc, 1);
         FDS_CUDA_TRY(cudaGetLastError());
     }

@@ -24,3 +24,6 @@ template <class C>
 C *sweep_leaf_out(fds_handle *h);
 // One sweep over nc columns (levels above sweep_split in complex64).
 int sweep_chunk(fds_handle *h, int nc, cudaStream_t s);
+// sweep_chunk, or (use_graph, on a capturable stream) the replay of a CUDA
+// graph of it captured on the first sweep of nc columns
+int sweep_chunk_run(fds_handle *h, int nc, cudaStream_t s);

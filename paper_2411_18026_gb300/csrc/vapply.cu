@@ -72,13 +72,17 @@ __global__ void k_vskel(int dir, const int *__restrict__ k1, const int *__restri
     }
 }
 
+size_t vref_bytes(const fds_handle *h, size_t ref_size) {
+    return (size_t)2 * fds_max_cells(h) * (3 * ref_size + sizeof(RowMaps)) + 64;
+}
+
 template <class T>
 int vapply(fds_handle *h, const Level &C, const T *Tb, int dir, const T *src, int64_t lds, T *dst, int64_t ldd,
            int nc, cudaStream_t s) {
     const int nb = C.nb;
     if (nb == 0 || nc == 0) return FDS_OK;
     const int maxnb = fds_max_cells(h);
-    const size_t need = (size_t)2 * maxnb * (3 * sizeof(MatRefT<T>) + sizeof(RowMaps)) + 64;
+    const size_t need = vref_bytes(h, sizeof(MatRefT<T>));
     if (h->wvref.n < need) FDS_TRY(h->wvref.alloc(need));
     MatRefT<T> *A = reinterpret_cast<MatRefT<T> *>(h->wvref.p);
     MatRefT<T> *B = A + 2 * maxnb, *Cr = B + 2 * maxnb;
@@ -99,6 +103,11 @@ template <class T>
 int apply_V(fds_handle *h, const Level &C, const T *Tb, const T *x, int64_t ldx, T *out, int64_t ldo, int nc,
             cudaStream_t s) {
     return vapply<T>(h, C, Tb, 0, x, ldx, out, ldo, nc, s);
+}
+
+int vapply_workspace(fds_handle *h) {
+    const size_t need = std::max(vref_bytes(h, sizeof(MatRefT<cplx>)), vref_bytes(h, sizeof(MatRefT<float4>)));
+    return h->wvref.n < need ? h->wvref.alloc(need) : FDS_OK;
 }
 
 template <class T>

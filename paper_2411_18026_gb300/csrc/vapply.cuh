@@ -7,6 +7,9 @@
 template <class T>
 int apply_V(fds_handle *h, const Level &C, const T *Tb, const T *x, int64_t ldx, T *out, int64_t ldo, int nc,
             cudaStream_t s);
+// Descriptor workspace of every structured application (allocated up front,
+// so that a sweep captured into a CUDA graph allocates nothing).
+int vapply_workspace(fds_handle *h);
 // y (D_l x nc) = V_l^H t (R_l x nc).
 template <class T>
 int apply_VH(fds_handle *h, const Level &C, const T *Tb, const T *t, int64_t ldt, T *y, int64_t ldy, int nc,

@@ -28,6 +28,8 @@ FDS_APPLY_FF = 0
 FDS_APPLY_FP64 = 1
 FDS_C64_SIMT = 0
 FDS_C64_TENSOR = 1
+FDS_FW_FF = 0
+FDS_FW_TENSOR = 1
 FDS_VARIANT_LU = 0
 FDS_VARIANT_MR2005 = 1
 FDS_RANK_ADAPTIVE = 0
@@ -68,7 +70,7 @@ class fds_options(ctypes.Structure):
                 ("sweep_ff", ctypes.c_int32), ("merge_c64", ctypes.c_int32), ("rank_mode", ctypes.c_int32),
                 ("mlp_params", ctypes.POINTER(ctypes.c_float)), ("sketch_extra", ctypes.c_int32),
                 ("record_features", ctypes.c_int32), ("c64_engine", ctypes.c_int32), ("tol_decay", ctypes.c_double),
-                ("variant", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("fw_engine", ctypes.c_int32)]
 
 
 class fds_stats(ctypes.Structure):
@@ -214,7 +216,8 @@ class Handle:
 def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy_ratio=1.5, proxy_points=64,
               alpha=None, stream=0, precision=FDS_FP64, ir_tol=None, ir_max_iter=None, ir_apply=None,
               mlp_params=None, sketch_extra=None, record_features=False, sweep_fp64_levels=None, merge_c64=False,
-              sweep_ff=1, c64_engine=FDS_C64_SIMT, tol_decay=None, variant=FDS_VARIANT_LU):
+              sweep_ff=1, c64_engine=FDS_C64_SIMT, tol_decay=None, variant=FDS_VARIANT_LU, use_graph=False,
+              fw_engine=FDS_FW_FF):
     """Factorise; mlp_params (FDS_MLP_NPARAM floats) selects the learned-rank ID."""
     xy = np.ascontiguousarray(xy, dtype=np.float64)
     g = fds_geometry(len(xy), xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(rho))
@@ -248,6 +251,8 @@ def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy
     if tol_decay is not None:
         o.tol_decay = float(tol_decay)
     o.variant = int(variant)
+    o.use_graph = 1 if use_graph else 0
+    o.fw_engine = int(fw_engine)
     out = ctypes.c_void_p()
     _check(lib().fds_build_ex(ctypes.byref(g), float(omega), float(lam), float(mu), float(tol), ctypes.byref(o),
                               ctypes.byref(out)), "fds_build")
@@ -255,7 +260,7 @@ def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy
 
 
 def fds_build_batch(cavities, lam, mu, tol, n_streams=8, rho=1.0, leaf_size=64, top_level=1, precision=FDS_FP64,
-                    ir_tol=None):
+                    ir_tol=None, use_graph=False):
     """Build many cavities concurrently (dicts with 'xy' and 'omega'); returns handles."""
     n = len(cavities)
     xys = [np.ascontiguousarray(c["xy"], dtype=np.float64) for c in cavities]
@@ -264,6 +269,7 @@ def fds_build_batch(cavities, lam, mu, tol, n_streams=8, rho=1.0, leaf_size=64, 
     om = np.ascontiguousarray([c["omega"] for c in cavities], dtype=np.float64)
     o = default_options()
     o.leaf_size, o.top_level, o.precision = leaf_size, top_level, precision
+    o.use_graph = 1 if use_graph else 0
     if ir_tol is not None:
         o.ir_tol = ir_tol
     out = (ctypes.c_void_p * n)()
