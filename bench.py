@@ -422,9 +422,7 @@ def run_mr2005(args, fds, torch, rank):
             fds.fds_timing_reset()
             fds.fds_timing_enable(it == args.warmup)
             h = fds.fds_build(xy, omega, 2.0, 1.0, args.eps, leaf_size=args.leaf, top_level=args.top,
-                              tol_decay=args.tol_decay,
-                          fw_engine=fds.FDS_FW_TENSOR if args.fw_engine == "tensor" and precision == fds.FDS_MIXED
-                          else fds.FDS_FW_FF, variant=var)
+                              tol_decay=args.tol_decay, variant=var)
             d = torch.empty((len(kinds), 2 * args.nodes), dtype=torch.complex128, device="cuda")
             fds.fds_rhs_plane_wave_device(h, torch.from_numpy(kinds).cuda(), torch.from_numpy(angles).cuda(), d)
             fds.fds_solve_device(h, d)
@@ -573,6 +571,8 @@ def main():
         h = fds.fds_build(xy, omega, 2.0, 1.0, args.eps, leaf_size=args.leaf, top_level=args.top, stream=stream,
                           precision=precision, ir_tol=args.ir_tol, sweep_fp64_levels=args.sweep_fp64_levels,
                           mlp_params=params, merge_c64=args.merge == "c64" and precision == fds.FDS_MIXED,
+                          fw_engine=fds.FDS_FW_TENSOR if args.fw_engine == "tensor" and precision == fds.FDS_MIXED
+                          else fds.FDS_FW_FF,
                           tol_decay=args.tol_decay,
                           sweep_ff=args.sweep_ff if precision == fds.FDS_MIXED else 0,
                           c64_engine=c64_engine)

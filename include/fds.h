@@ -417,6 +417,21 @@ int fds_cgemm_c64_batched(int32_t batch, const int32_t *m, const int32_t *n, con
                           uint64_t stream);
 
 /*
+ * The tensor-core product of the forward operator's leaf blocks (stage entry
+ * for tests and benchmarks; fw_engine = FDS_FW_TENSOR): Y_b += A_b X_b for
+ * b < batch, A_b d[b] x d[b] complex128 (1 <= d[b] <= 128) stored column-major
+ * back to back at d_A, X and Y the row blocks of one (sum d) x nc complex128
+ * matrix (column-major, leading dimension sum d), block b at rows
+ * sum_{c<b} d[c].  Operands are cut into six bf16 slices with per-row /
+ * per-column powers of two and the 21 slice products with i + j <= 5 are
+ * accumulated on the tensor cores (the vectors pass through float pairs, as
+ * in the refinement).  d: host array.  Allocates its temporaries; synchronises
+ * the stream; FDS_ERR_TIMEOUT if a tensor-core pipeline wait gave up.
+ */
+int fds_zgemm_blocks_tc(int32_t batch, const int32_t *d, const double *d_A, const double *d_X, double *d_Y,
+                        int32_t nc, uint64_t stream);
+
+/*
  * Training data of the learned-rank network (extension): the 16 features of
  * each (cell, component) of levels L..l0+1 and the fraction k / n that the
  * adaptive ID kept there, recorded by a build with record_features = 1.

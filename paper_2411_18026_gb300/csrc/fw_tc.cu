@@ -366,39 +366,117 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
 }  // namespace
 
-int oz_leaf_prepare(Level &C, const MatRef *d_blocks, cudaStream_t s) {
-    const int nb = C.nb;
-    for (int b = 0; b < nb; ++b)
-        if (C.n1[b] + C.n2[b] > 128) return FDS_ERR_ARG;
-    FDS_TRY(C.oz_a.alloc((size_t)nb * 2 * OZ_KC * OZ_SLICES * OZ_TILE));
-    FDS_TRY(C.oz_rowexp.alloc((size_t)nb * 256));
+namespace {
+
+int oz_slice_blocks(int nb, const MatRef *d_blocks, DBuf<unsigned char> &aslices, DBuf<int> &rowexp,
+                    cudaStream_t s) {
+    FDS_TRY(aslices.alloc((size_t)nb * 2 * OZ_KC * OZ_SLICES * OZ_TILE));
+    FDS_TRY(rowexp.alloc((size_t)nb * 256));
     const int64_t warps = (int64_t)nb * 256;
-    fds_count_launch(), k_oz_slice_a<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(nb, d_blocks, C.oz_a.p,
-                                                                                         C.oz_rowexp.p);
+    fds_count_launch(), k_oz_slice_a<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(nb, d_blocks, aslices.p,
+                                                                                         rowexp.p);
     FDS_CUDA_TRY(cudaGetLastError());
     return FDS_OK;
 }
 
-int oz_leaf_apply(fds_handle *h, Level &C, const float4 *x, float4 *y, int64_t ld, int nc, cudaStream_t s) {
-    const int nb = C.nb;
+int oz_apply(int nb, const int64_t *d_doff, const unsigned char *aslices, const int *rowexp,
+             DBuf<unsigned char> &xs, DBuf<int> &colexp, const float4 *x, float4 *y, int64_t ld, int nc,
+             cudaStream_t s) {
     if (nb == 0 || nc == 0) return FDS_OK;
     const int ntile = (nc + 127) / 128;
     const size_t need = (size_t)nb * ntile * OZ_KC * OZ_SLICES * OZ_TILE;
-    if (h->oz_x.n < need) FDS_TRY(h->oz_x.alloc(need));
-    if (h->oz_colexp.n < (size_t)nb * ntile * 128) FDS_TRY(h->oz_colexp.alloc((size_t)nb * ntile * 128));
+    if (xs.n < need) FDS_TRY(xs.alloc(need));
+    if (colexp.n < (size_t)nb * ntile * 128) FDS_TRY(colexp.alloc((size_t)nb * ntile * 128));
     const int64_t warps = (int64_t)nb * ntile * 128;
-    fds_count_launch(), k_oz_slice_x<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(
-        nb, C.d_doff.p, x, ld, nc, ntile, h->oz_x.p, h->oz_colexp.p);
+    fds_count_launch(), k_oz_slice_x<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(nb, d_doff, x, ld, nc,
+                                                                                          ntile, xs.p, colexp.p);
     FDS_CUDA_TRY(cudaGetLastError());
     constexpr int smem = OzLayout::TOTAL;
     FDS_TRY(ensure_dyn_smem(k_oz_leaf, smem));
     const int64_t tiles = (int64_t)nb * 2 * ntile;
     if (tiles > 2147483647) return FDS_ERR_ARG;
-    fds_count_launch(), k_oz_leaf<<<(unsigned)tiles, OZ_THREADS, smem, s>>>(nb, ntile, C.d_doff.p, C.oz_a.p,
-                                                                            C.oz_rowexp.p, h->oz_x.p,
-                                                                            h->oz_colexp.p, y, ld, nc);
+    fds_count_launch(), k_oz_leaf<<<(unsigned)tiles, OZ_THREADS, smem, s>>>(nb, ntile, d_doff, aslices, rowexp,
+                                                                            xs.p, colexp.p, y, ld, nc);
     FDS_CUDA_TRY(cudaGetLastError());
     return FDS_OK;
+}
+
+// complex128 <-> float pairs
+__global__ void k_oz_to_pairs(const cplx *__restrict__ a, float4 *b, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const cplx v = a[e];
+        const float rh = (float)v.x, ih = (float)v.y;
+        b[e] = make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));
+    }
+}
+__global__ void k_oz_from_pairs(const float4 *__restrict__ a, cplx *b, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = a[e];
+        b[e] = mkc((double)v.x + v.z, (double)v.y + v.w);
+    }
+}
+
+__global__ void k_oz_block_refs(int nb, cplx *A, const int64_t *__restrict__ aoff, const int64_t *__restrict__ doff,
+                                MatRef *out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int d = (int)(doff[b + 1] - doff[b]);
+    out[b].p = A + aoff[b];
+    out[b].rows = out[b].cols = d;
+    out[b].ld = d > 1 ? d : 1;
+}
+
+}  // namespace
+
+int oz_leaf_prepare(Level &C, const MatRef *d_blocks, cudaStream_t s) {
+    for (int b = 0; b < C.nb; ++b)
+        if (C.n1[b] + C.n2[b] > 128) return FDS_ERR_ARG;
+    return oz_slice_blocks(C.nb, d_blocks, C.oz_a, C.oz_rowexp, s);
+}
+
+int oz_leaf_apply(fds_handle *h, Level &C, const float4 *x, float4 *y, int64_t ld, int nc, cudaStream_t s) {
+    return oz_apply(C.nb, C.d_doff.p, C.oz_a.p, C.oz_rowexp.p, h->oz_x, h->oz_colexp, x, y, ld, nc, s);
+}
+
+extern "C" int fds_zgemm_blocks_tc(int32_t batch, const int32_t *d, const double *d_A, const double *d_X,
+                                   double *d_Y, int32_t nc, uint64_t stream) {
+    if (batch < 0 || nc < 0) return FDS_ERR_ARG;
+    if (batch == 0 || nc == 0) return FDS_OK;
+    if (!d || !d_A || !d_X || !d_Y) return FDS_ERR_ARG;
+    std::vector<int64_t> doff(batch + 1, 0), aoff(batch + 1, 0);
+    for (int b = 0; b < batch; ++b) {
+        if (d[b] < 1 || d[b] > 128) return FDS_ERR_ARG;
+        doff[b + 1] = doff[b] + d[b];
+        aoff[b + 1] = aoff[b] + (int64_t)d[b] * d[b];
+    }
+    const int64_t D = doff[batch];
+    if ((int64_t)batch * 2 * ((nc + 127) / 128) > 2147483647) return FDS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    FDS_TRY(ensure_gauss_tables());
+    DBuf<int64_t> d_doff, d_aoff;
+    DBuf<MatRef> refs;
+    DBuf<float4> xp, yp;
+    DBuf<unsigned char> as, xs;
+    DBuf<int> rowexp, colexp;
+    FDS_TRY(d_doff.upload(doff, s));
+    FDS_TRY(d_aoff.upload(aoff, s));
+    FDS_TRY(refs.alloc(batch));
+    fds_count_launch(), k_oz_block_refs<<<(batch + 127) / 128, 128, 0, s>>>(batch, (cplx *)d_A, d_aoff.p, d_doff.p,
+                                                                            refs.p);
+    FDS_CUDA_TRY(cudaGetLastError());
+    FDS_TRY(xp.alloc((size_t)D * nc));
+    FDS_TRY(yp.alloc((size_t)D * nc));
+    fds_count_launch(), k_oz_to_pairs<<<1024, 256, 0, s>>>((const cplx *)d_X, xp.p, D * nc);
+    fds_count_launch(), k_oz_to_pairs<<<1024, 256, 0, s>>>((const cplx *)d_Y, yp.p, D * nc);
+    FDS_CUDA_TRY(cudaGetLastError());
+    FDS_TRY(oz_slice_blocks(batch, refs.p, as, rowexp, s));
+    FDS_TRY(oz_apply(batch, d_doff.p, as.p, rowexp.p, xs, colexp, xp.p, yp.p, D, nc, s));
+    fds_count_launch(), k_oz_from_pairs<<<1024, 256, 0, s>>>(yp.p, (cplx *)d_Y, D * nc);
+    FDS_CUDA_TRY(cudaGetLastError());
+    FDS_CUDA_TRY(cudaStreamSynchronize(s));
+    int st = 0;
+    FDS_TRY(oz_status_take(s, &st));
+    return st ? FDS_ERR_TIMEOUT : FDS_OK;
 }
 
 int oz_status_take(cudaStream_t s, int *status) {

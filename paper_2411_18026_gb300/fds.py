@@ -123,6 +123,7 @@ def lib():
     L.fds_cgemm_c64_batched.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), i64p,
                                         i64p, i64p, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, i32, u64]
     L.fds_alu_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
+    L.fds_zgemm_blocks_tc.argtypes = [i32, ctypes.POINTER(i32), vp, vp, vp, i32, u64]
     L.fds_autotune_enable.argtypes = [i32]
     L.fds_autotune_enable.restype = None
     L.fds_autotune_reset.argtypes = []
@@ -437,6 +438,17 @@ def fds_alu_peak(kind):
     v = ctypes.c_double()
     _check(lib().fds_alu_peak(int(kind), ctypes.byref(v)), "fds_alu_peak")
     return v.value
+
+
+def fds_zgemm_blocks_tc(d, d_A, d_X, d_Y, stream=None):
+    """Y_b += A_b X_b on the tensor cores (six bf16 slices per FP64 operand).
+    d: block sizes; d_A: complex128 CUDA tensor of the blocks back to back
+    (column-major); d_X, d_Y: complex128 (nc, sum d) tensors (column-major
+    (sum d) x nc); d_Y updated in place."""
+    d = np.ascontiguousarray(d, dtype=np.int32)
+    nc = d_X.shape[0] if d_X.dim() == 2 else 1
+    _check(lib().fds_zgemm_blocks_tc(len(d), d.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _ptr(d_A),
+                                     _ptr(d_X), _ptr(d_Y), nc, _stream(stream)), "fds_zgemm_blocks_tc")
 
 
 def fds_autotune_enable(on=True):
