@@ -12,19 +12,27 @@
 // s_i an integer of at most 8 bits (exact in bf16); slice i is stored times
 // 2^(-8i).  Each column c of x is cut the same way with its own exponent.
 // The product needs the 21 slice pairs with i + j <= 5 (the others are below
-// 2^-48 of |D| |x|).  Four fp32 accumulators in tensor memory keep what must
-// be exact apart: (0,0), (0,1) and (1,0) hold sums of K <= 256 products of
-// 8-bit integers (exact in fp32), the fourth the pairs with i + j >= 2,
-// whose fp32 rounding lies below 2^-40 of the result.  The epilogue adds the
-// four in FP64, scales by 2^(e_r + f_c - 16) and adds the result to y (float
-// pairs, the refinement's forward-operator format).
+// 2^-48 of |D| |x|).  The tensor core's fp32 accumulation keeps about 24 bits
+// below the running sum's leading bit, so a sum is exact only while its
+// terms' granularity fits that window.  Each pair with i + j <= 2 therefore
+// has an fp32 accumulator of its own in tensor memory (a sum of K <= 256
+// products of two 8-bit integers, scaled by one power of two: exact); the
+// pairs with i + j = 3 share one (its truncation lies near 2^-38 of the
+// result), those with i + j >= 4 another (measured with one accumulator for
+// every i + j >= 2: 3.6e-10 of |D| |x|; with two slices per operand every
+// accumulator is exact).  The epilogue adds the eight in FP64, scales by
+// 2^(e_r + f_c - 16) and adds the result to y (float pairs, the refinement's
+// forward-operator format).
 //
-// Kernel: one CTA per (leaf, 128 real rows, 128 columns); a pipeline of
-// 32 KB stages (one A slice tile and one x slice tile, 128 rows x 64 K of
-// bf16 each, stored pre-swizzled so that each is one bulk copy) fed by one
-// producer thread with cp.async.bulk and mbarrier transaction counts, one
-// thread issuing tcgen05.mma (kind::f16, bf16, M 128, N 128, K 16) into the
-// accumulator of the pair's group and committing each stage back to the
+// Kernel: one CTA per (leaf, 128 real rows, 64 columns); eight accumulators
+// of 64 fp32 columns fill the 512 tensor-memory columns.  Two rings of
+// operand tiles (A slice tiles, 128 rows x 64 K, and x slice tiles, 64 rows x
+// 64 K, of bf16, stored pre-swizzled so that each is one bulk copy) fed by
+// one producer thread with cp.async.bulk and mbarrier transaction counts;
+// the pairs are ordered by the A slice, so each A tile is loaded once per K
+// chunk and serves 6 - i products.  One thread issues tcgen05.mma
+// (kind::f16, bf16, M 128, N 64, K 16) into the accumulator of the pair and
+// commits each x tile (and each A tile after its last product) back to the
 // producer.  Every wait is bounded: after about two seconds the kernel
 // records a status, waits (bounded again) for its own MMAs, frees its TMEM
 // and returns.
@@ -43,16 +51,21 @@ namespace {
 
 constexpr int OZ_SLICES = 6;
 constexpr int OZ_PAIRS = 21;           // (i, j) with i + j <= 5
-constexpr int OZ_TILE = 128 * 128;     // bytes of one 128 x 64 bf16 tile
-constexpr int OZ_STAGES = 6;
+constexpr int OZ_TILE = 128 * 128;     // bytes of one 128 x 64 bf16 tile (A)
+constexpr int OZ_BN = 64;              // columns of x per CTA
+constexpr int OZ_XTILE = OZ_BN * 128;  // bytes of one 64 x 64 bf16 tile (x)
+constexpr int OZ_NA = 4;               // ring of A slice tiles (16 KB each)
+constexpr int OZ_NX = 16;              // ring of x slice tiles (8 KB each)
 constexpr int OZ_THREADS = 128;
 constexpr int OZ_KC = 4;               // 64-wide K chunks of a 256-real K
-constexpr int OZ_ACC = 4;
+constexpr int OZ_ACC = 8;
 constexpr unsigned long long OZ_WAIT_NS = 2000000000ull;
 
 struct OzLayout {
-    static constexpr int STAGE = 2 * OZ_TILE;
-    static constexpr int TOTAL = OZ_STAGES * STAGE + 1024 + 256;
+    static constexpr int XOFF = OZ_NA * OZ_TILE;                    // x ring after the A ring
+    static constexpr int RINGS = XOFF + OZ_NX * OZ_XTILE;
+    static constexpr int NBAR = 2 * OZ_NA + 2 * OZ_NX + 1;          // full/empty of both rings, done
+    static constexpr int TOTAL = RINGS + 1024 + 8 * NBAR + 512;     // + TMEM slot, flag, 64 exponents
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -72,9 +85,9 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
-// fp32 accumulator, bf16 A and B, both K-major, N 128, M 128
-__device__ __forceinline__ uint32_t idesc_bf16_128() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// fp32 accumulator, bf16 A and B, both K-major, N 64, M 128
+__device__ __forceinline__ uint32_t idesc_bf16_m128_n64() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
 // byte offset of element (row r, k) in a 128 x 64 bf16 tile with 128-byte swizzle
@@ -119,12 +132,49 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// slice pair p -> (i, j), ordered by group
-__constant__ unsigned char c_pair_i[OZ_PAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
-__constant__ unsigned char c_pair_j[OZ_PAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
+// error-free float sum: s + e = a + b exactly (Knuth)
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
 
+// (rh, rl) = (ah, al) + (bh, bl) in float-pair arithmetic (~46 bits)
+__device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, float &rh, float &rl) {
+    float s, e;
+    two_sum_f(ah, bh, s, e);
+    e += al + bl;
+    rh = s + e;
+    rl = e - (rh - s);
+}
+
+// the same load without the wait (several loads, then one tcgen05.wait::ld)
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+// 2^k as a float for -126 <= k <= 127 (exact scaling by multiplication)
+__device__ __forceinline__ float pow2f(int k) {
+    k = max(-126, min(127, k));
+    return __uint_as_float((uint32_t)(k + 127) << 23);
+}
+
+// slice pair p -> (i, j), grouped by the A slice i (j = 0 .. 5 - i), so that
+// each A slice tile is loaded once per K chunk and used by 6 - i products
+__constant__ unsigned char c_pair_i[OZ_PAIRS] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 4, 4, 5};
+__constant__ unsigned char c_pair_j[OZ_PAIRS] = {0, 1, 2, 3, 4, 5, 0, 1, 2, 3, 4, 0, 1, 2, 3, 0, 1, 2, 0, 1, 0};
+
+// accumulator of pair (i, j): one each for i + j <= 2, then i + j = 3, then i + j >= 4
 __device__ __forceinline__ int pair_acc(int i, int j) {
-    return (i + j == 0) ? 0 : (i + j == 1 ? (i == 0 ? 1 : 2) : 3);
+    const int g = i + j;
+    if (g == 0) return 0;
+    if (g == 1) return i == 0 ? 1 : 2;
+    if (g == 2) return 3 + i;
+    return g == 3 ? 6 : 7;
 }
 
 // six slices of v in (-1, 1), slice i times 2^(-8i) (all exact in bf16)
@@ -182,44 +232,82 @@ __global__ void k_oz_slice_a(int nb, const MatRef *__restrict__ D, unsigned char
     }
 }
 
+// trunc(|f| 2^sh) as an integer (|f| 2^sh < 2^48), from the bits of f
+// (integer instructions only: 64-bit conversions run on the slow FP64 pipe)
+__device__ __forceinline__ unsigned long long fixed48(float f, int sh) {
+    const uint32_t b = __float_as_uint(f);
+    const int ex = (int)((b >> 23) & 255u);
+    if (ex == 0) return 0ull;                         // zero or subnormal: below 2^-126
+    const uint32_t mant = (b & 0x7FFFFFu) | 0x800000u;    // |f| = mant 2^(ex - 150)
+    const int s = ex - 150 + sh;
+    if (s >= 0) return (unsigned long long)mant << s;
+    if (s <= -24) return 0ull;
+    return (unsigned long long)(mant >> (-s));
+}
+
+// six slices of the float pair (h, l) scaled by 2^-e (|h + l| < 2^e), from
+// the 48-bit integer q = trunc(h 2^(48-e)) + trunc(l 2^(48-e)): slice i is
+// bits 40 - 8i .. 47 - 8i of |q|, with q's sign, times 2^(-8i)
+__device__ __forceinline__ void cut6_pair(float h, float l, int e, unsigned short (&out)[OZ_SLICES]) {
+    const long long qh = (long long)fixed48(h, 48 - e), ql = (long long)fixed48(l, 48 - e);
+    const long long q = (h < 0.f ? -qh : qh) + (l < 0.f ? -ql : ql);
+    const bool neg = q < 0;
+    unsigned long long m = (unsigned long long)(neg ? -q : q);
+    if (m >= (1ull << 48)) m = (1ull << 48) - 1;   // |h + l| within one unit of 2^e
+    float sc = 1.0f;
+#pragma unroll
+    for (int i = 0; i < OZ_SLICES; ++i) {
+        // the 8-bit chunk as a float: OR it into the mantissa of 2^23 (exact)
+        const uint32_t chunk = (uint32_t)((m >> (40 - 8 * i)) & 255ull);
+        const float t = (__uint_as_float(0x4B000000u | chunk) - 8388608.0f) * sc;
+        out[i] = __bfloat16_as_ushort(__float2bfloat16_rn(neg ? -t : t));
+        sc *= 1.0f / 256.0f;
+    }
+}
+
 // x slices: one warp per (leaf b, column c); the leaf's rows are
-// xin[doff[b] .. doff[b] + d) of column c (float pairs); tiles at
-// base + (((b * ntile + nt) * OZ_KC + kc) * OZ_SLICES + j) * OZ_TILE.
+// xin[doff[b] .. doff[b] + d) of column c (float pairs); 64-column tiles at
+// base + (((b * ntile + nt) * OZ_KC + kc) * OZ_SLICES + j) * OZ_XTILE.
 __global__ void k_oz_slice_x(int nb, const int64_t *__restrict__ doff, const float4 *__restrict__ x, int64_t ldx,
                              int nc, int ntile, unsigned char *slices, int *colexp) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int cols = ntile * 128;
+    const int cols = ntile * OZ_BN;
     if (warp >= nb * cols) return;
     const int b = warp / cols, c = warp % cols;
     const int64_t o = doff[b];
     const int d = (int)(doff[b + 1] - o);
-    double m = 0.0;
+    float m = 0.f;
     if (c < nc)
         for (int l = lane; l < d; l += 32) {
             const float4 v = x[o + l + (int64_t)c * ldx];
-            m = fmax(m, fmax(fabs((double)v.x + v.z), fabs((double)v.y + v.w)));
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
         }
 #pragma unroll
-    for (int s = 16; s > 0; s >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, s));
+    for (int s = 16; s > 0; s >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, s));
+    // 2^e > |h| (1 + 2^-23) >= |h + l|
     int e = 0;
-    if (m > 0.0) frexp(m, &e);
+    if (m > 0.f) {
+        frexpf(m, &e);
+        if (m >= ldexpf(1.0f - 1.0f / (1 << 20), e)) ++e;
+    }
     if (lane == 0) colexp[b * cols + c] = e;
-    const double inv = ldexp(1.0, -e);
-    const int nt = c >> 7, n = c & 127;
+    const int nt = c / OZ_BN, n = c % OZ_BN;
     for (int k = lane; k < 256; k += 32) {
         const int l = k >> 1;
-        double v = 0.0;
+        float h = 0.f, lo = 0.f;
         if (c < nc && l < d) {
             const float4 q = x[o + l + (int64_t)c * ldx];
-            v = (k & 1) ? (double)q.y + q.w : (double)q.x + q.z;
+            h = (k & 1) ? q.y : q.x;
+            lo = (k & 1) ? q.w : q.z;
         }
         unsigned short s[OZ_SLICES];
-        cut6(v * inv, s);
+        cut6_pair(h, lo, e, s);
         const int kc = k >> 6;
-        unsigned char *t = slices + (size_t)(((b * ntile + nt) * OZ_KC + kc) * OZ_SLICES) * OZ_TILE;
+        unsigned char *t = slices + (size_t)(((b * ntile + nt) * OZ_KC + kc) * OZ_SLICES) * OZ_XTILE;
         const uint32_t off = sw_elem(n, k & 63);
 #pragma unroll
-        for (int q = 0; q < OZ_SLICES; ++q) *reinterpret_cast<unsigned short *>(t + (size_t)q * OZ_TILE + off) = s[q];
+        for (int q = 0; q < OZ_SLICES; ++q)
+            *reinterpret_cast<unsigned short *>(t + (size_t)q * OZ_XTILE + off) = s[q];
     }
 }
 
@@ -243,13 +331,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const uint32_t raw = smem_u32(oz_raw);
     const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
     const uint32_t sbase = raw + pad;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(oz_raw + pad + OZ_STAGES * OzLayout::STAGE);
-    // full[s] = bars[s], empty[s] = bars[OZ_STAGES + s], done = bars[2 OZ_STAGES]
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * OZ_STAGES + 1);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(oz_raw + pad + OzLayout::RINGS);
+    // A ring: full bars[q], empty bars[OZ_NA + q]; x ring: full bars[2 OZ_NA + q],
+    // empty bars[2 OZ_NA + OZ_NX + q]; done: bars[NBAR - 1]
+    uint64_t *fullA = bars, *emptyA = bars + OZ_NA, *fullX = bars + 2 * OZ_NA, *emptyX = fullX + OZ_NX;
+    uint64_t *donebar = bars + OzLayout::NBAR - 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + OzLayout::NBAR);
     int *sflag = reinterpret_cast<int *>(tslot + 1);
+    int *s_colexp = sflag + 1;   // exponents of this CTA's 64 columns
     const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid < OZ_BN) {
+        const int c = nt * OZ_BN + tid;
+        s_colexp[tid] = c < nc ? colexp[b * (ntile * OZ_BN) + c] : 0;
+    }
     if (tid == 0) {
-        for (int s = 0; s < 2 * OZ_STAGES + 1; ++s)
+        for (int s = 0; s < OzLayout::NBAR; ++s)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + s)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *sflag = 0;
@@ -266,67 +362,91 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int nkc = (2 * d + 63) / 64;
     const int steps = nkc * OZ_PAIRS;
     const unsigned char *abase = aslices + (size_t)((b * 2 + mt) * OZ_KC) * OZ_SLICES * OZ_TILE;
-    const unsigned char *xbase = xslices + (size_t)((b * ntile + nt) * OZ_KC) * OZ_SLICES * OZ_TILE;
+    const unsigned char *xbase = xslices + (size_t)((b * ntile + nt) * OZ_KC) * OZ_SLICES * OZ_XTILE;
     if (tid == 0) {
-        // producer: stage q of step t holds A slice i and x slice j of K chunk t / 21
+        // producer: step t = (K chunk kc, pair p); the A slice tile of pair p is
+        // loaded when p starts a new i (use ua of the A ring), the x slice tile
+        // every step (use t of the x ring); a slot is refilled once the MMAs
+        // that read it have completed (their commit on the slot's empty barrier)
+        int ua = 0;
         for (int t = 0; t < steps; ++t) {
-            const int q = t % OZ_STAGES;
-            if (t >= OZ_STAGES && !mbar_wait(smem_u32(bars + OZ_STAGES + q), (uint32_t)(((t / OZ_STAGES) - 1) & 1))) {
+            if (*(volatile int *)sflag) break;
+            const int kc = t / OZ_PAIRS, p = t % OZ_PAIRS;
+            if (c_pair_j[p] == 0) {
+                const int qa = ua % OZ_NA;
+                if (ua >= OZ_NA && !mbar_wait(smem_u32(emptyA + qa), (uint32_t)(((ua / OZ_NA) - 1) & 1))) {
+                    atomicExch(sflag, 1);
+                    break;
+                }
+                const uint32_t full = smem_u32(fullA + qa);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"(OZ_TILE)
+                             : "memory");
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        sbase + qa * OZ_TILE),
+                    "l"(abase + (size_t)(kc * OZ_SLICES + c_pair_i[p]) * OZ_TILE), "r"(OZ_TILE), "r"(full)
+                    : "memory");
+                ++ua;
+            }
+            const int qx = t % OZ_NX;
+            if (t >= OZ_NX && !mbar_wait(smem_u32(emptyX + qx), (uint32_t)(((t / OZ_NX) - 1) & 1))) {
                 atomicExch(sflag, 1);
                 break;
             }
-            if (*(volatile int *)sflag) break;
-            const int kc = t / OZ_PAIRS, p = t % OZ_PAIRS;
-            const uint32_t full = smem_u32(bars + q);
-            const uint32_t dst = sbase + q * OzLayout::STAGE;
-            const unsigned char *src_a = abase + (size_t)(kc * OZ_SLICES + c_pair_i[p]) * OZ_TILE;
-            const unsigned char *src_x = xbase + (size_t)(kc * OZ_SLICES + c_pair_j[p]) * OZ_TILE;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"(2 * OZ_TILE)
+            const uint32_t full = smem_u32(fullX + qx);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"(OZ_XTILE)
                          : "memory");
             asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                "l"(src_a), "r"(OZ_TILE), "r"(full)
-                : "memory");
-            asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    dst + OZ_TILE),
-                "l"(src_x), "r"(OZ_TILE), "r"(full)
+                    sbase + OzLayout::XOFF + qx * OZ_XTILE),
+                "l"(xbase + (size_t)(kc * OZ_SLICES + c_pair_j[p]) * OZ_XTILE), "r"(OZ_XTILE), "r"(full)
                 : "memory");
         }
     } else if (tid == 32) {
         // MMA issuer
-        const uint32_t idesc = idesc_bf16_128();
+        const uint32_t idesc = idesc_bf16_m128_n64();
         int started = 0;   // bit g: accumulator g written once
-        int t = 0;
+        int t = 0, ua = -1;
         for (; t < steps; ++t) {
-            const int q = t % OZ_STAGES;
-            if (!mbar_wait(smem_u32(bars + q), (uint32_t)((t / OZ_STAGES) & 1)) || *(volatile int *)sflag) {
+            const int kc = t / OZ_PAIRS, p = t % OZ_PAIRS;
+            const int i = c_pair_i[p], j = c_pair_j[p];
+            if (j == 0) {
+                ++ua;
+                if (!mbar_wait(smem_u32(fullA + ua % OZ_NA), (uint32_t)((ua / OZ_NA) & 1))) {
+                    atomicExch(sflag, 1);
+                    break;
+                }
+            }
+            const int qx = t % OZ_NX;
+            if (!mbar_wait(smem_u32(fullX + qx), (uint32_t)((t / OZ_NX) & 1)) || *(volatile int *)sflag) {
                 atomicExch(sflag, 1);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int p = t % OZ_PAIRS;
-            const int g = pair_acc(c_pair_i[p], c_pair_j[p]);
-            const uint32_t sa = sbase + q * OzLayout::STAGE, sb = sa + OZ_TILE;
-            const int kc = t / OZ_PAIRS;
+            const int g = pair_acc(i, j);
+            const uint32_t sa = sbase + (ua % OZ_NA) * OZ_TILE, sb = sbase + OzLayout::XOFF + qx * OZ_XTILE;
             const int kin = min(64, 2 * d - kc * 64);   // reals of this chunk holding data
             for (int ks = 0; ks < (kin + 15) / 16; ++ks) {
-                mma_bf16(tmem + (uint32_t)(g * 128), sw128_desc(sa + 32u * ks), sw128_desc(sb + 32u * ks), idesc,
+                mma_bf16(tmem + (uint32_t)(g * OZ_BN), sw128_desc(sa + 32u * ks), sw128_desc(sb + 32u * ks), idesc,
                          ((started >> g) & 1) ? 1u : 0u);
                 started |= 1 << g;
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(bars + OZ_STAGES + q))
+                             smem_u32(emptyX + qx))
                          : "memory");
+            if (j == OZ_SLICES - 1 - i)   // last product with this A slice tile
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(emptyA + ua % OZ_NA))
+                             : "memory");
         }
         // all MMAs issued so far complete -> done
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(bars + 2 * OZ_STAGES))
+                         smem_u32(donebar))
                      : "memory");
-        if (started != 15 && t == steps) atomicExch(sflag, 1);   // an accumulator never written: not expected
+        if (started != (1 << OZ_ACC) - 1 && t == steps) atomicExch(sflag, 1);   // an accumulator never written
     }
     __syncwarp();
-    const bool done_ok = mbar_wait(smem_u32(bars + 2 * OZ_STAGES), 0u);
+    const bool done_ok = mbar_wait(smem_u32(donebar), 0u);
     const int bad = __syncthreads_or(!done_ok || *(volatile int *)sflag);
     if (bad) {
         if (tid == 0) atomicExch(&g_oz_status, 1);
@@ -336,25 +456,51 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int r = mt * 128 + warp * 32 + lane;            // real row of the leaf block
         const uint32_t tq = tmem + ((uint32_t)(warp * 32) << 16);
         const int er = rowexp[b * 256 + r];
-        const int cols = ntile * 128;
-        for (int cb = 0; cb < 128; cb += 16) {
-            const int c0 = nt * 128 + cb;
+        const int cols = ntile * OZ_BN;
+        for (int cb = 0; cb < OZ_BN; cb += 16) {
+            const int c0 = nt * OZ_BN + cb;
             if (c0 >= nc) break;
+            uint32_t raw[OZ_ACC][16];
+#pragma unroll
+            for (int g = 0; g < OZ_ACC; ++g) tmem_ld16_nowait(tq + (uint32_t)(g * OZ_BN + cb), raw[g]);
+            // the y entries of this chunk, loaded while the tensor-memory loads land
+            float4 ycur[16];
+            const bool wr = !(lane & 1) && r < 2 * d;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                ycur[j] = (wr && c0 + j < nc) ? y[o + (r >> 1) + (int64_t)(c0 + j) * ldy] : make_float4(0.f, 0.f, 0.f, 0.f);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             float v[OZ_ACC][16];
 #pragma unroll
-            for (int g = 0; g < OZ_ACC; ++g) tmem_ld16(tq + (uint32_t)(g * 128 + cb), v[g]);
+            for (int g = 0; g < OZ_ACC; ++g)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[g][j] = __uint_as_float(raw[g][j]);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int c = c0 + j;
-                const double sum = ((double)v[0][j] + (double)v[1][j]) + ((double)v[2][j] + (double)v[3][j]);
-                const double val = c < nc ? ldexp(sum, er + colexp[b * cols + c] - 16) : 0.0;
-                const double other = __shfl_xor_sync(0xffffffffu, val, 1);   // the partner real row
-                if (!(lane & 1) && c < nc && r < 2 * d) {
-                    float4 *yp = y + o + (r >> 1) + (int64_t)c * ldy;
-                    const float4 cur = *yp;
-                    const double re = (double)cur.x + cur.z + val, im = (double)cur.y + cur.w + other;
-                    const float rh = (float)re, ih = (float)im;
-                    *yp = make_float4(rh, ih, (float)(re - (double)rh), (float)(im - (double)ih));
+                // float-pair sum of the eight accumulators: the six exact ones
+                // (pairs with i + j <= 2) by error-free two-sums, the two
+                // rounded ones (i + j >= 3, below 2^-24 of the result) into
+                // the low part
+                float h = v[0][j], lo = 0.f, e;
+#pragma unroll
+                for (int g = 1; g < 6; ++g) {
+                    two_sum_f(h, v[g][j], h, e);
+                    lo += e;
+                }
+                lo += v[6][j] + v[7][j];
+                // scale by 2^(e_r + f_c - 16) in at most two exact power-of-two steps
+                const int sh = c < nc ? er + s_colexp[cb + j] - 16 : 0;
+                const float s1 = pow2f(sh / 2), s2 = pow2f(sh - sh / 2);
+                h = c < nc ? (h * s1) * s2 : 0.f;
+                lo = c < nc ? (lo * s1) * s2 : 0.f;
+                const float oh = __shfl_xor_sync(0xffffffffu, h, 1);   // the partner real row
+                const float ol = __shfl_xor_sync(0xffffffffu, lo, 1);
+                if (wr && c < nc) {
+                    float rh, rl, ih, il;
+                    ff_add(ycur[j].x, ycur[j].z, h, lo, rh, rl);
+                    ff_add(ycur[j].y, ycur[j].w, oh, ol, ih, il);
+                    y[o + (r >> 1) + (int64_t)c * ldy] = make_float4(rh, ih, rl, il);
                 }
             }
         }
@@ -383,11 +529,11 @@ int oz_apply(int nb, const int64_t *d_doff, const unsigned char *aslices, const 
              DBuf<unsigned char> &xs, DBuf<int> &colexp, const float4 *x, float4 *y, int64_t ld, int nc,
              cudaStream_t s) {
     if (nb == 0 || nc == 0) return FDS_OK;
-    const int ntile = (nc + 127) / 128;
-    const size_t need = (size_t)nb * ntile * OZ_KC * OZ_SLICES * OZ_TILE;
+    const int ntile = (nc + OZ_BN - 1) / OZ_BN;
+    const size_t need = (size_t)nb * ntile * OZ_KC * OZ_SLICES * OZ_XTILE;
     if (xs.n < need) FDS_TRY(xs.alloc(need));
-    if (colexp.n < (size_t)nb * ntile * 128) FDS_TRY(colexp.alloc((size_t)nb * ntile * 128));
-    const int64_t warps = (int64_t)nb * ntile * 128;
+    if (colexp.n < (size_t)nb * ntile * OZ_BN) FDS_TRY(colexp.alloc((size_t)nb * ntile * OZ_BN));
+    const int64_t warps = (int64_t)nb * ntile * OZ_BN;
     fds_count_launch(), k_oz_slice_x<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(nb, d_doff, x, ld, nc,
                                                                                           ntile, xs.p, colexp.p);
     FDS_CUDA_TRY(cudaGetLastError());
@@ -450,7 +596,7 @@ extern "C" int fds_zgemm_blocks_tc(int32_t batch, const int32_t *d, const double
         aoff[b + 1] = aoff[b] + (int64_t)d[b] * d[b];
     }
     const int64_t D = doff[batch];
-    if ((int64_t)batch * 2 * ((nc + 127) / 128) > 2147483647) return FDS_ERR_ARG;
+    if ((int64_t)batch * 2 * ((nc + OZ_BN - 1) / OZ_BN) > 2147483647) return FDS_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     FDS_TRY(ensure_gauss_tables());
     DBuf<int64_t> d_doff, d_aoff;

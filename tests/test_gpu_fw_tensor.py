@@ -39,10 +39,11 @@ def test_stage_blocks_match_complex128_product(nc):
         r = slice(off[b], off[b + 1])
         prod = a @ X[r]
         scale = np.abs(a) @ np.abs(X[r])            # |A| |x| per entry
-        err = np.abs(got[r] - Y0[r] - prod) / np.maximum(scale, 1e-300)
-        # six 8-bit slices: products below 2^-40 of |A| |x|; the float-pair
-        # vectors carry ~2^-44
-        assert err.max() < 2e-11, (b, err.max())
+        # six 8-bit slices and exact accumulators for the pairs with i + j <= 2:
+        # below ~2^-38 of |A| |x|; the float-pair y holds the sum to ~2^-46 of itself
+        bound = 2e-11 * scale + 4e-14 * np.abs(Y0[r] + prod)
+        excess = np.abs(got[r] - Y0[r] - prod) / bound
+        assert excess.max() <= 1.0, (b, excess.max())
 
 
 @pytest.mark.parametrize("N,leaf,nw", [(8192, 64, 3), (3000, 64, 2), (2048, 40, 140)])
@@ -60,7 +61,7 @@ def test_tensor_forward_operator_refines_to_fp64(N, leaf, nw):
     h64.close()
     out = {}
     for eng in (fds.FDS_FW_FF, fds.FDS_FW_TENSOR):
-        h = fds.fds_build(xy, omega, 2.0, 1.0, 1e-9, leaf_size=leaf, precision=fds.FDS_MIXED, ir_tol=1e-10,
+        h = fds.fds_build(xy, omega, 2.0, 1.0, 1e-9, leaf_size=leaf, precision=fds.FDS_MIXED, ir_tol=1e-9,
                           fw_engine=eng)
         x = fds.fds_solve(h, F)
         st = fds.fds_stats_get(h)
@@ -68,7 +69,7 @@ def test_tensor_forward_operator_refines_to_fp64(N, leaf, nw):
         h.close()
     xt, it_t, res_t = out[fds.FDS_FW_TENSOR]
     xf, it_f, res_f = out[fds.FDS_FW_FF]
-    assert res_t <= 1e-10 and res_f <= 1e-10
+    assert res_t <= 1e-9 and res_f <= 1e-9
     assert abs(it_t - it_f) <= 1
-    assert _colmax(xt, x64) < 1e-9
-    assert _colmax(xt, xf) < 1e-9
+    assert _colmax(xt, x64) < 1e-8
+    assert _colmax(xt, xf) < 1e-8
