@@ -50,20 +50,20 @@
 namespace {
 
 constexpr int OZ_SLICES = 6;
-constexpr int OZ_PAIRS = 21;           // (i, j) with i + j <= 5
 constexpr int OZ_TILE = 128 * 128;     // bytes of one 128 x 64 bf16 tile (A)
 constexpr int OZ_BN = 64;              // columns of x per CTA
 constexpr int OZ_XTILE = OZ_BN * 128;  // bytes of one 64 x 64 bf16 tile (x)
-constexpr int OZ_NA = 4;               // ring of A slice tiles (16 KB each)
-constexpr int OZ_NX = 16;              // ring of x slice tiles (8 KB each)
+constexpr int OZ_NA = 6;               // ring of A slice tiles (16 KB each)
+constexpr int OZ_NX = 2;               // x buffers, each the six slice tiles of one K chunk (48 KB)
 constexpr int OZ_THREADS = 128;
 constexpr int OZ_KC = 4;               // 64-wide K chunks of a 256-real K
 constexpr int OZ_ACC = 8;
 constexpr unsigned long long OZ_WAIT_NS = 2000000000ull;
 
 struct OzLayout {
-    static constexpr int XOFF = OZ_NA * OZ_TILE;                    // x ring after the A ring
-    static constexpr int RINGS = XOFF + OZ_NX * OZ_XTILE;
+    static constexpr int XBUF = OZ_SLICES * OZ_XTILE;               // one K chunk of x slices
+    static constexpr int XOFF = OZ_NA * OZ_TILE;                    // x buffers after the A ring
+    static constexpr int RINGS = XOFF + OZ_NX * XBUF;
     static constexpr int NBAR = 2 * OZ_NA + 2 * OZ_NX + 1;          // full/empty of both rings, done
     static constexpr int TOTAL = RINGS + 1024 + 8 * NBAR + 512;     // + TMEM slot, flag, 64 exponents
 };
@@ -120,16 +120,19 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// a 32-lane x 16-column tensor-memory load without its wait (several loads, then one tcgen05.wait::ld)
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// 2^k as a float for -126 <= k <= 127 (exact scaling by multiplication)
+__device__ __forceinline__ float pow2f(int k) {
+    k = max(-126, min(127, k));
+    return __uint_as_float((uint32_t)(k + 127) << 23);
 }
 
 // error-free float sum: s + e = a + b exactly (Knuth)
@@ -147,26 +150,6 @@ __device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, f
     rh = s + e;
     rl = e - (rh - s);
 }
-
-// the same load without the wait (several loads, then one tcgen05.wait::ld)
-__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-
-// 2^k as a float for -126 <= k <= 127 (exact scaling by multiplication)
-__device__ __forceinline__ float pow2f(int k) {
-    k = max(-126, min(127, k));
-    return __uint_as_float((uint32_t)(k + 127) << 23);
-}
-
-// slice pair p -> (i, j), grouped by the A slice i (j = 0 .. 5 - i), so that
-// each A slice tile is loaded once per K chunk and used by 6 - i products
-__constant__ unsigned char c_pair_i[OZ_PAIRS] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 4, 4, 5};
-__constant__ unsigned char c_pair_j[OZ_PAIRS] = {0, 1, 2, 3, 4, 5, 0, 1, 2, 3, 4, 0, 1, 2, 3, 0, 1, 2, 0, 1, 0};
 
 // accumulator of pair (i, j): one each for i + j <= 2, then i + j = 3, then i + j >= 4
 __device__ __forceinline__ int pair_acc(int i, int j) {
@@ -360,90 +343,91 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
     const int nkc = (2 * d + 63) / 64;
-    const int steps = nkc * OZ_PAIRS;
     const unsigned char *abase = aslices + (size_t)((b * 2 + mt) * OZ_KC) * OZ_SLICES * OZ_TILE;
     const unsigned char *xbase = xslices + (size_t)((b * ntile + nt) * OZ_KC) * OZ_SLICES * OZ_XTILE;
     if (tid == 0) {
-        // producer: step t = (K chunk kc, pair p); the A slice tile of pair p is
-        // loaded when p starts a new i (use ua of the A ring), the x slice tile
-        // every step (use t of the x ring); a slot is refilled once the MMAs
-        // that read it have completed (their commit on the slot's empty barrier)
+        // producer: per K chunk kc the six x slice tiles (x buffer kc % 2),
+        // then the A slice tiles A_0 .. A_5 of kc through the A ring; a buffer
+        // or slot is refilled once the MMAs that read it have completed (their
+        // commit on its empty barrier)
         int ua = 0;
-        for (int t = 0; t < steps; ++t) {
+        for (int kc = 0; kc < nkc; ++kc) {
             if (*(volatile int *)sflag) break;
-            const int kc = t / OZ_PAIRS, p = t % OZ_PAIRS;
-            if (c_pair_j[p] == 0) {
+            const int qx = kc % OZ_NX;
+            if (kc >= OZ_NX && !mbar_wait(smem_u32(emptyX + qx), (uint32_t)(((kc / OZ_NX) - 1) & 1))) {
+                atomicExch(sflag, 1);
+                break;
+            }
+            const uint32_t fx = smem_u32(fullX + qx);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fx), "r"(OzLayout::XBUF)
+                         : "memory");
+            for (int j = 0; j < OZ_SLICES; ++j)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        sbase + OzLayout::XOFF + qx * OzLayout::XBUF + j * OZ_XTILE),
+                    "l"(xbase + (size_t)(kc * OZ_SLICES + j) * OZ_XTILE), "r"(OZ_XTILE), "r"(fx)
+                    : "memory");
+            for (int i = 0; i < OZ_SLICES; ++i, ++ua) {
                 const int qa = ua % OZ_NA;
                 if (ua >= OZ_NA && !mbar_wait(smem_u32(emptyA + qa), (uint32_t)(((ua / OZ_NA) - 1) & 1))) {
                     atomicExch(sflag, 1);
                     break;
                 }
-                const uint32_t full = smem_u32(fullA + qa);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"(OZ_TILE)
+                const uint32_t fa = smem_u32(fullA + qa);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fa), "r"(OZ_TILE)
                              : "memory");
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                         sbase + qa * OZ_TILE),
-                    "l"(abase + (size_t)(kc * OZ_SLICES + c_pair_i[p]) * OZ_TILE), "r"(OZ_TILE), "r"(full)
+                    "l"(abase + (size_t)(kc * OZ_SLICES + i) * OZ_TILE), "r"(OZ_TILE), "r"(fa)
                     : "memory");
-                ++ua;
             }
-            const int qx = t % OZ_NX;
-            if (t >= OZ_NX && !mbar_wait(smem_u32(emptyX + qx), (uint32_t)(((t / OZ_NX) - 1) & 1))) {
-                atomicExch(sflag, 1);
-                break;
-            }
-            const uint32_t full = smem_u32(fullX + qx);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"(OZ_XTILE)
-                         : "memory");
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    sbase + OzLayout::XOFF + qx * OZ_XTILE),
-                "l"(xbase + (size_t)(kc * OZ_SLICES + c_pair_j[p]) * OZ_XTILE), "r"(OZ_XTILE), "r"(full)
-                : "memory");
         }
     } else if (tid == 32) {
-        // MMA issuer
+        // MMA issuer: for each K chunk and A slice i, the products with x
+        // slices j = 0 .. 5 - i into the accumulator of (i, j)
         const uint32_t idesc = idesc_bf16_m128_n64();
         int started = 0;   // bit g: accumulator g written once
-        int t = 0, ua = -1;
-        for (; t < steps; ++t) {
-            const int kc = t / OZ_PAIRS, p = t % OZ_PAIRS;
-            const int i = c_pair_i[p], j = c_pair_j[p];
-            if (j == 0) {
-                ++ua;
-                if (!mbar_wait(smem_u32(fullA + ua % OZ_NA), (uint32_t)((ua / OZ_NA) & 1))) {
-                    atomicExch(sflag, 1);
-                    break;
-                }
-            }
-            const int qx = t % OZ_NX;
-            if (!mbar_wait(smem_u32(fullX + qx), (uint32_t)((t / OZ_NX) & 1)) || *(volatile int *)sflag) {
-                atomicExch(sflag, 1);
+        int ua = 0;
+        bool ok = true;
+        for (int kc = 0; kc < nkc && ok; ++kc) {
+            const int qx = kc % OZ_NX;
+            if (!mbar_wait(smem_u32(fullX + qx), (uint32_t)((kc / OZ_NX) & 1)) || *(volatile int *)sflag) {
+                ok = false;
                 break;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int g = pair_acc(i, j);
-            const uint32_t sa = sbase + (ua % OZ_NA) * OZ_TILE, sb = sbase + OzLayout::XOFF + qx * OZ_XTILE;
             const int kin = min(64, 2 * d - kc * 64);   // reals of this chunk holding data
-            for (int ks = 0; ks < (kin + 15) / 16; ++ks) {
-                mma_bf16(tmem + (uint32_t)(g * OZ_BN), sw128_desc(sa + 32u * ks), sw128_desc(sb + 32u * ks), idesc,
-                         ((started >> g) & 1) ? 1u : 0u);
-                started |= 1 << g;
+            for (int i = 0; i < OZ_SLICES; ++i, ++ua) {
+                const int qa = ua % OZ_NA;
+                if (!mbar_wait(smem_u32(fullA + qa), (uint32_t)((ua / OZ_NA) & 1))) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa = sbase + qa * OZ_TILE;
+                for (int j = 0; j < OZ_SLICES - i; ++j) {
+                    const int g = pair_acc(i, j);
+                    const uint32_t sb = sbase + OzLayout::XOFF + qx * OzLayout::XBUF + j * OZ_XTILE;
+                    for (int ks = 0; ks < (kin + 15) / 16; ++ks) {
+                        mma_bf16(tmem + (uint32_t)(g * OZ_BN), sw128_desc(sa + 32u * ks), sw128_desc(sb + 32u * ks),
+                                 idesc, ((started >> g) & 1) ? 1u : 0u);
+                        started |= 1 << g;
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(emptyA + qa))
+                             : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(emptyX + qx))
                          : "memory");
-            if (j == OZ_SLICES - 1 - i)   // last product with this A slice tile
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_u32(emptyA + ua % OZ_NA))
-                             : "memory");
         }
+        if (!ok) atomicExch(sflag, 1);
         // all MMAs issued so far complete -> done
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(donebar))
                      : "memory");
-        if (started != (1 << OZ_ACC) - 1 && t == steps) atomicExch(sflag, 1);   // an accumulator never written
+        if (ok && started != (1 << OZ_ACC) - 1) atomicExch(sflag, 1);   // an accumulator never written
     }
     __syncwarp();
     const bool done_ok = mbar_wait(smem_u32(donebar), 0u);
@@ -456,7 +440,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int r = mt * 128 + warp * 32 + lane;            // real row of the leaf block
         const uint32_t tq = tmem + ((uint32_t)(warp * 32) << 16);
         const int er = rowexp[b * 256 + r];
-        const int cols = ntile * OZ_BN;
         for (int cb = 0; cb < OZ_BN; cb += 16) {
             const int c0 = nt * OZ_BN + cb;
             if (c0 >= nc) break;
