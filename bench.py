@@ -61,9 +61,9 @@ def parse():
     p.add_argument("--tol-decay", type=float, default=0.5,
                    help="ID tolerance eps at the leaves, eps * decay^(L-l) at level l (1: the paper's single eps)")
     p.add_argument("--autotune", action="store_true", help="GEMM tile shapes from the autotuner (tuned in warm-up)")
-    p.add_argument("--fw-engine", default="ff", choices=["ff", "tensor"],
-                   help="mixed: leaf blocks of the refinement's forward operator as double-float products (ff) "
-                        "or on the tensor cores (six bf16 slices per FP64 operand)")
+    p.add_argument("--fw-engine", default="tensor", choices=["ff", "tensor"],
+                   help="mixed: leaf blocks of the refinement's forward operator on the tensor cores (default, six "
+                        "bf16 slices per FP64 operand) or as double-float products (ff)")
     p.add_argument("--c64-engine", default="simt", choices=["tensor", "simt"],
                    help="complex64 products on the tensor cores (bf16 pieces) or the FP32 pipe")
     p.add_argument("--sweep-ff", type=int, default=1, choices=[0, 1, 2],
