@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--sweep-fp64-levels", type=int, default=-1)
     p.add_argument("--merge", default="c64", choices=["c64", "fp64"],
                    help="mixed: merge the complex64 levels in complex64 (default) or FP64")
+    p.add_argument("--merge-c64-levels", type=int, default=0,
+                   help="with --merge c64: merge only the lowest N complex64 levels in complex64 (0: all)")
     p.add_argument("--tol-decay", type=float, default=0.5,
                    help="ID tolerance eps at the leaves, eps * decay^(L-l) at level l (1: the paper's single eps)")
     p.add_argument("--autotune", action="store_true", help="GEMM tile shapes from the autotuner (tuned in warm-up)")
@@ -573,7 +575,7 @@ def main():
                           mlp_params=params, merge_c64=args.merge == "c64" and precision == fds.FDS_MIXED,
                           fw_engine=fds.FDS_FW_TENSOR if args.fw_engine == "tensor" and precision == fds.FDS_MIXED
                           else fds.FDS_FW_FF,
-                          tol_decay=args.tol_decay,
+                          tol_decay=args.tol_decay, merge_c64_levels=args.merge_c64_levels,
                           sweep_ff=args.sweep_ff if precision == fds.FDS_MIXED else 0,
                           c64_engine=c64_engine)
         fds.fds_rhs_plane_wave_device(h, d_kinds, d_angles, out, stream)
@@ -663,6 +665,7 @@ def main():
         o.leaf_size, o.top_level = args.leaf, args.top
         o.precision, o.ir_tol, o.sweep_fp64_levels = prec, args.ir_tol, args.sweep_fp64_levels
         o.merge_c64 = 1 if args.merge == "c64" and prec == fds.FDS_MIXED else 0
+        o.merge_c64_levels = args.merge_c64_levels
         o.tol_decay = args.tol_decay
         o.fw_engine = fds.FDS_FW_TENSOR if args.fw_engine == "tensor" and prec == fds.FDS_MIXED else fds.FDS_FW_FF
         o.sweep_ff = args.sweep_ff
@@ -768,6 +771,7 @@ def main():
                                   + ", %s rank" % rank_used),
                    "l2": "working set (factors, vectors) larger than L2; no flush",
                    "precision": args.precision, "c64_engine": args.c64_engine, "merge": args.merge,
+                   "merge_c64_levels": args.merge_c64_levels,
                    "tol_decay": args.tol_decay, "autotune": bool(args.autotune), "fw_engine": args.fw_engine,
                    "fp64_reference": "plain FP64 build (adaptive CPQR, same eps and tol_decay) on the same inputs"},
         "ir_iters": info.get("ir_iters"), "ir_residual": info.get("ir_residual"),

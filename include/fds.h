@@ -161,6 +161,9 @@ typedef struct {
                               have one); default 0 */
     int32_t fw_engine;     /* FDS_MIXED: FDS_FW_FF (default) or FDS_FW_TENSOR for the leaf
                               diagonal blocks of the refinement's forward operator */
+    int32_t merge_c64_levels; /* with merge_c64 = 1: only the lowest merge_c64_levels of the
+                              complex64 levels are merged in complex64, the others in FP64;
+                              0 (default): all of them */
 } fds_options;
 
 /* Statistics of a built handle. */
@@ -287,6 +290,56 @@ int fds_alu_peak(int32_t kind, double *tflops);
 void fds_autotune_enable(int32_t on);
 void fds_autotune_reset(void);
 int fds_autotune_report(char *buf, int32_t cap);
+
+/*
+ * Fault injection for tests of the failure paths (an extension, not in the
+ * paper).  Every fault is made on the host or by withholding work, never by
+ * a bad access: the device context stays usable afterwards.  An armed fault
+ * fires once and then disarms itself.
+ *   FDS_FAULT_NONE         disarm every fault (arg ignored).
+ *   FDS_FAULT_ALLOC        the arg-th device allocation of the library from
+ *                          now on (arg >= 1) fails as if the device were out
+ *                          of memory: the call returns FDS_ERR_OOM after
+ *                          freeing what it had allocated.
+ *   FDS_FAULT_NAN_BLOCK    the next build writes a NaN into the first entry
+ *                          of the first leaf's diagonal block after the
+ *                          kernel evaluation: the block LU meets a
+ *                          non-finite pivot and the build returns
+ *                          FDS_ERR_SINGULAR.
+ *   FDS_FAULT_TC_STALL_FW  in the next launch of the tensor-core leaf-block
+ *                          product (fw_engine = FDS_FW_TENSOR,
+ *                          fds_zgemm_blocks_tc), the first CTA's producer
+ *                          issues no copies: its MMA thread's bounded wait
+ *                          (about 2 s) runs out, the kernel records a status,
+ *                          frees its tensor memory and returns; the call
+ *                          returns FDS_ERR_TIMEOUT.
+ *   FDS_FAULT_TC_STALL_C64 the same for the complex64 tensor-core GEMM
+ *                          (FDS_C64_TENSOR, fds_cgemm_c64_batched): the first
+ *                          CTA issues no MMAs, so its completion waits run out.
+ * Returns FDS_OK, FDS_ERR_ARG (unknown kind, arg < 1 for FDS_FAULT_ALLOC) or
+ * FDS_ERR_CUDA (the device flag of a stall could not be set).  Process-wide;
+ * not meant to be armed while another thread builds or solves.  The
+ * environment variable FDS_FAULT ("alloc:N", "nan", "stall_fw" or
+ * "stall_c64") arms the same fault once per process, at the first build.
+ */
+/*
+ * Bounds-checked build: a library compiled with -DFDS_CHECKS
+ * (paper_2411_18026_gb300/libfds_checked.so, build(checked=True)) checks
+ * every index-mapped gather and scatter (row maps of the batched GEMMs, the
+ * skeleton and child-to-parent placements, the leaf-order permutation)
+ * against the extent of the buffer it addresses, skips an access out of
+ * range and counts it.  fds_bounds_violations synchronises the device and
+ * writes the count since the previous call (then resets it) to *count;
+ * FDS_ERR_STATE in a library built without the checks.
+ */
+int fds_bounds_violations(int64_t *count);
+
+#define FDS_FAULT_NONE 0
+#define FDS_FAULT_ALLOC 1
+#define FDS_FAULT_NAN_BLOCK 2
+#define FDS_FAULT_TC_STALL_FW 3
+#define FDS_FAULT_TC_STALL_C64 4
+int fds_fault_inject(int32_t kind, int64_t arg);
 
 /* ------------------------------------------------------------------------
  * Stage entry points: each runs one step of the hot path on caller-provided

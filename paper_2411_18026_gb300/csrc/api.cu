@@ -3,9 +3,14 @@
 #include <algorithm>
 #include <cmath>
 #include <vector>
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
 #include <new>
 
 #include "fds_internal.cuh"
+#include "fw_tc.cuh"
 
 thread_local cudaStream_t g_alloc_stream = 0;
 thread_local int g_c64_tensor = 1;
@@ -20,6 +25,7 @@ extern "C" void fds_default_options(fds_options *o) {
     o->variant = FDS_VARIANT_LU;
     o->use_graph = 0;
     o->fw_engine = FDS_FW_FF;
+    o->merge_c64_levels = 0;
     o->precision = FDS_FP64;
     o->alpha_re = 0.0;
     o->alpha_im = 0.0;
@@ -54,8 +60,11 @@ extern "C" const char *fds_error_string(int code) {
 
 // Build one handle; owned != 0: the handle takes ownership of that stream and
 // runs on it (batched builds), otherwise it runs on opt->cuda_stream.
+void fault_from_env();
+
 int fds_build_owned(const fds_geometry *g, double omega, double lambda, double mu, double tol,
                     const fds_options *opt, cudaStream_t owned, fds_handle **out) {
+    fault_from_env();
     // the stream is owned from here on: destroyed on every early return
     struct StreamGuard {
         cudaStream_t s;
@@ -79,7 +88,7 @@ int fds_build_owned(const fds_geometry *g, double omega, double lambda, double m
         !(o.tol_decay > 0.0 && o.tol_decay <= 1.0) ||
         (o.variant != FDS_VARIANT_LU && o.variant != FDS_VARIANT_MR2005) ||
         (o.variant == FDS_VARIANT_MR2005 && o.precision != FDS_FP64) ||
-        (o.fw_engine != FDS_FW_FF && o.fw_engine != FDS_FW_TENSOR))
+        (o.fw_engine != FDS_FW_FF && o.fw_engine != FDS_FW_TENSOR) || o.merge_c64_levels < 0)
         return FDS_ERR_ARG;
     for (int i = 0; i < 2 * g->n_nodes; ++i)
         if (!std::isfinite(g->xy[i])) return FDS_ERR_ARG;
@@ -303,4 +312,98 @@ extern "C" void fds_destroy(fds_handle *h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     delete h;
+}
+
+// ------------------------------------------------------------------ fault injection
+namespace {
+std::atomic<int64_t> g_fault_alloc{0};   // allocations left before the injected failure (0: disarmed)
+std::atomic<int> g_fault_nan{0};
+std::atomic<int> g_fault_tc_armed{0};    // bit 0: leaf-block product, bit 1: complex64 GEMM
+}  // namespace
+
+bool fds_fault_alloc_fires() {
+    int64_t v = g_fault_alloc.load(std::memory_order_relaxed);
+    while (v > 0)
+        if (g_fault_alloc.compare_exchange_weak(v, v - 1)) return v == 1;
+    return false;
+}
+
+bool fds_fault_nan_fires() { return g_fault_nan.exchange(0) != 0; }
+
+extern "C" int fds_fault_inject(int32_t kind, int64_t arg) {
+    switch (kind) {
+        case FDS_FAULT_NONE: {
+            g_fault_alloc.store(0);
+            g_fault_nan.store(0);
+            // the device flags are touched only if a stall was armed
+            const int armed = g_fault_tc_armed.exchange(0);
+            if (armed & 1) FDS_TRY(oz_fault_arm(0));
+            if (armed & 2) FDS_TRY(tc_fault_arm(0));
+            return FDS_OK;
+        }
+        case FDS_FAULT_ALLOC:
+            if (arg < 1) return FDS_ERR_ARG;
+            g_fault_alloc.store(arg);
+            return FDS_OK;
+        case FDS_FAULT_NAN_BLOCK:
+            g_fault_nan.store(1);
+            return FDS_OK;
+        case FDS_FAULT_TC_STALL_FW:
+            FDS_TRY(oz_fault_arm(1));
+            g_fault_tc_armed.fetch_or(1);
+            return FDS_OK;
+        case FDS_FAULT_TC_STALL_C64:
+            FDS_TRY(tc_fault_arm(1));
+            g_fault_tc_armed.fetch_or(2);
+            return FDS_OK;
+        default:
+            return FDS_ERR_ARG;
+    }
+}
+
+// FDS_FAULT in the environment (alloc:N, nan, stall_fw, stall_c64) arms that
+// fault once per process, at the first build
+void fault_from_env() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char *v = std::getenv("FDS_FAULT");
+        if (!v) return;
+        if (!std::strncmp(v, "alloc:", 6)) {
+            const long long n = std::atoll(v + 6);
+            if (n >= 1) fds_fault_inject(FDS_FAULT_ALLOC, n);
+        } else if (!std::strcmp(v, "nan")) {
+            fds_fault_inject(FDS_FAULT_NAN_BLOCK, 0);
+        } else if (!std::strcmp(v, "stall_fw")) {
+            fds_fault_inject(FDS_FAULT_TC_STALL_FW, 0);
+        } else if (!std::strcmp(v, "stall_c64")) {
+            fds_fault_inject(FDS_FAULT_TC_STALL_C64, 0);
+        }
+    });
+}
+
+// ------------------------------------------------------------------ bounds-checked build
+namespace {
+std::vector<unsigned long long (*)()> &bounds_units() {
+    static std::vector<unsigned long long (*)()> v;
+    return v;
+}
+}  // namespace
+
+int fds_bounds_register(unsigned long long (*take)()) {
+    bounds_units().push_back(take);
+    return 1;
+}
+
+extern "C" int fds_bounds_violations(int64_t *count) {
+#ifdef FDS_CHECKS
+    if (!count) return FDS_ERR_ARG;
+    FDS_CUDA_TRY(cudaDeviceSynchronize());
+    unsigned long long t = 0;
+    for (auto f : bounds_units()) t += f();
+    *count = (int64_t)t;
+    return FDS_OK;
+#else
+    (void)count;
+    return FDS_ERR_STATE;
+#endif
 }

@@ -682,6 +682,12 @@ int fds_build_impl(fds_handle *h) {
             ps.units = pc.read();
         }
         FDS_CUDA_TRY(cudaGetLastError());
+        if (fds_fault_nan_fires()) {
+            // injected fault: a NaN in the first leaf's diagonal block
+            const cplx bad = mkc(std::nan(""), 0.0);
+            FDS_CUDA_TRY(cudaMemcpyAsync(Lf.LU.p, &bad, sizeof(cplx), cudaMemcpyHostToDevice, s));
+            FDS_CUDA_TRY(cudaStreamSynchronize(s));
+        }
         if (h->opt.precision == FDS_MIXED) FDS_TRY(fds_keep_blocks(Lf, Lf.Dfw, Lf.rDfw, s));
         FDS_TRY(sync_check(s));
     }
@@ -955,7 +961,10 @@ int fds_build_impl(fds_handle *h) {
             else C.c64 = (l == L) || 8 * C.D > h->lv[L].D;
             if (!C.c64) h->fp64_reached = true;
         }
-        const bool merge64 = C.c64 && h->opt.merge_c64;   // merged in complex64 (else FP64, converted later)
+        // merged in complex64 (else FP64, converted later): every complex64
+        // level, or the lowest merge_c64_levels of them
+        const bool merge64 = C.c64 && h->opt.merge_c64 &&
+                             (h->opt.merge_c64_levels <= 0 || l > L - h->opt.merge_c64_levels);
         FDS_TRY(C.V.alloc(C.offV[nb]));
         FDS_TRY(C.At.alloc(C.offAt[nb]));
         FDS_TRY(C.piv.alloc(C.offpiv[nb]));

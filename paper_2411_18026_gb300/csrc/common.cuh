@@ -126,6 +126,36 @@ extern "C" const char *fds_last_error_detail(void);
 // Counts kernel launches of this library (fds_launch_count).
 void fds_count_launch();
 
+// Bounds checks of the index-mapped gathers and scatters.  In a library built
+// with -DFDS_CHECKS, FDS_IN_RANGE(i, n) is false for i outside [0, n), counts
+// the miss in a device word of this translation unit, and the caller skips
+// the access; fds_bounds_violations() reads and clears every unit's word.
+// Without the flag it is the constant true.
+int fds_bounds_register(unsigned long long (*take)());
+#ifdef FDS_CHECKS
+static __device__ unsigned long long g_bounds_miss;
+__device__ __forceinline__ bool fds_in_range(long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    atomicAdd(&g_bounds_miss, 1ull);
+    return false;
+}
+#define FDS_IN_RANGE(i, n) fds_in_range((long long)(i), (long long)(n))
+namespace {
+unsigned long long bounds_take_unit() {
+    unsigned long long v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_bounds_miss, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (v) cudaMemcpyToSymbol(g_bounds_miss, &z, sizeof(z));
+    return v;
+}
+const int g_bounds_registered = fds_bounds_register(&bounds_take_unit);
+}  // namespace
+#else
+#define FDS_IN_RANGE(i, n) true
+#endif
+
 static inline unsigned ceil_div_u(long a, long b) { return (unsigned)((a + b - 1) / b); }
 
 // Raise a kernel's dynamic shared-memory limit to at least `bytes`, never

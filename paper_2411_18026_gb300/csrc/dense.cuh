@@ -18,8 +18,9 @@ typedef MatRefT<float4> MatRefP;
 
 // Row maps of one batch entry of a mapped GEMM (device pointers, nullable).
 struct RowMaps {
-    const int *b;   // B row k is read from row b[k]
-    const int *c;   // C row i is written to row c[i]
+    const int *b;   // B row k is read from row b[k] (0 <= b[k] < B.rows)
+    const int *c;   // C row i is written to row c[i] (0 <= c[i] < cext)
+    int cext;       // rows of the buffer C's map addresses
 };
 
 // Launch helpers (device pointers to descriptor arrays; all enqueue on stream).
@@ -64,6 +65,8 @@ int dense_gemm_tc(int batch, int max_m, int max_n, const MatRefF *d_A, int opA, 
 int dense_lu_blocked(int n, cplx *A, int ld, int *d_piv, int *d_info, cudaStream_t s);
 // Reads and clears the tensor-core timeout status (synchronises s).
 int tc_status_take(cudaStream_t s, int *status);
+// Arms (1) or clears (0) the injected stall of the next complex64 tensor-core GEMM launch.
+int tc_fault_arm(int on);
 // complex64 versions (mixed-precision merge and sweep)
 int dense_lu(int batch, int max_n, const MatRefF *d_A, int *d_piv, const int64_t *d_poff, int *d_info,
              cudaStream_t s);

@@ -27,6 +27,11 @@ struct AllocStreamScope {
     ~AllocStreamScope() { g_alloc_stream = prev; }
 };
 
+// Injected faults (fds_fault_inject): true once, for the allocation or build
+// that the armed fault names.
+bool fds_fault_alloc_fires();
+bool fds_fault_nan_fires();
+
 // Device buffer owned by the handle (freed in the destructor).
 template <class T>
 struct DBuf {
@@ -58,6 +63,7 @@ struct DBuf {
         release();
         if (count == 0) count = 1;
         st = g_alloc_stream;
+        if (fds_fault_alloc_fires()) return FDS_ERR_OOM;
         cudaError_t e = st ? cudaMallocAsync((void **)&p, count * sizeof(T), st)
                            : cudaMalloc((void **)&p, count * sizeof(T));
         if (e != cudaSuccess) {

@@ -252,6 +252,7 @@ __global__ void k_field_gather(const int *__restrict__ gidx, int64_t D, const cp
     const int64_t tot = D * cols;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = e % D, c = e / D;
+        if (!FDS_IN_RANGE(gidx[q], D)) continue;
         dst[q + c * ldd] = u[gidx[q] + c * ldu];
     }
 }
@@ -269,7 +270,9 @@ __global__ void k_field_to_parent(int nb, const int64_t *__restrict__ roff, cons
     for (int64_t e = threadIdx.x; e < (int64_t)r * cols; e += blockDim.x) {
         const int q = (int)(e % r);
         const int64_t c = e / r;
-        parent[pb + (q < k1[b] ? pos1[b] + q : pos2[b] + (q - k1[b])) + c * ldp] = child[o + q + c * ldc];
+        const int64_t pr = q < k1[b] ? pos1[b] + q : pos2[b] + (q - k1[b]);
+        if (!FDS_IN_RANGE(pr, pdoff[(b >> 1) + 1] - pb)) continue;
+        parent[pb + pr + c * ldp] = child[o + q + c * ldc];
     }
 }
 

@@ -297,6 +297,7 @@ __global__ void k_oz_slice_x(int nb, const int64_t *__restrict__ doff, const flo
 }  // namespace
 
 __device__ int g_oz_status;   // 1 once a leaf-block tensor-core product gave up waiting
+__device__ int g_oz_fault;    // injected fault: the next launch's first CTA issues no copies
 
 namespace {
 
@@ -349,9 +350,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         // producer: per K chunk kc the six x slice tiles (x buffer kc % 2),
         // then the A slice tiles A_0 .. A_5 of kc through the A ring; a buffer
         // or slot is refilled once the MMAs that read it have completed (their
-        // commit on its empty barrier)
+        // commit on its empty barrier).  With the injected stall the first
+        // CTA issues nothing and its MMA thread's wait runs out.
+        const bool stall = blockIdx.x == 0 && atomicExch(&g_oz_fault, 0) != 0;
         int ua = 0;
-        for (int kc = 0; kc < nkc; ++kc) {
+        for (int kc = 0; kc < nkc && !stall; ++kc) {
             if (*(volatile int *)sflag) break;
             const int qx = kc % OZ_NX;
             if (kc >= OZ_NX && !mbar_wait(smem_u32(emptyX + qx), (uint32_t)(((kc / OZ_NX) - 1) & 1))) {
@@ -433,7 +436,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const bool done_ok = mbar_wait(smem_u32(donebar), 0u);
     const int bad = __syncthreads_or(!done_ok || *(volatile int *)sflag);
     if (bad) {
-        if (tid == 0) atomicExch(&g_oz_status, 1);
+        if (tid == 0) {
+            atomicExch(&g_oz_status, 1);
+            // the MMAs issued before the give-up (committed to done) complete
+            // before the tensor memory is freed (bounded again)
+            mbar_wait(smem_u32(donebar), 0u);
+        }
     } else {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int lane = tid & 31;
@@ -614,5 +622,11 @@ int oz_status_take(cudaStream_t s, int *status) {
     FDS_CUDA_TRY(cudaStreamSynchronize(s));
     if (v) FDS_CUDA_TRY(cudaMemcpyToSymbolAsync(g_oz_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
     *status = v;
+    return FDS_OK;
+}
+
+int oz_fault_arm(int on) {
+    const int v = on ? 1 : 0;
+    FDS_CUDA_TRY(cudaMemcpyToSymbol(g_oz_fault, &v, sizeof(int)));
     return FDS_OK;
 }

@@ -12,3 +12,5 @@ int oz_leaf_prepare(Level &C, const MatRef *d_blocks, cudaStream_t s);
 int oz_leaf_apply(fds_handle *h, Level &C, const float4 *x, float4 *y, int64_t ld, int nc, cudaStream_t s);
 // Reads and clears the timeout status of the leaf-block products (synchronises s).
 int oz_status_take(cudaStream_t s, int *status);
+// Arms (1) or clears (0) the injected stall of the next leaf-block product launch.
+int oz_fault_arm(int on);

@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(NT) k_gemm_rt(const MatRefT<typename Ar::G> *_
         for (int q = 0; q < TJ; ++q) {
             const int k = t & 15, j = (t >> 4) + 16 * q;
             const int gk = k0 + k, gj = j0 + j;
-            sb[k][j] = (gk < K && gj < N) ? Ar::stage_b(B.p[(bmap ? bmap[gk] : gk) + (int64_t)gj * B.ld]) : Ar::zb();
+            const int rk = (gk < K && gj < N) ? (bmap ? bmap[gk] : gk) : -1;
+            sb[k][j] = (rk >= 0 && FDS_IN_RANGE(rk, B.rows)) ? Ar::stage_b(B.p[rk + (int64_t)gj * B.ld]) : Ar::zb();
         }
         __syncthreads();
         const int kmax = min(BK, K - k0);
@@ -233,7 +234,9 @@ __global__ void __launch_bounds__(NT) k_gemm_rt(const MatRefT<typename Ar::G> *_
         for (int j = 0; j < TJ; ++j) {
             const int gi = i0 + tx + 16 * i, gj = j0 + ty + 16 * j;
             if (gi < M && gj < N) {
-                G *c = &Cm.p[(cmap ? cmap[gi] : gi) + (int64_t)gj * Cm.ld];
+                const int ri = cmap ? cmap[gi] : gi;
+                if (!FDS_IN_RANGE(ri, cmap ? maps[blockIdx.y].cext : M)) continue;
+                G *c = &Cm.p[ri + (int64_t)gj * Cm.ld];
                 *c = Ar::finish(acc[i][j], alpha, beta, use_beta ? c : nullptr);
             }
         }

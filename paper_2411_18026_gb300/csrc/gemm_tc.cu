@@ -174,7 +174,10 @@ __device__ __forceinline__ void load_stage(Stage &S, const MatRefF &A, const Mat
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             float2 v = make_float2(0.f, 0.f);
-            if (col < N && ck + t < Kc) v = bc[bmap ? bmap[ck + t] : ck + t];
+            if (col < N && ck + t < Kc) {
+                const int rk = bmap ? bmap[ck + t] : ck + t;
+                if (FDS_IN_RANGE(rk, B.rows)) v = bc[rk];
+            }
             S.b[u][t] = v;
         }
     }
@@ -233,6 +236,7 @@ __device__ __forceinline__ void store_stage(const Stage &S, unsigned char *buf, 
 }  // namespace
 
 __device__ int g_tc_status;   // 1 once a tensor-core GEMM gave up waiting on its MMAs
+__device__ int g_tc_fault;    // injected fault: the next launch's first CTA issues no MMAs
 
 namespace {
 
@@ -277,6 +281,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int ci0 = i0 >> 1;
     bool bad = false;
     int committed = -1;   // last stage whose MMAs were committed
+    // injected stall: the first CTA issues no MMAs, so its completion waits run out
+    const bool stall = tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && atomicExch(&g_tc_fault, 0) != 0;
     Stage S;
     if (nch > 0) load_stage(S, A, B, bmap, opA, Mc, N, Kc, ci0, j0, 0, tid);
     for (int kc = 0; kc < nch; ++kc) {
@@ -292,7 +298,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (kc + 1 < nch) load_stage(S, A, B, bmap, opA, Mc, N, Kc, ci0, j0, (kc + 1) * TC_KC, tid);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !stall) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t idesc = idesc_bf16();
             const uint32_t sa = sbase + buf * Lay::STAGE;
@@ -310,8 +316,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(bars + buf))
                          : "memory");
+            committed = kc;
         }
-        committed = kc;
     }
     if (!bad && nch > 0) {
         const int kl = nch - 1;
@@ -330,11 +336,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int q = warp & 3, half = warp >> 2;
         const int rr = i0 + q * 32 + (tid & 31);
         const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
-        const bool row_ok = rr < 2 * Mc;
+        bool row_ok = rr < 2 * Mc;
         float *cp = nullptr;
         if (row_ok) {
             const int ci = rr >> 1;
-            cp = reinterpret_cast<float *>(Cm.p) + 2 * (int64_t)(cmap ? cmap[ci] : ci) + (rr & 1);
+            const int ri = cmap ? cmap[ci] : ci;
+            row_ok = FDS_IN_RANGE(ri, cmap ? maps[blockIdx.y].cext : Mc);
+            if (row_ok) cp = reinterpret_cast<float *>(Cm.p) + 2 * (int64_t)ri + (rr & 1);
         }
         for (int cb = half * (TC_BN / 2); cb < (half + 1) * (TC_BN / 2); cb += 16) {
             if (j0 + cb >= N) break;
@@ -388,6 +396,12 @@ int tc_status_take(cudaStream_t s, int *status) {
     FDS_CUDA_TRY(cudaStreamSynchronize(s));
     if (v) FDS_CUDA_TRY(cudaMemcpyToSymbolAsync(g_tc_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
     *status = v;
+    return FDS_OK;
+}
+
+int tc_fault_arm(int on) {
+    const int v = on ? 1 : 0;
+    FDS_CUDA_TRY(cudaMemcpyToSymbol(g_tc_fault, &v, sizeof(int)));
     return FDS_OK;
 }
 

@@ -60,6 +60,7 @@ __global__ void k_child_parent_t(int nb, const int64_t *__restrict__ roff, const
         const int q = (int)(e % r);
         const int64_t c = e / r;
         const int64_t pr = pb + (q < kk ? p1 + q : p2 + (q - kk));
+        if (!FDS_IN_RANGE(pr - pb, pdoff[(b >> 1) + 1] - pb)) continue;
         if (dir == 0) parent[pr + c * ldp] = child[o + q + c * ldc];
         else child[o + q + c * ldc] = parent[pr + c * ldp];
     }
@@ -93,6 +94,7 @@ __global__ void k_residual(const int *__restrict__ gidx, int64_t D, const cplx *
     const int c = blockIdx.y;
     double rr = 0.0, ff = 0.0;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < D; q += (int64_t)gridDim.x * blockDim.x) {
+        if (!FDS_IN_RANGE(gidx[q], D)) continue;
         const cplx f = F[gidx[q] + c * ldf];
         cplx r = f;
         if (Y) r = csub(f, to_c128(Y[q + c * D]));
@@ -143,6 +145,7 @@ __global__ void k_leaf_scatter(const int *__restrict__ gidx, int64_t D, const cp
     const int64_t tot = D * cols;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = e % D, c = e / D;
+        if (!FDS_IN_RANGE(gidx[q], D)) continue;
         out[gidx[q] + c * ldo] = X[q + c * D];
     }
 }
@@ -206,6 +209,7 @@ __global__ void k_srefs(int nb, const T *Sc, const int64_t *__restrict__ scoff, 
     Cm[e].ld = (int)ldy;
     M[e].b = side ? pm : pm + a;
     M[e].c = side ? pm + a : pm;
+    M[e].cext = (int)(doff[p + 1] - doff[p]);
 }
 
 double level_d2(const Level &C) {

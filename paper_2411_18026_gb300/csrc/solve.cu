@@ -35,6 +35,7 @@ __global__ void k_leaf_gather(const int *__restrict__ gidx, int64_t D, const cpl
     const int64_t tot = D * cols;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = e % D, c = e / D;
+        if (!FDS_IN_RANGE(gidx[q], D)) continue;
         const int64_t g = gidx[q] + c * lds;
         if (dir == 0) dst[q + c * D] = src[g];
         else ((cplx *)src)[g] = dst[q + c * D];
@@ -58,6 +59,7 @@ __global__ void k_child_parent(int nb, const int64_t *__restrict__ roff, const i
         const int q = (int)(e % r);
         const int64_t c = e / r;
         const int64_t pr = pb + (q < kk ? p1 + q : p2 + (q - kk));
+        if (!FDS_IN_RANGE(pr - pb, pdoff[(b >> 1) + 1] - pb)) continue;
         if (dir == 0) parent[pr + c * ldp] = child[o + q + c * ldc];
         else child[o + q + c * ldc] = parent[pr + c * ldp];
     }

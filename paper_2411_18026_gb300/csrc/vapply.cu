@@ -38,6 +38,7 @@ __global__ void k_vrefs(int nb, int dir, const T *Tb, const int64_t *__restrict_
         Cm[e].ld = (int)ldd;
         M[e].b = vm + k;
         M[e].c = nullptr;
+        M[e].cext = 0;
     } else {              // y[rest] = T^H t
         B[e].p = (T *)src + ooff;
         B[e].rows = k;
@@ -47,6 +48,7 @@ __global__ void k_vrefs(int nb, int dir, const T *Tb, const int64_t *__restrict_
         Cm[e].ld = (int)ldd;
         M[e].b = nullptr;
         M[e].c = vm + k;
+        M[e].cext = (int)(doff[b + 1] - doff[b]);
     }
     B[e].cols = nc;
     Cm[e].cols = nc;
@@ -65,7 +67,9 @@ __global__ void k_vskel(int dir, const int *__restrict__ k1, const int *__restri
         const int64_t col = e / kt;
         const int c = q < ka ? 0 : 1;
         const int qq = c ? q - ka : q;
-        const int64_t cell = doff[b] + vmap[doff[b] + (c ? n1[b] : 0) + qq];
+        const int li = vmap[doff[b] + (c ? n1[b] : 0) + qq];
+        if (!FDS_IN_RANGE(li, doff[b + 1] - doff[b])) continue;
+        const int64_t cell = doff[b] + li;
         const int64_t skel = roff[b] + q;
         if (dir == 0) dst[skel + col * ldd] = src[cell + col * lds];
         else dst[cell + col * ldd] = src[skel + col * lds];

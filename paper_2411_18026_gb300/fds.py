@@ -12,7 +12,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libfds.so")
+# FDS_LIB selects another build of the library (e.g. the bounds-checked libfds_checked.so)
+LIB_PATH = os.environ.get("FDS_LIB") or os.path.join(HERE, "libfds.so")
 
 FDS_OK = 0
 FDS_ERR_ARG = -1
@@ -34,6 +35,11 @@ FDS_VARIANT_LU = 0
 FDS_VARIANT_MR2005 = 1
 FDS_RANK_ADAPTIVE = 0
 FDS_RANK_LEARNED = 1
+FDS_FAULT_NONE = 0
+FDS_FAULT_ALLOC = 1
+FDS_FAULT_NAN_BLOCK = 2
+FDS_FAULT_TC_STALL_FW = 3
+FDS_FAULT_TC_STALL_C64 = 4
 FDS_MLP_NIN = 16
 FDS_MLP_NTRAIN = 5313
 FDS_MLP_NPARAM = 5345
@@ -70,7 +76,8 @@ class fds_options(ctypes.Structure):
                 ("sweep_ff", ctypes.c_int32), ("merge_c64", ctypes.c_int32), ("rank_mode", ctypes.c_int32),
                 ("mlp_params", ctypes.POINTER(ctypes.c_float)), ("sketch_extra", ctypes.c_int32),
                 ("record_features", ctypes.c_int32), ("c64_engine", ctypes.c_int32), ("tol_decay", ctypes.c_double),
-                ("variant", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("fw_engine", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("fw_engine", ctypes.c_int32),
+                ("merge_c64_levels", ctypes.c_int32)]
 
 
 class fds_stats(ctypes.Structure):
@@ -124,6 +131,8 @@ def lib():
                                         i64p, i64p, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, i32, u64]
     L.fds_alu_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
     L.fds_zgemm_blocks_tc.argtypes = [i32, ctypes.POINTER(i32), vp, vp, vp, i32, u64]
+    L.fds_fault_inject.argtypes = [i32, ctypes.c_int64]
+    L.fds_bounds_violations.argtypes = [ctypes.POINTER(ctypes.c_int64)]
     L.fds_autotune_enable.argtypes = [i32]
     L.fds_autotune_enable.restype = None
     L.fds_autotune_reset.argtypes = []
@@ -218,7 +227,7 @@ def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy
               alpha=None, stream=0, precision=FDS_FP64, ir_tol=None, ir_max_iter=None, ir_apply=None,
               mlp_params=None, sketch_extra=None, record_features=False, sweep_fp64_levels=None, merge_c64=False,
               sweep_ff=1, c64_engine=FDS_C64_SIMT, tol_decay=None, variant=FDS_VARIANT_LU, use_graph=False,
-              fw_engine=FDS_FW_FF):
+              fw_engine=FDS_FW_FF, merge_c64_levels=0):
     """Factorise; mlp_params (FDS_MLP_NPARAM floats) selects the learned-rank ID."""
     xy = np.ascontiguousarray(xy, dtype=np.float64)
     g = fds_geometry(len(xy), xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(rho))
@@ -254,6 +263,7 @@ def fds_build(xy, omega, lam, mu, tol, rho=1.0, leaf_size=64, top_level=1, proxy
     o.variant = int(variant)
     o.use_graph = 1 if use_graph else 0
     o.fw_engine = int(fw_engine)
+    o.merge_c64_levels = int(merge_c64_levels)
     out = ctypes.c_void_p()
     _check(lib().fds_build_ex(ctypes.byref(g), float(omega), float(lam), float(mu), float(tol), ctypes.byref(o),
                               ctypes.byref(out)), "fds_build")
@@ -449,6 +459,20 @@ def fds_zgemm_blocks_tc(d, d_A, d_X, d_Y, stream=None):
     nc = d_X.shape[0] if d_X.dim() == 2 else 1
     _check(lib().fds_zgemm_blocks_tc(len(d), d.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _ptr(d_A),
                                      _ptr(d_X), _ptr(d_Y), nc, _stream(stream)), "fds_zgemm_blocks_tc")
+
+
+def fds_fault_inject(kind, arg=0):
+    """Arms one injected fault (FDS_FAULT_*; fires once) or, with
+    FDS_FAULT_NONE, disarms all of them."""
+    _check(lib().fds_fault_inject(int(kind), int(arg)), "fds_fault_inject")
+
+
+def fds_bounds_violations():
+    """Out-of-range mapped accesses since the last call (bounds-checked
+    library only; FdsError with FDS_ERR_STATE otherwise)."""
+    n = ctypes.c_int64(0)
+    _check(lib().fds_bounds_violations(ctypes.byref(n)), "fds_bounds_violations")
+    return int(n.value)
 
 
 def fds_autotune_enable(on=True):

@@ -51,3 +51,19 @@ def test_argument_errors_without_gpu(fds):
     assert L.fds_lu_batched(0, None, None, None, None, None, None, 0) == fds.FDS_OK
     L.fds_destroy(None)
     assert fds.lib().fds_error_string(-4) == b"singular or non-finite pivot"
+
+
+def test_fault_injection_arming_without_gpu(fds):
+    # host-side faults arm and disarm without touching the device
+    L = fds.lib()
+    assert L.fds_fault_inject(fds.FDS_FAULT_ALLOC, 0) == fds.FDS_ERR_ARG
+    assert L.fds_fault_inject(99, 0) == fds.FDS_ERR_ARG
+    assert L.fds_fault_inject(fds.FDS_FAULT_ALLOC, 3) == fds.FDS_OK
+    assert L.fds_fault_inject(fds.FDS_FAULT_NAN_BLOCK, 0) == fds.FDS_OK
+    assert L.fds_fault_inject(fds.FDS_FAULT_NONE, 0) == fds.FDS_OK
+
+
+def test_default_library_has_no_bounds_checks(fds):
+    import ctypes as C
+    n = C.c_int64(-1)
+    assert fds.lib().fds_bounds_violations(C.byref(n)) == fds.FDS_ERR_STATE

@@ -1,0 +1,42 @@
+"""Run-to-run reproducibility: two builds of the same seeded cavity pick the
+same skeleton ranks at every level and give the same solution to rounding.
+(The tile evaluator sums the element-pair contributions of a hat entry with
+shared-memory atomics, so matrix entries, and everything after them, agree
+to rounding rather than bit for bit.)"""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_util import fdslib, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("mode", ["fp64", "learned_mixed"])
+def test_two_builds_same_skeletons_and_solution(mode):
+    torch_cuda()
+    fds = fdslib()
+    xy = workloads.star(8192, 0.2, 5, rot=0.1)
+    omega = workloads.omega_for_kTa(15.0)
+    kw = {}
+    if mode == "learned_mixed":
+        from paper_2411_18026_gb300 import learned
+        prm = learned.load_params()
+        assert prm is not None
+        kw = dict(precision=fds.FDS_MIXED, ir_tol=1e-10, mlp_params=prm, fw_engine=fds.FDS_FW_TENSOR)
+    kinds, ang = workloads.plane_wave_set(2)
+    runs = []
+    for _ in range(2):
+        h = fds.fds_build(xy, omega, 2.0, 1.0, 1e-9, **kw)
+        st = fds.fds_stats_get(h)
+        ranks = [fds.fds_level_ranks(h, l, 1 << l) for l in range(st.top_level + 1, st.levels + 1)]
+        F = fds.fds_rhs_plane_wave(h, kinds, ang)
+        x = fds.fds_solve(h, F)
+        h.close()
+        runs.append((ranks, x))
+    (r0, x0), (r1, x1) = runs
+    assert len(r0) == len(r1) > 0
+    diff = [int((a != b).sum()) for a, b in zip(r0, r1)]
+    rel = np.linalg.norm(x1 - x0) / np.linalg.norm(x0)
+    assert sum(diff) == 0, (diff, rel)
+    assert rel <= 1e-12, rel
