@@ -485,6 +485,28 @@ int fds_zgemm_blocks_tc(int32_t batch, const int32_t *d, const double *d_A, cons
                         int32_t nc, uint64_t stream);
 
 /*
+ * General block products of the forward operator on the tensor cores (stage
+ * entry; the sibling and interpolation blocks with fw_engine =
+ * FDS_FW_TENSOR use the same kernels): for each job e < njobs,
+ *   Y[y_row[e] + ymap_e[i], :] (+)= sum_l op(A_e)[i][l] X[x_row[e] + xmap_e[l], :]
+ * for i < m[e], l < k[e], where op(A_e) = A_e (op[e] = 0, stored m x k) or
+ * A_e^H (op[e] = 1, stored k x m), the stored block column-major at
+ * d_A + 2 a_off[e] doubles with leading dimension lda[e] (complex128).
+ * xmap_e = maps + xmap_off[e] (k[e] entries) and ymap_e = maps + ymap_off[e]
+ * (m[e] entries); an offset of -1 means rows taken in order (map = identity).
+ * set[e] != 0: Y = product, else Y += product.  Jobs must write disjoint rows
+ * of Y.  X (ldx) and Y (ldy) are complex128, column-major, nc columns, on the
+ * device; all other arrays are host arrays.  Same slicing, accuracy and
+ * float-pair vectors as fds_zgemm_blocks_tc; op(A_e) wider than 128 complex
+ * columns runs as several passes.  Allocates its temporaries; synchronises
+ * the stream; FDS_ERR_TIMEOUT if a tensor-core pipeline wait gave up.
+ */
+int fds_zgemm_jobs_tc(int32_t njobs, const int32_t *m, const int32_t *k, const int32_t *op, const int64_t *a_off,
+                      const int32_t *lda, const int64_t *x_row, const int64_t *xmap_off, const int64_t *y_row,
+                      const int64_t *ymap_off, const int32_t *set, const int32_t *maps, const double *d_A,
+                      const double *d_X, int64_t ldx, double *d_Y, int64_t ldy, int32_t nc, uint64_t stream);
+
+/*
  * Training data of the learned-rank network (extension): the 16 features of
  * each (cell, component) of levels L..l0+1 and the fraction k / n that the
  * adaptive ID kept there, recorded by a build with record_features = 1.

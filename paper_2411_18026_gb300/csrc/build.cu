@@ -1004,6 +1004,7 @@ int fds_build_impl(fds_handle *h) {
                 }
             FDS_TRY(C.d_vmap.upload(vmap, s));
             FDS_TRY(C.d_toff.upload(toff, s));
+            C.toff_h = toff;
             FDS_TRY(C.d_n1.upload(C.n1, s));
             FDS_TRY(C.d_n2.upload(C.n2, s));
             C.T = std::move(d_T);

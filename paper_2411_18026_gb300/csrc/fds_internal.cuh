@@ -85,6 +85,30 @@ struct DBuf {
 
 // One tree level: its cells, their active DOFs and (for compressed levels) the
 // stored factors of Sec. 7.3 step 3(b).
+// One launch of the tensor-core block products of the forward operator
+// (fw_tc.cu): jobs y[ymap] (+)= op(A_e) x[xmap], op(A_e) m x k complex with
+// k <= 128 (wider blocks are split into passes, one launch each).
+struct OzJob {
+    int64_t a_tile;      // first operator slice tile (16 KB each)
+    int64_t x_tile;      // first vector slice group (sum of nkc over earlier jobs)
+    int64_t x_row, y_row;   // row offsets into x and y
+    int32_t xmap, ymap;     // offsets into the plan's map array (-1: rows contiguous)
+    int32_t m, k;           // complex rows and columns of op(A_e)
+    int32_t nmt, nkc;       // 128-real row tiles, 64-real K chunks
+    int32_t rexp;           // first row exponent (nmt * 128 entries)
+    int32_t flags;          // 1: y = product (y is not read)
+};
+struct OzPlan {
+    int njobs = 0, ntiles = 0;   // ntiles: (job, row tile) pairs
+    int64_t xgroups = 0;         // sum of nkc over the jobs
+    double flops = 0;            // 8 m k per column, summed over the jobs
+    DBuf<OzJob> jobs;
+    DBuf<int2> tiles;            // (job, row tile)
+    DBuf<int> maps;
+    DBuf<unsigned char> aslices;
+    DBuf<int> rowexp;
+};
+
 struct Level {
     int nb = 0;                  // cells
     // --- DOFs: per cell, comp-1 DOF nodes then comp-2 DOF nodes
@@ -156,6 +180,11 @@ struct Level {
     //     blocks in pre-swizzled tensor-core tiles and their row exponents
     DBuf<unsigned char> oz_a;
     DBuf<int> oz_rowexp;
+    // fw_engine = FDS_FW_TENSOR: plans of the level's forward-operator
+    // products on the tensor cores (one entry per K pass): leaf blocks,
+    // interpolation up (T^c) and down (T^cH), sibling blocks
+    std::vector<OzPlan> oz_leaf, oz_up, oz_down, oz_sib;
+    std::vector<int64_t> toff_h;   // host copy of the T^c block offsets
     int srmax = 0;
     double sum_s2 = 0;            // sum over cells of 2 r_a r_b
 };

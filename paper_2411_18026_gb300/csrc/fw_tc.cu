@@ -505,6 +505,520 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
 namespace {
 
+// ------------------------------------------------------------------ general block products
+// The same split for any batch of jobs y[ymap] (+)= op(A_e) x[xmap]
+// (leaf blocks, the interpolation blocks T^c and T^cH, the sibling blocks),
+// op(A_e) m x k complex with k <= 128 per launch: a persistent kernel, one
+// CTA per SM, looping over work items (job, 128-real row tile, 32-column
+// tile).  Warp roles: warps 0-3 drain tensor memory (thread t owns row t of
+// the tile), warp 4 loads (one thread, cp.async.bulk into a ring of operator
+// slice tiles and a ring of vector slice buffers), warp 5 issues the MMAs
+// (one thread).  Tensor memory holds two sets of the eight accumulators (32
+// columns each), so the MMAs of one item run while the epilogue drains the
+// previous one.
+constexpr int OZJ_BN = 32;                     // columns per work item
+constexpr int OZJ_XTILE = OZJ_BN * 128;        // one 32 x 64 bf16 vector slice tile
+constexpr int OZJ_NA = 8;                      // operator slice ring (16 KB slots)
+constexpr int OZJ_NX = 3;                      // vector slice buffers (six tiles of one K chunk each)
+constexpr int OZJ_THREADS = 192;
+
+struct OzjLayout {
+    static constexpr int XBUF = OZ_SLICES * OZJ_XTILE;
+    static constexpr int XOFF = OZJ_NA * OZ_TILE;
+    static constexpr int RINGS = XOFF + OZJ_NX * XBUF;
+    // fullA, emptyA, fullX, emptyX, tfull[2], tempty[2], done
+    static constexpr int NBAR = 2 * OZJ_NA + 2 * OZJ_NX + 5;
+    static constexpr int TOTAL = RINGS + 1024 + 8 * NBAR + 64;
+};
+
+struct OzSrc {
+    const cplx *a;   // the stored block
+    int lda;
+    int op;          // 0: op(A) = A (m x k); 1: op(A) = A^H of the stored k x m block
+};
+
+// fp32 accumulator, bf16 A and B, both K-major, M 128, N n
+__device__ __forceinline__ uint32_t idesc_bf16_m128(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+// operator slices of every job: block j of the grid, its warps over the
+// job's nmt * 128 real rows (rows and K positions beyond the job are zero)
+__global__ void k_ozj_slice_a(const OzJob *__restrict__ jobs, const OzSrc *__restrict__ src,
+                              unsigned char *slices, int *rowexp) {
+    const OzJob J = jobs[blockIdx.x];
+    const OzSrc S = src[blockIdx.x];
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int K = J.nkc * 64;
+    for (int r = threadIdx.x >> 5; r < J.nmt * 128; r += nw) {
+        const int i = r >> 1;
+        const bool im_row = r & 1, valid = i < J.m;
+        double mx = 0.0;
+        if (valid)
+            for (int l = lane; l < J.k; l += 32) {
+                const cplx a = S.op ? S.a[l + (int64_t)i * S.lda] : S.a[i + (int64_t)l * S.lda];
+                mx = fmax(mx, fmax(fabs(a.x), fabs(a.y)));
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        int e = 0;
+        if (mx > 0.0) frexp(mx, &e);
+        if (lane == 0) rowexp[J.rexp + r] = e;
+        const double inv = ldexp(1.0, -e);
+        const int mt = r >> 7, rr = r & 127;
+        for (int kk = lane; kk < K; kk += 32) {
+            const int l = kk >> 1;
+            double v = 0.0;
+            if (valid && l < J.k) {
+                cplx a = S.op ? S.a[l + (int64_t)i * S.lda] : S.a[i + (int64_t)l * S.lda];
+                if (S.op) a.y = -a.y;
+                v = !im_row ? ((kk & 1) ? -a.y : a.x) : ((kk & 1) ? a.x : a.y);
+            }
+            unsigned short s[OZ_SLICES];
+            cut6(v * inv, s);
+            unsigned char *t = slices + (size_t)(J.a_tile + (int64_t)(mt * J.nkc + (kk >> 6)) * OZ_SLICES) * OZ_TILE;
+            const uint32_t off = sw_elem(rr, kk & 63);
+#pragma unroll
+            for (int q = 0; q < OZ_SLICES; ++q)
+                *reinterpret_cast<unsigned short *>(t + (size_t)q * OZ_TILE + off) = s[q];
+        }
+    }
+}
+
+// vector slices of every job for this application: block (j, 8-column
+// group), one warp per column; the job's rows of x are gathered through its
+// map; colexp[j * cols + c] receives the column's exponent
+__global__ void k_ozj_slice_x(const OzJob *__restrict__ jobs, const int *__restrict__ maps,
+                              const float4 *__restrict__ x, int64_t ldx, int nc, int ntile,
+                              unsigned char *slices, int *colexp) {
+    const int jb = blockIdx.x;
+    const OzJob J = jobs[jb];
+    const int lane = threadIdx.x & 31;
+    const int cols = ntile * OZJ_BN;
+    const int c = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= cols) return;
+    const bool live = c < nc;
+    float m = 0.f;
+    if (live)
+        for (int l = lane; l < J.k; l += 32) {
+            const int64_t row = J.x_row + (J.xmap >= 0 ? maps[J.xmap + l] : l);
+            const float4 v = x[row + (int64_t)c * ldx];
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, s));
+    int e = 0;
+    if (m > 0.f) {
+        frexpf(m, &e);
+        if (m >= ldexpf(1.0f - 1.0f / (1 << 20), e)) ++e;
+    }
+    if (lane == 0) colexp[(int64_t)jb * cols + c] = e;
+    const int nt = c / OZJ_BN, n = c % OZJ_BN;
+    const int K = J.nkc * 64;
+    for (int kk = lane; kk < K; kk += 32) {
+        const int l = kk >> 1;
+        float h = 0.f, lo = 0.f;
+        if (live && l < J.k) {
+            const float4 q = x[J.x_row + (J.xmap >= 0 ? maps[J.xmap + l] : l) + (int64_t)c * ldx];
+            h = (kk & 1) ? q.y : q.x;
+            lo = (kk & 1) ? q.w : q.z;
+        }
+        unsigned short s[OZ_SLICES];
+        cut6_pair(h, lo, e, s);
+        unsigned char *t =
+            slices + (size_t)((J.x_tile * ntile + (int64_t)nt * J.nkc + (kk >> 6)) * OZ_SLICES) * OZJ_XTILE;
+        const uint32_t off = sw_elem(n, kk & 63);
+#pragma unroll
+        for (int q = 0; q < OZ_SLICES; ++q)
+            *reinterpret_cast<unsigned short *>(t + (size_t)q * OZJ_XTILE + off) = s[q];
+    }
+}
+
+}  // namespace
+
+__device__ int g_ozj_status;   // 1 once a general block product gave up waiting
+__device__ int g_ozj_fault;    // injected fault: the next launch's first CTA issues no copies
+
+namespace {
+
+__global__ void __launch_bounds__(OZJ_THREADS, 1)
+    k_ozj(const OzJob *__restrict__ jobs, const int2 *__restrict__ tiles, int nitems, int ntile,
+          const int *__restrict__ maps, const unsigned char *__restrict__ aslices, const int *__restrict__ rowexp,
+          const unsigned char *__restrict__ xslices, const int *__restrict__ colexp, float4 *y, int64_t ldy,
+          int nc) {
+    extern __shared__ unsigned char ozj_raw[];
+    const uint32_t raw = smem_u32(ozj_raw);
+    const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
+    const uint32_t sbase = raw + pad;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ozj_raw + pad + OzjLayout::RINGS);
+    uint64_t *fullA = bars, *emptyA = bars + OZJ_NA, *fullX = bars + 2 * OZJ_NA, *emptyX = fullX + OZJ_NX;
+    uint64_t *tfull = emptyX + OZJ_NX, *tempty = tfull + 2, *donebar = tempty + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + OzjLayout::NBAR);
+    int *sflag = reinterpret_cast<int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int cols = ntile * OZJ_BN;
+    if (tid == 0) {
+        for (int q = 0; q < OzjLayout::NBAR; ++q) {
+            // tempty: one arrival per epilogue warp; the others: one arrival (+ bytes)
+            const int cnt = (q == 2 * OZJ_NA + 2 * OZJ_NX + 2 || q == 2 * OZJ_NA + 2 * OZJ_NX + 3) ? 4 : 1;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + q)), "r"(cnt));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *sflag = 0;
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // producer: per item and K chunk, the six vector slice tiles into
+            // a buffer, then the operator slice tiles A_0 .. A_5 through the ring
+            const bool stall = blockIdx.x == 0 && atomicExch(&g_ozj_fault, 0) != 0;
+            int ua = 0, ux = 0;
+            for (int it = blockIdx.x; it < nitems && !stall; it += gridDim.x) {
+                const int2 tl = tiles[it / ntile];
+                const int nt = it % ntile;
+                const OzJob J = jobs[tl.x];
+                const unsigned char *ab = aslices + (size_t)(J.a_tile + (int64_t)tl.y * J.nkc * OZ_SLICES) * OZ_TILE;
+                const unsigned char *xb =
+                    xslices + (size_t)((J.x_tile * ntile + (int64_t)nt * J.nkc) * OZ_SLICES) * OZJ_XTILE;
+                bool ok = true;
+                for (int kc = 0; kc < J.nkc && ok; ++kc) {
+                    if (*(volatile int *)sflag) { ok = false; break; }
+                    const int qx = ux % OZJ_NX;
+                    if (ux >= OZJ_NX && !mbar_wait(smem_u32(emptyX + qx), (uint32_t)(((ux / OZJ_NX) - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fx = smem_u32(fullX + qx);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fx),
+                                 "r"(OzjLayout::XBUF)
+                                 : "memory");
+                    for (int j = 0; j < OZ_SLICES; ++j)
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+                            "[%3];" ::"r"(sbase + OzjLayout::XOFF + qx * OzjLayout::XBUF + j * OZJ_XTILE),
+                            "l"(xb + (size_t)(kc * OZ_SLICES + j) * OZJ_XTILE), "r"(OZJ_XTILE), "r"(fx)
+                            : "memory");
+                    ++ux;
+                    for (int i = 0; i < OZ_SLICES; ++i) {
+                        const int qa = ua % OZJ_NA;
+                        if (ua >= OZJ_NA && !mbar_wait(smem_u32(emptyA + qa), (uint32_t)(((ua / OZJ_NA) - 1) & 1))) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t fa = smem_u32(fullA + qa);
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fa), "r"(OZ_TILE)
+                                     : "memory");
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+                            "[%3];" ::"r"(sbase + qa * OZ_TILE),
+                            "l"(ab + (size_t)(kc * OZ_SLICES + i) * OZ_TILE), "r"(OZ_TILE), "r"(fa)
+                            : "memory");
+                        ++ua;
+                    }
+                }
+                if (!ok) {
+                    atomicExch(sflag, 1);
+                    break;
+                }
+            }
+            // every copy issued has landed before the CTA may exit (bounded)
+            for (int q = 0; q < OZJ_NA && q < ua; ++q) {
+                const int last = q + ((ua - 1 - q) / OZJ_NA) * OZJ_NA;   // last use of slot q
+                mbar_wait(smem_u32(fullA + q), (uint32_t)((last / OZJ_NA) & 1));
+            }
+            for (int q = 0; q < OZJ_NX && q < ux; ++q) {
+                const int last = q + ((ux - 1 - q) / OZJ_NX) * OZJ_NX;
+                mbar_wait(smem_u32(fullX + q), (uint32_t)((last / OZJ_NX) & 1));
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // MMA issuer: item it accumulates into tensor-memory set it % 2
+            // once the epilogue has drained that set's previous item
+            const uint32_t idesc = idesc_bf16_m128(OZJ_BN);
+            int ua = 0, ux = 0, n = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++n) {
+                const OzJob J = jobs[tiles[it / ntile].x];
+                const int tb = n & 1;
+                if (n >= 2 && !mbar_wait(smem_u32(tempty + tb), (uint32_t)(((n >> 1) - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t tacc = tmem + (uint32_t)(tb * OZ_ACC * OZJ_BN);
+                int started = 0;
+                for (int kc = 0; kc < J.nkc && ok; ++kc) {
+                    const int qx = ux % OZJ_NX;
+                    if (!mbar_wait(smem_u32(fullX + qx), (uint32_t)((ux / OZJ_NX) & 1)) || *(volatile int *)sflag) {
+                        ok = false;
+                        break;
+                    }
+                    // k-steps of 16 reals holding data (one zero step for a job without columns)
+                    const int kin = min(64, 2 * J.k - kc * 64);
+                    const int nks = max(1, (kin + 15) / 16);
+                    for (int i = 0; i < OZ_SLICES; ++i) {
+                        const int qa = ua % OZJ_NA;
+                        if (!mbar_wait(smem_u32(fullA + qa), (uint32_t)((ua / OZJ_NA) & 1))) {
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t sa = sbase + qa * OZ_TILE;
+                        for (int j = 0; j < OZ_SLICES - i; ++j) {
+                            const int g = pair_acc(i, j);
+                            const uint32_t sb = sbase + OzjLayout::XOFF + qx * OzjLayout::XBUF + j * OZJ_XTILE;
+                            for (int ks = 0; ks < nks; ++ks) {
+                                mma_bf16(tacc + (uint32_t)(g * OZJ_BN), sw128_desc(sa + 32u * ks),
+                                         sw128_desc(sb + 32u * ks), idesc, ((started >> g) & 1) ? 1u : 0u);
+                                started |= 1 << g;
+                            }
+                        }
+                        asm volatile(
+                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                smem_u32(emptyA + qa))
+                            : "memory");
+                        ++ua;
+                    }
+                    if (!ok) break;
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(emptyX + qx))
+                                 : "memory");
+                    ++ux;
+                }
+                if (!ok) break;
+                if (started != (1 << OZ_ACC) - 1) {   // an accumulator never written
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(tfull + tb))
+                             : "memory");
+            }
+            if (!ok) atomicExch(sflag, 1);
+            // all MMAs issued have completed before the tensor memory is freed (bounded)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(donebar))
+                         : "memory");
+            mbar_wait(smem_u32(donebar), 0u);
+        }
+    } else {
+        // epilogue: thread t owns real row t of the item's row tile
+        int n = 0;
+        for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++n) {
+            const int tb = n & 1;
+            bool ok = mbar_wait(smem_u32(tfull + tb), (uint32_t)((n >> 1) & 1)) && !*(volatile int *)sflag;
+            ok = __all_sync(0xffffffffu, ok);   // the warp leaves together (its loads and shuffles are warp-wide)
+            if (!ok) {
+                if (lane == 0) atomicExch(sflag, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int2 tl = tiles[it / ntile];
+            const int nt = it % ntile;
+            const OzJob J = jobs[tl.x];
+            const int r = tl.y * 128 + warp * 32 + lane;   // real row of op(A_e)
+            const bool valid = r < 2 * J.m;
+            const int er = rowexp[J.rexp + r];
+            const int64_t yr = valid ? J.y_row + (J.ymap >= 0 ? maps[J.ymap + (r >> 1)] : (r >> 1)) : 0;
+            const bool set = J.flags & 1;
+            const uint32_t tq = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(tb * OZ_ACC * OZJ_BN);
+            const int *ce = colexp + (int64_t)tl.x * cols;
+            for (int cb = 0; cb < OZJ_BN; cb += 16) {
+                const int c0 = nt * OZJ_BN + cb;
+                uint32_t rw[OZ_ACC][16];
+#pragma unroll
+                for (int g = 0; g < OZ_ACC; ++g) tmem_ld16_nowait(tq + (uint32_t)(g * OZJ_BN + cb), rw[g]);
+                float4 ycur[16];
+                const bool wr = !(lane & 1) && valid;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    ycur[j] = (wr && !set && c0 + j < nc) ? y[yr + (int64_t)(c0 + j) * ldy]
+                                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (cb + 16 == OZJ_BN) {
+                    // the set is in registers: hand it back to the MMA issuer
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0)
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty + tb))
+                                     : "memory");
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int c = c0 + j;
+                    float h = __uint_as_float(rw[0][j]), lo = 0.f, e;
+#pragma unroll
+                    for (int g = 1; g < 6; ++g) {
+                        two_sum_f(h, __uint_as_float(rw[g][j]), h, e);
+                        lo += e;
+                    }
+                    lo += __uint_as_float(rw[6][j]) + __uint_as_float(rw[7][j]);
+                    const int sh = c < nc ? er + ce[c] - 16 : 0;
+                    const float s1 = pow2f(sh / 2), s2 = pow2f(sh - sh / 2);
+                    h = c < nc ? (h * s1) * s2 : 0.f;
+                    lo = c < nc ? (lo * s1) * s2 : 0.f;
+                    const float oh = __shfl_xor_sync(0xffffffffu, h, 1);   // the partner real row
+                    const float ol = __shfl_xor_sync(0xffffffffu, lo, 1);
+                    if (wr && c < nc) {
+                        float rh, rl, ih, il;
+                        ff_add(ycur[j].x, ycur[j].z, h, lo, rh, rl);
+                        ff_add(ycur[j].y, ycur[j].w, oh, ol, ih, il);
+                        y[yr + (int64_t)c * ldy] = make_float4(rh, ih, rl, il);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && *(volatile int *)sflag) atomicExch(&g_ozj_status, 1);
+    if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 1;
+    }
+    return n;
+}
+
+}  // namespace
+
+int oz_plan_build(const std::vector<OzSpec> &specs, std::vector<OzPlan> &passes, cudaStream_t s) {
+    passes.clear();
+    int maxk = 0;
+    for (const OzSpec &q : specs) {
+        if (q.m < 0 || q.k < 0 || (q.m > 0 && !q.a && q.k > 0)) return FDS_ERR_ARG;
+        maxk = std::max(maxk, q.k);
+    }
+    const int npass = std::max(1, (maxk + 127) / 128);
+    for (int p = 0; p < npass; ++p) {
+        std::vector<OzJob> jobs;
+        std::vector<int2> tiles;
+        std::vector<int> maps;
+        std::vector<OzSrc> src;
+        int64_t atile = 0, xg = 0, rexp = 0;
+        double fl = 0;
+        for (const OzSpec &q : specs) {
+            const int k0 = 128 * p;
+            if (q.m == 0 || (p > 0 && k0 >= q.k)) continue;
+            const int kp = std::max(0, std::min(128, q.k - k0));
+            if (kp == 0 && !q.set) continue;   // nothing to add
+            OzJob J;
+            J.m = q.m;
+            J.k = kp;
+            J.nmt = (2 * q.m + 127) / 128;
+            J.nkc = std::max(1, (2 * kp + 63) / 64);
+            J.a_tile = atile;
+            atile += (int64_t)J.nmt * J.nkc * OZ_SLICES;
+            J.x_tile = xg;
+            xg += J.nkc;
+            J.rexp = (int32_t)rexp;
+            rexp += (int64_t)J.nmt * 128;
+            J.x_row = q.x_row + (q.xmap ? 0 : k0);
+            J.xmap = -1;
+            if (q.xmap && kp > 0) {
+                J.xmap = (int32_t)maps.size();
+                maps.insert(maps.end(), q.xmap + k0, q.xmap + k0 + kp);
+            }
+            J.y_row = q.y_row;
+            J.ymap = -1;
+            if (q.ymap) {
+                J.ymap = (int32_t)maps.size();
+                maps.insert(maps.end(), q.ymap, q.ymap + q.m);
+            }
+            J.flags = (q.set && p == 0) ? 1 : 0;
+            OzSrc S;
+            S.a = q.a ? (q.op ? q.a + k0 : q.a + (int64_t)k0 * q.lda) : nullptr;
+            S.lda = q.lda;
+            S.op = q.op;
+            for (int mt = 0; mt < J.nmt; ++mt) tiles.push_back(make_int2((int)jobs.size(), mt));
+            jobs.push_back(J);
+            src.push_back(S);
+            fl += 8.0 * q.m * kp;
+        }
+        if (jobs.empty()) continue;
+        if (rexp > 2147483647LL || maps.size() > 2147483647ULL || jobs.size() > 2147483647ULL) return FDS_ERR_ARG;
+        OzPlan P;
+        P.njobs = (int)jobs.size();
+        P.ntiles = (int)tiles.size();
+        P.xgroups = xg;
+        P.flops = fl;
+        if (maps.empty()) maps.push_back(0);
+        FDS_TRY(P.jobs.upload(jobs, s));
+        FDS_TRY(P.tiles.upload(tiles, s));
+        FDS_TRY(P.maps.upload(maps, s));
+        FDS_TRY(P.aslices.alloc((size_t)atile * OZ_TILE));
+        FDS_TRY(P.rowexp.alloc((size_t)rexp));
+        DBuf<OzSrc> d_src;
+        FDS_TRY(d_src.upload(src, s));
+        fds_count_launch(), k_ozj_slice_a<<<P.njobs, 256, 0, s>>>(P.jobs.p, d_src.p, P.aslices.p, P.rowexp.p);
+        FDS_CUDA_TRY(cudaGetLastError());
+        FDS_CUDA_TRY(cudaStreamSynchronize(s));   // d_src is freed on return
+        passes.push_back(std::move(P));
+    }
+    return FDS_OK;
+}
+
+int oz_plan_apply(fds_handle *h, const std::vector<OzPlan> &passes, const float4 *x, int64_t ldx, float4 *y,
+                  int64_t ldy, int nc, cudaStream_t s) {
+    if (nc <= 0) return FDS_OK;
+    const int ntile = (nc + OZJ_BN - 1) / OZJ_BN;
+    const int cols = ntile * OZJ_BN;
+    if (cols / 8 > 65535) return FDS_ERR_ARG;
+    for (const OzPlan &P : passes) {
+        const size_t xs = (size_t)P.xgroups * ntile * OZ_SLICES * OZJ_XTILE;
+        if (h->oz_x.n < xs) FDS_TRY(h->oz_x.alloc(xs));
+        if (h->oz_colexp.n < (size_t)P.njobs * cols) FDS_TRY(h->oz_colexp.alloc((size_t)P.njobs * cols));
+        fds_count_launch(), k_ozj_slice_x<<<dim3(P.njobs, cols / 8), 256, 0, s>>>(
+            P.jobs.p, P.maps.p, x, ldx, nc, ntile, h->oz_x.p, h->oz_colexp.p);
+        FDS_CUDA_TRY(cudaGetLastError());
+        const int64_t items = (int64_t)P.ntiles * ntile;
+        if (items > 2147483647LL) return FDS_ERR_ARG;
+        constexpr int smem = OzjLayout::TOTAL;
+        FDS_TRY(ensure_dyn_smem(k_ozj, smem));
+        const int grid = (int)std::min<int64_t>(items, sm_count());
+        fds_count_launch(), k_ozj<<<grid, OZJ_THREADS, smem, s>>>(P.jobs.p, P.tiles.p, (int)items, ntile, P.maps.p,
+                                                                  P.aslices.p, P.rowexp.p, h->oz_x.p,
+                                                                  h->oz_colexp.p, y, ldy, nc);
+        FDS_CUDA_TRY(cudaGetLastError());
+    }
+    return FDS_OK;
+}
+
+int ozj_status_take(cudaStream_t s, int *status) {
+    int v = 0, zero = 0;
+    FDS_CUDA_TRY(cudaMemcpyFromSymbolAsync(&v, g_ozj_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+    FDS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (v) FDS_CUDA_TRY(cudaMemcpyToSymbolAsync(g_ozj_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    *status = v;
+    return FDS_OK;
+}
+
+int ozj_fault_arm(int on) {
+    const int v = on ? 1 : 0;
+    FDS_CUDA_TRY(cudaMemcpyToSymbol(g_ozj_fault, &v, sizeof(int)));
+    return FDS_OK;
+}
+
+namespace {
+
 int oz_slice_blocks(int nb, const MatRef *d_blocks, DBuf<unsigned char> &aslices, DBuf<int> &rowexp,
                     cudaStream_t s) {
     FDS_TRY(aslices.alloc((size_t)nb * 2 * OZ_KC * OZ_SLICES * OZ_TILE));
@@ -613,6 +1127,61 @@ extern "C" int fds_zgemm_blocks_tc(int32_t batch, const int32_t *d, const double
     FDS_CUDA_TRY(cudaStreamSynchronize(s));
     int st = 0;
     FDS_TRY(oz_status_take(s, &st));
+    return st ? FDS_ERR_TIMEOUT : FDS_OK;
+}
+
+extern "C" int fds_zgemm_jobs_tc(int32_t njobs, const int32_t *m, const int32_t *k, const int32_t *op,
+                                 const int64_t *a_off, const int32_t *lda, const int64_t *x_row,
+                                 const int64_t *xmap_off, const int64_t *y_row, const int64_t *ymap_off,
+                                 const int32_t *set, const int32_t *maps, const double *d_A, const double *d_X,
+                                 int64_t ldx, double *d_Y, int64_t ldy, int32_t nc, uint64_t stream) {
+    if (njobs < 0 || nc < 0 || ldx < 1 || ldy < 1) return FDS_ERR_ARG;
+    if (njobs == 0 || nc == 0) return FDS_OK;
+    if (!m || !k || !op || !a_off || !lda || !x_row || !xmap_off || !y_row || !ymap_off || !set || !d_A || !d_X ||
+        !d_Y)
+        return FDS_ERR_ARG;
+    std::vector<OzSpec> specs(njobs);
+    for (int e = 0; e < njobs; ++e) {
+        if (m[e] < 0 || k[e] < 0 || (op[e] != 0 && op[e] != 1) || lda[e] < std::max(1, op[e] ? k[e] : m[e]) ||
+            a_off[e] < 0 || x_row[e] < 0 || y_row[e] < 0 || ((xmap_off[e] >= 0 || ymap_off[e] >= 0) && !maps))
+            return FDS_ERR_ARG;
+        OzSpec &q = specs[e];
+        q.a = reinterpret_cast<const cplx *>(d_A) + a_off[e];
+        q.lda = lda[e];
+        q.op = op[e];
+        q.m = m[e];
+        q.k = k[e];
+        q.x_row = x_row[e];
+        q.y_row = y_row[e];
+        q.xmap = xmap_off[e] >= 0 ? maps + xmap_off[e] : nullptr;
+        q.ymap = ymap_off[e] >= 0 ? maps + ymap_off[e] : nullptr;
+        q.set = set[e] != 0;
+        // every row addressed stays inside X and Y
+        for (int l = 0; l < q.k; ++l) {
+            const int64_t r = q.x_row + (q.xmap ? q.xmap[l] : l);
+            if (r < 0 || r >= ldx) return FDS_ERR_ARG;
+        }
+        for (int i = 0; i < q.m; ++i) {
+            const int64_t r = q.y_row + (q.ymap ? q.ymap[i] : i);
+            if (r < 0 || r >= ldy) return FDS_ERR_ARG;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    fds_handle h;   // workspace holder for the vector slices
+    std::vector<OzPlan> passes;
+    FDS_TRY(oz_plan_build(specs, passes, s));
+    DBuf<float4> xp, yp;
+    FDS_TRY(xp.alloc((size_t)ldx * nc));
+    FDS_TRY(yp.alloc((size_t)ldy * nc));
+    fds_count_launch(), k_oz_to_pairs<<<1024, 256, 0, s>>>((const cplx *)d_X, xp.p, ldx * nc);
+    fds_count_launch(), k_oz_to_pairs<<<1024, 256, 0, s>>>((const cplx *)d_Y, yp.p, ldy * nc);
+    FDS_CUDA_TRY(cudaGetLastError());
+    FDS_TRY(oz_plan_apply(&h, passes, xp.p, ldx, yp.p, ldy, nc, s));
+    fds_count_launch(), k_oz_from_pairs<<<1024, 256, 0, s>>>(yp.p, (cplx *)d_Y, ldy * nc);
+    FDS_CUDA_TRY(cudaGetLastError());
+    FDS_CUDA_TRY(cudaStreamSynchronize(s));
+    int st = 0;
+    FDS_TRY(ozj_status_take(s, &st));
     return st ? FDS_ERR_TIMEOUT : FDS_OK;
 }
 

@@ -131,6 +131,7 @@ def lib():
                                         i64p, i64p, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, i32, u64]
     L.fds_alu_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
     L.fds_zgemm_blocks_tc.argtypes = [i32, ctypes.POINTER(i32), vp, vp, vp, i32, u64]
+    L.fds_zgemm_jobs_tc.argtypes = [i32] + [vp] * 12 + [vp, vp, ctypes.c_int64, vp, ctypes.c_int64, i32, u64]
     L.fds_fault_inject.argtypes = [i32, ctypes.c_int64]
     L.fds_bounds_violations.argtypes = [ctypes.POINTER(ctypes.c_int64)]
     L.fds_autotune_enable.argtypes = [i32]
@@ -473,6 +474,21 @@ def fds_bounds_violations():
     n = ctypes.c_int64(0)
     _check(lib().fds_bounds_violations(ctypes.byref(n)), "fds_bounds_violations")
     return int(n.value)
+
+
+def fds_zgemm_jobs_tc(m, k, op, a_off, lda, x_row, xmap_off, y_row, ymap_off, set_, maps, d_A, d_X, d_Y,
+                      stream=None):
+    """General block products on the tensor cores (see include/fds.h):
+    per-job host arrays, maps (int32 host array), d_A complex128 CUDA
+    tensor, d_X / d_Y complex128 (nc, rows) tensors (column-major rows x nc,
+    leading dimension = rows); d_Y updated in place."""
+    a = [np.ascontiguousarray(v, dtype=t) for v, t in
+         ((m, np.int32), (k, np.int32), (op, np.int32), (a_off, np.int64), (lda, np.int32), (x_row, np.int64),
+          (xmap_off, np.int64), (y_row, np.int64), (ymap_off, np.int64), (set_, np.int32))]
+    mp = np.ascontiguousarray(maps if maps is not None and len(maps) else np.zeros(1), dtype=np.int32)
+    nc = d_X.shape[0]
+    _check(lib().fds_zgemm_jobs_tc(len(a[0]), *[v.ctypes.data for v in a], mp.ctypes.data, _ptr(d_A), _ptr(d_X),
+                                   d_X.shape[1], _ptr(d_Y), d_Y.shape[1], nc, _stream(stream)), "fds_zgemm_jobs_tc")
 
 
 def fds_autotune_enable(on=True):
