@@ -98,6 +98,13 @@ def parse():
     return p.parse_args()
 
 
+# forward-operator phases on the tensor cores with --fw-engine tensor, and
+# their algorithmic flops per column
+TENSOR_FW = {"a7.fw_leaf_diag": "8 d^2 per leaf", "a7.fw_sibling": "8 x 2 r_a r_b per parent",
+             "a7.fw_interp_up": "8 k (n - k) per cell and component",
+             "a7.fw_interp_down": "8 k (n - k) per cell and component"}
+
+
 def max_over_ranks(value, device):
     """The largest of the ranks' values (the job's time is its slowest rank)."""
     import torch
@@ -716,11 +723,11 @@ def main():
         fp32 = phase_on_fp32(name, args.precision, args.merge == "c64")
         peak = alu["fp32_tflops"] if fp32 else alu["fp64_tflops"]
         pipe, bound = "fp32" if fp32 else "fp64", "alu"
-        if name == "a7.fw_leaf_diag" and args.fw_engine == "tensor" and args.precision == "mixed":
+        if name in TENSOR_FW and args.fw_engine == "tensor" and args.precision == "mixed":
             # 21 bf16 slice products per FP64-accurate product, on the tensor cores
             flops, pipe, bound = 21.0 * flops, "tensor (bf16)", "tensor"
             peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0))
-            basis = "21 bf16 products x the phase's algorithmic flops (8 d^2 per column per leaf)"
+            basis = "21 bf16 products x the phase's algorithmic flops (%s)" % TENSOR_FW[name]
         ent = {"ms_per_step": d["ms"] / args.steps, "launches_per_step": d["launches"] / args.steps,
                "bound": bound, "pipe": pipe, "basis": basis}
         if flops > 0:

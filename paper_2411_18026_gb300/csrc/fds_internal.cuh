@@ -181,9 +181,9 @@ struct Level {
     DBuf<unsigned char> oz_a;
     DBuf<int> oz_rowexp;
     // fw_engine = FDS_FW_TENSOR: plans of the level's forward-operator
-    // products on the tensor cores (one entry per K pass): leaf blocks,
-    // interpolation up (T^c) and down (T^cH), sibling blocks
-    std::vector<OzPlan> oz_leaf, oz_up, oz_down, oz_sib;
+    // products on the tensor cores (one entry per K pass): downward
+    // interpolation (T^cH) and sibling blocks
+    std::vector<OzPlan> oz_down, oz_sib;
     std::vector<int64_t> toff_h;   // host copy of the T^c block offsets
     int srmax = 0;
     double sum_s2 = 0;            // sum over cells of 2 r_a r_b
@@ -247,7 +247,8 @@ struct fds_handle {
     DBuf<MatRefF> wrefsf;
     DBuf<double> wnorm;
     DBuf<int> wundo;           // per-column flags of the refinement's take-back step
-    DBuf<unsigned char> oz_x;  // fw_engine = FDS_FW_TENSOR: bf16 slices of the leaf vectors
+    bool oz_jobs = false;      // fw_engine = FDS_FW_TENSOR: the forward operator runs the levels' plans
+    DBuf<unsigned char> oz_x;  // fw_engine = FDS_FW_TENSOR: bf16 slices of the vectors
     DBuf<int> oz_colexp;
     // use_graph: one CUDA graph of the sweep per column count, with the
     // workspace layout (hash of its buffer addresses) it was captured against

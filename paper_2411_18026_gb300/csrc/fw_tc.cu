@@ -1195,7 +1195,8 @@ int oz_status_take(cudaStream_t s, int *status) {
 }
 
 int oz_fault_arm(int on) {
+    // both tensor-core product kernels (leaf-block stage entry, general plans)
     const int v = on ? 1 : 0;
     FDS_CUDA_TRY(cudaMemcpyToSymbol(g_oz_fault, &v, sizeof(int)));
-    return FDS_OK;
+    return ozj_fault_arm(on);
 }

@@ -312,18 +312,34 @@ int apply_S(fds_handle *h, const Level &C, const T *x, int64_t ldx, T *y, int64_
     return dense_gemm_map(2 * nb, std::max(C.srmax, 1), nc, A, 0, B, Cr, M, 1, s);
 }
 
-// leaf blocks on the tensor cores: float-pair vectors with slices prepared
+// products on the tensor cores (fw_engine = FDS_FW_TENSOR): float-pair
+// vectors, with the plans of every level prepared by fds_mixed_prepare
 template <class T>
-bool leaf_on_tensor(const Level &C) {
+bool fw_on_tensor(const fds_handle *h) {
     return false;
 }
 template <>
-bool leaf_on_tensor<float4>(const Level &C) {
-    return C.oz_a.p != nullptr;
+bool fw_on_tensor<float4>(const fds_handle *h) {
+    return h->oz_jobs;
 }
-inline int oz_leaf(fds_handle *h, Level &C, const cplx *, cplx *, int64_t, int, cudaStream_t) { return FDS_ERR_STATE; }
+inline int oz_run(fds_handle *, const std::vector<OzPlan> &, const cplx *, int64_t, cplx *, int64_t, int,
+                  cudaStream_t) {
+    return FDS_ERR_STATE;
+}
+inline int oz_run(fds_handle *h, const std::vector<OzPlan> &P, const float4 *x, int64_t ldx, float4 *y, int64_t ldy,
+                  int nc, cudaStream_t s) {
+    return oz_plan_apply(h, P, x, ldx, y, ldy, nc, s);
+}
+inline int oz_leaf(fds_handle *, Level &, const cplx *, cplx *, int64_t, int, cudaStream_t) { return FDS_ERR_STATE; }
 inline int oz_leaf(fds_handle *h, Level &C, const float4 *x, float4 *y, int64_t ld, int nc, cudaStream_t s) {
     return oz_leaf_apply(h, C, x, y, ld, nc, s);
+}
+inline int vskel(const Level &, int, const cplx *, int64_t, cplx *, int64_t, int, cudaStream_t) {
+    return FDS_ERR_STATE;
+}
+inline int vskel(const Level &C, int dir, const float4 *x, int64_t ldx, float4 *y, int64_t ldy, int nc,
+                 cudaStream_t s) {
+    return vskel_apply<float4>(C, dir, x, ldx, y, ldy, nc, s);
 }
 
 // Y = A X for nc leaf-order columns (both D_L x nc, column-major).
@@ -335,6 +351,7 @@ int forward_apply(fds_handle *h, const T *X, T *Y, int nc, cudaStream_t s) {
     MatRefT<T> *rZ = F::refs(h).p, *rT = rZ + maxnb, *rY = rT + maxnb, *rX = rY + maxnb;   // rX: 2 slots
     auto &wz = F::z(h), &wt = F::t(h), &wy = F::y(h);
     ProfScope ps("a7.forward_apply", s);
+    const bool tc = fw_on_tensor<T>(h);
     double fl = 0;
     // up
     for (int l = L; l > l0; --l) {
@@ -371,7 +388,8 @@ int forward_apply(fds_handle *h, const T *X, T *Y, int nc, cudaStream_t s) {
         FDS_TRY(F::gemm(1, (int)h->Dtop, nc, F::top(h), 0, rX, rX + 1, 0, s));
         fl += 8.0 * (double)h->Dtop * h->Dtop * nc;
         if (L > l0) {
-            FDS_TRY(apply_S<T>(h, Tl, xt, h->Dtop, yt, h->Dtop, nc, s));
+            if (tc) FDS_TRY(oz_run(h, Tl.oz_sib, xt, h->Dtop, yt, h->Dtop, nc, s));
+            else FDS_TRY(apply_S<T>(h, Tl, xt, h->Dtop, yt, h->Dtop, nc, s));
             fl += 8.0 * Tl.sum_s2 * nc;
         } else {
             fds_count_launch(), k_refs<T><<<(Tl.nb + 127) / 128, 128, 0, s>>>(Tl.nb, xt, Tl.d_doff.p, nc, h->Dtop,
@@ -398,17 +416,23 @@ int forward_apply(fds_handle *h, const T *X, T *Y, int nc, cudaStream_t s) {
         {
             ProfScope pv("a7.fw_interp_down", s);
             pv.flops = 8.0 * C.sum_tm * nc;
-            FDS_TRY(apply_VH<T>(h, C, F::Tm(C), wt[l].p, ldr, yl, C.D, nc, s));
+            if (tc) {
+                FDS_TRY(vskel(C, 1, wt[l].p, ldr, yl, C.D, nc, s));
+                FDS_TRY(oz_run(h, C.oz_down, wt[l].p, ldr, yl, C.D, nc, s));
+            } else {
+                FDS_TRY(apply_VH<T>(h, C, F::Tm(C), wt[l].p, ldr, yl, C.D, nc, s));
+            }
         }
         if (l < L) {
             ProfScope pss("a7.fw_sibling", s);
             pss.flops = 8.0 * C.sum_s2 * nc;
-            FDS_TRY(apply_S<T>(h, C, xl, C.D, yl, C.D, nc, s));
+            if (tc) FDS_TRY(oz_run(h, C.oz_sib, xl, C.D, yl, C.D, nc, s));
+            else FDS_TRY(apply_S<T>(h, C, xl, C.D, yl, C.D, nc, s));
             fl += 8.0 * (C.sum_tm + C.sum_s2) * nc;
         } else {
             ProfScope pd("a7.fw_leaf_diag", s);
             pd.flops = 8.0 * level_d2(C) * nc;
-            if (leaf_on_tensor<T>(C)) {
+            if (tc && C.oz_a.p) {
                 FDS_TRY(oz_leaf(h, C, xl, yl, C.D, nc, s));
             } else {
                 fds_count_launch(), k_refs<T><<<(nb + 127) / 128, 128, 0, s>>>(nb, yl, C.d_doff.p, nc, C.D, rY);
@@ -442,6 +466,46 @@ int fds_keep_blocks(const Level &Lv, DBuf<cplx> &dst, DBuf<MatRef> &rdst, cudaSt
     std::vector<int> d(Lv.nb);
     for (int b = 0; b < Lv.nb; ++b) d[b] = Lv.n1[b] + Lv.n2[b];
     return make_refs_t(rdst, dst.p, Lv.offA, d, d, s);
+}
+
+// Tensor-core products of level C: the plan of its downward interpolation
+// blocks (y[other rows] = T^cH t) and, at the leaf level, the slices of its
+// diagonal blocks for the leaf kernel.  The upward blocks T^c (k_c rows,
+// typically 30-100) stay double-float: on the 128-row tensor-core tiles they
+// measured no faster.
+int oz_interp_leaf_plans(fds_handle *h, Level &C, bool leaf, cudaStream_t s, int64_t &bytes) {
+    std::vector<int> vmap(C.D);
+    for (int b = 0; b < C.nb; ++b)
+        for (int c = 0; c < 2; ++c) {
+            const int n = c ? C.n2[b] : C.n1[b], coff = c ? C.n1[b] : 0;
+            for (int q = 0; q < n; ++q) vmap[C.doff[b] + coff + q] = coff + C.perm[C.permoff[2 * b + c] + q];
+        }
+    std::vector<OzSpec> down;
+    down.reserve(2 * (size_t)C.nb);
+    for (int b = 0; b < C.nb; ++b)
+        for (int c = 0; c < 2; ++c) {
+            const int n = c ? C.n2[b] : C.n1[b], k = c ? C.k2[b] : C.k1[b], m = n - k;
+            const int coff = c ? C.n1[b] : 0;
+            const int *vm = vmap.data() + C.doff[b] + coff;
+            OzSpec q;
+            q.a = C.T.p + C.toff_h[2 * b + c];
+            q.lda = std::max(k, 1);
+            q.op = 1;              // y[rest] (m rows) = T^H (m x k) t
+            q.m = m;
+            q.k = k;
+            q.x_row = C.roff[b] + (c ? C.k1[b] : 0);
+            q.y_row = C.doff[b];
+            q.ymap = vm + k;
+            q.set = true;
+            down.push_back(q);
+        }
+    FDS_TRY(oz_plan_build(down, C.oz_down, s));
+    for (const OzPlan &P : C.oz_down) bytes += (int64_t)(P.aslices.bytes() + P.rowexp.bytes());
+    if (leaf && C.dmax <= 128) {   // larger leaves stay double-float
+        FDS_TRY(oz_leaf_prepare(C, C.rDfw.p, s));
+        bytes += (int64_t)(C.oz_a.bytes() + C.oz_rowexp.bytes());
+    }
+    return FDS_OK;
 }
 
 int fds_mixed_prepare(fds_handle *h) {
@@ -492,6 +556,9 @@ int fds_mixed_prepare(fds_handle *h) {
         FDS_TRY(split_blocks(C.W, C.Wp, C.rWp, C.offW, dv, rv, s));
         FDS_TRY(split_blocks(C.At, C.Atp, C.rAtp, C.offAt, rv, rv, s));
     }
+    // fw_engine = FDS_FW_TENSOR: every block product of the forward operator
+    // (leaf, interpolation, sibling) on the tensor cores
+    const bool tensor_fw = h->opt.ir_apply == FDS_APPLY_FF && h->opt.fw_engine == FDS_FW_TENSOR && L > l0;
     // compact sibling blocks of every parent level (l0 .. L-1): child a's and
     // b's skeleton DOFs of the parent, grouped by child
     for (int l = L - 1; l >= l0; --l) {
@@ -532,6 +599,33 @@ int fds_mixed_prepare(fds_handle *h) {
             fds_count_launch(), k_split<<<1024, 256, 0, s>>>(Pn.Sc.p, Pn.Scp.p, (int64_t)Pn.Sc.n);
             FDS_CUDA_TRY(cudaGetLastError());
         }
+        if (tensor_fw) {
+            // y_a += S_ab x_b and y_b += S_ba x_a per parent, rows through sperm
+            std::vector<OzSpec> sp;
+            sp.reserve(2 * (size_t)Pn.nb);
+            for (int p = 0; p < Pn.nb; ++p) {
+                const int a = ra[p], b = rb[p];
+                const int64_t o = Pn.doff[p];
+                OzSpec q;
+                q.a = Pn.Sc.p + scoff[2 * p];
+                q.lda = std::max(a, 1);
+                q.m = a;
+                q.k = b;
+                q.x_row = q.y_row = o;
+                q.xmap = sperm.data() + o + a;
+                q.ymap = sperm.data() + o;
+                sp.push_back(q);
+                q.a = Pn.Sc.p + scoff[2 * p + 1];
+                q.lda = std::max(b, 1);
+                q.m = b;
+                q.k = a;
+                q.xmap = sperm.data() + o;
+                q.ymap = sperm.data() + o + a;
+                sp.push_back(q);
+            }
+            FDS_TRY(oz_plan_build(sp, Pn.oz_sib, s));
+            for (const OzPlan &P : Pn.oz_sib) bytes += (int64_t)(P.aslices.bytes() + P.rowexp.bytes());
+        }
         bytes += (int64_t)(Pn.Sc.bytes() + Pn.Scp.bytes()) - (int64_t)Pn.Sfw.bytes();
     }
     if (h->opt.ir_apply == FDS_APPLY_FF || h->opt.sweep_ff) {
@@ -552,9 +646,7 @@ int fds_mixed_prepare(fds_handle *h) {
                 rv[b] = l > l0 ? C.k1[b] + C.k2[b] : 0;
             }
             if (C.Dfw.p) FDS_TRY(split_blocks(C.Dfw, C.Dp, C.rDp, C.offA, dv, dv, s));
-            // tensor-core slices of the leaf blocks (leaves of up to 64 nodes)
-            if (l == L && L > l0 && C.Dfw.p && h->opt.fw_engine == FDS_FW_TENSOR && C.dmax <= 128)
-                FDS_TRY(oz_leaf_prepare(C, C.rDfw.p, s));
+            if (tensor_fw && l > l0) FDS_TRY(oz_interp_leaf_plans(h, C, l == L, s, bytes));
 
         }
         {
@@ -563,6 +655,7 @@ int fds_mixed_prepare(fds_handle *h) {
             FDS_TRY(split_blocks(h->Atop_off, h->Atop_offp, h->rtop_offp, off, d, d, s));
         }
     }
+    if (tensor_fw) h->oz_jobs = true;
     FDS_CUDA_TRY(cudaStreamSynchronize(s));
     for (int l = L; l >= l0; --l) {   // the compact blocks replace the d x d sibling coupling
         Level &C = h->lv[l];
@@ -715,9 +808,11 @@ int fds_solve_mixed_impl(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
     // the refinement's sweep vectors are in the leaf level's precision
     const int rc = (h->L > h->l0 && level_prec(h, h->L) == PREC_FF) ? solve_mixed<float4>(h, d_rhs, nrhs, s)
                                                                    : solve_mixed<cplxf>(h, d_rhs, nrhs, s);
-    if (h->L > h->l0 && h->lv[h->L].oz_a.p) {
-        int st = 0;
-        FDS_TRY(oz_status_take(s, &st));
+    if (h->oz_jobs) {
+        int st = 0, st2 = 0;
+        FDS_TRY(ozj_status_take(s, &st));
+        FDS_TRY(oz_status_take(s, &st2));
+        st |= st2;
         if (st) {
             fds_set_error_detail("tensor-core forward operator: wait on a pipeline barrier timed out");
             return FDS_ERR_TIMEOUT;

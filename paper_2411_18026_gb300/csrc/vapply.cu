@@ -104,6 +104,16 @@ int vapply(fds_handle *h, const Level &C, const T *Tb, int dir, const T *src, in
 }  // namespace
 
 template <class T>
+int vskel_apply(const Level &C, int dir, const T *src, int64_t lds, T *dst, int64_t ldd, int nc, cudaStream_t s) {
+    if (C.nb == 0 || nc == 0) return FDS_OK;
+    fds_count_launch(), k_vskel<T><<<C.nb, 256, 0, s>>>(dir, C.d_k1.p, C.d_k2.p, C.d_n1.p, C.d_doff.p, C.d_roff.p,
+                                                        C.d_vmap.p, src, lds, dst, ldd, nc);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
+}
+template int vskel_apply<float4>(const Level &, int, const float4 *, int64_t, float4 *, int64_t, int, cudaStream_t);
+
+template <class T>
 int apply_V(fds_handle *h, const Level &C, const T *Tb, const T *x, int64_t ldx, T *out, int64_t ldo, int nc,
             cudaStream_t s) {
     return vapply<T>(h, C, Tb, 0, x, ldx, out, ldo, nc, s);

@@ -131,7 +131,7 @@ def lib():
                                         i64p, i64p, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, i32, u64]
     L.fds_alu_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
     L.fds_zgemm_blocks_tc.argtypes = [i32, ctypes.POINTER(i32), vp, vp, vp, i32, u64]
-    L.fds_zgemm_jobs_tc.argtypes = [i32] + [vp] * 12 + [vp, vp, ctypes.c_int64, vp, ctypes.c_int64, i32, u64]
+    L.fds_zgemm_jobs_tc.argtypes = [i32] + [vp] * 11 + [vp, vp, ctypes.c_int64, vp, ctypes.c_int64, i32, u64]
     L.fds_fault_inject.argtypes = [i32, ctypes.c_int64]
     L.fds_bounds_violations.argtypes = [ctypes.POINTER(ctypes.c_int64)]
     L.fds_autotune_enable.argtypes = [i32]

@@ -67,3 +67,11 @@ def test_default_library_has_no_bounds_checks(fds):
     import ctypes as C
     n = C.c_int64(-1)
     assert fds.lib().fds_bounds_violations(C.byref(n)) == fds.FDS_ERR_STATE
+
+
+def test_stage_entries_argument_checks_without_gpu(fds):
+    # empty batches return before any device work; the bindings' argument lists match
+    L = fds.lib()
+    assert L.fds_zgemm_jobs_tc(0, *([None] * 11), None, None, 1, None, 1, 0, 0) == fds.FDS_OK
+    assert L.fds_zgemm_jobs_tc(-1, *([None] * 11), None, None, 1, None, 1, 0, 0) == fds.FDS_ERR_ARG
+    assert L.fds_zgemm_blocks_tc(0, None, None, None, None, 0, 0) == fds.FDS_OK
