@@ -160,6 +160,42 @@ __device__ __forceinline__ int pair_acc(int i, int j) {
     return g == 3 ? 6 : 7;
 }
 
+// The products of operator slice I with vector slices j = 0 .. 5 - I for one
+// K chunk (nks k-steps of 16): descriptors da (slice I's tile) and db[j]
+// (the chunk's vector slice tiles) advance by 32 bytes (2 in the address
+// field) per k-step; pair (I, j) accumulates into group pair_acc(I, j) of
+// the set at tacc (ncol columns per group) and overwrites it when it is the
+// group's first pair of the item's first chunk.  All indexes are
+// compile-time constants, so each MMA costs a few instructions to issue.
+template <int I>
+__device__ __forceinline__ void mma_slice(uint32_t tacc, uint32_t ncol, uint64_t da, const uint64_t (&db)[6],
+                                          uint32_t idesc, int nks, bool first_chunk) {
+#pragma unroll
+    for (int j = 0; j < 6 - I; ++j) {
+        const int g = pair_acc(I, j);
+        // first pair of its group in issue order (i outer, j inner): (0, 0..4), (1, 0), (1, 1), (2, 0)
+        const bool grp_first = (I == 0 && j <= 4) || (I == 1 && j <= 1) || (I == 2 && j == 0);
+        const uint32_t d = tacc + (uint32_t)g * ncol;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+            if (ks < nks)
+                mma_bf16(d, da + 2ull * ks, db[j] + 2ull * ks, idesc,
+                         (first_chunk && ks == 0 && grp_first) ? 0u : 1u);
+    }
+}
+
+__device__ __forceinline__ void mma_slice_rt(int i, uint32_t tacc, uint32_t ncol, uint64_t da,
+                                             const uint64_t (&db)[6], uint32_t idesc, int nks, bool first_chunk) {
+    switch (i) {
+        case 0: mma_slice<0>(tacc, ncol, da, db, idesc, nks, first_chunk); break;
+        case 1: mma_slice<1>(tacc, ncol, da, db, idesc, nks, first_chunk); break;
+        case 2: mma_slice<2>(tacc, ncol, da, db, idesc, nks, first_chunk); break;
+        case 3: mma_slice<3>(tacc, ncol, da, db, idesc, nks, first_chunk); break;
+        case 4: mma_slice<4>(tacc, ncol, da, db, idesc, nks, first_chunk); break;
+        default: mma_slice<5>(tacc, ncol, da, db, idesc, nks, first_chunk); break;
+    }
+}
+
 // six slices of v in (-1, 1), slice i times 2^(-8i) (all exact in bf16)
 __device__ __forceinline__ void cut6(double v, unsigned short (&out)[OZ_SLICES]) {
     double sc = 1.0;
@@ -390,7 +426,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         // MMA issuer: for each K chunk and A slice i, the products with x
         // slices j = 0 .. 5 - i into the accumulator of (i, j)
         const uint32_t idesc = idesc_bf16_m128_n64();
-        int started = 0;   // bit g: accumulator g written once
         int ua = 0;
         bool ok = true;
         for (int kc = 0; kc < nkc && ok; ++kc) {
@@ -400,6 +435,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 break;
             }
             const int kin = min(64, 2 * d - kc * 64);   // reals of this chunk holding data
+            const int nks = (kin + 15) / 16;
+            uint64_t db[OZ_SLICES];
+#pragma unroll
+            for (int j = 0; j < OZ_SLICES; ++j)
+                db[j] = sw128_desc(sbase + OzLayout::XOFF + qx * OzLayout::XBUF + j * OZ_XTILE);
             for (int i = 0; i < OZ_SLICES; ++i, ++ua) {
                 const int qa = ua % OZ_NA;
                 if (!mbar_wait(smem_u32(fullA + qa), (uint32_t)((ua / OZ_NA) & 1))) {
@@ -407,16 +447,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t sa = sbase + qa * OZ_TILE;
-                for (int j = 0; j < OZ_SLICES - i; ++j) {
-                    const int g = pair_acc(i, j);
-                    const uint32_t sb = sbase + OzLayout::XOFF + qx * OzLayout::XBUF + j * OZ_XTILE;
-                    for (int ks = 0; ks < (kin + 15) / 16; ++ks) {
-                        mma_bf16(tmem + (uint32_t)(g * OZ_BN), sw128_desc(sa + 32u * ks), sw128_desc(sb + 32u * ks),
-                                 idesc, ((started >> g) & 1) ? 1u : 0u);
-                        started |= 1 << g;
-                    }
-                }
+                mma_slice_rt(i, tmem, OZ_BN, sw128_desc(sbase + qa * OZ_TILE), db, idesc, nks, kc == 0);
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                  smem_u32(emptyA + qa))
                              : "memory");
@@ -430,7 +461,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(donebar))
                      : "memory");
-        if (ok && started != (1 << OZ_ACC) - 1) atomicExch(sflag, 1);   // an accumulator never written
     }
     __syncwarp();
     const bool done_ok = mbar_wait(smem_u32(donebar), 0u);
@@ -448,9 +478,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int r = mt * 128 + warp * 32 + lane;            // real row of the leaf block
         const uint32_t tq = tmem + ((uint32_t)(warp * 32) << 16);
         const int er = rowexp[b * 256 + r];
+        const float rs1 = pow2f(er / 2), rs2 = pow2f(er - er / 2);   // 2^e_r in two exact factors
         for (int cb = 0; cb < OZ_BN; cb += 16) {
             const int c0 = nt * OZ_BN + cb;
             if (c0 >= nc) break;
+            // 2^(f_c - 16) of column c0 + j in two exact factors, held by lane j
+            const int fj = (lane < 16 && c0 + lane < nc) ? s_colexp[cb + lane] - 16 : 0;
+            const float cs1 = pow2f(fj / 2), cs2 = pow2f(fj - fj / 2);
             uint32_t raw[OZ_ACC][16];
 #pragma unroll
             for (int g = 0; g < OZ_ACC; ++g) tmem_ld16_nowait(tq + (uint32_t)(g * OZ_BN + cb), raw[g]);
@@ -480,11 +514,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                     lo += e;
                 }
                 lo += v[6][j] + v[7][j];
-                // scale by 2^(e_r + f_c - 16) in at most two exact power-of-two steps
-                const int sh = c < nc ? er + s_colexp[cb + j] - 16 : 0;
-                const float s1 = pow2f(sh / 2), s2 = pow2f(sh - sh / 2);
-                h = c < nc ? (h * s1) * s2 : 0.f;
-                lo = c < nc ? (lo * s1) * s2 : 0.f;
+                // scale by 2^(e_r + f_c - 16) in exact power-of-two steps
+                const float a1 = __shfl_sync(0xffffffffu, cs1, j), a2 = __shfl_sync(0xffffffffu, cs2, j);
+                h = c < nc ? (((h * rs1) * rs2) * a1) * a2 : 0.f;
+                lo = c < nc ? (((lo * rs1) * rs2) * a1) * a2 : 0.f;
                 const float oh = __shfl_xor_sync(0xffffffffu, h, 1);   // the partner real row
                 const float ol = __shfl_xor_sync(0xffffffffu, lo, 1);
                 if (wr && c < nc) {
@@ -682,10 +715,13 @@ __global__ void __launch_bounds__(OZJ_THREADS, 1)
             // a buffer, then the operator slice tiles A_0 .. A_5 through the ring
             const bool stall = blockIdx.x == 0 && atomicExch(&g_ozj_fault, 0) != 0;
             int ua = 0, ux = 0;
+            int2 tl = blockIdx.x < nitems ? tiles[blockIdx.x / ntile] : make_int2(0, 0);
+            OzJob J = jobs[tl.x];
             for (int it = blockIdx.x; it < nitems && !stall; it += gridDim.x) {
-                const int2 tl = tiles[it / ntile];
                 const int nt = it % ntile;
-                const OzJob J = jobs[tl.x];
+                // the next item's tile, loaded while this item's copies are issued
+                const int itn = it + gridDim.x;
+                const int2 tln = itn < nitems ? tiles[itn / ntile] : tl;
                 const unsigned char *ab = aslices + (size_t)(J.a_tile + (int64_t)tl.y * J.nkc * OZ_SLICES) * OZ_TILE;
                 const unsigned char *xb =
                     xslices + (size_t)((J.x_tile * ntile + (int64_t)nt * J.nkc) * OZ_SLICES) * OZJ_XTILE;
@@ -729,6 +765,8 @@ __global__ void __launch_bounds__(OZJ_THREADS, 1)
                     atomicExch(sflag, 1);
                     break;
                 }
+                tl = tln;
+                J = jobs[tl.x];
             }
             // every copy issued has landed before the CTA may exit (bounded)
             for (int q = 0; q < OZJ_NA && q < ua; ++q) {
@@ -756,7 +794,6 @@ __global__ void __launch_bounds__(OZJ_THREADS, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t tacc = tmem + (uint32_t)(tb * OZ_ACC * OZJ_BN);
-                int started = 0;
                 for (int kc = 0; kc < J.nkc && ok; ++kc) {
                     const int qx = ux % OZJ_NX;
                     if (!mbar_wait(smem_u32(fullX + qx), (uint32_t)((ux / OZJ_NX) & 1)) || *(volatile int *)sflag) {
@@ -766,6 +803,10 @@ __global__ void __launch_bounds__(OZJ_THREADS, 1)
                     // k-steps of 16 reals holding data (one zero step for a job without columns)
                     const int kin = min(64, 2 * J.k - kc * 64);
                     const int nks = max(1, (kin + 15) / 16);
+                    uint64_t db[OZ_SLICES];
+#pragma unroll
+                    for (int j = 0; j < OZ_SLICES; ++j)
+                        db[j] = sw128_desc(sbase + OzjLayout::XOFF + qx * OzjLayout::XBUF + j * OZJ_XTILE);
                     for (int i = 0; i < OZ_SLICES; ++i) {
                         const int qa = ua % OZJ_NA;
                         if (!mbar_wait(smem_u32(fullA + qa), (uint32_t)((ua / OZJ_NA) & 1))) {
@@ -773,16 +814,7 @@ __global__ void __launch_bounds__(OZJ_THREADS, 1)
                             break;
                         }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint32_t sa = sbase + qa * OZ_TILE;
-                        for (int j = 0; j < OZ_SLICES - i; ++j) {
-                            const int g = pair_acc(i, j);
-                            const uint32_t sb = sbase + OzjLayout::XOFF + qx * OzjLayout::XBUF + j * OZJ_XTILE;
-                            for (int ks = 0; ks < nks; ++ks) {
-                                mma_bf16(tacc + (uint32_t)(g * OZJ_BN), sw128_desc(sa + 32u * ks),
-                                         sw128_desc(sb + 32u * ks), idesc, ((started >> g) & 1) ? 1u : 0u);
-                                started |= 1 << g;
-                            }
-                        }
+                        mma_slice_rt(i, tacc, OZJ_BN, sw128_desc(sbase + qa * OZ_TILE), db, idesc, nks, kc == 0);
                         asm volatile(
                             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                 smem_u32(emptyA + qa))
@@ -796,10 +828,6 @@ __global__ void __launch_bounds__(OZJ_THREADS, 1)
                     ++ux;
                 }
                 if (!ok) break;
-                if (started != (1 << OZ_ACC) - 1) {   // an accumulator never written
-                    ok = false;
-                    break;
-                }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                  smem_u32(tfull + tb))
                              : "memory");
@@ -816,6 +844,18 @@ __global__ void __launch_bounds__(OZJ_THREADS, 1)
         int n = 0;
         for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++n) {
             const int tb = n & 1;
+            // the item's description, loaded while its MMAs run
+            const int2 tl = tiles[it / ntile];
+            const int nt = it % ntile;
+            const OzJob J = jobs[tl.x];
+            const int r = tl.y * 128 + warp * 32 + lane;   // real row of op(A_e)
+            const bool valid = r < 2 * J.m;
+            const bool live = __any_sync(0xffffffffu, valid);   // the warp holds rows of the job
+            const int er = rowexp[J.rexp + r];
+            const int64_t yr = valid ? J.y_row + (J.ymap >= 0 ? maps[J.ymap + (r >> 1)] : (r >> 1)) : 0;
+            const bool set = J.flags & 1;
+            const float rs1 = pow2f(er / 2), rs2 = pow2f(er - er / 2);   // 2^e_r in two exact factors
+            const int *ce = colexp + (int64_t)tl.x * cols;
             bool ok = mbar_wait(smem_u32(tfull + tb), (uint32_t)((n >> 1) & 1)) && !*(volatile int *)sflag;
             ok = __all_sync(0xffffffffu, ok);   // the warp leaves together (its loads and shuffles are warp-wide)
             if (!ok) {
@@ -823,28 +863,24 @@ __global__ void __launch_bounds__(OZJ_THREADS, 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int2 tl = tiles[it / ntile];
-            const int nt = it % ntile;
-            const OzJob J = jobs[tl.x];
-            const int r = tl.y * 128 + warp * 32 + lane;   // real row of op(A_e)
-            const bool valid = r < 2 * J.m;
-            const int er = rowexp[J.rexp + r];
-            const int64_t yr = valid ? J.y_row + (J.ymap >= 0 ? maps[J.ymap + (r >> 1)] : (r >> 1)) : 0;
-            const bool set = J.flags & 1;
             const uint32_t tq = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(tb * OZ_ACC * OZJ_BN);
-            const int *ce = colexp + (int64_t)tl.x * cols;
             for (int cb = 0; cb < OZJ_BN; cb += 16) {
                 const int c0 = nt * OZJ_BN + cb;
+                // 2^(f_c - 16) of column c0 + j in two exact factors, held by lane j
+                const int fj = (lane < 16 && c0 + lane < nc) ? ce[c0 + lane] - 16 : 0;
+                const float cs1 = pow2f(fj / 2), cs2 = pow2f(fj - fj / 2);
                 uint32_t rw[OZ_ACC][16];
-#pragma unroll
-                for (int g = 0; g < OZ_ACC; ++g) tmem_ld16_nowait(tq + (uint32_t)(g * OZJ_BN + cb), rw[g]);
                 float4 ycur[16];
                 const bool wr = !(lane & 1) && valid;
+                if (live) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    ycur[j] = (wr && !set && c0 + j < nc) ? y[yr + (int64_t)(c0 + j) * ldy]
-                                                          : make_float4(0.f, 0.f, 0.f, 0.f);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    for (int g = 0; g < OZ_ACC; ++g) tmem_ld16_nowait(tq + (uint32_t)(g * OZJ_BN + cb), rw[g]);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        ycur[j] = (wr && !set && c0 + j < nc) ? y[yr + (int64_t)(c0 + j) * ldy]
+                                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                }
                 if (cb + 16 == OZJ_BN) {
                     // the set is in registers: hand it back to the MMA issuer
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -853,6 +889,7 @@ __global__ void __launch_bounds__(OZJ_THREADS, 1)
                         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty + tb))
                                      : "memory");
                 }
+                if (!live) continue;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int c = c0 + j;
@@ -863,10 +900,9 @@ __global__ void __launch_bounds__(OZJ_THREADS, 1)
                         lo += e;
                     }
                     lo += __uint_as_float(rw[6][j]) + __uint_as_float(rw[7][j]);
-                    const int sh = c < nc ? er + ce[c] - 16 : 0;
-                    const float s1 = pow2f(sh / 2), s2 = pow2f(sh - sh / 2);
-                    h = c < nc ? (h * s1) * s2 : 0.f;
-                    lo = c < nc ? (lo * s1) * s2 : 0.f;
+                    const float a1 = __shfl_sync(0xffffffffu, cs1, j), a2 = __shfl_sync(0xffffffffu, cs2, j);
+                    h = (((h * rs1) * rs2) * a1) * a2;
+                    lo = (((lo * rs1) * rs2) * a1) * a2;
                     const float oh = __shfl_xor_sync(0xffffffffu, h, 1);   // the partner real row
                     const float ol = __shfl_xor_sync(0xffffffffu, lo, 1);
                     if (wr && c < nc) {
