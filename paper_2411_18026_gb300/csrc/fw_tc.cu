@@ -107,6 +107,7 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;   // the common case: no timer read
     const unsigned long long t0 = global_ns();
     while (!mbar_try(bar, parity))
         if (global_ns() - t0 > OZ_WAIT_NS) return false;
