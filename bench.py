@@ -460,11 +460,14 @@ def run_mr2005(args, fds, torch, rank):
 
 def run_batch(args, fds, torch, world, rank, local):
     """64 seeded cavities (ellipses / stars, 2^12..2^15 nodes, k_T a in [1, 20],
-    eps 1e-8, leaf 64) built with fds_build_batch on --streams concurrent
-    streams, 16 plane waves each (8 P + 8 SV), solved with fds_solve_batch.
+    eps 1e-8, leaf 64, complex128 as in the batched configuration) built
+    with fds_build_batch on --streams concurrent streams, 16 plane waves each
+    (8 P + 8 SV), solved with one launch per tree level and phase across the
+    cavities (fds_solve_batch_levels; CUDA-graph replay unless --no-graph).
     One step = batch build + load vectors + batch solve; after the timed
-    steps the same work one cavity at a time (1 stream) is timed once for
-    comparison."""
+    steps the same work one cavity at a time (1 stream) is timed once, and
+    the solve alone of one built batch both ways (level-batched launches,
+    per-cavity streams)."""
     import workloads
     cav = workloads.random_cavities(64, seed=workloads.SEED + 2 + 97 * rank)
     for c in cav:
@@ -474,14 +477,25 @@ def run_batch(args, fds, torch, world, rank, local):
     d_a = torch.from_numpy(angles).cuda()
     d_F = [torch.empty((16, 2 * c["N"]), dtype=torch.complex128, device="cuda") for c in cav]
     eps = 1e-8
-    prec = fds.FDS_MIXED if args.precision == "mixed" else fds.FDS_FP64
+    prec = fds.FDS_FP64
+    stream = torch.cuda.Stream()
 
-    def step(streams, graph=not args.no_graph):
-        hs = fds.fds_build_batch(cav, 2.0, 1.0, eps, n_streams=streams, leaf_size=args.leaf, precision=prec,
-                                 use_graph=graph)
+    def load(hs):
         for h, F in zip(hs, d_F):
             fds.fds_rhs_plane_wave_device(h, d_k, d_a, F, fds.fds_handle_stream(h))
-        fds.fds_solve_batch(hs, d_F, n_streams=streams)
+
+    def solve(hs, levels, graph, streams):
+        if levels:
+            with torch.cuda.stream(stream):
+                fds.fds_solve_batch_levels(hs, d_F, use_graph=graph, stream=stream.cuda_stream)
+        else:
+            fds.fds_solve_batch(hs, d_F, n_streams=streams)
+
+    def step(streams, graph=not args.no_graph, levels=True):
+        hs = fds.fds_build_batch(cav, 2.0, 1.0, eps, n_streams=streams, leaf_size=args.leaf, precision=prec,
+                                 use_graph=graph)
+        load(hs)
+        solve(hs, levels and streams > 1, graph, streams)
         for h in hs:
             h.close()
 
@@ -506,24 +520,40 @@ def run_batch(args, fds, torch, world, rank, local):
     step(1)
     torch.cuda.synchronize()
     seq_ms = (time.perf_counter() - t1) * 1e3
-    # the other sweep mode (graph replay vs kernel by kernel), once
-    t2 = time.perf_counter()
-    step(args.streams, graph=args.no_graph)
-    torch.cuda.synchronize()
-    other_ms = (time.perf_counter() - t2) * 1e3
+    # the solve alone of one built batch: level-batched launches (graph and
+    # plain) against per-cavity streams, best of three each
+    hs = fds.fds_build_batch(cav, 2.0, 1.0, eps, n_streams=args.streams, leaf_size=args.leaf, precision=prec)
+    solve_ms, solve_launches = {}, {}
+    for name, levels, graph in (("levels_graph", True, True), ("levels", True, False), ("streams", False, False)):
+        best = None
+        for _ in range(3):
+            load(hs)
+            torch.cuda.synchronize()
+            l0_ = fds.fds_launch_count()
+            t = time.perf_counter()
+            solve(hs, levels, graph, args.streams)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t) * 1e3
+            best = dt if best is None else min(best, dt)
+            solve_launches[name] = int(fds.fds_launch_count() - l0_)
+        solve_ms[name] = best
+    for h in hs:
+        h.close()
     if rank != 0:
         return
     nodes = sum(c["N"] for c in cav)
     line = {"metric": "batched build + solve of 64 cavities (s per batch)", "value": ms / 1e3, "unit": "s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "c128+c64" if prec == fds.FDS_MIXED else "c128", "data": "synthetic",
+            "dtype": "c128", "data": "synthetic",
             "config": {"workload": "64 seeded cavities (ellipse aspect 1-4 / star e in [0,0.3], m in 3..8), "
                                    "2^12-2^15 nodes (%d in total), k_T a in [1,20], eps 1e-8, leaf %d, "
-                                   "16 plane waves each, %d streams" % (nodes, args.leaf, args.streams),
+                                   "16 plane waves each, complex128, build on %d streams, solve with one "
+                                   "launch per level and phase across the cavities" % (nodes, args.leaf,
+                                                                                        args.streams),
                        "timing": "host wall clock around the whole batch (several streams), synchronised"},
             "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / ms, "gpu_launches": int(launches),
-            "graph": not args.no_graph, ("no_graph_ms" if not args.no_graph else "graph_ms"): other_ms,
+            "graph": not args.no_graph, "solve_only_ms": solve_ms, "solve_only_launches": solve_launches,
             "clocks": clk}
     print(json.dumps(line))
 

@@ -563,6 +563,28 @@ int fds_solve_batch(int32_t count, fds_handle *const *h, double *const *d_rhs, c
                     int32_t n_streams);
 uint64_t fds_handle_stream(const fds_handle *h);
 
+/*
+ * Solve of many cavities with one launch per tree level and phase across all
+ * of them (Sec. 7.3's sweep, whose cells of one level are independent, over
+ * the cells of every cavity at once): for handles h[0..count) built with
+ * precision FDS_FP64 and the LU variant, each with at least one level below
+ * its top, the upward sweep runs aligned from the leaves (step j: level
+ * L_i - j of every cavity that has it), the top solves as one batched GEMM,
+ * the downward sweep aligned from the top; each phase of a step (Z =
+ * A^{-1} R, the two parts of V, A~ U, the parent placement; downward the
+ * gathers and the two updates) is one launch over the cells of all
+ * participating cavities.  d_rhs[i]: device, 2 n_i x nrhs[i] complex128,
+ * solved in place in chunks of 256 columns.  use_graph != 0 captures the
+ * sweep of a chunk shape into a CUDA graph on its first chunk and replays
+ * it for the later chunks of that shape (needs a non-default stream).
+ * Waits for each handle's stream, runs on `stream`, synchronises it at the
+ * end.  Results equal fds_solve's on each handle (same kernels, same
+ * summation order).  FDS_ERR_ARG for a handle of another precision or
+ * variant, or with a single cell.
+ */
+int fds_solve_batch_levels(int32_t count, fds_handle *const *h, double *const *d_rhs, const int32_t *nrhs,
+                           int32_t use_graph, uint64_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -133,6 +133,7 @@ def lib():
     L.fds_zgemm_blocks_tc.argtypes = [i32, ctypes.POINTER(i32), vp, vp, vp, i32, u64]
     L.fds_zgemm_jobs_tc.argtypes = [i32] + [vp] * 11 + [vp, vp, ctypes.c_int64, vp, ctypes.c_int64, i32, u64]
     L.fds_fault_inject.argtypes = [i32, ctypes.c_int64]
+    L.fds_solve_batch_levels.argtypes = [i32, vp, vp, vp, i32, u64]
     L.fds_bounds_violations.argtypes = [ctypes.POINTER(ctypes.c_int64)]
     L.fds_autotune_enable.argtypes = [i32]
     L.fds_autotune_enable.restype = None
@@ -297,6 +298,18 @@ def fds_solve_batch(handles, d_rhs_list, n_streams=8):
     ps = (ctypes.c_void_p * n)(*[t.data_ptr() for t in d_rhs_list])
     nr = (ctypes.c_int32 * n)(*[t.shape[0] for t in d_rhs_list])
     _check(lib().fds_solve_batch(n, hs, ps, nr, int(n_streams)), "fds_solve_batch")
+
+
+def fds_solve_batch_levels(handles, d_rhs_list, use_graph=False, stream=None):
+    """Solve in place with one launch per tree level and phase across the
+    cavities (FP64, LU-variant handles): d_rhs_list[i] complex128 CUDA
+    tensor (nrhs_i, 2 n_i) for handle i."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.ptr.value for h in handles])
+    ps = (ctypes.c_void_p * n)(*[t.data_ptr() for t in d_rhs_list])
+    nr = (ctypes.c_int32 * n)(*[t.shape[0] for t in d_rhs_list])
+    _check(lib().fds_solve_batch_levels(n, hs, ps, nr, 1 if use_graph else 0, _stream(stream)),
+           "fds_solve_batch_levels")
 
 
 def fds_handle_stream(h):

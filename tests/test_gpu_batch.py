@@ -79,3 +79,37 @@ def test_batch_error_releases_everything():
     with pytest.raises(fds.FdsError) as e:
         fds.fds_build_batch(cav, 2.0, 1.0, 1e-8, n_streams=2)
     assert e.value.code == fds.FDS_ERR_ARG
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_level_batched_solve_equals_per_cavity_solves(use_graph):
+    # one launch per tree level and phase across cavities of different
+    # depths (2^9..2^11 nodes: 3-5 levels below the top) and different
+    # numbers of right-hand sides (300 = a full chunk + a ragged one; 1; 0);
+    # the same kernels in the same summation order give the same bits
+    torch = torch_cuda()
+    fds = fdslib()
+    cav = _cavities(6, workloads.SEED + 24)
+    hb = fds.fds_build_batch(cav, 2.0, 1.0, 1e-9, n_streams=3, leaf_size=64)
+    rng = np.random.default_rng(77)
+    counts = [300, 16, 1, 0, 40, 257]
+    d_rhs, ref = [], []
+    for h, nr in zip(hb, counts):
+        F = rng.standard_normal((2 * h.n, nr)) + 1j * rng.standard_normal((2 * h.n, nr))
+        ref.append(fds.fds_solve(h, F.copy()) if nr else F)
+        d_rhs.append(torch.tensor(np.ascontiguousarray(F.T), device="cuda"))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        fds.fds_solve_batch_levels(hb, d_rhs, use_graph=use_graph, stream=s.cuda_stream)
+    s.synchronize()
+    for d, x, nr in zip(d_rhs, ref, counts):
+        if nr:
+            assert np.array_equal(d.cpu().numpy().T, x)
+    # handles of another precision are refused
+    hm = fds.fds_build(cav[0]["xy"], cav[0]["omega"], 2.0, 1.0, 1e-9, precision=fds.FDS_MIXED)
+    with pytest.raises(fds.FdsError) as e:
+        fds.fds_solve_batch_levels([hm], [d_rhs[0]])
+    assert e.value.code == fds.FDS_ERR_ARG
+    hm.close()
+    for h in hb:
+        h.close()
