@@ -187,51 +187,32 @@ __global__ void __launch_bounds__(NT) k_gemm_rt(const MatRefT<typename Ar::G> *_
     for (int i = 0; i < MI; ++i)
 #pragma unroll
         for (int j = 0; j < TJ; ++j) Ar::zero(acc[i][j]);
-    // the next K slab is loaded into registers while the current one is
-    // multiplied out of shared memory (the summation order is unchanged)
-    SA pa[MI];
-    SB pb[TJ];
-    auto load = [&](int k0) {
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        // stage op(A)[i0:i0+BMt, k0:k0+16] as sa[k][i]
         if (opA == 0) {
 #pragma unroll
             for (int q = 0; q < MI; ++q) {
                 const int e = t + NT * q, i = e % BMt, k = e / BMt;
                 const int gi = i0 + i, gk = k0 + k;
-                pa[q] = (gi < M && gk < K) ? Ar::stage_a(A.p[gi + (int64_t)gk * A.ld], false) : Ar::za();
+                sa[k][i] = (gi < M && gk < K) ? Ar::stage_a(A.p[gi + (int64_t)gk * A.ld], false) : Ar::za();
             }
         } else {
 #pragma unroll
             for (int q = 0; q < MI; ++q) {
                 const int k = t & 15, i = (t >> 4) + 16 * q;
                 const int gi = i0 + i, gk = k0 + k;
-                pa[q] = (gi < M && gk < K) ? Ar::stage_a(A.p[gk + (int64_t)gi * A.ld], true) : Ar::za();
+                sa[k][i] = (gi < M && gk < K) ? Ar::stage_a(A.p[gk + (int64_t)gi * A.ld], true) : Ar::za();
             }
         }
+        // stage B[k0:k0+16, j0:j0+BN] as sb[k][j]
 #pragma unroll
         for (int q = 0; q < TJ; ++q) {
             const int k = t & 15, j = (t >> 4) + 16 * q;
             const int gk = k0 + k, gj = j0 + j;
             const int rk = (gk < K && gj < N) ? (bmap ? bmap[gk] : gk) : -1;
-            pb[q] = (rk >= 0 && FDS_IN_RANGE(rk, B.rows)) ? Ar::stage_b(B.p[rk + (int64_t)gj * B.ld]) : Ar::zb();
+            sb[k][j] = (rk >= 0 && FDS_IN_RANGE(rk, B.rows)) ? Ar::stage_b(B.p[rk + (int64_t)gj * B.ld]) : Ar::zb();
         }
-    };
-    if (K > 0) load(0);
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        // op(A)[i0:i0+BMt, k0:k0+16] as sa[k][i], B[k0:k0+16, j0:j0+BN] as sb[k][j]
-        if (opA == 0) {
-#pragma unroll
-            for (int q = 0; q < MI; ++q) {
-                const int e = t + NT * q;
-                sa[e / BMt][e % BMt] = pa[q];
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < MI; ++q) sa[t & 15][(t >> 4) + 16 * q] = pa[q];
-        }
-#pragma unroll
-        for (int q = 0; q < TJ; ++q) sb[t & 15][(t >> 4) + 16 * q] = pb[q];
         __syncthreads();
-        if (k0 + BK < K) load(k0 + BK);
         const int kmax = min(BK, K - k0);
         for (int k = 0; k < kmax; ++k) {
             SA a[MI];
