@@ -371,6 +371,66 @@ __global__ void k_cast(const A *__restrict__ src, B *dst, int64_t n) {
     }
 }
 
+// float pairs (float4: re_hi, im_hi, re_lo, im_lo) from complex128 / complex64
+template <class A>
+__global__ void k_to_ff(const A *__restrict__ src, float4 *dst, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const double re = src[e].x, im = src[e].y;
+        const float rh = (float)re, ih = (float)im;
+        dst[e] = make_float4(rh, ih, (float)(re - (double)rh), (float)(im - (double)ih));
+    }
+}
+
+// complex64 (rounded) or complex128 from float pairs
+template <class B>
+__global__ void k_from_ff(const float4 *__restrict__ src, B *dst, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = src[e];
+        dst[e].x = (double)v.x + (double)v.z;
+        dst[e].y = (double)v.y + (double)v.w;
+    }
+}
+
+// X1 = X0 + D (float pairs X0, complex64 correction D): the float-pair sum
+// (renormalised) and its complex64 rounding
+__global__ void k_ff_add_c64(const float4 *__restrict__ x0, const cplxf *__restrict__ d, float4 *x1, cplxf *x1f,
+                             int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = x0[e];
+        const cplxf b = d[e];
+        float h[2] = {a.x, a.y}, l[2] = {a.z, a.w};
+        const float c[2] = {b.x, b.y};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float s = h[q] + c[q], bb = s - h[q];
+            const float err = (h[q] - (s - bb)) + (c[q] - bb) + l[q];
+            h[q] = s + err;
+            l[q] = err - (h[q] - s);
+        }
+        x1[e] = make_float4(h[0], h[1], l[0], l[1]);
+        x1f[e] = mkcf(h[0] + l[0], h[1] + l[1]);
+    }
+}
+
+// R = I - R on every block (float pairs)
+__global__ void k_ff_identity_minus(const MatRefP *__restrict__ Ms) {
+    const MatRefP M = Ms[blockIdx.x];
+    for (int64_t e = threadIdx.x; e < (int64_t)M.rows * M.cols; e += blockDim.x) {
+        const int i = (int)(e % M.rows), j = (int)(e / M.rows);
+        float4 &v = M.p[i + (int64_t)j * M.ld];
+        float rh = -v.x, rl = -v.z;
+        if (i == j) {
+            // 1 - (h + l): two-sum of 1 and -h, then the low parts (Knuth)
+            const float s1 = 1.0f + rh, bb = s1 - 1.0f;
+            const float err = (1.0f - (s1 - bb)) + (rh - bb);
+            const float lo = err + rl;
+            rh = s1 + lo;
+            rl = lo - (rh - s1);
+        }
+        v = make_float4(rh, -v.y, rl, -v.w);
+    }
+}
+
 __global__ void k_zero(cplx *p, int64_t n) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
         p[e] = mkc(0, 0);
@@ -1028,8 +1088,16 @@ int fds_build_impl(fds_handle *h) {
         FDS_TRY(d_sp.upload(spoff, s));
         FDS_TRY(info2.alloc(nb));
         if (merge64) {
-            // complex64 copies of the level's blocks and of V; W, A_i^{-1},
-            // S and A~ in complex64; A~ back in complex128 for the parent
+            // complex64 LU of the level's blocks for first inverses, each
+            // refined by one Newton step whose residual is formed in
+            // double-float arithmetic (float pairs on the FP32 pipe):
+            //   X1 = X0 + X0 (I - A X0)   against the FP64 blocks A,
+            //   W = X1 V^H, S = V W       (complex64),
+            //   A~ = Y0 + Y0 (I - S Y0)   Y0 from a complex64 LU of S.
+            // The refined inverses, rounded to complex64 for the sweep, are as
+            // accurate as FP64 ones rounded (without the steps the first
+            // solve's residual is ~1000x larger and the refinement needs one
+            // more sweep); A~ goes to the parent in complex128.
             const int64_t nA = C.offA[nb], nV = C.offV[nb], nS = C.offAt[nb];
             DBuf<cplxf> LUf, Sf;
             DBuf<MatRefF> rLUf, rSf;
@@ -1045,20 +1113,35 @@ int fds_build_impl(fds_handle *h) {
             FDS_TRY(make_refs_t(C.rAinvf, C.Ainvf.p, C.offA, dv, dv, s));
             FDS_TRY(make_refs_t(C.rAtf, C.Atf.p, C.offAt, rv, rv, s));
             FDS_TRY(make_refs_t(rSf, Sf.p, C.offAt, rv, rv, s));
+            // double-float work buffers: A, X0, R, X1 (d x d); S, Y0, RS, Y1 (r x r)
+            // (nS, nV <= nA: the r x r and d x r blocks fit the d x d complex64 buffers below)
+            DBuf<float4> Ap, Xp, Rp, X1p, Sp, Yp, RSp, Y1p;
+            DBuf<MatRefP> rAp, rXp, rRp, rX1p, rSp, rYp, rRSp, rY1p;
+            for (auto *b : {&Ap, &Xp, &Rp, &X1p}) FDS_TRY(b->alloc(nA));
+            for (auto *b : {&Sp, &Yp, &RSp, &Y1p}) FDS_TRY(b->alloc(nS));
+            // complex64 residual and correction of the Newton steps (d x d, reused for r x r)
+            DBuf<cplxf> Rf, Df;
+            DBuf<MatRefF> rRf, rDf, rRSf, rDSf;
+            FDS_TRY(Rf.alloc(nA));
+            FDS_TRY(Df.alloc(nA));
+            FDS_TRY(make_refs_t(rRf, Rf.p, C.offA, dv, dv, s));
+            FDS_TRY(make_refs_t(rDf, Df.p, C.offA, dv, dv, s));
+            FDS_TRY(make_refs_t(rAp, Ap.p, C.offA, dv, dv, s));
+            FDS_TRY(make_refs_t(rXp, Xp.p, C.offA, dv, dv, s));
+            FDS_TRY(make_refs_t(rRp, Rp.p, C.offA, dv, dv, s));
+            FDS_TRY(make_refs_t(rX1p, X1p.p, C.offA, dv, dv, s));
+            FDS_TRY(make_refs_t(rSp, Sp.p, C.offAt, rv, rv, s));
+            FDS_TRY(make_refs_t(rYp, Yp.p, C.offAt, rv, rv, s));
+            FDS_TRY(make_refs_t(rRSp, RSp.p, C.offAt, rv, rv, s));
+            FDS_TRY(make_refs_t(rY1p, Y1p.p, C.offAt, rv, rv, s));
             fds_count_launch(), k_cast<cplx, cplxf><<<1024, 256, 0, s>>>(C.LU.p, LUf.p, nA);
             fds_count_launch(), k_cast<cplx, cplxf><<<1024, 256, 0, s>>>(C.V.p, C.Vf.p, nV);
+            fds_count_launch(), k_to_ff<cplx><<<1024, 256, 0, s>>>(C.LU.p, Ap.p, nA);
             FDS_CUDA_TRY(cudaGetLastError());
             {
                 ProfScope ps("a3.merge_lu", s);
                 ps.flops = fl_lu;
                 FDS_TRY(dense_lu(nb, C.dmax, rLUf.p, C.piv.p, C.d_offpiv.p, info.p, s));
-            }
-            fds_count_launch(), k_conj_transpose<cplxf><<<nb, 256, 0, s>>>(C.rVf.p, C.rWf.p);
-            FDS_CUDA_TRY(cudaGetLastError());
-            {
-                ProfScope ps("a3.merge_w_solve", s);
-                ps.flops = fl_w;
-                FDS_TRY(dense_lu_solve(nb, C.dmax, C.rmax, rLUf.p, C.piv.p, C.d_offpiv.p, C.rWf.p, s));
             }
             fds_count_launch(), k_set_identity<cplxf><<<nb, 256, 0, s>>>(C.rAinvf.p);
             FDS_CUDA_TRY(cudaGetLastError());
@@ -1068,9 +1151,37 @@ int fds_build_impl(fds_handle *h) {
                 FDS_TRY(dense_lu_solve(nb, C.dmax, C.dmax, rLUf.p, C.piv.p, C.d_offpiv.p, C.rAinvf.p, s));
             }
             {
+                // X1 = X0 + X0 (I - A X0) in double-float, rounded to complex64
+                ProfScope ps("a3.merge_refine", s);
+                ps.flops = fl_lu * 6.0;   // two d^3 complex products per cell
+                fds_count_launch(), k_to_ff<cplxf><<<1024, 256, 0, s>>>(C.Ainvf.p, Xp.p, nA);
+                FDS_CUDA_TRY(cudaGetLastError());
+                FDS_TRY(dense_gemm_ffp(nb, C.dmax, C.dmax, rAp.p, 0, rXp.p, rRp.p, 0, s));
+                fds_count_launch(), k_ff_identity_minus<<<nb, 256, 0, s>>>(rRp.p);
+                // the correction X0 R (~|R| |X0|) needs complex64 accuracy only
+                fds_count_launch(), k_from_ff<cplxf><<<1024, 256, 0, s>>>(Rp.p, Rf.p, nA);
+                FDS_CUDA_TRY(cudaGetLastError());
+                FDS_TRY(dense_gemm_rt(nb, C.dmax, C.dmax, C.rAinvf.p, 0, rRf.p, rDf.p, mkcf(1, 0), mkcf(0, 0), s));
+                fds_count_launch(), k_ff_add_c64<<<1024, 256, 0, s>>>(Xp.p, Df.p, X1p.p, C.Ainvf.p, nA);
+                FDS_CUDA_TRY(cudaGetLastError());
+            }
+            {
+                // W = A^{-1} U = X1 V^H (complex64, V^H staged in the correction buffer)
+                ProfScope ps("a3.merge_w_solve", s);
+                ps.flops = fl_w;
+                DBuf<MatRefF> rVHf;
+                FDS_TRY(make_refs_t(rVHf, Df.p, C.offW, dv, rv, s));
+                fds_count_launch(), k_conj_transpose<cplxf><<<nb, 256, 0, s>>>(C.rVf.p, rVHf.p);
+                FDS_CUDA_TRY(cudaGetLastError());
+                FDS_TRY(dense_gemm_rt(nb, C.dmax, C.rmax, C.rAinvf.p, 0, rVHf.p, C.rWf.p, mkcf(1, 0), mkcf(0, 0), s));
+                FDS_CUDA_TRY(cudaStreamSynchronize(s));   // rVHf is freed on leaving the block
+            }
+            {
                 ProfScope ps("a3.merge_s_gemm", s);
                 ps.flops = fl_s;
-                FDS_TRY(dense_gemm(nb, C.rmax, C.rmax, C.rVf.p, 0, C.rWf.p, 0, rSf.p, mkcf(1, 0), mkcf(0, 0), s));
+                FDS_TRY(dense_gemm_rt(nb, C.rmax, C.rmax, C.rVf.p, 0, C.rWf.p, rSf.p, mkcf(1, 0), mkcf(0, 0), s));
+                fds_count_launch(), k_to_ff<cplxf><<<1024, 256, 0, s>>>(Sf.p, Sp.p, nS);
+                FDS_CUDA_TRY(cudaGetLastError());
             }
             {
                 ProfScope ps("a3.merge_s_lu", s);
@@ -1084,8 +1195,24 @@ int fds_build_impl(fds_handle *h) {
                 ps.flops = fl_at;
                 FDS_TRY(dense_lu_solve(nb, C.rmax, C.rmax, rSf.p, spiv.p, d_sp.p, C.rAtf.p, s));
             }
-            fds_count_launch(), k_cast<cplxf, cplx><<<1024, 256, 0, s>>>(C.Atf.p, C.At.p, nS);
-            FDS_CUDA_TRY(cudaGetLastError());
+            {
+                // A~ = Y0 + Y0 (I - S Y0) in double-float: complex64 for the sweep, complex128 for the parent
+                ProfScope ps("a3.merge_refine", s);
+                ps.flops = fl_at * 2.0;
+                fds_count_launch(), k_to_ff<cplxf><<<1024, 256, 0, s>>>(C.Atf.p, Yp.p, nS);
+                FDS_CUDA_TRY(cudaGetLastError());
+                FDS_TRY(dense_gemm_ffp(nb, C.rmax, C.rmax, rSp.p, 0, rYp.p, rRSp.p, 0, s));
+                fds_count_launch(), k_ff_identity_minus<<<nb, 256, 0, s>>>(rRSp.p);
+                fds_count_launch(), k_from_ff<cplxf><<<1024, 256, 0, s>>>(RSp.p, Rf.p, nS);
+                FDS_CUDA_TRY(cudaGetLastError());
+                FDS_TRY(make_refs_t(rRSf, Rf.p, C.offAt, rv, rv, s));
+                FDS_TRY(make_refs_t(rDSf, Df.p, C.offAt, rv, rv, s));
+                FDS_TRY(dense_gemm_rt(nb, C.rmax, C.rmax, C.rAtf.p, 0, rRSf.p, rDSf.p, mkcf(1, 0), mkcf(0, 0), s));
+                fds_count_launch(), k_ff_add_c64<<<1024, 256, 0, s>>>(Yp.p, Df.p, Y1p.p, C.Atf.p, nS);
+                fds_count_launch(), k_from_ff<cplx><<<1024, 256, 0, s>>>(Y1p.p, C.At.p, nS);
+                FDS_CUDA_TRY(cudaGetLastError());
+            }
+            FDS_CUDA_TRY(cudaStreamSynchronize(s));   // the work buffers are freed on leaving the block
         } else {
             {
                 ProfScope ps("a3.merge_lu", s);
@@ -1273,7 +1400,11 @@ int fds_build_impl(fds_handle *h) {
         }
         FDS_TRY(T.d_doff.upload(T.doff, s));
     }
-    if (h->opt.precision == FDS_MIXED) FDS_TRY(fds_mixed_prepare(h));
+    if (h->opt.precision == FDS_MIXED) {
+        // complex64 / float-pair copies of the factors, the forward operator's blocks and their tensor-core slices
+        ProfScope ps("a4.mixed_prepare", h->stream);
+        FDS_TRY(fds_mixed_prepare(h));
+    }
     // the solve applies V through T (vapply.cu): the dense V_i are not kept
     FDS_TRY(sync_check(s));
     for (int l = L; l > h->l0; --l) {

@@ -197,16 +197,30 @@ __device__ __forceinline__ void mma_slice_rt(int i, uint32_t tacc, uint32_t ncol
     }
 }
 
-// six slices of v in (-1, 1), slice i times 2^(-8i) (all exact in bf16)
-__device__ __forceinline__ void cut6(double v, unsigned short (&out)[OZ_SLICES]) {
-    double sc = 1.0;
+// Six slices of v = a 2^-e (|v| < 1): s_i = trunc(256 v_i), v_{i+1} =
+// 256 v_i - s_i (v_0 = v), slice i stored times 2^(-8i) (exact in bf16).
+// Computed from the bits of a: q = trunc(|v| 2^48) by an integer shift of
+// a's 53-bit significand, s_i = bits 40 - 8i .. 47 - 8i of q with a's sign
+// (the same values as the FP64 recurrence, whose steps are all exact, on
+// the integer pipe instead of the slow FP64 one).
+__device__ __forceinline__ void cut6_bits(double a, int e, unsigned short (&out)[OZ_SLICES]) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    const int ex = (int)((b >> 52) & 2047ull);
+    unsigned long long q = 0;
+    if (ex != 0) {   // zero or subnormal: below 2^-1022, no bit at 2^-48 of v
+        const unsigned long long mant = (b & ((1ull << 52) - 1ull)) | (1ull << 52);   // |a| = mant 2^(ex - 1075)
+        const int sh = 1027 - ex + e;                                               // |v| 2^48 = mant 2^-sh
+        q = sh >= 64 ? 0ull : (sh > 0 ? (mant >> sh) : (mant << min(-sh, 11)));
+    }
+    if (q >= (1ull << 48)) q = (1ull << 48) - 1;   // |v| < 1
+    const bool neg = (b >> 63) != 0ull;
+    float sc = 1.0f;
 #pragma unroll
     for (int i = 0; i < OZ_SLICES; ++i) {
-        v *= 256.0;
-        const double t = trunc(v);
-        v -= t;
-        out[i] = __bfloat16_as_ushort(__double2bfloat16(t * sc));
-        sc *= 1.0 / 256.0;
+        const uint32_t chunk = (uint32_t)((q >> (40 - 8 * i)) & 255ull);
+        const float t = (__uint_as_float(0x4B000000u | chunk) - 8388608.0f) * sc;
+        out[i] = __bfloat16_as_ushort(__float2bfloat16_rn(neg ? -t : t));
+        sc *= 1.0f / 256.0f;
     }
 }
 
@@ -233,7 +247,6 @@ __global__ void k_oz_slice_a(int nb, const MatRef *__restrict__ D, unsigned char
     int e = 0;
     if (m > 0.0) frexp(m, &e);
     if (lane == 0) rowexp[b * 256 + r] = e;
-    const double inv = ldexp(1.0, -e);
     const int mt = r >> 7, rr = r & 127;
     for (int k = lane; k < 256; k += 32) {
         double v = 0.0;
@@ -243,7 +256,7 @@ __global__ void k_oz_slice_a(int nb, const MatRef *__restrict__ D, unsigned char
             v = !im_row ? ((k & 1) ? -a.y : a.x) : ((k & 1) ? a.x : a.y);
         }
         unsigned short s[OZ_SLICES];
-        cut6(v * inv, s);
+        cut6_bits(v, e, s);
         const int kc = k >> 6;
         unsigned char *t = slices + (size_t)(((b * 2 + mt) * OZ_KC + kc) * OZ_SLICES) * OZ_TILE;
         const uint32_t off = sw_elem(rr, k & 63);
@@ -598,7 +611,6 @@ __global__ void k_ozj_slice_a(const OzJob *__restrict__ jobs, const OzSrc *__res
         int e = 0;
         if (mx > 0.0) frexp(mx, &e);
         if (lane == 0) rowexp[J.rexp + r] = e;
-        const double inv = ldexp(1.0, -e);
         const int mt = r >> 7, rr = r & 127;
         for (int kk = lane; kk < K; kk += 32) {
             const int l = kk >> 1;
@@ -609,7 +621,7 @@ __global__ void k_ozj_slice_a(const OzJob *__restrict__ jobs, const OzSrc *__res
                 v = !im_row ? ((kk & 1) ? -a.y : a.x) : ((kk & 1) ? a.x : a.y);
             }
             unsigned short s[OZ_SLICES];
-            cut6(v * inv, s);
+            cut6_bits(v, e, s);
             unsigned char *t = slices + (size_t)(J.a_tile + (int64_t)(mt * J.nkc + (kk >> 6)) * OZ_SLICES) * OZ_TILE;
             const uint32_t off = sw_elem(rr, kk & 63);
 #pragma unroll
