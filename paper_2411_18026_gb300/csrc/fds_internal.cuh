@@ -247,6 +247,8 @@ struct fds_handle {
     DBuf<MatRefF> wrefsf;
     DBuf<double> wnorm;
     DBuf<int> wundo;           // per-column flags of the refinement's take-back step
+    DBuf<int> wcmap;           // refinement: right-hand side of each compact column
+    DBuf<unsigned char> wperm; // refinement: staging of a column permutation
     bool oz_jobs = false;      // fw_engine = FDS_FW_TENSOR: the forward operator runs the levels' plans
     DBuf<unsigned char> oz_x;  // fw_engine = FDS_FW_TENSOR: bf16 slices of the vectors
     DBuf<int> oz_colexp;

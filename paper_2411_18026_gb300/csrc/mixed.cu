@@ -88,14 +88,17 @@ __device__ __forceinline__ void put(const cplx &a, float4 &b) {
     b = make_float4(rh, ih, (float)(a.x - (double)rh), (float)(a.y - (double)ih));
 }
 
+// r = f - y for the compact columns c (right-hand side cmap[c]), leaf order,
+// with ||r||^2 and ||f||^2 per column
 template <class T, class LT>
 __global__ void k_residual(const int *__restrict__ gidx, int64_t D, const cplx *__restrict__ F, int64_t ldf,
-                           const T *__restrict__ Y, LT *R, double *norms) {
+                           const int *__restrict__ cmap, const T *__restrict__ Y, LT *R, double *norms) {
     const int c = blockIdx.y;
+    const int64_t fc = cmap[c];
     double rr = 0.0, ff = 0.0;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < D; q += (int64_t)gridDim.x * blockDim.x) {
         if (!FDS_IN_RANGE(gidx[q], D)) continue;
-        const cplx f = F[gidx[q] + c * ldf];
+        const cplx f = F[gidx[q] + fc * ldf];
         cplx r = f;
         if (Y) r = csub(f, to_c128(Y[q + c * D]));
         put(r, R[q + c * D]);
@@ -139,14 +142,22 @@ __global__ void k_undo_cols(cplx *X, const LT *__restrict__ dX, int64_t D, int c
     }
 }
 
-// natural-order vector <- leaf-order vector
+// dst column j = src column perm[j] (D entries per column)
+template <class T>
+__global__ void k_permute_cols(const T *__restrict__ src, T *dst, int64_t D, const int *__restrict__ perm, int cols) {
+    const int64_t n = D * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = src[e % D + (int64_t)perm[e / D] * D];
+}
+
+// natural-order right-hand side column cmap[c] <- leaf-order compact column c
 __global__ void k_leaf_scatter(const int *__restrict__ gidx, int64_t D, const cplx *__restrict__ X, cplx *out,
-                               int64_t ldo, int cols) {
+                               int64_t ldo, const int *__restrict__ cmap, int cols) {
     const int64_t tot = D * cols;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = e % D, c = e / D;
         if (!FDS_IN_RANGE(gidx[q], D)) continue;
-        out[gidx[q] + c * ldo] = X[q + c * D];
+        out[gidx[q] + (int64_t)cmap[c] * ldo] = X[q + c * D];
     }
 }
 
@@ -714,81 +725,116 @@ int solve_mixed(fds_handle *h, cplx *d_rhs, int nrhs, cudaStream_t s) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
+    if (h->wcmap.n < (size_t)ncmax) FDS_TRY(h->wcmap.alloc((size_t)ncmax));
+    if (refine && h->wperm.n < (size_t)D * ncmax * sizeof(cplx))
+        FDS_TRY(h->wperm.alloc((size_t)D * ncmax * sizeof(cplx)));
     for (int c0 = 0; c0 < nrhs; c0 += SOLVE_CHUNK) {
         const int nc = std::min(SOLVE_CHUNK, nrhs - c0);
         cplx *F = d_rhs + (int64_t)c0 * ld_rhs;
         const unsigned gx = (unsigned)std::min<int64_t>((D + 255) / 256, 64);
+        // the iterate's columns are kept with the columns still refining first:
+        // compact column j holds right-hand side cmap[j] of the chunk
+        std::vector<int> cmap(nc);
+        for (int c = 0; c < nc; ++c) cmap[c] = c;
+        FDS_CUDA_TRY(cudaMemcpyAsync(h->wcmap.p, cmap.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
         // x = sweep(f)
         FDS_CUDA_TRY(cudaMemsetAsync(h->wnorm.p, 0, sizeof(double) * 2 * nc, s));
         {
             ProfScope ps("a7.residual", s);
-            fds_count_launch(), k_residual<cplx, LT><<<dim3(gx, nc), 256, 0, s>>>(h->d_leaf_gidx.p, D, F, ld_rhs,
-                                                                              nullptr, leaf_in, h->wnorm.p);
+            fds_count_launch(), k_residual<cplx, LT><<<dim3(gx, nc), 256, 0, s>>>(
+                h->d_leaf_gidx.p, D, F, ld_rhs, h->wcmap.p, nullptr, leaf_in, h->wnorm.p);
         }
         FDS_CUDA_TRY(cudaGetLastError());
         FDS_TRY(sweep_chunk_run(h, nc, s));
         fds_count_launch(), k_update<LT><<<1024, 256, 0, s>>>(h->wX.p, leaf, D * nc, 1);
         FDS_CUDA_TRY(cudaGetLastError());
-        // refinement against the FP64 compressed operator; prevc[c] is the
-        // residual of column c before the latest correction
-        double prev = INFINITY;
+        // refinement against the FP64 compressed operator, column by column:
+        // a column stops when its residual meets ir_tol, stops contracting or
+        // the sweeps run out, and keeps the better of its last two iterates;
+        // the forward operator and the sweeps then run on the others only
+        int nact = nc;
         std::vector<double> prevc(nc, INFINITY), resc(nc, 0.0);
-        for (int it = 0; refine; ++it) {
+        for (int it = 0; refine && nact > 0; ++it) {
             if (ffp) {
-                fds_count_launch(), k_split<<<1024, 256, 0, s>>>(h->wX.p, h->wXp.p, D * nc);
-                FDS_TRY(forward_apply<float4>(h, h->wXp.p, Ypleaf, nc, s));
+                fds_count_launch(), k_split<<<1024, 256, 0, s>>>(h->wX.p, h->wXp.p, D * nact);
+                FDS_TRY(forward_apply<float4>(h, h->wXp.p, Ypleaf, nact, s));
             } else {
-                FDS_TRY(forward_apply<cplx>(h, h->wX.p, Yleaf, nc, s));
+                FDS_TRY(forward_apply<cplx>(h, h->wX.p, Yleaf, nact, s));
             }
-            FDS_CUDA_TRY(cudaMemsetAsync(h->wnorm.p, 0, sizeof(double) * 2 * nc, s));
+            FDS_CUDA_TRY(cudaMemsetAsync(h->wnorm.p, 0, sizeof(double) * 2 * nact, s));
             {
                 ProfScope ps("a7.residual", s);
                 if (ffp)
-                    fds_count_launch(), k_residual<float4, LT><<<dim3(gx, nc), 256, 0, s>>>(
-                        h->d_leaf_gidx.p, D, F, ld_rhs, Ypleaf, leaf_in, h->wnorm.p);
+                    fds_count_launch(), k_residual<float4, LT><<<dim3(gx, nact), 256, 0, s>>>(
+                        h->d_leaf_gidx.p, D, F, ld_rhs, h->wcmap.p, Ypleaf, leaf_in, h->wnorm.p);
                 else
-                    fds_count_launch(), k_residual<cplx, LT><<<dim3(gx, nc), 256, 0, s>>>(
-                        h->d_leaf_gidx.p, D, F, ld_rhs, Yleaf, leaf_in, h->wnorm.p);
+                    fds_count_launch(), k_residual<cplx, LT><<<dim3(gx, nact), 256, 0, s>>>(
+                        h->d_leaf_gidx.p, D, F, ld_rhs, h->wcmap.p, Yleaf, leaf_in, h->wnorm.p);
             }
             FDS_CUDA_TRY(cudaGetLastError());
-            FDS_CUDA_TRY(cudaMemcpyAsync(nrm.data(), h->wnorm.p, sizeof(double) * 2 * nc, cudaMemcpyDeviceToHost, s));
+            FDS_CUDA_TRY(cudaMemcpyAsync(nrm.data(), h->wnorm.p, sizeof(double) * 2 * nact, cudaMemcpyDeviceToHost, s));
             FDS_CUDA_TRY(cudaStreamSynchronize(s));
-            double res = 0;
-            for (int c = 0; c < nc; ++c) {
-                resc[c] = nrm[2 * c + 1] > 0 ? std::sqrt(nrm[2 * c] / nrm[2 * c + 1]) : 0.0;
-                if (!(resc[c] == resc[c])) return FDS_ERR_SINGULAR;
-                res = std::max(res, resc[c]);
-            }
-            // stop when converged, out of sweeps, or no longer contracting
-            if (res <= h->opt.ir_tol || it >= h->opt.ir_max_iter || res > 0.5 * prev) {
-                // keep, per column, the iterate with the smaller residual: a
-                // correction that made column c worse is taken back
-                std::vector<int> undo(nc, 0);
-                bool any = false;
-                double best = 0;
-                for (int c = 0; c < nc; ++c) {
-                    if (resc[c] > prevc[c]) undo[c] = 1, any = true;
-                    best = std::max(best, std::min(resc[c], prevc[c]));
+            std::vector<int> undo(nact, 0), keep, done;
+            bool any_undo = false;
+            for (int j = 0; j < nact; ++j) {
+                resc[j] = nrm[2 * j + 1] > 0 ? std::sqrt(nrm[2 * j] / nrm[2 * j + 1]) : 0.0;
+                if (!(resc[j] == resc[j])) return FDS_ERR_SINGULAR;
+                const bool stop = resc[j] <= h->opt.ir_tol || it >= h->opt.ir_max_iter || resc[j] > 0.5 * prevc[j];
+                if (!stop) {
+                    keep.push_back(j);
+                    continue;
                 }
-                if (any) {
-                    FDS_TRY(grow(h->wundo, (size_t)nc));
-                    FDS_CUDA_TRY(cudaMemcpyAsync(h->wundo.p, undo.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
-                    fds_count_launch(), k_undo_cols<LT><<<1024, 256, 0, s>>>(h->wX.p, leaf, D, nc, h->wundo.p);
-                    FDS_CUDA_TRY(cudaGetLastError());
-                    FDS_CUDA_TRY(cudaStreamSynchronize(s));   // undo[] is a host vector
-                }
+                // a correction that made the column worse is taken back
+                if (resc[j] > prevc[j]) undo[j] = 1, any_undo = true;
+                const double best = std::min(resc[j], prevc[j]);
                 worst = std::max(worst, best);
                 if (best > h->opt.ir_tol) converged = false;
                 iters = std::max(iters, it);
+                done.push_back(j);
+            }
+            if (any_undo) {
+                FDS_TRY(grow(h->wundo, (size_t)nact));
+                FDS_CUDA_TRY(cudaMemcpyAsync(h->wundo.p, undo.data(), sizeof(int) * nact, cudaMemcpyHostToDevice, s));
+                fds_count_launch(), k_undo_cols<LT><<<1024, 256, 0, s>>>(h->wX.p, leaf, D, nact, h->wundo.p);
+                FDS_CUDA_TRY(cudaGetLastError());
+            }
+            const int nkeep = (int)keep.size();
+            if (nkeep == 0) {
+                FDS_CUDA_TRY(cudaStreamSynchronize(s));   // undo[] is a host vector
                 break;
             }
-            prev = res;
-            prevc = resc;
-            FDS_TRY(sweep_chunk_run(h, nc, s));
-            fds_count_launch(), k_update<LT><<<1024, 256, 0, s>>>(h->wX.p, leaf, D * nc, 0);
+            if (nkeep < nact) {
+                // the refining columns first: permute the iterate, the residual and the maps
+                std::vector<int> perm(keep);
+                perm.insert(perm.end(), done.begin(), done.end());
+                std::vector<int> cm(nact);
+                std::vector<double> pr(nact);
+                for (int j = 0; j < nact; ++j) {
+                    cm[j] = cmap[perm[j]];
+                    pr[j] = resc[perm[j]];
+                }
+                std::copy(cm.begin(), cm.end(), cmap.begin());
+                std::copy(pr.begin(), pr.end(), resc.begin());
+                FDS_TRY(grow(h->wundo, (size_t)nact));
+                FDS_CUDA_TRY(cudaMemcpyAsync(h->wundo.p, perm.data(), sizeof(int) * nact, cudaMemcpyHostToDevice, s));
+                cplx *tx = reinterpret_cast<cplx *>(h->wperm.p);
+                fds_count_launch(), k_permute_cols<cplx><<<1024, 256, 0, s>>>(h->wX.p, tx, D, h->wundo.p, nact);
+                FDS_CUDA_TRY(cudaMemcpyAsync(h->wX.p, tx, sizeof(cplx) * D * nact, cudaMemcpyDeviceToDevice, s));
+                LT *tr = reinterpret_cast<LT *>(h->wperm.p);
+                fds_count_launch(), k_permute_cols<LT><<<1024, 256, 0, s>>>(leaf_in, tr, D, h->wundo.p, nkeep);
+                FDS_CUDA_TRY(cudaMemcpyAsync(leaf_in, tr, sizeof(LT) * D * nkeep, cudaMemcpyDeviceToDevice, s));
+                FDS_CUDA_TRY(cudaMemcpyAsync(h->wcmap.p, cmap.data(), sizeof(int) * nact, cudaMemcpyHostToDevice, s));
+                FDS_CUDA_TRY(cudaGetLastError());
+                FDS_CUDA_TRY(cudaStreamSynchronize(s));   // perm, cmap: host vectors
+            }
+            nact = nkeep;
+            for (int j = 0; j < nact; ++j) prevc[j] = resc[j];
+            FDS_TRY(sweep_chunk_run(h, nact, s));
+            fds_count_launch(), k_update<LT><<<1024, 256, 0, s>>>(h->wX.p, leaf, D * nact, 0);
             FDS_CUDA_TRY(cudaGetLastError());
         }
-        fds_count_launch(), k_leaf_scatter<<<1024, 256, 0, s>>>(h->d_leaf_gidx.p, D, h->wX.p, F, ld_rhs, nc);
+        fds_count_launch(), k_leaf_scatter<<<1024, 256, 0, s>>>(h->d_leaf_gidx.p, D, h->wX.p, F, ld_rhs, h->wcmap.p,
+                                                                 nc);
         FDS_CUDA_TRY(cudaGetLastError());
     }
     cudaEventRecord(e1, s);
