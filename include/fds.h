@@ -64,13 +64,13 @@ extern "C" {
 #define FDS_C64_TENSOR 1
 /* Engine of the refinement's forward operator (FDS_MIXED with
  * FDS_APPLY_FF): double-float products on the FP32 pipe, or the tensor cores
- * for the leaf diagonal blocks (leaves of at most 64 nodes), the sibling
- * blocks and the downward interpolation blocks, with the FP64 blocks and the
- * vectors cut into six bf16 slices each (per-row / per-column powers of
- * two), the 21 slice products with i + j <= 5 accumulated in fp32 tensor
- * memory (exact for the leading groups) and summed in float pairs: about
- * 2^-40 of |A| |x|, against 2^-44 for the double-float products.  The
- * upward interpolation blocks stay double-float. */
+ * for the leaf diagonal blocks (leaves of at most 64 nodes; larger ones stay
+ * double-float), the sibling blocks and the interpolation blocks, with the
+ * FP64 blocks and the vectors cut into six bf16 slices each (per-row /
+ * per-column powers of two), the 21 slice products with i + j <= 5
+ * accumulated in fp32 tensor memory (exact for the leading groups) and
+ * summed in float pairs: about 2^-40 of |A| |x|, against 2^-44 for the
+ * double-float products. */
 #define FDS_FW_FF     0
 #define FDS_FW_TENSOR 1
 
@@ -162,8 +162,8 @@ typedef struct {
                               needs a non-default stream (handles built by fds_build_batch
                               have one); default 0 */
     int32_t fw_engine;     /* FDS_MIXED: FDS_FW_FF (default) or FDS_FW_TENSOR for the leaf,
-                              sibling and downward interpolation blocks of the refinement's
-                              forward operator */
+                              sibling and interpolation blocks of the refinement's forward
+                              operator */
     int32_t merge_c64_levels; /* with merge_c64 = 1: only the lowest merge_c64_levels of the
                               complex64 levels are merged in complex64, the others in FP64;
                               0 (default): all of them */

@@ -183,7 +183,7 @@ struct Level {
     // fw_engine = FDS_FW_TENSOR: plans of the level's forward-operator
     // products on the tensor cores (one entry per K pass): downward
     // interpolation (T^cH) and sibling blocks
-    std::vector<OzPlan> oz_down, oz_sib;
+    std::vector<OzPlan> oz_up, oz_down, oz_sib;
     std::vector<int64_t> toff_h;   // host copy of the T^c block offsets
     int srmax = 0;
     double sum_s2 = 0;            // sum over cells of 2 r_a r_b

@@ -374,7 +374,12 @@ int forward_apply(fds_handle *h, const T *X, T *Y, int nc, cudaStream_t s) {
         {
             ProfScope pv("a7.fw_interp_up", s);
             pv.flops = 8.0 * C.sum_tm * nc;
-            FDS_TRY(apply_V<T>(h, C, F::Tm(C), xl, C.D, wt[l].p, ldr, nc, s));
+            if (tc) {
+                FDS_TRY(vskel(C, 0, xl, C.D, wt[l].p, ldr, nc, s));
+                FDS_TRY(oz_run(h, C.oz_up, xl, C.D, wt[l].p, ldr, nc, s));
+            } else {
+                FDS_TRY(apply_V<T>(h, C, F::Tm(C), xl, C.D, wt[l].p, ldr, nc, s));
+            }
         }
         T *par = (l - 1 > l0) ? wz[l - 1].p : F::xtop(h).p;
         const int64_t ldp = (l - 1 > l0) ? Pn.D : h->Dtop;
@@ -479,11 +484,10 @@ int fds_keep_blocks(const Level &Lv, DBuf<cplx> &dst, DBuf<MatRef> &rdst, cudaSt
     return make_refs_t(rdst, dst.p, Lv.offA, d, d, s);
 }
 
-// Tensor-core products of level C: the plan of its downward interpolation
-// blocks (y[other rows] = T^cH t) and, at the leaf level, the slices of its
-// diagonal blocks for the leaf kernel.  The upward blocks T^c (k_c rows,
-// typically 30-100) stay double-float: on the 128-row tensor-core tiles they
-// measured no faster.
+// Tensor-core products of level C: the plans of its interpolation blocks
+// (up: out[skeleton rows] += T^c x[other rows]; down: y[other rows] =
+// T^cH t) and, at the leaf level, the slices of its diagonal blocks for the
+// leaf kernel.
 int oz_interp_leaf_plans(fds_handle *h, Level &C, bool leaf, cudaStream_t s, int64_t &bytes) {
     std::vector<int> vmap(C.D);
     for (int b = 0; b < C.nb; ++b)
@@ -491,7 +495,8 @@ int oz_interp_leaf_plans(fds_handle *h, Level &C, bool leaf, cudaStream_t s, int
             const int n = c ? C.n2[b] : C.n1[b], coff = c ? C.n1[b] : 0;
             for (int q = 0; q < n; ++q) vmap[C.doff[b] + coff + q] = coff + C.perm[C.permoff[2 * b + c] + q];
         }
-    std::vector<OzSpec> down;
+    std::vector<OzSpec> up, down;
+    up.reserve(2 * (size_t)C.nb);
     down.reserve(2 * (size_t)C.nb);
     for (int b = 0; b < C.nb; ++b)
         for (int c = 0; c < 2; ++c) {
@@ -501,7 +506,15 @@ int oz_interp_leaf_plans(fds_handle *h, Level &C, bool leaf, cudaStream_t s, int
             OzSpec q;
             q.a = C.T.p + C.toff_h[2 * b + c];
             q.lda = std::max(k, 1);
+            q.op = 0;              // out (k rows) += T (k x m) x[rest]
+            q.m = k;
+            q.k = m;
+            q.x_row = C.doff[b];
+            q.xmap = vm + k;
+            q.y_row = C.roff[b] + (c ? C.k1[b] : 0);
+            up.push_back(q);
             q.op = 1;              // y[rest] (m rows) = T^H (m x k) t
+            q.xmap = nullptr;
             q.m = m;
             q.k = k;
             q.x_row = C.roff[b] + (c ? C.k1[b] : 0);
@@ -510,8 +523,10 @@ int oz_interp_leaf_plans(fds_handle *h, Level &C, bool leaf, cudaStream_t s, int
             q.set = true;
             down.push_back(q);
         }
+    FDS_TRY(oz_plan_build(up, C.oz_up, s));
     FDS_TRY(oz_plan_build(down, C.oz_down, s));
-    for (const OzPlan &P : C.oz_down) bytes += (int64_t)(P.aslices.bytes() + P.rowexp.bytes());
+    for (auto *v : {&C.oz_up, &C.oz_down})
+        for (const OzPlan &P : *v) bytes += (int64_t)(P.aslices.bytes() + P.rowexp.bytes());
     if (leaf && C.dmax <= 128) {   // larger leaves stay double-float
         FDS_TRY(oz_leaf_prepare(C, C.rDfw.p, s));
         bytes += (int64_t)(C.oz_a.bytes() + C.oz_rowexp.bytes());
