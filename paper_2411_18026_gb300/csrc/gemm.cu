@@ -179,8 +179,9 @@ __global__ void __launch_bounds__(NT) k_gemm_rt(const MatRefT<typename Ar::G> *_
     constexpr int BN = 16 * TJ, BMt = 16 * MI;
     const int i0 = (blockIdx.x % tiles_m) * BMt, j0 = (blockIdx.x / tiles_m) * BN;
     if (i0 >= M || j0 >= N) return;
-    __shared__ SA sa[BK][BMt];
-    __shared__ SB sb[BK][16 * TJ];
+    // rows padded by one element: the staging stores walk K across threads
+    __shared__ SA sa[BK][BMt + 1];
+    __shared__ SB sb[BK][16 * TJ + 1];
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
     typename Ar::Acc acc[MI][TJ];
 #pragma unroll
@@ -265,8 +266,9 @@ __global__ void __launch_bounds__(NT) k_gemm_c64_async(const MatRefT<cplxf> *__r
     constexpr int BN = 16 * TJ, BMt = 16 * MI;
     const int i0 = (blockIdx.x % tiles_m) * BMt, j0 = (blockIdx.x / tiles_m) * BN;
     if (i0 >= M || j0 >= N) return;
-    __shared__ __align__(16) cplxf sa[2][BK][BMt];
-    __shared__ __align__(16) cplxf sb[2][BK][16 * TJ];
+    // rows padded by one element: the B copies walk K across threads
+    __shared__ __align__(16) cplxf sa[2][BK][BMt + 1];
+    __shared__ __align__(16) cplxf sb[2][BK][16 * TJ + 1];
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
     auto issue = [&](int k0, int buf) {
 #pragma unroll
