@@ -237,3 +237,51 @@ def test_refinement_returns_the_smallest_residual_reached():
     floor = min(res)
     assert all(b <= 1.1 * a or b <= 2 * floor for a, b in zip(res, res[1:])), res
     assert 0 < res[-1] < 1e-9 and res[-1] <= 2 * floor
+
+
+def test_complex64_merge_newton_steps_reach_fp64_quality():
+    # the Newton steps of the complex64 merge: one correction sweep reaches
+    # the residual of the FP64-merged factors (measured ~5e-9 at 2^20
+    # unknowns; without the steps ~1e-5 after one correction)
+    torch_cuda()
+    fds = fdslib()
+    xy = workloads.star(16384, 0.2, 5)
+    omega = workloads.omega_for_kTa(15.0)
+    kinds, ang = workloads.plane_wave_set(4)
+    res = {}
+    for merge in (True, False):
+        h = fds.fds_build(xy, omega, 2.0, 1.0, 1e-9, precision=fds.FDS_MIXED, ir_tol=1e-14, ir_max_iter=1,
+                          merge_c64=merge)
+        F = fds.fds_rhs_plane_wave(h, kinds, ang)
+        with pytest.raises(fds.FdsError):
+            fds.fds_solve(h, F)          # a target of 1e-14 is out of reach in one sweep
+        res[merge] = fds.fds_stats_get(h).ir_residual
+        h.close()
+    assert res[True] <= 1e-8, res
+    assert res[True] <= 4 * res[False], res
+
+
+def test_per_column_refinement_mixed_convergence():
+    # columns that converge at once (zero right-hand side), after one sweep
+    # and (with a tight tolerance) later are refined independently: every
+    # column matches the FP64 solve, the zero column stays exactly zero
+    torch_cuda()
+    fds = fdslib()
+    xy = workloads.star(4096, 0.25, 6, rot=0.4)
+    omega = workloads.omega_for_kTa(12.0)
+    h64, hmx = _pair(fds, xy, omega, 1e-9)
+    hmx.close()
+    hmx = fds.fds_build(xy, omega, 2.0, 1.0, 1e-9, precision=fds.FDS_MIXED, ir_tol=1e-11, merge_c64=True)
+    kinds, ang = workloads.plane_wave_set(150)            # 300 columns: a full chunk and a ragged one
+    F = fds.fds_rhs_plane_wave(h64, kinds, ang)
+    F[:, 7] = 0.0
+    F[:, 260] *= 1e-6                                     # scaled: same relative residuals
+    x64 = fds.fds_solve(h64, F)
+    xm = fds.fds_solve(hmx, F)
+    st = fds.fds_stats_get(hmx)
+    assert st.ir_residual <= 1e-11
+    assert np.all(xm[:, 7] == 0)
+    cols = [c for c in range(F.shape[1]) if c != 7]
+    assert _colmax(xm[:, cols], x64[:, cols]) < 1e-8
+    h64.close()
+    hmx.close()
