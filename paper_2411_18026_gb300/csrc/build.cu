@@ -1088,12 +1088,13 @@ int fds_build_impl(fds_handle *h) {
         FDS_TRY(d_sp.upload(spoff, s));
         FDS_TRY(info2.alloc(nb));
         if (merge64) {
-            // complex64 LU of the level's blocks for first inverses, each
-            // refined by one Newton step whose residual is formed in
-            // double-float arithmetic (float pairs on the FP32 pipe):
+            // first inverses in complex64 (Gauss-Jordan in shared memory for
+            // blocks of order <= GJ_MAX_N, else LU and solves), each refined
+            // by one Newton step whose residual is formed in double-float
+            // arithmetic (float pairs on the FP32 pipe):
             //   X1 = X0 + X0 (I - A X0)   against the FP64 blocks A,
             //   W = X1 V^H, S = V W       (complex64),
-            //   A~ = Y0 + Y0 (I - S Y0)   Y0 from a complex64 LU of S.
+            //   A~ = Y0 + Y0 (I - S Y0)   Y0 a complex64 inverse of S.
             // The refined inverses, rounded to complex64 for the sweep, are as
             // accurate as FP64 ones rounded (without the steps the first
             // solve's residual is ~1000x larger and the refinement needs one
@@ -1138,14 +1139,19 @@ int fds_build_impl(fds_handle *h) {
             fds_count_launch(), k_cast<cplx, cplxf><<<1024, 256, 0, s>>>(C.V.p, C.Vf.p, nV);
             fds_count_launch(), k_to_ff<cplx><<<1024, 256, 0, s>>>(C.LU.p, Ap.p, nA);
             FDS_CUDA_TRY(cudaGetLastError());
-            {
-                ProfScope ps("a3.merge_lu", s);
-                ps.flops = fl_lu;
-                FDS_TRY(dense_lu(nb, C.dmax, rLUf.p, C.piv.p, C.d_offpiv.p, info.p, s));
-            }
-            fds_count_launch(), k_set_identity<cplxf><<<nb, 256, 0, s>>>(C.rAinvf.p);
-            FDS_CUDA_TRY(cudaGetLastError());
-            {
+            if (C.dmax <= GJ_MAX_N) {
+                // the first inverse by Gauss-Jordan in shared memory (no LU is kept)
+                ProfScope ps("a3.merge_a_inverse", s);
+                ps.flops = fl_lu * 3.0;
+                FDS_TRY(dense_inverse_gj(nb, C.dmax, rLUf.p, C.rAinvf.p, info.p, s));
+            } else {
+                {
+                    ProfScope ps("a3.merge_lu", s);
+                    ps.flops = fl_lu;
+                    FDS_TRY(dense_lu(nb, C.dmax, rLUf.p, C.piv.p, C.d_offpiv.p, info.p, s));
+                }
+                fds_count_launch(), k_set_identity<cplxf><<<nb, 256, 0, s>>>(C.rAinvf.p);
+                FDS_CUDA_TRY(cudaGetLastError());
                 ProfScope ps("a3.merge_a_inverse", s);
                 ps.flops = fl_lu * 3.0;
                 FDS_TRY(dense_lu_solve(nb, C.dmax, C.dmax, rLUf.p, C.piv.p, C.d_offpiv.p, C.rAinvf.p, s));
@@ -1183,14 +1189,18 @@ int fds_build_impl(fds_handle *h) {
                 fds_count_launch(), k_to_ff<cplxf><<<1024, 256, 0, s>>>(Sf.p, Sp.p, nS);
                 FDS_CUDA_TRY(cudaGetLastError());
             }
-            {
-                ProfScope ps("a3.merge_s_lu", s);
-                ps.flops = fl_slu;
-                FDS_TRY(dense_lu(nb, C.rmax, rSf.p, spiv.p, d_sp.p, info2.p, s));
-            }
-            fds_count_launch(), k_set_identity<cplxf><<<nb, 256, 0, s>>>(C.rAtf.p);
-            FDS_CUDA_TRY(cudaGetLastError());
-            {
+            if (C.rmax <= GJ_MAX_N) {
+                ProfScope ps("a3.merge_inverse", s);
+                ps.flops = fl_at + fl_slu;
+                FDS_TRY(dense_inverse_gj(nb, C.rmax, rSf.p, C.rAtf.p, info2.p, s));
+            } else {
+                {
+                    ProfScope ps("a3.merge_s_lu", s);
+                    ps.flops = fl_slu;
+                    FDS_TRY(dense_lu(nb, C.rmax, rSf.p, spiv.p, d_sp.p, info2.p, s));
+                }
+                fds_count_launch(), k_set_identity<cplxf><<<nb, 256, 0, s>>>(C.rAtf.p);
+                FDS_CUDA_TRY(cudaGetLastError());
                 ProfScope ps("a3.merge_inverse", s);
                 ps.flops = fl_at;
                 FDS_TRY(dense_lu_solve(nb, C.rmax, C.rmax, rSf.p, spiv.p, d_sp.p, C.rAtf.p, s));

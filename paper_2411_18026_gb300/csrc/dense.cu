@@ -279,6 +279,105 @@ int dense_lu(int batch, int max_n, const MatRef *d_A, int *d_piv, const int64_t 
     FDS_CUDA_TRY(cudaGetLastError());
     return FDS_OK;
 }
+// In-place Gauss-Jordan inversion with partial (row) pivoting of each
+// complex64 block A[b] (n x n, n <= GJ_MAX_N), held in shared memory by one
+// CTA: per step k the pivot row (largest |a_ik|, i >= k) is swapped to k,
+// row k becomes its scaled self with 1 / a_kk on the diagonal, every other
+// row i loses a_ik times it and gets -a_ik / a_kk in column k; the row swaps
+// are undone as column swaps in reverse order at the end.  X[b] = A[b]^{-1};
+// info[b] = first step with a zero or non-finite pivot (0: none).
+constexpr int GJ_THREADS = 1024;
+__global__ void __launch_bounds__(GJ_THREADS) k_gj_inverse(const MatRefF *__restrict__ As,
+                                                          const MatRefF *__restrict__ Xs, int *info) {
+    extern __shared__ cplxf gj[];
+    const MatRefF A = As[blockIdx.x], X = Xs[blockIdx.x];
+    const int n = A.rows, ld = n + 1;   // padded columns
+    cplxf *a = gj;                       // n x n, column-major, leading dimension ld
+    cplxf *fcol = a + (size_t)ld * n;    // column k before the step
+    cplxf *rowk = fcol + n;              // row k after the step
+    int *perm = reinterpret_cast<int *>(rowk + n);
+    __shared__ int s_p, s_bad;
+    __shared__ cplxf s_inv;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < n * n; e += blockDim.x) {
+        const int i = e % n, j = e / n;
+        a[i + j * ld] = A.p[i + (int64_t)j * A.ld];
+    }
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (tid < 32) {
+            float best = -1.f;
+            int bi = k;
+            for (int i = k + tid; i < n; i += 32) {
+                const float v = cabs2(a[i + k * ld]);
+                if (v > best) { best = v; bi = i; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float v2 = __shfl_xor_sync(0xffffffffu, best, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+            }
+            if (tid == 0) {
+                s_p = bi;
+                perm[k] = bi;
+            }
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != k)
+            for (int j = tid; j < n; j += blockDim.x) {
+                const cplxf t = a[k + j * ld];
+                a[k + j * ld] = a[p + j * ld];
+                a[p + j * ld] = t;
+            }
+        __syncthreads();
+        if (tid == 0) {
+            const cplxf d = a[k + k * ld];
+            const double m = (double)d.x * d.x + (double)d.y * d.y;
+            cplxf inv = mkcf(0.f, 0.f);
+            if (m > 0.0 && isfinite(m)) inv = mkcf((float)(d.x / m), (float)(-d.y / m));
+            else if (!s_bad) s_bad = k + 1;
+            s_inv = inv;
+        }
+        __syncthreads();
+        const cplxf inv = s_inv;
+        for (int t = tid; t < 2 * n; t += blockDim.x) {
+            if (t < n) fcol[t] = t == k ? mkcf(0.f, 0.f) : a[t + k * ld];
+            else {
+                const int j = t - n;
+                rowk[j] = j == k ? inv : cmul(a[k + j * ld], inv);
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < n * n; e += blockDim.x) {
+            const int i = e % n, j = e / n;
+            cplxf &v = a[i + j * ld];
+            if (i == k) v = rowk[j];
+            else if (j == k) v = cmul(mkcf(-fcol[i].x, -fcol[i].y), inv);
+            else cfms(v, fcol[i], rowk[j]);
+        }
+        __syncthreads();
+    }
+    // the row swaps of step k become a swap of columns k and perm[k], in reverse order
+    for (int k = n - 1; k >= 0; --k) {
+        const int p = perm[k];
+        if (p != k)
+            for (int i = tid; i < n; i += blockDim.x) {
+                const cplxf t = a[i + k * ld];
+                a[i + k * ld] = a[i + p * ld];
+                a[i + p * ld] = t;
+            }
+        __syncthreads();
+    }
+    for (int e = tid; e < n * n; e += blockDim.x) {
+        const int i = e % n, j = e / n;
+        X.p[i + (int64_t)j * X.ld] = a[i + j * ld];
+    }
+    if (tid == 0) info[blockIdx.x] = s_bad;
+}
+
 int dense_lu(int batch, int max_n, const MatRefF *d_A, int *d_piv, const int64_t *d_poff, int *d_info,
              cudaStream_t s) {
     if (batch <= 0) return FDS_OK;
@@ -450,4 +549,14 @@ extern "C" int fds_lu_batched_noalloc(int32_t batch, const int32_t *d_d, const i
     fds_count_launch(), k_make_refs<<<(batch + 127) / 128, 128, 0, s>>>(batch, d_d, d_off, d_A, refs);
     FDS_CUDA_TRY(cudaGetLastError());
     return dense_lu(batch, 0, refs, d_piv, d_poff, d_info, s);
+}
+
+int dense_inverse_gj(int batch, int max_n, const MatRefF *d_A, const MatRefF *d_X, int *d_info, cudaStream_t s) {
+    if (batch <= 0) return FDS_OK;
+    if (max_n < 1 || max_n > GJ_MAX_N) return FDS_ERR_ARG;
+    const size_t smem = sizeof(cplxf) * ((size_t)(max_n + 1) * max_n + 2 * max_n) + sizeof(int) * max_n;
+    FDS_TRY(ensure_dyn_smem(k_gj_inverse, smem));
+    fds_count_launch(), k_gj_inverse<<<batch, GJ_THREADS, smem, s>>>(d_A, d_X, d_info);
+    FDS_CUDA_TRY(cudaGetLastError());
+    return FDS_OK;
 }

@@ -67,6 +67,11 @@ int dense_lu_blocked(int n, cplx *A, int ld, int *d_piv, int *d_info, cudaStream
 int tc_status_take(cudaStream_t s, int *status);
 // Arms (1) or clears (0) the injected stall of the next complex64 tensor-core GEMM launch.
 int tc_fault_arm(int on);
+// X[b] = A[b]^{-1} for complex64 blocks of order n <= GJ_MAX_N by Gauss-Jordan
+// elimination with row pivoting in shared memory (one CTA per block; A is
+// read, not changed); info[b] as for dense_lu.  FDS_ERR_ARG for max_n > GJ_MAX_N.
+constexpr int GJ_MAX_N = 160;
+int dense_inverse_gj(int batch, int max_n, const MatRefF *d_A, const MatRefF *d_X, int *d_info, cudaStream_t s);
 // complex64 versions (mixed-precision merge and sweep)
 int dense_lu(int batch, int max_n, const MatRefF *d_A, int *d_piv, const int64_t *d_poff, int *d_info,
              cudaStream_t s);
