@@ -283,8 +283,9 @@ int dense_lu(int batch, int max_n, const MatRef *d_A, int *d_piv, const int64_t 
 // complex64 block A[b] (n x n, n <= GJ_MAX_N), held in shared memory by one
 // CTA: per step k the pivot row (largest |a_ik|, i >= k) is swapped to k,
 // row k becomes its scaled self with 1 / a_kk on the diagonal, every other
-// row i loses a_ik times it and gets -a_ik / a_kk in column k; the row swaps
-// are undone as column swaps in reverse order at the end.  X[b] = A[b]^{-1};
+// row i loses a_ik times it and gets -a_ik / a_kk in column k (three
+// barriers per step: pivot search, the staged column / rows, the update);
+// the row swaps are undone as column swaps in reverse order at the end.  X[b] = A[b]^{-1};
 // info[b] = first step with a zero or non-finite pivot (0: none).
 constexpr int GJ_THREADS = 1024;
 __global__ void __launch_bounds__(GJ_THREADS) k_gj_inverse(const MatRefF *__restrict__ As,
@@ -295,9 +296,9 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gj_inverse(const MatRefF *__rest
     cplxf *a = gj;                       // n x n, column-major, leading dimension ld
     cplxf *fcol = a + (size_t)ld * n;    // column k before the step
     cplxf *rowk = fcol + n;              // row k after the step
-    int *perm = reinterpret_cast<int *>(rowk + n);
+    cplxf *rowold = rowk + n;            // row k before the step
+    int *perm = reinterpret_cast<int *>(rowold + n);
     __shared__ int s_p, s_bad;
-    __shared__ cplxf s_inv;
     const int tid = threadIdx.x;
     for (int e = tid; e < n * n; e += blockDim.x) {
         const int i = e % n, j = e / n;
@@ -325,38 +326,42 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gj_inverse(const MatRefF *__rest
             }
         }
         __syncthreads();
+        // the swap of rows k and p is folded into the two phases below: row
+        // k's new values come from row p, row p's from the saved old row k
         const int p = s_p;
-        if (p != k)
-            for (int j = tid; j < n; j += blockDim.x) {
-                const cplxf t = a[k + j * ld];
-                a[k + j * ld] = a[p + j * ld];
-                a[p + j * ld] = t;
-            }
-        __syncthreads();
-        if (tid == 0) {
-            const cplxf d = a[k + k * ld];
-            const double m = (double)d.x * d.x + (double)d.y * d.y;
-            cplxf inv = mkcf(0.f, 0.f);
-            if (m > 0.0 && isfinite(m)) inv = mkcf((float)(d.x / m), (float)(-d.y / m));
-            else if (!s_bad) s_bad = k + 1;
-            s_inv = inv;
-        }
-        __syncthreads();
-        const cplxf inv = s_inv;
-        for (int t = tid; t < 2 * n; t += blockDim.x) {
-            if (t < n) fcol[t] = t == k ? mkcf(0.f, 0.f) : a[t + k * ld];
-            else {
-                const int j = t - n;
-                rowk[j] = j == k ? inv : cmul(a[k + j * ld], inv);
+        const cplxf d = a[p + k * ld];
+        const float m = d.x * d.x + d.y * d.y;
+        const bool ok = m > 0.f && isfinite(m);
+        const cplxf inv = ok ? mkcf(d.x / m, -d.y / m) : mkcf(0.f, 0.f);
+        if (tid == 0 && !ok && !s_bad) s_bad = k + 1;
+        for (int t = tid; t < 3 * n; t += blockDim.x) {
+            if (t < n) {
+                const int r = t == k ? p : (t == p ? k : t);   // row t after the swap
+                fcol[t] = t == k ? mkcf(0.f, 0.f) : a[r + k * ld];
+            } else if (t < 2 * n) {
+                const int c = t - n;
+                rowk[c] = c == k ? inv : cmul(a[p + c * ld], inv);
+            } else {
+                const int c = t - 2 * n;
+                rowold[c] = a[k + c * ld];
             }
         }
         __syncthreads();
         for (int e = tid; e < n * n; e += blockDim.x) {
-            const int i = e % n, j = e / n;
-            cplxf &v = a[i + j * ld];
-            if (i == k) v = rowk[j];
-            else if (j == k) v = cmul(mkcf(-fcol[i].x, -fcol[i].y), inv);
-            else cfms(v, fcol[i], rowk[j]);
+            const int i = e % n, c = e / n;
+            cplxf &v = a[i + c * ld];
+            if (i == k) {
+                v = rowk[c];
+            } else {
+                const cplxf base = (i == p) ? rowold[c] : v;
+                if (c == k) {
+                    v = cmul(mkcf(-fcol[i].x, -fcol[i].y), inv);
+                } else {
+                    cplxf w = base;
+                    cfms(w, fcol[i], rowk[c]);
+                    v = w;
+                }
+            }
         }
         __syncthreads();
     }
@@ -554,7 +559,7 @@ extern "C" int fds_lu_batched_noalloc(int32_t batch, const int32_t *d_d, const i
 int dense_inverse_gj(int batch, int max_n, const MatRefF *d_A, const MatRefF *d_X, int *d_info, cudaStream_t s) {
     if (batch <= 0) return FDS_OK;
     if (max_n < 1 || max_n > GJ_MAX_N) return FDS_ERR_ARG;
-    const size_t smem = sizeof(cplxf) * ((size_t)(max_n + 1) * max_n + 2 * max_n) + sizeof(int) * max_n;
+    const size_t smem = sizeof(cplxf) * ((size_t)(max_n + 1) * max_n + 3 * max_n) + sizeof(int) * max_n;
     FDS_TRY(ensure_dyn_smem(k_gj_inverse, smem));
     fds_count_launch(), k_gj_inverse<<<batch, GJ_THREADS, smem, s>>>(d_A, d_X, d_info);
     FDS_CUDA_TRY(cudaGetLastError());
