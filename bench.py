@@ -10,9 +10,11 @@ r(t) = 1 + 0.2 cos 5t with 2^19 nodes (2^20 complex unknowns), lambda = 2,
 mu = 1, rho = 1, k_T a = 20, leaf 64, l0 = 1, ID tolerance 1e-9 at the leaves
 and halved per level up, 1000 right-hand sides (plane P and SV waves at 500
 angles), learned rank (the trained network sizes a sketched ID, adaptive
-CPQR as fallback), mixed precision (complex64 merges and sweep of the lower
-tree levels, double-float sweep of the upper ones, refined against the FP64
-compressed operator to max_c ||f - A x|| / ||f|| <= 1e-8).  After the timed
+CPQR as fallback), mixed precision (complex64 merges with Newton-refined
+inverses and complex64 sweep of the lower tree levels, double-float sweep of
+the upper ones, refined column by column against the FP64 compressed
+operator, whose block products run on the tensor cores, to
+||f - A x|| / ||f|| <= 1e-8).  After the timed
 steps one plain-FP64 step (adaptive CPQR, FP64 merges and sweep) runs on the
 same inputs: its build and solve times and the relative error between the
 two solutions are reported beside the headline.  The working set (factors, vectors) is far larger than L2, so no
@@ -64,8 +66,8 @@ def parse():
                    help="ID tolerance eps at the leaves, eps * decay^(L-l) at level l (1: the paper's single eps)")
     p.add_argument("--autotune", action="store_true", help="GEMM tile shapes from the autotuner (tuned in warm-up)")
     p.add_argument("--fw-engine", default="tensor", choices=["ff", "tensor"],
-                   help="mixed: leaf blocks of the refinement's forward operator on the tensor cores (default, six "
-                        "bf16 slices per FP64 operand) or as double-float products (ff)")
+                   help="mixed: the refinement's forward operator (leaf, sibling and interpolation blocks) on the "
+                        "tensor cores (default, six bf16 slices per FP64 operand) or as double-float products (ff)")
     p.add_argument("--c64-engine", default="simt", choices=["tensor", "simt"],
                    help="complex64 products on the tensor cores (bf16 pieces) or the FP32 pipe")
     p.add_argument("--sweep-ff", type=int, default=1, choices=[0, 1, 2],
@@ -240,14 +242,16 @@ def run_reference(args):
     from oracle import build as ob
     ob.build()
     cores = os.cpu_count()
-    n_s = 384
+    # the sample of the bench's cpu_baseline leg (1024 nodes, 8 waves): large
+    # enough that the LU time follows its O(N^3) law, a few seconds per step
+    n_s = 1024
     for _ in range(args.warmup):
-        oracle_sample(args, n_s, 4)
+        oracle_sample(args, n_s, 8)
     vals = []
     t0 = time.perf_counter()
     last = None
     for _ in range(args.steps):
-        last = oracle_sample(args, n_s, 4)
+        last = oracle_sample(args, n_s, 8)
         vals.append(last["full_s"])
     wall = time.perf_counter() - t0
     v = float(np.median(vals))
